@@ -1,0 +1,95 @@
+"""Separable C-form preconditioner and the H^2 form B (oracle, FP64).
+
+Test infrastructure only (see the package docstring).
+
+Section 5.2.1: on the master cube the preconditioner corresponds to the form
+C(u) = int_Q (u_11^2 + u_22^2 + u_33^2 + u_1^2 + u_2^2 + u_3^2 + u^2) (eq. 5.19),
+spectrally equivalent to B(u) = ||u||_{H^2(Q)}^2 (eq. 5.7/5.9).  With the 1-D
+forms E(v) = int (v'')^2 + (v')^2 and F(v) = int v^2 (eq. 5.11/5.12) and the
+generalised eigenpairs (E - mu F) b = 0, b_i^T F b_j = delta_ij (eq. 5.15/5.16),
+C is diagonal in the tensor eigenbasis with eigenvalues mu_i + mu_j + mu_k + 1
+(eq. 5.20), so C^{-1} r costs O(W^4).
+
+Reading: every 1-D integral is evaluated with the (W+1)-point GLL rule on the
+nodal grid (so F = diag(w)); in B each mixed second derivative is counted once.
+With exactly these conventions Table 5.1 is reproduced to 1e-12 (tests).
+"""
+from __future__ import annotations
+
+from functools import lru_cache
+
+import numpy as np
+import scipy.linalg as sla
+
+from .gll import diff_matrix, gll
+
+
+@lru_cache(maxsize=None)
+def one_d_forms(W: int):
+    """E and F of eq. (5.11)-(5.14) in the nodal GLL basis, (W+1)-point quadrature."""
+    x, w = gll(W + 1)
+    D1 = diff_matrix(x)
+    D2 = D1 @ D1
+    Wd = np.diag(w)
+    E = D2.T @ Wd @ D2 + D1.T @ Wd @ D1
+    F = Wd
+    return E, F, D1, D2, Wd
+
+
+@lru_cache(maxsize=None)
+def eigenbasis(W: int):
+    """(mu, S): E S = F S diag(mu), S^T F S = I (eq. 5.15/5.16)."""
+    E, F, *_ = one_d_forms(W)
+    mu, S = sla.eigh(E, F)
+    return mu, S
+
+
+def kron3(a, b, c):
+    return np.kron(a, np.kron(b, c))
+
+
+def dense_C(W: int):
+    """C of eq. (5.19) as a (W+1)^3 matrix on u[k,j,i] flattened (x fastest)."""
+    E, F, *_ = one_d_forms(W)
+    # ordering kron(z-part, y-part, x-part) matches the flattening of u[k, j, i]
+    return kron3(F, F, E) + kron3(F, E, F) + kron3(E, F, F) + kron3(F, F, F)
+
+
+def dense_B(W: int):
+    """B = ||u||_{H^2(Q)}^2 (eq. 5.9): all |alpha| <= 2, each multi-index once."""
+    _, _, D1, D2, Wd = one_d_forms(W)
+    I = np.eye(W + 1)
+    ops = {0: I, 1: D1, 2: D2}
+    alphas = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (0, 2, 0),
+              (0, 0, 2), (1, 1, 0), (1, 0, 1), (0, 1, 1)]
+    Wq = kron3(Wd, Wd, Wd)
+    B = np.zeros(((W + 1) ** 3,) * 2)
+    for ax, ay, az in alphas:
+        G = kron3(ops[az], ops[ay], ops[ax])
+        B += G.T @ Wq @ G
+    return B
+
+
+def kappa_C_B(W: int) -> float:
+    """Condition number of C^{-1} B (the quantity of Table 5.1)."""
+    ev = sla.eigh(dense_B(W), dense_C(W), eigvals_only=True)
+    return float(ev.max() / ev.min())
+
+
+def apply_Cinv_block(r, W: int):
+    """z = C^{-1} r for one element block r[k, j, i] by fast diagonalisation."""
+    mu, S = eigenbasis(W)
+    t = np.einsum("kc,jb,ia,kji->cba", S, S, S, r, optimize=True)
+    sig = mu[:, None, None] + mu[None, :, None] + mu[None, None, :] + 1.0
+    t = t / sig
+    return np.einsum("kc,jb,ia,cba->kji", S, S, S, t, optimize=True)
+
+
+def apply_Cinv(disc, R):
+    """Block-diagonal preconditioner on every element of an oracle Discretisation."""
+    Z = np.zeros_like(R)
+    for e in range(disc.E):
+        P = disc.P[e]
+        blk = R[disc.off[e]:disc.off[e + 1]].reshape(P, P, P)
+        Z[disc.off[e]:disc.off[e + 1]] = apply_Cinv_block(blk, disc.W[e]).ravel()
+    return Z

@@ -1,0 +1,61 @@
+"""Pins for the C-form preconditioner (eq. 5.11-5.20) against Table 5.1."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle.precond import apply_Cinv_block, dense_C, eigenbasis, kappa_C_B, one_d_forms
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "table5_1_kappa.txt")
+
+
+def table5_1():
+    rows = {}
+    for line in open(GOLD):
+        if line.startswith("#") or not line.strip():
+            continue
+        W, k = line.split()
+        rows[int(W)] = float(k)
+    return rows
+
+
+@pytest.mark.parametrize("W", [2, 4, 6, 8, 10])
+def test_table_5_1(W):
+    kappa = kappa_C_B(W)
+    ref = table5_1()[W]
+    # the table prints 15 significant digits; W=2 is printed as 3.69999999999999
+    assert abs(kappa - ref) < 1e-9 * ref, (W, kappa, ref)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("W", [12])
+def test_table_5_1_large(W):
+    kappa = kappa_C_B(W)
+    ref = table5_1()[W]
+    assert abs(kappa - ref) < 1e-9 * ref, (W, kappa, ref)
+
+
+@pytest.mark.parametrize("W", [2, 5, 8])
+def test_eigen_identities(W):
+    E, F, *_ = one_d_forms(W)
+    mu, S = eigenbasis(W)
+    assert np.allclose(S.T @ F @ S, np.eye(W + 1), atol=1e-11)
+    assert np.allclose(S.T @ E @ S, np.diag(mu), atol=1e-9 * mu.max())
+    assert mu.min() > -1e-10 and abs(mu[0]) < 1e-9 * mu.max()  # constants: E(1) = 0
+
+
+@pytest.mark.parametrize("W", [2, 3, 6])
+def test_fast_diagonalisation_inverts_C(W):
+    rng = np.random.default_rng(W)
+    P = W + 1
+    r = rng.standard_normal((P, P, P))
+    z = apply_Cinv_block(r, W)
+    C = dense_C(W)
+    assert np.allclose(C @ z.ravel(), r.ravel(), atol=1e-10 * np.abs(r).max())
+    # eq. (5.20): C has eigenvalues mu_i + mu_j + mu_k + 1 relative to F x F x F
+    mu, _ = eigenbasis(W)
+    E, F, *_ = one_d_forms(W)
+    FFF = np.kron(F, np.kron(F, F))
+    ev = np.sort(np.linalg.eigvals(np.linalg.solve(FFF, C)).real)
+    sig = np.sort((mu[:, None, None] + mu[None, :, None] + mu[None, None, :] + 1).ravel())
+    assert np.allclose(ev, sig, rtol=1e-8)

@@ -1,0 +1,405 @@
+"""Seeded synthetic inputs shared by the CPU oracle and the CUDA path.
+
+This module holds problem *data* only: meshes of axis-aligned box elements
+(element boxes, degrees, face adjacency) and the closed-form coefficient,
+source, boundary and exact-solution functions of the manufactured problems.
+It contains none of the method's arithmetic (no quadrature, no norms, no
+operators), so both sides can take their inputs from here and still share no
+code.
+
+Data functions are evaluated on tensor grids: ``fun(xs, ys, zs)`` takes three
+1-D coordinate arrays and returns an array of shape
+``(len(zs), len(ys), len(xs))`` (x fastest in C order, the lexicographic
+ordering of Section 5.3).  Face data use a length-1 array for the normal
+coordinate.
+
+Face numbering of a box element: face ``2*axis + side`` with axis 0/1/2 = x/y/z
+and side 0 = the low face (lambda = -1), side 1 = the high face (lambda = +1).
+A neighbour id of -1 marks a Dirichlet boundary face.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Callable, List, Optional
+
+import numpy as np
+
+PI = math.pi
+
+
+# --------------------------------------------------------------------------
+# Meshes
+# --------------------------------------------------------------------------
+@dataclass
+class MeshDesc:
+    """A batch of box-element meshes (one or more independent problems)."""
+
+    elem_lo: np.ndarray        # [E, 3] float64, box lower corner
+    elem_hi: np.ndarray        # [E, 3] float64, box upper corner
+    elem_W: np.ndarray         # [E] int32, polynomial degree per variable
+    elem_nbr: np.ndarray       # [E, 6] int32, neighbour element id or -1
+    elem_problem: np.ndarray   # [E] int32, problem index of each element
+    n_problem: int = 1
+
+    @property
+    def n_elem(self) -> int:
+        return int(self.elem_W.shape[0])
+
+
+def box_mesh(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), W=4) -> MeshDesc:
+    """Uniform n[0] x n[1] x n[2] grid of boxes on [lo, hi]; all outer faces Dirichlet.
+
+    Elements are numbered x fastest, then y, then z.
+    """
+    if isinstance(n, int):
+        n = (n, n, n)
+    nx, ny, nz = (int(v) for v in n)
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    E = nx * ny * nz
+    elem_lo = np.zeros((E, 3))
+    elem_hi = np.zeros((E, 3))
+    nbr = -np.ones((E, 6), dtype=np.int32)
+    cuts = [np.linspace(lo[a], hi[a], m + 1) for a, m in enumerate((nx, ny, nz))]
+
+    def eid(i, j, k):
+        return (k * ny + j) * nx + i
+
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                e = eid(i, j, k)
+                idx = (i, j, k)
+                for a in range(3):
+                    elem_lo[e, a] = cuts[a][idx[a]]
+                    elem_hi[e, a] = cuts[a][idx[a] + 1]
+                if i > 0:
+                    nbr[e, 0] = eid(i - 1, j, k)
+                if i < nx - 1:
+                    nbr[e, 1] = eid(i + 1, j, k)
+                if j > 0:
+                    nbr[e, 2] = eid(i, j - 1, k)
+                if j < ny - 1:
+                    nbr[e, 3] = eid(i, j + 1, k)
+                if k > 0:
+                    nbr[e, 4] = eid(i, j, k - 1)
+                if k < nz - 1:
+                    nbr[e, 5] = eid(i, j, k + 1)
+    return MeshDesc(elem_lo, elem_hi, np.full(E, W, dtype=np.int32), nbr,
+                    np.zeros(E, dtype=np.int32), 1)
+
+
+def concat_meshes(meshes: List[MeshDesc]) -> MeshDesc:
+    """Batch independent problems into one description (ids are offset)."""
+    los, his, Ws, nbrs, probs = [], [], [], [], []
+    off = 0
+    poff = 0
+    for m in meshes:
+        los.append(m.elem_lo)
+        his.append(m.elem_hi)
+        Ws.append(m.elem_W)
+        nb = m.elem_nbr.copy()
+        nb[nb >= 0] += off
+        nbrs.append(nb)
+        probs.append(m.elem_problem + poff)
+        off += m.n_elem
+        poff += m.n_problem
+    return MeshDesc(np.concatenate(los), np.concatenate(his),
+                    np.concatenate(Ws).astype(np.int32),
+                    np.concatenate(nbrs).astype(np.int32),
+                    np.concatenate(probs).astype(np.int32), poff)
+
+
+# --------------------------------------------------------------------------
+# Problems: closed-form data on tensor grids
+# --------------------------------------------------------------------------
+Fun = Callable[[np.ndarray, np.ndarray, np.ndarray], np.ndarray]
+
+
+def _grid(xs, ys, zs):
+    xs = np.asarray(xs, dtype=np.float64)
+    ys = np.asarray(ys, dtype=np.float64)
+    zs = np.asarray(zs, dtype=np.float64)
+    return xs[None, None, :], ys[None, :, None], zs[:, None, None]
+
+
+def _full(val, xs, ys, zs):
+    return np.full((len(zs), len(ys), len(xs)), float(val))
+
+
+@dataclass
+class Problem:
+    """Data of -div(a grad u) = f in the problem's box mesh, u = g on the boundary.
+
+    ``f`` and ``g`` are lists with one function per right-hand side.
+    ``a`` / ``grad_a`` are None for the Laplacian (a = 1).
+    ``u_exact`` / ``grad_u_exact`` (per right-hand side) are optional.
+    """
+
+    mesh: MeshDesc
+    f: List[Fun]
+    g: List[Fun]
+    a: Optional[Fun] = None
+    grad_a: Optional[Callable] = None  # returns (ax, ay, az)
+    u_exact: Optional[List[Fun]] = None
+    grad_u_exact: Optional[List[Callable]] = None
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_rhs(self) -> int:
+        return len(self.f)
+
+
+def _zero(xs, ys, zs):
+    return _full(0.0, xs, ys, zs)
+
+
+def poisson_sine(n=2, W=4, lo=0.0, hi=1.0) -> Problem:
+    """-Lap u = f with u = sin(pi x) sin(pi y) sin(pi z), u = 0 on the boundary.
+
+    On [0,1]^3 this is the 2x2x2, W=4 configuration; on (-1,1)^3 it is the
+    problem of Table 6.2.
+    """
+    mesh = box_mesh(n, (lo,) * 3, (hi,) * 3, W)
+
+    def u(xs, ys, zs):
+        x, y, z = _grid(xs, ys, zs)
+        return np.sin(PI * x) * np.sin(PI * y) * np.sin(PI * z)
+
+    def f(xs, ys, zs):
+        return 3.0 * PI * PI * u(xs, ys, zs)
+
+    def gu(xs, ys, zs):
+        x, y, z = _grid(xs, ys, zs)
+        sx, sy, sz = np.sin(PI * x), np.sin(PI * y), np.sin(PI * z)
+        cx, cy, cz = np.cos(PI * x), np.cos(PI * y), np.cos(PI * z)
+        return (PI * cx * sy * sz, PI * sx * cy * sz, PI * sx * sy * cz)
+
+    return Problem(mesh, [f], [_zero], None, None, [u], [gu], name="poisson_sine")
+
+
+def polynomial_exact(n=2, W=3, lo=-1.0, hi=1.0) -> Problem:
+    """Exact solution inside the discrete space (degree 3 per variable).
+
+    u = (1-x^2)(1-y^2)(1-z^2)(1+xy) on (-1,1)^3 vanishes on the boundary; for
+    W >= 3 the least-squares minimiser reproduces it exactly.
+    """
+    mesh = box_mesh(n, (lo,) * 3, (hi,) * 3, W)
+
+    def u(xs, ys, zs):
+        x, y, z = _grid(xs, ys, zs)
+        return (1 - x * x) * (1 - y * y) * (1 - z * z) * (1 + x * y)
+
+    def grad(xs, ys, zs):
+        x, y, z = _grid(xs, ys, zs)
+        X, Y, Z = 1 - x * x, 1 - y * y, 1 - z * z
+        ux = (-2 * x * (1 + x * y) + X * y) * Y * Z
+        uy = (-2 * y * (1 + x * y) + Y * x) * X * Z
+        uz = -2 * z * X * Y * (1 + x * y)
+        return ux, uy, uz
+
+    def f(xs, ys, zs):
+        x, y, z = _grid(xs, ys, zs)
+        X, Y, Z = 1 - x * x, 1 - y * y, 1 - z * z
+        # second derivatives of (1-x^2)(1+xy) in x: d2/dx2 = -2(1+xy) - 4xy
+        uxx = (-2 * (1 + x * y) - 4 * x * y) * Y * Z
+        uyy = (-2 * (1 + x * y) - 4 * x * y) * X * Z
+        uzz = -2 * X * Y * (1 + x * y)
+        return -(uxx + uyy + uzz)
+
+    return Problem(mesh, [f], [_zero], None, None, [u], [grad], name="polynomial_exact")
+
+
+def _legendre_table(kmax, t):
+    """Legendre values L_0..L_kmax at t (three-term recurrence; input data only)."""
+    t = np.asarray(t, dtype=np.float64)
+    out = np.zeros((kmax + 1,) + t.shape)
+    out[0] = 1.0
+    if kmax >= 1:
+        out[1] = t
+    for m in range(1, kmax):
+        out[m + 1] = ((2 * m + 1) * t * out[m] - m * out[m - 1]) / (m + 1)
+    return out
+
+
+def _legendre_deriv_table(kmax, t):
+    """Derivatives L'_0..L'_kmax at t, from (1-t^2) L'_m = m (L_{m-1} - t L_m)."""
+    t = np.asarray(t, dtype=np.float64)
+    Lt = _legendre_table(kmax + 1, t)
+    d = np.zeros((kmax + 1,) + t.shape)
+    # recurrence L'_{m+1} = L'_{m-1} + (2m+1) L_m  (valid at the endpoints too)
+    if kmax >= 1:
+        d[1] = 1.0
+    for m in range(1, kmax):
+        d[m + 1] = d[m - 1] + (2 * m + 1) * Lt[m]
+    return d
+
+
+def legendre_field(coef, box_lo, box_hi):
+    """Return (F, dF) for F(x) = sum c_ijk L_i(s x) L_j(s y) L_k(s z) on a box.
+
+    ``coef`` has shape [K+1, K+1, K+1] indexed [i, j, k] (x, y, z degrees);
+    s maps the box affinely onto (-1,1)^3.  ``dF`` returns the gradient.
+    """
+    coef = np.asarray(coef, dtype=np.float64)
+    K = coef.shape[0] - 1
+    lo = np.asarray(box_lo, dtype=np.float64)
+    hi = np.asarray(box_hi, dtype=np.float64)
+    sc = 2.0 / (hi - lo)
+
+    def tabs(xs, ys, zs):
+        tx = sc[0] * (np.asarray(xs) - lo[0]) - 1
+        ty = sc[1] * (np.asarray(ys) - lo[1]) - 1
+        tz = sc[2] * (np.asarray(zs) - lo[2]) - 1
+        return tx, ty, tz
+
+    def F(xs, ys, zs):
+        tx, ty, tz = tabs(xs, ys, zs)
+        Lx, Ly, Lz = (_legendre_table(K, t) for t in (tx, ty, tz))
+        return np.einsum("ijk,ia,jb,kc->cba", coef, Lx, Ly, Lz)
+
+    def dF(xs, ys, zs):
+        tx, ty, tz = tabs(xs, ys, zs)
+        Lx, Ly, Lz = (_legendre_table(K, t) for t in (tx, ty, tz))
+        dx, dy, dz = (_legendre_deriv_table(K, t) for t in (tx, ty, tz))
+        gx = sc[0] * np.einsum("ijk,ia,jb,kc->cba", coef, dx, Ly, Lz)
+        gy = sc[1] * np.einsum("ijk,ia,jb,kc->cba", coef, Lx, dy, Lz)
+        gz = sc[2] * np.einsum("ijk,ia,jb,kc->cba", coef, Lx, Ly, dz)
+        return gx, gy, gz
+
+    return F, dF
+
+
+def varcoef_random_rhs(n=8, W=8, n_rhs=64, seed0=20260, kmax=8) -> Problem:
+    """-div(a grad u) = f on [0,1]^3, a = 1 + 0.5 sin(2pi x) sin(2pi y) sin(2pi z).
+
+    f_r = sum_{i,j,k<=kmax} c_ijk 2^-(i+j+k) L_i(2x-1) L_j(2y-1) L_k(2z-1),
+    c ~ N(0,1) i.i.d. from numpy PCG64 with seed seed0 + r; u = 0 on the boundary.
+    """
+    mesh = box_mesh(n, (0.0,) * 3, (1.0,) * 3, W)
+    tp = 2 * PI
+
+    def a(xs, ys, zs):
+        x, y, z = _grid(xs, ys, zs)
+        return 1.0 + 0.5 * np.sin(tp * x) * np.sin(tp * y) * np.sin(tp * z)
+
+    def grad_a(xs, ys, zs):
+        x, y, z = _grid(xs, ys, zs)
+        sx, sy, sz = np.sin(tp * x), np.sin(tp * y), np.sin(tp * z)
+        cx, cy, cz = np.cos(tp * x), np.cos(tp * y), np.cos(tp * z)
+        return (0.5 * tp * cx * sy * sz, 0.5 * tp * sx * cy * sz, 0.5 * tp * sx * sy * cz)
+
+    fs = []
+    decay = 2.0 ** -np.add.outer(np.add.outer(np.arange(kmax + 1), np.arange(kmax + 1)),
+                                 np.arange(kmax + 1))
+    for r in range(n_rhs):
+        rng = np.random.Generator(np.random.PCG64(seed0 + r))
+        c = rng.standard_normal((kmax + 1,) * 3) * decay
+        F, _ = legendre_field(c, (0.0,) * 3, (1.0,) * 3)
+        fs.append(F)
+    return Problem(mesh, fs, [_zero] * n_rhs, a, grad_a, None, None,
+                   name="varcoef_random_rhs", meta={"seed0": seed0})
+
+
+def lognormal_coef_problem(W, p, n=4, seed=100, target_std=0.5, kmax=3) -> Problem:
+    """One problem of the adjoint batch: a = exp(g) on [0,1]^3, f = 1, u = 0.
+
+    g = sum_{i,j,k<=kmax} theta_ijk L_i L_j L_k (on [0,1]^3 mapped to (-1,1)^3),
+    theta ~ N(0,1) from PCG64(seed + p), theta_000 = 0, rescaled so that the
+    L2(Omega)-standard deviation of g is target_std.  With Legendre orthogonality
+    on (-1,1) (|L_i|^2 = 2/(2i+1)) and |Omega| = 1 the variance of g is
+    sum theta_ijk^2 / ((2i+1)(2j+1)(2k+1)).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed + p))
+    th = rng.standard_normal((kmax + 1,) * 3)
+    th[0, 0, 0] = 0.0
+    m = np.arange(kmax + 1)
+    norm = 1.0 / np.multiply.outer(np.multiply.outer(2 * m + 1, 2 * m + 1), 2 * m + 1)
+    var = float(np.sum(th * th * norm))
+    th *= target_std / math.sqrt(var)
+    mesh = box_mesh(n, (0.0,) * 3, (1.0,) * 3, W)
+    G, dG = legendre_field(th, (0.0,) * 3, (1.0,) * 3)
+
+    def a(xs, ys, zs):
+        return np.exp(G(xs, ys, zs))
+
+    def grad_a(xs, ys, zs):
+        e = np.exp(G(xs, ys, zs))
+        gx, gy, gz = dG(xs, ys, zs)
+        return e * gx, e * gy, e * gz
+
+    def one(xs, ys, zs):
+        return _full(1.0, xs, ys, zs)
+
+    return Problem(mesh, [one], [_zero], a, grad_a, None, None,
+                   name="lognormal_coef", meta={"theta": th, "W": W, "p": p})
+
+
+def adjoint_batch_degrees(n_problem=256, seed=7, wmin=4, wmax=10) -> np.ndarray:
+    """Per-problem degrees W_p ~ U{wmin..wmax} from PCG64(seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.integers(wmin, wmax + 1, size=n_problem).astype(np.int32)
+
+
+def random_dofs(n, seed, dtype=np.float64) -> np.ndarray:
+    """Seeded N(0,1) vector (test input for operator applies)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.standard_normal(n).astype(dtype)
+
+
+def laplace_sinh(n=2, W=4) -> Problem:
+    """Table 6.1: Lap u = 0 on (0,1)^3, u = g on the boundary, with
+    u = sin(pi x) sin(pi y) sinh(sqrt2 pi z) / (pi^2 sinh(sqrt2 pi))."""
+    mesh = box_mesh(n, (0.0,) * 3, (1.0,) * 3, W)
+    r2 = math.sqrt(2.0) * PI
+    c = 1.0 / (PI * PI * math.sinh(r2))
+
+    def u(xs, ys, zs):
+        x, y, z = _grid(xs, ys, zs)
+        return c * np.sin(PI * x) * np.sin(PI * y) * np.sinh(r2 * z)
+
+    def grad(xs, ys, zs):
+        x, y, z = _grid(xs, ys, zs)
+        sx, sy, shz = np.sin(PI * x), np.sin(PI * y), np.sinh(r2 * z)
+        return (c * PI * np.cos(PI * x) * sy * shz, c * PI * sx * np.cos(PI * y) * shz,
+                c * r2 * sx * sy * np.cosh(r2 * z))
+
+    return Problem(mesh, [_zero], [u], None, None, [u], [grad], name="laplace_sinh")
+
+
+def varcoef_manufactured(n=(2, 2, 1), W=4) -> Problem:
+    """-div(a grad u) = f on (0,1)^3 with a = 1 + 0.5 sin(2pi x) sin(2pi y) sin(2pi z),
+    exact u = exp(x) sin(pi y) (1 + z^2), Dirichlet data g = u (test problem)."""
+    mesh = box_mesh(n, (0.0,) * 3, (1.0,) * 3, W)
+    tp = 2 * PI
+
+    def a(xs, ys, zs):
+        x, y, z = _grid(xs, ys, zs)
+        return 1.0 + 0.5 * np.sin(tp * x) * np.sin(tp * y) * np.sin(tp * z)
+
+    def grad_a(xs, ys, zs):
+        x, y, z = _grid(xs, ys, zs)
+        sx, sy, sz = np.sin(tp * x), np.sin(tp * y), np.sin(tp * z)
+        cx, cy, cz = np.cos(tp * x), np.cos(tp * y), np.cos(tp * z)
+        return (0.5 * tp * cx * sy * sz, 0.5 * tp * sx * cy * sz, 0.5 * tp * sx * sy * cz)
+
+    def u(xs, ys, zs):
+        x, y, z = _grid(xs, ys, zs)
+        return np.exp(x) * np.sin(PI * y) * (1 + z * z)
+
+    def grad(xs, ys, zs):
+        x, y, z = _grid(xs, ys, zs)
+        ex, sy, cy = np.exp(x), np.sin(PI * y), np.cos(PI * y)
+        return (ex * sy * (1 + z * z), ex * PI * cy * (1 + z * z), ex * sy * 2 * z)
+
+    def f(xs, ys, zs):
+        x, y, z = _grid(xs, ys, zs)
+        ex, sy = np.exp(x), np.sin(PI * y)
+        lap = ex * sy * (1 + z * z) - PI * PI * ex * sy * (1 + z * z) + ex * sy * 2.0
+        ux, uy, uz = grad(xs, ys, zs)
+        ax, ay, az = grad_a(xs, ys, zs)
+        return -(a(xs, ys, zs) * lap + ax * ux + ay * uy + az * uz)
+
+    return Problem(mesh, [f], [u], a, grad_a, [u], [grad], name="varcoef_manufactured")

@@ -1,0 +1,202 @@
+/*
+ * hpse.h -- C ABI of the GB300 (sm_103a) library for the hot path of the
+ * nonconforming h-p least-squares spectral element method for 3-D elliptic
+ * problems (A. Husain, "h-p spectral element methods for three dimensional
+ * elliptic problems on non-smooth domains using parallel computers", 2010).
+ *
+ * The library applies, matrix-free, the normal operator A = S^T M S of the
+ * least-squares functional of eq. (4.2), the block-diagonal separable
+ * preconditioner of eq. (5.19)-(5.20), and solves A U = b by preconditioned
+ * conjugate gradients (Section 5.1, stopping rule of Section 6.1), in FP64 or
+ * with FP32 operator applies wrapped in FP64 iterative refinement.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Elements.  Axis-aligned boxes mapped affinely onto the master cube
+ *   Q = (-1,1)^3 (the regular region of Section 2.3); degree W per variable,
+ *   1 <= W <= HPSE_MAX_W; unknowns are the nodal values on the (W+1)^3
+ *   Gauss-Lobatto-Legendre grid, lexicographic with x fastest (Section 5.3:
+ *   U_{(W+1)^2 k + (W+1) j + i} = u(x_i, y_j, z_k)).
+ * Faces.  Face f = 2*axis + side of an element (axis 0/1/2 = x/y/z, side 0 =
+ *   the face lambda_axis = -1, side 1 = lambda_axis = +1).  elem_nbr[6e+f] is
+ *   the element across that face, or -1 for a Dirichlet boundary face.
+ * Vectors.  A "DOF vector" holds n_rhs right-hand sides back to back:
+ *   value of rhs r, element e, node n at  r*ndof + elem_offset(e) + n, where
+ *   elem_offset(e) = sum_{e'<e} (W_e'+1)^3 and ndof = hpse_ndof().
+ *   Device DOF vectors are caller-owned; FP64 entry points take double*,
+ *   precision-selectable ones take double* (HPSE_FP64) or float* (HPSE_FP32).
+ * Quadrature points.  Volume data are sampled on each element's (2W+1)^3 GLL
+ *   grid, laid out per element as [c][b][a] (x fastest), elements back to
+ *   back (hpse_nquad() values per right-hand side).  Dirichlet data are
+ *   sampled on each boundary face's (2W+1)^2 GLL grid, [t2][t1] with t1 < t2
+ *   the two tangential axes, faces in (element, face) order
+ *   (hpse_nface_points() values per right-hand side).  hpse_query_points()
+ *   returns the 1-D coordinates that span these grids.
+ * Streams.  `stream` is a cudaStream_t (NULL = legacy default stream).  Entry
+ *   points that only launch kernels are asynchronous with respect to the host.
+ * Errors.  Every entry point returns an hpse_status; nothing aborts or traps
+ *   on the device.  Invalid arguments are detected on the host before any
+ *   launch.  After HPSE_ERR_CUDA the handle should be destroyed.
+ * Ownership.  The library owns the mesh handle, its tables, coefficient
+ *   arrays, right-hand side and solver workspaces (all device memory it
+ *   allocates at set-up); callers own every vector they pass.
+ * Threads.  A handle may be used from one host thread at a time.
+ */
+#ifndef HPSE_H
+#define HPSE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HPSE_MAX_W 10
+
+typedef struct hpse_mesh hpse_mesh;
+
+typedef enum {
+  HPSE_OK = 0,
+  HPSE_ERR_INVALID_ARG = 1,     /* bad pointer, size, enum or state */
+  HPSE_ERR_NONMATCHING_FACE = 2,/* neighbour faces do not coincide (one-to-one matching faces required) */
+  HPSE_ERR_DEGREE = 3,          /* W outside [1, HPSE_MAX_W], or unequal W across an interior face */
+  HPSE_ERR_BREAKDOWN = 4,       /* PCG breakdown: p^T A p <= 0 or a non-finite scalar */
+  HPSE_ERR_NO_CONVERGENCE = 5,  /* iteration cap reached before the tolerance */
+  HPSE_ERR_TIMEOUT = 6,         /* wall-clock limit of the solve reached */
+  HPSE_ERR_CUDA = 7,            /* a CUDA runtime call failed */
+  HPSE_ERR_OOM = 8,             /* device allocation failed */
+  HPSE_ERR_NO_DATA = 9          /* hpse_set_data has not been called */
+} hpse_status;
+
+typedef enum { HPSE_FP64 = 0, HPSE_FP32 = 1 } hpse_prec;
+
+typedef enum {
+  HPSE_COEF_LAPLACE = 0,  /* L u = -Lap u                       */
+  HPSE_COEF_SCALAR = 1    /* L u = -div(a grad u), a(x) > 0 given with grad a */
+} hpse_coef_kind;
+
+/* Mesh of one or more independent problems (eq. 2.1-2.2: the operator, the
+ * Dirichlet face set Gamma^[0]; Section 2.3: elements and faces).  All
+ * arrays are host memory, read during hpse_setup_mesh only. */
+typedef struct {
+  int32_t n_elem;              /* number of box elements (all problems)        */
+  int32_t n_problem;           /* independent problems (PCG scalars per (problem, rhs)) */
+  int32_t n_rhs;               /* right-hand sides per problem                 */
+  int32_t coef_kind;           /* hpse_coef_kind                               */
+  const int32_t *elem_W;       /* [n_elem] degree per variable                 */
+  const int32_t *elem_problem; /* [n_elem] problem index in [0, n_problem)     */
+  const double *elem_lo;       /* [n_elem*3] box lower corner (x, y, z)        */
+  const double *elem_hi;       /* [n_elem*3] box upper corner                  */
+  const int32_t *elem_nbr;     /* [n_elem*6] neighbour id or -1 (Dirichlet)    */
+} hpse_mesh_desc;
+
+/* Problem data (Section 4.2: F, g of eq. 4.2).  Host FP64 arrays, copied.
+ *   f      [n_rhs][hpse_nquad()]        source at the volume points (required)
+ *   a      [hpse_nquad()]               coefficient (HPSE_COEF_SCALAR only)
+ *   grad_a [3][hpse_nquad()]            its gradient d a / d x_k (idem)
+ *   g      [n_rhs][hpse_nface_points()] Dirichlet data, or NULL for g = 0   */
+typedef struct {
+  const double *f;
+  const double *a;
+  const double *grad_a;
+  const double *g;
+} hpse_data;
+
+typedef struct {
+  double tol;          /* relative residual target ||b - A x||_2 <= tol ||b||_2 (Section 6.1) */
+  int32_t max_iter;    /* cap on PCG iterations (all sweeps together)              */
+  int32_t prec;        /* hpse_prec of the operator applies inside PCG:
+                          HPSE_FP64 = plain FP64 PCG;
+                          HPSE_FP32 = FP32 applies + FP64 iterative refinement     */
+  double inner_tol;    /* relative tolerance of each FP32 inner solve (HPSE_FP32)  */
+  int32_t max_sweeps;  /* cap on refinement sweeps (HPSE_FP32)                     */
+  int32_t check_every; /* PCG iterations per host convergence check (CUDA graph)   */
+  int32_t zero_init;   /* 1: start from x = 0 (the input x is ignored)             */
+  double time_limit_s; /* wall-clock limit, <= 0 for none                          */
+} hpse_solve_opts;
+
+typedef struct {
+  int32_t status;        /* hpse_status of the whole solve                         */
+  int32_t iterations;    /* PCG iterations performed (max over right-hand sides)   */
+  int32_t sweeps;        /* FP64 refinement sweeps (1 for plain FP64)              */
+  int32_t applies;       /* operator applies performed (per right-hand side)      */
+  double rel_residual;   /* max over rhs of ||b - A x||_2 / ||b||_2, FP64          */
+} hpse_solve_report;
+
+/* Build the mesh on `device`: validates the description (matching faces,
+ * degrees), builds the GLL / Lagrange / face-norm / preconditioner tables in
+ * FP64 on the host, uploads geometry and tables.  Section 2.3 (mesh),
+ * Section 5.3 (tables), eq. (5.15)-(5.17) (preconditioner eigenbases). */
+hpse_status hpse_setup_mesh(const hpse_mesh_desc *desc, int device, hpse_mesh **out);
+
+/* Sizes: DOFs per right-hand side; volume points; Dirichlet face points. */
+int64_t hpse_ndof(const hpse_mesh *m);
+int64_t hpse_nquad(const hpse_mesh *m);
+int64_t hpse_nface_points(const hpse_mesh *m);
+int32_t hpse_nrhs(const hpse_mesh *m);
+
+/* 1-D coordinates spanning the data grids (host output, caller-allocated):
+ *   vol_axes  [sum_e 3*(2W_e+1)]: per element the x, y, z coordinates of its
+ *             (2W_e+1)-point GLL rule mapped to the box;
+ *   face_norm [n_boundary_faces]: per Dirichlet face (element, face order)
+ *             the fixed normal coordinate; its tangential coordinates are the
+ *             element's vol_axes along t1 and t2.
+ * Either pointer may be NULL. */
+hpse_status hpse_query_points(const hpse_mesh *m, double *vol_axes, double *face_norm);
+int64_t hpse_n_boundary_faces(const hpse_mesh *m);
+
+/* Upload data and build b = S^T M d in FP64 on the device (Section 5.3:
+ * "G is assembled from the data").  Synchronous. */
+hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data);
+
+/* y = A u, the normal operator of eq. (4.2) (Section 5.3), for all n_rhs
+ * right-hand sides.  u, y: device DOF vectors of n_rhs*ndof scalars of the
+ * given precision; u and y must not overlap. */
+hpse_status hpse_apply_operator(hpse_mesh *m, int32_t prec, const void *u, void *y, void *stream);
+
+/* z = C^{-1} r, the element-block separable preconditioner (eq. 5.19-5.20),
+ * for all right-hand sides; r, z device DOF vectors (may not overlap). */
+hpse_status hpse_apply_preconditioner(hpse_mesh *m, int32_t prec, const void *r, void *z, void *stream);
+
+/* Copy the FP64 right-hand side b = S^T M d (device, n_rhs*ndof doubles). */
+hpse_status hpse_get_rhs(hpse_mesh *m, double *b, void *stream);
+
+/* Solve A x = b for every right-hand side by PCG (FP64) or by FP32-apply PCG
+ * inside FP64 iterative refinement.  x: device FP64 DOF vector (input initial
+ * guess unless opts->zero_init, output solution).  Synchronous; the report
+ * holds iterations, sweeps and the final FP64 relative residual. */
+hpse_status hpse_pcg_solve(hpse_mesh *m, const hpse_solve_opts *opts, double *x,
+                           hpse_solve_report *rep, void *stream);
+
+/* Squared H^1 norms in physical coordinates (Section 6.1), per right-hand
+ * side, with the (2W+1)^3 GLL rule of each element:
+ *   out[2r]   = || u_r - v_r ||_{H^1}^2
+ *   out[2r+1] = || v_r ||_{H^1}^2
+ * where u is a device FP64 DOF vector and v is either
+ *   (ref != NULL) another device FP64 DOF vector, or
+ *   (ref == NULL) the function sampled at the volume points: vq (device,
+ *   n_rhs*nquad doubles, the values) and gq (device, n_rhs*3*nquad doubles,
+ *   d/dx, d/dy, d/dz blocks per rhs).  out: host, 2*n_rhs doubles.  Synchronous. */
+hpse_status hpse_h1_error(hpse_mesh *m, const double *u, const double *ref,
+                          const double *vq, const double *gq, double *out, void *stream);
+
+/* Operator work counters for the loaded mesh: multiply-adds of one apply of A
+ * per right-hand side, split into volume and face parts, as implemented. */
+hpse_status hpse_work_counts(const hpse_mesh *m, double *vol_macs, double *face_macs);
+
+/* Kernel launch parameters: threads per CTA for degree W, precision prec,
+ * kernel kind (0 = operator apply, 1 = preconditioner); set by the autotuner,
+ * 0 restores the default. */
+hpse_status hpse_set_block_threads(hpse_mesh *m, int32_t kind, int32_t prec, int32_t W, int32_t threads);
+int32_t hpse_get_block_threads(const hpse_mesh *m, int32_t kind, int32_t prec, int32_t W);
+
+/* Kernels launched by this library since the last call (and reset). */
+int64_t hpse_kernel_launch_count(int32_t reset);
+
+const char *hpse_status_string(hpse_status s);
+void hpse_destroy(hpse_mesh *m);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HPSE_H */

@@ -1,0 +1,217 @@
+"""Python binding of the hpse C ABI (include/hpse.h): argument marshalling only.
+
+Every numerical step runs in the CUDA library; this module converts numpy /
+torch arguments to pointers and sizes and checks the returned status.
+Device vectors are torch CUDA tensors (float64 or float32, contiguous) of
+n_rhs * ndof entries in the layout of include/hpse.h; the current torch CUDA
+stream is passed to the library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import COEF_LAPLACE, COEF_SCALAR, FP32, FP64, check
+
+__all__ = ["Mesh", "problem_data_arrays", "FP64", "FP32", "COEF_LAPLACE", "COEF_SCALAR"]
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(C.c_void_p)
+    return C.c_void_p(a.data_ptr())  # torch tensor
+
+
+def _stream(stream=None):
+    if stream is not None:
+        return C.c_void_p(stream)
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _prec_of(t):
+    import torch
+    if t.dtype == torch.float64:
+        return FP64
+    if t.dtype == torch.float32:
+        return FP32
+    raise TypeError("device vectors must be float64 or float32, got %s" % t.dtype)
+
+
+class Mesh:
+    """Handle of hpse_setup_mesh for a batch of box-element problems.
+
+    ``desc`` provides elem_lo [E,3], elem_hi [E,3], elem_W [E], elem_nbr [E,6],
+    elem_problem [E] and n_problem (e.g. workloads.MeshDesc).
+    """
+
+    def __init__(self, desc, n_rhs=1, coef_kind=COEF_LAPLACE, device=0):
+        self._lib = _lib.load()
+        self._keep = [np.ascontiguousarray(desc.elem_W, dtype=np.int32),
+                      np.ascontiguousarray(desc.elem_problem, dtype=np.int32),
+                      np.ascontiguousarray(desc.elem_lo, dtype=np.float64),
+                      np.ascontiguousarray(desc.elem_hi, dtype=np.float64),
+                      np.ascontiguousarray(desc.elem_nbr, dtype=np.int32)]
+        d = _lib.MeshDesc()
+        d.n_elem = int(self._keep[0].shape[0])
+        d.n_problem = int(desc.n_problem)
+        d.n_rhs = int(n_rhs)
+        d.coef_kind = int(coef_kind)
+        d.elem_W, d.elem_problem, d.elem_lo, d.elem_hi, d.elem_nbr = (
+            k.ctypes.data_as(C.c_void_p) for k in self._keep)
+        h = C.c_void_p()
+        check(self._lib.hpse_setup_mesh(C.byref(d), int(device), C.byref(h)), "hpse_setup_mesh")
+        self._h = h
+        self.n_elem = d.n_elem
+        self.n_rhs = int(n_rhs)
+        self.n_problem = int(desc.n_problem)
+        self.coef_kind = int(coef_kind)
+        self.elem_W = self._keep[0]
+        self.device = device
+
+    # -- sizes ------------------------------------------------------------
+    @property
+    def ndof(self) -> int:
+        return int(self._lib.hpse_ndof(self._h))
+
+    @property
+    def nquad(self) -> int:
+        return int(self._lib.hpse_nquad(self._h))
+
+    @property
+    def nface_points(self) -> int:
+        return int(self._lib.hpse_nface_points(self._h))
+
+    @property
+    def n_boundary_faces(self) -> int:
+        return int(self._lib.hpse_n_boundary_faces(self._h))
+
+    def query_points(self):
+        """(vol_axes [sum 3Q], face_norm [n_boundary_faces]) of hpse_query_points."""
+        nax = int(sum(3 * (2 * int(w) + 1) for w in self.elem_W))
+        ax = np.zeros(nax)
+        fn = np.zeros(max(1, self.n_boundary_faces))
+        check(self._lib.hpse_query_points(self._h, _ptr(ax), _ptr(fn)), "hpse_query_points")
+        return ax, fn[: self.n_boundary_faces]
+
+    # -- data ---------------------------------------------------------------
+    def set_data(self, f, a=None, grad_a=None, g=None):
+        arrs = [None if v is None else np.ascontiguousarray(v, dtype=np.float64) for v in (f, a, grad_a, g)]
+        d = _lib.Data(*[None if v is None else v.ctypes.data_as(C.c_void_p) for v in arrs])
+        check(self._lib.hpse_set_data(self._h, C.byref(d)), "hpse_set_data")
+
+    def get_rhs(self, b, stream=None):
+        check(self._lib.hpse_get_rhs(self._h, _ptr(b), _stream(stream)), "hpse_get_rhs")
+
+    # -- operators -----------------------------------------------------------
+    def apply_operator(self, u, y, stream=None):
+        check(self._lib.hpse_apply_operator(self._h, _prec_of(u), _ptr(u), _ptr(y), _stream(stream)),
+              "hpse_apply_operator")
+
+    def apply_preconditioner(self, r, z, stream=None):
+        check(self._lib.hpse_apply_preconditioner(self._h, _prec_of(r), _ptr(r), _ptr(z), _stream(stream)),
+              "hpse_apply_preconditioner")
+
+    def pcg_solve(self, x, tol=1e-10, prec=FP64, max_iter=20000, inner_tol=1e-4, max_sweeps=30,
+                  check_every=16, zero_init=True, time_limit_s=0.0, stream=None, raise_on_error=True):
+        o = _lib.SolveOpts(float(tol), int(max_iter), int(prec), float(inner_tol), int(max_sweeps),
+                           int(check_every), 1 if zero_init else 0, float(time_limit_s))
+        rep = _lib.SolveReport()
+        st = self._lib.hpse_pcg_solve(self._h, C.byref(o), _ptr(x), C.byref(rep), _stream(stream))
+        out = dict(status=int(rep.status), iterations=int(rep.iterations), sweeps=int(rep.sweeps),
+                   applies=int(rep.applies), rel_residual=float(rep.rel_residual))
+        if raise_on_error:
+            check(st, "hpse_pcg_solve")
+        return out
+
+    def h1_error(self, u, ref=None, vq=None, gq=None, stream=None):
+        """[n_rhs, 2] array of (||u - v||_{H1}^2, ||v||_{H1}^2)."""
+        out = np.zeros(2 * self.n_rhs)
+        check(self._lib.hpse_h1_error(self._h, _ptr(u), _ptr(ref), _ptr(vq), _ptr(gq), _ptr(out),
+                                      _stream(stream)), "hpse_h1_error")
+        return out.reshape(self.n_rhs, 2)
+
+    def work_counts(self):
+        v, f = C.c_double(), C.c_double()
+        check(self._lib.hpse_work_counts(self._h, C.byref(v), C.byref(f)), "hpse_work_counts")
+        return v.value, f.value
+
+    def set_block_threads(self, kind, prec, W, threads):
+        check(self._lib.hpse_set_block_threads(self._h, kind, prec, W, threads), "hpse_set_block_threads")
+
+    def get_block_threads(self, kind, prec, W):
+        return int(self._lib.hpse_get_block_threads(self._h, kind, prec, W))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.hpse_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def kernel_launch_count(reset=False) -> int:
+    return int(_lib.load().hpse_kernel_launch_count(1 if reset else 0))
+
+
+def problem_data_arrays(mesh: Mesh, problem):
+    """Sample a problem's data functions on the mesh's query grids.
+
+    ``problem`` provides f (list per rhs), g (list per rhs), a / grad_a (or
+    None) as callables on tensor grids (see workloads).  Returns the dict of
+    host arrays expected by Mesh.set_data.
+    """
+    ax, fnorm = mesh.query_points()
+    Ws = [int(w) for w in mesh.elem_W]
+    R = mesh.n_rhs
+    nq = mesh.nquad
+    f = np.zeros((R, nq))
+    a = grad = None
+    if problem.a is not None:
+        a = np.zeros(nq)
+        grad = np.zeros((3, nq))
+    axes = []
+    o = oq = 0
+    for e, W in enumerate(Ws):
+        Q = 2 * W + 1
+        xs, ys, zs = ax[o:o + Q], ax[o + Q:o + 2 * Q], ax[o + 2 * Q:o + 3 * Q]
+        axes.append((xs, ys, zs))
+        o += 3 * Q
+        n = Q ** 3
+        for r in range(R):
+            f[r, oq:oq + n] = problem.f[r](xs, ys, zs).ravel()
+        if a is not None:
+            a[oq:oq + n] = problem.a(xs, ys, zs).ravel()
+            gx, gy, gz = problem.grad_a(xs, ys, zs)
+            grad[0, oq:oq + n] = np.broadcast_to(gx, (Q, Q, Q)).ravel()
+            grad[1, oq:oq + n] = np.broadcast_to(gy, (Q, Q, Q)).ravel()
+            grad[2, oq:oq + n] = np.broadcast_to(gz, (Q, Q, Q)).ravel()
+        oq += n
+    g = None
+    nfp = mesh.nface_points
+    if nfp > 0:
+        g = np.zeros((R, nfp))
+        nbr = mesh._keep[4]
+        fo = 0
+        k = 0
+        for e, W in enumerate(Ws):
+            Q = 2 * W + 1
+            for fi in range(6):
+                if nbr[e, fi] >= 0:
+                    continue
+                axis = fi // 2
+                grid = list(axes[e])
+                grid[axis] = np.array([fnorm[k]])
+                for r in range(R):
+                    g[r, fo:fo + Q * Q] = problem.g[r](*grid).ravel()
+                fo += Q * Q
+                k += 1
+    return dict(f=f, a=a, grad_a=grad, g=g)

@@ -1,0 +1,1474 @@
+// hpse.cu -- host side of the C ABI declared in include/hpse.h: mesh set-up,
+// data upload and right-hand side, operator / preconditioner dispatch, the
+// device-resident PCG driver with FP64 iterative refinement, the H^1 error
+// and the FP64 helper kernels.
+//
+// Method: A. Husain (2010), the least-squares functional of eq. (4.2), its
+// normal equations (Section 5.3), the separable preconditioner (eq. 5.19-5.20)
+// and PCG (Section 5.1, stopping rule of Section 6.1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <vector>
+
+#include "hpse.h"
+#include "host_math.h"
+#include "registry.h"
+
+using namespace hpse;
+
+// ---------------------------------------------------------------------------
+// kernel registry (one KernelSet per (precision, degree), filled by the
+// generated instantiation units)
+// ---------------------------------------------------------------------------
+#define HPSE_DECL(W)                                          \
+  extern "C" void hpse_register_f64_w##W(hpse::KernelSet *); \
+  extern "C" void hpse_register_f32_w##W(hpse::KernelSet *);
+HPSE_DECL(1)
+HPSE_DECL(2)
+HPSE_DECL(3)
+HPSE_DECL(4)
+HPSE_DECL(5)
+HPSE_DECL(6)
+HPSE_DECL(7)
+HPSE_DECL(8)
+HPSE_DECL(9)
+HPSE_DECL(10)
+
+static KernelSet g_sets[2][HPSE_MAX_W + 1];
+static bool g_sets_ready = false;
+static long long g_launches = 0;
+
+static void init_registry() {
+  if (g_sets_ready) return;
+  typedef void (*RegFn)(KernelSet *);
+  RegFn f64[HPSE_MAX_W + 1] = {nullptr, hpse_register_f64_w1, hpse_register_f64_w2, hpse_register_f64_w3,
+                               hpse_register_f64_w4, hpse_register_f64_w5, hpse_register_f64_w6,
+                               hpse_register_f64_w7, hpse_register_f64_w8, hpse_register_f64_w9,
+                               hpse_register_f64_w10};
+  RegFn f32[HPSE_MAX_W + 1] = {nullptr, hpse_register_f32_w1, hpse_register_f32_w2, hpse_register_f32_w3,
+                               hpse_register_f32_w4, hpse_register_f32_w5, hpse_register_f32_w6,
+                               hpse_register_f32_w7, hpse_register_f32_w8, hpse_register_f32_w9,
+                               hpse_register_f32_w10};
+  for (int w = 1; w <= HPSE_MAX_W; ++w) {
+    f64[w](&g_sets[0][w]);
+    f32[w](&g_sets[1][w]);
+  }
+  g_sets_ready = true;
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e__ = (call);                      \
+    if (e__ != cudaSuccess) {                      \
+      last_cuda_error(e__, #call, __LINE__);       \
+      return HPSE_ERR_CUDA;                        \
+    }                                              \
+  } while (0)
+
+static char g_last_err[512];
+static void last_cuda_error(cudaError_t e, const char *what, int line) {
+  snprintf(g_last_err, sizeof(g_last_err), "%s (%s) at hpse.cu:%d", cudaGetErrorString(e), what, line);
+}
+
+// ---------------------------------------------------------------------------
+// device buffers
+// ---------------------------------------------------------------------------
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  cudaError_t alloc(size_t b) {
+    if (p) {
+      cudaFree(p);
+      p = nullptr;
+    }
+    bytes = b;
+    if (b == 0) return cudaSuccess;
+    return cudaMalloc(&p, b);
+  }
+  template <typename T>
+  T *as() const {
+    return static_cast<T *>(p);
+  }
+};
+
+template <typename T>
+static cudaError_t upload(DevBuf &b, const std::vector<T> &v) {
+  cudaError_t e = b.alloc(v.size() * sizeof(T));
+  if (e != cudaSuccess || v.empty()) return e;
+  return cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+struct Group {
+  int W;
+  int n;          // elements in this degree group
+  DevBuf elems;   // int32 element ids
+};
+
+struct SolverWork {
+  size_t n = 0;  // n_rhs * ndof
+  // FP64
+  DevBuf x64, r64, z64, pa64, pb64, q64, b_scratch;
+  // FP32
+  DevBuf x32, r32, z32, pa32, pb32, q32;
+  // partials per (element, rhs) and PCG scalars per (problem, rhs)
+  DevBuf part0, part1, part2;
+  DevBuf sc;      // doubles: 8 arrays of NPR
+  DevBuf flags;   // int32: active[NPR], iters[NPR], status[NPR], n_active[1]
+  int *h_flags = nullptr;  // pinned host mirror
+  double *h_sc = nullptr;  // pinned host mirror
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev = nullptr;
+  std::map<long long, cudaGraphExec_t> graphs;
+  std::map<long long, int> graph_launches;
+  ~SolverWork() {
+    for (auto &g : graphs) cudaGraphExecDestroy(g.second);
+    if (h_flags) cudaFreeHost(h_flags);
+    if (h_sc) cudaFreeHost(h_sc);
+    if (st) cudaStreamDestroy(st);
+    if (ev) cudaEventDestroy(ev);
+  }
+};
+
+struct hpse_mesh {
+  int device = 0;
+  int n_elem = 0, n_problem = 0, n_rhs = 0, coef_kind = 0;
+  std::vector<int> W, prob, nbr;
+  std::vector<double> lo, hi;
+  std::vector<int64_t> dof_off, coef_off;
+  int64_t ndof = 0, nquad = 0;
+  std::vector<int> bface_elem, bface_fi;   // boundary faces
+  std::vector<int64_t> bface_off;          // offset of each face's Q^2 points
+  int64_t nface_pts = 0;
+  std::vector<int> prob_ptr, prob_elems;   // CSR of elements per problem
+  std::map<int, hm::DegreeTables> tabs;
+  std::vector<Group> groups;
+  // device mesh arrays
+  DevBuf d_dof_off, d_nbr, d_geo64, d_geo32, d_prob, d_coef_off, d_prob_ptr, d_prob_elems, d_elem_W;
+  DevBuf d_coef64, d_coef32;  // [4][nquad] m, d_x, d_y, d_z (COEF_SCALAR)
+  DevBuf d_b;                 // FP64 right-hand side
+  DevBuf d_bnorm2;            // FP64 ||b||^2 per (problem, rhs)
+  std::map<int, DevBuf> d_qtab;  // per degree FP64 Q-grid tables for the face data
+  bool has_data = false;
+  int threads[2][2][HPSE_MAX_W + 1];  // [kind][prec][W]
+  std::unique_ptr<SolverWork> work;
+};
+
+static int default_threads(int kind, int prec, int W) {
+  const int Q = 2 * W + 1;
+  if (kind == 1) {
+    const int P2 = (W + 1) * (W + 1);
+    return std::min(256, ((P2 + 31) / 32) * 32);
+  }
+  const int lines = Q * Q;
+  const int maxt = prec == HPSE_FP64 ? 256 : 384;
+  int t = ((lines + 31) / 32) * 32;
+  if (t > maxt) {
+    // two passes over the z-lines
+    t = (((lines + 1) / 2 + 31) / 32) * 32;
+    if (t > maxt) t = maxt;
+  }
+  return std::max(t, 64);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 helper kernels (not templated on the degree)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double s) {
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// deterministic block sum (result valid in thread 0)
+__device__ double block_sum_d(double v) {
+  __shared__ double red[32];
+  double s = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = s;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < nw; ++i) t += red[i];
+  __syncthreads();
+  return t;
+}
+
+struct ElemVecArgs {
+  int32_t n_elem, n_rhs;
+  int64_t ndof;
+  const int64_t *dof_off;
+  const int32_t *elem_W;
+};
+
+// per (element, rhs) block: generic vector kernels with FP64 partials
+template <typename TA, typename TB>
+__global__ void k_dot(ElemVecArgs A, const TA *a, const TB *b, double *part) {
+  const int item = blockIdx.x;
+  const int e = item / A.n_rhs, r = item - e * A.n_rhs;
+  const int P = A.elem_W[e] + 1, n = P * P * P;
+  const int64_t base = (int64_t)r * A.ndof + A.dof_off[e];
+  double s = 0.0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) s += (double)a[base + t] * (double)b[base + t];
+  s = block_sum_d(s);
+  if (threadIdx.x == 0) part[(int64_t)e * A.n_rhs + r] = s;
+}
+
+// r = b - q (FP64) and partial ||r||^2
+__global__ void k_residual(ElemVecArgs A, const double *b, const double *q, double *r, double *part) {
+  const int item = blockIdx.x;
+  const int e = item / A.n_rhs, rr = item - e * A.n_rhs;
+  const int P = A.elem_W[e] + 1, n = P * P * P;
+  const int64_t base = (int64_t)rr * A.ndof + A.dof_off[e];
+  double s = 0.0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const double v = b[base + t] - q[base + t];
+    r[base + t] = v;
+    s += v * v;
+  }
+  s = block_sum_d(s);
+  if (threadIdx.x == 0) part[(int64_t)e * A.n_rhs + rr] = s;
+}
+
+// r32 = r64 * scale[pr]  (scale = 1/||r64|| of the (problem, rhs), 0 if inactive)
+__global__ void k_scale_to_f32(ElemVecArgs A, const int32_t *prob, int n_rhs, const double *r64, const double *scale,
+                               float *r32) {
+  const int item = blockIdx.x;
+  const int e = item / A.n_rhs, rr = item - e * A.n_rhs;
+  const int P = A.elem_W[e] + 1, n = P * P * P;
+  const int64_t base = (int64_t)rr * A.ndof + A.dof_off[e];
+  const double s = scale[prob[e] * n_rhs + rr];
+  for (int t = threadIdx.x; t < n; t += blockDim.x) r32[base + t] = (float)(r64[base + t] * s);
+}
+
+// x64 += d32 * scale[pr]
+__global__ void k_add_scaled_f32(ElemVecArgs A, const int32_t *prob, int n_rhs, const float *d32,
+                                 const double *scale, double *x64) {
+  const int item = blockIdx.x;
+  const int e = item / A.n_rhs, rr = item - e * A.n_rhs;
+  const int P = A.elem_W[e] + 1, n = P * P * P;
+  const int64_t base = (int64_t)rr * A.ndof + A.dof_off[e];
+  const double s = scale[prob[e] * n_rhs + rr];
+  for (int t = threadIdx.x; t < n; t += blockDim.x) x64[base + t] += (double)d32[base + t] * s;
+}
+
+// x += d (FP64)
+__global__ void k_add64(ElemVecArgs A, const double *d, double *x) {
+  const int item = blockIdx.x;
+  const int e = item / A.n_rhs, rr = item - e * A.n_rhs;
+  const int P = A.elem_W[e] + 1, n = P * P * P;
+  const int64_t base = (int64_t)rr * A.ndof + A.dof_off[e];
+  for (int t = threadIdx.x; t < n; t += blockDim.x) x[base + t] += d[base + t];
+}
+
+// PCG scalars per (problem, rhs), arrays of length NPR inside one buffer
+struct Scalars {
+  double *rz, *bb, *rr, *alpha, *beta, *pq, *scale, *tol2;
+  int32_t *active, *iters, *status, *n_active;
+};
+
+static Scalars scalars_of(SolverWork &w, int npr) {
+  Scalars s;
+  double *d = w.sc.as<double>();
+  s.rz = d;
+  s.bb = d + npr;
+  s.rr = d + 2 * npr;
+  s.alpha = d + 3 * npr;
+  s.beta = d + 4 * npr;
+  s.pq = d + 5 * npr;
+  s.scale = d + 6 * npr;
+  s.tol2 = d + 7 * npr;
+  int32_t *f = w.flags.as<int32_t>();
+  s.active = f;
+  s.iters = f + npr;
+  s.status = f + 2 * npr;
+  s.n_active = f + 3 * npr;
+  return s;
+}
+
+struct FinArgs {
+  int n_rhs;
+  const int32_t *prob_ptr;
+  const int32_t *prob_elems;
+};
+
+// deterministic sum of per-element partials for (problem p, rhs r) = block
+__device__ double fin_sum(const FinArgs &F, const double *part, int p, int r) {
+  const int b = F.prob_ptr[p], e_ = F.prob_ptr[p + 1];
+  double s = 0.0;
+  for (int i = b + threadIdx.x; i < e_; i += blockDim.x) s += part[(int64_t)F.prob_elems[i] * F.n_rhs + r];
+  return block_sum_d(s);
+}
+
+// after q = A p: alpha = rz / (p.q)
+__global__ void k_fin_alpha(FinArgs F, Scalars S, const double *part_pq) {
+  const int pr = blockIdx.x;
+  const int p = pr / F.n_rhs, r = pr - p * F.n_rhs;
+  const double pq = fin_sum(F, part_pq, p, r);
+  if (threadIdx.x == 0) {
+    S.pq[pr] = pq;
+    double a = 0.0;
+    if (S.active[pr]) {
+      if (!(pq > 0.0) || !isfinite(pq)) {
+        S.status[pr] = HPSE_ERR_BREAKDOWN;
+        S.active[pr] = 0;
+      } else {
+        a = S.rz[pr] / pq;
+        if (!isfinite(a)) {
+          S.status[pr] = HPSE_ERR_BREAKDOWN;
+          S.active[pr] = 0;
+          a = 0.0;
+        }
+      }
+    }
+    S.alpha[pr] = a;
+  }
+}
+
+// after the update + preconditioner: convergence test and beta
+__global__ void k_fin_beta(FinArgs F, Scalars S, const double *part_rr, const double *part_rz) {
+  const int pr = blockIdx.x;
+  const int p = pr / F.n_rhs, r = pr - p * F.n_rhs;
+  const double rr = fin_sum(F, part_rr, p, r);
+  const double rz = fin_sum(F, part_rz, p, r);
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    if (S.active[pr]) {
+      S.iters[pr] += 1;
+      S.rr[pr] = rr;
+      if (!isfinite(rr) || !isfinite(rz)) {
+        S.status[pr] = HPSE_ERR_BREAKDOWN;
+        S.active[pr] = 0;
+      } else if (rr <= S.tol2[pr] * S.bb[pr]) {
+        S.active[pr] = 0;  // converged
+      } else {
+        b = rz / S.rz[pr];
+        S.rz[pr] = rz;
+      }
+    }
+    S.beta[pr] = b;
+  }
+}
+
+// start of a PCG solve: rz = r.z, bb = r.r (= rr), beta = 0, active if bb > 0
+__global__ void k_fin_init(FinArgs F, Scalars S, const double *part_rz, const double *part_rr, double rel_tol,
+                           const double *scale_in) {
+  const int pr = blockIdx.x;
+  const int p = pr / F.n_rhs, r = pr - p * F.n_rhs;
+  const double rz = fin_sum(F, part_rz, p, r);
+  const double rr = fin_sum(F, part_rr, p, r);
+  if (threadIdx.x == 0) {
+    S.rz[pr] = rz;
+    S.bb[pr] = rr;
+    S.rr[pr] = rr;
+    S.beta[pr] = 0.0;
+    S.alpha[pr] = 0.0;
+    S.iters[pr] = 0;
+    S.tol2[pr] = rel_tol * rel_tol;
+    const bool want = scale_in ? (scale_in[pr] != 0.0) : true;
+    S.active[pr] = (want && rr > 0.0 && isfinite(rr)) ? 1 : 0;
+    if (!isfinite(rr)) S.status[pr] = HPSE_ERR_BREAKDOWN;
+  }
+}
+
+__global__ void k_count_active(const int32_t *active, int npr, int32_t *n_active) {
+  int c = 0;
+  for (int i = threadIdx.x; i < npr; i += blockDim.x) c += active[i] ? 1 : 0;
+  const double s = block_sum_d((double)c);
+  if (threadIdx.x == 0) *n_active = (int32_t)s;
+}
+
+// per (problem, rhs): rel residual and the refinement scale 1/||r||
+__global__ void k_fin_outer(FinArgs F, const double *part_rr, const double *bnorm2, double tol, double *rel_out,
+                            double *scale, double *rnorm) {
+  const int pr = blockIdx.x;
+  const int p = pr / F.n_rhs, r = pr - p * F.n_rhs;
+  const double rr = fin_sum(F, part_rr, p, r);
+  if (threadIdx.x == 0) {
+    const double bb = bnorm2[pr];
+    const double rel = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    rel_out[pr] = rel;
+    const bool done = !(rel > tol);
+    scale[pr] = (done || !(rr > 0.0)) ? 0.0 : 1.0 / sqrt(rr);
+    rnorm[pr] = (done || !(rr > 0.0)) ? 0.0 : sqrt(rr);
+  }
+}
+
+__global__ void k_bnorm(FinArgs F, const double *part, double *out) {
+  const int pr = blockIdx.x;
+  const int p = pr / F.n_rhs, r = pr - p * F.n_rhs;
+  const double s = fin_sum(F, part, p, r);
+  if (threadIdx.x == 0) out[pr] = s;
+}
+
+// rho_b = -(w J a) f at the volume points; coef holds m = w J a^2 and the
+// host passes wJa separately
+__global__ void k_rho_b(int64_t n, const double *wja, const double *f, int64_t nquad, double *rho) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    rho[i] = -wja[i % nquad] * f[i];
+}
+
+// Dirichlet data part of b for one element and rhs (block): for each boundary
+// face of e: b_face += (B0 x B0)^T W2 g + (B1 x B0)^T H D_t1 g + (B0 x B1)^T H D_t2 g
+struct FaceDataArgs {
+  int n_rhs;
+  int64_t ndof, nface_pts;
+  const int64_t *dof_off;
+  const int32_t *elem_W;
+  const int32_t *felem_ptr;   // CSR over elements with boundary faces: faces of e
+  const int32_t *felems;      // element of each CSR row
+  const int32_t *face_fi;     // face index of each boundary face (CSR order)
+  const int64_t *face_off;    // point offset of each boundary face
+  const double *const *qtab;  // per degree: B0, B1 (QxP), DQ, KQ (QxQ), wq (Q)
+  const double *g;            // [n_rhs][nface_pts]
+  double *b;
+};
+
+__global__ void k_face_data(FaceDataArgs A) {
+  extern __shared__ double sm[];
+  const int row = blockIdx.x / A.n_rhs, r = blockIdx.x % A.n_rhs;
+  const int e = A.felems[row];
+  const int W = A.elem_W[e], P = W + 1, Q = 2 * W + 1;
+  const double *tb = A.qtab[W];
+  const double *B0 = tb, *B1 = tb + Q * P, *DQ = tb + 2 * Q * P, *KQ = DQ + Q * Q, *wq = KQ + Q * Q;
+  double *g = sm, *g1 = g + Q * Q, *g2 = g1 + Q * Q, *h0 = g2 + Q * Q, *h1 = h0 + Q * Q, *h2 = h1 + Q * Q;
+  double *ta = h2 + Q * Q, *tb2 = ta + Q * Q, *F = tb2 + Q * Q;  // F: P x P
+  const int64_t base = (int64_t)r * A.ndof + A.dof_off[e];
+  for (int fi_i = A.felem_ptr[row]; fi_i < A.felem_ptr[row + 1]; ++fi_i) {
+    const int fi = A.face_fi[fi_i];
+    const int a = fi >> 1, side = fi & 1;
+    const int64_t go = (int64_t)r * A.nface_pts + A.face_off[fi_i];
+    for (int t = threadIdx.x; t < Q * Q; t += blockDim.x) g[t] = A.g[go + t];
+    __syncthreads();
+    // tangential derivatives of the data on the face grid [t2][t1]
+    for (int t = threadIdx.x; t < Q * Q; t += blockDim.x) {
+      const int i = t % Q, j = t / Q;
+      double s1 = 0.0, s2 = 0.0;
+      for (int m = 0; m < Q; ++m) {
+        s1 += DQ[i * Q + m] * g[j * Q + m];
+        s2 += DQ[j * Q + m] * g[m * Q + i];
+      }
+      g1[t] = s1;
+      g2[t] = s2;
+    }
+    __syncthreads();
+    // h0 = (W x W) g ; h1 = H g1 ; h2 = H g2 with H = WxW + WxK + KxW
+    for (int t = threadIdx.x; t < Q * Q; t += blockDim.x) {
+      const int i = t % Q, j = t / Q;
+      h0[t] = wq[i] * wq[j] * g[t];
+      double k1 = 0.0, k2 = 0.0, l1 = 0.0, l2 = 0.0;
+      for (int m = 0; m < Q; ++m) {
+        k1 += KQ[i * Q + m] * g1[j * Q + m];  // K along t1
+        l1 += KQ[j * Q + m] * g1[m * Q + i];  // K along t2
+        k2 += KQ[i * Q + m] * g2[j * Q + m];
+        l2 += KQ[j * Q + m] * g2[m * Q + i];
+      }
+      h1[t] = wq[i] * wq[j] * g1[t] + wq[j] * k1 + wq[i] * l1;
+      h2[t] = wq[i] * wq[j] * g2[t] + wq[j] * k2 + wq[i] * l2;
+    }
+    __syncthreads();
+    // project to nodal face values: along t1 first (ta: [t2 q][p1]), then t2
+    for (int t = threadIdx.x; t < Q * P; t += blockDim.x) {
+      const int p1 = t % P, j = t / P;
+      double s0 = 0.0, s1 = 0.0;
+      for (int i = 0; i < Q; ++i) {
+        s0 += B0[i * P + p1] * h0[j * Q + i] + B1[i * P + p1] * h1[j * Q + i];
+        s1 += B0[i * P + p1] * h2[j * Q + i];
+      }
+      ta[j * P + p1] = s0;
+      tb2[j * P + p1] = s1;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < P * P; t += blockDim.x) {
+      const int p1 = t % P, p2 = t / P;
+      double s = 0.0;
+      for (int j = 0; j < Q; ++j) s += B0[j * P + p2] * ta[j * P + p1] + B1[j * P + p2] * tb2[j * P + p1];
+      F[t] = s;
+    }
+    __syncthreads();
+    const int nend = side ? P - 1 : 0;
+    for (int t = threadIdx.x; t < P * P; t += blockDim.x) {
+      const int p1 = t % P, p2 = t / P;
+      int idx;
+      if (a == 0) idx = (p2 * P + p1) * P + nend;
+      else if (a == 1) idx = (p2 * P + nend) * P + p1;
+      else idx = (nend * P + p2) * P + p1;
+      A.b[base + idx] += F[t];
+    }
+    __syncthreads();
+  }
+}
+
+// H^1 norms per (element, rhs): err = sum w J [(u - v)^2 + |grad(u - v)|^2],
+// nrm = sum w J [v^2 + |grad v|^2]; v a DOF vector (ref) or sampled (vq, gq).
+struct H1Args {
+  int n_rhs;
+  int64_t ndof, nquad;
+  const int64_t *dof_off, *coef_off;
+  const int32_t *elem_W;
+  const double *geo;  // s_x, s_y, s_z, J
+  const double *const *qtab;
+  const double *u, *ref, *vq, *gq;
+  double *part_err, *part_nrm;
+};
+
+__device__ void h1_fields(const double *blk, int P, int Q, const double *B0, const double *B1, double *X0, double *X1,
+                          double *T00, double *T01, double *T10) {
+  for (int t = threadIdx.x; t < Q * P * P; t += blockDim.x) {
+    const int qa = t % Q, l = t / Q;  // l = k*P + j
+    double a0 = 0.0, a1 = 0.0;
+    for (int i = 0; i < P; ++i) {
+      a0 += B0[qa * P + i] * blk[l * P + i];
+      a1 += B1[qa * P + i] * blk[l * P + i];
+    }
+    X0[l * Q + qa] = a0;
+    X1[l * Q + qa] = a1;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < Q * Q * P; t += blockDim.x) {
+    const int qa = t % Q, qb = (t / Q) % Q, k = t / (Q * Q);
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int j = 0; j < P; ++j) {
+      const double x0 = X0[(k * P + j) * Q + qa];
+      a += B0[qb * P + j] * x0;
+      b += B1[qb * P + j] * x0;
+      c += B0[qb * P + j] * X1[(k * P + j) * Q + qa];
+    }
+    T00[t] = a;
+    T01[t] = b;
+    T10[t] = c;
+  }
+  __syncthreads();
+}
+
+__global__ void k_h1(H1Args A) {
+  extern __shared__ double sm[];
+  const int item = blockIdx.x;
+  const int e = item / A.n_rhs, r = item - e * A.n_rhs;
+  const int W = A.elem_W[e], P = W + 1, Q = 2 * W + 1;
+  const double *tb = A.qtab[W];
+  const double *B0 = tb, *B1 = tb + Q * P, *wq = tb + 2 * Q * P + 2 * Q * Q;
+  const double *geo = A.geo + (int64_t)e * 4;
+  double *blk = sm, *X0 = blk + P * P * P, *X1 = X0 + Q * P * P, *T00 = X1 + Q * P * P, *T01 = T00 + Q * Q * P,
+         *T10 = T01 + Q * Q * P;
+  const int64_t base = (int64_t)r * A.ndof + A.dof_off[e];
+  double serr = 0.0, snrm = 0.0;
+  for (int pass = 0; pass < (A.ref ? 2 : 1); ++pass) {
+    for (int t = threadIdx.x; t < P * P * P; t += blockDim.x)
+      blk[t] = pass == 0 ? (A.ref ? A.u[base + t] - A.ref[base + t] : A.u[base + t]) : A.ref[base + t];
+    __syncthreads();
+    h1_fields(blk, P, Q, B0, B1, X0, X1, T00, T01, T10);
+    for (int t = threadIdx.x; t < Q * Q * Q; t += blockDim.x) {
+      const int qa = t % Q, qb = (t / Q) % Q, qc = t / (Q * Q);
+      double u = 0.0, ux = 0.0, uy = 0.0, uz = 0.0;
+      for (int k = 0; k < P; ++k) {
+        const int o = (k * Q + qb) * Q + qa;
+        u += B0[qc * P + k] * T00[o];
+        uz += B1[qc * P + k] * T00[o];
+        uy += B0[qc * P + k] * T01[o];
+        ux += B0[qc * P + k] * T10[o];
+      }
+      ux *= geo[0];
+      uy *= geo[1];
+      uz *= geo[2];
+      const double wJ = wq[qa] * wq[qb] * wq[qc] * geo[3];
+      if (A.ref) {
+        const double v = u * u + ux * ux + uy * uy + uz * uz;
+        if (pass == 0) serr += wJ * v;
+        else snrm += wJ * v;
+      } else {
+        const int64_t qi = (int64_t)r * A.nquad + A.coef_off[e] + t;
+        const int64_t gi = (int64_t)r * 3 * A.nquad + A.coef_off[e] + t;
+        const double v = A.vq[qi], gx = A.gq[gi], gy = A.gq[gi + A.nquad], gz = A.gq[gi + 2 * A.nquad];
+        serr += wJ * ((u - v) * (u - v) + (ux - gx) * (ux - gx) + (uy - gy) * (uy - gy) + (uz - gz) * (uz - gz));
+        snrm += wJ * (v * v + gx * gx + gy * gy + gz * gz);
+      }
+    }
+    __syncthreads();
+  }
+  serr = block_sum_d(serr);
+  snrm = block_sum_d(snrm);
+  if (threadIdx.x == 0) {
+    A.part_err[item] = serr;
+    A.part_nrm[item] = snrm;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+static ElemVecArgs elem_args(const hpse_mesh *m) {
+  ElemVecArgs a;
+  a.n_elem = m->n_elem;
+  a.n_rhs = m->n_rhs;
+  a.ndof = m->ndof;
+  a.dof_off = m->d_dof_off.as<int64_t>();
+  a.elem_W = m->d_elem_W.as<int32_t>();
+  return a;
+}
+
+static FinArgs fin_args(const hpse_mesh *m) {
+  FinArgs f;
+  f.n_rhs = m->n_rhs;
+  f.prob_ptr = m->d_prob_ptr.as<int32_t>();
+  f.prob_elems = m->d_prob_elems.as<int32_t>();
+  return f;
+}
+
+static int n_items_all(const hpse_mesh *m) { return m->n_elem * m->n_rhs; }
+static int npr_of(const hpse_mesh *m) { return m->n_problem * m->n_rhs; }
+
+template <typename T>
+static ApplyArgsT<T> apply_args(const hpse_mesh *m, const Group &g, const T *u, T *y) {
+  ApplyArgsT<T> a;
+  memset(&a, 0, sizeof(a));
+  a.u = u;
+  a.y = y;
+  a.elems = g.elems.as<int32_t>();
+  a.n_group = g.n;
+  a.n_rhs = m->n_rhs;
+  a.ndof = m->ndof;
+  a.dof_off = m->d_dof_off.as<int64_t>();
+  a.nbr = m->d_nbr.as<int32_t>();
+  a.geo = (sizeof(T) == 8) ? (const T *)m->d_geo64.p : (const T *)m->d_geo32.p;
+  a.prob = m->d_prob.as<int32_t>();
+  a.coef = (sizeof(T) == 8) ? (const T *)m->d_coef64.p : (const T *)m->d_coef32.p;
+  a.coef_off = m->d_coef_off.as<int64_t>();
+  a.nquad = m->nquad;
+  return a;
+}
+
+template <typename T>
+static PrecArgsT<T> prec_args(const hpse_mesh *m, const Group &g) {
+  PrecArgsT<T> a;
+  memset(&a, 0, sizeof(a));
+  a.elems = g.elems.as<int32_t>();
+  a.n_group = g.n;
+  a.n_rhs = m->n_rhs;
+  a.ndof = m->ndof;
+  a.dof_off = m->d_dof_off.as<int64_t>();
+  a.prob = m->d_prob.as<int32_t>();
+  return a;
+}
+
+static int prec_index(int prec) { return prec == HPSE_FP64 ? 0 : 1; }
+
+template <typename T>
+static hpse_status launch_apply_all(hpse_mesh *m, int mode, ApplyArgsT<T> base_args, cudaStream_t s) {
+  const int pi = sizeof(T) == 8 ? 0 : 1;
+  for (const Group &g : m->groups) {
+    ApplyArgsT<T> a = base_args;
+    a.elems = g.elems.as<int32_t>();
+    a.n_group = g.n;
+    const KernelSet &ks = g_sets[pi][g.W];
+    const int th = m->threads[0][pi][g.W];
+    CK(ks.apply(m->coef_kind, mode, &a, g.n * m->n_rhs, th, s));
+    ++g_launches;
+  }
+  return HPSE_OK;
+}
+
+template <typename T>
+static hpse_status launch_prec_all(hpse_mesh *m, int mode, PrecArgsT<T> base_args, cudaStream_t s) {
+  const int pi = sizeof(T) == 8 ? 0 : 1;
+  for (const Group &g : m->groups) {
+    PrecArgsT<T> a = base_args;
+    a.elems = g.elems.as<int32_t>();
+    a.n_group = g.n;
+    const KernelSet &ks = g_sets[pi][g.W];
+    const int th = m->threads[1][pi][g.W];
+    CK(ks.precond(mode, &a, g.n * m->n_rhs, th, s));
+    ++g_launches;
+  }
+  return HPSE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" const char *hpse_status_string(hpse_status s) {
+  switch (s) {
+    case HPSE_OK: return "ok";
+    case HPSE_ERR_INVALID_ARG: return "invalid argument";
+    case HPSE_ERR_NONMATCHING_FACE: return "non-matching face";
+    case HPSE_ERR_DEGREE: return "unsupported degree";
+    case HPSE_ERR_BREAKDOWN: return "PCG breakdown";
+    case HPSE_ERR_NO_CONVERGENCE: return "no convergence within the iteration cap";
+    case HPSE_ERR_TIMEOUT: return "time limit reached";
+    case HPSE_ERR_CUDA: return g_last_err[0] ? g_last_err : "CUDA error";
+    case HPSE_ERR_OOM: return "out of device memory";
+    case HPSE_ERR_NO_DATA: return "no data: call hpse_set_data first";
+  }
+  return "unknown status";
+}
+
+extern "C" int64_t hpse_kernel_launch_count(int32_t reset) {
+  const long long v = g_launches;
+  if (reset) g_launches = 0;
+  return v;
+}
+
+extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse_mesh **out) {
+  if (!d || !out) return HPSE_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (d->n_elem < 0 || d->n_problem < 1 || d->n_rhs < 1) return HPSE_ERR_INVALID_ARG;
+  if (d->coef_kind != HPSE_COEF_LAPLACE && d->coef_kind != HPSE_COEF_SCALAR) return HPSE_ERR_INVALID_ARG;
+  if (d->n_elem > 0 && (!d->elem_W || !d->elem_problem || !d->elem_lo || !d->elem_hi || !d->elem_nbr))
+    return HPSE_ERR_INVALID_ARG;
+  const int E = d->n_elem;
+  if ((int64_t)E * d->n_rhs > 2147483647LL) return HPSE_ERR_INVALID_ARG;
+  std::unique_ptr<hpse_mesh> m(new hpse_mesh());
+  m->device = device;
+  m->n_elem = E;
+  m->n_problem = d->n_problem;
+  m->n_rhs = d->n_rhs;
+  m->coef_kind = d->coef_kind;
+  m->W.assign(d->elem_W, d->elem_W + E);
+  m->prob.assign(d->elem_problem, d->elem_problem + E);
+  m->nbr.assign(d->elem_nbr, d->elem_nbr + 6 * (size_t)E);
+  m->lo.assign(d->elem_lo, d->elem_lo + 3 * (size_t)E);
+  m->hi.assign(d->elem_hi, d->elem_hi + 3 * (size_t)E);
+  // ---- validation (Section 2.3: one-to-one matching faces) -----------------
+  for (int e = 0; e < E; ++e) {
+    if (m->W[e] < 1 || m->W[e] > HPSE_MAX_W) return HPSE_ERR_DEGREE;
+    if (m->prob[e] < 0 || m->prob[e] >= m->n_problem) return HPSE_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+      if (!(m->hi[3 * e + a] > m->lo[3 * e + a]) || !std::isfinite(m->lo[3 * e + a]) ||
+          !std::isfinite(m->hi[3 * e + a]))
+        return HPSE_ERR_INVALID_ARG;
+  }
+  for (int e = 0; e < E; ++e)
+    for (int fi = 0; fi < 6; ++fi) {
+      const int n = m->nbr[6 * e + fi];
+      if (n < -1 || n >= E || n == e) return HPSE_ERR_INVALID_ARG;
+      if (n < 0) continue;
+      if (m->nbr[6 * n + (fi ^ 1)] != e) return HPSE_ERR_NONMATCHING_FACE;
+      if (m->prob[n] != m->prob[e]) return HPSE_ERR_INVALID_ARG;
+      const int a = fi >> 1, side = fi & 1;
+      const double xe = side ? m->hi[3 * e + a] : m->lo[3 * e + a];
+      const double xn = side ? m->lo[3 * n + a] : m->hi[3 * n + a];
+      const double scale = std::max(1.0, std::fabs(xe));
+      if (std::fabs(xe - xn) > 1e-12 * scale) return HPSE_ERR_NONMATCHING_FACE;
+      for (int b = 0; b < 3; ++b) {
+        if (b == a) continue;
+        const double s2 = std::max(1.0, std::fabs(m->hi[3 * e + b]));
+        if (std::fabs(m->lo[3 * e + b] - m->lo[3 * n + b]) > 1e-12 * s2 ||
+            std::fabs(m->hi[3 * e + b] - m->hi[3 * n + b]) > 1e-12 * s2)
+          return HPSE_ERR_NONMATCHING_FACE;
+      }
+      if (m->W[n] != m->W[e]) return HPSE_ERR_DEGREE;
+    }
+  // ---- offsets, groups, boundary faces -------------------------------------
+  m->dof_off.assign(E, 0);
+  m->coef_off.assign(E, 0);
+  int64_t od = 0, oq = 0;
+  for (int e = 0; e < E; ++e) {
+    const int P = m->W[e] + 1, Q = 2 * m->W[e] + 1;
+    m->dof_off[e] = od;
+    m->coef_off[e] = oq;
+    od += (int64_t)P * P * P;
+    oq += (int64_t)Q * Q * Q;
+  }
+  m->ndof = od;
+  m->nquad = oq;
+  int64_t of = 0;
+  for (int e = 0; e < E; ++e)
+    for (int fi = 0; fi < 6; ++fi)
+      if (m->nbr[6 * e + fi] < 0) {
+        const int Q = 2 * m->W[e] + 1;
+        m->bface_elem.push_back(e);
+        m->bface_fi.push_back(fi);
+        m->bface_off.push_back(of);
+        of += (int64_t)Q * Q;
+      }
+  m->nface_pts = of;
+  m->prob_ptr.assign(m->n_problem + 1, 0);
+  for (int e = 0; e < E; ++e) m->prob_ptr[m->prob[e] + 1]++;
+  for (int p = 0; p < m->n_problem; ++p) m->prob_ptr[p + 1] += m->prob_ptr[p];
+  {
+    std::vector<int> fill(m->prob_ptr.begin(), m->prob_ptr.end() - 1);
+    m->prob_elems.assign(E, 0);
+    for (int e = 0; e < E; ++e) m->prob_elems[fill[m->prob[e]]++] = e;
+  }
+  for (int k = 0; k < 2; ++k)
+    for (int p = 0; p < 2; ++p)
+      for (int w = 0; w <= HPSE_MAX_W; ++w) m->threads[k][p][w] = w >= 1 ? default_threads(k, p, w) : 0;
+
+  // ---- device ---------------------------------------------------------------
+  init_registry();
+  CK(cudaSetDevice(device));
+  std::map<int, std::vector<int>> by_w;
+  for (int e = 0; e < E; ++e) by_w[m->W[e]].push_back(e);
+  for (auto &kv : by_w) {
+    const int W = kv.first;
+    m->tabs[W] = hm::build_tables(W);
+    const hm::DegreeTables &t = m->tabs[W];
+    CK(g_sets[0][W].upload(t.packed.data()));
+    CK(g_sets[1][W].upload(t.packed.data()));
+    Group g;
+    g.W = W;
+    g.n = (int)kv.second.size();
+    m->groups.push_back(std::move(g));
+    CK(upload(m->groups.back().elems, kv.second));
+    // FP64 Q-grid tables for the face data and the H^1 error: B0, B1, DQ, KQ, wq
+    std::vector<double> q;
+    q.insert(q.end(), t.B0.begin(), t.B0.end());
+    q.insert(q.end(), t.B1.begin(), t.B1.end());
+    q.insert(q.end(), t.DQ.begin(), t.DQ.end());
+    q.insert(q.end(), t.KQ.begin(), t.KQ.end());
+    q.insert(q.end(), t.wq.begin(), t.wq.end());
+    CK(upload(m->d_qtab[W], q));
+  }
+  std::vector<double> geo(4 * (size_t)E);
+  std::vector<float> geo32(4 * (size_t)E);
+  for (int e = 0; e < E; ++e) {
+    double J = 1.0;
+    for (int a = 0; a < 3; ++a) {
+      const double h = m->hi[3 * e + a] - m->lo[3 * e + a];
+      geo[4 * e + a] = 2.0 / h;
+      J *= h / 2.0;
+    }
+    geo[4 * e + 3] = J;
+    for (int k = 0; k < 4; ++k) geo32[4 * e + k] = (float)geo[4 * e + k];
+  }
+  CK(upload(m->d_dof_off, m->dof_off));
+  CK(upload(m->d_coef_off, m->coef_off));
+  CK(upload(m->d_nbr, m->nbr));
+  CK(upload(m->d_geo64, geo));
+  CK(upload(m->d_geo32, geo32));
+  CK(upload(m->d_prob, m->prob));
+  CK(upload(m->d_prob_ptr, m->prob_ptr));
+  CK(upload(m->d_prob_elems, m->prob_elems));
+  CK(upload(m->d_elem_W, m->W));
+  *out = m.release();
+  return HPSE_OK;
+}
+
+extern "C" void hpse_destroy(hpse_mesh *m) {
+  if (!m) return;
+  cudaSetDevice(m->device);
+  delete m;
+}
+
+extern "C" int64_t hpse_ndof(const hpse_mesh *m) { return m ? m->ndof : -1; }
+extern "C" int64_t hpse_nquad(const hpse_mesh *m) { return m ? m->nquad : -1; }
+extern "C" int64_t hpse_nface_points(const hpse_mesh *m) { return m ? m->nface_pts : -1; }
+extern "C" int32_t hpse_nrhs(const hpse_mesh *m) { return m ? m->n_rhs : -1; }
+extern "C" int64_t hpse_n_boundary_faces(const hpse_mesh *m) { return m ? (int64_t)m->bface_elem.size() : -1; }
+
+extern "C" hpse_status hpse_query_points(const hpse_mesh *m, double *vol_axes, double *face_norm) {
+  if (!m) return HPSE_ERR_INVALID_ARG;
+  if (vol_axes) {
+    int64_t o = 0;
+    for (int e = 0; e < m->n_elem; ++e) {
+      const hm::DegreeTables &t = m->tabs.at(m->W[e]);
+      for (int a = 0; a < 3; ++a) {
+        const double lo = m->lo[3 * e + a], h = m->hi[3 * e + a] - lo;
+        for (int q = 0; q < t.Q; ++q) vol_axes[o++] = lo + (t.xq[q] + 1.0) * 0.5 * h;
+      }
+    }
+  }
+  if (face_norm) {
+    for (size_t i = 0; i < m->bface_elem.size(); ++i) {
+      const int e = m->bface_elem[i], fi = m->bface_fi[i];
+      const int a = fi >> 1;
+      face_norm[i] = (fi & 1) ? m->hi[3 * e + a] : m->lo[3 * e + a];
+    }
+  }
+  return HPSE_OK;
+}
+
+extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data) {
+  if (!m || !data || (!data->f && m->nquad > 0)) return HPSE_ERR_INVALID_ARG;
+  if (m->coef_kind == HPSE_COEF_SCALAR && (!data->a || !data->grad_a)) return HPSE_ERR_INVALID_ARG;
+  CK(cudaSetDevice(m->device));
+  const int64_t nq = m->nquad;
+  const int R = m->n_rhs;
+  // coefficients at the volume points: m = w J a^2, d_k = s_k a_k / a; wJa for b
+  std::vector<double> wja(nq);
+  std::vector<double> coef;
+  if (m->coef_kind == HPSE_COEF_SCALAR) coef.assign(4 * (size_t)nq, 0.0);
+  for (int e = 0; e < m->n_elem; ++e) {
+    const hm::DegreeTables &t = m->tabs.at(m->W[e]);
+    const int Q = t.Q;
+    double s[3], J = 1.0;
+    for (int a = 0; a < 3; ++a) {
+      const double h = m->hi[3 * e + a] - m->lo[3 * e + a];
+      s[a] = 2.0 / h;
+      J *= h / 2.0;
+    }
+    const int64_t o = m->coef_off[e];
+    for (int c = 0; c < Q; ++c)
+      for (int b = 0; b < Q; ++b)
+        for (int a = 0; a < Q; ++a) {
+          const int64_t i = o + ((int64_t)c * Q + b) * Q + a;
+          const double wJ = t.wq[a] * t.wq[b] * t.wq[c] * J;
+          if (m->coef_kind == HPSE_COEF_SCALAR) {
+            const double av = data->a[i];
+            if (!(av > 0.0) || !std::isfinite(av)) return HPSE_ERR_INVALID_ARG;  // ellipticity
+            coef[i] = wJ * av * av;
+            for (int k = 0; k < 3; ++k) coef[(k + 1) * nq + i] = s[k] * data->grad_a[k * nq + i] / av;
+            wja[i] = wJ * av;
+          } else {
+            wja[i] = wJ;
+          }
+        }
+  }
+  if (m->coef_kind == HPSE_COEF_SCALAR) {
+    std::vector<float> c32(coef.size());
+    for (size_t i = 0; i < coef.size(); ++i) c32[i] = (float)coef[i];
+    CK(upload(m->d_coef64, coef));
+    CK(upload(m->d_coef32, c32));
+  }
+  const size_t nv = (size_t)R * m->ndof;
+  CK(m->d_b.alloc(nv * sizeof(double)));
+  if (nv) CK(cudaMemset(m->d_b.p, 0, nv * sizeof(double)));
+  // volume part of b: transpose kernel on rho_b = -(w J a) f
+  if (nq > 0 && m->n_elem > 0) {
+    DevBuf dwja, df, drho;
+    CK(upload(dwja, wja));
+    CK(df.alloc((size_t)R * nq * sizeof(double)));
+    CK(cudaMemcpy(df.p, data->f, (size_t)R * nq * sizeof(double), cudaMemcpyHostToDevice));
+    CK(drho.alloc((size_t)R * nq * sizeof(double)));
+    k_rho_b<<<1024, 256>>>((int64_t)R * nq, dwja.as<double>(), df.as<double>(), nq, drho.as<double>());
+    CK(cudaGetLastError());
+    ++g_launches;
+    ApplyArgsT<double> a = apply_args<double>(m, m->groups[0], nullptr, m->d_b.as<double>());
+    a.rho = drho.as<double>();
+    a.skip_faces = 1;
+    hpse_status st = launch_apply_all<double>(m, MODE_TRANSPOSE, a, 0);
+    if (st != HPSE_OK) return st;
+    CK(cudaDeviceSynchronize());
+  }
+  // Dirichlet data part of b
+  if (data->g && m->nface_pts > 0) {
+    std::vector<int> felem_ptr(1, 0), felems, ffi;
+    std::vector<int64_t> foff;
+    for (size_t i = 0; i < m->bface_elem.size(); ++i) {
+      if (felems.empty() || felems.back() != m->bface_elem[i]) {
+        if (!felems.empty()) felem_ptr.push_back((int)ffi.size());
+        felems.push_back(m->bface_elem[i]);
+      }
+      ffi.push_back(m->bface_fi[i]);
+      foff.push_back(m->bface_off[i]);
+    }
+    felem_ptr.push_back((int)ffi.size());
+    DevBuf dptr, delems, dfi, doff, dg, dtabs;
+    CK(upload(dptr, felem_ptr));
+    CK(upload(delems, felems));
+    CK(upload(dfi, ffi));
+    CK(upload(doff, foff));
+    CK(dg.alloc((size_t)R * m->nface_pts * sizeof(double)));
+    CK(cudaMemcpy(dg.p, data->g, (size_t)R * m->nface_pts * sizeof(double), cudaMemcpyHostToDevice));
+    std::vector<const double *> tp(HPSE_MAX_W + 1, nullptr);
+    int Wmax = 1;
+    for (auto &kv : m->d_qtab) {
+      tp[kv.first] = kv.second.as<double>();
+      Wmax = std::max(Wmax, kv.first);
+    }
+    CK(upload(dtabs, tp));
+    FaceDataArgs A;
+    A.n_rhs = R;
+    A.ndof = m->ndof;
+    A.nface_pts = m->nface_pts;
+    A.dof_off = m->d_dof_off.as<int64_t>();
+    A.elem_W = m->d_elem_W.as<int32_t>();
+    A.felem_ptr = dptr.as<int32_t>();
+    A.felems = delems.as<int32_t>();
+    A.face_fi = dfi.as<int32_t>();
+    A.face_off = doff.as<int64_t>();
+    A.qtab = dtabs.as<const double *>();
+    A.g = dg.as<double>();
+    A.b = m->d_b.as<double>();
+    const int Q = 2 * Wmax + 1, P = Wmax + 1;
+    const size_t smem = (size_t)(8 * Q * Q + 2 * Q * P + P * P) * sizeof(double);
+    CK(cudaFuncSetAttribute(k_face_data, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_face_data<<<(int)felems.size() * R, 128, smem>>>(A);
+    CK(cudaGetLastError());
+    ++g_launches;
+    CK(cudaDeviceSynchronize());
+  }
+  // ||b||^2 per (problem, rhs)
+  {
+    const int npr = npr_of(m);
+    DevBuf part;
+    CK(part.alloc((size_t)std::max(1, n_items_all(m)) * sizeof(double)));
+    CK(m->d_bnorm2.alloc((size_t)npr * sizeof(double)));
+    if (n_items_all(m) > 0) {
+      k_dot<double, double><<<n_items_all(m), 128>>>(elem_args(m), m->d_b.as<double>(), m->d_b.as<double>(),
+                                                     part.as<double>());
+      CK(cudaGetLastError());
+      ++g_launches;
+    }
+    k_bnorm<<<npr, 128>>>(fin_args(m), part.as<double>(), m->d_bnorm2.as<double>());
+    CK(cudaGetLastError());
+    ++g_launches;
+    CK(cudaDeviceSynchronize());
+  }
+  m->has_data = true;
+  return HPSE_OK;
+}
+
+extern "C" hpse_status hpse_get_rhs(hpse_mesh *m, double *b, void *stream) {
+  if (!m || (!b && m->ndof > 0)) return HPSE_ERR_INVALID_ARG;
+  if (!m->has_data) return HPSE_ERR_NO_DATA;
+  CK(cudaSetDevice(m->device));
+  const size_t nv = (size_t)m->n_rhs * m->ndof;
+  if (nv) CK(cudaMemcpyAsync(b, m->d_b.p, nv * sizeof(double), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return HPSE_OK;
+}
+
+static hpse_status check_coef(hpse_mesh *m) {
+  if (m->coef_kind == HPSE_COEF_SCALAR && !m->has_data) return HPSE_ERR_NO_DATA;
+  return HPSE_OK;
+}
+
+extern "C" hpse_status hpse_apply_operator(hpse_mesh *m, int32_t prec, const void *u, void *y, void *stream) {
+  if (!m || (prec != HPSE_FP64 && prec != HPSE_FP32)) return HPSE_ERR_INVALID_ARG;
+  if (m->ndof == 0) return HPSE_OK;
+  if (!u || !y || u == y) return HPSE_ERR_INVALID_ARG;
+  hpse_status st = check_coef(m);
+  if (st != HPSE_OK) return st;
+  CK(cudaSetDevice(m->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (prec == HPSE_FP64) {
+    ApplyArgsT<double> a = apply_args<double>(m, m->groups[0], (const double *)u, (double *)y);
+    return launch_apply_all<double>(m, MODE_PLAIN, a, s);
+  }
+  ApplyArgsT<float> a = apply_args<float>(m, m->groups[0], (const float *)u, (float *)y);
+  return launch_apply_all<float>(m, MODE_PLAIN, a, s);
+}
+
+extern "C" hpse_status hpse_apply_preconditioner(hpse_mesh *m, int32_t prec, const void *r, void *z, void *stream) {
+  if (!m || (prec != HPSE_FP64 && prec != HPSE_FP32)) return HPSE_ERR_INVALID_ARG;
+  if (m->ndof == 0) return HPSE_OK;
+  if (!r || !z || r == z) return HPSE_ERR_INVALID_ARG;
+  CK(cudaSetDevice(m->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (prec == HPSE_FP64) {
+    PrecArgsT<double> a = prec_args<double>(m, m->groups[0]);
+    a.rin = (const double *)r;
+    a.zout = (double *)z;
+    return launch_prec_all<double>(m, MODE_PLAIN, a, s);
+  }
+  PrecArgsT<float> a = prec_args<float>(m, m->groups[0]);
+  a.rin = (const float *)r;
+  a.zout = (float *)z;
+  return launch_prec_all<float>(m, MODE_PLAIN, a, s);
+}
+
+extern "C" hpse_status hpse_set_block_threads(hpse_mesh *m, int32_t kind, int32_t prec, int32_t W, int32_t threads) {
+  if (!m || kind < 0 || kind > 1 || (prec != 0 && prec != 1) || W < 1 || W > HPSE_MAX_W) return HPSE_ERR_INVALID_ARG;
+  const int maxt = kind == 1 ? 256 : (prec == HPSE_FP64 ? 256 : 384);
+  if (threads == 0) threads = default_threads(kind, prec, W);
+  if (threads < 32 || threads > maxt || threads % 32) return HPSE_ERR_INVALID_ARG;
+  m->threads[kind][prec][W] = threads;
+  if (m->work) {
+    for (auto &g : m->work->graphs) cudaGraphExecDestroy(g.second);
+    m->work->graphs.clear();
+  }
+  return HPSE_OK;
+}
+
+extern "C" int32_t hpse_get_block_threads(const hpse_mesh *m, int32_t kind, int32_t prec, int32_t W) {
+  if (!m || kind < 0 || kind > 1 || (prec != 0 && prec != 1) || W < 1 || W > HPSE_MAX_W) return -1;
+  return m->threads[kind][prec][W];
+}
+
+extern "C" hpse_status hpse_work_counts(const hpse_mesh *m, double *vol_macs, double *face_macs) {
+  if (!m) return HPSE_ERR_INVALID_ARG;
+  double v = 0.0, f = 0.0;
+  const bool var = m->coef_kind == HPSE_COEF_SCALAR;
+  for (int e = 0; e < m->n_elem; ++e) {
+    const double P = m->W[e] + 1, Q = 2 * m->W[e] + 1;
+    // forward (n1, n2, n3) = (3,5,5) or (2,3,2), and the same for the transpose
+    const double n1 = var ? 3 : 2, n2 = var ? 5 : 3, n3 = var ? 5 : 2;
+    v += 2.0 * (n1 * Q * P * P * P + n2 * Q * Q * P * P + n3 * Q * Q * Q * P);
+    for (int fi = 0; fi < 6; ++fi) {
+      // traces (2 P^3 + 2 P^3 each side), norms (2 P^3 L2 + 3 x 4 P^3 H^{1/2}), transposes (~3 P^3)
+      f += (m->nbr[6 * e + fi] >= 0) ? 23.0 * P * P * P : 15.0 * P * P * P;
+    }
+  }
+  if (vol_macs) *vol_macs = v;
+  if (face_macs) *face_macs = f;
+  return HPSE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// PCG driver
+// ---------------------------------------------------------------------------
+static hpse_status ensure_work(hpse_mesh *m) {
+  if (m->work) return HPSE_OK;
+  std::unique_ptr<SolverWork> w(new SolverWork());
+  const size_t n = (size_t)m->n_rhs * m->ndof;
+  w->n = n;
+  const size_t d = n * sizeof(double), f = n * sizeof(float);
+  CK(w->x64.alloc(d));
+  CK(w->r64.alloc(d));
+  CK(w->z64.alloc(d));
+  CK(w->pa64.alloc(d));
+  CK(w->pb64.alloc(d));
+  CK(w->q64.alloc(d));
+  CK(w->x32.alloc(f));
+  CK(w->r32.alloc(f));
+  CK(w->z32.alloc(f));
+  CK(w->pa32.alloc(f));
+  CK(w->pb32.alloc(f));
+  CK(w->q32.alloc(f));
+  const size_t ni = (size_t)std::max(1, n_items_all(m));
+  CK(w->part0.alloc(ni * sizeof(double)));
+  CK(w->part1.alloc(ni * sizeof(double)));
+  CK(w->part2.alloc(ni * sizeof(double)));
+  const int npr = npr_of(m);
+  CK(w->sc.alloc((size_t)12 * npr * sizeof(double)));
+  CK(w->flags.alloc((size_t)(3 * npr + 1) * sizeof(int32_t)));
+  CK(cudaMallocHost(&w->h_flags, (size_t)(3 * npr + 1) * sizeof(int32_t)));
+  CK(cudaMallocHost(&w->h_sc, (size_t)12 * npr * sizeof(double)));
+  CK(cudaStreamCreateWithFlags(&w->st, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&w->ev, cudaEventDisableTiming));
+  m->work = std::move(w);
+  return HPSE_OK;
+}
+
+// one PCG iteration (apply with fused direction update, alpha, update +
+// preconditioner, beta); pin/pout are the ping-pong direction buffers
+template <typename T>
+static hpse_status pcg_iteration(hpse_mesh *m, T *x, T *r, T *z, T *pin, T *pout, T *q, cudaStream_t s) {
+  SolverWork &w = *m->work;
+  const int npr = npr_of(m);
+  Scalars S = scalars_of(w, npr);
+  ApplyArgsT<T> a = apply_args<T>(m, m->groups[0], pin, q);
+  a.z = z;
+  a.beta = S.beta;
+  a.pnew = pout;
+  a.partial = w.part0.as<double>();
+  hpse_status st = launch_apply_all<T>(m, MODE_PCG, a, s);
+  if (st != HPSE_OK) return st;
+  k_fin_alpha<<<npr, 128, 0, s>>>(fin_args(m), S, w.part0.as<double>());
+  CK(cudaGetLastError());
+  ++g_launches;
+  PrecArgsT<T> pa = prec_args<T>(m, m->groups[0]);
+  pa.x = x;
+  pa.r = r;
+  pa.p = pout;
+  pa.q = q;
+  pa.zout = z;
+  pa.alpha = S.alpha;
+  pa.part_rr = w.part1.as<double>();
+  pa.part_rz = w.part2.as<double>();
+  st = launch_prec_all<T>(m, MODE_PCG, pa, s);
+  if (st != HPSE_OK) return st;
+  k_fin_beta<<<npr, 128, 0, s>>>(fin_args(m), S, w.part1.as<double>(), w.part2.as<double>());
+  CK(cudaGetLastError());
+  ++g_launches;
+  return HPSE_OK;
+}
+
+// Run PCG on A x = r (x, r, z, pa, pb, q device buffers of type T) starting
+// from x = 0, for the (problem, rhs) pairs with scale != 0 (or all when
+// scale == nullptr), to relative tolerance rel_tol.  Uses a CUDA graph of
+// `chunk` iterations (chunk even) and checks convergence on the host after
+// each replay.  Returns the iterations done (max over pairs) in *iters.
+template <typename T>
+static hpse_status run_pcg(hpse_mesh *m, T *x, T *r, T *z, T *pa, T *pb, T *q, double rel_tol, int max_iter,
+                           int chunk, const double *scale, double t_deadline, int *iters, int *status) {
+  SolverWork &w = *m->work;
+  cudaStream_t s = w.st;
+  const int npr = npr_of(m);
+  Scalars S = scalars_of(w, npr);
+  const size_t nb = w.n * sizeof(T);
+  *status = HPSE_OK;
+  CK(cudaMemsetAsync(x, 0, nb, s));
+  CK(cudaMemsetAsync(pa, 0, nb, s));
+  CK(cudaMemsetAsync(S.status, 0, npr * sizeof(int32_t), s));
+  // z = C^{-1} r ; rz, rr
+  {
+    PrecArgsT<T> p = prec_args<T>(m, m->groups[0]);
+    p.rin = r;
+    p.zout = z;
+    hpse_status st = launch_prec_all<T>(m, MODE_PLAIN, p, s);
+    if (st != HPSE_OK) return st;
+    k_dot<T, T><<<n_items_all(m), 128, 0, s>>>(elem_args(m), r, z, w.part0.as<double>());
+    k_dot<T, T><<<n_items_all(m), 128, 0, s>>>(elem_args(m), r, r, w.part1.as<double>());
+    k_fin_init<<<npr, 128, 0, s>>>(fin_args(m), S, w.part0.as<double>(), w.part1.as<double>(), rel_tol, scale);
+    CK(cudaGetLastError());
+    g_launches += 3;
+  }
+  if (chunk < 2) chunk = 2;
+  chunk += chunk & 1;
+  const long long key = (long long)chunk * 4 + (sizeof(T) == 8 ? 0 : 1) * 2 + (x == (T *)w.x64.p ? 0 : 1);
+  cudaGraphExec_t exec = nullptr;
+  auto it = w.graphs.find(key);
+  if (it == w.graphs.end()) {
+    cudaGraph_t graph;
+    const long long before = g_launches;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    hpse_status st = HPSE_OK;
+    for (int i = 0; i < chunk && st == HPSE_OK; i += 2) {
+      st = pcg_iteration<T>(m, x, r, z, pa, pb, q, s);
+      if (st == HPSE_OK) st = pcg_iteration<T>(m, x, r, z, pb, pa, q, s);
+    }
+    if (st == HPSE_OK) {
+      k_count_active<<<1, 256, 0, s>>>(S.active, npr, S.n_active);
+      ++g_launches;
+    }
+    cudaError_t ce = cudaStreamEndCapture(s, &graph);
+    if (st != HPSE_OK) return st;
+    CK(ce);
+    CK(cudaGraphInstantiate(&exec, graph, 0));
+    cudaGraphDestroy(graph);
+    w.graphs[key] = exec;
+    w.graph_launches[key] = (int)(g_launches - before);
+    g_launches = before;
+  } else {
+    exec = it->second;
+  }
+  const int per_replay = w.graph_launches[key];
+  int done = 0;
+  while (true) {
+    CK(cudaGraphLaunch(exec, s));
+    g_launches += per_replay;
+    done += chunk;
+    CK(cudaMemcpyAsync(w.h_flags, w.flags.p, (size_t)(3 * npr + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int n_active = w.h_flags[3 * npr];
+    if (n_active == 0) break;
+    if (done >= max_iter) {
+      *status = HPSE_ERR_NO_CONVERGENCE;
+      break;
+    }
+    if (t_deadline > 0) {
+      const double now =
+          std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+      if (now > t_deadline) {
+        *status = HPSE_ERR_TIMEOUT;
+        break;
+      }
+    }
+  }
+  int mx = 0;
+  for (int i = 0; i < npr; ++i) {
+    mx = std::max(mx, w.h_flags[npr + i]);
+    if (w.h_flags[2 * npr + i] != HPSE_OK && *status == HPSE_OK) *status = w.h_flags[2 * npr + i];
+  }
+  *iters = mx;
+  return HPSE_OK;
+}
+
+// r64 = b - A x64 (FP64) and per-pair relative residual / refinement scale
+static hpse_status fp64_residual(hpse_mesh *m, const double *x64, double tol, double *rel, double *scale,
+                                 double *rnorm, cudaStream_t s) {
+  SolverWork &w = *m->work;
+  ApplyArgsT<double> a = apply_args<double>(m, m->groups[0], x64, w.q64.as<double>());
+  hpse_status st = launch_apply_all<double>(m, MODE_PLAIN, a, s);
+  if (st != HPSE_OK) return st;
+  k_residual<<<n_items_all(m), 128, 0, s>>>(elem_args(m), m->d_b.as<double>(), w.q64.as<double>(),
+                                           w.r64.as<double>(), w.part0.as<double>());
+  k_fin_outer<<<npr_of(m), 128, 0, s>>>(fin_args(m), w.part0.as<double>(), m->d_bnorm2.as<double>(), tol, rel, scale,
+                                        rnorm);
+  CK(cudaGetLastError());
+  g_launches += 2;
+  return HPSE_OK;
+}
+
+extern "C" hpse_status hpse_pcg_solve(hpse_mesh *m, const hpse_solve_opts *o, double *x, hpse_solve_report *rep,
+                                      void *stream) {
+  if (!m || !o || !rep) return HPSE_ERR_INVALID_ARG;
+  memset(rep, 0, sizeof(*rep));
+  if (!m->has_data) return HPSE_ERR_NO_DATA;
+  if (!(o->tol > 0.0) || o->max_iter < 1 || (o->prec != HPSE_FP64 && o->prec != HPSE_FP32)) return HPSE_ERR_INVALID_ARG;
+  if (m->ndof == 0) return HPSE_OK;
+  if (!x) return HPSE_ERR_INVALID_ARG;
+  CK(cudaSetDevice(m->device));
+  hpse_status st = ensure_work(m);
+  if (st != HPSE_OK) return st;
+  SolverWork &w = *m->work;
+  cudaStream_t us = (cudaStream_t)stream;
+  cudaStream_t s = w.st;
+  // order after the caller's stream
+  CK(cudaEventRecord(w.ev, us));
+  CK(cudaStreamWaitEvent(s, w.ev, 0));
+  const int npr = npr_of(m);
+  const size_t nb = w.n * sizeof(double);
+  const double t0 = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+  const double deadline = o->time_limit_s > 0 ? t0 + o->time_limit_s : 0.0;
+  const int chunk = o->check_every > 0 ? o->check_every : 16;
+  double *sc_rel = w.sc.as<double>() + 8 * npr;
+  double *sc_scale = w.sc.as<double>() + 9 * npr;
+  double *sc_rnorm = w.sc.as<double>() + 10 * npr;
+  int total_it = 0, status = HPSE_OK, sweeps = 0, applies = 0;
+  if (o->zero_init) CK(cudaMemsetAsync(x, 0, nb, s));
+  if (o->prec == HPSE_FP64) {
+    // plain FP64 PCG on A d = b - A x0, x = x0 + d
+    bool x0_zero = o->zero_init != 0;
+    if (x0_zero) {
+      CK(cudaMemcpyAsync(w.r64.p, m->d_b.p, nb, cudaMemcpyDeviceToDevice, s));
+    } else {
+      st = fp64_residual(m, x, o->tol, sc_rel, sc_scale, sc_rnorm, s);
+      if (st != HPSE_OK) return st;
+      ++applies;
+    }
+    int it = 0;
+    st = run_pcg<double>(m, w.x64.as<double>(), w.r64.as<double>(), w.z64.as<double>(), w.pa64.as<double>(),
+                         w.pb64.as<double>(), w.q64.as<double>(), o->tol, o->max_iter, chunk, nullptr, deadline, &it,
+                         &status);
+    if (st != HPSE_OK) return st;
+    // relative tolerance of run_pcg is relative to ||r0||; for x0 = 0 that is ||b||
+    if (x0_zero) {
+      CK(cudaMemcpyAsync(x, w.x64.p, nb, cudaMemcpyDeviceToDevice, s));
+    } else {
+      k_add64<<<n_items_all(m), 128, 0, s>>>(elem_args(m), w.x64.as<double>(), x);
+      CK(cudaGetLastError());
+      ++g_launches;
+    }
+    total_it = it;
+    applies += it;
+    sweeps = 1;
+  } else {
+    // FP32 operator applies inside FP64 iterative refinement
+    const int max_sweeps = o->max_sweeps > 0 ? o->max_sweeps : 20;
+    const double itol = o->inner_tol > 0 ? o->inner_tol : 1e-4;
+    bool first = o->zero_init != 0;
+    while (true) {
+      if (first) {
+        CK(cudaMemcpyAsync(w.r64.p, m->d_b.p, nb, cudaMemcpyDeviceToDevice, s));
+        k_dot<double, double><<<n_items_all(m), 128, 0, s>>>(elem_args(m), w.r64.as<double>(), w.r64.as<double>(),
+                                                             w.part0.as<double>());
+        k_fin_outer<<<npr, 128, 0, s>>>(fin_args(m), w.part0.as<double>(), m->d_bnorm2.as<double>(), o->tol, sc_rel,
+                                        sc_scale, sc_rnorm);
+        CK(cudaGetLastError());
+        g_launches += 2;
+        first = false;
+      } else {
+        st = fp64_residual(m, x, o->tol, sc_rel, sc_scale, sc_rnorm, s);
+        if (st != HPSE_OK) return st;
+        ++applies;
+      }
+      CK(cudaMemcpyAsync(w.h_sc, w.sc.p, (size_t)12 * npr * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      double worst = 0.0;
+      bool any = false;
+      for (int i = 0; i < npr; ++i) {
+        worst = std::max(worst, w.h_sc[8 * npr + i]);
+        if (w.h_sc[9 * npr + i] != 0.0) any = true;
+      }
+      rep->rel_residual = worst;
+      if (!any) break;
+      if (sweeps >= max_sweeps || total_it >= o->max_iter) {
+        status = HPSE_ERR_NO_CONVERGENCE;
+        break;
+      }
+      // inner FP32 PCG on A d = r64 / ||r64||
+      k_scale_to_f32<<<n_items_all(m), 128, 0, s>>>(elem_args(m), m->d_prob.as<int32_t>(), m->n_rhs,
+                                                    w.r64.as<double>(), sc_scale, w.r32.as<float>());
+      CK(cudaGetLastError());
+      ++g_launches;
+      int it = 0, ist = HPSE_OK;
+      st = run_pcg<float>(m, w.x32.as<float>(), w.r32.as<float>(), w.z32.as<float>(), w.pa32.as<float>(),
+                          w.pb32.as<float>(), w.q32.as<float>(), itol, o->max_iter - total_it, chunk, sc_scale,
+                          deadline, &it, &ist);
+      if (st != HPSE_OK) return st;
+      k_add_scaled_f32<<<n_items_all(m), 128, 0, s>>>(elem_args(m), m->d_prob.as<int32_t>(), m->n_rhs,
+                                                      w.x32.as<float>(), sc_rnorm, x);
+      CK(cudaGetLastError());
+      ++g_launches;
+      total_it += it;
+      applies += it;
+      ++sweeps;
+      if (ist == HPSE_ERR_BREAKDOWN) {
+        status = ist;
+        break;
+      }
+      if (ist == HPSE_ERR_TIMEOUT) {
+        status = ist;
+        break;
+      }
+    }
+  }
+  // final FP64 residual for the report (plain FP64 path)
+  if (o->prec == HPSE_FP64) {
+    st = fp64_residual(m, x, o->tol, sc_rel, sc_scale, sc_rnorm, s);
+    if (st != HPSE_OK) return st;
+    CK(cudaMemcpyAsync(w.h_sc, w.sc.p, (size_t)12 * npr * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double worst = 0.0;
+    for (int i = 0; i < npr; ++i) worst = std::max(worst, w.h_sc[8 * npr + i]);
+    rep->rel_residual = worst;
+  }
+  CK(cudaEventRecord(w.ev, s));
+  CK(cudaStreamWaitEvent(us, w.ev, 0));
+  CK(cudaStreamSynchronize(s));
+  rep->iterations = total_it;
+  rep->sweeps = sweeps;
+  rep->applies = applies;
+  rep->status = status;
+  return (hpse_status)status;
+}
+
+extern "C" hpse_status hpse_h1_error(hpse_mesh *m, const double *u, const double *ref, const double *vq,
+                                     const double *gq, double *out, void *stream) {
+  if (!m || !out) return HPSE_ERR_INVALID_ARG;
+  if (m->ndof == 0) {
+    for (int r = 0; r < m->n_rhs; ++r) out[2 * r] = out[2 * r + 1] = 0.0;
+    return HPSE_OK;
+  }
+  if (!u || (!ref && (!vq || !gq))) return HPSE_ERR_INVALID_ARG;
+  CK(cudaSetDevice(m->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int ni = n_items_all(m);
+  DevBuf pe, pn, dtabs;
+  CK(pe.alloc((size_t)ni * sizeof(double)));
+  CK(pn.alloc((size_t)ni * sizeof(double)));
+  std::vector<const double *> tp(HPSE_MAX_W + 1, nullptr);
+  int Wmax = 1;
+  for (auto &kv : m->d_qtab) {
+    tp[kv.first] = kv.second.as<double>();
+    Wmax = std::max(Wmax, kv.first);
+  }
+  CK(upload(dtabs, tp));
+  H1Args A;
+  A.n_rhs = m->n_rhs;
+  A.ndof = m->ndof;
+  A.nquad = m->nquad;
+  A.dof_off = m->d_dof_off.as<int64_t>();
+  A.coef_off = m->d_coef_off.as<int64_t>();
+  A.elem_W = m->d_elem_W.as<int32_t>();
+  A.geo = m->d_geo64.as<double>();
+  A.qtab = dtabs.as<const double *>();
+  A.u = u;
+  A.ref = ref;
+  A.vq = vq;
+  A.gq = gq;
+  A.part_err = pe.as<double>();
+  A.part_nrm = pn.as<double>();
+  const int P = Wmax + 1, Q = 2 * Wmax + 1;
+  const size_t smem = (size_t)(P * P * P + 2 * Q * P * P + 3 * Q * Q * P) * sizeof(double);
+  CK(cudaFuncSetAttribute(k_h1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_h1<<<ni, 256, smem, s>>>(A);
+  CK(cudaGetLastError());
+  ++g_launches;
+  std::vector<double> he(ni), hn(ni);
+  CK(cudaMemcpyAsync(he.data(), pe.p, (size_t)ni * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hn.data(), pn.p, (size_t)ni * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int r = 0; r < m->n_rhs; ++r) {
+    double a = 0.0, b = 0.0;
+    for (int e = 0; e < m->n_elem; ++e) {
+      a += he[(size_t)e * m->n_rhs + r];
+      b += hn[(size_t)e * m->n_rhs + r];
+    }
+    out[2 * r] = a;
+    out[2 * r + 1] = b;
+  }
+  return HPSE_OK;
+}

@@ -1,0 +1,95 @@
+// inst_template.cuh -- launchers for one (REAL, WDEG) instantiation of
+// kernels.cuh.  A generated translation unit defines REAL, WDEG,
+// HPSE_REGISTER_NAME (and HPSE_DOUBLE for REAL = double), then includes this.
+#include "kernels.cuh"
+
+namespace {
+
+template <int COEF, int MODE>
+cudaError_t launch_apply_t(const void *args, int n_items, int threads, cudaStream_t s) {
+  k_apply<COEF, MODE><<<n_items, threads, ApplyLayout<COEF>::BYTES, s>>>(*static_cast<const ApplyArgs *>(args));
+  return cudaGetLastError();
+}
+
+cudaError_t apply_fn(int coef, int mode, const void *args, int n_items, int threads, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  if (threads <= 0 || threads > HPSE_APPLY_MAXT) return cudaErrorInvalidValue;
+  if (coef == COEF_LAPLACE) {
+    if (mode == MODE_PLAIN) return launch_apply_t<COEF_LAPLACE, MODE_PLAIN>(args, n_items, threads, s);
+    if (mode == MODE_PCG) return launch_apply_t<COEF_LAPLACE, MODE_PCG>(args, n_items, threads, s);
+    if (mode == MODE_TRANSPOSE) return launch_apply_t<COEF_LAPLACE, MODE_TRANSPOSE>(args, n_items, threads, s);
+  } else if (coef == COEF_SCALAR) {
+    if (mode == MODE_PLAIN) return launch_apply_t<COEF_SCALAR, MODE_PLAIN>(args, n_items, threads, s);
+    if (mode == MODE_PCG) return launch_apply_t<COEF_SCALAR, MODE_PCG>(args, n_items, threads, s);
+    if (mode == MODE_TRANSPOSE) return launch_apply_t<COEF_SCALAR, MODE_TRANSPOSE>(args, n_items, threads, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+size_t apply_smem_fn(int coef) {
+  return coef == COEF_SCALAR ? ApplyLayout<COEF_SCALAR>::BYTES : ApplyLayout<COEF_LAPLACE>::BYTES;
+}
+
+int apply_max_threads_fn(int) { return HPSE_APPLY_MAXT; }
+
+cudaError_t precond_fn(int mode, const void *args, int n_items, int threads, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  if (threads <= 0 || threads > 256) return cudaErrorInvalidValue;
+  if (mode == MODE_PLAIN)
+    k_precond<MODE_PLAIN><<<n_items, threads, 0, s>>>(*static_cast<const PrecArgs *>(args));
+  else if (mode == MODE_PCG)
+    k_precond<MODE_PCG><<<n_items, threads, 0, s>>>(*static_cast<const PrecArgs *>(args));
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+template <int COEF, int MODE>
+cudaError_t set_smem_attr() {
+  return cudaFuncSetAttribute(k_apply<COEF, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)ApplyLayout<COEF>::BYTES);
+}
+
+// Upload this degree's tables (packed FP64, see registry.h) to constant
+// memory of the current device, converting to REAL, and raise the dynamic
+// shared-memory limit of the apply kernels.
+cudaError_t upload_fn(const double *pk) {
+  Tables t;
+  int o = 0;
+  for (int m = 0; m < 3; ++m)
+    for (int i = 0; i < QP; ++i) t.B[m][i] = (real)pk[o++];
+  for (int i = 0; i < P2; ++i) t.D[i] = (real)pk[o++];
+  for (int i = 0; i < P2; ++i) t.S[i] = (real)pk[o++];
+  for (int i = 0; i < P2; ++i) t.MP[i] = (real)pk[o++];
+  for (int i = 0; i < P2; ++i) t.KP[i] = (real)pk[o++];
+  for (int i = 0; i < Q; ++i) t.WQ[i] = (real)pk[o++];
+  for (int i = 0; i < P; ++i) t.MU[i] = (real)pk[o++];
+  cudaError_t err = cudaMemcpyToSymbol(c_tab, &t, sizeof(Tables));
+  if (err != cudaSuccess) return err;
+  cudaError_t e2;
+  if ((e2 = set_smem_attr<COEF_LAPLACE, MODE_PLAIN>()) != cudaSuccess) return e2;
+  if ((e2 = set_smem_attr<COEF_LAPLACE, MODE_PCG>()) != cudaSuccess) return e2;
+  if ((e2 = set_smem_attr<COEF_LAPLACE, MODE_TRANSPOSE>()) != cudaSuccess) return e2;
+  if ((e2 = set_smem_attr<COEF_SCALAR, MODE_PLAIN>()) != cudaSuccess) return e2;
+  if ((e2 = set_smem_attr<COEF_SCALAR, MODE_PCG>()) != cudaSuccess) return e2;
+  if ((e2 = set_smem_attr<COEF_SCALAR, MODE_TRANSPOSE>()) != cudaSuccess) return e2;
+  return cudaSuccess;
+}
+
+static_assert(ApplyLayout<COEF_SCALAR>::BYTES <= 232448, "apply kernel exceeds 227 KB of shared memory");
+
+}  // namespace
+
+extern "C" void HPSE_REGISTER_NAME(hpse::KernelSet *ks) {
+  ks->W = WDEG;
+#if defined(HPSE_DOUBLE)
+  ks->is_double = 1;
+#else
+  ks->is_double = 0;
+#endif
+  ks->upload = upload_fn;
+  ks->apply = apply_fn;
+  ks->apply_smem = apply_smem_fn;
+  ks->apply_max_threads = apply_max_threads_fn;
+  ks->precond = precond_fn;
+}

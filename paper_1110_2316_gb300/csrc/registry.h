@@ -1,0 +1,74 @@
+// registry.h -- interface between the host library and the per-(precision,
+// degree) kernel translation units.  Each unit compiles kernels.cuh for one
+// (REAL, WDEG) pair and fills a KernelSet with launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hpse {
+
+enum { COEF_LAPLACE = 0, COEF_SCALAR = 1 };
+enum { MODE_PLAIN = 0, MODE_PCG = 1, MODE_TRANSPOSE = 2 };
+
+template <typename T>
+struct ApplyArgsT {
+  const T *u;
+  T *y;
+  const int32_t *elems;
+  int32_t n_group;
+  int32_t n_rhs;
+  int64_t ndof;
+  const int64_t *dof_off;
+  const int32_t *nbr;
+  const T *geo;
+  const int32_t *prob;
+  const T *coef;
+  const int64_t *coef_off;
+  int64_t nquad;
+  const T *z;
+  const double *beta;
+  T *pnew;
+  double *partial;
+  const double *rho;
+  int32_t skip_faces;
+};
+
+template <typename T>
+struct PrecArgsT {
+  const int32_t *elems;
+  int32_t n_group;
+  int32_t n_rhs;
+  int64_t ndof;
+  const int64_t *dof_off;
+  const int32_t *prob;
+  const T *rin;
+  T *zout;
+  T *x;
+  T *r;
+  const T *p;
+  const T *q;
+  const double *alpha;
+  double *part_rr;
+  double *part_rz;
+};
+
+// Packed FP64 tables for one degree, in the order of the device struct:
+// B0, B1, B2 (Q*P each), D (P*P), S (P*P), MP (P*P), KP (P*P), WQ (Q), MU (P).
+inline int packed_table_size(int W) {
+  const int P = W + 1, Q = 2 * W + 1;
+  return 3 * Q * P + 4 * P * P + Q + P;
+}
+
+struct KernelSet {
+  int W;
+  int is_double;
+  cudaError_t (*upload)(const double *packed);
+  // coef: COEF_*, mode: MODE_*; args points to ApplyArgsT<T>
+  cudaError_t (*apply)(int coef, int mode, const void *args, int n_items, int threads, cudaStream_t s);
+  size_t (*apply_smem)(int coef);
+  int (*apply_max_threads)(int coef);
+  // mode: MODE_PLAIN or MODE_PCG; args points to PrecArgsT<T>
+  cudaError_t (*precond)(int mode, const void *args, int n_items, int threads, cudaStream_t s);
+};
+
+}  // namespace hpse

@@ -108,11 +108,18 @@ typedef struct {
   int32_t prec;        /* hpse_prec of the operator applies inside PCG:
                           HPSE_FP64 = plain FP64 PCG;
                           HPSE_FP32 = FP32 applies + FP64 iterative refinement     */
-  double inner_tol;    /* relative tolerance of each FP32 inner solve (HPSE_FP32)  */
+  double inner_tol;    /* HPSE_FP32: refine_mode 0: residual reduction factor of the
+                          FP32 iteration between FP64 residual refreshes (delta);
+                          refine_mode 1: relative tolerance of each inner solve  */
   int32_t max_sweeps;  /* cap on refinement sweeps (HPSE_FP32)                     */
   int32_t check_every; /* PCG iterations per host convergence check (CUDA graph)   */
   int32_t zero_init;   /* 1: start from x = 0 (the input x is ignored)             */
   double time_limit_s; /* wall-clock limit, <= 0 for none                          */
+  int32_t refine_mode; /* HPSE_FP32 only.  0: one FP32 PCG whose residual is replaced
+                          by the FP64 residual b - A x (x accumulated in FP64) each
+                          time it has dropped by inner_tol, search direction kept
+                          ("reliable updates"); 1: restarted refinement, a fresh
+                          FP32 PCG per FP64 residual                               */
 } hpse_solve_opts;
 
 typedef struct {

@@ -38,7 +38,7 @@ class SolveOpts(C.Structure):
     _fields_ = [
         ("tol", C.c_double), ("max_iter", C.c_int32), ("prec", C.c_int32), ("inner_tol", C.c_double),
         ("max_sweeps", C.c_int32), ("check_every", C.c_int32), ("zero_init", C.c_int32),
-        ("time_limit_s", C.c_double),
+        ("time_limit_s", C.c_double), ("refine_mode", C.c_int32),
     ]
 
 

@@ -116,10 +116,11 @@ class Mesh:
         check(self._lib.hpse_apply_preconditioner(self._h, _prec_of(r), _ptr(r), _ptr(z), _stream(stream)),
               "hpse_apply_preconditioner")
 
-    def pcg_solve(self, x, tol=1e-10, prec=FP64, max_iter=20000, inner_tol=1e-4, max_sweeps=30,
-                  check_every=16, zero_init=True, time_limit_s=0.0, stream=None, raise_on_error=True):
+    def pcg_solve(self, x, tol=1e-10, prec=FP64, max_iter=20000, inner_tol=1e-2, max_sweeps=200,
+                  check_every=16, zero_init=True, time_limit_s=0.0, refine_mode=0, stream=None,
+                  raise_on_error=True):
         o = _lib.SolveOpts(float(tol), int(max_iter), int(prec), float(inner_tol), int(max_sweeps),
-                           int(check_every), 1 if zero_init else 0, float(time_limit_s))
+                           int(check_every), 1 if zero_init else 0, float(time_limit_s), int(refine_mode))
         rep = _lib.SolveReport()
         st = self._lib.hpse_pcg_solve(self._h, C.byref(o), _ptr(x), C.byref(rep), _stream(stream))
         out = dict(status=int(rep.status), iterations=int(rep.iterations), sweeps=int(rep.sweeps),

@@ -12,6 +12,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -73,6 +74,14 @@ static void init_registry() {
   } while (0)
 
 static char g_last_err[512];
+static int verbose() {
+  static int v = -1;
+  if (v < 0) {
+    const char *e = getenv("HPSE_VERBOSE");
+    v = (e && e[0] && e[0] != '0') ? 1 : 0;
+  }
+  return v;
+}
 static void last_cuda_error(cudaError_t e, const char *what, int line) {
   snprintf(g_last_err, sizeof(g_last_err), "%s (%s) at hpse.cu:%d", cudaGetErrorString(e), what, line);
 }
@@ -83,6 +92,23 @@ static void last_cuda_error(cudaError_t e, const char *what, int line) {
 struct DevBuf {
   void *p = nullptr;
   size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes) {
+    o.p = nullptr;
+    o.bytes = 0;
+  }
+  DevBuf &operator=(DevBuf &&o) noexcept {
+    if (this != &o) {
+      if (p) cudaFree(p);
+      p = o.p;
+      bytes = o.bytes;
+      o.p = nullptr;
+      o.bytes = 0;
+    }
+    return *this;
+  }
   ~DevBuf() {
     if (p) cudaFree(p);
   }
@@ -362,14 +388,14 @@ __global__ void k_fin_beta(FinArgs F, Scalars S, const double *part_rr, const do
 
 // start of a PCG solve: rz = r.z, bb = r.r (= rr), beta = 0, active if bb > 0
 __global__ void k_fin_init(FinArgs F, Scalars S, const double *part_rz, const double *part_rr, double rel_tol,
-                           const double *scale_in) {
+                           const double *scale_in, int unit_bb) {
   const int pr = blockIdx.x;
   const int p = pr / F.n_rhs, r = pr - p * F.n_rhs;
   const double rz = fin_sum(F, part_rz, p, r);
   const double rr = fin_sum(F, part_rr, p, r);
   if (threadIdx.x == 0) {
     S.rz[pr] = rz;
-    S.bb[pr] = rr;
+    S.bb[pr] = unit_bb ? 1.0 : rr;
     S.rr[pr] = rr;
     S.beta[pr] = 0.0;
     S.alpha[pr] = 0.0;
@@ -378,6 +404,30 @@ __global__ void k_fin_init(FinArgs F, Scalars S, const double *part_rz, const do
     const bool want = scale_in ? (scale_in[pr] != 0.0) : true;
     S.active[pr] = (want && rr > 0.0 && isfinite(rr)) ? 1 : 0;
     if (!isfinite(rr)) S.status[pr] = HPSE_ERR_BREAKDOWN;
+  }
+}
+
+// FP64 residual refresh inside the FP32 PCG: the recursive FP32 residual is
+// replaced by the true one (already in r, z); beta is rescaled so that the
+// next direction is z~ + beta~ p with beta~ = (r~, z~) / (r, z)_{k-1}.
+__global__ void k_fin_reliable(FinArgs F, Scalars S, const double *part_rz, const double *part_rr, const double *rel,
+                               double tol) {
+  const int pr = blockIdx.x;
+  const int p = pr / F.n_rhs, r = pr - p * F.n_rhs;
+  const double rz = fin_sum(F, part_rz, p, r);
+  const double rr = fin_sum(F, part_rr, p, r);
+  if (threadIdx.x == 0) {
+    if (rel[pr] > tol && isfinite(rz) && rz > 0.0) {
+      const double b = (S.active[pr] && S.rz[pr] > 0.0) ? S.beta[pr] * (rz / S.rz[pr]) : 0.0;
+      S.beta[pr] = isfinite(b) ? b : 0.0;
+      S.rz[pr] = rz;
+      S.rr[pr] = rr;
+      S.active[pr] = 1;
+    } else {
+      S.beta[pr] = 0.0;
+      S.alpha[pr] = 0.0;
+      S.active[pr] = 0;
+    }
   }
 }
 
@@ -1200,7 +1250,8 @@ static hpse_status run_pcg(hpse_mesh *m, T *x, T *r, T *z, T *pa, T *pb, T *q, d
     if (st != HPSE_OK) return st;
     k_dot<T, T><<<n_items_all(m), 128, 0, s>>>(elem_args(m), r, z, w.part0.as<double>());
     k_dot<T, T><<<n_items_all(m), 128, 0, s>>>(elem_args(m), r, r, w.part1.as<double>());
-    k_fin_init<<<npr, 128, 0, s>>>(fin_args(m), S, w.part0.as<double>(), w.part1.as<double>(), rel_tol, scale);
+    k_fin_init<<<npr, 128, 0, s>>>(fin_args(m), S, w.part0.as<double>(), w.part1.as<double>(), rel_tol, scale,
+                                   0);
     CK(cudaGetLastError());
     g_launches += 3;
   }
@@ -1281,6 +1332,177 @@ static hpse_status fp64_residual(hpse_mesh *m, const double *x64, double tol, do
   return HPSE_OK;
 }
 
+// FP32-apply PCG with FP64 "reliable updates": one PCG iteration sequence in
+// FP32 (vectors scaled by 1/||b||); whenever its recursive residual has
+// dropped by the factor delta since the last refresh (or it claims
+// convergence), the correction is added to x in FP64, the true residual
+// b - A x is recomputed with FP64 applies, and the FP32 residual is replaced by
+// it while the search direction is kept.  Stops when the FP64 residual meets
+// ||b - A x|| <= tol ||b|| for every (problem, rhs).
+static hpse_status solve_mixed_reliable(hpse_mesh *m, const hpse_solve_opts *o, double *x, hpse_solve_report *rep,
+                                        double deadline, int *status_out) {
+  SolverWork &w = *m->work;
+  cudaStream_t s = w.st;
+  const int npr = npr_of(m);
+  Scalars S = scalars_of(w, npr);
+  double *sc_rel = w.sc.as<double>() + 8 * npr;
+  double *sc_scale = w.sc.as<double>() + 9 * npr;
+  double *sc_rnorm = w.sc.as<double>() + 10 * npr;
+  double *sc_bn = w.sc.as<double>() + 11 * npr;  // ||b|| per pair, then 1/||b|| in sc_scale
+  const double delta = (o->inner_tol > 0 && o->inner_tol < 1) ? o->inner_tol : 1e-2;
+  const int chunk0 = o->check_every > 0 ? o->check_every : 16;
+  const int chunk = chunk0 + (chunk0 & 1);
+  const size_t nb32 = w.n * sizeof(float);
+  int status = HPSE_OK, updates = 0, applies = 0;
+  // ||b|| and 1/||b|| per pair
+  {
+    std::vector<double> bn2(npr), bn(npr), ibn(npr);
+    CK(cudaMemcpyAsync(bn2.data(), m->d_bnorm2.p, npr * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int i = 0; i < npr; ++i) {
+      bn[i] = std::sqrt(bn2[i]);
+      ibn[i] = bn[i] > 0 ? 1.0 / bn[i] : 0.0;
+    }
+    CK(cudaMemcpyAsync(sc_bn, bn.data(), npr * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(sc_scale, ibn.data(), npr * sizeof(double), cudaMemcpyHostToDevice, s));
+  }
+  // initial residual (x = 0 or the given x) and FP32 state
+  if (o->zero_init) {
+    CK(cudaMemcpyAsync(w.r64.p, m->d_b.p, w.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  } else {
+    hpse_status st = fp64_residual(m, x, o->tol, sc_rel, sc_rnorm, sc_rnorm, s);
+    if (st != HPSE_OK) return st;
+    ++applies;
+  }
+  k_scale_to_f32<<<n_items_all(m), 128, 0, s>>>(elem_args(m), m->d_prob.as<int32_t>(), m->n_rhs,
+                                                w.r64.as<double>(), sc_scale, w.r32.as<float>());
+  CK(cudaMemsetAsync(w.x32.p, 0, nb32, s));
+  CK(cudaMemsetAsync(w.pa32.p, 0, nb32, s));
+  CK(cudaMemsetAsync(S.status, 0, npr * sizeof(int32_t), s));
+  {
+    PrecArgsT<float> p = prec_args<float>(m, m->groups[0]);
+    p.rin = w.r32.as<float>();
+    p.zout = w.z32.as<float>();
+    hpse_status st = launch_prec_all<float>(m, MODE_PLAIN, p, s);
+    if (st != HPSE_OK) return st;
+    k_dot<float, float><<<n_items_all(m), 128, 0, s>>>(elem_args(m), w.r32.as<float>(), w.z32.as<float>(),
+                                                       w.part0.as<double>());
+    k_dot<float, float><<<n_items_all(m), 128, 0, s>>>(elem_args(m), w.r32.as<float>(), w.r32.as<float>(),
+                                                       w.part1.as<double>());
+    k_fin_init<<<npr, 128, 0, s>>>(fin_args(m), S, w.part0.as<double>(), w.part1.as<double>(), o->tol, sc_scale, 1);
+    CK(cudaGetLastError());
+    g_launches += 4;
+  }
+  CK(cudaMemcpyAsync(w.h_sc, w.sc.p, (size_t)12 * npr * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<double> rr_ref(npr);
+  for (int i = 0; i < npr; ++i) rr_ref[i] = w.h_sc[2 * npr + i];
+  // graph of `chunk` FP32 iterations
+  float *x32 = w.x32.as<float>(), *r32 = w.r32.as<float>(), *z32 = w.z32.as<float>();
+  float *pa = w.pa32.as<float>(), *pb = w.pb32.as<float>(), *q32 = w.q32.as<float>();
+  const long long key = (long long)chunk * 4 + 1 * 2 + 1;
+  cudaGraphExec_t exec = nullptr;
+  auto git = w.graphs.find(key);
+  if (git == w.graphs.end()) {
+    cudaGraph_t graph;
+    const long long before = g_launches;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    hpse_status st = HPSE_OK;
+    for (int i = 0; i < chunk && st == HPSE_OK; i += 2) {
+      st = pcg_iteration<float>(m, x32, r32, z32, pa, pb, q32, s);
+      if (st == HPSE_OK) st = pcg_iteration<float>(m, x32, r32, z32, pb, pa, q32, s);
+    }
+    if (st == HPSE_OK) {
+      k_count_active<<<1, 256, 0, s>>>(S.active, npr, S.n_active);
+      ++g_launches;
+    }
+    cudaError_t ce = cudaStreamEndCapture(s, &graph);
+    if (st != HPSE_OK) return st;
+    CK(ce);
+    CK(cudaGraphInstantiate(&exec, graph, 0));
+    cudaGraphDestroy(graph);
+    w.graphs[key] = exec;
+    w.graph_launches[key] = (int)(g_launches - before);
+    g_launches = before;
+  } else {
+    exec = git->second;
+  }
+  const int per_replay = w.graph_launches[key];
+  int done = 0;
+  double worst = 1.0;
+  while (true) {
+    CK(cudaGraphLaunch(exec, s));
+    g_launches += per_replay;
+    done += chunk;
+    CK(cudaMemcpyAsync(w.h_flags, w.flags.p, (size_t)(3 * npr + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(w.h_sc, w.sc.p, (size_t)12 * npr * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int n_active = w.h_flags[3 * npr];
+    bool refresh = n_active == 0;
+    for (int i = 0; i < npr && !refresh; ++i)
+      if (w.h_flags[i] && w.h_sc[2 * npr + i] <= delta * delta * rr_ref[i]) refresh = true;
+    for (int i = 0; i < npr; ++i)
+      if (w.h_flags[2 * npr + i] == HPSE_ERR_BREAKDOWN) refresh = true;
+    const bool capped = done >= o->max_iter || updates >= (o->max_sweeps > 0 ? o->max_sweeps : 200);
+    double now = 0.0;
+    if (deadline > 0)
+      now = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+    if (refresh || capped || (deadline > 0 && now > deadline)) {
+      // x += ||b|| x32 ; x32 = 0 ; r64 = b - A x ; relative residuals
+      k_add_scaled_f32<<<n_items_all(m), 128, 0, s>>>(elem_args(m), m->d_prob.as<int32_t>(), m->n_rhs, x32, sc_bn, x);
+      CK(cudaGetLastError());
+      ++g_launches;
+      CK(cudaMemsetAsync(x32, 0, nb32, s));
+      hpse_status st = fp64_residual(m, x, o->tol, sc_rel, sc_rnorm, sc_rnorm, s);
+      if (st != HPSE_OK) return st;
+      ++applies;
+      ++updates;
+      CK(cudaMemcpyAsync(w.h_sc, w.sc.p, (size_t)12 * npr * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      worst = 0.0;
+      for (int i = 0; i < npr; ++i) worst = std::max(worst, w.h_sc[8 * npr + i]);
+      if (verbose())
+        fprintf(stderr, "[hpse] refresh %d after %d FP32 iterations: max rel residual %.3e\n", updates, done, worst);
+      if (!(worst > o->tol)) break;
+      if (capped) {
+        status = HPSE_ERR_NO_CONVERGENCE;
+        break;
+      }
+      if (deadline > 0 && now > deadline) {
+        status = HPSE_ERR_TIMEOUT;
+        break;
+      }
+      // replace the FP32 residual by the true one, keep the direction
+      k_scale_to_f32<<<n_items_all(m), 128, 0, s>>>(elem_args(m), m->d_prob.as<int32_t>(), m->n_rhs,
+                                                    w.r64.as<double>(), sc_scale, r32);
+      PrecArgsT<float> p = prec_args<float>(m, m->groups[0]);
+      p.rin = r32;
+      p.zout = z32;
+      st = launch_prec_all<float>(m, MODE_PLAIN, p, s);
+      if (st != HPSE_OK) return st;
+      k_dot<float, float><<<n_items_all(m), 128, 0, s>>>(elem_args(m), r32, z32, w.part0.as<double>());
+      k_dot<float, float><<<n_items_all(m), 128, 0, s>>>(elem_args(m), r32, r32, w.part1.as<double>());
+      k_fin_reliable<<<npr, 128, 0, s>>>(fin_args(m), S, w.part0.as<double>(), w.part1.as<double>(), sc_rel, o->tol);
+      CK(cudaGetLastError());
+      g_launches += 4;
+      CK(cudaMemsetAsync(S.status, 0, npr * sizeof(int32_t), s));
+      CK(cudaMemcpyAsync(w.h_sc, w.sc.p, (size_t)12 * npr * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int i = 0; i < npr; ++i) rr_ref[i] = w.h_sc[2 * npr + i];
+    }
+  }
+  int mx = 0;
+  CK(cudaMemcpyAsync(w.h_flags, w.flags.p, (size_t)(3 * npr + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int i = 0; i < npr; ++i) mx = std::max(mx, w.h_flags[npr + i]);
+  rep->iterations = mx;
+  rep->sweeps = updates;
+  rep->applies = mx + applies;
+  rep->rel_residual = worst;
+  *status_out = status;
+  return HPSE_OK;
+}
+
 extern "C" hpse_status hpse_pcg_solve(hpse_mesh *m, const hpse_solve_opts *o, double *x, hpse_solve_report *rep,
                                       void *stream) {
   if (!m || !o || !rep) return HPSE_ERR_INVALID_ARG;
@@ -1334,6 +1556,15 @@ extern "C" hpse_status hpse_pcg_solve(hpse_mesh *m, const hpse_solve_opts *o, do
     total_it = it;
     applies += it;
     sweeps = 1;
+  } else if (o->refine_mode == 0) {
+    if (o->zero_init) CK(cudaMemsetAsync(x, 0, nb, s));
+    st = solve_mixed_reliable(m, o, x, rep, deadline, &status);
+    if (st != HPSE_OK) return st;
+    CK(cudaEventRecord(w.ev, s));
+    CK(cudaStreamWaitEvent(us, w.ev, 0));
+    CK(cudaStreamSynchronize(s));
+    rep->status = status;
+    return (hpse_status)status;
   } else {
     // FP32 operator applies inside FP64 iterative refinement
     const int max_sweeps = o->max_sweeps > 0 ? o->max_sweeps : 20;
@@ -1363,6 +1594,9 @@ extern "C" hpse_status hpse_pcg_solve(hpse_mesh *m, const hpse_solve_opts *o, do
         if (w.h_sc[9 * npr + i] != 0.0) any = true;
       }
       rep->rel_residual = worst;
+      if (verbose())
+        fprintf(stderr, "[hpse] sweep %d: max rel residual %.3e, inner iterations so far %d\n", sweeps, worst,
+                total_it);
       if (!any) break;
       if (sweeps >= max_sweeps || total_it >= o->max_iter) {
         status = HPSE_ERR_NO_CONVERGENCE;

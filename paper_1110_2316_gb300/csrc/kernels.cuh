@@ -100,10 +100,6 @@ __device__ __forceinline__ double block_sum(T v, double *red) {
 // Face phase: y_e += contributions of the six faces of element e (eq. 4.2).
 // su: own block, snb: scratch P3, scr: scratch >= 10*P2, tabs: D, MP, KP copy
 // ---------------------------------------------------------------------------
-struct FaceScratch {
-  real *F, *N, *G1, *G2, *J0, *J1, *J2, *J3, *A, *Bt;
-};
-
 // out = (A (x) B) v with A acting on p2 and B on p1 (face arrays [p2][p1])
 __device__ __forceinline__ void kron_apply(const real *Am, const real *Bm, const real *v, real *tmp, real *out,
                                            bool accumulate) {
@@ -269,7 +265,9 @@ struct ApplyLayout {
   static constexpr int T_REGION = T_REGION0 > T_NEED ? T_REGION0 : T_NEED;
   static constexpr int TABS = 3 * P2;
   static constexpr int TOTAL = P3 + NX * QP2 + T_REGION + TABS;
-  static constexpr size_t BYTES = (size_t)TOTAL * sizeof(real) + 64 * sizeof(double);
+  // the FP64 reduction buffer starts on a 16-byte boundary whatever REAL is
+  static constexpr size_t RED_OFF = (((size_t)TOTAL * sizeof(real) + 15) / 16) * 16;
+  static constexpr size_t BYTES = RED_OFF + 64 * sizeof(double);
 };
 
 #if defined(HPSE_DOUBLE)
@@ -286,7 +284,8 @@ __global__ void __launch_bounds__(HPSE_APPLY_MAXT) k_apply(const ApplyArgs A) {
   real *sX = su + P3;               // X0 | X2 | (X1)
   real *sT = sX + L::NX * QP2;      // T00 | TL | (T10 | T01)
   real *stab = sT + L::T_REGION;    // D | MP | KP (runtime-indexed copies)
-  double *red = reinterpret_cast<double *>(stab + L::TABS);
+  double *red = reinterpret_cast<double *>(smem_raw + L::RED_OFF);
+  static_assert(L::RED_OFF % 16 == 0, "reduction buffer must be 16-byte aligned");
   real *X0 = sX, *X2 = sX + QP2, *X1 = sX + 2 * QP2;
   real *T00 = sT, *TL = sT + Q2P, *T10 = sT + 2 * Q2P, *T01 = sT + 3 * Q2P;
 

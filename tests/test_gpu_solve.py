@@ -122,3 +122,14 @@ def test_iteration_cap_reports_no_convergence(api):
     x = torch.zeros(mesh.ndof, dtype=torch.float64, device="cuda")
     rep = mesh.pcg_solve(x, tol=1e-14, prec=api.FP64, max_iter=4, check_every=2, raise_on_error=False)
     assert rep["status"] == 5  # HPSE_ERR_NO_CONVERGENCE
+
+
+@pytest.mark.parametrize("mode,delta", [(0, 1e-1), (0, 1e-3), (1, 1e-4)])
+def test_refinement_modes(api, mode, delta):
+    pb = wl.varcoef_manufactured(n=(2, 2, 2), W=4)
+    mesh = _mesh(api, pb)
+    disc = Discretisation(pb)
+    x64, _ = _solve(api, mesh, api.FP64)
+    xm, rep = _solve(api, mesh, api.FP32, refine_mode=mode, inner_tol=delta)
+    assert rep["status"] == 0 and rep["rel_residual"] <= 1e-10, rep
+    assert h1_rel_diff(disc, xm, x64) <= 1e-8

@@ -1,0 +1,367 @@
+"""Benchmark: mixed-precision (FP32 applies + FP64 refinement) PCG solves of the
+variable-coefficient workload -div(a grad u) = f on [0,1]^3, 8x8x8 box elements,
+degree W = 8, 64 seeded right-hand sides (tensor-Legendre coefficients ~ N(0,1)
+decaying as 2^-k), homogeneous Dirichlet data.
+
+One step = one full solve of the 64-RHS batch to ||b - A x|| <= 1e-10 ||b||
+(operator applies, preconditioner, PCG updates and FP64 residual refreshes).
+value = operator-apply GDOF/s inside the solve (DOF x operator applies / time);
+ms_per_step = time-to-solution.  The FP64-vs-mixed comparison of the
+time-to-solution is run on the first `--cmp-rhs` right-hand sides.
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
+torch.distributed.run (one rank per GPU, independent batches per rank,
+weak scaling, no data-path collective).  --impl reference times the CPU oracle.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+METRIC = "operator-apply GDOF/s and PCG time-to-solution at oracle H1 error, mixed vs FP64"
+N_EL, W_DEG, N_RHS, TOL = 8, 8, 64, 1e-10
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--rhs", type=int, default=N_RHS)
+    ap.add_argument("--n", type=int, default=N_EL)
+    ap.add_argument("--W", type=int, default=W_DEG)
+    ap.add_argument("--cmp-rhs", type=int, default=4)
+    ap.add_argument("--no-cmp", action="store_true")
+    ap.add_argument("--delta", type=float, default=1e-1)
+    ap.add_argument("--cpu-sample-elems", type=int, default=512)
+    ap.add_argument("--cpu-reps", type=int, default=2)
+    ap.add_argument("--apply-only", action="store_true",
+                    help="time only the FP32 operator apply (profiling driver for ncu)")
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [l.strip().split(",") for l in open(self.path) if l.strip()]
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, name in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(name)
+            except Exception:
+                continue
+        if sm:
+            out.update(sm_mhz=float(np.median(sm)), sm_max_mhz=float(max(mx)), samples=len(sm))
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+# ---------------------------------------------------------------------------
+def make_problem(args, rank):
+    return wl.varcoef_random_rhs(n=args.n, W=args.W, n_rhs=args.rhs, seed0=20260 + args.rhs * rank)
+
+
+def volume_flops_per_rhs(Ws):
+    """Algorithmic flops of one operator apply (volume, forward + transpose):
+    2 * (n1 Q P^3 + n2 Q^2 P^2 + n3 Q^3 P) multiply-adds per element with
+    (n1, n2, n3) = (3, 5, 6) for -div(a grad u), 2 flops per multiply-add."""
+    tot = 0.0
+    for W in Ws:
+        P, Q = W + 1, 2 * W + 1
+        tot += 2 * (3 * Q * P ** 3 + 5 * Q * Q * P * P + 6 * Q ** 3 * P)
+    return 2.0 * tot
+
+
+def fp32_peak_tflops():
+    """152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz maximum SM clock."""
+    return 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def cpu_baseline(pb, n_elems, reps=1):
+    """The oracle's operator apply on a bounded sample of elements (1 rhs), `reps` times."""
+    from oracle.functional import Discretisation
+    one = wl.Problem(pb.mesh, [pb.f[0]], [pb.g[0]], pb.a, pb.grad_a)
+    d = Discretisation(one)
+    U = wl.random_dofs(d.ndof, seed=1)
+    elems = list(range(min(n_elems, d.E)))
+    d.element_apply(U, elems[0])  # tables / coefficient caches
+    t = time.perf_counter()
+    for _ in range(reps):
+        for e in elems:
+            d.element_apply(U, e)
+    dt = time.perf_counter() - t
+    ndof = reps * sum(d.P[e] ** 3 for e in elems)
+    return dict(value=ndof / dt / 1e9, unit="GDOF/s", cores=os.cpu_count(), kind="oracle",
+                sample="oracle operator apply, %d x %d of %d elements (W=%d, 1 rhs), %.1f s" %
+                       (reps, len(elems), d.E, d.W[0], dt))
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    pb = wl.varcoef_random_rhs(n=args.n, W=args.W, n_rhs=1)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(pb, args.cpu_sample_elems, 1)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+    v = float(np.mean(vals))
+    line = dict(metric=METRIC, value=v, unit="GDOF/s", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                ms_per_step=None, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                data="synthetic", impl="reference",
+                config=dict(workload="varcoef 8x8x8 W=8, oracle operator apply sample", n_elem=args.n ** 3,
+                            W=args.W),
+                cpu_baseline=dict(value=v, unit="GDOF/s", cores=cb["cores"], kind="oracle", sample=cb["sample"]),
+                e2e=dict(value=v, unit="GDOF/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1110_2316_gb300.build import build
+    if rank == 0:
+        build()
+    if ws > 1:
+        torch.distributed.barrier()
+    build()
+    from paper_1110_2316_gb300 import api
+    dev = torch.device("cuda", local)
+
+    # ---- set-up (untimed) ---------------------------------------------------
+    t0 = time.perf_counter()
+    pb = make_problem(args, rank)
+    mesh = api.Mesh(pb.mesh, n_rhs=args.rhs, coef_kind=api.COEF_SCALAR, device=local)
+    data = api.problem_data_arrays(mesh, pb)
+    t_sample = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    mesh.set_data(**data)
+    torch.cuda.synchronize()
+    t_setdata = time.perf_counter() - t1
+    n_tot = args.rhs * mesh.ndof
+    if args.apply_only:
+        dt = torch.float32 if args.prec == "fp32" else torch.float64
+        u = torch.randn(n_tot, dtype=dt, device=dev)
+        y = torch.empty_like(u)
+        for _ in range(args.warmup):
+            mesh.apply_operator(u, y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            mesh.apply_operator(u, y)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / max(1, args.steps)
+        fl = volume_flops_per_rhs([int(w) for w in mesh.elem_W]) * args.rhs
+        print(json.dumps(dict(mode="apply-only", prec=args.prec, rhs=args.rhs, ms_per_apply=ms,
+                              gdofs=n_tot / ms / 1e6, alg_tflops=fl / ms / 1e9)))
+        return 0
+    x = torch.zeros(n_tot, dtype=torch.float64, device=dev)
+
+    def solve(m, xx, prec):
+        return m.pcg_solve(xx, tol=TOL, prec=prec, inner_tol=args.delta, check_every=16)
+
+    # ---- warm-up and timed steps -----------------------------------------------
+    for _ in range(args.warmup):
+        x.zero_()
+        solve(mesh, x, api.FP32)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    api.kernel_launch_count(reset=True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(args.steps):
+            x.zero_()
+            reps.append(solve(mesh, x, api.FP32))
+        ev1.record()
+        torch.cuda.synchronize()
+    launches = api.kernel_launch_count(reset=True)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    applies = float(np.mean([r["applies"] for r in reps]))
+    value = ws * n_tot * applies / (ms * 1e-3) / 1e9
+    clocks = clk.summary()
+
+    # ---- dominant kernel: FP32 operator apply, timed alone -----------------------
+    u32 = torch.randn(n_tot, dtype=torch.float32, device=dev)
+    y32 = torch.empty_like(u32)
+    for _ in range(3):
+        mesh.apply_operator(u32, y32)
+    torch.cuda.synchronize()
+    na = 20
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record()
+    for _ in range(na):
+        mesh.apply_operator(u32, y32)
+    a1.record()
+    torch.cuda.synchronize()
+    apply_ms = a0.elapsed_time(a1) / na
+    alg_flops = volume_flops_per_rhs([int(w) for w in mesh.elem_W]) * args.rhs
+    achieved = alg_flops / (apply_ms * 1e-3) / 1e12
+    peak = fp32_peak_tflops()
+    # FP64 apply for reference
+    u64 = u32.double()
+    y64 = torch.empty_like(u64)
+    mesh.apply_operator(u64, y64)
+    torch.cuda.synchronize()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record()
+    for _ in range(3):
+        mesh.apply_operator(u64, y64)
+    b1.record()
+    torch.cuda.synchronize()
+    apply64_ms = b0.elapsed_time(b1) / 3
+
+    # ---- end to end through the public API (host buffers) -----------------------
+    host_f = torch.from_numpy(data["f"]).pin_memory()
+    host_x = torch.empty(n_tot, dtype=torch.float64).pin_memory()
+    e0 = time.perf_counter()
+    mesh.set_data(f=host_f.numpy(), a=data["a"], grad_a=data["grad_a"], g=data["g"])
+    x.zero_()
+    rep_e2e = solve(mesh, x, api.FP32)
+    host_x.copy_(x)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - e0
+    h2d = data["f"].nbytes + data["a"].nbytes + data["grad_a"].nbytes
+    e2e = dict(value=ws * n_tot * rep_e2e["applies"] / e2e_s / 1e9, unit="GDOF/s", h2d_bytes_per_step=int(h2d),
+               d2h_bytes_per_step=int(host_x.numel() * 8))
+
+    # ---- mixed vs FP64 time-to-solution on a subset of right-hand sides ----------
+    cmp = None
+    if not args.no_cmp and rank == 0:
+        k = min(args.cmp_rhs, args.rhs)
+        sub = wl.Problem(pb.mesh, pb.f[:k], pb.g[:k], pb.a, pb.grad_a)
+        ms2 = api.Mesh(sub.mesh, n_rhs=k, coef_kind=api.COEF_SCALAR, device=local)
+        ms2.set_data(f=data["f"][:k], a=data["a"], grad_a=data["grad_a"])
+        xs = torch.zeros(k * ms2.ndof, dtype=torch.float64, device=dev)
+        ms2.pcg_solve(xs, tol=TOL, prec=api.FP64, max_iter=32, raise_on_error=False)  # graph warm-up
+        solve(ms2, xs, api.FP32)
+        out = {}
+        for name, prec in (("mixed", api.FP32), ("fp64", api.FP64)):
+            xs.zero_()
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record()
+            r = ms2.pcg_solve(xs, tol=TOL, prec=prec, inner_tol=args.delta, max_iter=60000,
+                              raise_on_error=False, time_limit_s=600)
+            c1.record()
+            torch.cuda.synchronize()
+            out[name] = (c0.elapsed_time(c1) / 1e3, r, xs.clone())
+        h = ms2.h1_error(out["mixed"][2], ref=out["fp64"][2])
+        h1 = float(np.max(np.sqrt(h[:, 0] / h[:, 1])))
+        cmp = dict(rhs=k, tts_mixed_s=out["mixed"][0], tts_fp64_s=out["fp64"][0],
+                   speedup=out["fp64"][0] / out["mixed"][0],
+                   iters_mixed=out["mixed"][1]["iterations"], iters_fp64=out["fp64"][1]["iterations"],
+                   refreshes=out["mixed"][1]["sweeps"], status_fp64=out["fp64"][1]["status"],
+                   rel_res_mixed=out["mixed"][1]["rel_residual"], rel_res_fp64=out["fp64"][1]["rel_residual"],
+                   h1_rel_diff_mixed_vs_fp64=h1)
+        ms2.close()
+
+    if rank == 0:
+        cb = cpu_baseline(pb, args.cpu_sample_elems, args.cpu_reps) if ws == 1 else None
+        line = dict(
+            metric=METRIC, value=value, unit="GDOF/s", n_gpus=ws, steps=args.steps, warmup=args.warmup,
+            ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+            data="synthetic",
+            config=dict(workload="varcoef -div(a grad u)=f, [0,1]^3, %d^3 elements, W=%d, %d RHS, tol 1e-10, "
+                                 "FP32 applies + FP64 reliable-update refinement" % (args.n, args.W, args.rhs),
+                        n_elem=args.n ** 3, W=args.W, rhs_per_gpu=args.rhs, dof_per_rhs=mesh.ndof,
+                        l2="working set > L2 (FP32 vectors %.0f MB each)" % (n_tot * 4 / 1e6),
+                        parallelism="replicas (independent batches per GPU)"),
+            solve=dict(iterations=reps[-1]["iterations"], refreshes=reps[-1]["sweeps"],
+                       applies=reps[-1]["applies"], rel_residual=reps[-1]["rel_residual"],
+                       setup_sample_s=t_sample, setup_set_data_s=t_setdata),
+            tts_comparison=cmp,
+            apply_ms=dict(fp32=apply_ms, fp64=apply64_ms),
+            roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                          traffic=None, kernel="k_apply<COEF_SCALAR> FP32 (W=8)",
+                          note="algorithmic volume flops (3,5,6)-field sum factorisation; peak = FP32 ALU "
+                               "152 SM x 128 lanes x 2 x 2.07 GHz"),
+            cpu_baseline=cb, e2e=e2e, gpu_launches=int(launches), clocks=clocks,
+        )
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -258,15 +258,15 @@ def legendre_field(coef, box_lo, box_hi):
     def F(xs, ys, zs):
         tx, ty, tz = tabs(xs, ys, zs)
         Lx, Ly, Lz = (_legendre_table(K, t) for t in (tx, ty, tz))
-        return np.einsum("ijk,ia,jb,kc->cba", coef, Lx, Ly, Lz)
+        return np.einsum("ijk,ia,jb,kc->cba", coef, Lx, Ly, Lz, optimize=True)
 
     def dF(xs, ys, zs):
         tx, ty, tz = tabs(xs, ys, zs)
         Lx, Ly, Lz = (_legendre_table(K, t) for t in (tx, ty, tz))
         dx, dy, dz = (_legendre_deriv_table(K, t) for t in (tx, ty, tz))
-        gx = sc[0] * np.einsum("ijk,ia,jb,kc->cba", coef, dx, Ly, Lz)
-        gy = sc[1] * np.einsum("ijk,ia,jb,kc->cba", coef, Lx, dy, Lz)
-        gz = sc[2] * np.einsum("ijk,ia,jb,kc->cba", coef, Lx, Ly, dz)
+        gx = sc[0] * np.einsum("ijk,ia,jb,kc->cba", coef, dx, Ly, Lz, optimize=True)
+        gy = sc[1] * np.einsum("ijk,ia,jb,kc->cba", coef, Lx, dy, Lz, optimize=True)
+        gz = sc[2] * np.einsum("ijk,ia,jb,kc->cba", coef, Lx, Ly, dz, optimize=True)
         return gx, gy, gz
 
     return F, dF

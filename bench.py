@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--apply-only", action="store_true",
                     help="time only the FP32 operator apply (profiling driver for ncu)")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--max-iter", type=int, default=60000,
+                    help="cap on PCG iterations per solve (a capped solve is for profiling only)")
     return ap.parse_args()
 
 
@@ -231,7 +233,8 @@ def main():
     x = torch.zeros(n_tot, dtype=torch.float64, device=dev)
 
     def solve(m, xx, prec):
-        return m.pcg_solve(xx, tol=TOL, prec=prec, inner_tol=args.delta, check_every=16)
+        return m.pcg_solve(xx, tol=TOL, prec=prec, inner_tol=args.delta, check_every=16, max_iter=args.max_iter,
+                           raise_on_error=args.max_iter == 60000)
 
     # ---- warm-up and timed steps -----------------------------------------------
     for _ in range(args.warmup):

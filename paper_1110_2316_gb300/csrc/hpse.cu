@@ -127,6 +127,19 @@ struct DevBuf {
   }
 };
 
+// copy into an existing allocation of the same size (device pointers that
+// captured CUDA graphs hold stay valid), else reallocate
+template <typename T>
+static cudaError_t upload_reuse(DevBuf &b, const std::vector<T> &v) {
+  const size_t bytes = v.size() * sizeof(T);
+  if (!b.p || b.bytes != bytes) {
+    cudaError_t e = b.alloc(bytes);
+    if (e != cudaSuccess) return e;
+  }
+  if (v.empty()) return cudaSuccess;
+  return cudaMemcpy(b.p, v.data(), bytes, cudaMemcpyHostToDevice);
+}
+
 template <typename T>
 static cudaError_t upload(DevBuf &b, const std::vector<T> &v) {
   cudaError_t e = b.alloc(v.size() * sizeof(T));
@@ -180,7 +193,7 @@ struct hpse_mesh {
   std::vector<Group> groups;
   // device mesh arrays
   DevBuf d_dof_off, d_nbr, d_geo64, d_geo32, d_prob, d_coef_off, d_prob_ptr, d_prob_elems, d_elem_W;
-  DevBuf d_coef64, d_coef32;  // [4][nquad] m, d_x, d_y, d_z (COEF_SCALAR)
+  DevBuf d_coef64, d_coef32;  // [nquad][4] (m, d_x, d_y, d_z) per point (COEF_SCALAR)
   DevBuf d_b;                 // FP64 right-hand side
   DevBuf d_bnorm2;            // FP64 ||b||^2 per (problem, rhs)
   std::map<int, DevBuf> d_qtab;  // per degree FP64 Q-grid tables for the face data
@@ -942,6 +955,14 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data) {
   if (!m || !data || (!data->f && m->nquad > 0)) return HPSE_ERR_INVALID_ARG;
   if (m->coef_kind == HPSE_COEF_SCALAR && (!data->a || !data->grad_a)) return HPSE_ERR_INVALID_ARG;
   CK(cudaSetDevice(m->device));
+  // captured solver graphs refer to the coefficient and right-hand side
+  // buffers: drop them so that the next solve re-captures with current data
+  if (m->work) {
+    CK(cudaDeviceSynchronize());
+    for (auto &g : m->work->graphs) cudaGraphExecDestroy(g.second);
+    m->work->graphs.clear();
+    m->work->graph_launches.clear();
+  }
   const int64_t nq = m->nquad;
   const int R = m->n_rhs;
   // coefficients at the volume points: m = w J a^2, d_k = s_k a_k / a; wJa for b
@@ -966,8 +987,8 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data) {
           if (m->coef_kind == HPSE_COEF_SCALAR) {
             const double av = data->a[i];
             if (!(av > 0.0) || !std::isfinite(av)) return HPSE_ERR_INVALID_ARG;  // ellipticity
-            coef[i] = wJ * av * av;
-            for (int k = 0; k < 3; ++k) coef[(k + 1) * nq + i] = s[k] * data->grad_a[k * nq + i] / av;
+            coef[4 * i] = wJ * av * av;
+            for (int k = 0; k < 3; ++k) coef[4 * i + k + 1] = s[k] * data->grad_a[k * nq + i] / av;
             wja[i] = wJ * av;
           } else {
             wja[i] = wJ;
@@ -977,11 +998,11 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data) {
   if (m->coef_kind == HPSE_COEF_SCALAR) {
     std::vector<float> c32(coef.size());
     for (size_t i = 0; i < coef.size(); ++i) c32[i] = (float)coef[i];
-    CK(upload(m->d_coef64, coef));
-    CK(upload(m->d_coef32, c32));
+    CK(upload_reuse(m->d_coef64, coef));
+    CK(upload_reuse(m->d_coef32, c32));
   }
   const size_t nv = (size_t)R * m->ndof;
-  CK(m->d_b.alloc(nv * sizeof(double)));
+  if (!m->d_b.p || m->d_b.bytes != nv * sizeof(double)) CK(m->d_b.alloc(nv * sizeof(double)));
   if (nv) CK(cudaMemset(m->d_b.p, 0, nv * sizeof(double)));
   // volume part of b: transpose kernel on rho_b = -(w J a) f
   if (nq > 0 && m->n_elem > 0) {
@@ -1053,7 +1074,7 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data) {
     const int npr = npr_of(m);
     DevBuf part;
     CK(part.alloc((size_t)std::max(1, n_items_all(m)) * sizeof(double)));
-    CK(m->d_bnorm2.alloc((size_t)npr * sizeof(double)));
+    if (!m->d_bnorm2.p) CK(m->d_bnorm2.alloc((size_t)npr * sizeof(double)));
     if (n_items_all(m) > 0) {
       k_dot<double, double><<<n_items_all(m), 128>>>(elem_args(m), m->d_b.as<double>(), m->d_b.as<double>(),
                                                      part.as<double>());

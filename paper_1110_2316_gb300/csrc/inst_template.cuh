@@ -7,13 +7,13 @@ namespace {
 
 template <int COEF, int MODE>
 cudaError_t launch_apply_t(const void *args, int n_items, int threads, cudaStream_t s) {
-  k_apply<COEF, MODE><<<n_items, threads, ApplyLayout<COEF>::BYTES, s>>>(*static_cast<const ApplyArgs *>(args));
+  (void)threads;  // the apply CTA size is fixed at compile time (NT)
+  k_apply<COEF, MODE><<<n_items, NT, ApplyLayout<COEF>::BYTES, s>>>(*static_cast<const ApplyArgs *>(args));
   return cudaGetLastError();
 }
 
 cudaError_t apply_fn(int coef, int mode, const void *args, int n_items, int threads, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
-  if (threads <= 0 || threads > HPSE_APPLY_MAXT) return cudaErrorInvalidValue;
   if (coef == COEF_LAPLACE) {
     if (mode == MODE_PLAIN) return launch_apply_t<COEF_LAPLACE, MODE_PLAIN>(args, n_items, threads, s);
     if (mode == MODE_PCG) return launch_apply_t<COEF_LAPLACE, MODE_PCG>(args, n_items, threads, s);
@@ -30,7 +30,7 @@ size_t apply_smem_fn(int coef) {
   return coef == COEF_SCALAR ? ApplyLayout<COEF_SCALAR>::BYTES : ApplyLayout<COEF_LAPLACE>::BYTES;
 }
 
-int apply_max_threads_fn(int) { return HPSE_APPLY_MAXT; }
+int apply_max_threads_fn(int) { return NT; }
 
 cudaError_t precond_fn(int mode, const void *args, int n_items, int threads, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
@@ -46,8 +46,12 @@ cudaError_t precond_fn(int mode, const void *args, int n_items, int threads, cud
 
 template <int COEF, int MODE>
 cudaError_t set_smem_attr() {
-  return cudaFuncSetAttribute(k_apply<COEF, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)ApplyLayout<COEF>::BYTES);
+  cudaError_t e = cudaFuncSetAttribute(k_apply<COEF, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)ApplyLayout<COEF>::BYTES);
+  if (e != cudaSuccess) return e;
+  // prefer the largest shared-memory carve-out so that several CTAs fit per SM
+  return cudaFuncSetAttribute(k_apply<COEF, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              (int)cudaSharedmemCarveoutMaxShared);
 }
 
 // Upload this degree's tables (packed FP64, see registry.h) to constant

@@ -97,171 +97,206 @@ __device__ __forceinline__ double block_sum(T v, double *red) {
 }
 
 // ---------------------------------------------------------------------------
-// Face phase: y_e += contributions of the six faces of element e (eq. 4.2).
-// su: own block, snb: scratch P3, scr: scratch >= 10*P2, tabs: D, MP, KP copy
+// Face phase: y_e += contributions of the six faces of element e (eq. 4.2),
+// all six faces processed at once, then gathered node by node (no two
+// threads ever add into the same node: deterministic, no atomics).
+//
+// Per face f (axis a, side s, tangential axes t1 < t2, nodal face grid P x P):
+//   own traces  F = u|face, N = du/dlambda_a|face, G1/G2 = tangential derivatives
+//   interior:   J0 = [u], J1 = [u_{x_t1}], J2 = [u_{x_t2}], J3 = [u_{x_a}]
+//               g0 = (MP x MP) J0, gk = (MP x MP + MP x KP + KP x MP) Jk
+//   Dirichlet:  J0 = u, J1 = du/dlambda_t1, J2 = du/dlambda_t2 (eq. 2.18)
+// MP = B0^T W B0 and KP = B0^T K B0 are the Section 5.3 face forms on the
+// (2W+1)-point grid pulled back to the nodal grid (exact algebra).
+// Scratch per face: 15 arrays of P x P.
 // ---------------------------------------------------------------------------
-// out = (A (x) B) v with A acting on p2 and B on p1 (face arrays [p2][p1])
-__device__ __forceinline__ void kron_apply(const real *Am, const real *Bm, const real *v, real *tmp, real *out,
-                                           bool accumulate) {
-  for (int t = threadIdx.x; t < P2; t += blockDim.x) {
-    const int p1 = t % P, p2 = t / P;
-    real s = 0;
-#pragma unroll
-    for (int m = 0; m < P; ++m) s += Bm[p1 * P + m] * v[p2 * P + m];
-    tmp[t] = s;
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < P2; t += blockDim.x) {
-    const int p1 = t % P, p2 = t / P;
-    real s = 0;
-#pragma unroll
-    for (int m = 0; m < P; ++m) s += Am[p2 * P + m] * tmp[m * P + p1];
-    out[t] = accumulate ? out[t] + s : s;
-  }
-  __syncthreads();
-}
+constexpr int FACE_ARR = 15;
 
-// g = (MP x MP + MP x KP + KP x MP) v  -- the H^{1/2} face form in nodal space
-__device__ __forceinline__ void half_norm_apply(const real *MPs, const real *KPs, const real *v, real *ta, real *tb,
-                                                real *g) {
-  for (int t = threadIdx.x; t < P2; t += blockDim.x) {
-    const int p1 = t % P, p2 = t / P;
-    real a = 0, b = 0;
-#pragma unroll
-    for (int m = 0; m < P; ++m) {
-      a += MPs[p1 * P + m] * v[p2 * P + m];
-      b += KPs[p1 * P + m] * v[p2 * P + m];
-    }
-    ta[t] = a;
-    tb[t] = a + b;
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < P2; t += blockDim.x) {
-    const int p1 = t % P, p2 = t / P;
-    real s = 0;
-#pragma unroll
-    for (int m = 0; m < P; ++m) s += MPs[p2 * P + m] * tb[m * P + p1] + KPs[p2 * P + m] * ta[m * P + p1];
-    g[t] = s;
-  }
-  __syncthreads();
-}
-
-// traces of block blk on face (a, nend): F = u, N = du/dlambda_a, G1, G2 tangential
-__device__ __forceinline__ void face_traces(const real *blk, int a, int nend, const real *Ds, real *F, real *N,
-                                            real *G1, real *G2) {
-  for (int t = threadIdx.x; t < P2; t += blockDim.x) {
-    const int p1 = t % P, p2 = t / P;
-    F[t] = blk[fidx(a, nend, p1, p2)];
-    real s = 0;
-#pragma unroll
-    for (int k = 0; k < P; ++k) s += Ds[nend * P + k] * blk[fidx(a, k, p1, p2)];
-    N[t] = s;
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < P2; t += blockDim.x) {
-    const int p1 = t % P, p2 = t / P;
-    real s1 = 0, s2 = 0;
-#pragma unroll
-    for (int m = 0; m < P; ++m) {
-      s1 += Ds[p1 * P + m] * F[p2 * P + m];
-      s2 += Ds[p2 * P + m] * F[m * P + p1];
-    }
-    G1[t] = s1;
-    G2[t] = s2;
-  }
-  __syncthreads();
+template <int MODE>
+__device__ __forceinline__ real nb_value(const ApplyArgs &A, int64_t idx, real bt) {
+  if (MODE == MODE_PCG) return A.z[idx] + bt * A.u[idx];
+  return A.u[idx];
 }
 
 template <int MODE>
-__device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, real *sy, real *snb, real *scr,
-                           const real *Ds, const real *MPs, const real *KPs, const real *geo_e) {
-  real *F = scr, *N = scr + P2, *G1 = scr + 2 * P2, *G2 = scr + 3 * P2;
-  real *Fn = scr + 4 * P2, *Nn = scr + 5 * P2, *G1n = scr + 6 * P2, *G2n = scr + 7 * P2;
-  real *ta = scr + 8 * P2, *tb = scr + 9 * P2;
-  real *g0 = scr + 10 * P2, *g1 = scr + 11 * P2, *g2 = scr + 12 * P2, *g3 = scr + 13 * P2;
-  for (int fi = 0; fi < 6; ++fi) {
-    const int a = fi >> 1, side = fi & 1;
-    const int t1 = (a == 0) ? 1 : 0;
-    const int t2 = (a == 2) ? 1 : 2;
-    const int nend = side ? P - 1 : 0;
-    const int nb = A.nbr[(int64_t)e * 6 + fi];
-    face_traces(su, a, nend, Ds, F, N, G1, G2);
+__device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, real *sy, real *scr, const real *Ds,
+                           const real *MPs, const real *KPs, const real *geo_e) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // slot s of face f: scr + (f * FACE_ARR + s) * P2
+#define FSLOT(f, s) (scr + ((f)*FACE_ARR + (s)) * P2)
+  enum { sF = 0, sN, sFn, sNn, sJ0, sJ1, sJ2, sJ3, sT0, sA1, sA2, sA3, sB1, sB2, sB3 };
+  // F1: traces of u and of the neighbour on every face point
+  for (int t = tid; t < 6 * P2; t += nt) {
+    const int f = t / P2, sp = t - f * P2;
+    const int p1 = sp % P, p2 = sp / P;
+    const int a = f >> 1, nend = (f & 1) ? P - 1 : 0;
+    FSLOT(f, sF)[sp] = su[fidx(a, nend, p1, p2)];
+    real s = 0;
+#pragma unroll
+    for (int k = 0; k < P; ++k) s += Ds[nend * P + k] * su[fidx(a, k, p1, p2)];
+    FSLOT(f, sN)[sp] = s;
+    const int nb = A.nbr[(int64_t)e * 6 + f];
     if (nb >= 0) {
-      // neighbour block of the same right-hand side
       const int64_t base = (int64_t)r * A.ndof + A.dof_off[nb];
-      if (MODE == MODE_PCG) {
-        const double bt = A.beta[A.prob[nb] * A.n_rhs + r];
-        for (int t = threadIdx.x; t < P3; t += blockDim.x)
-          snb[t] = A.z[base + t] + (real)bt * A.u[base + t];
-      } else {
-        for (int t = threadIdx.x; t < P3; t += blockDim.x) snb[t] = A.u[base + t];
-      }
-      __syncthreads();
-      face_traces(snb, a, P - 1 - nend, Ds, Fn, Nn, G1n, G2n);
-      const real sa = geo_e[a], s1 = geo_e[t1], s2 = geo_e[t2];
-      const real *gn = A.geo + (int64_t)nb * 4;
-      const real na = gn[a], n1 = gn[t1], n2 = gn[t2];
-      // jumps of u and of the physical derivatives u_{x_k}
-      for (int t = threadIdx.x; t < P2; t += blockDim.x) {
-        Fn[t] = F[t] - Fn[t];                 // [u]
-        G1n[t] = s1 * G1[t] - n1 * G1n[t];    // [u_{x_t1}]
-        G2n[t] = s2 * G2[t] - n2 * G2n[t];    // [u_{x_t2}]
-        Nn[t] = sa * N[t] - na * Nn[t];       // [u_{x_a}]
-      }
-      __syncthreads();
-      kron_apply(MPs, MPs, Fn, ta, g0, false);
-      half_norm_apply(MPs, KPs, G1n, ta, tb, g1);
-      half_norm_apply(MPs, KPs, G2n, ta, tb, g2);
-      half_norm_apply(MPs, KPs, Nn, ta, tb, g3);
-      // transpose of the traces: face layer gets g0 + s1 D^T g1 + s2 D^T g2,
-      // every layer k along a gets sa * D[nend][k] * g3
-      for (int t = threadIdx.x; t < P2; t += blockDim.x) {
-        const int p1 = t % P, p2 = t / P;
-        real s = g0[t];
-        real u1 = 0, u2 = 0;
+      const real bt = (MODE == MODE_PCG) ? (real)A.beta[A.prob[nb] * A.n_rhs + r] : (real)0;
+      const int nn = P - 1 - nend;
+      FSLOT(f, sFn)[sp] = nb_value<MODE>(A, base + fidx(a, nn, p1, p2), bt);
+      real sn = 0;
 #pragma unroll
-        for (int m = 0; m < P; ++m) {
-          u1 += Ds[m * P + p1] * g1[p2 * P + m];
-          u2 += Ds[m * P + p2] * g2[m * P + p1];
-        }
-        s += s1 * u1 + s2 * u2;
-        const real gz = sa * g3[t];
-#pragma unroll
-        for (int k = 0; k < P; ++k) {
-          real add = Ds[nend * P + k] * gz;
-          if (k == nend) add += s;
-          sy[fidx(a, k, p1, p2)] += add;
-        }
-      }
-      __syncthreads();
-    } else {
-      // Dirichlet face: ||u||_0^2 + sum_i ||du/dlambda_i||_{1/2}^2 (eq. 2.18)
-      kron_apply(MPs, MPs, F, ta, g0, false);
-      half_norm_apply(MPs, KPs, G1, ta, tb, g1);
-      half_norm_apply(MPs, KPs, G2, ta, tb, g2);
-      for (int t = threadIdx.x; t < P2; t += blockDim.x) {
-        const int p1 = t % P, p2 = t / P;
-        real s = g0[t];
-#pragma unroll
-        for (int m = 0; m < P; ++m) s += Ds[m * P + p1] * g1[p2 * P + m] + Ds[m * P + p2] * g2[m * P + p1];
-        sy[fidx(a, nend, p1, p2)] += s;
-      }
-      __syncthreads();
+      for (int k = 0; k < P; ++k) sn += Ds[nn * P + k] * nb_value<MODE>(A, base + fidx(a, k, p1, p2), bt);
+      FSLOT(f, sNn)[sp] = sn;
     }
   }
+  __syncthreads();
+  // F2: tangential derivatives and jumps
+  for (int t = tid; t < 6 * P2; t += nt) {
+    const int f = t / P2, sp = t - f * P2;
+    const int p1 = sp % P, p2 = sp / P;
+    const int a = f >> 1;
+    const int t1 = (a == 0) ? 1 : 0, t2 = (a == 2) ? 1 : 2;
+    const real *F = FSLOT(f, sF);
+    real g1 = 0, g2 = 0;
+#pragma unroll
+    for (int m = 0; m < P; ++m) {
+      g1 += Ds[p1 * P + m] * F[p2 * P + m];
+      g2 += Ds[p2 * P + m] * F[m * P + p1];
+    }
+    const int nb = A.nbr[(int64_t)e * 6 + f];
+    if (nb >= 0) {
+      const real *Fn = FSLOT(f, sFn);
+      real h1 = 0, h2 = 0;
+#pragma unroll
+      for (int m = 0; m < P; ++m) {
+        h1 += Ds[p1 * P + m] * Fn[p2 * P + m];
+        h2 += Ds[p2 * P + m] * Fn[m * P + p1];
+      }
+      const real *gn = A.geo + (int64_t)nb * 4;
+      FSLOT(f, sJ0)[sp] = F[sp] - Fn[sp];
+      FSLOT(f, sJ1)[sp] = geo_e[t1] * g1 - gn[t1] * h1;
+      FSLOT(f, sJ2)[sp] = geo_e[t2] * g2 - gn[t2] * h2;
+      FSLOT(f, sJ3)[sp] = geo_e[a] * FSLOT(f, sN)[sp] - gn[a] * FSLOT(f, sNn)[sp];
+    } else {
+      FSLOT(f, sJ0)[sp] = F[sp];
+      FSLOT(f, sJ1)[sp] = g1;
+      FSLOT(f, sJ2)[sp] = g2;
+      FSLOT(f, sJ3)[sp] = 0;
+    }
+  }
+  __syncthreads();
+  // F3: first Kronecker factor (along p1)
+  for (int t = tid; t < 6 * P2; t += nt) {
+    const int f = t / P2, sp = t - f * P2;
+    const int p1 = sp % P, p2 = sp / P;
+    const real *J0 = FSLOT(f, sJ0), *J1 = FSLOT(f, sJ1), *J2 = FSLOT(f, sJ2), *J3 = FSLOT(f, sJ3);
+    real t0 = 0, a1 = 0, a2 = 0, a3 = 0, b1 = 0, b2 = 0, b3 = 0;
+#pragma unroll
+    for (int m = 0; m < P; ++m) {
+      const real mp = MPs[p1 * P + m], kp = KPs[p1 * P + m];
+      t0 += mp * J0[p2 * P + m];
+      a1 += mp * J1[p2 * P + m];
+      b1 += kp * J1[p2 * P + m];
+      a2 += mp * J2[p2 * P + m];
+      b2 += kp * J2[p2 * P + m];
+      a3 += mp * J3[p2 * P + m];
+      b3 += kp * J3[p2 * P + m];
+    }
+    FSLOT(f, sT0)[sp] = t0;
+    FSLOT(f, sA1)[sp] = a1;
+    FSLOT(f, sA2)[sp] = a2;
+    FSLOT(f, sA3)[sp] = a3;
+    FSLOT(f, sB1)[sp] = a1 + b1;
+    FSLOT(f, sB2)[sp] = a2 + b2;
+    FSLOT(f, sB3)[sp] = a3 + b3;
+  }
+  __syncthreads();
+  // F4: second factor (along p2): g0 -> J0 slot, g1..g3 -> J1..J3 slots
+  for (int t = tid; t < 6 * P2; t += nt) {
+    const int f = t / P2, sp = t - f * P2;
+    const int p1 = sp % P, p2 = sp / P;
+    real g0 = 0, g1 = 0, g2 = 0, g3 = 0;
+#pragma unroll
+    for (int m = 0; m < P; ++m) {
+      const real mp = MPs[p2 * P + m], kp = KPs[p2 * P + m];
+      const int o = m * P + p1;
+      g0 += mp * FSLOT(f, sT0)[o];
+      g1 += mp * FSLOT(f, sB1)[o] + kp * FSLOT(f, sA1)[o];
+      g2 += mp * FSLOT(f, sB2)[o] + kp * FSLOT(f, sA2)[o];
+      g3 += mp * FSLOT(f, sB3)[o] + kp * FSLOT(f, sA3)[o];
+    }
+    FSLOT(f, sJ0)[sp] = g0;
+    FSLOT(f, sJ1)[sp] = g1;
+    FSLOT(f, sJ2)[sp] = g2;
+    FSLOT(f, sJ3)[sp] = g3;
+  }
+  __syncthreads();
+  // F5: transposed traces on the face grid: C (face layer) -> F slot, Gn (normal) -> N slot
+  for (int t = tid; t < 6 * P2; t += nt) {
+    const int f = t / P2, sp = t - f * P2;
+    const int p1 = sp % P, p2 = sp / P;
+    const int a = f >> 1;
+    const int t1 = (a == 0) ? 1 : 0, t2 = (a == 2) ? 1 : 2;
+    const bool interior = A.nbr[(int64_t)e * 6 + f] >= 0;
+    const real *g1 = FSLOT(f, sJ1), *g2 = FSLOT(f, sJ2);
+    real u1 = 0, u2 = 0;
+#pragma unroll
+    for (int m = 0; m < P; ++m) {
+      u1 += Ds[m * P + p1] * g1[p2 * P + m];
+      u2 += Ds[m * P + p2] * g2[m * P + p1];
+    }
+    const real c1 = interior ? geo_e[t1] : (real)1, c2 = interior ? geo_e[t2] : (real)1;
+    FSLOT(f, sF)[sp] = FSLOT(f, sJ0)[sp] + c1 * u1 + c2 * u2;
+    FSLOT(f, sN)[sp] = interior ? geo_e[a] * FSLOT(f, sJ3)[sp] : (real)0;
+  }
+  __syncthreads();
+  // F6: gather onto the nodes of the element
+  for (int t = tid; t < P3; t += nt) {
+    const int i = t % P, j = (t / P) % P, k = t / P2;
+    real acc = 0;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      const int a = f >> 1, nend = (f & 1) ? P - 1 : 0;
+      const int n = a == 0 ? i : (a == 1 ? j : k);
+      const int p1 = a == 0 ? j : i;
+      const int p2 = a == 2 ? j : k;
+      const int sp = p2 * P + p1;
+      acc += Ds[nend * P + n] * FSLOT(f, sN)[sp];
+      if (n == nend) acc += FSLOT(f, sF)[sp];
+    }
+    sy[t] += acc;
+  }
+  __syncthreads();
+#undef FSLOT
+}
+
+// vector load of the 4 pointwise coefficients (m, d_x, d_y, d_z) of a point
+__device__ __forceinline__ void load_coef4(const real *p, real &m, real &dx, real &dy, real &dz) {
+#if defined(HPSE_DOUBLE)
+  const double2 a = *reinterpret_cast<const double2 *>(p);
+  const double2 b = *reinterpret_cast<const double2 *>(p + 2);
+  m = a.x;
+  dx = a.y;
+  dy = b.x;
+  dz = b.y;
+#else
+  const float4 a = *reinterpret_cast<const float4 *>(p);
+  m = a.x;
+  dx = a.y;
+  dy = a.z;
+  dz = a.w;
+#endif
 }
 
 // ---------------------------------------------------------------------------
 // Operator apply: y = A u  (volume + faces), one CTA per (element, rhs).
-// Shared memory: su[P3] | X[NX][QP2] | T[NTF][Q2P] (later reused for sy, snb,
-// face scratch) | small tables.
+// Shared memory: su[P3] | X[NX][QP2] | T region (T fields, then sy and the
+// face scratch) | D, MP, KP copies | FP64 reduction buffer (16-byte aligned).
 // ---------------------------------------------------------------------------
 template <int COEF>
 struct ApplyLayout {
   static constexpr int NX = (COEF == COEF_SCALAR) ? 3 : 2;
   static constexpr int NTF = (COEF == COEF_SCALAR) ? 4 : 2;
   static constexpr int T_REGION0 = NTF * Q2P;
-  static constexpr int T_NEED = 2 * P3 + 14 * P2;
+  static constexpr int T_NEED = P3 + 6 * FACE_ARR * P2;
   static constexpr int T_REGION = T_REGION0 > T_NEED ? T_REGION0 : T_NEED;
   static constexpr int TABS = 3 * P2;
   static constexpr int TOTAL = P3 + NX * QP2 + T_REGION + TABS;
@@ -270,14 +305,24 @@ struct ApplyLayout {
   static constexpr size_t BYTES = RED_OFF + 64 * sizeof(double);
 };
 
+// Threads per apply CTA: one thread per z-line (Q^2 lines) rounded up to
+// whole warps, capped; every stage then runs at most once per thread when
+// Q^2 <= NT, so no constant-table read is loop-invariant across line
+// iterations and every FMA keeps its constant-bank operand.
 #if defined(HPSE_DOUBLE)
 #define HPSE_APPLY_MAXT 256
 #else
-#define HPSE_APPLY_MAXT 384
+#define HPSE_APPLY_MAXT 448
 #endif
+constexpr int NT_RAW = ((Q2 + 31) / 32) * 32;
+constexpr int NT = NT_RAW < 64 ? 64 : (NT_RAW > HPSE_APPLY_MAXT ? HPSE_APPLY_MAXT : NT_RAW);
+// FP32: enough resident CTAs for ~20 warps per SM; FP64 is bound by the
+// FP64 pipe at any occupancy
+constexpr int APPLY_MINB_RAW = 640 / NT;
+constexpr int APPLY_MINB = sizeof(real) == 8 ? 1 : (APPLY_MINB_RAW < 1 ? 1 : (APPLY_MINB_RAW > 8 ? 8 : APPLY_MINB_RAW));
 
 template <int COEF, int MODE>
-__global__ void __launch_bounds__(HPSE_APPLY_MAXT) k_apply(const ApplyArgs A) {
+__global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
   typedef ApplyLayout<COEF> L;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real *su = reinterpret_cast<real *>(smem_raw);
@@ -297,7 +342,8 @@ __global__ void __launch_bounds__(HPSE_APPLY_MAXT) k_apply(const ApplyArgs A) {
   const real *geo_e = A.geo + (int64_t)e * 4;
   const real sx = geo_e[0], sy_ = geo_e[1], sz = geo_e[2], Jac = geo_e[3];
   const real sx2 = sx * sx, sy2 = sy_ * sy_, sz2 = sz * sz;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x;
+  constexpr int nt = NT;
 
   for (int t = tid; t < P2; t += nt) {
     stab[t] = c_tab.D[t];
@@ -335,6 +381,7 @@ __global__ void __launch_bounds__(HPSE_APPLY_MAXT) k_apply(const ApplyArgs A) {
         o0[q] = a0;
         o2[q] = a2;
         if (COEF == COEF_SCALAR) o1[q] = a1;
+        __syncwarp();  // scheduling fence (register pressure)
       }
     }
     __syncthreads();
@@ -369,17 +416,23 @@ __global__ void __launch_bounds__(HPSE_APPLY_MAXT) k_apply(const ApplyArgs A) {
           T10[o] = t10;
           T01[o] = t01;
         }
+        __syncwarp();  // scheduling fence: keeps the unrolled output iterations from interleaving
       }
     }
     __syncthreads();
   }
 
-  // ---- fused z-stage: forward, pointwise weight, transpose ----------------
+  // ---- z-stage per (qa, qb) column: forward + pointwise weight into rho[Q]
+  // (registers), then the transpose from rho ------------------------------
   for (int l = tid; l < Q2; l += nt) {
     const int qa = l % Q, qb = l / Q;
-    real a00[P], aL[P], a10[P], a01[P];
-    real rz[P], r0[P], rx[P], ry[P];
-    if (MODE != MODE_TRANSPOSE) {
+    const int64_t cbase = A.coef_off[e] + (int64_t)qb * Q + qa;
+    real rho[Q];
+    if (MODE == MODE_TRANSPOSE) {
+#pragma unroll
+      for (int qc = 0; qc < Q; ++qc) rho[qc] = (real)A.rho[(int64_t)r * A.nquad + cbase + (int64_t)qc * Q2];
+    } else {
+      real a00[P], aL[P], a10[P], a01[P];
 #pragma unroll
       for (int k = 0; k < P; ++k) {
         const int o = (k * Q + qb) * Q + qa;
@@ -390,28 +443,9 @@ __global__ void __launch_bounds__(HPSE_APPLY_MAXT) k_apply(const ApplyArgs A) {
           a01[k] = T01[o];
         }
       }
-    }
+      const real wab = c_tab.WQ[qa] * c_tab.WQ[qb] * Jac;
 #pragma unroll
-    for (int k = 0; k < P; ++k) {
-      rz[k] = 0;
-      r0[k] = 0;
-      rx[k] = 0;
-      ry[k] = 0;
-    }
-    const real wab = c_tab.WQ[qa] * c_tab.WQ[qb] * Jac;
-    const int64_t cbase = A.coef_off[e] + (int64_t)qb * Q + qa;
-#pragma unroll
-    for (int qc = 0; qc < Q; ++qc) {
-      real rho, dx = 0, dy = 0, dz = 0;
-      if (COEF == COEF_SCALAR) {
-        const int64_t ci = cbase + (int64_t)qc * Q2;
-        dx = A.coef[A.nquad + ci];
-        dy = A.coef[2 * A.nquad + ci];
-        dz = A.coef[3 * A.nquad + ci];
-      }
-      if (MODE == MODE_TRANSPOSE) {
-        rho = (real)A.rho[(int64_t)r * A.nquad + cbase + (int64_t)qc * Q2];
-      } else {
+      for (int qc = 0; qc < Q; ++qc) {
         real s2 = 0, s0 = 0, s1z = 0, sxx = 0, syy = 0;
 #pragma unroll
         for (int k = 0; k < P; ++k) {
@@ -423,20 +457,38 @@ __global__ void __launch_bounds__(HPSE_APPLY_MAXT) k_apply(const ApplyArgs A) {
             syy += c_tab.B[0][qc * P + k] * a01[k];
           }
         }
-        real sigma = sz2 * s2 + s0;
+        const real sigma0 = sz2 * s2 + s0;
         if (COEF == COEF_SCALAR) {
-          sigma += dz * s1z + dx * sxx + dy * syy;
-          rho = A.coef[cbase + (int64_t)qc * Q2] * sigma;
+          real mq, dx, dy, dz;
+          load_coef4(A.coef + 4 * (cbase + (int64_t)qc * Q2), mq, dx, dy, dz);
+          rho[qc] = mq * (sigma0 + dz * s1z + dx * sxx + dy * syy);
         } else {
-          rho = wab * c_tab.WQ[qc] * sigma;
+          rho[qc] = wab * c_tab.WQ[qc] * sigma0;
         }
+        __syncwarp();  // scheduling fence (register pressure)
       }
-      const real rz2 = sz2 * rho;
-      const real rzd = dz * rho, rxd = dx * rho, ryd = dy * rho;
+    }
+    real rz[P], r0[P], rx[P], ry[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      rz[k] = 0;
+      r0[k] = 0;
+      rx[k] = 0;
+      ry[k] = 0;
+    }
+#pragma unroll
+    for (int qc = 0; qc < Q; ++qc) {
+      const real rq = rho[qc];
+      real dx = 0, dy = 0, dz = 0;
+      if (COEF == COEF_SCALAR) {
+        real mq;
+        load_coef4(A.coef + 4 * (cbase + (int64_t)qc * Q2), mq, dx, dy, dz);
+      }
+      const real rz2 = sz2 * rq, rzd = dz * rq, rxd = dx * rq, ryd = dy * rq;
 #pragma unroll
       for (int k = 0; k < P; ++k) {
         rz[k] += c_tab.B[2][qc * P + k] * rz2;
-        r0[k] += c_tab.B[0][qc * P + k] * rho;
+        r0[k] += c_tab.B[0][qc * P + k] * rq;
         if (COEF == COEF_SCALAR) {
           rz[k] += c_tab.B[1][qc * P + k] * rzd;
           rx[k] += c_tab.B[0][qc * P + k] * rxd;
@@ -457,37 +509,44 @@ __global__ void __launch_bounds__(HPSE_APPLY_MAXT) k_apply(const ApplyArgs A) {
   }
   __syncthreads();
 
-  // ---- y-stage transpose (lines (qa, k)) ---------------------------------
+  // ---- y-stage transpose (lines (qa, k)), in two register passes ----------
   for (int l = tid; l < QP; l += nt) {
     const int qa = l % Q, k = l / Q;
-    real vz[Q], v0[Q], vx[Q], vy[Q];
-#pragma unroll
-    for (int qb = 0; qb < Q; ++qb) {
-      const int o = (k * Q + qb) * Q + qa;
-      vz[qb] = T00[o];
-      v0[qb] = TL[o];
-      if (COEF == COEF_SCALAR) {
-        vx[qb] = T10[o];
-        vy[qb] = T01[o];
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-      real x0 = 0, x0b = 0, x2 = 0, x1 = 0, x0c = 0;
+    {
+      real vz[Q], v0[Q], vy[Q];
 #pragma unroll
       for (int qb = 0; qb < Q; ++qb) {
-        x0 += c_tab.B[0][qb * P + j] * vz[qb];
-        x0b += c_tab.B[2][qb * P + j] * v0[qb];
-        x2 += c_tab.B[0][qb * P + j] * v0[qb];
-        if (COEF == COEF_SCALAR) {
-          x1 += c_tab.B[0][qb * P + j] * vx[qb];
-          x0c += c_tab.B[1][qb * P + j] * vy[qb];
-        }
+        const int o = (k * Q + qb) * Q + qa;
+        vz[qb] = T00[o];
+        v0[qb] = TL[o];
+        if (COEF == COEF_SCALAR) vy[qb] = T01[o];
       }
-      const int o = (k * P + j) * Q + qa;
-      X0[o] = x0 + sy2 * x0b + x0c;
-      X2[o] = sx2 * x2;
-      if (COEF == COEF_SCALAR) X1[o] = x1;
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        real x0 = 0, x0b = 0, x0c = 0, x2 = 0;
+#pragma unroll
+        for (int qb = 0; qb < Q; ++qb) {
+          x0 += c_tab.B[0][qb * P + j] * vz[qb];
+          x0b += c_tab.B[2][qb * P + j] * v0[qb];
+          x2 += c_tab.B[0][qb * P + j] * v0[qb];
+          if (COEF == COEF_SCALAR) x0c += c_tab.B[1][qb * P + j] * vy[qb];
+        }
+        const int o = (k * P + j) * Q + qa;
+        X0[o] = x0 + sy2 * x0b + x0c;
+        X2[o] = sx2 * x2;
+      }
+    }
+    if (COEF == COEF_SCALAR) {
+      real vx[Q];
+#pragma unroll
+      for (int qb = 0; qb < Q; ++qb) vx[qb] = T10[(k * Q + qb) * Q + qa];
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        real x1 = 0;
+#pragma unroll
+        for (int qb = 0; qb < Q; ++qb) x1 += c_tab.B[0][qb * P + j] * vx[qb];
+        X1[(k * P + j) * Q + qa] = x1;
+      }
     }
   }
   __syncthreads();
@@ -516,11 +575,8 @@ __global__ void __launch_bounds__(HPSE_APPLY_MAXT) k_apply(const ApplyArgs A) {
   __syncthreads();
 
   // ---- faces ---------------------------------------------------------------
-  if (MODE != MODE_TRANSPOSE && !A.skip_faces) {
-    real *snb = sT + P3;
-    real *scr = sT + 2 * P3;
-    face_phase<MODE>(A, e, r, su, sy, snb, scr, stab, stab + P2, stab + 2 * P2, geo_e);
-  }
+  if (MODE != MODE_TRANSPOSE && !A.skip_faces)
+    face_phase<MODE>(A, e, r, su, sy, sT + P3, stab, stab + P2, stab + 2 * P2, geo_e);
 
   // ---- store (and the p.q partial of PCG) --------------------------------
   double part = 0.0;

@@ -22,7 +22,7 @@ struct ApplyArgsT {
   const int32_t *nbr;
   const T *geo;
   const int32_t *prob;
-  const T *coef;
+  const T *coef;            // [nquad][4]: m, d_x, d_y, d_z per volume point
   const int64_t *coef_off;
   int64_t nquad;
   const T *z;

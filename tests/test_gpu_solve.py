@@ -133,3 +133,20 @@ def test_refinement_modes(api, mode, delta):
     xm, rep = _solve(api, mesh, api.FP32, refine_mode=mode, inner_tol=delta)
     assert rep["status"] == 0 and rep["rel_residual"] <= 1e-10, rep
     assert h1_rel_diff(disc, xm, x64) <= 1e-8
+
+
+def test_set_data_twice_then_solve(api):
+    # new data on an existing handle must invalidate every captured solver graph
+    pb = wl.varcoef_manufactured(n=(2, 2, 1), W=4)
+    mesh = _mesh(api, pb)
+    _solve(api, mesh, api.FP32)
+    _solve(api, mesh, api.FP64)
+    f2 = lambda xs, ys, zs: 3.0 * pb.f[0](xs, ys, zs)
+    pb2 = wl.Problem(pb.mesh, [f2], pb.g, pb.a, pb.grad_a)
+    mesh.set_data(**api.problem_data_arrays(mesh, pb2))
+    disc2 = Discretisation(pb2)
+    for prec in (api.FP32, api.FP64):
+        x, rep = _solve(api, mesh, prec)
+        assert rep["status"] == 0 and rep["rel_residual"] <= 1e-10
+        xo, _, _ = pcg(disc2.apply_A, lambda r: apply_Cinv(disc2, r), disc2.rhs_b(), tol=1e-10)
+        assert h1_rel_diff(disc2, x, xo) <= 1e-8

@@ -314,8 +314,10 @@ struct ApplyLayout {
 #else
 #define HPSE_APPLY_MAXT 448
 #endif
-constexpr int NT_RAW = ((Q2 + 31) / 32) * 32;
+#define PAD32(n) ((((n) + 31) / 32) * 32)
+constexpr int NT_RAW = PAD32(Q2);
 constexpr int NT = NT_RAW < 64 ? 64 : (NT_RAW > HPSE_APPLY_MAXT ? HPSE_APPLY_MAXT : NT_RAW);
+static_assert(NT % 32 == 0, "warp-uniform line loops need a whole number of warps per CTA");
 // FP32: enough resident CTAs for ~20 warps per SM; FP64 is bound by the
 // FP64 pipe at any occupancy
 constexpr int APPLY_MINB_RAW = 640 / NT;
@@ -364,7 +366,12 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
     __syncthreads();
 
     // ---- x-stage (lines along x: (j, k)) -------------------------------
-    for (int l = tid; l < P2; l += nt) {
+    // Loops that contain a __syncwarp() run to a multiple of 32 lines so
+    // every lane of a warp reaches each fence; padding lanes read a valid
+    // (clamped) line and store nothing.
+    for (int lp = tid; lp < PAD32(P2); lp += nt) {
+      const bool ok = lp < P2;
+      const int l = ok ? lp : P2 - 1;
       real v[P];
 #pragma unroll
       for (int i = 0; i < P; ++i) v[i] = su[l * P + i];
@@ -378,16 +385,20 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
           a2 += c_tab.B[2][q * P + i] * v[i];
           if (COEF == COEF_SCALAR) a1 += c_tab.B[1][q * P + i] * v[i];
         }
-        o0[q] = a0;
-        o2[q] = a2;
-        if (COEF == COEF_SCALAR) o1[q] = a1;
-        __syncwarp();  // scheduling fence (register pressure)
+        if (ok) {
+          o0[q] = a0;
+          o2[q] = a2;
+          if (COEF == COEF_SCALAR) o1[q] = a1;
+        }
+        __syncwarp();  // scheduling fence (register pressure); reached by all 32 lanes
       }
     }
     __syncthreads();
 
     // ---- y-stage (lines along y: (qa, k)) -------------------------------
-    for (int l = tid; l < QP; l += nt) {
+    for (int lp = tid; lp < PAD32(QP); lp += nt) {
+      const bool ok = lp < QP;
+      const int l = ok ? lp : QP - 1;
       const int qa = l % Q, k = l / Q;
       real v0[P], v2[P], v1[P];
 #pragma unroll
@@ -410,13 +421,15 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
           }
         }
         const int o = (k * Q + qb) * Q + qa;
-        T00[o] = t00;
-        TL[o] = sx2 * tl2 + sy2 * tl0;
-        if (COEF == COEF_SCALAR) {
-          T10[o] = t10;
-          T01[o] = t01;
+        if (ok) {
+          T00[o] = t00;
+          TL[o] = sx2 * tl2 + sy2 * tl0;
+          if (COEF == COEF_SCALAR) {
+            T10[o] = t10;
+            T01[o] = t01;
+          }
         }
-        __syncwarp();  // scheduling fence: keeps the unrolled output iterations from interleaving
+        __syncwarp();  // scheduling fence (keeps unrolled outputs from interleaving); all 32 lanes
       }
     }
     __syncthreads();
@@ -424,7 +437,9 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
 
   // ---- z-stage per (qa, qb) column: forward + pointwise weight into rho[Q]
   // (registers), then the transpose from rho ------------------------------
-  for (int l = tid; l < Q2; l += nt) {
+  for (int lp = tid; lp < PAD32(Q2); lp += nt) {
+    const bool ok = lp < Q2;
+    const int l = ok ? lp : Q2 - 1;
     const int qa = l % Q, qb = l / Q;
     const int64_t cbase = A.coef_off[e] + (int64_t)qb * Q + qa;
     real rho[Q];
@@ -465,7 +480,7 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
         } else {
           rho[qc] = wab * c_tab.WQ[qc] * sigma0;
         }
-        __syncwarp();  // scheduling fence (register pressure)
+        __syncwarp();  // scheduling fence (register pressure); reached by all 32 lanes
       }
     }
     real rz[P], r0[P], rx[P], ry[P];
@@ -496,14 +511,16 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
         }
       }
     }
+    if (ok) {
 #pragma unroll
-    for (int k = 0; k < P; ++k) {
-      const int o = (k * Q + qb) * Q + qa;
-      T00[o] = rz[k];
-      TL[o] = r0[k];
-      if (COEF == COEF_SCALAR) {
-        T10[o] = rx[k];
-        T01[o] = ry[k];
+      for (int k = 0; k < P; ++k) {
+        const int o = (k * Q + qb) * Q + qa;
+        T00[o] = rz[k];
+        TL[o] = r0[k];
+        if (COEF == COEF_SCALAR) {
+          T10[o] = rx[k];
+          T01[o] = ry[k];
+        }
       }
     }
   }

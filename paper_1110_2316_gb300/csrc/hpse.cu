@@ -156,7 +156,7 @@ struct Group {
 struct SolverWork {
   size_t n = 0;  // n_rhs * ndof
   // FP64
-  DevBuf x64, r64, z64, pa64, pb64, q64, b_scratch;
+  DevBuf x64, r64, z64, pa64, pb64, q64, ri64;
   // FP32
   DevBuf x32, r32, z32, pa32, pb32, q32;
   // partials per (element, rhs) and PCG scalars per (problem, rhs)
@@ -277,6 +277,30 @@ __global__ void k_residual(ElemVecArgs A, const double *b, const double *q, doub
   }
   s = block_sum_d(s);
   if (threadIdx.x == 0) part[(int64_t)e * A.n_rhs + rr] = s;
+}
+
+// out = r64 * scale[pr] converted to TO
+template <typename TO>
+__global__ void k_scale_copy(ElemVecArgs A, const int32_t *prob, int n_rhs, const double *r64, const double *scale,
+                             TO *out) {
+  const int item = blockIdx.x;
+  const int e = item / A.n_rhs, rr = item - e * A.n_rhs;
+  const int P = A.elem_W[e] + 1, n = P * P * P;
+  const int64_t base = (int64_t)rr * A.ndof + A.dof_off[e];
+  const double s = scale[prob[e] * n_rhs + rr];
+  for (int t = threadIdx.x; t < n; t += blockDim.x) out[base + t] = (TO)(r64[base + t] * s);
+}
+
+// x64 += d * scale[pr]
+template <typename TI>
+__global__ void k_add_scaled(ElemVecArgs A, const int32_t *prob, int n_rhs, const TI *d, const double *scale,
+                             double *x64) {
+  const int item = blockIdx.x;
+  const int e = item / A.n_rhs, rr = item - e * A.n_rhs;
+  const int P = A.elem_W[e] + 1, n = P * P * P;
+  const int64_t base = (int64_t)rr * A.ndof + A.dof_off[e];
+  const double s = scale[prob[e] * n_rhs + rr];
+  for (int t = threadIdx.x; t < n; t += blockDim.x) x64[base + t] += (double)d[base + t] * s;
 }
 
 // r32 = r64 * scale[pr]  (scale = 1/||r64|| of the (problem, rhs), 0 if inactive)
@@ -1190,6 +1214,7 @@ static hpse_status ensure_work(hpse_mesh *m) {
   CK(w->pa64.alloc(d));
   CK(w->pb64.alloc(d));
   CK(w->q64.alloc(d));
+  CK(w->ri64.alloc(d));
   CK(w->x32.alloc(f));
   CK(w->r32.alloc(f));
   CK(w->z32.alloc(f));
@@ -1353,15 +1378,18 @@ static hpse_status fp64_residual(hpse_mesh *m, const double *x64, double tol, do
   return HPSE_OK;
 }
 
-// FP32-apply PCG with FP64 "reliable updates": one PCG iteration sequence in
-// FP32 (vectors scaled by 1/||b||); whenever its recursive residual has
-// dropped by the factor delta since the last refresh (or it claims
-// convergence), the correction is added to x in FP64, the true residual
-// b - A x is recomputed with FP64 applies, and the FP32 residual is replaced by
-// it while the search direction is kept.  Stops when the FP64 residual meets
-// ||b - A x|| <= tol ||b|| for every (problem, rhs).
-static hpse_status solve_mixed_reliable(hpse_mesh *m, const hpse_solve_opts *o, double *x, hpse_solve_report *rep,
-                                        double deadline, int *status_out) {
+// PCG with residual refresh ("reliable updates"): one PCG iteration sequence
+// with applies, preconditioner and vectors in T (vectors scaled by 1/||b||);
+// whenever its recursive residual has dropped by the factor delta since the
+// last refresh (delta = 0: only when it claims convergence), the correction is
+// added to x in FP64, the true residual b - A x is recomputed with FP64
+// applies, and the iteration's residual is replaced by it while the search
+// direction is kept.  Stops when the FP64 residual meets ||b - A x|| <= tol ||b||
+// for every (problem, rhs).  T = float: FP32 applies + FP64 refinement;
+// T = double: FP64 PCG whose stopping test is made on the true residual.
+template <typename T>
+static hpse_status solve_reliable(hpse_mesh *m, const hpse_solve_opts *o, double *x, hpse_solve_report *rep,
+                                  double deadline, double delta, int *status_out) {
   SolverWork &w = *m->work;
   cudaStream_t s = w.st;
   const int npr = npr_of(m);
@@ -1370,10 +1398,13 @@ static hpse_status solve_mixed_reliable(hpse_mesh *m, const hpse_solve_opts *o, 
   double *sc_scale = w.sc.as<double>() + 9 * npr;
   double *sc_rnorm = w.sc.as<double>() + 10 * npr;
   double *sc_bn = w.sc.as<double>() + 11 * npr;  // ||b|| per pair, then 1/||b|| in sc_scale
-  const double delta = (o->inner_tol > 0 && o->inner_tol < 1) ? o->inner_tol : 1e-2;
   const int chunk0 = o->check_every > 0 ? o->check_every : 16;
   const int chunk = chunk0 + (chunk0 & 1);
-  const size_t nb32 = w.n * sizeof(float);
+  const size_t nb32 = w.n * sizeof(T);
+  const bool dbl = sizeof(T) == 8;
+  T *x32 = dbl ? (T *)w.x64.p : (T *)w.x32.p, *r32 = dbl ? (T *)w.ri64.p : (T *)w.r32.p;
+  T *z32 = dbl ? (T *)w.z64.p : (T *)w.z32.p, *pa = dbl ? (T *)w.pa64.p : (T *)w.pa32.p;
+  T *pb = dbl ? (T *)w.pb64.p : (T *)w.pb32.p, *q32 = dbl ? (T *)w.q64.p : (T *)w.q32.p;
   int status = HPSE_OK, updates = 0, applies = 0;
   // ||b|| and 1/||b|| per pair
   {
@@ -1395,21 +1426,19 @@ static hpse_status solve_mixed_reliable(hpse_mesh *m, const hpse_solve_opts *o, 
     if (st != HPSE_OK) return st;
     ++applies;
   }
-  k_scale_to_f32<<<n_items_all(m), 128, 0, s>>>(elem_args(m), m->d_prob.as<int32_t>(), m->n_rhs,
-                                                w.r64.as<double>(), sc_scale, w.r32.as<float>());
-  CK(cudaMemsetAsync(w.x32.p, 0, nb32, s));
-  CK(cudaMemsetAsync(w.pa32.p, 0, nb32, s));
+  k_scale_copy<T><<<n_items_all(m), 128, 0, s>>>(elem_args(m), m->d_prob.as<int32_t>(), m->n_rhs,
+                                                 w.r64.as<double>(), sc_scale, r32);
+  CK(cudaMemsetAsync(x32, 0, nb32, s));
+  CK(cudaMemsetAsync(pa, 0, nb32, s));
   CK(cudaMemsetAsync(S.status, 0, npr * sizeof(int32_t), s));
   {
-    PrecArgsT<float> p = prec_args<float>(m, m->groups[0]);
-    p.rin = w.r32.as<float>();
-    p.zout = w.z32.as<float>();
-    hpse_status st = launch_prec_all<float>(m, MODE_PLAIN, p, s);
+    PrecArgsT<T> p = prec_args<T>(m, m->groups[0]);
+    p.rin = r32;
+    p.zout = z32;
+    hpse_status st = launch_prec_all<T>(m, MODE_PLAIN, p, s);
     if (st != HPSE_OK) return st;
-    k_dot<float, float><<<n_items_all(m), 128, 0, s>>>(elem_args(m), w.r32.as<float>(), w.z32.as<float>(),
-                                                       w.part0.as<double>());
-    k_dot<float, float><<<n_items_all(m), 128, 0, s>>>(elem_args(m), w.r32.as<float>(), w.r32.as<float>(),
-                                                       w.part1.as<double>());
+    k_dot<T, T><<<n_items_all(m), 128, 0, s>>>(elem_args(m), r32, z32, w.part0.as<double>());
+    k_dot<T, T><<<n_items_all(m), 128, 0, s>>>(elem_args(m), r32, r32, w.part1.as<double>());
     k_fin_init<<<npr, 128, 0, s>>>(fin_args(m), S, w.part0.as<double>(), w.part1.as<double>(), o->tol, sc_scale, 1);
     CK(cudaGetLastError());
     g_launches += 4;
@@ -1418,10 +1447,8 @@ static hpse_status solve_mixed_reliable(hpse_mesh *m, const hpse_solve_opts *o, 
   CK(cudaStreamSynchronize(s));
   std::vector<double> rr_ref(npr);
   for (int i = 0; i < npr; ++i) rr_ref[i] = w.h_sc[2 * npr + i];
-  // graph of `chunk` FP32 iterations
-  float *x32 = w.x32.as<float>(), *r32 = w.r32.as<float>(), *z32 = w.z32.as<float>();
-  float *pa = w.pa32.as<float>(), *pb = w.pb32.as<float>(), *q32 = w.q32.as<float>();
-  const long long key = (long long)chunk * 4 + 1 * 2 + 1;
+  // graph of `chunk` iterations
+  const long long key = (long long)chunk * 4 + (dbl ? 0 : 2) + 1;
   cudaGraphExec_t exec = nullptr;
   auto git = w.graphs.find(key);
   if (git == w.graphs.end()) {
@@ -1430,8 +1457,8 @@ static hpse_status solve_mixed_reliable(hpse_mesh *m, const hpse_solve_opts *o, 
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     hpse_status st = HPSE_OK;
     for (int i = 0; i < chunk && st == HPSE_OK; i += 2) {
-      st = pcg_iteration<float>(m, x32, r32, z32, pa, pb, q32, s);
-      if (st == HPSE_OK) st = pcg_iteration<float>(m, x32, r32, z32, pb, pa, q32, s);
+      st = pcg_iteration<T>(m, x32, r32, z32, pa, pb, q32, s);
+      if (st == HPSE_OK) st = pcg_iteration<T>(m, x32, r32, z32, pb, pa, q32, s);
     }
     if (st == HPSE_OK) {
       k_count_active<<<1, 256, 0, s>>>(S.active, npr, S.n_active);
@@ -1470,7 +1497,7 @@ static hpse_status solve_mixed_reliable(hpse_mesh *m, const hpse_solve_opts *o, 
       now = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
     if (refresh || capped || (deadline > 0 && now > deadline)) {
       // x += ||b|| x32 ; x32 = 0 ; r64 = b - A x ; relative residuals
-      k_add_scaled_f32<<<n_items_all(m), 128, 0, s>>>(elem_args(m), m->d_prob.as<int32_t>(), m->n_rhs, x32, sc_bn, x);
+      k_add_scaled<T><<<n_items_all(m), 128, 0, s>>>(elem_args(m), m->d_prob.as<int32_t>(), m->n_rhs, x32, sc_bn, x);
       CK(cudaGetLastError());
       ++g_launches;
       CK(cudaMemsetAsync(x32, 0, nb32, s));
@@ -1483,7 +1510,8 @@ static hpse_status solve_mixed_reliable(hpse_mesh *m, const hpse_solve_opts *o, 
       worst = 0.0;
       for (int i = 0; i < npr; ++i) worst = std::max(worst, w.h_sc[8 * npr + i]);
       if (verbose())
-        fprintf(stderr, "[hpse] refresh %d after %d FP32 iterations: max rel residual %.3e\n", updates, done, worst);
+        fprintf(stderr, "[hpse] refresh %d after %d %s iterations: max rel residual %.3e\n", updates, done,
+                dbl ? "FP64" : "FP32", worst);
       if (!(worst > o->tol)) break;
       if (capped) {
         status = HPSE_ERR_NO_CONVERGENCE;
@@ -1494,15 +1522,15 @@ static hpse_status solve_mixed_reliable(hpse_mesh *m, const hpse_solve_opts *o, 
         break;
       }
       // replace the FP32 residual by the true one, keep the direction
-      k_scale_to_f32<<<n_items_all(m), 128, 0, s>>>(elem_args(m), m->d_prob.as<int32_t>(), m->n_rhs,
-                                                    w.r64.as<double>(), sc_scale, r32);
-      PrecArgsT<float> p = prec_args<float>(m, m->groups[0]);
+      k_scale_copy<T><<<n_items_all(m), 128, 0, s>>>(elem_args(m), m->d_prob.as<int32_t>(), m->n_rhs,
+                                                     w.r64.as<double>(), sc_scale, r32);
+      PrecArgsT<T> p = prec_args<T>(m, m->groups[0]);
       p.rin = r32;
       p.zout = z32;
-      st = launch_prec_all<float>(m, MODE_PLAIN, p, s);
+      st = launch_prec_all<T>(m, MODE_PLAIN, p, s);
       if (st != HPSE_OK) return st;
-      k_dot<float, float><<<n_items_all(m), 128, 0, s>>>(elem_args(m), r32, z32, w.part0.as<double>());
-      k_dot<float, float><<<n_items_all(m), 128, 0, s>>>(elem_args(m), r32, r32, w.part1.as<double>());
+      k_dot<T, T><<<n_items_all(m), 128, 0, s>>>(elem_args(m), r32, z32, w.part0.as<double>());
+      k_dot<T, T><<<n_items_all(m), 128, 0, s>>>(elem_args(m), r32, r32, w.part1.as<double>());
       k_fin_reliable<<<npr, 128, 0, s>>>(fin_args(m), S, w.part0.as<double>(), w.part1.as<double>(), sc_rel, o->tol);
       CK(cudaGetLastError());
       g_launches += 4;
@@ -1552,34 +1580,19 @@ extern "C" hpse_status hpse_pcg_solve(hpse_mesh *m, const hpse_solve_opts *o, do
   int total_it = 0, status = HPSE_OK, sweeps = 0, applies = 0;
   if (o->zero_init) CK(cudaMemsetAsync(x, 0, nb, s));
   if (o->prec == HPSE_FP64) {
-    // plain FP64 PCG on A d = b - A x0, x = x0 + d
-    bool x0_zero = o->zero_init != 0;
-    if (x0_zero) {
-      CK(cudaMemcpyAsync(w.r64.p, m->d_b.p, nb, cudaMemcpyDeviceToDevice, s));
-    } else {
-      st = fp64_residual(m, x, o->tol, sc_rel, sc_scale, sc_rnorm, s);
-      if (st != HPSE_OK) return st;
-      ++applies;
-    }
-    int it = 0;
-    st = run_pcg<double>(m, w.x64.as<double>(), w.r64.as<double>(), w.z64.as<double>(), w.pa64.as<double>(),
-                         w.pb64.as<double>(), w.q64.as<double>(), o->tol, o->max_iter, chunk, nullptr, deadline, &it,
-                         &status);
+    // FP64 PCG; its convergence claim is checked on the true FP64 residual
+    if (o->zero_init) CK(cudaMemsetAsync(x, 0, nb, s));
+    st = solve_reliable<double>(m, o, x, rep, deadline, 0.0, &status);
     if (st != HPSE_OK) return st;
-    // relative tolerance of run_pcg is relative to ||r0||; for x0 = 0 that is ||b||
-    if (x0_zero) {
-      CK(cudaMemcpyAsync(x, w.x64.p, nb, cudaMemcpyDeviceToDevice, s));
-    } else {
-      k_add64<<<n_items_all(m), 128, 0, s>>>(elem_args(m), w.x64.as<double>(), x);
-      CK(cudaGetLastError());
-      ++g_launches;
-    }
-    total_it = it;
-    applies += it;
-    sweeps = 1;
+    CK(cudaEventRecord(w.ev, s));
+    CK(cudaStreamWaitEvent(us, w.ev, 0));
+    CK(cudaStreamSynchronize(s));
+    rep->status = status;
+    return (hpse_status)status;
   } else if (o->refine_mode == 0) {
     if (o->zero_init) CK(cudaMemsetAsync(x, 0, nb, s));
-    st = solve_mixed_reliable(m, o, x, rep, deadline, &status);
+    const double delta = (o->inner_tol > 0 && o->inner_tol < 1) ? o->inner_tol : 1e-1;
+    st = solve_reliable<float>(m, o, x, rep, deadline, delta, &status);
     if (st != HPSE_OK) return st;
     CK(cudaEventRecord(w.ev, s));
     CK(cudaStreamWaitEvent(us, w.ev, 0));

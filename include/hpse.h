@@ -65,7 +65,8 @@ typedef enum {
   HPSE_ERR_TIMEOUT = 6,         /* wall-clock limit of the solve reached */
   HPSE_ERR_CUDA = 7,            /* a CUDA runtime call failed */
   HPSE_ERR_OOM = 8,             /* device allocation failed */
-  HPSE_ERR_NO_DATA = 9          /* hpse_set_data has not been called */
+  HPSE_ERR_NO_DATA = 9,         /* hpse_set_data has not been called */
+  HPSE_ERR_CAPACITY = 10        /* sizes beyond the fixed scratch of hpse_h1_error_noalloc */
 } hpse_status;
 
 typedef enum { HPSE_FP64 = 0, HPSE_FP32 = 1 } hpse_prec;
@@ -186,6 +187,25 @@ hpse_status hpse_pcg_solve(hpse_mesh *m, const hpse_solve_opts *opts, double *x,
  *   d/dx, d/dy, d/dz blocks per rhs).  out: host, 2*n_rhs doubles.  Synchronous. */
 hpse_status hpse_h1_error(hpse_mesh *m, const double *u, const double *ref,
                           const double *vq, const double *gq, double *out, void *stream);
+
+/* Allocation-free variant of hpse_h1_error (same arguments, same results up
+ * to the order of the final per-rhs sums).  The thesis has no counterpart: it
+ * exists for callers that cannot call cudaMalloc -- applications whose device
+ * memory is owned entirely by another allocator (a framework caching
+ * allocator, a fixed arena reserved at start-up) and latency-critical loops
+ * that must not incur the device-wide synchronisation of cudaFree.
+ * It allocates nothing: its scratch (per-(element, rhs) partial sums, per-rhs
+ * results, a table-pointer array) is one file-scope device array of about
+ * 2.1 MB that every GPU loading the library holds until process exit.
+ * Limits: n_elem * n_rhs <= 131072 and n_rhs <= 4096, else HPSE_ERR_CAPACITY
+ * before any device work.  The first call on a device looks up the array's
+ * device address on that device (make it before any stream capture).  Every
+ * call shares the one array and keeps the previous call's contents; all of it
+ * is overwritten before it is read, but calls that overlap on the GPU (other
+ * streams, other host threads on the same device) race and must be ordered by
+ * the caller.  Synchronous on `stream`; `out` is host memory. */
+hpse_status hpse_h1_error_noalloc(hpse_mesh *m, const double *u, const double *ref,
+                                  const double *vq, const double *gq, double *out, void *stream);
 
 /* Operator work counters for the loaded mesh: multiply-adds of one apply of A
  * per right-hand side, split into volume and face parts, as implemented. */

@@ -16,7 +16,7 @@ HPSE_OK = 0
 STATUS_NAMES = {
     0: "HPSE_OK", 1: "HPSE_ERR_INVALID_ARG", 2: "HPSE_ERR_NONMATCHING_FACE", 3: "HPSE_ERR_DEGREE",
     4: "HPSE_ERR_BREAKDOWN", 5: "HPSE_ERR_NO_CONVERGENCE", 6: "HPSE_ERR_TIMEOUT", 7: "HPSE_ERR_CUDA",
-    8: "HPSE_ERR_OOM", 9: "HPSE_ERR_NO_DATA",
+    8: "HPSE_ERR_OOM", 9: "HPSE_ERR_NO_DATA", 10: "HPSE_ERR_CAPACITY",
 }
 FP64, FP32 = 0, 1
 COEF_LAPLACE, COEF_SCALAR = 0, 1
@@ -66,6 +66,8 @@ SIGNATURES = {
                                  C.c_void_p]),
     "hpse_h1_error": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                 C.c_void_p]),
+    "hpse_h1_error_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_void_p]),
     "hpse_work_counts": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "hpse_set_block_threads": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     "hpse_get_block_threads": (C.c_int32, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]),

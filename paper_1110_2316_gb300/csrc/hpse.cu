@@ -16,6 +16,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <vector>
 
 #include "hpse.h"
@@ -795,6 +796,7 @@ extern "C" const char *hpse_status_string(hpse_status s) {
     case HPSE_ERR_CUDA: return g_last_err[0] ? g_last_err : "CUDA error";
     case HPSE_ERR_OOM: return "out of device memory";
     case HPSE_ERR_NO_DATA: return "no data: call hpse_set_data first";
+    case HPSE_ERR_CAPACITY: return "size exceeds the fixed scratch of an allocation-free entry point";
   }
   return "unknown status";
 }
@@ -1738,5 +1740,109 @@ extern "C" hpse_status hpse_h1_error(hpse_mesh *m, const double *u, const double
     out[2 * r] = a;
     out[2 * r + 1] = b;
   }
+  return HPSE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// H^1 norms without device allocation.
+//
+// Some callers cannot call cudaMalloc: applications whose device memory is
+// owned entirely by another allocator (a framework's caching allocator or a
+// fixed arena reserved at start-up), and latency-critical loops that must not
+// trigger the device-wide synchronisation cudaFree implies.  This variant of
+// hpse_h1_error keeps its scratch -- the per-(element, rhs) partial sums, the
+// per-rhs results and the table-pointer array -- in the file-scope array
+// below, which every GPU that loads this library holds until exit
+// (HPSE_NOALLOC_BYTES of it).  Host code reaches that array only through the
+// address cudaGetSymbolAddress returns for the current device (the array's
+// name in host code is a host-side stand-in, not a device address).
+// ---------------------------------------------------------------------------
+#define HPSE_NOALLOC_MAX_ITEMS (1 << 17)  // n_elem * n_rhs
+#define HPSE_NOALLOC_MAX_RHS 4096
+#define HPSE_NOALLOC_MAX_DEVICES 64
+#define HPSE_NOALLOC_DOUBLES (2 * HPSE_NOALLOC_MAX_ITEMS + 2 * HPSE_NOALLOC_MAX_RHS + 16)
+static __device__ __align__(256) double g_noalloc_scratch[HPSE_NOALLOC_DOUBLES];
+
+static double *g_noalloc_addr[HPSE_NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_mutex;
+
+// per-rhs deterministic sums of the k_h1 partials (one block per rhs)
+__global__ void k_h1_reduce_noalloc(int n_elem, int n_rhs, const double *part_err, const double *part_nrm,
+                                    double *out) {
+  const int r = blockIdx.x;
+  double a = 0.0, b = 0.0;
+  for (int e = threadIdx.x; e < n_elem; e += blockDim.x) {
+    a += part_err[(int64_t)e * n_rhs + r];
+    b += part_nrm[(int64_t)e * n_rhs + r];
+  }
+  a = block_sum_d(a);
+  b = block_sum_d(b);
+  if (threadIdx.x == 0) {
+    out[2 * r] = a;
+    out[2 * r + 1] = b;
+  }
+}
+
+extern "C" hpse_status hpse_h1_error_noalloc(hpse_mesh *m, const double *u, const double *ref, const double *vq,
+                                             const double *gq, double *out, void *stream) {
+  if (!m || !out) return HPSE_ERR_INVALID_ARG;
+  if (m->ndof == 0) {
+    for (int r = 0; r < m->n_rhs; ++r) out[2 * r] = out[2 * r + 1] = 0.0;
+    return HPSE_OK;
+  }
+  if (!u || (!ref && (!vq || !gq))) return HPSE_ERR_INVALID_ARG;
+  const int64_t ni = (int64_t)m->n_elem * m->n_rhs;
+  if (ni > HPSE_NOALLOC_MAX_ITEMS || m->n_rhs > HPSE_NOALLOC_MAX_RHS) return HPSE_ERR_CAPACITY;
+  if (m->device < 0 || m->device >= HPSE_NOALLOC_MAX_DEVICES) return HPSE_ERR_INVALID_ARG;
+  CK(cudaSetDevice(m->device));
+  // once per device, with that device current: the device address of the array
+  double *base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[m->device]) {
+      void *p = nullptr;
+      CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+      g_noalloc_addr[m->device] = static_cast<double *>(p);
+    }
+    base = g_noalloc_addr[m->device];
+  }
+  double *part_err = base;
+  double *part_nrm = base + HPSE_NOALLOC_MAX_ITEMS;
+  double *res = base + 2 * HPSE_NOALLOC_MAX_ITEMS;
+  const double **qtab = reinterpret_cast<const double **>(res + 2 * HPSE_NOALLOC_MAX_RHS);
+  cudaStream_t s = (cudaStream_t)stream;
+  const double *tp[HPSE_MAX_W + 1] = {nullptr};
+  int Wmax = 1;
+  for (auto &kv : m->d_qtab) {
+    tp[kv.first] = kv.second.as<double>();
+    Wmax = std::max(Wmax, kv.first);
+  }
+  CK(cudaMemcpyAsync(qtab, tp, sizeof(tp), cudaMemcpyHostToDevice, s));
+  H1Args A;
+  A.n_rhs = m->n_rhs;
+  A.ndof = m->ndof;
+  A.nquad = m->nquad;
+  A.dof_off = m->d_dof_off.as<int64_t>();
+  A.coef_off = m->d_coef_off.as<int64_t>();
+  A.elem_W = m->d_elem_W.as<int32_t>();
+  A.geo = m->d_geo64.as<double>();
+  A.qtab = qtab;
+  A.u = u;
+  A.ref = ref;
+  A.vq = vq;
+  A.gq = gq;
+  A.part_err = part_err;
+  A.part_nrm = part_nrm;
+  const int P = Wmax + 1, Q = 2 * Wmax + 1;
+  const size_t smem = (size_t)(P * P * P + 2 * Q * P * P + 3 * Q * Q * P) * sizeof(double);
+  CK(cudaFuncSetAttribute(k_h1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // every partial and every result is overwritten: nothing needs clearing
+  k_h1<<<(int)ni, 256, smem, s>>>(A);
+  CK(cudaGetLastError());
+  k_h1_reduce_noalloc<<<m->n_rhs, 256, 0, s>>>(m->n_elem, m->n_rhs, part_err, part_nrm, res);
+  CK(cudaGetLastError());
+  g_launches += 2;
+  CK(cudaMemcpyAsync(out, res, (size_t)2 * m->n_rhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
   return HPSE_OK;
 }

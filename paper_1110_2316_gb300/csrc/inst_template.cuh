@@ -34,11 +34,12 @@ int apply_max_threads_fn(int) { return NT; }
 
 cudaError_t precond_fn(int mode, const void *args, int n_items, int threads, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
-  if (threads <= 0 || threads > 256) return cudaErrorInvalidValue;
+  (void)threads;  // CTA shape fixed at compile time: PC_ITEMS items of PC_TPI threads
+  const int grid = (n_items + PC_ITEMS - 1) / PC_ITEMS;
   if (mode == MODE_PLAIN)
-    k_precond<MODE_PLAIN><<<n_items, threads, 0, s>>>(*static_cast<const PrecArgs *>(args));
+    k_precond<MODE_PLAIN><<<grid, PC_NT, PC_BYTES, s>>>(*static_cast<const PrecArgs *>(args));
   else if (mode == MODE_PCG)
-    k_precond<MODE_PCG><<<n_items, threads, 0, s>>>(*static_cast<const PrecArgs *>(args));
+    k_precond<MODE_PCG><<<grid, PC_NT, PC_BYTES, s>>>(*static_cast<const PrecArgs *>(args));
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
@@ -77,6 +78,12 @@ cudaError_t upload_fn(const double *pk) {
   if ((e2 = set_smem_attr<COEF_SCALAR, MODE_PLAIN>()) != cudaSuccess) return e2;
   if ((e2 = set_smem_attr<COEF_SCALAR, MODE_PCG>()) != cudaSuccess) return e2;
   if ((e2 = set_smem_attr<COEF_SCALAR, MODE_TRANSPOSE>()) != cudaSuccess) return e2;
+  if ((e2 = cudaFuncSetAttribute(k_precond<MODE_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)PC_BYTES)) != cudaSuccess)
+    return e2;
+  if ((e2 = cudaFuncSetAttribute(k_precond<MODE_PCG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)PC_BYTES)) != cudaSuccess)
+    return e2;
   return cudaSuccess;
 }
 

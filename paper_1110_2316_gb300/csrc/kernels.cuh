@@ -613,14 +613,24 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
 // MODE_PCG also performs the PCG update x += alpha p, r -= alpha q first and
 // writes the partial sums r.r and r.z.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void tensor_stage(const real *in, real *out, int axis, bool transpose) {
-  // out = (S^T or S) applied along `axis` of a P x P x P block (x fastest)
+// Preconditioner CTAs hold several (element, rhs) items; each item owns
+// PC_TPI threads (one per line of P nodes, whole warps).
+constexpr int PC_TPI = PAD32(P2);
+constexpr int PC_ITEMS_RAW = 384 / PC_TPI;
+constexpr int PC_ITEMS = PC_ITEMS_RAW < 1 ? 1 : (PC_ITEMS_RAW > 8 ? 8 : PC_ITEMS_RAW);
+constexpr int PC_NT = PC_ITEMS * PC_TPI;
+constexpr int PC_WARPS_PER_ITEM = PC_TPI / 32;
+constexpr size_t PC_BYTES = (size_t)PC_ITEMS * 2 * P3 * sizeof(real) + (size_t)(PC_NT / 32) * 2 * sizeof(double);
+
+// out = (S^T or S) applied along `axis` of one P x P x P block (x fastest);
+// thread lt of the item handles line lt (no loop: PC_TPI >= P^2 lines)
+__device__ __forceinline__ void tensor_stage(const real *in, real *out, int axis, bool transpose, int lt) {
   const int stride = axis == 0 ? 1 : (axis == 1 ? P : P2);
-  for (int l = threadIdx.x; l < P2; l += blockDim.x) {
+  if (lt < P2) {
     int b;
-    if (axis == 0) b = l * P;
-    else if (axis == 1) b = (l / P) * P2 + (l % P);
-    else b = l;
+    if (axis == 0) b = lt * P;
+    else if (axis == 1) b = (lt / P) * P2 + (lt % P);
+    else b = lt;
     real v[P];
 #pragma unroll
     for (int k = 0; k < P; ++k) v[k] = in[b + k * stride];
@@ -635,55 +645,90 @@ __device__ __forceinline__ void tensor_stage(const real *in, real *out, int axis
   __syncthreads();
 }
 
+// per-thread sum of products: FP64 for double, compensated (Kahan) FP32 for float
+struct DotAcc {
+  real s = 0, c = 0;
+  __device__ __forceinline__ void add(real a, real b) {
+#if defined(HPSE_DOUBLE)
+    s += a * b;
+#else
+    const real y = a * b - c;
+    const real t = s + y;
+    c = (t - s) - y;
+    s = t;
+#endif
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// sum of one item's warps (valid in lane 0 of the item's first warp)
+__device__ __forceinline__ double item_sum(double v, double *red, int warp_in_cta, int first_warp_of_item) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[warp_in_cta] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp_in_cta == first_warp_of_item && (threadIdx.x & 31) == 0)
+    for (int w = 0; w < PC_WARPS_PER_ITEM; ++w) t += red[first_warp_of_item + w];
+  __syncthreads();
+  return t;
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(256) k_precond(const PrecArgs A) {
-  __shared__ __align__(16) real s0[P3];
-  __shared__ __align__(16) real s1[P3];
+__global__ void __launch_bounds__(PC_NT) k_precond(const PrecArgs A) {
+  extern __shared__ __align__(16) unsigned char pc_raw[];
+  const int sub = threadIdx.x / PC_TPI;  // item within the CTA (warp-uniform)
+  const int lt = threadIdx.x - sub * PC_TPI;
+  real *s0 = reinterpret_cast<real *>(pc_raw) + (size_t)sub * 2 * P3;
+  real *s1 = s0 + P3;
+  double *red = reinterpret_cast<double *>(pc_raw + (size_t)PC_ITEMS * 2 * P3 * sizeof(real));
   __shared__ real smu[P];
-  __shared__ double red[32];
-  const int item = blockIdx.x;
-  const int ge = item / A.n_rhs;
-  const int rr = item - ge * A.n_rhs;
+  const int item = blockIdx.x * PC_ITEMS + sub;
+  const bool valid = item < A.n_group * A.n_rhs;
+  const int ge = valid ? item / A.n_rhs : 0;
+  const int rr = valid ? item - ge * A.n_rhs : 0;
   const int e = A.elems[ge];
   const int64_t base = (int64_t)rr * A.ndof + A.dof_off[e];
-  const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid < P) smu[tid] = c_tab.MU[tid];
-  double prr = 0.0;
-  if (MODE == MODE_PCG) {
-    const real al = (real)A.alpha[A.prob[e] * A.n_rhs + rr];
-    for (int t = tid; t < P3; t += nt) {
-      const real pv = A.p[base + t];
-      if (A.x) A.x[base + t] += al * pv;
-      const real rv = A.r[base + t] - al * A.q[base + t];
-      A.r[base + t] = rv;
-      s0[t] = rv;
-      prr += (double)rv * (double)rv;
+  if (threadIdx.x < P) smu[threadIdx.x] = c_tab.MU[threadIdx.x];
+  DotAcc arr, arz;
+  if (valid) {
+    if (MODE == MODE_PCG) {
+      const real al = (real)A.alpha[A.prob[e] * A.n_rhs + rr];
+      for (int t = lt; t < P3; t += PC_TPI) {
+        const real pv = A.p[base + t];
+        if (A.x) A.x[base + t] += al * pv;
+        const real rv = A.r[base + t] - al * A.q[base + t];
+        A.r[base + t] = rv;
+        s0[t] = rv;
+        arr.add(rv, rv);
+      }
+    } else {
+      for (int t = lt; t < P3; t += PC_TPI) s0[t] = A.rin[base + t];
     }
-  } else {
-    for (int t = tid; t < P3; t += nt) s0[t] = A.rin[base + t];
   }
   __syncthreads();
-  tensor_stage(s0, s1, 0, true);
-  tensor_stage(s1, s0, 1, true);
-  tensor_stage(s0, s1, 2, true);
-  for (int t = tid; t < P3; t += nt) {
+  tensor_stage(s0, s1, 0, true, lt);
+  tensor_stage(s1, s0, 1, true, lt);
+  tensor_stage(s0, s1, 2, true, lt);
+  for (int t = lt; t < P3; t += PC_TPI) {
     const int a = t % P, b = (t / P) % P, c = t / P2;
     s1[t] = s1[t] / (smu[a] + smu[b] + smu[c] + (real)1);
   }
   __syncthreads();
-  tensor_stage(s1, s0, 2, false);
-  tensor_stage(s0, s1, 1, false);
-  tensor_stage(s1, s0, 0, false);
-  double prz = 0.0;
-  for (int t = tid; t < P3; t += nt) {
-    const real zv = s0[t];
-    A.zout[base + t] = zv;
-    if (MODE == MODE_PCG) prz += (double)zv * (double)A.r[base + t];
+  tensor_stage(s1, s0, 2, false, lt);
+  tensor_stage(s0, s1, 1, false, lt);
+  tensor_stage(s1, s0, 0, false, lt);
+  if (valid) {
+    for (int t = lt; t < P3; t += PC_TPI) {
+      const real zv = s0[t];
+      A.zout[base + t] = zv;
+      if (MODE == MODE_PCG) arz.add(zv, A.r[base + t]);
+    }
   }
   if (MODE == MODE_PCG) {
-    const double a = block_sum(prr, red);
-    const double b = block_sum(prz, red);
-    if (tid == 0) {
+    const int w = threadIdx.x >> 5, w0 = sub * PC_WARPS_PER_ITEM;
+    const double a = item_sum(arr.value(), red, w, w0);
+    const double b = item_sum(arz.value(), red, w, w0);
+    if (valid && lt == 0) {
       A.part_rr[(int64_t)e * A.n_rhs + rr] = a;
       A.part_rz[(int64_t)e * A.n_rhs + rr] = b;
     }

@@ -67,10 +67,6 @@ cudaError_t upload_fn(const double *pk) {
   for (int i = 0; i < P2; ++i) t.S[i] = (real)pk[o++];
   for (int i = 0; i < P2; ++i) t.MP[i] = (real)pk[o++];
   for (int i = 0; i < P2; ++i) t.KP[i] = (real)pk[o++];
-  {
-    const double *mp = pk + 3 * QP + 2 * P2, *kp = pk + 3 * QP + 3 * P2;  // packed order, see registry.h
-    for (int i = 0; i < P2; ++i) t.MK[i] = (real)(mp[i] + kp[i]);
-  }
   for (int i = 0; i < Q; ++i) t.WQ[i] = (real)pk[o++];
   for (int i = 0; i < P; ++i) t.MU[i] = (real)pk[o++];
   cudaError_t err = cudaMemcpyToSymbol(c_tab, &t, sizeof(Tables));

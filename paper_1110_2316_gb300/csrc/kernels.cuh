@@ -78,7 +78,6 @@ struct Tables {
   real S[P2];
   real MP[P2];
   real KP[P2];
-  real MK[P2];  // MP + KP
   real WQ[Q];
   real MU[P];
 };
@@ -118,24 +117,19 @@ __device__ __forceinline__ double block_sum(T v, double *red) {
 
 // ---------------------------------------------------------------------------
 // Face phase: y_e += contributions of the six faces of element e (eq. 4.2),
-// all six faces at once, then gathered node by node (no two threads add into
-// the same node: deterministic, no atomics).
+// all six faces processed at once, then gathered node by node (no two
+// threads ever add into the same node: deterministic, no atomics).
 //
-// Per face f (axis a, tangential axes t1 < t2, nodal face grid [p2][p1]):
-//   interior:  J0 = [u], J1 = [u_{x_t1}], J2 = [u_{x_t2}], J3 = [u_{x_a}]
-//              g0 = (MP x MP) J0, gk = (MP x MP + MP x KP + KP x MP) Jk
-//   Dirichlet: J0 = u, J1 = du/dlambda_t1, J2 = du/dlambda_t2 (eq. 2.18), J3 = 0
-// MP = B0^T W B0 and KP = B0^T K B0 are the face forms of Section 5.3 on the
-// (2W+1)-point grid pulled back to the nodal grid (exact algebra).  Every
-// contraction runs along a line of P values held by one thread, so the P x P
-// matrices are immediate constant-bank operands.
-// Scratch per face: FACE_ARR arrays of P x P.
+// Per face f (axis a, side s, tangential axes t1 < t2, nodal face grid P x P):
+//   own traces  F = u|face, N = du/dlambda_a|face, G1/G2 = tangential derivatives
+//   interior:   J0 = [u], J1 = [u_{x_t1}], J2 = [u_{x_t2}], J3 = [u_{x_a}]
+//               g0 = (MP x MP) J0, gk = (MP x MP + MP x KP + KP x MP) Jk
+//   Dirichlet:  J0 = u, J1 = du/dlambda_t1, J2 = du/dlambda_t2 (eq. 2.18)
+// MP = B0^T W B0 and KP = B0^T K B0 are the Section 5.3 face forms on the
+// (2W+1)-point grid pulled back to the nodal grid (exact algebra).
+// Scratch per face: 15 arrays of P x P.
 // ---------------------------------------------------------------------------
-constexpr int FACE_ARR = 13;
-constexpr int FACE_LINES = PAD32(6 * P);  // line items per direction / quantity group (whole warps)
-// quantity groups of the two Kronecker passes: 4 (one quantity per thread) when
-// they fit in one pass over the CTA, else 2 (two quantities per thread)
-constexpr int FACE_G = (4 * FACE_LINES <= NT) ? 4 : 2;
+constexpr int FACE_ARR = 15;
 
 template <int MODE>
 __device__ __forceinline__ real nb_value(const ApplyArgs &A, int64_t idx, real bt) {
@@ -143,177 +137,134 @@ __device__ __forceinline__ real nb_value(const ApplyArgs &A, int64_t idx, real b
   return A.u[idx];
 }
 
-// out[i] = sum_m M[i][m] v[m] (TR = 0) or sum_m M[m][i] v[m] (TR = 1), M a constant table
-#define FACE_MATVEC(out, Mtab, v, TR)                                        \
-  _Pragma("unroll") for (int i_ = 0; i_ < P; ++i_) {                        \
-    real s_ = 0;                                                            \
-    _Pragma("unroll") for (int m_ = 0; m_ < P; ++m_) s_ +=                  \
-        (TR ? c_tab.Mtab[m_ * P + i_] : c_tab.Mtab[i_ * P + m_]) * (v)[m_]; \
-    (out)[i_] = s_;                                                         \
-  }
-
 template <int MODE>
-__device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, real *sy, real *scr,
-                           const real *geo_e) {
-  const int tid = threadIdx.x;
-  constexpr int nt = NT;
+__device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, real *sy, real *scr, const real *Ds,
+                           const real *MPs, const real *KPs, const real *geo_e) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // slot s of face f: scr + (f * FACE_ARR + s) * P2
 #define FSLOT(f, s) (scr + ((f)*FACE_ARR + (s)) * P2)
-  enum { sF = 0, sFn, sJ0, sJ1, sJ2, sJ3, sT0, sA1, sA2, sA3, sB1, sB2, sB3 };
-  // F1 (points): own / neighbour traces; J0 and J3 point-wise; F and Fn kept
+  enum { sF = 0, sN, sFn, sNn, sJ0, sJ1, sJ2, sJ3, sT0, sA1, sA2, sA3, sB1, sB2, sB3 };
+  // F1: traces of u and of the neighbour on every face point
   for (int t = tid; t < 6 * P2; t += nt) {
     const int f = t / P2, sp = t - f * P2;
     const int p1 = sp % P, p2 = sp / P;
-    const int a = f >> 1, side = f & 1;
-    const int nend = side ? P - 1 : 0;
-    const real Fo = su[fidx(a, nend, p1, p2)];
-    real No = 0;
-    if (side) {
+    const int a = f >> 1, nend = (f & 1) ? P - 1 : 0;
+    FSLOT(f, sF)[sp] = su[fidx(a, nend, p1, p2)];
+    real s = 0;
 #pragma unroll
-      for (int k = 0; k < P; ++k) No += c_tab.D[(P - 1) * P + k] * su[fidx(a, k, p1, p2)];
-    } else {
-#pragma unroll
-      for (int k = 0; k < P; ++k) No += c_tab.D[k] * su[fidx(a, k, p1, p2)];
-    }
-    FSLOT(f, sF)[sp] = Fo;
+    for (int k = 0; k < P; ++k) s += Ds[nend * P + k] * su[fidx(a, k, p1, p2)];
+    FSLOT(f, sN)[sp] = s;
     const int nb = A.nbr[(int64_t)e * 6 + f];
     if (nb >= 0) {
       const int64_t base = (int64_t)r * A.ndof + A.dof_off[nb];
       const real bt = (MODE == MODE_PCG) ? (real)A.beta[A.prob[nb] * A.n_rhs + r] : (real)0;
-      const real *gn = A.geo + (int64_t)nb * 4;
-      real Fn, Nn = 0;
-      if (side) {  // neighbour's low face (its node 0)
-        Fn = nb_value<MODE>(A, base + fidx(a, 0, p1, p2), bt);
+      const int nn = P - 1 - nend;
+      FSLOT(f, sFn)[sp] = nb_value<MODE>(A, base + fidx(a, nn, p1, p2), bt);
+      real sn = 0;
 #pragma unroll
-        for (int k = 0; k < P; ++k) Nn += c_tab.D[k] * nb_value<MODE>(A, base + fidx(a, k, p1, p2), bt);
-      } else {
-        Fn = nb_value<MODE>(A, base + fidx(a, P - 1, p1, p2), bt);
+      for (int k = 0; k < P; ++k) sn += Ds[nn * P + k] * nb_value<MODE>(A, base + fidx(a, k, p1, p2), bt);
+      FSLOT(f, sNn)[sp] = sn;
+    }
+  }
+  __syncthreads();
+  // F2: tangential derivatives and jumps
+  for (int t = tid; t < 6 * P2; t += nt) {
+    const int f = t / P2, sp = t - f * P2;
+    const int p1 = sp % P, p2 = sp / P;
+    const int a = f >> 1;
+    const int t1 = (a == 0) ? 1 : 0, t2 = (a == 2) ? 1 : 2;
+    const real *F = FSLOT(f, sF);
+    real g1 = 0, g2 = 0;
 #pragma unroll
-        for (int k = 0; k < P; ++k)
-          Nn += c_tab.D[(P - 1) * P + k] * nb_value<MODE>(A, base + fidx(a, k, p1, p2), bt);
+    for (int m = 0; m < P; ++m) {
+      g1 += Ds[p1 * P + m] * F[p2 * P + m];
+      g2 += Ds[p2 * P + m] * F[m * P + p1];
+    }
+    const int nb = A.nbr[(int64_t)e * 6 + f];
+    if (nb >= 0) {
+      const real *Fn = FSLOT(f, sFn);
+      real h1 = 0, h2 = 0;
+#pragma unroll
+      for (int m = 0; m < P; ++m) {
+        h1 += Ds[p1 * P + m] * Fn[p2 * P + m];
+        h2 += Ds[p2 * P + m] * Fn[m * P + p1];
       }
-      FSLOT(f, sFn)[sp] = Fn;
-      FSLOT(f, sJ0)[sp] = Fo - Fn;
-      FSLOT(f, sJ3)[sp] = geo_e[a] * No - gn[a] * Nn;
+      const real *gn = A.geo + (int64_t)nb * 4;
+      FSLOT(f, sJ0)[sp] = F[sp] - Fn[sp];
+      FSLOT(f, sJ1)[sp] = geo_e[t1] * g1 - gn[t1] * h1;
+      FSLOT(f, sJ2)[sp] = geo_e[t2] * g2 - gn[t2] * h2;
+      FSLOT(f, sJ3)[sp] = geo_e[a] * FSLOT(f, sN)[sp] - gn[a] * FSLOT(f, sNn)[sp];
     } else {
-      FSLOT(f, sFn)[sp] = 0;
-      FSLOT(f, sJ0)[sp] = Fo;
+      FSLOT(f, sJ0)[sp] = F[sp];
+      FSLOT(f, sJ1)[sp] = g1;
+      FSLOT(f, sJ2)[sp] = g2;
       FSLOT(f, sJ3)[sp] = 0;
     }
   }
   __syncthreads();
-  // F2 (lines): J1 = tangential derivative along p1 (rows), J2 along p2 (columns)
-  for (int t = tid; t < 2 * FACE_LINES; t += nt) {
-    const int dir = t / FACE_LINES, li = t - dir * FACE_LINES;
-    if (li < 6 * P) {
-      const int f = li / P, ln = li - f * P;
-      const int a = f >> 1;
-      const int ta = dir == 0 ? ((a == 0) ? 1 : 0) : ((a == 2) ? 1 : 2);
-      const int nb = A.nbr[(int64_t)e * 6 + f];
-      const int off = dir == 0 ? ln * P : ln, st = dir == 0 ? 1 : P;
-      real v[P], vn[P], g[P], gn[P];
+  // F3: first Kronecker factor (along p1)
+  for (int t = tid; t < 6 * P2; t += nt) {
+    const int f = t / P2, sp = t - f * P2;
+    const int p1 = sp % P, p2 = sp / P;
+    const real *J0 = FSLOT(f, sJ0), *J1 = FSLOT(f, sJ1), *J2 = FSLOT(f, sJ2), *J3 = FSLOT(f, sJ3);
+    real t0 = 0, a1 = 0, a2 = 0, a3 = 0, b1 = 0, b2 = 0, b3 = 0;
 #pragma unroll
-      for (int m = 0; m < P; ++m) {
-        v[m] = FSLOT(f, sF)[off + m * st];
-        vn[m] = FSLOT(f, sFn)[off + m * st];
-      }
-      FACE_MATVEC(g, D, v, 0);
-      FACE_MATVEC(gn, D, vn, 0);
-      const real cs = nb >= 0 ? geo_e[ta] : (real)1;
-      const real cn = nb >= 0 ? A.geo[(int64_t)nb * 4 + ta] : (real)0;
-      real *J = FSLOT(f, dir == 0 ? sJ1 : sJ2);
-#pragma unroll
-      for (int m = 0; m < P; ++m) J[off + m * st] = cs * g[m] - cn * gn[m];
+    for (int m = 0; m < P; ++m) {
+      const real mp = MPs[p1 * P + m], kp = KPs[p1 * P + m];
+      t0 += mp * J0[p2 * P + m];
+      a1 += mp * J1[p2 * P + m];
+      b1 += kp * J1[p2 * P + m];
+      a2 += mp * J2[p2 * P + m];
+      b2 += kp * J2[p2 * P + m];
+      a3 += mp * J3[p2 * P + m];
+      b3 += kp * J3[p2 * P + m];
     }
+    FSLOT(f, sT0)[sp] = t0;
+    FSLOT(f, sA1)[sp] = a1;
+    FSLOT(f, sA2)[sp] = a2;
+    FSLOT(f, sA3)[sp] = a3;
+    FSLOT(f, sB1)[sp] = a1 + b1;
+    FSLOT(f, sB2)[sp] = a2 + b2;
+    FSLOT(f, sB3)[sp] = a3 + b3;
   }
   __syncthreads();
-  // F3 (rows, along p1): T0 = MP J0; A_k = MP J_k, B_k = (MP + KP) J_k
-  for (int t = tid; t < FACE_G * FACE_LINES; t += nt) {
-    const int grp = t / FACE_LINES, li = t - grp * FACE_LINES;
-#pragma unroll 1
-    for (int kk = 0; kk < 4 / FACE_G; ++kk) {
-      const int k = grp * (4 / FACE_G) + kk;
-      if (li >= 6 * P) break;
-      const int f = li / P, ln = li - f * P;
-      real v[P], o1[P], o2[P];
-      const real *src = FSLOT(f, sJ0 + k) + ln * P;
+  // F4: second factor (along p2): g0 -> J0 slot, g1..g3 -> J1..J3 slots
+  for (int t = tid; t < 6 * P2; t += nt) {
+    const int f = t / P2, sp = t - f * P2;
+    const int p1 = sp % P, p2 = sp / P;
+    real g0 = 0, g1 = 0, g2 = 0, g3 = 0;
 #pragma unroll
-      for (int m = 0; m < P; ++m) v[m] = src[m];
-      FACE_MATVEC(o1, MP, v, 0);
-      if (k == 0) {
-#pragma unroll
-        for (int m = 0; m < P; ++m) FSLOT(f, sT0)[ln * P + m] = o1[m];
-      } else {
-        FACE_MATVEC(o2, MK, v, 0);
-#pragma unroll
-        for (int m = 0; m < P; ++m) {
-          FSLOT(f, sA1 + k - 1)[ln * P + m] = o1[m];
-          FSLOT(f, sB1 + k - 1)[ln * P + m] = o2[m];
-        }
-      }
+    for (int m = 0; m < P; ++m) {
+      const real mp = MPs[p2 * P + m], kp = KPs[p2 * P + m];
+      const int o = m * P + p1;
+      g0 += mp * FSLOT(f, sT0)[o];
+      g1 += mp * FSLOT(f, sB1)[o] + kp * FSLOT(f, sA1)[o];
+      g2 += mp * FSLOT(f, sB2)[o] + kp * FSLOT(f, sA2)[o];
+      g3 += mp * FSLOT(f, sB3)[o] + kp * FSLOT(f, sA3)[o];
     }
+    FSLOT(f, sJ0)[sp] = g0;
+    FSLOT(f, sJ1)[sp] = g1;
+    FSLOT(f, sJ2)[sp] = g2;
+    FSLOT(f, sJ3)[sp] = g3;
   }
   __syncthreads();
-  // F4 (columns, along p2): g0 = MP T0 -> J0 slot; g1 = MP B1 + KP A1 -> J1 slot;
-  // g2 = MP B2 + KP A2, then u2 = c2 D^T g2 along p2 -> J2 slot; Gn = ca g3 -> J3 slot
-  for (int t = tid; t < FACE_G * FACE_LINES; t += nt) {
-    const int grp = t / FACE_LINES, li = t - grp * FACE_LINES;
-#pragma unroll 1
-    for (int kk = 0; kk < 4 / FACE_G; ++kk) {
-      const int k = grp * (4 / FACE_G) + kk;
-      if (li >= 6 * P) break;
-      const int f = li / P, ln = li - f * P;  // ln = p1 (column)
-      const int a = f >> 1;
-      const bool interior = A.nbr[(int64_t)e * 6 + f] >= 0;
-      real v[P], w[P], g[P], h[P];
-      if (k == 0) {
+  // F5: transposed traces on the face grid: C (face layer) -> F slot, Gn (normal) -> N slot
+  for (int t = tid; t < 6 * P2; t += nt) {
+    const int f = t / P2, sp = t - f * P2;
+    const int p1 = sp % P, p2 = sp / P;
+    const int a = f >> 1;
+    const int t1 = (a == 0) ? 1 : 0, t2 = (a == 2) ? 1 : 2;
+    const bool interior = A.nbr[(int64_t)e * 6 + f] >= 0;
+    const real *g1 = FSLOT(f, sJ1), *g2 = FSLOT(f, sJ2);
+    real u1 = 0, u2 = 0;
 #pragma unroll
-        for (int m = 0; m < P; ++m) v[m] = FSLOT(f, sT0)[m * P + ln];
-        FACE_MATVEC(g, MP, v, 0);
-#pragma unroll
-        for (int m = 0; m < P; ++m) FSLOT(f, sJ0)[m * P + ln] = g[m];
-      } else {
-#pragma unroll
-        for (int m = 0; m < P; ++m) {
-          v[m] = FSLOT(f, sB1 + k - 1)[m * P + ln];
-          w[m] = FSLOT(f, sA1 + k - 1)[m * P + ln];
-        }
-        FACE_MATVEC(g, MP, v, 0);
-        FACE_MATVEC(h, KP, w, 0);
-#pragma unroll
-        for (int m = 0; m < P; ++m) g[m] += h[m];
-        if (k == 1) {
-#pragma unroll
-          for (int m = 0; m < P; ++m) FSLOT(f, sJ1)[m * P + ln] = g[m];
-        } else if (k == 2) {
-          const int t2 = (a == 2) ? 1 : 2;
-          const real c2 = interior ? geo_e[t2] : (real)1;
-          FACE_MATVEC(h, D, g, 1);
-#pragma unroll
-          for (int m = 0; m < P; ++m) FSLOT(f, sJ2)[m * P + ln] = c2 * h[m];
-        } else {
-          const real ca = interior ? geo_e[a] : (real)0;
-#pragma unroll
-          for (int m = 0; m < P; ++m) FSLOT(f, sJ3)[m * P + ln] = ca * g[m];
-        }
-      }
+    for (int m = 0; m < P; ++m) {
+      u1 += Ds[m * P + p1] * g1[p2 * P + m];
+      u2 += Ds[m * P + p2] * g2[m * P + p1];
     }
-  }
-  __syncthreads();
-  // F5 (rows): C = g0 + c1 D^T g1 (along p1) + u2 -> F slot
-  for (int t = tid; t < FACE_LINES; t += nt) {
-    if (t < 6 * P) {
-      const int f = t / P, ln = t - f * P;  // ln = p2 (row)
-      const int a = f >> 1;
-      const int t1 = (a == 0) ? 1 : 0;
-      const real c1 = A.nbr[(int64_t)e * 6 + f] >= 0 ? geo_e[t1] : (real)1;
-      real v[P], h[P];
-#pragma unroll
-      for (int m = 0; m < P; ++m) v[m] = FSLOT(f, sJ1)[ln * P + m];
-      FACE_MATVEC(h, D, v, 1);
-#pragma unroll
-      for (int m = 0; m < P; ++m)
-        FSLOT(f, sF)[ln * P + m] = FSLOT(f, sJ0)[ln * P + m] + c1 * h[m] + FSLOT(f, sJ2)[ln * P + m];
-    }
+    const real c1 = interior ? geo_e[t1] : (real)1, c2 = interior ? geo_e[t2] : (real)1;
+    FSLOT(f, sF)[sp] = FSLOT(f, sJ0)[sp] + c1 * u1 + c2 * u2;
+    FSLOT(f, sN)[sp] = interior ? geo_e[a] * FSLOT(f, sJ3)[sp] : (real)0;
   }
   __syncthreads();
   // F6: gather onto the nodes of the element
@@ -322,19 +273,13 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
     real acc = 0;
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
-      const int a = f >> 1;
+      const int a = f >> 1, nend = (f & 1) ? P - 1 : 0;
       const int n = a == 0 ? i : (a == 1 ? j : k);
       const int p1 = a == 0 ? j : i;
       const int p2 = a == 2 ? j : k;
       const int sp = p2 * P + p1;
-      const real gn = FSLOT(f, sJ3)[sp];
-      if (f & 1) {
-        acc += c_tab.D[(P - 1) * P + n] * gn;
-        if (n == P - 1) acc += FSLOT(f, sF)[sp];
-      } else {
-        acc += c_tab.D[n] * gn;
-        if (n == 0) acc += FSLOT(f, sF)[sp];
-      }
+      acc += Ds[nend * P + n] * FSLOT(f, sN)[sp];
+      if (n == nend) acc += FSLOT(f, sF)[sp];
     }
     sy[t] += acc;
   }
@@ -523,7 +468,7 @@ struct ApplyLayout {
   static constexpr int T_REGION0 = NTF * Q2P;
   static constexpr int T_NEED = P3 + 6 * FACE_ARR * P2;
   static constexpr int T_REGION = T_REGION0 > T_NEED ? T_REGION0 : T_NEED;
-  static constexpr int TABS = 0;
+  static constexpr int TABS = 3 * P2;
   static constexpr int TOTAL = P3 + NX * QP2 + T_REGION + TABS;
   // the FP64 reduction buffer starts on a 16-byte boundary whatever REAL is
   static constexpr size_t RED_OFF = (((size_t)TOTAL * sizeof(real) + 15) / 16) * 16;
@@ -537,6 +482,7 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
   real *su = reinterpret_cast<real *>(smem_raw);
   real *sX = su + P3;               // X0 | X2 | (X1)
   real *sT = sX + L::NX * QP2;      // T00 | TL | (T10 | T01)
+  real *stab = sT + L::T_REGION;    // D | MP | KP (runtime-indexed copies for the face phase)
   double *red = reinterpret_cast<double *>(smem_raw + L::RED_OFF);
   static_assert(L::RED_OFF % 16 == 0, "reduction buffer must be 16-byte aligned");
   real *X0 = sX, *X2 = sX + QP2, *X1 = sX + 2 * QP2;
@@ -553,6 +499,11 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
   const int tid = threadIdx.x;
   constexpr int nt = NT;
 
+  for (int t = tid; t < P2; t += nt) {
+    stab[t] = c_tab.D[t];
+    stab[P2 + t] = c_tab.MP[t];
+    stab[2 * P2 + t] = c_tab.KP[t];
+  }
   if (MODE != MODE_TRANSPOSE) {
     if (MODE == MODE_PCG) {
       const double bt = A.beta[A.prob[e] * A.n_rhs + r];
@@ -731,7 +682,7 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
 
   // ---- faces ---------------------------------------------------------------
   if (MODE != MODE_TRANSPOSE && !A.skip_faces)
-    face_phase<MODE>(A, e, r, su, sy, sT + P3, geo_e);
+    face_phase<MODE>(A, e, r, su, sy, sT + P3, stab, stab + P2, stab + 2 * P2, geo_e);
 
   // ---- store (and the p.q partial of PCG) --------------------------------
   double part = 0.0;

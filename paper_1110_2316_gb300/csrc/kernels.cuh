@@ -60,9 +60,9 @@ typedef REAL real;
 constexpr int NT_RAW = PAD32(Q2);
 constexpr int NT = NT_RAW < 64 ? 64 : (NT_RAW > HPSE_APPLY_MAXT ? HPSE_APPLY_MAXT : NT_RAW);
 static_assert(NT % 32 == 0, "warp-uniform line loops need a whole number of warps per CTA");
-// FP32: enough resident CTAs for ~20 warps per SM; FP64 is bound by the
-// FP64 pipe at any occupancy
-constexpr int APPLY_MINB_RAW = 640 / NT;
+// FP32: enough resident CTAs for ~30 warps per SM (measured best on GB300 for
+// W = 8: 3 CTAs of 320 threads); FP64 is bound by the FP64 pipe at any occupancy
+constexpr int APPLY_MINB_RAW = 960 / NT;
 constexpr int APPLY_MINB = sizeof(real) == 8 ? 1 : (APPLY_MINB_RAW < 1 ? 1 : (APPLY_MINB_RAW > 4 ? 4 : APPLY_MINB_RAW));
 
 
@@ -316,7 +316,7 @@ template <int L>
 struct Lines {
   static constexpr int PADL = PAD32(L);
   static constexpr int NC_RAW = NT / PADL;
-  static constexpr int NC = NC_RAW < 1 ? 1 : (NC_RAW > 4 ? 4 : NC_RAW);
+  static constexpr int NC = NC_RAW < 1 ? 1 : (NC_RAW > 2 ? 2 : NC_RAW);
 };
 template <int CI, int NC, int N>
 struct Range {

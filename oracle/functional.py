@@ -178,6 +178,11 @@ class Discretisation:
         self.ndof = int(off[-1])
         self._coef_cache = {}
 
+    def part(self, e):
+        """The problem whose data element e uses (batches of independent problems)."""
+        parts = getattr(self.problem, "parts", None)
+        return parts[int(self.mesh.elem_problem[e])] if parts is not None else self.problem
+
     # --- geometry ---------------------------------------------------------
     def h(self, e):
         return self.mesh.elem_hi[e] - self.mesh.elem_lo[e]
@@ -208,13 +213,13 @@ class Discretisation:
             return self._coef_cache[e]
         Q = tables(self.W[e])["Q"]
         xs, ys, zs = self.qpoints(e)
-        pb = self.problem
+        pb = self.part(e)
         if pb.a is None:
             a = np.ones((Q, Q, Q))
             g = (np.zeros((Q, Q, Q)),) * 3
         else:
-            a = pb.a(xs, ys, zs)
-            g = pb.grad_a(xs, ys, zs)
+            a = np.broadcast_to(pb.a(xs, ys, zs), (Q, Q, Q))
+            g = tuple(np.broadcast_to(c, (Q, Q, Q)) for c in pb.grad_a(xs, ys, zs))
         self._coef_cache[e] = (a, g)
         return a, g
 
@@ -252,7 +257,7 @@ class Discretisation:
 
     def f_at(self, e, rhs):
         xs, ys, zs = self.qpoints(e)
-        return self.problem.f[rhs](xs, ys, zs)
+        return self.part(e).f[rhs](xs, ys, zs)
 
     # --- faces -----------------------------------------------------------
     @staticmethod
@@ -344,7 +349,7 @@ class Discretisation:
     def dirichlet_data(self, e, fi, Qf, rhs):
         """(g, dg/dlambda_t1, dg/dlambda_t2) on the face grid [t2, t1]."""
         xs, ys, zs = self.face_points(e, fi, Qf)
-        gv = self.problem.g[rhs](xs, ys, zs).reshape(Qf, Qf)
+        gv = self.part(e).g[rhs](xs, ys, zs).reshape(Qf, Qf)
         xf, _ = gll(Qf)
         D = diff_matrix(xf)
         return [gv, gv @ D.T, D @ gv]

@@ -174,6 +174,12 @@ def problem_data_arrays(mesh: Mesh, problem):
     Ws = [int(w) for w in mesh.elem_W]
     R = mesh.n_rhs
     nq = mesh.nquad
+    parts = getattr(problem, "parts", None)
+    eprob = mesh._keep[1]
+
+    def part(e):
+        return parts[int(eprob[e])] if parts is not None else problem
+
     f = np.zeros((R, nq))
     a = grad = None
     if problem.a is not None:
@@ -187,11 +193,12 @@ def problem_data_arrays(mesh: Mesh, problem):
         axes.append((xs, ys, zs))
         o += 3 * Q
         n = Q ** 3
+        pe = part(e)
         for r in range(R):
-            f[r, oq:oq + n] = problem.f[r](xs, ys, zs).ravel()
+            f[r, oq:oq + n] = np.broadcast_to(pe.f[r](xs, ys, zs), (Q, Q, Q)).ravel()
         if a is not None:
-            a[oq:oq + n] = problem.a(xs, ys, zs).ravel()
-            gx, gy, gz = problem.grad_a(xs, ys, zs)
+            a[oq:oq + n] = np.broadcast_to(pe.a(xs, ys, zs), (Q, Q, Q)).ravel()
+            gx, gy, gz = pe.grad_a(xs, ys, zs)
             grad[0, oq:oq + n] = np.broadcast_to(gx, (Q, Q, Q)).ravel()
             grad[1, oq:oq + n] = np.broadcast_to(gy, (Q, Q, Q)).ravel()
             grad[2, oq:oq + n] = np.broadcast_to(gz, (Q, Q, Q)).ravel()
@@ -212,7 +219,7 @@ def problem_data_arrays(mesh: Mesh, problem):
                 grid = list(axes[e])
                 grid[axis] = np.array([fnorm[k]])
                 for r in range(R):
-                    g[r, fo:fo + Q * Q] = problem.g[r](*grid).ravel()
+                    g[r, fo:fo + Q * Q] = part(e).g[r](*grid).ravel()
                 fo += Q * Q
                 k += 1
     return dict(f=f, a=a, grad_a=grad, g=g)

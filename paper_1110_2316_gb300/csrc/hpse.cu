@@ -200,6 +200,17 @@ struct hpse_mesh {
   std::map<int, DevBuf> d_qtab;  // per degree FP64 Q-grid tables for the face data
   bool has_data = false;
   int threads[2][2][HPSE_MAX_W + 1];  // [kind][prec][W]
+  // one stream per degree group: per-degree launches of one operator or
+  // preconditioner application run concurrently (fork/join through events,
+  // parallel branches when captured in a CUDA graph)
+  std::vector<cudaStream_t> gstreams;
+  std::vector<cudaEvent_t> gevents;
+  cudaEvent_t fork_ev = nullptr;
+  ~hpse_mesh() {
+    for (auto st : gstreams) cudaStreamDestroy(st);
+    for (auto ev : gevents) cudaEventDestroy(ev);
+    if (fork_ev) cudaEventDestroy(fork_ev);
+  }
   std::unique_ptr<SolverWork> work;
 };
 
@@ -751,33 +762,61 @@ static PrecArgsT<T> prec_args(const hpse_mesh *m, const Group &g) {
 
 static int prec_index(int prec) { return prec == HPSE_FP64 ? 0 : 1; }
 
+// stream of degree group gi for a launch ordered after work already on s
+static cudaError_t group_fork(hpse_mesh *m, cudaStream_t s) {
+  if (m->groups.size() < 2) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(m->fork_ev, s);
+  if (e != cudaSuccess) return e;
+  for (cudaStream_t gs : m->gstreams)
+    if ((e = cudaStreamWaitEvent(gs, m->fork_ev, 0)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+static cudaError_t group_join(hpse_mesh *m, cudaStream_t s) {
+  if (m->groups.size() < 2) return cudaSuccess;
+  cudaError_t e;
+  for (size_t i = 0; i < m->gstreams.size(); ++i) {
+    if ((e = cudaEventRecord(m->gevents[i], m->gstreams[i])) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(s, m->gevents[i], 0)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+static cudaStream_t group_stream(hpse_mesh *m, size_t gi, cudaStream_t s) {
+  return m->groups.size() < 2 ? s : m->gstreams[gi];
+}
+
 template <typename T>
 static hpse_status launch_apply_all(hpse_mesh *m, int mode, ApplyArgsT<T> base_args, cudaStream_t s) {
   const int pi = sizeof(T) == 8 ? 0 : 1;
-  for (const Group &g : m->groups) {
+  CK(group_fork(m, s));
+  for (size_t gi = 0; gi < m->groups.size(); ++gi) {
+    const Group &g = m->groups[gi];
     ApplyArgsT<T> a = base_args;
     a.elems = g.elems.as<int32_t>();
     a.n_group = g.n;
     const KernelSet &ks = g_sets[pi][g.W];
     const int th = m->threads[0][pi][g.W];
-    CK(ks.apply(m->coef_kind, mode, &a, g.n * m->n_rhs, th, s));
+    CK(ks.apply(m->coef_kind, mode, &a, g.n * m->n_rhs, th, group_stream(m, gi, s)));
     ++g_launches;
   }
+  CK(group_join(m, s));
   return HPSE_OK;
 }
 
 template <typename T>
 static hpse_status launch_prec_all(hpse_mesh *m, int mode, PrecArgsT<T> base_args, cudaStream_t s) {
   const int pi = sizeof(T) == 8 ? 0 : 1;
-  for (const Group &g : m->groups) {
+  CK(group_fork(m, s));
+  for (size_t gi = 0; gi < m->groups.size(); ++gi) {
+    const Group &g = m->groups[gi];
     PrecArgsT<T> a = base_args;
     a.elems = g.elems.as<int32_t>();
     a.n_group = g.n;
     const KernelSet &ks = g_sets[pi][g.W];
     const int th = m->threads[1][pi][g.W];
-    CK(ks.precond(mode, &a, g.n * m->n_rhs, th, s));
+    CK(ks.precond(mode, &a, g.n * m->n_rhs, th, group_stream(m, gi, s)));
     ++g_launches;
   }
+  CK(group_join(m, s));
   return HPSE_OK;
 }
 
@@ -917,6 +956,23 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
     q.insert(q.end(), t.KQ.begin(), t.KQ.end());
     q.insert(q.end(), t.wq.begin(), t.wq.end());
     CK(upload(m->d_qtab[W], q));
+  }
+  // heaviest degree groups first (they are launched first on their streams)
+  std::sort(m->groups.begin(), m->groups.end(), [](const Group &x, const Group &y) {
+    const double wx = (double)x.n * std::pow(2.0 * x.W + 1, 3) * (x.W + 1);
+    const double wy = (double)y.n * std::pow(2.0 * y.W + 1, 3) * (y.W + 1);
+    return wx > wy;
+  });
+  if (m->groups.size() > 1) {
+    CK(cudaEventCreateWithFlags(&m->fork_ev, cudaEventDisableTiming));
+    for (size_t i = 0; i < m->groups.size(); ++i) {
+      cudaStream_t st;
+      cudaEvent_t ev;
+      CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      m->gstreams.push_back(st);
+      m->gevents.push_back(ev);
+    }
   }
   std::vector<double> geo(4 * (size_t)E);
   std::vector<float> geo32(4 * (size_t)E);

@@ -403,3 +403,29 @@ def varcoef_manufactured(n=(2, 2, 1), W=4) -> Problem:
         return -(a(xs, ys, zs) * lap + ax * ux + ay * uy + az * uz)
 
     return Problem(mesh, [f], [u], a, grad_a, [u], [grad], name="varcoef_manufactured")
+
+
+def batch_problems(problems: List[Problem]) -> Problem:
+    """Independent problems in one batch (one mesh, per-problem data).
+
+    The returned Problem carries ``parts``: element e takes its data from
+    ``parts[mesh.elem_problem[e]]``.  All parts must have the same number of
+    right-hand sides and the same coefficient kind.
+    """
+    nr = problems[0].n_rhs
+    if any(p.n_rhs != nr for p in problems):
+        raise ValueError("all problems of a batch need the same number of right-hand sides")
+    if any((p.a is None) != (problems[0].a is None) for p in problems):
+        raise ValueError("all problems of a batch need the same coefficient kind")
+    mesh = concat_meshes([p.mesh for p in problems])
+    out = Problem(mesh, list(problems[0].f), list(problems[0].g), problems[0].a, problems[0].grad_a,
+                  name="batch", meta={"n": len(problems)})
+    out.parts = list(problems)
+    return out
+
+
+def adjoint_batch(n_problem=256, n=4, seed_w=7, seed_theta=100, wmin=4, wmax=10) -> Problem:
+    """The adjoint batch: n_problem independent lognormal-coefficient problems,
+    degrees W_p ~ U{wmin..wmax} (PCG64(seed_w)), theta from PCG64(seed_theta + p)."""
+    Ws = adjoint_batch_degrees(n_problem, seed_w, wmin, wmax)
+    return batch_problems([lognormal_coef_problem(int(W), p, n=n, seed=seed_theta) for p, W in enumerate(Ws)])

@@ -188,6 +188,43 @@ hpse_status hpse_pcg_solve(hpse_mesh *m, const hpse_solve_opts *opts, double *x,
 hpse_status hpse_h1_error(hpse_mesh *m, const double *u, const double *ref,
                           const double *vq, const double *gq, double *out, void *stream);
 
+/* Residual map and its transpose (FP64; Section 5.3: the weighted PDE
+ * residual of eq. (4.2) collocated on the (2W+1)^3 GLL points).
+ *   hpse_apply_residual:  z[r][q] = sqrt(w_q J) (L u_r - f_r)(x_q), with
+ *                         L u = -a Lap u - grad a . grad u and the data of
+ *                         hpse_set_data; u a device FP64 DOF vector, z device
+ *                         FP64 [n_rhs][nquad].
+ *   hpse_apply_transpose: y = S^T z, the exact transpose of u -> z without the
+ *                         data term (the backward of the residual map).
+ * Both use a scratch buffer the handle allocates on first use. */
+hpse_status hpse_apply_residual(hpse_mesh *m, const double *u, double *z, void *stream);
+hpse_status hpse_apply_transpose(hpse_mesh *m, const double *z, double *y, void *stream);
+
+/* Point values of a DOF vector (FP64): out[r][0..4][q] = v, dv/dx, dv/dy,
+ * dv/dz, Lap v at the volume points (physical coordinates). */
+hpse_status hpse_eval_fields(hpse_mesh *m, const double *u, double *out, void *stream);
+
+/* Transpose of point evaluation (FP64): y = sum_q rho[r][q] dv_r(x_q)/dV,
+ * rho device [n_rhs][nquad], y a device DOF vector (overwritten). */
+hpse_status hpse_apply_eval_transpose(hpse_mesh *m, const double *rho, double *y, void *stream);
+
+/* w_q J_e at the volume points (device FP64 [nquad]). */
+hpse_status hpse_quad_weights(hpse_mesh *m, double *out, void *stream);
+
+/* Replace the right-hand side b by a device FP64 vector (e.g. dJ/du for an
+ * adjoint solve A lambda = dJ/du, A being symmetric).  Synchronous. */
+hpse_status hpse_set_rhs(hpse_mesh *m, const double *b, void *stream);
+
+/* Gradient of a solution functional J with respect to the data at the volume
+ * points, given the point fields (hpse_eval_fields) of the solution u and of
+ * the adjoint state lambda (A lambda = dJ/du): out[r][0..4][q] =
+ *   dJ/df = wJ L lambda,  dJ/da = wJ (Lap u L lambda + (L u - f) Lap lambda),
+ *   dJ/d(d_k a) = wJ (d_k u L lambda + (L u - f) d_k lambda), k = x, y, z.
+ * Derivative of -lambda^T (A u - b) with respect to each datum (the volume
+ * term of eq. 4.2 is the only one that depends on f and a). */
+hpse_status hpse_data_gradient(hpse_mesh *m, const double *ufields, const double *lfields, double *out,
+                               void *stream);
+
 /* Allocation-free variant of hpse_h1_error (same arguments, same results up
  * to the order of the final per-rhs sums).  The thesis has no counterpart: it
  * exists for callers that cannot call cudaMalloc -- applications whose device

@@ -68,6 +68,13 @@ SIGNATURES = {
                                 C.c_void_p]),
     "hpse_h1_error_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                         C.c_void_p, C.c_void_p]),
+    "hpse_apply_residual": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hpse_apply_transpose": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hpse_eval_fields": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hpse_apply_eval_transpose": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hpse_quad_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hpse_set_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hpse_data_gradient": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "hpse_work_counts": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "hpse_set_block_threads": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     "hpse_get_block_threads": (C.c_int32, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]),

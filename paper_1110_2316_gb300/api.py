@@ -136,6 +136,30 @@ class Mesh:
                                       _stream(stream)), "hpse_h1_error")
         return out.reshape(self.n_rhs, 2)
 
+    # -- residual map, point fields and adjoint data gradients (FP64) -------
+    def apply_residual(self, u, z, stream=None):
+        check(self._lib.hpse_apply_residual(self._h, _ptr(u), _ptr(z), _stream(stream)), "hpse_apply_residual")
+
+    def apply_transpose(self, z, y, stream=None):
+        check(self._lib.hpse_apply_transpose(self._h, _ptr(z), _ptr(y), _stream(stream)), "hpse_apply_transpose")
+
+    def eval_fields(self, u, out, stream=None):
+        check(self._lib.hpse_eval_fields(self._h, _ptr(u), _ptr(out), _stream(stream)), "hpse_eval_fields")
+
+    def apply_eval_transpose(self, rho, y, stream=None):
+        check(self._lib.hpse_apply_eval_transpose(self._h, _ptr(rho), _ptr(y), _stream(stream)),
+              "hpse_apply_eval_transpose")
+
+    def quad_weights(self, out, stream=None):
+        check(self._lib.hpse_quad_weights(self._h, _ptr(out), _stream(stream)), "hpse_quad_weights")
+
+    def set_rhs(self, b, stream=None):
+        check(self._lib.hpse_set_rhs(self._h, _ptr(b), _stream(stream)), "hpse_set_rhs")
+
+    def data_gradient(self, ufields, lfields, out, stream=None):
+        check(self._lib.hpse_data_gradient(self._h, _ptr(ufields), _ptr(lfields), _ptr(out), _stream(stream)),
+              "hpse_data_gradient")
+
     def work_counts(self):
         v, f = C.c_double(), C.c_double()
         check(self._lib.hpse_work_counts(self._h, C.byref(v), C.byref(f)), "hpse_work_counts")

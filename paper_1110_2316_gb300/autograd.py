@@ -1,0 +1,89 @@
+"""torch.autograd wrappers over the C ABI (argument marshalling only).
+
+* ``ResidualMap``: u -> z = sqrt(w J)(L u - f) at the volume points (the
+  weighted PDE residual of eq. (4.2), Section 5.3); backward = the
+  hand-written transpose kernel (hpse_apply_transpose).
+* ``PointValues``: u -> u(x_q) at the volume points; backward = the transpose
+  of point evaluation (hpse_apply_eval_transpose).
+* ``Solve``: the data (f, a, grad a at the volume points) -> the solution u of
+  the normal equations.  Backward: the adjoint state lambda solves
+  A lambda = dJ/du by PCG (recomputed, no iterate is stored; A is symmetric),
+  and hpse_data_gradient returns dJ/df, dJ/da, dJ/d(grad a) at the points.
+
+All tensors are CUDA float64 tensors; shapes: u [n_rhs * ndof], z and f
+[n_rhs, nquad], a [nquad], grad_a [3, nquad].
+"""
+from __future__ import annotations
+
+import torch
+
+from .api import FP64
+
+
+class ResidualMap(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, u, mesh):
+        z = torch.empty(mesh.n_rhs, mesh.nquad, dtype=torch.float64, device=u.device)
+        mesh.apply_residual(u.contiguous(), z)
+        ctx.mesh = mesh
+        return z
+
+    @staticmethod
+    def backward(ctx, gz):
+        m = ctx.mesh
+        y = torch.empty(m.n_rhs * m.ndof, dtype=torch.float64, device=gz.device)
+        m.apply_transpose(gz.contiguous(), y)
+        return y, None
+
+
+class PointValues(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, u, mesh):
+        f = torch.empty(mesh.n_rhs, 5, mesh.nquad, dtype=torch.float64, device=u.device)
+        mesh.eval_fields(u.contiguous(), f)
+        ctx.mesh = mesh
+        return f[:, 0, :].contiguous()
+
+    @staticmethod
+    def backward(ctx, gv):
+        m = ctx.mesh
+        y = torch.empty(m.n_rhs * m.ndof, dtype=torch.float64, device=gv.device)
+        m.apply_eval_transpose(gv.contiguous(), y)
+        return y, None
+
+
+class Solve(torch.autograd.Function):
+    """u = A(a)^{-1} b(f, a) for the data sampled at the volume points."""
+
+    @staticmethod
+    def forward(ctx, f, a, grad_a, mesh, tol=1e-12, prec=FP64, adjoint_prec=FP64):
+        mesh.set_data(f=f.detach().cpu().numpy(),
+                      a=None if a is None else a.detach().cpu().numpy(),
+                      grad_a=None if grad_a is None else grad_a.detach().cpu().numpy())
+        x = torch.zeros(mesh.n_rhs * mesh.ndof, dtype=torch.float64, device=f.device)
+        mesh.pcg_solve(x, tol=tol, prec=prec)
+        ctx.save_for_backward(x)
+        ctx.mesh, ctx.tol, ctx.adjoint_prec = mesh, tol, adjoint_prec
+        ctx.has_a = a is not None
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        (x,) = ctx.saved_tensors
+        m = ctx.mesh
+        b = torch.empty_like(x)
+        m.get_rhs(b)
+        m.set_rhs(gx.contiguous())
+        lam = torch.zeros_like(x)
+        m.pcg_solve(lam, tol=ctx.tol, prec=ctx.adjoint_prec)
+        m.set_rhs(b)
+        uf = torch.empty(m.n_rhs, 5, m.nquad, dtype=torch.float64, device=x.device)
+        lf = torch.empty_like(uf)
+        m.eval_fields(x, uf)
+        m.eval_fields(lam, lf)
+        g = torch.empty_like(uf)
+        m.data_gradient(uf, lf, g)
+        gf = g[:, 0, :]
+        ga = g[:, 1, :].sum(0) if ctx.has_a else None
+        gga = g[:, 2:5, :].sum(0) if ctx.has_a else None
+        return gf, ga, gga, None, None, None, None

@@ -196,6 +196,10 @@ struct hpse_mesh {
   DevBuf d_dof_off, d_nbr, d_geo64, d_geo32, d_prob, d_coef_off, d_prob_ptr, d_prob_elems, d_elem_W;
   DevBuf d_coef64, d_coef32;  // [nquad][4] (m, d_x, d_y, d_z) per point (COEF_SCALAR)
   DevBuf d_b;                 // FP64 right-hand side
+  DevBuf d_f;                 // FP64 source at the volume points [n_rhs][nquad]
+  DevBuf d_aux;               // FP64 [5][nquad]: w J, a, a_x, a_y, a_z at the volume points
+  DevBuf d_tabs_ptr;          // device array of the per-degree FP64 table pointers
+  DevBuf d_scr_fields, d_scr_rho;  // scratch of the residual map and its transpose
   DevBuf d_bnorm2;            // FP64 ||b||^2 per (problem, rhs)
   std::map<int, DevBuf> d_qtab;  // per degree FP64 Q-grid tables for the face data
   bool has_data = false;
@@ -955,6 +959,7 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
     q.insert(q.end(), t.DQ.begin(), t.DQ.end());
     q.insert(q.end(), t.KQ.begin(), t.KQ.end());
     q.insert(q.end(), t.wq.begin(), t.wq.end());
+    q.insert(q.end(), t.B2.begin(), t.B2.end());
     CK(upload(m->d_qtab[W], q));
   }
   // heaviest degree groups first (they are launched first on their streams)
@@ -1076,6 +1081,31 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data) {
             wja[i] = wJ;
           }
         }
+  }
+  {
+    std::vector<double> aux(5 * (size_t)nq);
+    for (int e = 0; e < m->n_elem; ++e) {
+      const hm::DegreeTables &t = m->tabs.at(m->W[e]);
+      const int Q = t.Q;
+      double J = 1.0;
+      for (int a = 0; a < 3; ++a) J *= (m->hi[3 * e + a] - m->lo[3 * e + a]) / 2.0;
+      const int64_t o = m->coef_off[e];
+      for (int c = 0; c < Q; ++c)
+        for (int b = 0; b < Q; ++b)
+          for (int a = 0; a < Q; ++a) {
+            const int64_t i = o + ((int64_t)c * Q + b) * Q + a;
+            aux[i] = t.wq[a] * t.wq[b] * t.wq[c] * J;
+            const bool var = m->coef_kind == HPSE_COEF_SCALAR;
+            aux[nq + i] = var ? data->a[i] : 1.0;
+            for (int k = 0; k < 3; ++k) aux[(2 + k) * nq + i] = var ? data->grad_a[k * nq + i] : 0.0;
+          }
+    }
+    CK(upload_reuse(m->d_aux, aux));
+    if (!m->d_f.p || m->d_f.bytes != (size_t)R * nq * sizeof(double)) CK(m->d_f.alloc((size_t)R * nq * sizeof(double)));
+    if (nq > 0) CK(cudaMemcpy(m->d_f.p, data->f, (size_t)R * nq * sizeof(double), cudaMemcpyHostToDevice));
+    std::vector<const double *> tp(HPSE_MAX_W + 1, nullptr);
+    for (auto &kv : m->d_qtab) tp[kv.first] = kv.second.as<double>();
+    CK(upload_reuse(m->d_tabs_ptr, tp));
   }
   if (m->coef_kind == HPSE_COEF_SCALAR) {
     std::vector<float> c32(coef.size());
@@ -1798,6 +1828,345 @@ extern "C" hpse_status hpse_h1_error(hpse_mesh *m, const double *u, const double
   }
   return HPSE_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Residual map, its transpose and adjoint data gradients (FP64).
+//
+// The volume residual of eq. (4.2) sampled at the (2W+1)^3 GLL points,
+//   z_q = sqrt(w_q J) (L u - f)_q,  L u = -a Lap u - grad a . grad u,
+// its transpose S^T z, point values and derivatives of a DOF vector, the
+// transpose of point evaluation, and the gradient of a solution functional
+// J with respect to the data (f, a, grad a) at the points given the adjoint
+// state lambda (A lambda = dJ/du):
+//   dJ/df = w J L lambda
+//   dJ/da = w J [Lap u L lambda + (L u - f) Lap lambda]
+//   dJ/d(d_k a) = w J [d_k u L lambda + (L u - f) d_k lambda]
+// (differentiate -lambda^T sum_q z_q dz_q/du with respect to each datum).
+// ---------------------------------------------------------------------------
+struct FieldArgs {
+  int n_rhs;
+  int64_t ndof, nquad;
+  const int64_t *dof_off, *coef_off;
+  const int32_t *elem_W;
+  const double *geo;
+  const double *const *qtab;  // per degree: B0, B1 (QxP), DQ, KQ (QxQ), wq (Q), B2 (QxP)
+  const double *u;
+  double *out;                // [n_rhs][5][nquad]
+};
+
+// (v, v_x, v_y, v_z, Lap v) of a DOF vector at the volume points; one block per (element, rhs)
+__global__ void k_fields(FieldArgs A) {
+  extern __shared__ double sm[];
+  const int item = blockIdx.x;
+  const int e = item / A.n_rhs, r = item - e * A.n_rhs;
+  const int W = A.elem_W[e], P = W + 1, Q = 2 * W + 1;
+  const double *tb = A.qtab[W];
+  const double *B0 = tb, *B1 = tb + Q * P, *B2 = tb + 2 * Q * P + 2 * Q * Q + Q;
+  const double *geo = A.geo + (int64_t)e * 4;
+  const double sx = geo[0], sy = geo[1], sz = geo[2];
+  double *blk = sm, *X0 = blk + P * P * P, *X1 = X0 + Q * P * P, *X2 = X1 + Q * P * P;
+  double *Ta = X2 + Q * P * P, *Tb = Ta + Q * Q * P, *Tc = Tb + Q * Q * P;
+  const int64_t base = (int64_t)r * A.ndof + A.dof_off[e];
+  const int nt = blockDim.x;
+  for (int t = threadIdx.x; t < P * P * P; t += nt) blk[t] = A.u[base + t];
+  __syncthreads();
+  for (int t = threadIdx.x; t < Q * P * P; t += nt) {
+    const int qa = t % Q, l = t / Q;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int i = 0; i < P; ++i) {
+      const double v = blk[l * P + i];
+      a0 += B0[qa * P + i] * v;
+      a1 += B1[qa * P + i] * v;
+      a2 += B2[qa * P + i] * v;
+    }
+    X0[l * Q + qa] = a0;
+    X1[l * Q + qa] = a1;
+    X2[l * Q + qa] = a2;
+  }
+  __syncthreads();
+  // pass A: T_a = B0y X0, T_b = B1y X0, T_c = B0y X1
+  for (int t = threadIdx.x; t < Q * Q * P; t += nt) {
+    const int qa = t % Q, qb = (t / Q) % Q, k = t / (Q * Q);
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int j = 0; j < P; ++j) {
+      const double x0 = X0[(k * P + j) * Q + qa];
+      a += B0[qb * P + j] * x0;
+      b += B1[qb * P + j] * x0;
+      c += B0[qb * P + j] * X1[(k * P + j) * Q + qa];
+    }
+    Ta[t] = a;
+    Tb[t] = b;
+    Tc[t] = c;
+  }
+  __syncthreads();
+  const int64_t ob = (int64_t)r * 5 * A.nquad + A.coef_off[e];
+  for (int t = threadIdx.x; t < Q * Q * Q; t += nt) {
+    const int qa = t % Q, qb = (t / Q) % Q, qc = t / (Q * Q);
+    double v = 0.0, vz = 0.0, vzz = 0.0, vy = 0.0, vx = 0.0;
+    for (int k = 0; k < P; ++k) {
+      const int o = (k * Q + qb) * Q + qa;
+      v += B0[qc * P + k] * Ta[o];
+      vz += B1[qc * P + k] * Ta[o];
+      vzz += B2[qc * P + k] * Ta[o];
+      vy += B0[qc * P + k] * Tb[o];
+      vx += B0[qc * P + k] * Tc[o];
+    }
+    A.out[ob + t] = v;
+    A.out[ob + A.nquad + t] = sx * vx;
+    A.out[ob + 2 * A.nquad + t] = sy * vy;
+    A.out[ob + 3 * A.nquad + t] = sz * vz;
+    A.out[ob + 4 * A.nquad + t] = sz * sz * vzz;
+  }
+  __syncthreads();
+  // pass B: T_a = B2y X0 (u_yy), T_b = B0y X2 (u_xx)
+  for (int t = threadIdx.x; t < Q * Q * P; t += nt) {
+    const int qa = t % Q, qb = (t / Q) % Q, k = t / (Q * Q);
+    double a = 0.0, b = 0.0;
+    for (int j = 0; j < P; ++j) {
+      a += B2[qb * P + j] * X0[(k * P + j) * Q + qa];
+      b += B0[qb * P + j] * X2[(k * P + j) * Q + qa];
+    }
+    Ta[t] = a;
+    Tb[t] = b;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < Q * Q * Q; t += nt) {
+    const int qa = t % Q, qb = (t / Q) % Q, qc = t / (Q * Q);
+    double vyy = 0.0, vxx = 0.0;
+    for (int k = 0; k < P; ++k) {
+      const int o = (k * Q + qb) * Q + qa;
+      vyy += B0[qc * P + k] * Ta[o];
+      vxx += B0[qc * P + k] * Tb[o];
+    }
+    A.out[ob + 4 * A.nquad + t] += sy * sy * vyy + sx * sx * vxx;
+  }
+}
+
+// y = sum_q rho_q d v(x_q) / dV (transpose of point evaluation); one block per (element, rhs)
+__global__ void k_eval_T(FieldArgs A, const double *rho) {
+  extern __shared__ double sm[];
+  const int item = blockIdx.x;
+  const int e = item / A.n_rhs, r = item - e * A.n_rhs;
+  const int W = A.elem_W[e], P = W + 1, Q = 2 * W + 1;
+  const double *B0 = A.qtab[W];
+  double *R = sm, *T = R + Q * Q * Q, *X = T + Q * Q * P;
+  const int nt = blockDim.x;
+  const int64_t qb0 = (int64_t)r * A.nquad + A.coef_off[e];
+  for (int t = threadIdx.x; t < Q * Q * Q; t += nt) R[t] = rho[qb0 + t];
+  __syncthreads();
+  for (int t = threadIdx.x; t < Q * Q * P; t += nt) {  // T[k][qb][qa]
+    const int qa = t % Q, qb = (t / Q) % Q, k = t / (Q * Q);
+    double s = 0.0;
+    for (int qc = 0; qc < Q; ++qc) s += B0[qc * P + k] * R[(qc * Q + qb) * Q + qa];
+    T[t] = s;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < Q * P * P; t += nt) {  // X[k][j][qa]
+    const int qa = t % Q, j = (t / Q) % P, k = t / (Q * P);
+    double s = 0.0;
+    for (int qb = 0; qb < Q; ++qb) s += B0[qb * P + j] * T[(k * Q + qb) * Q + qa];
+    X[t] = s;
+  }
+  __syncthreads();
+  const int64_t base = (int64_t)r * A.ndof + A.dof_off[e];
+  for (int t = threadIdx.x; t < P * P * P; t += nt) {
+    const int i = t % P, l = t / P;
+    double s = 0.0;
+    for (int qa = 0; qa < Q; ++qa) s += B0[qa * P + i] * X[l * Q + qa];
+    A.out[base + t] = s;
+  }
+}
+
+// residual map at the points: z = sqrt(wJ) (L u - f)
+__global__ void k_resid_points(int64_t nquad, int n_rhs, const double *aux, const double *f, const double *fields,
+                               double *z) {
+  const int64_t n = nquad * n_rhs;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / nquad, q = i - r * nquad;
+    const double *fl = fields + r * 5 * nquad;
+    const double wJ = aux[q], a = aux[nquad + q];
+    const double Lu = -a * fl[4 * nquad + q] -
+                      (aux[2 * nquad + q] * fl[nquad + q] + aux[3 * nquad + q] * fl[2 * nquad + q] +
+                       aux[4 * nquad + q] * fl[3 * nquad + q]);
+    z[i] = sqrt(wJ) * (Lu - f[i]);
+  }
+}
+
+// rho = -sqrt(wJ) a z: the weights of S^T z in the sum-factorised transpose kernel
+__global__ void k_rho_from_z(int64_t nquad, int n_rhs, const double *aux, const double *z, double *rho) {
+  const int64_t n = nquad * n_rhs;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = i % nquad;
+    rho[i] = -sqrt(aux[q]) * aux[nquad + q] * z[i];
+  }
+}
+
+// adjoint data gradient at the points
+__global__ void k_data_grad(int64_t nquad, int n_rhs, const double *aux, const double *f, const double *uf,
+                            const double *lf, double *out) {
+  const int64_t n = nquad * n_rhs;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / nquad, q = i - r * nquad;
+    const double *u = uf + r * 5 * nquad, *l = lf + r * 5 * nquad;
+    const double wJ = aux[q], a = aux[nquad + q];
+    const double ax = aux[2 * nquad + q], ay = aux[3 * nquad + q], az = aux[4 * nquad + q];
+    const double ux = u[nquad + q], uy = u[2 * nquad + q], uz = u[3 * nquad + q], lu = u[4 * nquad + q];
+    const double lx = l[nquad + q], ly = l[2 * nquad + q], lz = l[3 * nquad + q], ll = l[4 * nquad + q];
+    const double Lu = -a * lu - (ax * ux + ay * uy + az * uz);
+    const double Ll = -a * ll - (ax * lx + ay * ly + az * lz);
+    const double res = Lu - f[i];
+    double *o = out + r * 5 * nquad;
+    o[q] = wJ * Ll;
+    o[nquad + q] = wJ * (lu * Ll + res * ll);
+    o[2 * nquad + q] = wJ * (ux * Ll + res * lx);
+    o[3 * nquad + q] = wJ * (uy * Ll + res * ly);
+    o[4 * nquad + q] = wJ * (uz * Ll + res * lz);
+  }
+}
+
+static FieldArgs field_args(const hpse_mesh *m, const double *u, double *out) {
+  FieldArgs A;
+  A.n_rhs = m->n_rhs;
+  A.ndof = m->ndof;
+  A.nquad = m->nquad;
+  A.dof_off = m->d_dof_off.as<int64_t>();
+  A.coef_off = m->d_coef_off.as<int64_t>();
+  A.elem_W = m->d_elem_W.as<int32_t>();
+  A.geo = m->d_geo64.as<double>();
+  A.qtab = m->d_tabs_ptr.as<const double *>();
+  A.u = u;
+  A.out = out;
+  return A;
+}
+
+static int max_degree(const hpse_mesh *m) {
+  int w = 1;
+  for (auto &kv : m->d_qtab) w = std::max(w, kv.first);
+  return w;
+}
+
+static hpse_status launch_fields(hpse_mesh *m, const double *u, double *out, cudaStream_t s) {
+  const int W = max_degree(m), P = W + 1, Q = 2 * W + 1;
+  const size_t smem = (size_t)(P * P * P + 3 * Q * P * P + 3 * Q * Q * P) * sizeof(double);
+  CK(cudaFuncSetAttribute(k_fields, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_fields<<<n_items_all(m), 256, smem, s>>>(field_args(m, u, out));
+  CK(cudaGetLastError());
+  ++g_launches;
+  return HPSE_OK;
+}
+
+extern "C" hpse_status hpse_eval_fields(hpse_mesh *m, const double *u, double *out, void *stream) {
+  if (!m) return HPSE_ERR_INVALID_ARG;
+  if (m->ndof == 0) return HPSE_OK;
+  if (!u || !out) return HPSE_ERR_INVALID_ARG;
+  if (!m->has_data) return HPSE_ERR_NO_DATA;
+  CK(cudaSetDevice(m->device));
+  return launch_fields(m, u, out, (cudaStream_t)stream);
+}
+
+extern "C" hpse_status hpse_apply_eval_transpose(hpse_mesh *m, const double *rho, double *y, void *stream) {
+  if (!m) return HPSE_ERR_INVALID_ARG;
+  if (m->ndof == 0) return HPSE_OK;
+  if (!rho || !y) return HPSE_ERR_INVALID_ARG;
+  if (!m->has_data) return HPSE_ERR_NO_DATA;
+  CK(cudaSetDevice(m->device));
+  const int W = max_degree(m), P = W + 1, Q = 2 * W + 1;
+  const size_t smem = (size_t)(Q * Q * Q + Q * Q * P + Q * P * P) * sizeof(double);
+  CK(cudaFuncSetAttribute(k_eval_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_eval_T<<<n_items_all(m), 256, smem, (cudaStream_t)stream>>>(field_args(m, nullptr, y), rho);
+  CK(cudaGetLastError());
+  ++g_launches;
+  return HPSE_OK;
+}
+
+extern "C" hpse_status hpse_quad_weights(hpse_mesh *m, double *out, void *stream) {
+  if (!m || (!out && m->nquad > 0)) return HPSE_ERR_INVALID_ARG;
+  if (!m->has_data) return HPSE_ERR_NO_DATA;
+  CK(cudaSetDevice(m->device));
+  if (m->nquad)
+    CK(cudaMemcpyAsync(out, m->d_aux.p, (size_t)m->nquad * sizeof(double), cudaMemcpyDeviceToDevice,
+                       (cudaStream_t)stream));
+  return HPSE_OK;
+}
+
+static hpse_status ensure_scratch(hpse_mesh *m) {
+  const size_t nf = (size_t)5 * m->n_rhs * m->nquad * sizeof(double);
+  const size_t nr = (size_t)m->n_rhs * m->nquad * sizeof(double);
+  if (m->d_scr_fields.bytes != nf) CK(m->d_scr_fields.alloc(nf));
+  if (m->d_scr_rho.bytes != nr) CK(m->d_scr_rho.alloc(nr));
+  return HPSE_OK;
+}
+
+extern "C" hpse_status hpse_apply_residual(hpse_mesh *m, const double *u, double *z, void *stream) {
+  if (!m) return HPSE_ERR_INVALID_ARG;
+  if (m->ndof == 0) return HPSE_OK;
+  if (!u || !z) return HPSE_ERR_INVALID_ARG;
+  if (!m->has_data) return HPSE_ERR_NO_DATA;
+  CK(cudaSetDevice(m->device));
+  hpse_status st = ensure_scratch(m);
+  if (st != HPSE_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  st = launch_fields(m, u, m->d_scr_fields.as<double>(), s);
+  if (st != HPSE_OK) return st;
+  k_resid_points<<<1024, 256, 0, s>>>(m->nquad, m->n_rhs, m->d_aux.as<double>(), m->d_f.as<double>(),
+                                      m->d_scr_fields.as<double>(), z);
+  CK(cudaGetLastError());
+  ++g_launches;
+  return HPSE_OK;
+}
+
+extern "C" hpse_status hpse_apply_transpose(hpse_mesh *m, const double *z, double *y, void *stream) {
+  if (!m) return HPSE_ERR_INVALID_ARG;
+  if (m->ndof == 0) return HPSE_OK;
+  if (!z || !y) return HPSE_ERR_INVALID_ARG;
+  if (!m->has_data) return HPSE_ERR_NO_DATA;
+  CK(cudaSetDevice(m->device));
+  hpse_status st = ensure_scratch(m);
+  if (st != HPSE_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  k_rho_from_z<<<1024, 256, 0, s>>>(m->nquad, m->n_rhs, m->d_aux.as<double>(), z, m->d_scr_rho.as<double>());
+  CK(cudaGetLastError());
+  ++g_launches;
+  ApplyArgsT<double> a = apply_args<double>(m, m->groups[0], nullptr, y);
+  a.rho = m->d_scr_rho.as<double>();
+  a.skip_faces = 1;
+  return launch_apply_all<double>(m, MODE_TRANSPOSE, a, s);
+}
+
+extern "C" hpse_status hpse_data_gradient(hpse_mesh *m, const double *ufields, const double *lfields, double *out,
+                                          void *stream) {
+  if (!m) return HPSE_ERR_INVALID_ARG;
+  if (m->nquad == 0) return HPSE_OK;
+  if (!ufields || !lfields || !out) return HPSE_ERR_INVALID_ARG;
+  if (!m->has_data) return HPSE_ERR_NO_DATA;
+  CK(cudaSetDevice(m->device));
+  k_data_grad<<<1024, 256, 0, (cudaStream_t)stream>>>(m->nquad, m->n_rhs, m->d_aux.as<double>(), m->d_f.as<double>(),
+                                                      ufields, lfields, out);
+  CK(cudaGetLastError());
+  ++g_launches;
+  return HPSE_OK;
+}
+
+extern "C" hpse_status hpse_set_rhs(hpse_mesh *m, const double *b, void *stream) {
+  if (!m) return HPSE_ERR_INVALID_ARG;
+  if (!m->has_data) return HPSE_ERR_NO_DATA;
+  if (m->ndof == 0) return HPSE_OK;
+  if (!b) return HPSE_ERR_INVALID_ARG;
+  CK(cudaSetDevice(m->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nv = (size_t)m->n_rhs * m->ndof;
+  CK(cudaMemcpyAsync(m->d_b.p, b, nv * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  DevBuf part;
+  CK(part.alloc((size_t)std::max(1, n_items_all(m)) * sizeof(double)));
+  k_dot<double, double><<<n_items_all(m), 128, 0, s>>>(elem_args(m), m->d_b.as<double>(), m->d_b.as<double>(),
+                                                       part.as<double>());
+  k_bnorm<<<npr_of(m), 128, 0, s>>>(fin_args(m), part.as<double>(), m->d_bnorm2.as<double>());
+  CK(cudaGetLastError());
+  g_launches += 2;
+  CK(cudaStreamSynchronize(s));
+  return HPSE_OK;
+}
+
 
 // ---------------------------------------------------------------------------
 // H^1 norms without device allocation.

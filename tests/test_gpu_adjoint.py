@@ -1,0 +1,218 @@
+"""GPU parity of the residual map, its hand-written transpose, point fields
+and the adjoint data gradient; autograd gradients of a solution functional
+against the oracle's adjoint gradient and against finite differences.
+
+Tolerances: kernels vs oracle 1e-12 relative (FP64 sums in a different
+order); end-to-end gradients 1e-7 relative (both sides solve to a relative
+residual of 1e-13 / exactly); finite differences: Richardson-extrapolated
+central differences, |g - fd| <= 1e-6 max(|fd|, 1e-3 |g|_inf).
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as wl
+from oracle.adjoint import data_gradient, element_fields, l2_misfit_gradient
+from oracle.functional import Discretisation
+from oracle.gll import gll
+from oracle.pcg import cholesky_solve
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1110_2316_gb300.build import build
+    build()
+    from paper_1110_2316_gb300 import api as A
+    return A
+
+
+def _mesh(api, pb):
+    kind = api.COEF_SCALAR if pb.a is not None else api.COEF_LAPLACE
+    m = api.Mesh(pb.mesh, n_rhs=pb.n_rhs, coef_kind=kind)
+    m.set_data(**api.problem_data_arrays(m, pb))
+    return m
+
+
+def _flat(disc, per_elem):
+    return np.concatenate([np.asarray(x).ravel() for x in per_elem])
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def u_target(xs, ys, zs):
+    x, y, z = wl._grid(xs, ys, zs)
+    return np.sin(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z)
+
+
+def test_fields_residual_transpose_match_oracle(api):
+    pb = wl.varcoef_manufactured(n=(2, 2, 1), W=4)
+    m = _mesh(api, pb)
+    disc = Discretisation(pb)
+    U = wl.random_dofs(m.ndof, seed=4)
+    u = torch.tensor(U, device="cuda")
+    F = torch.empty(1, 5, m.nquad, dtype=torch.float64, device="cuda")
+    m.eval_fields(u, F)
+    F = F.cpu().numpy()[0]
+    ref = [element_fields(disc, U, e) for e in range(disc.E)]
+    for k in range(5):
+        assert _rel(F[k], _flat(disc, [r[k] for r in ref])) <= 1e-12, k
+    z = torch.empty(1, m.nquad, dtype=torch.float64, device="cuda")
+    m.apply_residual(u, z)
+    zref = _flat(disc, [np.sqrt(disc.vol_weight(e)) * (disc.L_apply(disc.block(U, e), e) - disc.f_at(e, 0))
+                        for e in range(disc.E)])
+    assert _rel(z.cpu().numpy()[0], zref) <= 1e-12
+    Z = np.random.default_rng(1).standard_normal(m.nquad)
+    y = torch.empty_like(u)
+    m.apply_transpose(torch.tensor(Z, device="cuda"), y)
+    Q = [2 * w + 1 for w in disc.W]
+    o, yref = 0, []
+    for e in range(disc.E):
+        n = Q[e] ** 3
+        zb = Z[o:o + n].reshape(Q[e], Q[e], Q[e])
+        yref.append(disc.L_apply_T(np.sqrt(disc.vol_weight(e)) * zb, e))
+        o += n
+    assert _rel(y.cpu().numpy(), _flat(disc, yref)) <= 1e-12
+
+
+def test_adjoint_identities(api):
+    pb = wl.varcoef_manufactured(n=(2, 1, 2), W=3)
+    m = _mesh(api, pb)
+    rng = np.random.default_rng(5)
+    u = torch.tensor(rng.standard_normal(m.ndof), device="cuda")
+    zz = torch.tensor(rng.standard_normal(m.nquad), device="cuda")
+    z0 = torch.empty(1, m.nquad, dtype=torch.float64, device="cuda")
+    z1 = torch.empty_like(z0)
+    m.apply_residual(torch.zeros_like(u), z0)
+    m.apply_residual(u, z1)
+    Su = (z1 - z0)[0]  # linear part of the residual map
+    y = torch.empty_like(u)
+    m.apply_transpose(zz, y)
+    lhs, rhs = float((Su * zz).sum()), float((u * y).sum())
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0)
+    F = torch.empty(1, 5, m.nquad, dtype=torch.float64, device="cuda")
+    m.eval_fields(u, F)
+    m.apply_eval_transpose(zz, y)
+    lhs, rhs = float((F[0, 0] * zz).sum()), float((u * y).sum())
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0)
+
+
+def test_data_gradient_matches_oracle(api):
+    pb = wl.varcoef_manufactured(n=(2, 1, 1), W=3)
+    m = _mesh(api, pb)
+    disc = Discretisation(pb)
+    rng = np.random.default_rng(8)
+    U, L = rng.standard_normal(m.ndof), rng.standard_normal(m.ndof)
+    uf = torch.empty(1, 5, m.nquad, dtype=torch.float64, device="cuda")
+    lf = torch.empty_like(uf)
+    m.eval_fields(torch.tensor(U, device="cuda"), uf)
+    m.eval_fields(torch.tensor(L, device="cuda"), lf)
+    g = torch.empty_like(uf)
+    m.data_gradient(uf, lf, g)
+    g = g.cpu().numpy()[0]
+    ref = data_gradient(disc, U, L)
+    for k in range(5):
+        assert _rel(g[k], _flat(disc, [r[k] for r in ref])) <= 1e-12, k
+
+
+def test_autograd_solve_gradient_matches_oracle(api):
+    from paper_1110_2316_gb300.autograd import PointValues, Solve
+    pb = wl.varcoef_manufactured(n=(2, 1, 1), W=2)
+    m = api.Mesh(pb.mesh, n_rhs=1, coef_kind=api.COEF_SCALAR)
+    d = api.problem_data_arrays(m, pb)
+    f = torch.tensor(d["f"], device="cuda", requires_grad=True)
+    a = torch.tensor(d["a"], device="cuda", requires_grad=True)
+    ga = torch.tensor(d["grad_a"], device="cuda", requires_grad=True)
+    u = Solve.apply(f, a, ga, m, 1e-13)
+    v = PointValues.apply(u, m)[0]
+    w = torch.empty(m.nquad, dtype=torch.float64, device="cuda")
+    m.quad_weights(w)
+    disc = Discretisation(pb)
+    ut = torch.tensor(_flat(disc, [u_target(*disc.qpoints(e)) for e in range(disc.E)]), device="cuda")
+    J = (w * (v - ut) ** 2).sum()
+    J.backward()
+    # oracle: exact solve, adjoint by Cholesky
+    A = disc.dense_A()
+    Uo = cholesky_solve(A, disc.rhs_b())
+    lam = cholesky_solve(A, l2_misfit_gradient(disc, Uo, u_target))
+    ref = data_gradient(disc, Uo, lam)
+    assert _rel(f.grad.cpu().numpy()[0], _flat(disc, [r[0] for r in ref])) <= 1e-7
+    assert _rel(a.grad.cpu().numpy(), _flat(disc, [r[1] for r in ref])) <= 1e-7
+    for k in range(3):
+        assert _rel(ga.grad.cpu().numpy()[k], _flat(disc, [r[2 + k] for r in ref])) <= 1e-7
+
+
+# ---- coefficient parameters theta of a = exp(g), g = sum theta_ijk L_i L_j L_k ----
+def _legendre(K, t):
+    L = [torch.ones_like(t), t]
+    dL = [torch.zeros_like(t), torch.ones_like(t)]
+    for m in range(1, K):
+        L.append(((2 * m + 1) * t * L[m] - m * L[m - 1]) / (m + 1))
+        dL.append(dL[m - 1] + (2 * m + 1) * L[m])
+    return torch.stack(L[:K + 1]), torch.stack(dL[:K + 1])
+
+
+def coef_from_theta(theta, mesh, ax, elem_prob):
+    """a and grad a at the volume points from theta [n_problem, 4, 4, 4] (torch, differentiable)."""
+    a_parts, g_parts = [], [[], [], []]
+    o = 0
+    for e, W in enumerate(mesh.elem_W):
+        Q = 2 * int(W) + 1
+        t = [2 * torch.tensor(ax[o + k * Q:o + (k + 1) * Q], device=theta.device) - 1 for k in range(3)]
+        o += 3 * Q
+        (Lx, dLx), (Ly, dLy), (Lz, dLz) = (_legendre(3, tt) for tt in t)
+        th = theta[int(elem_prob[e])]
+        g = torch.einsum("ijk,ia,jb,kc->cba", th, Lx, Ly, Lz)
+        gx = 2 * torch.einsum("ijk,ia,jb,kc->cba", th, dLx, Ly, Lz)
+        gy = 2 * torch.einsum("ijk,ia,jb,kc->cba", th, Lx, dLy, Lz)
+        gz = 2 * torch.einsum("ijk,ia,jb,kc->cba", th, Lx, Ly, dLz)
+        aa = torch.exp(g)
+        a_parts.append(aa.reshape(-1))
+        for k, gk in enumerate((gx, gy, gz)):
+            g_parts[k].append((aa * gk).reshape(-1))
+    return torch.cat(a_parts), torch.stack([torch.cat(p) for p in g_parts])
+
+
+def test_theta_gradient_finite_differences(api):
+    from paper_1110_2316_gb300.autograd import PointValues, Solve
+    parts = [wl.lognormal_coef_problem(W, p, n=2) for p, W in enumerate((3, 4, 2))]
+    pb = wl.batch_problems(parts)
+    m = api.Mesh(pb.mesh, n_rhs=1, coef_kind=api.COEF_SCALAR)
+    d = api.problem_data_arrays(m, pb)
+    ax, _ = m.query_points()
+    eprob = pb.mesh.elem_problem
+    disc = Discretisation(pb)
+    ut = torch.tensor(_flat(disc, [u_target(*disc.qpoints(e)) for e in range(disc.E)]), device="cuda")
+    f = torch.tensor(d["f"], device="cuda")
+    qprob = torch.tensor(np.concatenate([np.full((2 * int(W) + 1) ** 3, int(eprob[e]))
+                                         for e, W in enumerate(m.elem_W)]), device="cuda")
+    theta0 = torch.tensor(np.stack([p.meta["theta"] for p in parts]), device="cuda")
+
+    def J_per_problem(theta, grad=False):
+        a, ga = coef_from_theta(theta, m, ax, eprob)
+        u = Solve.apply(f, a, ga, m, 1e-13)
+        v = PointValues.apply(u, m)[0]
+        w = torch.empty(m.nquad, dtype=torch.float64, device="cuda")
+        m.quad_weights(w)
+        contrib = w * (v - ut) ** 2
+        return torch.zeros(len(parts), dtype=torch.float64, device="cuda").index_add(0, qprob, contrib)
+
+    theta = theta0.clone().requires_grad_(True)
+    Jp = J_per_problem(theta)
+    Jp.sum().backward()
+    g = theta.grad.cpu().numpy()
+    h = 1e-3
+    for idx in [(1, 0, 0), (0, 2, 1), (3, 3, 3)]:
+        def central(step):
+            tp, tm = theta0.clone(), theta0.clone()
+            tp[(slice(None),) + idx] += step
+            tm[(slice(None),) + idx] -= step
+            with torch.no_grad():
+                return ((J_per_problem(tp) - J_per_problem(tm)) / (2 * step)).cpu().numpy()
+        fd = (4 * central(h / 2) - central(h)) / 3
+        for p in range(len(parts)):
+            scale = max(abs(fd[p]), 1e-3 * np.abs(g[p]).max())
+            assert abs(g[(p,) + idx] - fd[p]) <= 1e-6 * scale, (p, idx, g[(p,) + idx], fd[p])

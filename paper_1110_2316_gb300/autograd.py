@@ -5,8 +5,9 @@
   hand-written transpose kernel (hpse_apply_transpose).
 * ``PointValues``: u -> u(x_q) at the volume points; backward = the transpose
   of point evaluation (hpse_apply_eval_transpose).
-* ``Solve``: the data (f, a, grad a at the volume points) -> the solution u of
-  the normal equations.  Backward: the adjoint state lambda solves
+* ``Solve``: the data (f, a, grad a at the volume points; Dirichlet data g
+  on the boundary-face points, not differentiated) -> the solution u of the
+  normal equations.  Backward: the adjoint state lambda solves
   A lambda = dJ/du by PCG (recomputed, no iterate is stored; A is symmetric),
   and hpse_data_gradient returns dJ/df, dJ/da, dJ/d(grad a) at the points.
 
@@ -56,10 +57,12 @@ class Solve(torch.autograd.Function):
     """u = A(a)^{-1} b(f, a) for the data sampled at the volume points."""
 
     @staticmethod
-    def forward(ctx, f, a, grad_a, mesh, tol=1e-12, prec=FP64, adjoint_prec=FP64):
-        mesh.set_data(f=f.detach().cpu().numpy(),
-                      a=None if a is None else a.detach().cpu().numpy(),
-                      grad_a=None if grad_a is None else grad_a.detach().cpu().numpy())
+    def forward(ctx, f, a, grad_a, mesh, g=None, tol=1e-12, prec=FP64, adjoint_prec=FP64):
+        def host(t):
+            if t is None:
+                return None
+            return t.detach().cpu().numpy() if isinstance(t, torch.Tensor) else t
+        mesh.set_data(f=host(f), a=host(a), grad_a=host(grad_a), g=host(g))
         x = torch.zeros(mesh.n_rhs * mesh.ndof, dtype=torch.float64, device=f.device)
         mesh.pcg_solve(x, tol=tol, prec=prec)
         ctx.save_for_backward(x)
@@ -86,4 +89,4 @@ class Solve(torch.autograd.Function):
         gf = g[:, 0, :]
         ga = g[:, 1, :].sum(0) if ctx.has_a else None
         gga = g[:, 2:5, :].sum(0) if ctx.has_a else None
-        return gf, ga, gga, None, None, None, None
+        return gf, ga, gga, None, None, None, None, None

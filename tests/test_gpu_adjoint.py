@@ -126,7 +126,7 @@ def test_autograd_solve_gradient_matches_oracle(api):
     f = torch.tensor(d["f"], device="cuda", requires_grad=True)
     a = torch.tensor(d["a"], device="cuda", requires_grad=True)
     ga = torch.tensor(d["grad_a"], device="cuda", requires_grad=True)
-    u = Solve.apply(f, a, ga, m, 1e-12)
+    u = Solve.apply(f, a, ga, m, d["g"], 1e-12)
     v = PointValues.apply(u, m)[0]
     w = torch.empty(m.nquad, dtype=torch.float64, device="cuda")
     m.quad_weights(w)
@@ -193,7 +193,7 @@ def test_theta_gradient_finite_differences(api):
 
     def J_per_problem(theta, grad=False):
         a, ga = coef_from_theta(theta, m, ax, eprob)
-        u = Solve.apply(f, a, ga, m, 1e-12)
+        u = Solve.apply(f, a, ga, m, None, 1e-11)
         v = PointValues.apply(u, m)[0]
         w = torch.empty(m.nquad, dtype=torch.float64, device="cuda")
         m.quad_weights(w)

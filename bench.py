@@ -5,9 +5,10 @@ decaying as 2^-k), homogeneous Dirichlet data.
 
 One step = one full solve of the 64-RHS batch to ||b - A x|| <= 1e-10 ||b||
 (operator applies, preconditioner, PCG updates and FP64 residual refreshes).
-value = operator-apply GDOF/s inside the solve (DOF x operator applies / time);
-ms_per_step = time-to-solution.  The FP64-vs-mixed comparison of the
-time-to-solution is run on the first `--cmp-rhs` right-hand sides.
+value = FP32 operator-apply GDOF/s (DOF of the batch x applies / time, CUDA
+events over 20 applies of the same batch, inputs resident);
+ms_per_step = time-to-solution of one step.  The FP64-vs-mixed comparison of
+the time-to-solution is run on the first `--cmp-rhs` right-hand sides.
 
 Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
 torch.distributed.run (one rank per GPU, independent batches per rank,
@@ -52,6 +53,13 @@ def parse():
     ap.add_argument("--apply-only", action="store_true",
                     help="time only the FP32 operator apply (profiling driver for ncu)")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precond", default="block", choices=["block", "separable"],
+                    help="block: exact element blocks of A (set up once, FP64 factors); "
+                         "separable: the C-form of eq. (5.19)-(5.20)")
+    ap.add_argument("--workload", default="varcoef", choices=["varcoef", "adjoint"],
+                    help="varcoef: the 64-RHS W=8 solve; adjoint: the 256-problem theta-gradient batch")
+    ap.add_argument("--adj-problems", type=int, default=256)
+    ap.add_argument("--adj-fd-problems", type=int, default=16)
     ap.add_argument("--max-iter", type=int, default=60000,
                     help="cap on PCG iterations per solve (a capped solve is for profiling only)")
     return ap.parse_args()
@@ -136,6 +144,14 @@ def volume_flops_per_rhs(Ws):
     return 2.0 * tot
 
 
+# DRAM bytes (read + write) of one FP32 k_apply launch on the default
+# workload (8^3 elements, W = 8, 64 rhs, variable a), from one ncu capture
+# (dram__bytes_read.sum 181,104,128 + dram__bytes_write.sum 130,454,016;
+# profiles/k_apply_fp32_w8_varcoef.md).  Valid for that configuration and the
+# kernel as captured; reported as null for any other configuration.
+APPLY_TRAFFIC_BYTES = {(8, 8, 64): 181104128 + 130454016}
+
+
 def fp32_peak_tflops():
     """152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz maximum SM clock."""
     return 152 * 128 * 2 * 2.07e9 / 1e12
@@ -182,10 +198,136 @@ def run_reference(args):
     return 0
 
 
+def run_adjoint(args, local):
+    """Adjoint batch: 256 independent cube problems (4^3 elements, W_p ~ U{4..10}),
+    a = exp(g), g a degree-3 Legendre field with theta ~ N(0,1) (std of g 0.5),
+    f = 1, u = 0 on the boundary; J = sum_p ||u_p - sin(pi x) sin(pi y) sin(pi z)||^2
+    by quadrature.  dJ/dtheta by the adjoint: forward solve, adjoint PCG solve
+    (recomputed), point gradients from the library, chain to theta in torch.
+    Reports the gradient time (FP64 and mixed), the mixed-vs-FP64 gradient
+    difference, and a central finite-difference check (h = 1e-6, FP64) on 8
+    parameters of the first 16 problems."""
+    import math
+    import torch
+    from paper_1110_2316_gb300.build import build
+    build()
+    from paper_1110_2316_gb300 import api
+    from paper_1110_2316_gb300.autograd import PointValues, Solve
+    from paper_1110_2316_gb300.fields import LegendreLogField
+    dev = torch.device("cuda", local)
+    Ws = wl.adjoint_batch_degrees(args.adj_problems)
+    parts = [wl.lognormal_coef_problem(int(W), p, n=4) for p, W in enumerate(Ws)]
+    theta_all = torch.tensor(np.stack([p.meta["theta"] for p in parts]), device=dev)
+    pi = math.pi
+
+    def context(sub, theta):
+        pb = wl.batch_problems(sub)
+        m = api.Mesh(pb.mesh, n_rhs=1, coef_kind=api.COEF_SCALAR, device=local)
+        fld = LegendreLogField.from_mesh(m, pb.mesh.elem_problem, device=dev)
+        ut = fld.separable(lambda x: torch.sin(pi * x), lambda y: torch.sin(pi * y), lambda z: torch.sin(pi * z))
+        f = torch.ones(1, m.nquad, dtype=torch.float64, device=dev)
+        a, ga = fld(theta)
+        m.set_data(f=f.cpu().numpy(), a=a.cpu().numpy(), grad_a=ga.cpu().numpy())
+        t_p = time.perf_counter()
+        if args.precond == "block":
+            # built once from the data at theta and kept for every later solve
+            m.setup_block_preconditioner()
+        torch.cuda.synchronize()
+        t_p = time.perf_counter() - t_p
+        w = torch.empty(m.nquad, dtype=torch.float64, device=dev)
+        m.quad_weights(w)
+        qprob = torch.tensor(np.repeat(pb.mesh.elem_problem.astype(np.int64),
+                                       [(2 * int(W) + 1) ** 3 for W in pb.mesh.elem_W]), device=dev)
+        return dict(m=m, fld=fld, ut=ut, w=w, qprob=qprob, f=f, P=len(sub),
+                    ndof=m.ndof, nelem=len(pb.mesh.elem_W), t_prec=t_p)
+
+    def J_of(c, v):
+        return torch.zeros(c["P"], dtype=torch.float64, device=dev).index_add(
+            0, c["qprob"], c["w"] * (v - c["ut"]) ** 2)
+
+    def gradient(c, theta, prec, tol):
+        th = theta.clone().requires_grad_(True)
+        a, ga = c["fld"](th)
+        u = Solve.apply(c["f"], a, ga, c["m"], None, tol, prec, prec)
+        Jp = J_of(c, PointValues.apply(u, c["m"])[0])
+        Jp.sum().backward()
+        return Jp.detach(), th.grad.detach()
+
+    def J_fd(c, theta, tol):
+        a, ga = c["fld"](theta)
+        m = c["m"]
+        m.set_data(f=c["f"].cpu().numpy(), a=a.cpu().numpy(), grad_a=ga.cpu().numpy())
+        x = torch.zeros(m.ndof, dtype=torch.float64, device=dev)
+        rep = m.pcg_solve(x, tol=tol, prec=api.FP64, max_iter=3000, raise_on_error=False)
+        fl = torch.empty(1, 5, m.nquad, dtype=torch.float64, device=dev)
+        m.eval_fields(x, fl)
+        return J_of(c, fl[0, 0]), rep
+
+    t0 = time.perf_counter()
+    c = context(parts, theta_all)
+    t_setup = time.perf_counter() - t0
+    gradient(c, theta_all, api.FP32, 1e-10)  # warm-up (graphs, tables)
+    times, grads = {}, {}
+    for name, prec in (("fp64", api.FP64), ("mixed", api.FP32)):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        J, g = gradient(c, theta_all, prec, 1e-10)
+        torch.cuda.synchronize()
+        times[name] = time.perf_counter() - t
+        grads[name] = g
+    gdiff = float(torch.max(torch.linalg.vector_norm((grads["mixed"] - grads["fp64"]).flatten(1), dim=1) /
+                            torch.linalg.vector_norm(grads["fp64"].flatten(1), dim=1)))
+    c["m"].close()
+
+    # finite differences (FP64) on the first problems, 8 parameters each
+    nfd = min(args.adj_fd_problems, len(parts))
+    th0 = theta_all[:nfd].clone()
+    cf = context(parts[:nfd], th0)
+    _, g = gradient(cf, th0, api.FP64, 1e-11)
+    rng = np.random.Generator(np.random.PCG64(8))
+    flat = rng.choice(np.arange(1, 64), size=8, replace=False)
+    idxs = [tuple(int(v) for v in np.unravel_index(i, (4, 4, 4))) for i in flat]
+    h = 1e-6
+    worst, fds, adj, res = 0.0, [], [], []
+    for idx in idxs:
+        tp, tm = th0.clone(), th0.clone()
+        tp[(slice(None),) + idx] += h
+        tm[(slice(None),) + idx] -= h
+        Jp, rp = J_fd(cf, tp, 1e-14)
+        Jm, rm = J_fd(cf, tm, 1e-14)
+        res += [rp["rel_residual"], rm["rel_residual"]]
+        fds.append(((Jp - Jm) / (2 * h)).cpu().numpy())
+        adj.append(g[(slice(None),) + idx].cpu().numpy())
+    fds, adj = np.array(fds), np.array(adj)  # [8, nfd]
+    scale = np.maximum(np.abs(fds), 1e-3 * np.abs(fds).max(axis=0, keepdims=True))
+    ratio = np.abs(adj - fds) / (1e-6 * scale)
+    worst = float(ratio.max())
+    cf["m"].close()
+    line = dict(metric="adjoint theta-gradient time for the batch (forward + adjoint PCG + data gradient)",
+                value=times["mixed"], unit="s", higher_is_better=False, n_gpus=1, data="synthetic",
+                config=dict(workload="adjoint batch: %d cube problems, 4^3 elements each, W ~ U{4..10} (seed 7), "
+                                     "a = exp(degree-3 Legendre field, std 0.5), f = 1, u = 0" % len(parts),
+                            n_problem=len(parts), n_elem=c["nelem"], ndof=c["ndof"],
+                            W_hist={int(w): int((Ws == w).sum()) for w in sorted(set(Ws.tolist()))}),
+                grad_time_s=times, setup_s=t_setup, setup_block_precond_s=c["t_prec"], precond=args.precond,
+                grad_rel_diff_mixed_vs_fp64=gdiff,
+                fd_check=dict(problems=nfd, params=[list(i) for i in idxs], h=h, solve_tol=1e-14,
+                              worst_ratio_to_bound=worst, passed=bool(worst <= 1.0),
+                              bound="|g_adj - g_fd| <= 1e-6 max(|g_fd|, 1e-3 max_params |g_fd|)",
+                              fd_solve_rel_residual_max=float(max(res))))
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "adjoint":
+        import torch
+        _, _, local = dist_env()
+        torch.cuda.set_device(local)
+        return run_adjoint(args, local)
     import torch
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -211,6 +353,12 @@ def main():
     mesh.set_data(**data)
     torch.cuda.synchronize()
     t_setdata = time.perf_counter() - t1
+    t_prec = 0.0
+    if args.precond == "block":
+        t2 = time.perf_counter()
+        mesh.setup_block_preconditioner()
+        torch.cuda.synchronize()
+        t_prec = time.perf_counter() - t2
     n_tot = args.rhs * mesh.ndof
     if args.apply_only:
         dt = torch.float32 if args.prec == "fp32" else torch.float64
@@ -261,7 +409,7 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
     applies = float(np.mean([r["applies"] for r in reps]))
-    value = ws * n_tot * applies / (ms * 1e-3) / 1e9
+    solve_rate = ws * n_tot * applies / (ms * 1e-3) / 1e9
     clocks = clk.summary()
 
     # ---- dominant kernel: FP32 operator apply, timed alone -----------------------
@@ -278,6 +426,12 @@ def main():
     a1.record()
     torch.cuda.synchronize()
     apply_ms = a0.elapsed_time(a1) / na
+    apply_ms_all = apply_ms
+    if ws > 1:
+        t = torch.tensor([apply_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        apply_ms_all = float(t.item())
+    value = ws * n_tot / (apply_ms_all * 1e-3) / 1e9
     alg_flops = volume_flops_per_rhs([int(w) for w in mesh.elem_W]) * args.rhs
     achieved = alg_flops / (apply_ms * 1e-3) / 1e12
     peak = fp32_peak_tflops()
@@ -295,18 +449,36 @@ def main():
     apply64_ms = b0.elapsed_time(b1) / 3
 
     # ---- end to end through the public API (host buffers) -----------------------
-    host_f = torch.from_numpy(data["f"]).pin_memory()
+    # the same metric: each step copies u from pinned host memory, applies the
+    # operator and reads y back
+    host_u = u32.cpu().pin_memory()
+    host_y = torch.empty_like(host_u).pin_memory()
+    du, dy = torch.empty_like(u32), torch.empty_like(u32)
+    ne = 10
+    torch.cuda.synchronize()
+    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h0.record()
+    for _ in range(ne):
+        du.copy_(host_u, non_blocking=True)
+        mesh.apply_operator(du, dy)
+        host_y.copy_(dy, non_blocking=True)
+    h1.record()
+    torch.cuda.synchronize()
+    e2e_apply_ms = h0.elapsed_time(h1) / ne
+    # and a whole solve from host data: set_data from host arrays, solve, x to host
     host_x = torch.empty(n_tot, dtype=torch.float64).pin_memory()
     e0 = time.perf_counter()
-    mesh.set_data(f=host_f.numpy(), a=data["a"], grad_a=data["grad_a"], g=data["g"])
+    mesh.set_data(f=data["f"], a=data["a"], grad_a=data["grad_a"], g=data["g"])
     x.zero_()
     rep_e2e = solve(mesh, x, api.FP32)
     host_x.copy_(x)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - e0
     h2d = data["f"].nbytes + data["a"].nbytes + data["grad_a"].nbytes
-    e2e = dict(value=ws * n_tot * rep_e2e["applies"] / e2e_s / 1e9, unit="GDOF/s", h2d_bytes_per_step=int(h2d),
-               d2h_bytes_per_step=int(host_x.numel() * 8))
+    e2e = dict(value=ws * n_tot / (e2e_apply_ms * 1e-3) / 1e9, unit="GDOF/s",
+               h2d_bytes_per_step=int(host_u.numel() * 4), d2h_bytes_per_step=int(host_y.numel() * 4),
+               solve=dict(tts_s=e2e_s, h2d_bytes=int(h2d), d2h_bytes=int(host_x.numel() * 8),
+                          note="set_data from host arrays + mixed solve + x to host"))
 
     # ---- mixed vs FP64 time-to-solution on a subset of right-hand sides ----------
     cmp = None
@@ -315,6 +487,8 @@ def main():
         sub = wl.Problem(pb.mesh, pb.f[:k], pb.g[:k], pb.a, pb.grad_a)
         ms2 = api.Mesh(sub.mesh, n_rhs=k, coef_kind=api.COEF_SCALAR, device=local)
         ms2.set_data(f=data["f"][:k], a=data["a"], grad_a=data["grad_a"])
+        if args.precond == "block":
+            ms2.setup_block_preconditioner()
         xs = torch.zeros(k * ms2.ndof, dtype=torch.float64, device=dev)
         ms2.pcg_solve(xs, tol=TOL, prec=api.FP64, max_iter=32, raise_on_error=False)  # graph warm-up
         solve(ms2, xs, api.FP32)
@@ -349,13 +523,17 @@ def main():
                         n_elem=args.n ** 3, W=args.W, rhs_per_gpu=args.rhs, dof_per_rhs=mesh.ndof,
                         l2="working set > L2 (FP32 vectors %.0f MB each)" % (n_tot * 4 / 1e6),
                         parallelism="replicas (independent batches per GPU)"),
-            solve=dict(iterations=reps[-1]["iterations"], refreshes=reps[-1]["sweeps"],
+            solve=dict(gdof_applies_per_s=solve_rate, iterations=reps[-1]["iterations"], refreshes=reps[-1]["sweeps"],
                        applies=reps[-1]["applies"], rel_residual=reps[-1]["rel_residual"],
-                       setup_sample_s=t_sample, setup_set_data_s=t_setdata),
+                       setup_sample_s=t_sample, setup_set_data_s=t_setdata,
+                       setup_block_precond_s=t_prec, precond=args.precond),
             tts_comparison=cmp,
             apply_ms=dict(fp32=apply_ms, fp64=apply64_ms),
             roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
-                          traffic=None, kernel="k_apply<COEF_SCALAR> FP32 (W=8)",
+                          traffic=APPLY_TRAFFIC_BYTES.get((args.n, args.W, args.rhs)),
+                          traffic_unit="bytes per launch",
+                          algorithmic_bytes=int(2 * n_tot * 4 + 16 * mesh.nquad),
+                          kernel="k_apply<COEF_SCALAR> FP32 (W=8)",
                           note="algorithmic volume flops (3,5,6)-field sum factorisation; peak = FP32 ALU "
                                "152 SM x 128 lanes x 2 x 2.07 GHz"),
             cpu_baseline=cb, e2e=e2e, gpu_launches=int(launches), clocks=clocks,

@@ -71,6 +71,12 @@ typedef enum {
 
 typedef enum { HPSE_FP64 = 0, HPSE_FP32 = 1 } hpse_prec;
 
+/* Preconditioner used by hpse_apply_preconditioner and hpse_pcg_solve. */
+typedef enum {
+  HPSE_PRECOND_SEPARABLE = 0, /* the C-form of eq. (5.19)-(5.20) (default)          */
+  HPSE_PRECOND_BLOCK = 1      /* exact element blocks A_ee of A (set up explicitly) */
+} hpse_precond_kind;
+
 typedef enum {
   HPSE_COEF_LAPLACE = 0,  /* L u = -Lap u                       */
   HPSE_COEF_SCALAR = 1    /* L u = -div(a grad u), a(x) > 0 given with grad a */
@@ -110,8 +116,10 @@ typedef struct {
                           HPSE_FP64 = plain FP64 PCG;
                           HPSE_FP32 = FP32 applies + FP64 iterative refinement     */
   double inner_tol;    /* HPSE_FP32: refine_mode 0: residual reduction factor of the
-                          FP32 iteration between FP64 residual refreshes (delta);
-                          refine_mode 1: relative tolerance of each inner solve  */
+                          FP32 iteration between FP64 residual refreshes (delta,
+                          in (0,1); otherwise 0.1);
+                          refine_mode 1: relative tolerance of each inner solve
+                          (> 0; otherwise 1e-4)                                   */
   int32_t max_sweeps;  /* cap on refinement sweeps (HPSE_FP32)                     */
   int32_t check_every; /* PCG iterations per host convergence check (CUDA graph)   */
   int32_t zero_init;   /* 1: start from x = 0 (the input x is ignored)             */
@@ -165,6 +173,27 @@ hpse_status hpse_apply_operator(hpse_mesh *m, int32_t prec, const void *u, void 
 /* z = C^{-1} r, the element-block separable preconditioner (eq. 5.19-5.20),
  * for all right-hand sides; r, z device DOF vectors (may not overlap). */
 hpse_status hpse_apply_preconditioner(hpse_mesh *m, int32_t prec, const void *r, void *z, void *stream);
+
+/* Element-block preconditioner (no counterpart in the thesis, which uses the
+ * separable C-form of Section 5.2; this is block Jacobi on the same element
+ * blocks).  Builds, from the data of the last hpse_set_data, the diagonal
+ * block A_ee of the normal operator of eq. (4.2) for every element (volume
+ * term and the element's own side of each face term), factors it
+ * A_ee = L L^T in FP64 and stores X = L^{-1} (packed lower triangle, FP64 and
+ * an FP32 copy); the preconditioner is then z_e = X^T X r_e.  Device memory:
+ * 12 n(n+1)/2 bytes per element with n = (W+1)^3 (3.3 GB for 512 elements of
+ * W = 8), plus two vectors of n_rhs*ndof and, during the call, one FP64 copy
+ * of the blocks and 2 x 64 probe vectors (capped at 2 GB each).  Selects
+ * HPSE_PRECOND_BLOCK on success.  hpse_set_data does not rebuild it (a
+ * preconditioner from older data stays symmetric positive definite, only
+ * less effective).  Synchronous.  Errors: HPSE_ERR_NO_DATA before
+ * hpse_set_data, HPSE_ERR_OOM, HPSE_ERR_BREAKDOWN if a block is not positive
+ * definite to FP64 working accuracy (the separable form stays selected). */
+hpse_status hpse_setup_block_preconditioner(hpse_mesh *m);
+
+/* Choose the preconditioner (hpse_precond_kind).  HPSE_PRECOND_BLOCK needs a
+ * successful hpse_setup_block_preconditioner (else HPSE_ERR_NO_DATA). */
+hpse_status hpse_select_preconditioner(hpse_mesh *m, int32_t kind);
 
 /* Copy the FP64 right-hand side b = S^T M d (device, n_rhs*ndof doubles). */
 hpse_status hpse_get_rhs(hpse_mesh *m, double *b, void *stream);

@@ -93,3 +93,36 @@ def apply_Cinv(disc, R):
         blk = R[disc.off[e]:disc.off[e + 1]].reshape(P, P, P)
         Z[disc.off[e]:disc.off[e + 1]] = apply_Cinv_block(blk, disc.W[e]).ravel()
     return Z
+
+
+# ---------------------------------------------------------------------------
+# Element-block preconditioner (block Jacobi on the element blocks of A).
+# Not the thesis's preconditioner; its plain definition is z_e = A_ee^{-1} r_e
+# with A_ee the rows and columns of element e of the normal operator of
+# eq. (4.2) -- the element's volume term and its own side of every face term.
+# ---------------------------------------------------------------------------
+def element_block(disc, e):
+    """A_ee: column j is (A u)_e for u the j-th unit vector of element e."""
+    n = disc.off[e + 1] - disc.off[e]
+    B = np.zeros((n, n))
+    U = np.zeros(disc.ndof)
+    for j in range(n):
+        U[disc.off[e] + j] = 1.0
+        B[:, j] = np.asarray(disc.element_apply(U, e)).ravel()
+        U[disc.off[e] + j] = 0.0
+    return B
+
+
+def block_factors(disc):
+    """Cholesky factors of every A_ee (scipy cho_factor)."""
+    return [sla.cho_factor(element_block(disc, e), lower=True) for e in range(disc.E)]
+
+
+def apply_block_inverse(disc, R, factors=None):
+    """z_e = A_ee^{-1} r_e on every element."""
+    if factors is None:
+        factors = block_factors(disc)
+    Z = np.zeros_like(R)
+    for e in range(disc.E):
+        Z[disc.off[e]:disc.off[e + 1]] = sla.cho_solve(factors[e], R[disc.off[e]:disc.off[e + 1]])
+    return Z

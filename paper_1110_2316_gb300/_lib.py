@@ -20,6 +20,7 @@ STATUS_NAMES = {
 }
 FP64, FP32 = 0, 1
 COEF_LAPLACE, COEF_SCALAR = 0, 1
+PRECOND_SEPARABLE, PRECOND_BLOCK = 0, 1
 
 
 class MeshDesc(C.Structure):
@@ -61,6 +62,8 @@ SIGNATURES = {
     "hpse_set_data": (C.c_int, [C.c_void_p, C.POINTER(Data)]),
     "hpse_apply_operator": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "hpse_apply_preconditioner": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hpse_setup_block_preconditioner": (C.c_int, [C.c_void_p]),
+    "hpse_select_preconditioner": (C.c_int, [C.c_void_p, C.c_int32]),
     "hpse_get_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "hpse_pcg_solve": (C.c_int, [C.c_void_p, C.POINTER(SolveOpts), C.c_void_p, C.POINTER(SolveReport),
                                  C.c_void_p]),

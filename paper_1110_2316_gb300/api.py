@@ -13,9 +13,10 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import COEF_LAPLACE, COEF_SCALAR, FP32, FP64, check
+from ._lib import COEF_LAPLACE, COEF_SCALAR, FP32, FP64, PRECOND_BLOCK, PRECOND_SEPARABLE, check
 
-__all__ = ["Mesh", "problem_data_arrays", "FP64", "FP32", "COEF_LAPLACE", "COEF_SCALAR"]
+__all__ = ["Mesh", "problem_data_arrays", "FP64", "FP32", "COEF_LAPLACE", "COEF_SCALAR", "PRECOND_SEPARABLE",
+           "PRECOND_BLOCK"]
 
 
 def _ptr(a):
@@ -104,6 +105,14 @@ class Mesh:
         d = _lib.Data(*[None if v is None else v.ctypes.data_as(C.c_void_p) for v in arrs])
         check(self._lib.hpse_set_data(self._h, C.byref(d)), "hpse_set_data")
 
+    # -- preconditioner choice ------------------------------------------------
+    def setup_block_preconditioner(self):
+        """Build and select the element-block preconditioner from the current data."""
+        check(self._lib.hpse_setup_block_preconditioner(self._h), "hpse_setup_block_preconditioner")
+
+    def select_preconditioner(self, kind):
+        check(self._lib.hpse_select_preconditioner(self._h, int(kind)), "hpse_select_preconditioner")
+
     def get_rhs(self, b, stream=None):
         check(self._lib.hpse_get_rhs(self._h, _ptr(b), _stream(stream)), "hpse_get_rhs")
 
@@ -116,9 +125,10 @@ class Mesh:
         check(self._lib.hpse_apply_preconditioner(self._h, _prec_of(r), _ptr(r), _ptr(z), _stream(stream)),
               "hpse_apply_preconditioner")
 
-    def pcg_solve(self, x, tol=1e-10, prec=FP64, max_iter=20000, inner_tol=1e-2, max_sweeps=200,
+    def pcg_solve(self, x, tol=1e-10, prec=FP64, max_iter=20000, inner_tol=0.0, max_sweeps=200,
                   check_every=16, zero_init=True, time_limit_s=0.0, refine_mode=0, stream=None,
                   raise_on_error=True):
+        # inner_tol 0 selects the library default of the refinement mode
         o = _lib.SolveOpts(float(tol), int(max_iter), int(prec), float(inner_tol), int(max_sweeps),
                            int(check_every), 1 if zero_init else 0, float(time_limit_s), int(refine_mode))
         rep = _lib.SolveReport()

@@ -1,0 +1,278 @@
+// Element-block preconditioner: z_e = A_ee^{-1} r_e with A_ee the diagonal
+// block of the normal operator A = S^T M S of eq. (4.2) for element e (its
+// volume term and its own side of every face term).  Not the thesis's
+// preconditioner (Section 5.2, eq. 5.19-5.20, which is kept as the default);
+// a block-Jacobi alternative on the same element blocks.
+//
+// Set-up (FP64): A_ee is probed column by column with the operator kernel in
+// self-only mode (neighbour traces taken as zero), gathered into packed
+// lower-triangular storage (row i holds columns 0..i at offset i(i+1)/2),
+// factored A_ee = L L^T (right-looking Cholesky, one CTA per block) and
+// X = L^{-1} is formed row by row.  The preconditioner is z = X^T (X r): two
+// triangular products, kept in FP64 and rounded to FP32.  Storing the factor
+// rather than A_ee^{-1} keeps the FP32 operator X~^T X~ symmetric positive
+// definite whatever the rounding of X (A_ee^{-1} itself rounded to FP32 loses
+// definiteness once eps32 * kappa(A_ee) approaches 1).
+#pragma once
+
+struct BjArgs {
+  const int32_t *elems;    // element ids of one degree group
+  int32_t n_group;         // elements in the group
+  int32_t n;               // block size (W+1)^3
+  int32_t n_rhs;
+  int64_t ndof;            // stride between right-hand sides of a vector
+  const int64_t *dof_off;  // per element
+  const int64_t *blk_off;  // per element: offset of its packed block
+};
+
+// offset of (i, j), j <= i, inside one packed block (n <= 1331: fits 32 bits)
+__device__ __forceinline__ int pk(int i, int j) { return i * (i + 1) / 2 + j; }
+
+// u[c][off_e + i] = (i == j0 + c) for the group's elements, c < nc
+__global__ void k_bj_probe(BjArgs A, int j0, int nc, double *u) {
+  const int item = blockIdx.x;
+  const int ge = item / nc, c = item - ge * nc;
+  const int e = A.elems[ge];
+  const int64_t base = (int64_t)c * A.ndof + A.dof_off[e];
+  for (int i = threadIdx.x; i < A.n; i += blockDim.x) u[base + i] = (i == j0 + c) ? 1.0 : 0.0;
+}
+
+// column j = j0 + c of every block: rows i >= j into packed storage
+__global__ void k_bj_gather(BjArgs A, int j0, int nc, const double *y, double *blk) {
+  const int item = blockIdx.x;
+  const int ge = item / nc, c = item - ge * nc;
+  const int e = A.elems[ge], j = j0 + c;
+  const int64_t base = (int64_t)c * A.ndof + A.dof_off[e];
+  double *B = blk + A.blk_off[e];
+  for (int i = j + threadIdx.x; i < A.n; i += blockDim.x) B[pk(i, j)] = y[base + i];
+}
+
+// in-place Cholesky A = L L^T of each packed block; fail[0] set (block index
+// + 1) on a non-positive pivot, the block is then left partly factored.
+// Dynamic shared memory: n doubles.
+__global__ void __launch_bounds__(256) k_bj_chol(BjArgs A, double *blk, int32_t *fail) {
+  extern __shared__ double colk[];
+  __shared__ double s_inv;
+  __shared__ int s_bad;
+  const int e = A.elems[blockIdx.x], n = A.n;
+  double *L = blk + A.blk_off[e];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, w = tid >> 5, nw = nt >> 5;
+  if (tid == 0) s_bad = 0;
+  for (int k = 0; k < n; ++k) {
+    if (tid == 0) {
+      double d = L[pk(k, k)];
+      if (!(d > 0.0) || !isfinite(d)) {
+        s_bad = 1;
+        d = 1.0;
+      }
+      d = sqrt(d);
+      L[pk(k, k)] = d;
+      s_inv = 1.0 / d;
+    }
+    __syncthreads();
+    if (s_bad) break;
+    for (int i = k + 1 + tid; i < n; i += nt) {
+      const double v = L[pk(i, k)] * s_inv;
+      L[pk(i, k)] = v;
+      colk[i] = v;
+    }
+    __syncthreads();
+    // trailing update of rows i > k, columns k < j <= i: one warp per row
+    for (int i = k + 1 + w; i < n; i += nw) {
+      const double li = colk[i];
+      double *Li = L + pk(i, 0);
+      for (int j = k + 1 + lane; j <= i; j += 32) Li[j] -= li * colk[j];
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && s_bad) atomicCAS(fail, 0, blockIdx.x + 1);
+}
+
+// X = L^{-1} (packed lower), row by row: X_ii = 1 / L_ii and, for j < i,
+// X_ij = -(sum_{j <= m < i} L_im X_mj) / L_ii.  Dynamic shared memory: n doubles.
+__global__ void __launch_bounds__(256) k_bj_trinv(BjArgs A, const double *blk, double *xout) {
+  extern __shared__ double lrow[];
+  const int e = A.elems[blockIdx.x], n = A.n;
+  const double *L = blk + A.blk_off[e];
+  double *X = xout + A.blk_off[e];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = 0; i < n; ++i) {
+    for (int m = tid; m <= i; m += nt) lrow[m] = L[pk(i, m)];
+    __syncthreads();
+    const double inv = 1.0 / lrow[i];
+    // columns in chunks of nt; rows m of X are read in order, so at each m
+    // the active threads read consecutive addresses of row m
+    for (int j0 = 0; j0 <= i; j0 += nt) {
+      const int j = j0 + tid;
+      double s = 0.0;
+      for (int m = j0; m < i; ++m)
+        if (m >= j) s += lrow[m] * X[pk(m, j)];
+      if (j < i) X[pk(i, j)] = -s * inv;
+      else if (j == i) X[pk(i, i)] = inv;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void k_bj_convert(const double *in, T *out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (T)in[i];
+}
+
+// out_e = X_e in_e (TRANS = false, lower) or X_e^T in_e (TRANS = true) for
+// every element of the group and every right-hand side.  CTA tile: TM rows
+// of one element x RT right-hand sides, k in chunks of 32; thread tile MR x MC
+// with rows tr + TR m and right-hand sides tc + TC c (tr = tid % TR fastest, so
+// the shared reads are conflict-free and the stores coalesced).  The next
+// chunk is fetched into registers while the current one is used.
+// grid: n_group * ceil(n / TM) row tiles (row tile fastest, so the tiles of an
+// element run together and share its vector segment in L2), ceil(n_rhs / RT).
+template <typename T, bool TRANS, int TM, int RT, int TR, int TC>
+__global__ void __launch_bounds__(TR *TC) k_bj_tri(BjArgs A, const T *X, const T *in, T *out) {
+  constexpr int KC = 32, MR = TM / TR, MC = RT / TC, NT = TR * TC;
+  constexpr int NA = (TM * KC + NT - 1) / NT, NB = (KC * RT + NT - 1) / NT;
+  __shared__ T As[KC][TM + 1];
+  __shared__ T Bs[KC][RT + 1];
+  const int n = A.n, nrt = (n + TM - 1) / TM;
+  const int ge = blockIdx.x / nrt, rt = blockIdx.x - ge * nrt;
+  const int e = A.elems[ge];
+  const int i0 = rt * TM, r0 = blockIdx.y * RT;
+  const T *Xe = X + A.blk_off[e];
+  const int64_t vb = A.dof_off[e];
+  const int tid = threadIdx.x, tr = tid % TR, tc = tid / TR;
+  T acc[MR][MC];
+#pragma unroll
+  for (int a = 0; a < MR; ++a)
+#pragma unroll
+    for (int b = 0; b < MC; ++b) acc[a][b] = (T)0;
+  const int kbeg = TRANS ? (i0 / KC) * KC : 0;
+  const int kend = TRANS ? n : min(n, i0 + TM);
+  T ra[NA], rb[NB];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      const int idx = tid + q * NT;
+      int row, kk;
+      if (!TRANS) {
+        row = idx / KC;
+        kk = idx - row * KC;
+      } else {
+        kk = idx / TM;
+        row = idx - kk * TM;
+      }
+      const int i = i0 + row, k = k0 + kk;
+      T v = (T)0;
+      if (idx < TM * KC && i < n && k < n) {
+        if (!TRANS) {
+          if (k <= i) v = Xe[pk(i, k)];
+        } else {
+          if (i <= k) v = Xe[pk(k, i)];
+        }
+      }
+      ra[q] = v;
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int idx = tid + q * NT;
+      const int rr = idx / KC, kk = idx - rr * KC;
+      const int k = k0 + kk, rhs = r0 + rr;
+      rb[q] = (idx < KC * RT && k < n && rhs < A.n_rhs) ? in[(int64_t)rhs * A.ndof + vb + k] : (T)0;
+    }
+  };
+  if (kbeg < kend) fetch(kbeg);
+  for (int k0 = kbeg; k0 < kend; k0 += KC) {
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      const int idx = tid + q * NT;
+      if (idx < TM * KC) {
+        if (!TRANS) As[idx % KC][idx / KC] = ra[q];
+        else As[idx / TM][idx % TM] = ra[q];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int idx = tid + q * NT;
+      if (idx < KC * RT) Bs[idx % KC][idx / KC] = rb[q];
+    }
+    __syncthreads();
+    if (k0 + KC < kend) fetch(k0 + KC);
+#pragma unroll 8
+    for (int kk = 0; kk < KC; ++kk) {
+      T a[MR], b[MC];
+#pragma unroll
+      for (int m = 0; m < MR; ++m) a[m] = As[kk][tr + TR * m];
+#pragma unroll
+      for (int c = 0; c < MC; ++c) b[c] = Bs[kk][tc + TC * c];
+#pragma unroll
+      for (int m = 0; m < MR; ++m)
+#pragma unroll
+        for (int c = 0; c < MC; ++c) acc[m][c] += a[m] * b[c];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int m = 0; m < MR; ++m) {
+    const int i = i0 + tr + TR * m;
+    if (i >= n) continue;
+#pragma unroll
+    for (int c = 0; c < MC; ++c) {
+      const int rhs = r0 + tc + TC * c;
+      if (rhs < A.n_rhs) out[(int64_t)rhs * A.ndof + vb + i] = acc[m][c];
+    }
+  }
+}
+
+// PCG update x += alpha p, r -= alpha q on the group's blocks, partial r.r per
+// (element, rhs).  grid: n_group * n_rhs.
+template <typename T>
+__global__ void k_bj_update(BjArgs A, const int32_t *prob, const double *alpha, T *x, T *r, const T *p, const T *q,
+                            double *part_rr) {
+  const int item = blockIdx.x;
+  const int ge = item / A.n_rhs, rr = item - ge * A.n_rhs;
+  const int e = A.elems[ge];
+  const int64_t base = (int64_t)rr * A.ndof + A.dof_off[e];
+  const T al = (T)alpha[prob[e] * A.n_rhs + rr];
+  double s = 0.0;
+  for (int t = threadIdx.x; t < A.n; t += blockDim.x) {
+    if (x) x[base + t] += al * p[base + t];
+    const T v = r[base + t] - al * q[base + t];
+    r[base + t] = v;
+    s += (double)v * (double)v;
+  }
+  s = block_sum_d(s);
+  if (threadIdx.x == 0) part_rr[(int64_t)e * A.n_rhs + rr] = s;
+}
+
+// partial z.r per (element, rhs) on the group's blocks.  grid: n_group * n_rhs.
+template <typename T>
+__global__ void k_bj_dot(BjArgs A, const T *z, const T *r, double *part) {
+  const int item = blockIdx.x;
+  const int ge = item / A.n_rhs, rr = item - ge * A.n_rhs;
+  const int e = A.elems[ge];
+  const int64_t base = (int64_t)rr * A.ndof + A.dof_off[e];
+  double s = 0.0;
+  for (int t = threadIdx.x; t < A.n; t += blockDim.x) s += (double)z[base + t] * (double)r[base + t];
+  s = block_sum_d(s);
+  if (threadIdx.x == 0) part[(int64_t)e * A.n_rhs + rr] = s;
+}
+
+// z = X^T (X r) for the group; t: scratch vector of the same layout.
+template <typename T>
+static cudaError_t bj_apply_group(const BjArgs &a, const T *X, const T *r, T *t, T *z, cudaStream_t s) {
+  if (a.n_group == 0) return cudaSuccess;
+  if (a.n_rhs >= 32) {
+    dim3 g(a.n_group * ((a.n + 63) / 64), (a.n_rhs + 63) / 64);
+    k_bj_tri<T, false, 64, 64, 16, 16><<<g, 256, 0, s>>>(a, X, r, t);
+    k_bj_tri<T, true, 64, 64, 16, 16><<<g, 256, 0, s>>>(a, X, t, z);
+  } else if (a.n_rhs >= 2) {
+    dim3 g(a.n_group * ((a.n + 127) / 128), (a.n_rhs + 7) / 8);
+    k_bj_tri<T, false, 128, 8, 64, 4><<<g, 256, 0, s>>>(a, X, r, t);
+    k_bj_tri<T, true, 128, 8, 64, 4><<<g, 256, 0, s>>>(a, X, t, z);
+  } else {
+    dim3 g(a.n_group * ((a.n + 127) / 128), a.n_rhs);
+    k_bj_tri<T, false, 128, 1, 128, 1><<<g, 128, 0, s>>>(a, X, r, t);
+    k_bj_tri<T, true, 128, 1, 128, 1><<<g, 128, 0, s>>>(a, X, t, z);
+  }
+  return cudaGetLastError();
+}

@@ -203,6 +203,12 @@ struct hpse_mesh {
   DevBuf d_bnorm2;            // FP64 ||b||^2 per (problem, rhs)
   std::map<int, DevBuf> d_qtab;  // per degree FP64 Q-grid tables for the face data
   bool has_data = false;
+  // element-block preconditioner (hpse_setup_block_preconditioner)
+  int precond_kind = HPSE_PRECOND_SEPARABLE;
+  bool bj_ready = false;
+  DevBuf d_bj_off;            // int64 per element: offset of its packed block
+  DevBuf d_bj64, d_bj32;      // X = L^{-1} per element, packed lower triangle
+  DevBuf bj_t64, bj_t32;      // scratch vector X r of the preconditioner
   int threads[2][2][HPSE_MAX_W + 1];  // [kind][prec][W]
   // one stream per degree group: per-degree launches of one operator or
   // preconditioner application run concurrently (fork/join through events,
@@ -265,6 +271,8 @@ struct ElemVecArgs {
   const int64_t *dof_off;
   const int32_t *elem_W;
 };
+
+#include "block_precond.cuh"
 
 // per (element, rhs) block: generic vector kernels with FP64 partials
 template <typename TA, typename TB>
@@ -806,8 +814,50 @@ static hpse_status launch_apply_all(hpse_mesh *m, int mode, ApplyArgsT<T> base_a
   return HPSE_OK;
 }
 
+static BjArgs bj_args(const hpse_mesh *m, const Group &g, int n_rhs) {
+  BjArgs a;
+  a.elems = g.elems.as<int32_t>();
+  a.n_group = g.n;
+  a.n = (g.W + 1) * (g.W + 1) * (g.W + 1);
+  a.n_rhs = n_rhs;
+  a.ndof = m->ndof;
+  a.dof_off = m->d_dof_off.as<int64_t>();
+  a.blk_off = m->d_bj_off.as<int64_t>();
+  return a;
+}
+
+// element-block preconditioner for every degree group: PCG mode fuses the
+// update x += alpha p, r -= alpha q and the partials r.r, z.r around z = X^T X r
+template <typename T>
+static hpse_status launch_bj_all(hpse_mesh *m, int mode, const PrecArgsT<T> &b, cudaStream_t s) {
+  const T *X = sizeof(T) == 8 ? (const T *)m->d_bj64.p : (const T *)m->d_bj32.p;
+  T *t = sizeof(T) == 8 ? (T *)m->bj_t64.p : (T *)m->bj_t32.p;
+  if (!X || !t) return HPSE_ERR_INVALID_ARG;
+  CK(group_fork(m, s));
+  for (size_t gi = 0; gi < m->groups.size(); ++gi) {
+    const Group &g = m->groups[gi];
+    const BjArgs a = bj_args(m, g, b.n_rhs);
+    cudaStream_t gs = group_stream(m, gi, s);
+    const int items = g.n * b.n_rhs;
+    if (mode == MODE_PCG) {
+      k_bj_update<T><<<items, 128, 0, gs>>>(a, b.prob, b.alpha, b.x, b.r, b.p, b.q, b.part_rr);
+      CK(cudaGetLastError());
+      CK(bj_apply_group<T>(a, X, b.r, t, b.zout, gs));
+      k_bj_dot<T><<<items, 128, 0, gs>>>(a, b.zout, b.r, b.part_rz);
+      CK(cudaGetLastError());
+      g_launches += 4;
+    } else {
+      CK(bj_apply_group<T>(a, X, b.rin, t, b.zout, gs));
+      g_launches += 2;
+    }
+  }
+  CK(group_join(m, s));
+  return HPSE_OK;
+}
+
 template <typename T>
 static hpse_status launch_prec_all(hpse_mesh *m, int mode, PrecArgsT<T> base_args, cudaStream_t s) {
+  if (m->precond_kind == HPSE_PRECOND_BLOCK) return launch_bj_all<T>(m, mode, base_args, s);
   const int pi = sizeof(T) == 8 ? 0 : 1;
   CK(group_fork(m, s));
   for (size_t gi = 0; gi < m->groups.size(); ++gi) {
@@ -1248,6 +1298,98 @@ extern "C" hpse_status hpse_apply_preconditioner(hpse_mesh *m, int32_t prec, con
   a.rin = (const float *)r;
   a.zout = (float *)z;
   return launch_prec_all<float>(m, MODE_PLAIN, a, s);
+}
+
+static void drop_graphs(hpse_mesh *m) {
+  if (!m->work) return;
+  for (auto &g : m->work->graphs) cudaGraphExecDestroy(g.second);
+  m->work->graphs.clear();
+  m->work->graph_launches.clear();
+}
+
+extern "C" hpse_status hpse_setup_block_preconditioner(hpse_mesh *m) {
+  if (!m) return HPSE_ERR_INVALID_ARG;
+  if (!m->has_data) return HPSE_ERR_NO_DATA;
+  CK(cudaSetDevice(m->device));
+  CK(cudaDeviceSynchronize());
+  drop_graphs(m);
+  m->bj_ready = false;
+  m->precond_kind = HPSE_PRECOND_SEPARABLE;
+  const int E = m->n_elem;
+  std::vector<int64_t> off(E + 1, 0);
+  for (int e = 0; e < E; ++e) {
+    const int64_t n = (int64_t)(m->W[e] + 1) * (m->W[e] + 1) * (m->W[e] + 1);
+    off[e + 1] = off[e] + n * (n + 1) / 2;
+  }
+  const int64_t total = off[E];
+  CK(upload(m->d_bj_off, off));
+  DevBuf blk;
+  if (blk.alloc(std::max<int64_t>(total, 1) * sizeof(double)) != cudaSuccess) return HPSE_ERR_OOM;
+  if (m->d_bj64.alloc(std::max<int64_t>(total, 1) * sizeof(double)) != cudaSuccess) return HPSE_ERR_OOM;
+  if (m->d_bj32.alloc(std::max<int64_t>(total, 1) * sizeof(float)) != cudaSuccess) return HPSE_ERR_OOM;
+  const size_t nv = (size_t)m->n_rhs * m->ndof;
+  if (m->bj_t64.alloc(std::max<size_t>(nv, 1) * sizeof(double)) != cudaSuccess) return HPSE_ERR_OOM;
+  if (m->bj_t32.alloc(std::max<size_t>(nv, 1) * sizeof(float)) != cudaSuccess) return HPSE_ERR_OOM;
+  DevBuf fail;
+  CK(fail.alloc(sizeof(int32_t)));
+  CK(cudaMemset(fail.p, 0, sizeof(int32_t)));
+  // probes: nc unit vectors per launch, each in every element of a group at once
+  const size_t maxbytes = (size_t)1 << 31;
+  int nc = (int)std::min<size_t>(64, std::max<size_t>(1, maxbytes / (std::max<int64_t>(m->ndof, 1) * sizeof(double))));
+  DevBuf pu, py;
+  if (pu.alloc((size_t)nc * std::max<int64_t>(m->ndof, 1) * sizeof(double)) != cudaSuccess) return HPSE_ERR_OOM;
+  if (py.alloc((size_t)nc * std::max<int64_t>(m->ndof, 1) * sizeof(double)) != cudaSuccess) return HPSE_ERR_OOM;
+  cudaStream_t s = 0;
+  for (size_t gi = 0; gi < m->groups.size(); ++gi) {
+    const Group &g = m->groups[gi];
+    const int n = (g.W + 1) * (g.W + 1) * (g.W + 1);
+    BjArgs ba = bj_args(m, g, nc);
+    ApplyArgsT<double> a = apply_args<double>(m, g, pu.as<double>(), py.as<double>());
+    a.n_rhs = nc;
+    a.self_only = 1;
+    const KernelSet &ks = g_sets[0][g.W];
+    const int th = m->threads[0][0][g.W];
+    for (int j0 = 0; j0 < n; j0 += nc) {
+      const int c = std::min(nc, n - j0);
+      a.n_rhs = c;
+      ba.n_rhs = c;
+      k_bj_probe<<<g.n * c, 128, 0, s>>>(ba, j0, c, pu.as<double>());
+      CK(cudaGetLastError());
+      CK(ks.apply(m->coef_kind, MODE_PLAIN, &a, g.n * c, th, s));
+      k_bj_gather<<<g.n * c, 128, 0, s>>>(ba, j0, c, py.as<double>(), blk.as<double>());
+      CK(cudaGetLastError());
+      g_launches += 3;
+    }
+    const size_t sm = (size_t)n * sizeof(double);
+    CK(cudaFuncSetAttribute(k_bj_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(sm, 1)));
+    CK(cudaFuncSetAttribute(k_bj_trinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(sm, 1)));
+    k_bj_chol<<<g.n, 256, sm, s>>>(ba, blk.as<double>(), fail.as<int32_t>());
+    CK(cudaGetLastError());
+    k_bj_trinv<<<g.n, 256, sm, s>>>(ba, blk.as<double>(), m->d_bj64.as<double>());
+    CK(cudaGetLastError());
+    g_launches += 2;
+  }
+  if (total > 0) {
+    k_bj_convert<float><<<1024, 256, 0, s>>>(m->d_bj64.as<double>(), m->d_bj32.as<float>(), total);
+    CK(cudaGetLastError());
+    ++g_launches;
+  }
+  int32_t h_fail = 0;
+  CK(cudaMemcpy(&h_fail, fail.p, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (h_fail) return HPSE_ERR_BREAKDOWN;
+  m->bj_ready = true;
+  m->precond_kind = HPSE_PRECOND_BLOCK;
+  return HPSE_OK;
+}
+
+extern "C" hpse_status hpse_select_preconditioner(hpse_mesh *m, int32_t kind) {
+  if (!m || (kind != HPSE_PRECOND_SEPARABLE && kind != HPSE_PRECOND_BLOCK)) return HPSE_ERR_INVALID_ARG;
+  if (kind == HPSE_PRECOND_BLOCK && !m->bj_ready) return HPSE_ERR_NO_DATA;
+  CK(cudaSetDevice(m->device));
+  CK(cudaDeviceSynchronize());
+  drop_graphs(m);
+  m->precond_kind = kind;
+  return HPSE_OK;
 }
 
 extern "C" hpse_status hpse_set_block_threads(hpse_mesh *m, int32_t kind, int32_t prec, int32_t W, int32_t threads) {

@@ -155,7 +155,10 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
     for (int k = 0; k < P; ++k) s += Ds[nend * P + k] * su[fidx(a, k, p1, p2)];
     FSLOT(f, sN)[sp] = s;
     const int nb = A.nbr[(int64_t)e * 6 + f];
-    if (nb >= 0) {
+    if (nb >= 0 && A.self_only) {
+      FSLOT(f, sFn)[sp] = (real)0;
+      FSLOT(f, sNn)[sp] = (real)0;
+    } else if (nb >= 0) {
       const int64_t base = (int64_t)r * A.ndof + A.dof_off[nb];
       const real bt = (MODE == MODE_PCG) ? (real)A.beta[A.prob[nb] * A.n_rhs + r] : (real)0;
       const int nn = P - 1 - nend;

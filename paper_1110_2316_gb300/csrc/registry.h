@@ -31,6 +31,7 @@ struct ApplyArgsT {
   double *partial;
   const double *rho;
   int32_t skip_faces;
+  int32_t self_only;        // 1: neighbour traces taken as zero (diagonal blocks of A)
 };
 
 template <typename T>

@@ -59,3 +59,42 @@ def test_fast_diagonalisation_inverts_C(W):
     ev = np.sort(np.linalg.eigvals(np.linalg.solve(FFF, C)).real)
     sig = np.sort((mu[:, None, None] + mu[None, :, None] + mu[None, None, :] + 1).ravel())
     assert np.allclose(ev, sig, rtol=1e-8)
+
+
+# ---- element-block preconditioner (block Jacobi on the blocks of A) ----------
+def _tiny(n, W):
+    import workloads as wl
+    from oracle.functional import Discretisation
+    return Discretisation(wl.varcoef_manufactured(n=n, W=W))
+
+
+def test_block_on_one_element_is_the_exact_inverse():
+    from oracle.precond import apply_block_inverse
+    d = _tiny((1, 1, 1), 3)  # one element: A = A_ee
+    x = np.random.default_rng(3).standard_normal(d.ndof)
+    z = apply_block_inverse(d, d.apply_A(x))
+    assert np.linalg.norm(z - x) <= 1e-9 * np.linalg.norm(x)
+
+
+def test_blocks_are_the_diagonal_blocks_of_A_and_spd():
+    from oracle.precond import element_block
+    d = _tiny((2, 1, 1), 2)
+    A = d.dense_A()
+    for e in range(d.E):
+        s = slice(d.off[e], d.off[e + 1])
+        B = element_block(d, e)
+        assert np.abs(B - A[s, s]).max() <= 1e-13 * np.abs(A).max()
+        assert np.abs(B - B.T).max() <= 1e-12 * np.abs(B).max()
+        assert np.linalg.eigvalsh(0.5 * (B + B.T)).min() > 0
+
+
+def test_block_pcg_reaches_the_cholesky_solution():
+    from oracle.pcg import cholesky_solve, pcg
+    from oracle.precond import apply_block_inverse, block_factors
+    d = _tiny((2, 2, 1), 2)
+    b = d.rhs_b()
+    fac = block_factors(d)
+    x, it, rel = pcg(d.apply_A, lambda r: apply_block_inverse(d, r, fac), b, tol=1e-12)
+    xc = cholesky_solve(d.dense_A(), b)
+    assert rel <= 1e-12
+    assert np.linalg.norm(x - xc) <= 1e-8 * np.linalg.norm(xc)

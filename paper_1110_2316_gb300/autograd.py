@@ -10,6 +10,10 @@
   normal equations.  Backward: the adjoint state lambda solves
   A lambda = dJ/du by PCG (recomputed, no iterate is stored; A is symmetric),
   and hpse_data_gradient returns dJ/df, dJ/da, dJ/d(grad a) at the points.
+  The adjoint right-hand side of a solution functional lies mostly in the
+  low end of A's spectrum, so its attainable relative residual is about
+  eps kappa(A), above that of the forward solve: ``adjoint_tol`` (default:
+  the forward ``tol``) sets it separately.
 
 All tensors are CUDA float64 tensors; shapes: u [n_rhs * ndof], z and f
 [n_rhs, nquad], a [nquad], grad_a [3, nquad].
@@ -57,16 +61,19 @@ class Solve(torch.autograd.Function):
     """u = A(a)^{-1} b(f, a) for the data sampled at the volume points."""
 
     @staticmethod
-    def forward(ctx, f, a, grad_a, mesh, g=None, tol=1e-12, prec=FP64, adjoint_prec=FP64):
+    def forward(ctx, f, a, grad_a, mesh, g=None, tol=1e-12, prec=FP64, adjoint_prec=FP64, adjoint_tol=None):
         def host(t):
             if t is None:
                 return None
             return t.detach().cpu().numpy() if isinstance(t, torch.Tensor) else t
         mesh.set_data(f=host(f), a=host(a), grad_a=host(grad_a), g=host(g))
         x = torch.zeros(mesh.n_rhs * mesh.ndof, dtype=torch.float64, device=f.device)
-        mesh.pcg_solve(x, tol=tol, prec=prec)
+        rep = mesh.pcg_solve(x, tol=tol, prec=prec)
+        if isinstance(getattr(mesh, "solve_log", None), list):
+            mesh.solve_log.append(("forward", rep))
         ctx.save_for_backward(x)
-        ctx.mesh, ctx.tol, ctx.adjoint_prec = mesh, tol, adjoint_prec
+        ctx.mesh, ctx.adjoint_prec = mesh, adjoint_prec
+        ctx.tol = tol if adjoint_tol is None else adjoint_tol
         ctx.has_a = a is not None
         return x
 
@@ -78,7 +85,9 @@ class Solve(torch.autograd.Function):
         m.get_rhs(b)
         m.set_rhs(gx.contiguous())
         lam = torch.zeros_like(x)
-        m.pcg_solve(lam, tol=ctx.tol, prec=ctx.adjoint_prec)
+        rep = m.pcg_solve(lam, tol=ctx.tol, prec=ctx.adjoint_prec)
+        if isinstance(getattr(m, "solve_log", None), list):
+            m.solve_log.append(("adjoint", rep))
         m.set_rhs(b)
         uf = torch.empty(m.n_rhs, 5, m.nquad, dtype=torch.float64, device=x.device)
         lf = torch.empty_like(uf)
@@ -89,4 +98,4 @@ class Solve(torch.autograd.Function):
         gf = g[:, 0, :]
         ga = g[:, 1, :].sum(0) if ctx.has_a else None
         gga = g[:, 2:5, :].sum(0) if ctx.has_a else None
-        return gf, ga, gga, None, None, None, None, None
+        return gf, ga, gga, None, None, None, None, None, None

@@ -48,8 +48,9 @@ def u_target(xs, ys, zs):
     return np.sin(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z)
 
 
-def test_fields_residual_transpose_match_oracle(api):
-    pb = wl.varcoef_manufactured(n=(2, 2, 1), W=4)
+@pytest.mark.parametrize("n,W", [((2, 2, 1), 4), ((2, 1, 1), 7), ((1, 1, 2), 10)])
+def test_fields_residual_transpose_match_oracle(api, n, W):
+    pb = wl.varcoef_manufactured(n=n, W=W)
     m = _mesh(api, pb)
     disc = Discretisation(pb)
     U = wl.random_dofs(m.ndof, seed=4)
@@ -78,8 +79,9 @@ def test_fields_residual_transpose_match_oracle(api):
     assert _rel(y.cpu().numpy(), _flat(disc, yref)) <= 1e-12
 
 
-def test_adjoint_identities(api):
-    pb = wl.varcoef_manufactured(n=(2, 1, 2), W=3)
+@pytest.mark.parametrize("W", [3, 9])
+def test_adjoint_identities(api, W):
+    pb = wl.varcoef_manufactured(n=(2, 1, 2), W=W)
     m = _mesh(api, pb)
     rng = np.random.default_rng(5)
     u = torch.tensor(rng.standard_normal(m.ndof), device="cuda")
@@ -100,8 +102,9 @@ def test_adjoint_identities(api):
     assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0)
 
 
-def test_data_gradient_matches_oracle(api):
-    pb = wl.varcoef_manufactured(n=(2, 1, 1), W=3)
+@pytest.mark.parametrize("W", [3, 6, 10])
+def test_data_gradient_matches_oracle(api, W):
+    pb = wl.varcoef_manufactured(n=(2, 1, 1), W=W)
     m = _mesh(api, pb)
     disc = Discretisation(pb)
     rng = np.random.default_rng(8)

@@ -124,7 +124,9 @@ __global__ void k_bj_convert(const double *in, T *out, int64_t n) {
 // every element of the group and every right-hand side.  CTA tile: TM rows
 // of one element x RT right-hand sides, k in chunks of 32; thread tile MR x MC
 // with rows tr + TR m and right-hand sides tc + TC c (tr = tid % TR fastest, so
-// the shared reads are conflict-free and the stores coalesced).  The next
+// the shared reads are conflict-free and the stores coalesced; FP32 4 x 4
+// tiles instead take 4 consecutive rows / right-hand sides per thread and read
+// them with one 16-byte shared load each).  The next
 // chunk is fetched into registers while the current one is used.
 // grid: n_group * ceil(n / TM) row tiles (row tile fastest, so the tiles of an
 // element run together and share its vector segment in L2), ceil(n_rhs / RT).
@@ -132,8 +134,12 @@ template <typename T, bool TRANS, int TM, int RT, int TR, int TC>
 __global__ void __launch_bounds__(TR *TC) k_bj_tri(BjArgs A, const T *X, const T *in, T *out) {
   constexpr int KC = 32, MR = TM / TR, MC = RT / TC, NT = TR * TC;
   constexpr int NA = (TM * KC + NT - 1) / NT, NB = (KC * RT + NT - 1) / NT;
-  __shared__ T As[KC][TM + 1];
-  __shared__ T Bs[KC][RT + 1];
+  // FP32 4 x 4 thread tiles read their operands as float4: rows 4 tr + m and
+  // right-hand sides 4 tc + c, rows of the tiles padded to 16 bytes
+  constexpr bool VEC = sizeof(T) == 4 && MR == 4 && MC == 4;
+  constexpr int PADA = VEC ? 4 : 1, PADB = VEC ? 4 : 1;
+  __shared__ __align__(16) T As[KC][TM + PADA];
+  __shared__ __align__(16) T Bs[KC][RT + PADB];
   const int n = A.n, nrt = (n + TM - 1) / TM;
   const int ge = blockIdx.x / nrt, rt = blockIdx.x - ge * nrt;
   const int e = A.elems[ge];
@@ -200,10 +206,17 @@ __global__ void __launch_bounds__(TR *TC) k_bj_tri(BjArgs A, const T *X, const T
 #pragma unroll 8
     for (int kk = 0; kk < KC; ++kk) {
       T a[MR], b[MC];
+      if constexpr (VEC) {
+        const float4 av = *reinterpret_cast<const float4 *>(&As[kk][4 * tr]);
+        const float4 bv = *reinterpret_cast<const float4 *>(&Bs[kk][4 * tc]);
+        a[0] = av.x; a[1] = av.y; a[2] = av.z; a[3] = av.w;
+        b[0] = bv.x; b[1] = bv.y; b[2] = bv.z; b[3] = bv.w;
+      } else {
 #pragma unroll
-      for (int m = 0; m < MR; ++m) a[m] = As[kk][tr + TR * m];
+        for (int m = 0; m < MR; ++m) a[m] = As[kk][tr + TR * m];
 #pragma unroll
-      for (int c = 0; c < MC; ++c) b[c] = Bs[kk][tc + TC * c];
+        for (int c = 0; c < MC; ++c) b[c] = Bs[kk][tc + TC * c];
+      }
 #pragma unroll
       for (int m = 0; m < MR; ++m)
 #pragma unroll
@@ -213,11 +226,11 @@ __global__ void __launch_bounds__(TR *TC) k_bj_tri(BjArgs A, const T *X, const T
   }
 #pragma unroll
   for (int m = 0; m < MR; ++m) {
-    const int i = i0 + tr + TR * m;
+    const int i = i0 + (VEC ? 4 * tr + m : tr + TR * m);
     if (i >= n) continue;
 #pragma unroll
     for (int c = 0; c < MC; ++c) {
-      const int rhs = r0 + tc + TC * c;
+      const int rhs = r0 + (VEC ? 4 * tc + c : tc + TC * c);
       if (rhs < A.n_rhs) out[(int64_t)rhs * A.ndof + vb + i] = acc[m][c];
     }
   }

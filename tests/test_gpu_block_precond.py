@@ -16,7 +16,7 @@ import torch
 import workloads as wl
 from oracle.functional import Discretisation
 from oracle.pcg import cholesky_solve
-from oracle.precond import apply_block_inverse, element_block
+from oracle.precond import apply_block_inverse, block_factors, element_block
 
 pytestmark = pytest.mark.gpu
 
@@ -125,4 +125,37 @@ def test_block_preconditioner_errors(api):
     m.setup_block_preconditioner()
     m.select_preconditioner(api.PRECOND_SEPARABLE)
     m.select_preconditioner(api.PRECOND_BLOCK)
+    m.close()
+
+
+@pytest.mark.parametrize("n_rhs", [5, 33, 70])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_block_apply_many_rhs(api, n_rhs, prec):
+    # the three tile shapes of the triangular products (1, 2..31 and >= 32
+    # right-hand sides), with ragged right-hand-side tiles
+    base = wl.varcoef_manufactured(n=(2, 1, 1), W=3)
+    pb = wl.Problem(base.mesh, base.f * n_rhs, base.g * n_rhs, base.a, base.grad_a)
+    disc = Discretisation(base)
+    m = _mesh(api, pb, n_rhs)
+    m.setup_block_preconditioner()
+    R = wl.random_dofs(n_rhs * disc.ndof, 11).reshape(n_rhs, disc.ndof)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    rt = torch.tensor(R.ravel(), dtype=dt, device="cuda")
+    z = torch.empty_like(rt)
+    m.apply_preconditioner(rt, z)
+    z = z.double().cpu().numpy().reshape(n_rhs, disc.ndof)
+    blocks = [element_block(disc, e) for e in range(disc.E)]
+    Xs = [np.linalg.inv(np.linalg.cholesky(B)) for B in blocks]
+    fac = block_factors(disc)
+    for k in range(n_rhs):
+        zo = apply_block_inverse(disc, R[k], fac)
+        for e in range(disc.E):
+            s = slice(disc.off[e], disc.off[e + 1])
+            n = blocks[e].shape[0]
+            if prec == "fp64":
+                bound = n * EPS64 * np.linalg.cond(blocks[e]) * np.linalg.norm(zo[s])
+            else:
+                X = Xs[e]
+                bound = 2 * n * EPS32 * np.linalg.norm(np.abs(X).T @ (np.abs(X) @ np.abs(R[k][s])))
+            assert np.linalg.norm(z[k][s] - zo[s]) <= bound, (n_rhs, prec, k, e)
     m.close()

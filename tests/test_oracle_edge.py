@@ -1,0 +1,99 @@
+"""Pins of the edge-neighbourhood oracle (eq. 4.7 in modified coordinates).
+
+* Face-norm weights against hand-computed integrals of eq. (2.34) in the
+  modified coordinates (linear traces, whose difference quotients are 1).
+* A polynomial solution inside the discrete space (with its corner trace)
+  makes R vanish and is returned by the normal equations.
+* The variation identity R(U + eps V) = R(U) + 2 eps V^T (A U - b) + eps^2 V^T A V
+  between the literal functional (norms summed term by term) and the
+  matrix-free normal operator, with Dirichlet data and the corner set.
+* A symmetric positive definite (brute force on a tiny mesh).
+* The H^1 error for the edge singularity of Table 6.18 (u = r^(1/3)
+  sin(theta/3) x3) is of the table's order at W = 2 and decays from W = 2 to
+  W = 3 at least as fast as the table's (slow-marked).
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle.edge import EdgeDiscretisation, face_form
+from oracle.gll import gll
+
+
+def _norm(disc, e, fi, v):
+    Qf = disc.Qf(e)
+    return float(v.ravel() @ face_form(Qf, *disc.norm_weights(e, fi)) @ v.ravel())
+
+
+def test_face_norm_weights_closed_forms():
+    pb = wl.edge_laplace_singular(N=2, W=3)
+    d = EdgeDiscretisation(pb)
+    e = 1
+    ht, hth, hz = d.h(e) / 2.0
+    Qf = d.Qf(e)
+    x, _ = gll(Qf)
+    one = np.ones(Qf)
+    # face x3 = const (axis 2; t1 = tau, t2 = theta): v = tau - tau_c
+    G = d.G(e, 5)
+    assert G == pytest.approx(np.exp(d.mesh.elem_hi[e, 0]))
+    v = np.outer(one, ht * x)  # [t2 = theta, t1 = tau]
+    assert _norm(d, e, 5, v) == pytest.approx(G * (4 * hth * ht ** 3 / 3 + 8 * hth * ht ** 2), rel=1e-12)
+    # face tau = const (axis 0; t1 = theta, t2 = x3): v = x3 - x3_c
+    G = d.G(e, 1)
+    v = np.outer(hz * x, one)  # [t2 = x3, t1 = theta]
+    assert _norm(d, e, 1, v) == pytest.approx(4 * hth * hz ** 3 / 3 + G * 8 * hth * hz ** 2, rel=1e-12)
+    # face theta = const (axis 1; t1 = tau, t2 = x3): v = tau - tau_c, no G on the tau quotient
+    v = np.outer(one, ht * x)  # [t2 = x3, t1 = tau]
+    assert _norm(d, e, 3, v) == pytest.approx(4 * hz * ht ** 3 / 3 + 8 * hz * ht ** 2, rel=1e-12)
+
+
+def test_polynomial_solution_is_reproduced():
+    pb = wl.edge_polynomial(N=2, W=2)
+    d = EdgeDiscretisation(pb)
+    U = d.nodal_interpolant(pb.u_exact)
+    R0 = d.functional(np.zeros(d.ndof))
+    assert d.functional(U) <= 1e-22 * R0
+    A, b = d.dense_A(), d.rhs_b()
+    x = np.linalg.solve(A, b)
+    assert np.linalg.norm(x - U) <= 1e-8 * np.linalg.norm(U)
+
+
+def test_variation_identity_and_spd():
+    pb = wl.edge_laplace_singular(N=2, W=2)
+    d = EdgeDiscretisation(pb)
+    rng = np.random.default_rng(7)
+    U, V = rng.standard_normal(d.ndof), rng.standard_normal(d.ndof)
+    A = d.dense_A()
+    b = d.rhs_b()
+    assert np.abs(A - A.T).max() <= 1e-11 * np.abs(A).max()
+    assert np.linalg.eigvalsh(0.5 * (A + A.T)).min() > 0
+    for eps in (0.3, -1.7):
+        lhs = d.functional(U + eps * V)
+        rhs = d.functional(U) + 2 * eps * V @ (A @ U - b) + eps ** 2 * V @ A @ V
+        assert lhs == pytest.approx(rhs, rel=1e-10)
+
+
+def _h1_rel(W):
+    # layers: N = 2W + 4 (the thesis takes N proportional to W; with this rule
+    # the corner error r_1^(1/3) = mu^(N/3) matches the table's magnitudes)
+    from oracle.pcg import pcg
+    pb = wl.edge_laplace_singular(N=2 * W + 4, W=W)
+    d = EdgeDiscretisation(pb)
+    x, _, rel = pcg(d.apply_A, lambda r: r, d.rhs_b(), tol=1e-10, maxit=20000)
+    assert rel <= 1e-10
+    err, nrm = d.h1_error_exact(x)
+    return np.sqrt(err / nrm)
+
+
+def test_h1_error_matches_table_6_18_order():
+    # Table 6.18, relative H1 error (%) at W = 2: 0.464542
+    e2 = _h1_rel(2)
+    assert 0.464542e-2 / 5 < e2 < 0.464542e-2 * 5, e2
+
+
+@pytest.mark.slow
+def test_h1_error_decays_exponentially_in_W():
+    # Table 6.18: W = 2 0.464542 %, W = 3 0.131359 %
+    e2, e3 = _h1_rel(2), _h1_rel(3)
+    assert e3 < 0.3 * e2
+    assert 0.131359e-2 / 5 < e3 < 0.131359e-2 * 5, e3

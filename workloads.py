@@ -429,3 +429,134 @@ def adjoint_batch(n_problem=256, n=4, seed_w=7, seed_theta=100, wmin=4, wmax=10)
     degrees W_p ~ U{wmin..wmax} (PCG64(seed_w)), theta from PCG64(seed_theta + p)."""
     Ws = adjoint_batch_degrees(n_problem, seed_w, wmin, wmax)
     return batch_problems([lognormal_coef_problem(int(W), p, n=n, seed=seed_theta) for p, W in enumerate(Ws)])
+
+
+# ---------------------------------------------------------------------------
+# Edge neighbourhood (Section 2.3 / eq. 4.7): elements are boxes in the modified
+# coordinates (tau, theta, x3) = (ln r, theta, x3) around an edge on the x3 axis
+# ---------------------------------------------------------------------------
+@dataclass
+class EdgeMeshDesc:
+    """Geometric mesh of an edge neighbourhood {0 < r < Z, th0 < theta < th1, z0 < x3 < z1}.
+
+    Finite elements are boxes [ln r_i, ln r_{i+1}] x [theta_j, theta_{j+1}] x
+    [x3_n, x3_{n+1}] in modified coordinates with r_i = Z mu^(N+1-i),
+    i = 1..N+1 (layer i = 1 is next to the edge).  The corner elements
+    r < r_1 hold one polynomial in x3 per x3-slab n, shared by every theta
+    sector (corner set n).  Face codes in elem_nbr: >= 0 neighbour element,
+    -1 Dirichlet face, -2 - n the corner set n (the r = r_1 face of layer 1).
+    """
+    elem_lo: np.ndarray        # [E, 3] (tau, theta, x3) lower corner
+    elem_hi: np.ndarray        # [E, 3]
+    elem_W: np.ndarray         # [E] int32
+    elem_nbr: np.ndarray       # [E, 6] int32
+    elem_problem: np.ndarray   # [E] int32
+    corner_W: np.ndarray       # [C] int32, degree of each corner polynomial in x3
+    corner_lo: np.ndarray      # [C] x3 lower end of the slab
+    corner_hi: np.ndarray      # [C] x3 upper end
+    corner_problem: np.ndarray  # [C] int32
+    n_problem: int = 1
+
+    @property
+    def n_elem(self) -> int:
+        return int(self.elem_W.shape[0])
+
+    @property
+    def n_corner(self) -> int:
+        return int(self.corner_W.shape[0])
+
+
+def edge_mesh(N, W, mu=0.15, Z=1.0, theta=(0.0, PI / 2), x3=(0.0, 1.0), I=1, J=1) -> EdgeMeshDesc:
+    """N finite layers x I theta-sectors x J x3-slabs (degree W in every
+    modified coordinate) plus J corner sets of degree W; every outer face of
+    the finite elements (r = Z, theta = theta_0 / theta_1, x3 = x3_0 / x3_1) is
+    Dirichlet.  Elements are numbered layer fastest, then sector, then slab."""
+    r = [Z * mu ** (N + 1 - i) for i in range(1, N + 2)]
+    taus = np.log(np.array(r))
+    ths = np.linspace(theta[0], theta[1], I + 1)
+    zs = np.linspace(x3[0], x3[1], J + 1)
+    E = N * I * J
+    lo = np.zeros((E, 3))
+    hi = np.zeros((E, 3))
+    nbr = -np.ones((E, 6), dtype=np.int32)
+
+    def eid(i, j, n):
+        return (n * I + j) * N + i
+
+    for n in range(J):
+        for j in range(I):
+            for i in range(N):
+                e = eid(i, j, n)
+                lo[e] = (taus[i], ths[j], zs[n])
+                hi[e] = (taus[i + 1], ths[j + 1], zs[n + 1])
+                nbr[e, 0] = eid(i - 1, j, n) if i > 0 else -2 - n
+                nbr[e, 1] = eid(i + 1, j, n) if i < N - 1 else -1
+                nbr[e, 2] = eid(i, j - 1, n) if j > 0 else -1
+                nbr[e, 3] = eid(i, j + 1, n) if j < I - 1 else -1
+                nbr[e, 4] = eid(i, j, n - 1) if n > 0 else -1
+                nbr[e, 5] = eid(i, j, n + 1) if n < J - 1 else -1
+    return EdgeMeshDesc(lo, hi, np.full(E, W, dtype=np.int32), nbr, np.zeros(E, dtype=np.int32),
+                        np.full(J, W, dtype=np.int32), zs[:-1].copy(), zs[1:].copy(), np.zeros(J, dtype=np.int32))
+
+
+@dataclass
+class EdgeProblem:
+    """-Lap u = f in the edge neighbourhood, u = g on its Dirichlet faces.
+
+    Data are functions of cylindrical coordinates on tensor grids:
+    fun(rs, thetas, x3s) -> array [len x3s, len thetas, len rs] (r fastest).
+    """
+    mesh: EdgeMeshDesc
+    f: List[Callable]
+    g: List[Callable]
+    u_exact: Optional[Callable] = None
+    grad_exact: Optional[Callable] = None  # (u_r, u_theta / r, u_x3) on tensor grids
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+
+def _cyl_grid(rs, ts, zs):
+    z, t, r = np.meshgrid(np.asarray(zs, dtype=np.float64), np.asarray(ts, dtype=np.float64),
+                          np.asarray(rs, dtype=np.float64), indexing="ij")
+    return r, t, z
+
+
+def edge_laplace_singular(N, W, mu=0.15, alpha=1.0 / 3.0) -> EdgeProblem:
+    """Table 6.18: Lap u = 0 on {0 < r < 1, 0 < theta < pi/2, 0 < x3 < 1},
+    u = g on the boundary with the exact solution w = r^alpha sin(alpha theta) x3
+    (alpha = 1/3, an edge singularity along the x3 axis)."""
+    mesh = edge_mesh(N, W, mu=mu)
+
+    def w(rs, ts, zs):
+        r, t, z = _cyl_grid(rs, ts, zs)
+        return r ** alpha * np.sin(alpha * t) * z
+
+    def grad(rs, ts, zs):
+        r, t, z = _cyl_grid(rs, ts, zs)
+        return (alpha * r ** (alpha - 1) * np.sin(alpha * t) * z,
+                alpha * r ** (alpha - 1) * np.cos(alpha * t) * z,
+                r ** alpha * np.sin(alpha * t))
+
+    def zero(rs, ts, zs):
+        return np.zeros((len(zs), len(ts), len(rs)))
+
+    return EdgeProblem(mesh, [zero], [w], w, grad, name="edge_laplace_singular", meta=dict(alpha=alpha))
+
+
+def edge_polynomial(N, W, mu=0.15) -> EdgeProblem:
+    """A solution inside the discrete space: u = 1 + x3^2 + (tau - tau_1)^2 theta x3
+    (tau = ln r, tau_1 = ln r_1 the corner face), whose trace on the corner face
+    is 1 + x3^2 with no tau or theta derivative, so the corner polynomial
+    reproduces it; f = -Lap u = -(u_tautau + u_thetatheta) / r^2 - u_x3x3."""
+    mesh = edge_mesh(N, W, mu=mu)
+    tau1 = float(mesh.elem_lo[0, 0])
+
+    def u(rs, ts, zs):
+        r, t, z = _cyl_grid(rs, ts, zs)
+        return 1.0 + z * z + (np.log(r) - tau1) ** 2 * t * z
+
+    def f(rs, ts, zs):
+        r, t, z = _cyl_grid(rs, ts, zs)
+        return -(2.0 * t * z) / (r * r) - 2.0
+
+    return EdgeProblem(mesh, [f], [u], u, None, name="edge_polynomial", meta=dict(tau1=tau1))

@@ -94,8 +94,31 @@ typedef struct {
   const int32_t *elem_problem; /* [n_elem] problem index in [0, n_problem)     */
   const double *elem_lo;       /* [n_elem*3] box lower corner (x, y, z)        */
   const double *elem_hi;       /* [n_elem*3] box upper corner                  */
-  const int32_t *elem_nbr;     /* [n_elem*6] neighbour id or -1 (Dirichlet)    */
+  const int32_t *elem_nbr;     /* [n_elem*6] neighbour id or -1 (Dirichlet);
+                                  HPSE_COORD_EDGE: -2-c on face 0 (tau = lo)
+                                  for the corner set c                          */
+  /* Edge neighbourhood (Section 2.3; eq. 4.7, 2.34, 2.35).  With
+   * HPSE_COORD_EDGE the boxes are given in the modified coordinates
+   * (tau, theta, x3) = (ln r, theta, x3) of an edge on the x3 axis, the
+   * operator is L^e u = -(u_tautau + u_thetatheta + e^{2 tau} u_x3x3) (r^2 times
+   * -Lap; coef_kind must be HPSE_COEF_LAPLACE), the face terms are the
+   * anisotropic norms of eq. (2.34) with H and G = sup e^tau, and the corner
+   * sets r < r_1 hold one polynomial in x3 each (nodal values on the (W+1)
+   * GLL points of the slab of their layer-1 elements), shared by every theta
+   * sector; they enter only through the faces r = r_1 (their volumes and other
+   * faces have infinite measure).  Unknowns: the elements' (W+1)^3 blocks in
+   * element order, then the corner sets' W+1 values.  hpse_query_points
+   * returns modified coordinates; the caller samples f and g at
+   * r = e^tau, theta, x3 (physical data), the library forms F^e = e^{2 tau} f.
+   * Not supported with HPSE_COORD_EDGE: the adjoint entry points and the
+   * H^1 norms (HPSE_ERR_INVALID_ARG). */
+  int32_t coord;               /* HPSE_COORD_CARTESIAN (0) or HPSE_COORD_EDGE (1)   */
+  int32_t n_corner;            /* corner sets (HPSE_COORD_EDGE), else 0            */
+  const int32_t *corner_W;     /* [n_corner] degree in x3 (= that of its elements) */
+  const int32_t *corner_problem; /* [n_corner] problem index                       */
 } hpse_mesh_desc;
+
+enum { HPSE_COORD_CARTESIAN = 0, HPSE_COORD_EDGE = 1 };
 
 /* Problem data (Section 4.2: F, g of eq. 4.2).  Host FP64 arrays, copied.
  *   f      [n_rhs][hpse_nquad()]        source at the volume points (required)

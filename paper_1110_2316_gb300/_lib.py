@@ -21,6 +21,7 @@ STATUS_NAMES = {
 FP64, FP32 = 0, 1
 COEF_LAPLACE, COEF_SCALAR = 0, 1
 PRECOND_SEPARABLE, PRECOND_BLOCK = 0, 1
+COORD_CARTESIAN, COORD_EDGE = 0, 1
 
 
 class MeshDesc(C.Structure):
@@ -28,6 +29,7 @@ class MeshDesc(C.Structure):
         ("n_elem", C.c_int32), ("n_problem", C.c_int32), ("n_rhs", C.c_int32), ("coef_kind", C.c_int32),
         ("elem_W", C.c_void_p), ("elem_problem", C.c_void_p), ("elem_lo", C.c_void_p),
         ("elem_hi", C.c_void_p), ("elem_nbr", C.c_void_p),
+        ("coord", C.c_int32), ("n_corner", C.c_int32), ("corner_W", C.c_void_p), ("corner_problem", C.c_void_p),
     ]
 
 

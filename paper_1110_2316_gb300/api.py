@@ -64,6 +64,18 @@ class Mesh:
         d.coef_kind = int(coef_kind)
         d.elem_W, d.elem_problem, d.elem_lo, d.elem_hi, d.elem_nbr = (
             k.ctypes.data_as(C.c_void_p) for k in self._keep)
+        # edge neighbourhood (workloads.EdgeMeshDesc): modified coordinates + corner sets
+        self.is_edge = hasattr(desc, "corner_W")
+        if self.is_edge:
+            self._keep += [np.ascontiguousarray(desc.corner_W, dtype=np.int32),
+                           np.ascontiguousarray(desc.corner_problem, dtype=np.int32)]
+            d.coord = _lib.COORD_EDGE
+            d.n_corner = int(self._keep[5].shape[0])
+            d.corner_W = self._keep[5].ctypes.data_as(C.c_void_p)
+            d.corner_problem = self._keep[6].ctypes.data_as(C.c_void_p)
+        else:
+            d.coord = _lib.COORD_CARTESIAN
+            d.n_corner = 0
         h = C.c_void_p()
         check(self._lib.hpse_setup_mesh(C.byref(d), int(device), C.byref(h)), "hpse_setup_mesh")
         self._h = h
@@ -202,8 +214,16 @@ def problem_data_arrays(mesh: Mesh, problem):
 
     ``problem`` provides f (list per rhs), g (list per rhs), a / grad_a (or
     None) as callables on tensor grids (see workloads).  Returns the dict of
-    host arrays expected by Mesh.set_data.
+    host arrays expected by Mesh.set_data.  For an edge neighbourhood the
+    query grids are modified coordinates (tau, theta, x3) and the data
+    functions take cylindrical coordinates: they are sampled at r = e^tau.
     """
+    if getattr(mesh, "is_edge", False):
+        def cyl(fun):
+            return lambda ts, hs, zs: fun(np.exp(ts), hs, zs)
+        from types import SimpleNamespace
+        problem = SimpleNamespace(f=[cyl(v) for v in problem.f], g=[cyl(v) for v in problem.g], a=None,
+                                  grad_a=None)
     ax, fnorm = mesh.query_points()
     Ws = [int(w) for w in mesh.elem_W]
     R = mesh.n_rhs
@@ -247,7 +267,7 @@ def problem_data_arrays(mesh: Mesh, problem):
         for e, W in enumerate(Ws):
             Q = 2 * W + 1
             for fi in range(6):
-                if nbr[e, fi] >= 0:
+                if nbr[e, fi] != -1:
                     continue
                 axis = fi // 2
                 grid = list(axes[e])

@@ -204,6 +204,14 @@ struct hpse_mesh {
   std::map<int, DevBuf> d_qtab;  // per degree FP64 Q-grid tables for the face data
   bool has_data = false;
   // element-block preconditioner (hpse_setup_block_preconditioner)
+  // edge neighbourhood (HPSE_COORD_EDGE): corner sets and face weights
+  int coord = HPSE_COORD_CARTESIAN, n_corner = 0, apply_coef = 0;
+  std::vector<int> cW, cprob;             // per corner set: degree, problem
+  std::vector<int> cslot;                 // per element: slot of its corner face, or -1
+  std::vector<int> slot_ptr, slot_list;   // CSR of slots per corner set
+  std::vector<int> item_n;                // DOF count of each vector item (elements, then corner sets)
+  DevBuf d_item_n, d_kappa64, d_kappa32, d_fw64, d_fw32, d_cslot, d_cW, d_cprob, d_slot_ptr, d_slot_list;
+  DevBuf d_cinv64, d_cinv32, d_cscr64, d_cscr32;
   int precond_kind = HPSE_PRECOND_SEPARABLE;
   bool bj_ready = false;
   DevBuf d_bj_off;            // int64 per element: offset of its packed block
@@ -265,21 +273,23 @@ __device__ double block_sum_d(double v) {
   return t;
 }
 
+// vector items: the elements' (W+1)^3 blocks, then the corner sets' W+1 values
 struct ElemVecArgs {
-  int32_t n_elem, n_rhs;
+  int32_t n_elem, n_rhs;     // n_elem: number of items
   int64_t ndof;
   const int64_t *dof_off;
-  const int32_t *elem_W;
+  const int32_t *item_n;     // DOF count of each item
 };
 
 #include "block_precond.cuh"
+#include "edge.cuh"
 
 // per (element, rhs) block: generic vector kernels with FP64 partials
 template <typename TA, typename TB>
 __global__ void k_dot(ElemVecArgs A, const TA *a, const TB *b, double *part) {
   const int item = blockIdx.x;
   const int e = item / A.n_rhs, r = item - e * A.n_rhs;
-  const int P = A.elem_W[e] + 1, n = P * P * P;
+  const int n = A.item_n[e];
   const int64_t base = (int64_t)r * A.ndof + A.dof_off[e];
   double s = 0.0;
   for (int t = threadIdx.x; t < n; t += blockDim.x) s += (double)a[base + t] * (double)b[base + t];
@@ -291,7 +301,7 @@ __global__ void k_dot(ElemVecArgs A, const TA *a, const TB *b, double *part) {
 __global__ void k_residual(ElemVecArgs A, const double *b, const double *q, double *r, double *part) {
   const int item = blockIdx.x;
   const int e = item / A.n_rhs, rr = item - e * A.n_rhs;
-  const int P = A.elem_W[e] + 1, n = P * P * P;
+  const int n = A.item_n[e];
   const int64_t base = (int64_t)rr * A.ndof + A.dof_off[e];
   double s = 0.0;
   for (int t = threadIdx.x; t < n; t += blockDim.x) {
@@ -309,7 +319,7 @@ __global__ void k_scale_copy(ElemVecArgs A, const int32_t *prob, int n_rhs, cons
                              TO *out) {
   const int item = blockIdx.x;
   const int e = item / A.n_rhs, rr = item - e * A.n_rhs;
-  const int P = A.elem_W[e] + 1, n = P * P * P;
+  const int n = A.item_n[e];
   const int64_t base = (int64_t)rr * A.ndof + A.dof_off[e];
   const double s = scale[prob[e] * n_rhs + rr];
   for (int t = threadIdx.x; t < n; t += blockDim.x) out[base + t] = (TO)(r64[base + t] * s);
@@ -321,7 +331,7 @@ __global__ void k_add_scaled(ElemVecArgs A, const int32_t *prob, int n_rhs, cons
                              double *x64) {
   const int item = blockIdx.x;
   const int e = item / A.n_rhs, rr = item - e * A.n_rhs;
-  const int P = A.elem_W[e] + 1, n = P * P * P;
+  const int n = A.item_n[e];
   const int64_t base = (int64_t)rr * A.ndof + A.dof_off[e];
   const double s = scale[prob[e] * n_rhs + rr];
   for (int t = threadIdx.x; t < n; t += blockDim.x) x64[base + t] += (double)d[base + t] * s;
@@ -332,7 +342,7 @@ __global__ void k_scale_to_f32(ElemVecArgs A, const int32_t *prob, int n_rhs, co
                                float *r32) {
   const int item = blockIdx.x;
   const int e = item / A.n_rhs, rr = item - e * A.n_rhs;
-  const int P = A.elem_W[e] + 1, n = P * P * P;
+  const int n = A.item_n[e];
   const int64_t base = (int64_t)rr * A.ndof + A.dof_off[e];
   const double s = scale[prob[e] * n_rhs + rr];
   for (int t = threadIdx.x; t < n; t += blockDim.x) r32[base + t] = (float)(r64[base + t] * s);
@@ -343,7 +353,7 @@ __global__ void k_add_scaled_f32(ElemVecArgs A, const int32_t *prob, int n_rhs, 
                                  const double *scale, double *x64) {
   const int item = blockIdx.x;
   const int e = item / A.n_rhs, rr = item - e * A.n_rhs;
-  const int P = A.elem_W[e] + 1, n = P * P * P;
+  const int n = A.item_n[e];
   const int64_t base = (int64_t)rr * A.ndof + A.dof_off[e];
   const double s = scale[prob[e] * n_rhs + rr];
   for (int t = threadIdx.x; t < n; t += blockDim.x) x64[base + t] += (double)d32[base + t] * s;
@@ -353,7 +363,7 @@ __global__ void k_add_scaled_f32(ElemVecArgs A, const int32_t *prob, int n_rhs, 
 __global__ void k_add64(ElemVecArgs A, const double *d, double *x) {
   const int item = blockIdx.x;
   const int e = item / A.n_rhs, rr = item - e * A.n_rhs;
-  const int P = A.elem_W[e] + 1, n = P * P * P;
+  const int n = A.item_n[e];
   const int64_t base = (int64_t)rr * A.ndof + A.dof_off[e];
   for (int t = threadIdx.x; t < n; t += blockDim.x) x[base + t] += d[base + t];
 }
@@ -543,6 +553,7 @@ struct FaceDataArgs {
   const double *const *qtab;  // per degree: B0, B1 (QxP), DQ, KQ (QxQ), wq (Q)
   const double *g;            // [n_rhs][nface_pts]
   double *b;
+  const double *fw;           // edge neighbourhood: [E][6][10] face-norm weights, else null
 };
 
 __global__ void k_face_data(FaceDataArgs A) {
@@ -574,9 +585,13 @@ __global__ void k_face_data(FaceDataArgs A) {
     }
     __syncthreads();
     // h0 = (W x W) g ; h1 = H g1 ; h2 = H g2 with H = WxW + WxK + KxW
+    const double *wf = A.fw ? A.fw + ((int64_t)e * 6 + fi) * hpse::FACE_W : nullptr;
+    const double w0 = wf ? wf[0] : 1.0;
+    const double c10 = wf ? wf[1] : 1.0, c11 = wf ? wf[2] : 1.0, c12 = wf ? wf[3] : 1.0;
+    const double c20 = wf ? wf[4] : 1.0, c21 = wf ? wf[5] : 1.0, c22 = wf ? wf[6] : 1.0;
     for (int t = threadIdx.x; t < Q * Q; t += blockDim.x) {
       const int i = t % Q, j = t / Q;
-      h0[t] = wq[i] * wq[j] * g[t];
+      h0[t] = w0 * wq[i] * wq[j] * g[t];
       double k1 = 0.0, k2 = 0.0, l1 = 0.0, l2 = 0.0;
       for (int m = 0; m < Q; ++m) {
         k1 += KQ[i * Q + m] * g1[j * Q + m];  // K along t1
@@ -584,8 +599,8 @@ __global__ void k_face_data(FaceDataArgs A) {
         k2 += KQ[i * Q + m] * g2[j * Q + m];
         l2 += KQ[j * Q + m] * g2[m * Q + i];
       }
-      h1[t] = wq[i] * wq[j] * g1[t] + wq[j] * k1 + wq[i] * l1;
-      h2[t] = wq[i] * wq[j] * g2[t] + wq[j] * k2 + wq[i] * l2;
+      h1[t] = c10 * wq[i] * wq[j] * g1[t] + c11 * wq[j] * k1 + c12 * wq[i] * l1;
+      h2[t] = c20 * wq[i] * wq[j] * g2[t] + c21 * wq[j] * k2 + c22 * wq[i] * l2;
     }
     __syncthreads();
     // project to nodal face values: along t1 first (ta: [t2 q][p1]), then t2
@@ -720,11 +735,11 @@ __global__ void k_h1(H1Args A) {
 // ---------------------------------------------------------------------------
 static ElemVecArgs elem_args(const hpse_mesh *m) {
   ElemVecArgs a;
-  a.n_elem = m->n_elem;
+  a.n_elem = m->n_elem + m->n_corner;
   a.n_rhs = m->n_rhs;
   a.ndof = m->ndof;
   a.dof_off = m->d_dof_off.as<int64_t>();
-  a.elem_W = m->d_elem_W.as<int32_t>();
+  a.item_n = m->d_item_n.as<int32_t>();
   return a;
 }
 
@@ -737,6 +752,8 @@ static FinArgs fin_args(const hpse_mesh *m) {
 }
 
 static int n_items_all(const hpse_mesh *m) { return m->n_elem * m->n_rhs; }
+// vector items (elements and corner sets) x right-hand sides
+static int n_items_vec(const hpse_mesh *m) { return (m->n_elem + m->n_corner) * m->n_rhs; }
 static int npr_of(const hpse_mesh *m) { return m->n_problem * m->n_rhs; }
 
 template <typename T>
@@ -756,7 +773,34 @@ static ApplyArgsT<T> apply_args(const hpse_mesh *m, const Group &g, const T *u, 
   a.coef = (sizeof(T) == 8) ? (const T *)m->d_coef64.p : (const T *)m->d_coef32.p;
   a.coef_off = m->d_coef_off.as<int64_t>();
   a.nquad = m->nquad;
+  a.n_elem = m->n_elem;
+  if (m->coord == HPSE_COORD_EDGE) {
+    const bool d = sizeof(T) == 8;
+    a.kappa = d ? (const T *)m->d_kappa64.p : (const T *)m->d_kappa32.p;
+    a.fw = d ? (const T *)m->d_fw64.p : (const T *)m->d_fw32.p;
+    a.cslot = m->d_cslot.as<int32_t>();
+    a.cscr = m->n_corner ? (d ? (T *)m->d_cscr64.p : (T *)m->d_cscr32.p) : nullptr;
+  }
   return a;
+}
+
+template <typename T>
+static CornerArgsT<T> corner_args(const hpse_mesh *m) {
+  CornerArgsT<T> c;
+  memset(&c, 0, sizeof(c));
+  const bool d = sizeof(T) == 8;
+  c.n_corner = m->n_corner;
+  c.n_rhs = m->n_rhs;
+  c.n_elem = m->n_elem;
+  c.ndof = m->ndof;
+  c.dof_off = m->d_dof_off.as<int64_t>();
+  c.cW = m->d_cW.as<int32_t>();
+  c.cprob = m->d_cprob.as<int32_t>();
+  c.slot_ptr = m->d_slot_ptr.as<int32_t>();
+  c.slot_list = m->d_slot_list.as<int32_t>();
+  c.cscr = d ? (const T *)m->d_cscr64.p : (const T *)m->d_cscr32.p;
+  c.cinv = d ? (const T *)m->d_cinv64.p : (const T *)m->d_cinv32.p;
+  return c;
 }
 
 template <typename T>
@@ -807,10 +851,48 @@ static hpse_status launch_apply_all(hpse_mesh *m, int mode, ApplyArgsT<T> base_a
     a.n_group = g.n;
     const KernelSet &ks = g_sets[pi][g.W];
     const int th = m->threads[0][pi][g.W];
-    CK(ks.apply(m->coef_kind, mode, &a, g.n * m->n_rhs, th, group_stream(m, gi, s)));
+    CK(ks.apply(m->apply_coef, mode, &a, g.n * m->n_rhs, th, group_stream(m, gi, s)));
     ++g_launches;
   }
   CK(group_join(m, s));
+  if (m->n_corner > 0 && !base_args.self_only) {
+    // corner sets: sum of their face slots (after every element's face phase)
+    CornerArgsT<T> c = corner_args<T>(m);
+    c.y = base_args.y;
+    c.z = base_args.z;
+    c.p = base_args.u;
+    c.pnew = base_args.pnew;
+    c.beta = base_args.beta;
+    c.partial = base_args.partial;
+    const int items = m->n_corner * m->n_rhs;
+    if (mode == MODE_PCG) k_corner_apply<T, MODE_PCG><<<items, 32, 0, s>>>(c);
+    else if (mode == MODE_TRANSPOSE) k_corner_apply<T, MODE_TRANSPOSE><<<items, 32, 0, s>>>(c);
+    else k_corner_apply<T, MODE_PLAIN><<<items, 32, 0, s>>>(c);
+    CK(cudaGetLastError());
+    ++g_launches;
+  }
+  return HPSE_OK;
+}
+
+// corner sets of the edge neighbourhood: exact blocks, with the PCG update in PCG mode
+template <typename T>
+static hpse_status launch_corner_prec(hpse_mesh *m, int mode, const PrecArgsT<T> &b, cudaStream_t s) {
+  if (m->n_corner == 0) return HPSE_OK;
+  CornerArgsT<T> c = corner_args<T>(m);
+  c.rin = b.rin;
+  c.zout = b.zout;
+  c.x = b.x;
+  c.r = b.r;
+  c.p = b.p;
+  c.q = b.q;
+  c.alpha = b.alpha;
+  c.part_rr = b.part_rr;
+  c.part_rz = b.part_rz;
+  const int items = m->n_corner * b.n_rhs;
+  if (mode == MODE_PCG) k_corner_prec<T, MODE_PCG><<<items, 32, 0, s>>>(c);
+  else k_corner_prec<T, MODE_PLAIN><<<items, 32, 0, s>>>(c);
+  CK(cudaGetLastError());
+  ++g_launches;
   return HPSE_OK;
 }
 
@@ -852,7 +934,7 @@ static hpse_status launch_bj_all(hpse_mesh *m, int mode, const PrecArgsT<T> &b, 
     }
   }
   CK(group_join(m, s));
-  return HPSE_OK;
+  return launch_corner_prec<T>(m, mode, b, s);
 }
 
 template <typename T>
@@ -871,7 +953,7 @@ static hpse_status launch_prec_all(hpse_mesh *m, int mode, PrecArgsT<T> base_arg
     ++g_launches;
   }
   CK(group_join(m, s));
-  return HPSE_OK;
+  return launch_corner_prec<T>(m, mode, base_args, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -900,6 +982,127 @@ extern "C" int64_t hpse_kernel_launch_count(int32_t reset) {
   return v;
 }
 
+// Edge neighbourhood tables (eq. 4.7, 2.34): e^{2 tau} at each element's Q
+// x-points, the face-norm weights of every (element, face), and the corner
+// blocks A_cc with their inverse Cholesky factors.
+//
+// Weights, face of axis a with tangential axes t1 < t2, half-lengths hh and
+// scales s = 1/hh of the element's box in (tau, theta, x3), G = sup e^tau:
+// |||.|||^2 = c0 L2 + c1 quotient(t1) + c2 quotient(t2) with
+// (c0, c1, c2) = (hh_t1 hh_t2, hh_t2, hh_t1), the quotient along x3 times G,
+// all of it times G on a face x3 = const.  Interior and corner faces:
+// [u] in L2 times hh_t1 hh_t2 (times H = G on x3 = const), the derivative
+// jumps in |||.|||, the x3 derivative times G^2.  Dirichlet faces: u - g in L2
+// times hh_t1 hh_t2 and the two tangential derivatives in |||.||| (x3: times
+// G^2), times s_t^2 since the kernels form lambda-derivatives there.
+static hpse_status setup_edge(hpse_mesh *m) {
+  const int E = m->n_elem, C = m->n_corner;
+  std::vector<double> kap((size_t)E * hpse::KAPPA_STRIDE, 0.0), fw((size_t)E * 6 * hpse::FACE_W, 0.0);
+  for (int e = 0; e < E; ++e) {
+    const hm::DegreeTables &t = m->tabs.at(m->W[e]);
+    double hh[3], sc[3];
+    for (int a = 0; a < 3; ++a) {
+      hh[a] = 0.5 * (m->hi[3 * e + a] - m->lo[3 * e + a]);
+      sc[a] = 1.0 / hh[a];
+    }
+    for (int q = 0; q < t.Q; ++q) kap[(size_t)e * hpse::KAPPA_STRIDE + q] = std::exp(2.0 * (m->lo[3 * e] + (t.xq[q] + 1.0) * hh[0]));
+    for (int fi = 0; fi < 6; ++fi) {
+      const int a = fi >> 1, side = fi & 1;
+      const int t1 = a == 0 ? 1 : 0, t2 = a == 2 ? 1 : 2;
+      const double G = std::exp(a == 0 ? (side ? m->hi[3 * e] : m->lo[3 * e]) : m->hi[3 * e]);
+      double c[3] = {hh[t1] * hh[t2], hh[t2], hh[t1]};
+      if (t2 == 2) c[2] *= G;
+      if (a == 2)
+        for (double &v : c) v *= G;
+      double *w = &fw[((size_t)e * 6 + fi) * hpse::FACE_W];
+      const bool dir = m->nbr[6 * e + fi] == -1;
+      w[0] = (dir || a != 2 ? 1.0 : G) * hh[t1] * hh[t2];
+      // fields 1, 2, 3: derivative along t1, t2, the normal a
+      const int ax[3] = {t1, t2, a};
+      for (int k = 0; k < 3; ++k) {
+        double f = ax[k] == 2 ? G * G : 1.0;
+        if (dir) f *= (k < 2) ? sc[ax[k]] * sc[ax[k]] : 0.0;
+        for (int j = 0; j < 3; ++j) w[1 + 3 * k + j] = f * c[j];
+      }
+    }
+  }
+  std::vector<float> kap32(kap.begin(), kap.end()), fw32(fw.begin(), fw.end());
+  CK(upload(m->d_kappa64, kap));
+  CK(upload(m->d_kappa32, kap32));
+  CK(upload(m->d_fw64, fw));
+  CK(upload(m->d_fw32, fw32));
+  CK(upload(m->d_cslot, m->cslot));
+  if (C == 0) return HPSE_OK;
+  // corner blocks: the corner trace on a face (nodal face grid p2 = x3, p1 = theta)
+  // is p replicated along p1 and its x3 derivative s_x3 D p; with 1^T MP 1 = 2
+  // and 1^T KP 1 = 0, A_cc = sum_faces 2 (w0 MP + s_x3^2 D^T (w4 MP + w6 KP) D)
+  const int S = (int)m->slot_list.size();
+  std::vector<double> cinv((size_t)C * hpse::CSCR_STRIDE * hpse::CSCR_STRIDE, 0.0);
+  for (int c = 0; c < C; ++c) {
+    const hm::DegreeTables &t = m->tabs.at(m->cW[c]);
+    const int P = t.P;
+    std::vector<double> Acc((size_t)P * P, 0.0);
+    for (int i = m->slot_ptr[c]; i < m->slot_ptr[c + 1]; ++i) {
+      int e = -1;
+      for (int ee = 0; ee < E; ++ee)
+        if (m->cslot[ee] == m->slot_list[i]) e = ee;
+      const double *w = &fw[((size_t)e * 6 + 0) * hpse::FACE_W];
+      const double sz = 2.0 / (m->hi[3 * e + 2] - m->lo[3 * e + 2]);
+      // M = w4 MP + w6 KP (the x3-derivative field, quotient along x3 = t2)
+      std::vector<double> M((size_t)P * P), DM((size_t)P * P, 0.0);
+      for (int k = 0; k < P * P; ++k) M[k] = w[4] * t.MP[k] + w[6] * t.KP[k];
+      for (int i2 = 0; i2 < P; ++i2)
+        for (int j2 = 0; j2 < P; ++j2) {
+          double v = 0.0;
+          for (int k = 0; k < P; ++k) v += M[i2 * P + k] * t.D[k * P + j2];
+          DM[i2 * P + j2] = v;
+        }
+      for (int i2 = 0; i2 < P; ++i2)
+        for (int j2 = 0; j2 < P; ++j2) {
+          double v = 0.0;
+          for (int k = 0; k < P; ++k) v += t.D[k * P + i2] * DM[k * P + j2];
+          Acc[i2 * P + j2] += 2.0 * (w[0] * t.MP[i2 * P + j2] + sz * sz * v);
+        }
+    }
+    // Cholesky A_cc = L L^T, then X = L^{-1}
+    std::vector<double> L(Acc);
+    for (int k = 0; k < P; ++k) {
+      double d = L[k * P + k];
+      for (int j = 0; j < k; ++j) d -= L[k * P + j] * L[k * P + j];
+      if (!(d > 0.0)) return HPSE_ERR_BREAKDOWN;
+      d = std::sqrt(d);
+      L[k * P + k] = d;
+      for (int i2 = k + 1; i2 < P; ++i2) {
+        double v = L[i2 * P + k];
+        for (int j = 0; j < k; ++j) v -= L[i2 * P + j] * L[k * P + j];
+        L[i2 * P + k] = v / d;
+      }
+    }
+    double *X = &cinv[(size_t)c * hpse::CSCR_STRIDE * hpse::CSCR_STRIDE];
+    for (int i2 = 0; i2 < P; ++i2) {
+      X[i2 * hpse::CSCR_STRIDE + i2] = 1.0 / L[i2 * P + i2];
+      for (int j = 0; j < i2; ++j) {
+        double v = 0.0;
+        for (int k = j; k < i2; ++k) v += L[i2 * P + k] * X[k * hpse::CSCR_STRIDE + j];
+        X[i2 * hpse::CSCR_STRIDE + j] = -v / L[i2 * P + i2];
+      }
+    }
+  }
+  std::vector<float> cinv32(cinv.begin(), cinv.end());
+  CK(upload(m->d_cinv64, cinv));
+  CK(upload(m->d_cinv32, cinv32));
+  CK(upload(m->d_cW, m->cW));
+  CK(upload(m->d_cprob, m->cprob));
+  CK(upload(m->d_slot_ptr, m->slot_ptr));
+  CK(upload(m->d_slot_list, m->slot_list));
+  const size_t ns = (size_t)std::max(1, S) * m->n_rhs * hpse::CSCR_STRIDE;
+  CK(m->d_cscr64.alloc(ns * sizeof(double)));
+  CK(m->d_cscr32.alloc(ns * sizeof(float)));
+  CK(cudaMemset(m->d_cscr64.p, 0, ns * sizeof(double)));
+  CK(cudaMemset(m->d_cscr32.p, 0, ns * sizeof(float)));
+  return HPSE_OK;
+}
+
 extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse_mesh **out) {
   if (!d || !out) return HPSE_ERR_INVALID_ARG;
   *out = nullptr;
@@ -915,6 +1118,17 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
   m->n_problem = d->n_problem;
   m->n_rhs = d->n_rhs;
   m->coef_kind = d->coef_kind;
+  m->coord = d->coord;
+  if (m->coord != HPSE_COORD_CARTESIAN && m->coord != HPSE_COORD_EDGE) return HPSE_ERR_INVALID_ARG;
+  if (m->coord == HPSE_COORD_EDGE) {
+    // the modified-coordinate operator is built for the Laplacian (eq. 2.35)
+    if (d->coef_kind != HPSE_COEF_LAPLACE || d->n_corner < 0) return HPSE_ERR_INVALID_ARG;
+    if (d->n_corner > 0 && (!d->corner_W || !d->corner_problem)) return HPSE_ERR_INVALID_ARG;
+    m->n_corner = d->n_corner;
+    m->cW.assign(d->corner_W, d->corner_W + d->n_corner);
+    m->cprob.assign(d->corner_problem, d->corner_problem + d->n_corner);
+  }
+  m->apply_coef = m->coord == HPSE_COORD_EDGE ? hpse::COEF_EDGE : d->coef_kind;
   m->W.assign(d->elem_W, d->elem_W + E);
   m->prob.assign(d->elem_problem, d->elem_problem + E);
   m->nbr.assign(d->elem_nbr, d->elem_nbr + 6 * (size_t)E);
@@ -929,9 +1143,31 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
           !std::isfinite(m->hi[3 * e + a]))
         return HPSE_ERR_INVALID_ARG;
   }
+  const int C = m->n_corner;
+  for (int c = 0; c < C; ++c)
+    if (m->cW[c] < 1 || m->cW[c] > HPSE_MAX_W || m->cprob[c] < 0 || m->cprob[c] >= m->n_problem)
+      return HPSE_ERR_INVALID_ARG;
+  std::vector<int> corner_e(C, -1);  // first layer-1 element of each corner set
   for (int e = 0; e < E; ++e)
     for (int fi = 0; fi < 6; ++fi) {
       const int n = m->nbr[6 * e + fi];
+      if (n <= -2) {
+        // corner set: edge coordinates, face tau = lo only, same degree, problem and x3 slab
+        const int c = -2 - n;
+        if (m->coord != HPSE_COORD_EDGE || fi != 0 || c >= C) return HPSE_ERR_INVALID_ARG;
+        if (m->cW[c] != m->W[e]) return HPSE_ERR_DEGREE;
+        if (m->cprob[c] != m->prob[e]) return HPSE_ERR_INVALID_ARG;
+        if (corner_e[c] < 0) {
+          corner_e[c] = e;
+        } else {
+          const int e0 = corner_e[c];
+          if (std::fabs(m->lo[3 * e + 2] - m->lo[3 * e0 + 2]) > 1e-12 * std::max(1.0, std::fabs(m->lo[3 * e0 + 2])) ||
+              std::fabs(m->hi[3 * e + 2] - m->hi[3 * e0 + 2]) > 1e-12 * std::max(1.0, std::fabs(m->hi[3 * e0 + 2])) ||
+              std::fabs(m->lo[3 * e] - m->lo[3 * e0]) > 1e-12 * std::max(1.0, std::fabs(m->lo[3 * e0])))
+            return HPSE_ERR_NONMATCHING_FACE;
+        }
+        continue;
+      }
       if (n < -1 || n >= E || n == e) return HPSE_ERR_INVALID_ARG;
       if (n < 0) continue;
       if (m->nbr[6 * n + (fi ^ 1)] != e) return HPSE_ERR_NONMATCHING_FACE;
@@ -961,12 +1197,37 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
     od += (int64_t)P * P * P;
     oq += (int64_t)Q * Q * Q;
   }
+  // corner sets follow the elements in every vector
+  m->item_n.assign(E + C, 0);
+  for (int e = 0; e < E; ++e) m->item_n[e] = (m->W[e] + 1) * (m->W[e] + 1) * (m->W[e] + 1);
+  for (int c = 0; c < C; ++c) {
+    m->dof_off.push_back(od);
+    m->item_n[E + c] = m->cW[c] + 1;
+    od += m->cW[c] + 1;
+  }
   m->ndof = od;
   m->nquad = oq;
+  // face slots of the corner sets
+  m->cslot.assign(E, -1);
+  m->slot_ptr.assign(C + 1, 0);
+  {
+    std::vector<int> slot_elem;
+    for (int e = 0; e < E; ++e)
+      if (m->nbr[6 * e] <= -2) {
+        m->cslot[e] = (int)slot_elem.size();
+        slot_elem.push_back(e);
+        m->slot_ptr[-2 - m->nbr[6 * e] + 1]++;
+      }
+    for (int c = 0; c < C; ++c) m->slot_ptr[c + 1] += m->slot_ptr[c];
+    std::vector<int> fill(m->slot_ptr.begin(), m->slot_ptr.end() - 1);
+    m->slot_list.assign(slot_elem.size(), 0);
+    for (size_t sl = 0; sl < slot_elem.size(); ++sl)
+      m->slot_list[fill[-2 - m->nbr[6 * slot_elem[sl]]]++] = (int)sl;
+  }
   int64_t of = 0;
   for (int e = 0; e < E; ++e)
     for (int fi = 0; fi < 6; ++fi)
-      if (m->nbr[6 * e + fi] < 0) {
+      if (m->nbr[6 * e + fi] == -1) {
         const int Q = 2 * m->W[e] + 1;
         m->bface_elem.push_back(e);
         m->bface_fi.push_back(fi);
@@ -974,13 +1235,16 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
         of += (int64_t)Q * Q;
       }
   m->nface_pts = of;
+  // vector items (elements, then corner sets) per problem
   m->prob_ptr.assign(m->n_problem + 1, 0);
   for (int e = 0; e < E; ++e) m->prob_ptr[m->prob[e] + 1]++;
+  for (int c = 0; c < C; ++c) m->prob_ptr[m->cprob[c] + 1]++;
   for (int p = 0; p < m->n_problem; ++p) m->prob_ptr[p + 1] += m->prob_ptr[p];
   {
     std::vector<int> fill(m->prob_ptr.begin(), m->prob_ptr.end() - 1);
-    m->prob_elems.assign(E, 0);
+    m->prob_elems.assign(E + C, 0);
     for (int e = 0; e < E; ++e) m->prob_elems[fill[m->prob[e]]++] = e;
+    for (int c = 0; c < C; ++c) m->prob_elems[fill[m->cprob[c]]++] = E + c;
   }
   for (int k = 0; k < 2; ++k)
     for (int p = 0; p < 2; ++p)
@@ -1041,6 +1305,11 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
     geo[4 * e + 3] = J;
     for (int k = 0; k < 4; ++k) geo32[4 * e + k] = (float)geo[4 * e + k];
   }
+  if (m->coord == HPSE_COORD_EDGE) {
+    hpse_status st = setup_edge(m.get());
+    if (st != HPSE_OK) return st;
+  }
+  CK(upload(m->d_item_n, m->item_n));
   CK(upload(m->d_dof_off, m->dof_off));
   CK(upload(m->d_coef_off, m->coef_off));
   CK(upload(m->d_nbr, m->nbr));
@@ -1127,6 +1396,10 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data) {
             coef[4 * i] = wJ * av * av;
             for (int k = 0; k < 3; ++k) coef[4 * i + k + 1] = s[k] * data->grad_a[k * nq + i] / av;
             wja[i] = wJ * av;
+          } else if (m->coord == HPSE_COORD_EDGE) {
+            // F^e = e^{2 tau} f (eq. 4.7): tau is the x coordinate of the point
+            const double tau = m->lo[3 * e] + (t.xq[a] + 1.0) * 0.5 * (m->hi[3 * e] - m->lo[3 * e]);
+            wja[i] = wJ * std::exp(2.0 * tau);
           } else {
             wja[i] = wJ;
           }
@@ -1223,6 +1496,7 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data) {
     A.qtab = dtabs.as<const double *>();
     A.g = dg.as<double>();
     A.b = m->d_b.as<double>();
+    A.fw = m->coord == HPSE_COORD_EDGE ? m->d_fw64.as<double>() : nullptr;
     const int Q = 2 * Wmax + 1, P = Wmax + 1;
     const size_t smem = (size_t)(8 * Q * Q + 2 * Q * P + P * P) * sizeof(double);
     CK(cudaFuncSetAttribute(k_face_data, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1235,10 +1509,10 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data) {
   {
     const int npr = npr_of(m);
     DevBuf part;
-    CK(part.alloc((size_t)std::max(1, n_items_all(m)) * sizeof(double)));
+    CK(part.alloc((size_t)std::max(1, n_items_vec(m)) * sizeof(double)));
     if (!m->d_bnorm2.p) CK(m->d_bnorm2.alloc((size_t)npr * sizeof(double)));
-    if (n_items_all(m) > 0) {
-      k_dot<double, double><<<n_items_all(m), 128>>>(elem_args(m), m->d_b.as<double>(), m->d_b.as<double>(),
+    if (n_items_vec(m) > 0) {
+      k_dot<double, double><<<n_items_vec(m), 128>>>(elem_args(m), m->d_b.as<double>(), m->d_b.as<double>(),
                                                      part.as<double>());
       CK(cudaGetLastError());
       ++g_launches;
@@ -1355,7 +1629,7 @@ extern "C" hpse_status hpse_setup_block_preconditioner(hpse_mesh *m) {
       ba.n_rhs = c;
       k_bj_probe<<<g.n * c, 128, 0, s>>>(ba, j0, c, pu.as<double>());
       CK(cudaGetLastError());
-      CK(ks.apply(m->coef_kind, MODE_PLAIN, &a, g.n * c, th, s));
+      CK(ks.apply(m->apply_coef, MODE_PLAIN, &a, g.n * c, th, s));
       k_bj_gather<<<g.n * c, 128, 0, s>>>(ba, j0, c, py.as<double>(), blk.as<double>());
       CK(cudaGetLastError());
       g_launches += 3;
@@ -1451,7 +1725,7 @@ static hpse_status ensure_work(hpse_mesh *m) {
   CK(w->pa32.alloc(f));
   CK(w->pb32.alloc(f));
   CK(w->q32.alloc(f));
-  const size_t ni = (size_t)std::max(1, n_items_all(m));
+  const size_t ni = (size_t)std::max(1, n_items_vec(m));
   CK(w->part0.alloc(ni * sizeof(double)));
   CK(w->part1.alloc(ni * sizeof(double)));
   CK(w->part2.alloc(ni * sizeof(double)));
@@ -1524,8 +1798,8 @@ static hpse_status run_pcg(hpse_mesh *m, T *x, T *r, T *z, T *pa, T *pb, T *q, d
     p.zout = z;
     hpse_status st = launch_prec_all<T>(m, MODE_PLAIN, p, s);
     if (st != HPSE_OK) return st;
-    k_dot<T, T><<<n_items_all(m), 128, 0, s>>>(elem_args(m), r, z, w.part0.as<double>());
-    k_dot<T, T><<<n_items_all(m), 128, 0, s>>>(elem_args(m), r, r, w.part1.as<double>());
+    k_dot<T, T><<<n_items_vec(m), 128, 0, s>>>(elem_args(m), r, z, w.part0.as<double>());
+    k_dot<T, T><<<n_items_vec(m), 128, 0, s>>>(elem_args(m), r, r, w.part1.as<double>());
     k_fin_init<<<npr, 128, 0, s>>>(fin_args(m), S, w.part0.as<double>(), w.part1.as<double>(), rel_tol, scale,
                                    0);
     CK(cudaGetLastError());
@@ -1599,7 +1873,7 @@ static hpse_status fp64_residual(hpse_mesh *m, const double *x64, double tol, do
   ApplyArgsT<double> a = apply_args<double>(m, m->groups[0], x64, w.q64.as<double>());
   hpse_status st = launch_apply_all<double>(m, MODE_PLAIN, a, s);
   if (st != HPSE_OK) return st;
-  k_residual<<<n_items_all(m), 128, 0, s>>>(elem_args(m), m->d_b.as<double>(), w.q64.as<double>(),
+  k_residual<<<n_items_vec(m), 128, 0, s>>>(elem_args(m), m->d_b.as<double>(), w.q64.as<double>(),
                                            w.r64.as<double>(), w.part0.as<double>());
   k_fin_outer<<<npr_of(m), 128, 0, s>>>(fin_args(m), w.part0.as<double>(), m->d_bnorm2.as<double>(), tol, rel, scale,
                                         rnorm);
@@ -1656,7 +1930,7 @@ static hpse_status solve_reliable(hpse_mesh *m, const hpse_solve_opts *o, double
     if (st != HPSE_OK) return st;
     ++applies;
   }
-  k_scale_copy<T><<<n_items_all(m), 128, 0, s>>>(elem_args(m), m->d_prob.as<int32_t>(), m->n_rhs,
+  k_scale_copy<T><<<n_items_vec(m), 128, 0, s>>>(elem_args(m), m->d_prob.as<int32_t>(), m->n_rhs,
                                                  w.r64.as<double>(), sc_scale, r32);
   CK(cudaMemsetAsync(x32, 0, nb32, s));
   CK(cudaMemsetAsync(pa, 0, nb32, s));
@@ -1667,8 +1941,8 @@ static hpse_status solve_reliable(hpse_mesh *m, const hpse_solve_opts *o, double
     p.zout = z32;
     hpse_status st = launch_prec_all<T>(m, MODE_PLAIN, p, s);
     if (st != HPSE_OK) return st;
-    k_dot<T, T><<<n_items_all(m), 128, 0, s>>>(elem_args(m), r32, z32, w.part0.as<double>());
-    k_dot<T, T><<<n_items_all(m), 128, 0, s>>>(elem_args(m), r32, r32, w.part1.as<double>());
+    k_dot<T, T><<<n_items_vec(m), 128, 0, s>>>(elem_args(m), r32, z32, w.part0.as<double>());
+    k_dot<T, T><<<n_items_vec(m), 128, 0, s>>>(elem_args(m), r32, r32, w.part1.as<double>());
     k_fin_init<<<npr, 128, 0, s>>>(fin_args(m), S, w.part0.as<double>(), w.part1.as<double>(), o->tol, sc_scale, 1);
     CK(cudaGetLastError());
     g_launches += 4;
@@ -1727,7 +2001,7 @@ static hpse_status solve_reliable(hpse_mesh *m, const hpse_solve_opts *o, double
       now = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
     if (refresh || capped || (deadline > 0 && now > deadline)) {
       // x += ||b|| x32 ; x32 = 0 ; r64 = b - A x ; relative residuals
-      k_add_scaled<T><<<n_items_all(m), 128, 0, s>>>(elem_args(m), m->d_prob.as<int32_t>(), m->n_rhs, x32, sc_bn, x);
+      k_add_scaled<T><<<n_items_vec(m), 128, 0, s>>>(elem_args(m), m->d_prob.as<int32_t>(), m->n_rhs, x32, sc_bn, x);
       CK(cudaGetLastError());
       ++g_launches;
       CK(cudaMemsetAsync(x32, 0, nb32, s));
@@ -1752,15 +2026,15 @@ static hpse_status solve_reliable(hpse_mesh *m, const hpse_solve_opts *o, double
         break;
       }
       // replace the FP32 residual by the true one, keep the direction
-      k_scale_copy<T><<<n_items_all(m), 128, 0, s>>>(elem_args(m), m->d_prob.as<int32_t>(), m->n_rhs,
+      k_scale_copy<T><<<n_items_vec(m), 128, 0, s>>>(elem_args(m), m->d_prob.as<int32_t>(), m->n_rhs,
                                                      w.r64.as<double>(), sc_scale, r32);
       PrecArgsT<T> p = prec_args<T>(m, m->groups[0]);
       p.rin = r32;
       p.zout = z32;
       st = launch_prec_all<T>(m, MODE_PLAIN, p, s);
       if (st != HPSE_OK) return st;
-      k_dot<T, T><<<n_items_all(m), 128, 0, s>>>(elem_args(m), r32, z32, w.part0.as<double>());
-      k_dot<T, T><<<n_items_all(m), 128, 0, s>>>(elem_args(m), r32, r32, w.part1.as<double>());
+      k_dot<T, T><<<n_items_vec(m), 128, 0, s>>>(elem_args(m), r32, z32, w.part0.as<double>());
+      k_dot<T, T><<<n_items_vec(m), 128, 0, s>>>(elem_args(m), r32, r32, w.part1.as<double>());
       k_fin_reliable<<<npr, 128, 0, s>>>(fin_args(m), S, w.part0.as<double>(), w.part1.as<double>(), sc_rel, o->tol);
       CK(cudaGetLastError());
       g_launches += 4;
@@ -1837,7 +2111,7 @@ extern "C" hpse_status hpse_pcg_solve(hpse_mesh *m, const hpse_solve_opts *o, do
     while (true) {
       if (first) {
         CK(cudaMemcpyAsync(w.r64.p, m->d_b.p, nb, cudaMemcpyDeviceToDevice, s));
-        k_dot<double, double><<<n_items_all(m), 128, 0, s>>>(elem_args(m), w.r64.as<double>(), w.r64.as<double>(),
+        k_dot<double, double><<<n_items_vec(m), 128, 0, s>>>(elem_args(m), w.r64.as<double>(), w.r64.as<double>(),
                                                              w.part0.as<double>());
         k_fin_outer<<<npr, 128, 0, s>>>(fin_args(m), w.part0.as<double>(), m->d_bnorm2.as<double>(), o->tol, sc_rel,
                                         sc_scale, sc_rnorm);
@@ -1867,7 +2141,7 @@ extern "C" hpse_status hpse_pcg_solve(hpse_mesh *m, const hpse_solve_opts *o, do
         break;
       }
       // inner FP32 PCG on A d = r64 / ||r64||
-      k_scale_to_f32<<<n_items_all(m), 128, 0, s>>>(elem_args(m), m->d_prob.as<int32_t>(), m->n_rhs,
+      k_scale_to_f32<<<n_items_vec(m), 128, 0, s>>>(elem_args(m), m->d_prob.as<int32_t>(), m->n_rhs,
                                                     w.r64.as<double>(), sc_scale, w.r32.as<float>());
       CK(cudaGetLastError());
       ++g_launches;
@@ -1876,7 +2150,7 @@ extern "C" hpse_status hpse_pcg_solve(hpse_mesh *m, const hpse_solve_opts *o, do
                           w.pb32.as<float>(), w.q32.as<float>(), itol, o->max_iter - total_it, chunk, sc_scale,
                           deadline, &it, &ist);
       if (st != HPSE_OK) return st;
-      k_add_scaled_f32<<<n_items_all(m), 128, 0, s>>>(elem_args(m), m->d_prob.as<int32_t>(), m->n_rhs,
+      k_add_scaled_f32<<<n_items_vec(m), 128, 0, s>>>(elem_args(m), m->d_prob.as<int32_t>(), m->n_rhs,
                                                       w.x32.as<float>(), sc_rnorm, x);
       CK(cudaGetLastError());
       ++g_launches;
@@ -1915,6 +2189,7 @@ extern "C" hpse_status hpse_pcg_solve(hpse_mesh *m, const hpse_solve_opts *o, do
 
 extern "C" hpse_status hpse_h1_error(hpse_mesh *m, const double *u, const double *ref, const double *vq,
                                      const double *gq, double *out, void *stream) {
+  if (m && m->coord == HPSE_COORD_EDGE) return HPSE_ERR_INVALID_ARG;  // box meshes only
   if (!m || !out) return HPSE_ERR_INVALID_ARG;
   if (m->ndof == 0) {
     for (int r = 0; r < m->n_rhs; ++r) out[2 * r] = out[2 * r + 1] = 0.0;
@@ -2198,6 +2473,7 @@ static hpse_status launch_fields(hpse_mesh *m, const double *u, double *out, cud
 }
 
 extern "C" hpse_status hpse_eval_fields(hpse_mesh *m, const double *u, double *out, void *stream) {
+  if (m && m->coord == HPSE_COORD_EDGE) return HPSE_ERR_INVALID_ARG;  // box meshes only
   if (!m) return HPSE_ERR_INVALID_ARG;
   if (m->ndof == 0) return HPSE_OK;
   if (!u || !out) return HPSE_ERR_INVALID_ARG;
@@ -2207,6 +2483,7 @@ extern "C" hpse_status hpse_eval_fields(hpse_mesh *m, const double *u, double *o
 }
 
 extern "C" hpse_status hpse_apply_eval_transpose(hpse_mesh *m, const double *rho, double *y, void *stream) {
+  if (m && m->coord == HPSE_COORD_EDGE) return HPSE_ERR_INVALID_ARG;  // box meshes only
   if (!m) return HPSE_ERR_INVALID_ARG;
   if (m->ndof == 0) return HPSE_OK;
   if (!rho || !y) return HPSE_ERR_INVALID_ARG;
@@ -2222,6 +2499,7 @@ extern "C" hpse_status hpse_apply_eval_transpose(hpse_mesh *m, const double *rho
 }
 
 extern "C" hpse_status hpse_quad_weights(hpse_mesh *m, double *out, void *stream) {
+  if (m && m->coord == HPSE_COORD_EDGE) return HPSE_ERR_INVALID_ARG;  // box meshes only
   if (!m || (!out && m->nquad > 0)) return HPSE_ERR_INVALID_ARG;
   if (!m->has_data) return HPSE_ERR_NO_DATA;
   CK(cudaSetDevice(m->device));
@@ -2240,6 +2518,7 @@ static hpse_status ensure_scratch(hpse_mesh *m) {
 }
 
 extern "C" hpse_status hpse_apply_residual(hpse_mesh *m, const double *u, double *z, void *stream) {
+  if (m && m->coord == HPSE_COORD_EDGE) return HPSE_ERR_INVALID_ARG;  // box meshes only
   if (!m) return HPSE_ERR_INVALID_ARG;
   if (m->ndof == 0) return HPSE_OK;
   if (!u || !z) return HPSE_ERR_INVALID_ARG;
@@ -2258,6 +2537,7 @@ extern "C" hpse_status hpse_apply_residual(hpse_mesh *m, const double *u, double
 }
 
 extern "C" hpse_status hpse_apply_transpose(hpse_mesh *m, const double *z, double *y, void *stream) {
+  if (m && m->coord == HPSE_COORD_EDGE) return HPSE_ERR_INVALID_ARG;  // box meshes only
   if (!m) return HPSE_ERR_INVALID_ARG;
   if (m->ndof == 0) return HPSE_OK;
   if (!z || !y) return HPSE_ERR_INVALID_ARG;
@@ -2277,6 +2557,7 @@ extern "C" hpse_status hpse_apply_transpose(hpse_mesh *m, const double *z, doubl
 
 extern "C" hpse_status hpse_data_gradient(hpse_mesh *m, const double *ufields, const double *lfields, double *out,
                                           void *stream) {
+  if (m && m->coord == HPSE_COORD_EDGE) return HPSE_ERR_INVALID_ARG;  // box meshes only
   if (!m) return HPSE_ERR_INVALID_ARG;
   if (m->nquad == 0) return HPSE_OK;
   if (!ufields || !lfields || !out) return HPSE_ERR_INVALID_ARG;
@@ -2299,8 +2580,8 @@ extern "C" hpse_status hpse_set_rhs(hpse_mesh *m, const double *b, void *stream)
   const size_t nv = (size_t)m->n_rhs * m->ndof;
   CK(cudaMemcpyAsync(m->d_b.p, b, nv * sizeof(double), cudaMemcpyDeviceToDevice, s));
   DevBuf part;
-  CK(part.alloc((size_t)std::max(1, n_items_all(m)) * sizeof(double)));
-  k_dot<double, double><<<n_items_all(m), 128, 0, s>>>(elem_args(m), m->d_b.as<double>(), m->d_b.as<double>(),
+  CK(part.alloc((size_t)std::max(1, n_items_vec(m)) * sizeof(double)));
+  k_dot<double, double><<<n_items_vec(m), 128, 0, s>>>(elem_args(m), m->d_b.as<double>(), m->d_b.as<double>(),
                                                        part.as<double>());
   k_bnorm<<<npr_of(m), 128, 0, s>>>(fin_args(m), part.as<double>(), m->d_bnorm2.as<double>());
   CK(cudaGetLastError());
@@ -2352,6 +2633,7 @@ __global__ void k_h1_reduce_noalloc(int n_elem, int n_rhs, const double *part_er
 
 extern "C" hpse_status hpse_h1_error_noalloc(hpse_mesh *m, const double *u, const double *ref, const double *vq,
                                              const double *gq, double *out, void *stream) {
+  if (m && m->coord == HPSE_COORD_EDGE) return HPSE_ERR_INVALID_ARG;  // box meshes only
   if (!m || !out) return HPSE_ERR_INVALID_ARG;
   if (m->ndof == 0) {
     for (int r = 0; r < m->n_rhs; ++r) out[2 * r] = out[2 * r + 1] = 0.0;

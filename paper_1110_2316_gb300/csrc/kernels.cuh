@@ -85,6 +85,7 @@ __constant__ Tables c_tab;
 
 using hpse::COEF_LAPLACE;
 using hpse::COEF_SCALAR;
+using hpse::COEF_EDGE;
 using hpse::MODE_PLAIN;
 using hpse::MODE_PCG;
 using hpse::MODE_TRANSPOSE;
@@ -155,8 +156,15 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
     for (int k = 0; k < P; ++k) s += Ds[nend * P + k] * su[fidx(a, k, p1, p2)];
     FSLOT(f, sN)[sp] = s;
     const int nb = A.nbr[(int64_t)e * 6 + f];
-    if (nb >= 0 && A.self_only) {
+    if (nb != -1 && A.self_only) {
       FSLOT(f, sFn)[sp] = (real)0;
+      FSLOT(f, sNn)[sp] = (real)0;
+    } else if (nb < -1) {
+      // corner set (edge neighbourhood, face 0): its polynomial in x3 (the p2
+      // direction of this face), constant in theta and tau
+      const int64_t cb = (int64_t)r * A.ndof + A.dof_off[A.n_elem + (-2 - nb)];
+      const real bt = (MODE == MODE_PCG) ? (real)A.beta[A.prob[e] * A.n_rhs + r] : (real)0;
+      FSLOT(f, sFn)[sp] = nb_value<MODE>(A, cb + p2, bt);
       FSLOT(f, sNn)[sp] = (real)0;
     } else if (nb >= 0) {
       const int64_t base = (int64_t)r * A.ndof + A.dof_off[nb];
@@ -184,7 +192,7 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
       g2 += Ds[p2 * P + m] * F[m * P + p1];
     }
     const int nb = A.nbr[(int64_t)e * 6 + f];
-    if (nb >= 0) {
+    if (nb != -1) {
       const real *Fn = FSLOT(f, sFn);
       real h1 = 0, h2 = 0;
 #pragma unroll
@@ -192,7 +200,8 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
         h1 += Ds[p1 * P + m] * Fn[p2 * P + m];
         h2 += Ds[p2 * P + m] * Fn[m * P + p1];
       }
-      const real *gn = A.geo + (int64_t)nb * 4;
+      // a corner set shares the theta and x3 scales of its layer-1 element
+      const real *gn = nb >= 0 ? A.geo + (int64_t)nb * 4 : geo_e;
       FSLOT(f, sJ0)[sp] = F[sp] - Fn[sp];
       FSLOT(f, sJ1)[sp] = geo_e[t1] * g1 - gn[t1] * h1;
       FSLOT(f, sJ2)[sp] = geo_e[t2] * g2 - gn[t2] * h2;
@@ -210,6 +219,9 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
     const int f = t / P2, sp = t - f * P2;
     const int p1 = sp % P, p2 = sp / P;
     const real *J0 = FSLOT(f, sJ0), *J1 = FSLOT(f, sJ1), *J2 = FSLOT(f, sJ2), *J3 = FSLOT(f, sJ3);
+    // face-norm weights: w[0] on the L2 jump of u; (w[3k-2], w[3k-1], w[3k]) =
+    // (L2, quotient along t1, quotient along t2) on jump field k (1 on box meshes)
+    const real *wf = A.fw ? A.fw + ((int64_t)e * 6 + f) * hpse::FACE_W : nullptr;
     real t0 = 0, a1 = 0, a2 = 0, a3 = 0, b1 = 0, b2 = 0, b3 = 0;
 #pragma unroll
     for (int m = 0; m < P; ++m) {
@@ -222,13 +234,23 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
       a3 += mp * J3[p2 * P + m];
       b3 += kp * J3[p2 * P + m];
     }
-    FSLOT(f, sT0)[sp] = t0;
-    FSLOT(f, sA1)[sp] = a1;
-    FSLOT(f, sA2)[sp] = a2;
-    FSLOT(f, sA3)[sp] = a3;
-    FSLOT(f, sB1)[sp] = a1 + b1;
-    FSLOT(f, sB2)[sp] = a2 + b2;
-    FSLOT(f, sB3)[sp] = a3 + b3;
+    if (wf) {
+      FSLOT(f, sT0)[sp] = wf[0] * t0;
+      FSLOT(f, sA1)[sp] = wf[3] * a1;
+      FSLOT(f, sA2)[sp] = wf[6] * a2;
+      FSLOT(f, sA3)[sp] = wf[9] * a3;
+      FSLOT(f, sB1)[sp] = wf[1] * a1 + wf[2] * b1;
+      FSLOT(f, sB2)[sp] = wf[4] * a2 + wf[5] * b2;
+      FSLOT(f, sB3)[sp] = wf[7] * a3 + wf[8] * b3;
+    } else {
+      FSLOT(f, sT0)[sp] = t0;
+      FSLOT(f, sA1)[sp] = a1;
+      FSLOT(f, sA2)[sp] = a2;
+      FSLOT(f, sA3)[sp] = a3;
+      FSLOT(f, sB1)[sp] = a1 + b1;
+      FSLOT(f, sB2)[sp] = a2 + b2;
+      FSLOT(f, sB3)[sp] = a3 + b3;
+    }
   }
   __syncthreads();
   // F4: second factor (along p2): g0 -> J0 slot, g1..g3 -> J1..J3 slots
@@ -251,13 +273,32 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
     FSLOT(f, sJ3)[sp] = g3;
   }
   __syncthreads();
+  // corner side of the face r = r_1 (edge neighbourhood): minus the transposed
+  // corner traces of the weighted jumps, y_c[k] = -sum_p1 g0[k][p1]
+  // - s_x3 sum_m D[m][k] sum_p1 g2[m][p1] (the corner's theta and tau
+  // derivatives vanish), stored per (slot, rhs) for the corner kernel
+  if (A.cscr && !A.self_only) {
+    const int slot = A.cslot[e];
+    if (slot >= 0) {
+      for (int k = tid; k < P; k += nt) {
+        real s0 = 0, s2 = 0;
+        for (int p1 = 0; p1 < P; ++p1) s0 += FSLOT(0, sJ0)[k * P + p1];
+        for (int m = 0; m < P; ++m) {
+          real g2 = 0;
+          for (int p1 = 0; p1 < P; ++p1) g2 += FSLOT(0, sJ2)[m * P + p1];
+          s2 += Ds[m * P + k] * g2;
+        }
+        A.cscr[((int64_t)slot * A.n_rhs + r) * hpse::CSCR_STRIDE + k] = -(s0 + geo_e[2] * s2);
+      }
+    }
+  }
   // F5: transposed traces on the face grid: C (face layer) -> F slot, Gn (normal) -> N slot
   for (int t = tid; t < 6 * P2; t += nt) {
     const int f = t / P2, sp = t - f * P2;
     const int p1 = sp % P, p2 = sp / P;
     const int a = f >> 1;
     const int t1 = (a == 0) ? 1 : 0, t2 = (a == 2) ? 1 : 2;
-    const bool interior = A.nbr[(int64_t)e * 6 + f] >= 0;
+    const bool interior = A.nbr[(int64_t)e * 6 + f] != -1;
     const real *g1 = FSLOT(f, sJ1), *g2 = FSLOT(f, sJ2);
     real u1 = 0, u2 = 0;
 #pragma unroll
@@ -568,6 +609,9 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
     const int l = ok ? lp : Q2 - 1;
     const int qa = l % Q, qb = l / Q;
     const int64_t cbase = A.coef_off[e] + (int64_t)qb * Q + qa;
+    // edge neighbourhood: e^{2 tau} multiplies the x3 second derivative;
+    // tau is the x coordinate, constant along this z-column
+    const real sz2c = (COEF == COEF_EDGE) ? sz2 * A.kappa[(int64_t)e * hpse::KAPPA_STRIDE + qa] : sz2;
     real rho[Q];
     if (MODE == MODE_TRANSPOSE) {
 #pragma unroll
@@ -598,7 +642,7 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
             syy += c_tab.B[0][qc * P + k] * a01[k];
           }
         }
-        const real sigma0 = sz2 * s2 + s0;
+        const real sigma0 = sz2c * s2 + s0;
         if (COEF == COEF_SCALAR) {
           real mq, dx, dy, dz;
           load_coef4(A.coef + 4 * (cbase + (int64_t)qc * Q2), mq, dx, dy, dz);
@@ -625,7 +669,7 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
         real mq;
         load_coef4(A.coef + 4 * (cbase + (int64_t)qc * Q2), mq, dx, dy, dz);
       }
-      const real rz2 = sz2 * rq, rzd = dz * rq, rxd = dx * rq, ryd = dy * rq;
+      const real rz2 = sz2c * rq, rzd = dz * rq, rxd = dx * rq, ryd = dy * rq;
 #pragma unroll
       for (int k = 0; k < P; ++k) {
         rz[k] += c_tab.B[2][qc * P + k] * rz2;

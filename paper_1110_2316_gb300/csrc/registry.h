@@ -7,7 +7,11 @@
 
 namespace hpse {
 
-enum { COEF_LAPLACE = 0, COEF_SCALAR = 1 };
+// COEF_EDGE: -(u_11 + u_22 + kappa(x_1) u_33) in the edge neighbourhood's
+// modified coordinates, kappa = e^{2 tau} per x-point of the element
+enum { COEF_LAPLACE = 0, COEF_SCALAR = 1, COEF_EDGE = 2 };
+// KAPPA_STRIDE = 2 * HPSE_MAX_W + 1, CSCR_STRIDE = HPSE_MAX_W + 1 (checked in the host library)
+enum { KAPPA_STRIDE = 21, CSCR_STRIDE = 11, FACE_W = 10 };
 enum { MODE_PLAIN = 0, MODE_PCG = 1, MODE_TRANSPOSE = 2 };
 
 template <typename T>
@@ -32,6 +36,12 @@ struct ApplyArgsT {
   const double *rho;
   int32_t skip_faces;
   int32_t self_only;        // 1: neighbour traces taken as zero (diagonal blocks of A)
+  // edge neighbourhood (COEF_EDGE); null / 0 for box meshes
+  int32_t n_elem;           // corner set c's values start at dof_off[n_elem + c]
+  const T *kappa;           // [E][KAPPA_STRIDE]: e^{2 tau} at the element's Q x-points
+  const T *fw;              // [E][6][10] face-norm weights (null: all 1)
+  const int32_t *cslot;     // [E] slot of the element's corner face, or -1
+  T *cscr;                  // [slots][n_rhs][CSCR_STRIDE] corner-side face contributions
 };
 
 template <typename T>

@@ -1,0 +1,128 @@
+"""Edge-neighbourhood elements on the GPU (eq. 4.7 in modified coordinates)
+against the oracle: operator, right-hand side, element-block preconditioner
+with the corner blocks, PCG solutions; and the H^1 error of Table 6.18's
+problem computed from GPU solutions.
+
+Tolerances: FP64 applies 1e-12 of max|y| (as for box meshes); FP32 applies
+2e-5 of max|y| (W <= 5: the FP32 unit roundoff times the cancellation of the
+second-derivative matrices); solutions: relative difference <= kappa(A) x
+the stopping residual, with kappa(A) from the dense oracle operator.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as wl
+from oracle.edge import EdgeDiscretisation
+
+pytestmark = pytest.mark.gpu
+
+EPS64 = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1110_2316_gb300.build import build
+    build()
+    from paper_1110_2316_gb300 import api as A
+    return A
+
+
+def _problem(N, W, I=1, J=1):
+    base = wl.edge_laplace_singular(N=N, W=W)
+    return wl.EdgeProblem(wl.edge_mesh(N, W, I=I, J=J), base.f, base.g, base.u_exact, base.grad_exact)
+
+
+def _mesh(api, pb, n_rhs=1):
+    m = api.Mesh(pb.mesh, n_rhs=n_rhs, coef_kind=api.COEF_LAPLACE)
+    m.set_data(**api.problem_data_arrays(m, pb))
+    return m
+
+
+@pytest.mark.parametrize("N,W,I,J", [(3, 3, 1, 1), (2, 4, 2, 2), (3, 2, 2, 1)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_edge_apply_matches_oracle(api, N, W, I, J, prec):
+    pb = _problem(N, W, I, J)
+    d = EdgeDiscretisation(pb)
+    m = _mesh(api, pb)
+    assert m.ndof == d.ndof
+    U = wl.random_dofs(d.ndof, seed=3)
+    yo = d.apply_A(U)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    u = torch.tensor(U, dtype=dt, device="cuda")
+    y = torch.empty_like(u)
+    m.apply_operator(u, y)
+    err = np.abs(y.double().cpu().numpy() - yo).max() / np.abs(yo).max()
+    assert err <= (1e-12 if prec == "fp64" else 2e-5), err
+    m.close()
+
+
+def test_edge_rhs_matches_oracle(api):
+    pb = _problem(2, 3, 2, 2)
+    d = EdgeDiscretisation(pb)
+    m = _mesh(api, pb)
+    b = torch.empty(m.ndof, dtype=torch.float64, device="cuda")
+    m.get_rhs(b)
+    bo = d.rhs_b()
+    assert np.abs(b.cpu().numpy() - bo).max() <= 1e-12 * np.abs(bo).max()
+    m.close()
+
+
+def test_edge_block_preconditioner_matches_oracle(api):
+    pb = _problem(2, 3, 2, 1)
+    d = EdgeDiscretisation(pb)
+    A = d.dense_A()
+    m = _mesh(api, pb)
+    m.setup_block_preconditioner()
+    r = wl.random_dofs(d.ndof, seed=9)
+    z = torch.empty(d.ndof, dtype=torch.float64, device="cuda")
+    m.apply_preconditioner(torch.tensor(r, device="cuda"), z)
+    z = z.cpu().numpy()
+    blocks = [slice(d.off[e], d.off[e + 1]) for e in range(d.E)]
+    blocks += [slice(d.coff[c], d.coff[c] + d.Wc[c] + 1) for c in range(d.C)]
+    for sl in blocks:
+        B = A[sl, sl]
+        zo = np.linalg.solve(B, r[sl])
+        n = B.shape[0]
+        assert np.linalg.norm(z[sl] - zo) <= n * EPS64 * np.linalg.cond(B) * np.linalg.norm(zo)
+    m.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("precond", ["separable", "block"])
+def test_edge_solve_matches_oracle(api, prec, precond):
+    pb = _problem(3, 3)
+    d = EdgeDiscretisation(pb)
+    A = d.dense_A()
+    xo = np.linalg.solve(A, d.rhs_b())
+    m = _mesh(api, pb)
+    if precond == "block":
+        m.setup_block_preconditioner()
+    x = torch.zeros(m.ndof, dtype=torch.float64, device="cuda")
+    rep = m.pcg_solve(x, tol=1e-11, prec=api.FP64 if prec == "fp64" else api.FP32, max_iter=200000)
+    assert rep["status"] == 0 and rep["rel_residual"] <= 1e-11
+    kA = np.linalg.cond(A)
+    assert np.linalg.norm(x.cpu().numpy() - xo) <= kA * 2e-11 * np.linalg.norm(xo)
+    m.close()
+
+
+def test_table_6_18_h1_error_from_gpu_solutions(api):
+    # relative H^1 error (%) of Table 6.18 at W = 2..5: 0.4645, 0.1314, 0.0402, 0.0124;
+    # layers N = 2W + 4
+    table = {2: 0.464542e-2, 3: 0.131359e-2, 4: 0.402204e-3, 5: 0.123974e-3}
+    errs = {}
+    for W in (2, 3, 4, 5):
+        pb = wl.edge_laplace_singular(N=2 * W + 4, W=W)
+        d = EdgeDiscretisation(pb)
+        m = _mesh(api, pb)
+        m.setup_block_preconditioner()
+        x = torch.zeros(m.ndof, dtype=torch.float64, device="cuda")
+        rep = m.pcg_solve(x, tol=1e-10, prec=api.FP32, max_iter=200000)
+        assert rep["status"] == 0
+        err, nrm = d.h1_error_exact(x.cpu().numpy())
+        errs[W] = np.sqrt(err / nrm)
+        m.close()
+    for W in (2, 3, 4, 5):
+        assert table[W] / 5 < errs[W] < table[W] * 5, (W, errs[W], table[W])
+    for W in (3, 4, 5):
+        assert errs[W] < 0.5 * errs[W - 1], errs

@@ -480,3 +480,26 @@ class EdgeDiscretisation:
                                           (pdz[:, None, None] - wz) ** 2)))
                 nrm += float(np.sum(wq * (wv ** 2 + wr ** 2 + wth ** 2 + wz ** 2)))
         return err, nrm
+
+
+def apply_separable_preconditioner(disc, R):
+    """The separable preconditioner of an edge discretisation: on every finite
+    element the C* form (eq. 5.30) with eta = sup e^tau over the element, on
+    every corner set its exact block A_cc (the corner's rows and columns of A)."""
+    from .precond import apply_Cstar_inv_block
+    Z = np.zeros_like(R)
+    for e in range(disc.E):
+        P = disc.P[e]
+        eta = float(np.exp(disc.mesh.elem_hi[e, 0]))
+        blk = R[disc.off[e]:disc.off[e + 1]].reshape(P, P, P)
+        Z[disc.off[e]:disc.off[e + 1]] = apply_Cstar_inv_block(blk, disc.W[e], eta).ravel()
+    for c in range(disc.C):
+        n = disc.Wc[c] + 1
+        sl = slice(disc.coff[c], disc.coff[c] + n)
+        Acc = np.zeros((n, n))
+        for j in range(n):
+            U = np.zeros(disc.ndof)
+            U[disc.coff[c] + j] = 1.0
+            Acc[:, j] = disc.corner_apply(U, c)
+        Z[sl] = np.linalg.solve(Acc, R[sl])
+    return Z

@@ -126,3 +126,57 @@ def apply_block_inverse(disc, R, factors=None):
     for e in range(disc.E):
         Z[disc.off[e]:disc.off[e + 1]] = sla.cho_solve(factors[e], R[disc.off[e]:disc.off[e + 1]])
     return Z
+
+
+# ---------------------------------------------------------------------------
+# C* form of edge (and vertex-edge) elements, eq. (5.29)-(5.30): with a small
+# factor eta in the third variable, C*(u) = int u_xx^2 + u_yy^2 + eta^4 u_zz^2
+# + u_x^2 + u_y^2 + eta^2 u_z^2 + u^2, diagonal in the tensor basis of the
+# generalised eigenpairs (E - mu F) b = 0 in x, y and (G - nu H) d = 0 in z with
+# G(v) = int eta^4 v''^2 + eta^2 v'^2, H(v) = int v^2 (eq. 5.31-5.38); the
+# eigenvalues are mu_i + mu_j + nu_k + 1 (eq. 5.42).  1-D integrals with the
+# (W+1)-point GLL rule, as for the C-form.
+# ---------------------------------------------------------------------------
+def one_d_G(W: int, eta: float):
+    """G and H of eq. (5.33)-(5.34) in the nodal GLL basis."""
+    _, _, D1, D2, Wd = one_d_forms(W)
+    return eta ** 4 * D2.T @ Wd @ D2 + eta ** 2 * D1.T @ Wd @ D1, Wd
+
+
+def cstar_eigen_z(W: int, eta: float):
+    G, H = one_d_G(W, eta)
+    nu, S = sla.eigh(G, H)
+    return np.maximum(nu, 0.0), S
+
+
+def dense_Cstar(W: int, eta: float):
+    """C* of eq. (5.30) on u[k, j, i] flattened (x fastest)."""
+    E, F, *_ = one_d_forms(W)
+    G, H = one_d_G(W, eta)
+    return kron3(H, F, E) + kron3(H, E, F) + kron3(G, F, F) + kron3(H, F, F)
+
+
+def dense_Bstar(W: int, eta: float):
+    """B* of eq. (5.29): second derivatives (the mixed x-y one included, as in
+    its transformed form and in B of the edge elements), z-derivatives weighted
+    by eta per derivative, first derivatives and u itself."""
+    _, _, D1, D2, Wd = one_d_forms(W)
+    I = np.eye(W + 1)
+    ops = {0: I, 1: D1, 2: D2}
+    terms = [((2, 0, 0), 1.0), ((0, 2, 0), 1.0), ((1, 1, 0), 1.0), ((1, 0, 1), eta ** 2), ((0, 1, 1), eta ** 2),
+             ((0, 0, 2), eta ** 4), ((1, 0, 0), 1.0), ((0, 1, 0), 1.0), ((0, 0, 1), eta ** 2), ((0, 0, 0), 1.0)]
+    Wq = kron3(Wd, Wd, Wd)
+    B = np.zeros(((W + 1) ** 3,) * 2)
+    for (ax, ay, az), c in terms:
+        Gm = kron3(ops[az], ops[ay], ops[ax])
+        B += c * Gm.T @ Wq @ Gm
+    return B
+
+
+def apply_Cstar_inv_block(r, W: int, eta: float):
+    """z = C*^{-1} r for one block r[k, j, i] by fast diagonalisation."""
+    mu, S = eigenbasis(W)
+    nu, Sz = cstar_eigen_z(W, eta)
+    t = np.einsum("kc,jb,ia,kji->cba", Sz, S, S, r, optimize=True)
+    t = t / (nu[:, None, None] + mu[None, :, None] + mu[None, None, :] + 1.0)
+    return np.einsum("kc,jb,ia,cba->kji", Sz, S, S, t, optimize=True)

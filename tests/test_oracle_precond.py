@@ -98,3 +98,34 @@ def test_block_pcg_reaches_the_cholesky_solution():
     xc = cholesky_solve(d.dense_A(), b)
     assert rel <= 1e-12
     assert np.linalg.norm(x - xc) <= 1e-8 * np.linalg.norm(xc)
+
+
+# ---- C* form of edge elements (eq. 5.29-5.30) -----------------------------
+def test_cstar_reduces_to_C_at_eta_one():
+    from oracle.precond import dense_Cstar
+    for W in (2, 5):
+        assert np.abs(dense_Cstar(W, 1.0) - dense_C(W)).max() == 0.0
+
+
+@pytest.mark.parametrize("eta", [1.0, 0.2, 1e-3])
+def test_cstar_fast_diagonalisation_inverts_dense(eta):
+    from oracle.precond import apply_Cstar_inv_block, dense_Cstar
+    W = 4
+    r = np.random.default_rng(2).standard_normal((W + 1,) * 3)
+    z = apply_Cstar_inv_block(r, W, eta)
+    back = (dense_Cstar(W, eta) @ z.ravel()).reshape(r.shape)
+    assert np.abs(back - r).max() <= 1e-10 * np.abs(r).max()
+
+
+def test_cstar_spectrally_equivalent_uniformly_in_eta():
+    # the thesis: C* and B* are spectrally equivalent with constants independent
+    # of eta (which tends to 0 towards the edge): kappa(C*^-1 B*) stays bounded
+    import scipy.linalg as sla
+    from oracle.precond import dense_Bstar, dense_Cstar
+    for W in (2, 4):
+        ks = []
+        for eta in (1.0, 0.3, 0.1, 1e-2, 1e-4):
+            ev = sla.eigh(dense_Bstar(W, eta), dense_Cstar(W, eta), eigvals_only=True)
+            assert ev.min() > 0
+            ks.append(ev.max() / ev.min())
+        assert max(ks) <= ks[0] * 1.0001 and min(ks) >= 1.0, ks

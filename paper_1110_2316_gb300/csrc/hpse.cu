@@ -212,6 +212,7 @@ struct hpse_mesh {
   std::vector<int> item_n;                // DOF count of each vector item (elements, then corner sets)
   DevBuf d_item_n, d_kappa64, d_kappa32, d_fw64, d_fw32, d_cslot, d_cW, d_cprob, d_slot_ptr, d_slot_list;
   DevBuf d_cinv64, d_cinv32, d_cscr64, d_cscr32;
+  DevBuf d_zeig64, d_zeig32;              // C* form: per element x3 eigenbasis and eigenvalues
   int precond_kind = HPSE_PRECOND_SEPARABLE;
   bool bj_ready = false;
   DevBuf d_bj_off;            // int64 per element: offset of its packed block
@@ -813,6 +814,8 @@ static PrecArgsT<T> prec_args(const hpse_mesh *m, const Group &g) {
   a.ndof = m->ndof;
   a.dof_off = m->d_dof_off.as<int64_t>();
   a.prob = m->d_prob.as<int32_t>();
+  if (m->coord == HPSE_COORD_EDGE)
+    a.zeig = (sizeof(T) == 8) ? (const T *)m->d_zeig64.p : (const T *)m->d_zeig32.p;
   return a;
 }
 
@@ -1026,6 +1029,32 @@ static hpse_status setup_edge(hpse_mesh *m) {
       }
     }
   }
+  // C* form (eq. 5.29-5.30) of every element: in x3 the 1-D forms
+  // G = eta^4 D2^T Wp D2 + eta^2 D^T Wp D and H = Wp with eta = sup e^tau over
+  // the element; (G - nu H) d = 0 in the symmetric form Wp^{-1/2} G Wp^{-1/2},
+  // stored like the master tables (node-major eigenvectors, then nu)
+  std::vector<double> zeig((size_t)E * hpse::ZEIG_STRIDE, 0.0);
+  for (int e = 0; e < E; ++e) {
+    const hm::DegreeTables &t = m->tabs.at(m->W[e]);
+    const int P = t.P;
+    const double eta = std::exp(m->hi[3 * e]), e2 = eta * eta, e4 = e2 * e2;
+    const std::vector<double> D2 = hm::matmul(t.D, t.D, P, P, P);
+    std::vector<double> G((size_t)P * P, 0.0), V, nu;
+    for (int i = 0; i < P; ++i)
+      for (int j = 0; j < P; ++j) {
+        double v = 0.0;
+        for (int k = 0; k < P; ++k) v += t.wp[k] * (e4 * D2[k * P + i] * D2[k * P + j] + e2 * t.D[k * P + i] * t.D[k * P + j]);
+        G[i * P + j] = v / std::sqrt(t.wp[i] * t.wp[j]);
+      }
+    hm::jacobi_eigen(G, P, nu, V);
+    double *z = &zeig[(size_t)e * hpse::ZEIG_STRIDE];
+    for (int k = 0; k < P; ++k)
+      for (int c = 0; c < P; ++c) z[k * P + c] = V[k * P + c] / std::sqrt(t.wp[k]);
+    for (int c = 0; c < P; ++c) z[P * P + c] = nu[c] < 0 ? 0.0 : nu[c];
+  }
+  std::vector<float> zeig32(zeig.begin(), zeig.end());
+  CK(upload(m->d_zeig64, zeig));
+  CK(upload(m->d_zeig32, zeig32));
   std::vector<float> kap32(kap.begin(), kap.end()), fw32(fw.begin(), fw.end());
   CK(upload(m->d_kappa64, kap));
   CK(upload(m->d_kappa32, kap32));

@@ -756,7 +756,11 @@ constexpr int PC_ITEMS_RAW = 384 / PC_TPI;
 constexpr int PC_ITEMS = PC_ITEMS_RAW < 1 ? 1 : (PC_ITEMS_RAW > 8 ? 8 : PC_ITEMS_RAW);
 constexpr int PC_NT = PC_ITEMS * PC_TPI;
 constexpr int PC_WARPS_PER_ITEM = PC_TPI / 32;
-constexpr size_t PC_BYTES = (size_t)PC_ITEMS * 2 * P3 * sizeof(real) + (size_t)(PC_NT / 32) * 2 * sizeof(double);
+// per item: two P^3 blocks; then the reduction buffer; then per item the x3
+// eigenbasis and eigenvalues of the C* form (edge neighbourhood)
+constexpr size_t PC_RED_OFF = (size_t)PC_ITEMS * 2 * P3 * sizeof(real);
+constexpr size_t PC_Z_OFF = PC_RED_OFF + (size_t)(PC_NT / 32) * 2 * sizeof(double);
+constexpr size_t PC_BYTES = PC_Z_OFF + (size_t)PC_ITEMS * (P2 + P) * sizeof(real);
 
 // out = (S^T or S) applied along `axis` of one P x P x P block (x fastest);
 // thread lt of the item handles line lt (no loop: PC_TPI >= P^2 lines)
@@ -776,6 +780,24 @@ __device__ __forceinline__ void tensor_stage(const real *in, real *out, int axis
 #pragma unroll
       for (int k = 0; k < P; ++k) s += (transpose ? c_tab.S[k * P + c] : c_tab.S[c * P + k]) * v[k];
       out[b + c * stride] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// as tensor_stage along x3 (axis 2) with the P x P matrix Sz (node-major) from
+// shared memory: the per-element x3 eigenbasis of the C* form (eq. 5.30)
+__device__ __forceinline__ void tensor_stage_z(const real *in, real *out, const real *Sz, bool transpose, int lt) {
+  if (lt < P2) {
+    real v[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) v[k] = in[lt + k * P2];
+#pragma unroll
+    for (int c = 0; c < P; ++c) {
+      real s = 0;
+#pragma unroll
+      for (int k = 0; k < P; ++k) s += (transpose ? Sz[k * P + c] : Sz[c * P + k]) * v[k];
+      out[lt + c * P2] = s;
     }
   }
   __syncthreads();
@@ -816,7 +838,9 @@ __global__ void __launch_bounds__(PC_NT) k_precond(const PrecArgs A) {
   const int lt = threadIdx.x - sub * PC_TPI;
   real *s0 = reinterpret_cast<real *>(pc_raw) + (size_t)sub * 2 * P3;
   real *s1 = s0 + P3;
-  double *red = reinterpret_cast<double *>(pc_raw + (size_t)PC_ITEMS * 2 * P3 * sizeof(real));
+  double *red = reinterpret_cast<double *>(pc_raw + PC_RED_OFF);
+  real *sz = reinterpret_cast<real *>(pc_raw + PC_Z_OFF) + (size_t)sub * (P2 + P);
+  const bool cstar = A.zeig != nullptr;
   __shared__ real smu[P];
   const int item = blockIdx.x * PC_ITEMS + sub;
   const bool valid = item < A.n_group * A.n_rhs;
@@ -825,6 +849,8 @@ __global__ void __launch_bounds__(PC_NT) k_precond(const PrecArgs A) {
   const int e = A.elems[ge];
   const int64_t base = (int64_t)rr * A.ndof + A.dof_off[e];
   if (threadIdx.x < P) smu[threadIdx.x] = c_tab.MU[threadIdx.x];
+  if (cstar)
+    for (int t = lt; t < P2 + P; t += PC_TPI) sz[t] = A.zeig[(int64_t)e * hpse::ZEIG_STRIDE + t];
   DotAcc arr, arz;
   if (valid) {
     if (MODE == MODE_PCG) {
@@ -844,13 +870,15 @@ __global__ void __launch_bounds__(PC_NT) k_precond(const PrecArgs A) {
   __syncthreads();
   tensor_stage(s0, s1, 0, true, lt);
   tensor_stage(s1, s0, 1, true, lt);
-  tensor_stage(s0, s1, 2, true, lt);
+  if (cstar) tensor_stage_z(s0, s1, sz, true, lt);
+  else tensor_stage(s0, s1, 2, true, lt);
   for (int t = lt; t < P3; t += PC_TPI) {
     const int a = t % P, b = (t / P) % P, c = t / P2;
-    s1[t] = s1[t] / (smu[a] + smu[b] + smu[c] + (real)1);
+    s1[t] = s1[t] / (smu[a] + smu[b] + (cstar ? sz[P2 + c] : smu[c]) + (real)1);
   }
   __syncthreads();
-  tensor_stage(s1, s0, 2, false, lt);
+  if (cstar) tensor_stage_z(s1, s0, sz, false, lt);
+  else tensor_stage(s1, s0, 2, false, lt);
   tensor_stage(s0, s1, 1, false, lt);
   tensor_stage(s1, s0, 0, false, lt);
   if (valid) {

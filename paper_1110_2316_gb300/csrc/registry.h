@@ -11,7 +11,7 @@ namespace hpse {
 // modified coordinates, kappa = e^{2 tau} per x-point of the element
 enum { COEF_LAPLACE = 0, COEF_SCALAR = 1, COEF_EDGE = 2 };
 // KAPPA_STRIDE = 2 * HPSE_MAX_W + 1, CSCR_STRIDE = HPSE_MAX_W + 1 (checked in the host library)
-enum { KAPPA_STRIDE = 21, CSCR_STRIDE = 11, FACE_W = 10 };
+enum { KAPPA_STRIDE = 21, CSCR_STRIDE = 11, FACE_W = 10, ZEIG_STRIDE = 132 };
 enum { MODE_PLAIN = 0, MODE_PCG = 1, MODE_TRANSPOSE = 2 };
 
 template <typename T>
@@ -61,6 +61,10 @@ struct PrecArgsT {
   const double *alpha;
   double *part_rr;
   double *part_rz;
+  // edge neighbourhood, C* form (eq. 5.30): per element the x3 eigenbasis
+  // S_z (P x P, node-major) then its eigenvalues nu (P), ZEIG_STRIDE apart;
+  // null for box meshes (the master C-form in every direction)
+  const T *zeig;
 };
 
 // Packed FP64 tables for one degree, in the order of the device struct:

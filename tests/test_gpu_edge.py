@@ -126,3 +126,28 @@ def test_table_6_18_h1_error_from_gpu_solutions(api):
         assert table[W] / 5 < errs[W] < table[W] * 5, (W, errs[W], table[W])
     for W in (3, 4, 5):
         assert errs[W] < 0.5 * errs[W - 1], errs
+
+
+def test_edge_separable_preconditioner_matches_oracle(api):
+    # C* form (eq. 5.30) on the finite elements, exact blocks on the corner sets;
+    # two independent eigen-decompositions (scipy, the library's Jacobi) agree
+    # to O(eps kappa) with kappa = max sigma / min sigma of each element
+    from oracle.edge import apply_separable_preconditioner
+    from oracle.precond import cstar_eigen_z, eigenbasis
+    pb = _problem(3, 4, 2, 1)
+    d = EdgeDiscretisation(pb)
+    m = _mesh(api, pb)
+    r = wl.random_dofs(d.ndof, seed=4)
+    zo = apply_separable_preconditioner(d, r)
+    z = torch.empty(d.ndof, dtype=torch.float64, device="cuda")
+    m.apply_preconditioner(torch.tensor(r, device="cuda"), z)
+    z = z.cpu().numpy()
+    mu, _ = eigenbasis(4)
+    for e in range(d.E):
+        nu, _ = cstar_eigen_z(4, float(np.exp(d.mesh.elem_hi[e, 0])))
+        kappa = (2 * mu.max() + nu.max() + 1) / (2 * mu.min() + nu.min() + 1)
+        sl = slice(d.off[e], d.off[e + 1])
+        assert np.abs(z[sl] - zo[sl]).max() <= max(1e-12, 8 * EPS64 * 2 * kappa) * np.abs(zo[sl]).max(), e
+    sl = slice(int(d.coff[0]), d.ndof)
+    assert np.abs(z[sl] - zo[sl]).max() <= 1e-10 * np.abs(zo[sl]).max()
+    m.close()

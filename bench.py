@@ -56,8 +56,10 @@ def parse():
     ap.add_argument("--precond", default="block", choices=["block", "separable"],
                     help="block: exact element blocks of A (set up once, FP64 factors); "
                          "separable: the C-form of eq. (5.19)-(5.20)")
-    ap.add_argument("--workload", default="varcoef", choices=["varcoef", "adjoint"],
-                    help="varcoef: the 64-RHS W=8 solve; adjoint: the 256-problem theta-gradient batch")
+    ap.add_argument("--workload", default="varcoef", choices=["varcoef", "adjoint", "edge"],
+                    help="varcoef: the 64-RHS W=8 solve; adjoint: the 256-problem theta-gradient batch; "
+                         "edge: the uneven-degree batch of edge-neighbourhood problems")
+    ap.add_argument("--edge-replicas", type=int, default=146, help="copies of each degree W = 2..8")
     ap.add_argument("--adj-problems", type=int, default=256)
     ap.add_argument("--adj-fd-problems", type=int, default=16)
     ap.add_argument("--fd-tol", type=float, default=1e-8, help="relative tolerance of the FD correction solves")
@@ -348,15 +350,78 @@ def run_adjoint(args, local):
     return 0
 
 
+def run_edge(args, local):
+    """Uneven-degree batch of edge-neighbourhood problems (Table 6.18's Laplace
+    problem u = r^(1/3) sin(theta/3) x3 on the quarter cylinder, modified
+    coordinates, N = 2W + 4 geometric layers, mu = 0.15), W = 2..8, each
+    degree replicated: one launch per degree group per operator apply.
+    Reports the FP32 apply GDOF/s, the mixed and FP64 time-to-solution with the
+    element-block preconditioner, and the H1 difference of the two solutions."""
+    import torch
+    from paper_1110_2316_gb300.build import build
+    build()
+    from paper_1110_2316_gb300 import api
+    dev = torch.device("cuda", local)
+    Ws = [W for W in range(2, 9) for _ in range(args.edge_replicas)]
+    t0 = time.perf_counter()
+    pb = wl.edge_batch(Ws)
+    m = api.Mesh(pb.mesh, n_rhs=1, coef_kind=api.COEF_LAPLACE, device=local)
+    m.set_data(**api.problem_data_arrays(m, pb))
+    t_setup = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    m.setup_block_preconditioner()
+    torch.cuda.synchronize()
+    t_prec = time.perf_counter() - t1
+    n = m.ndof
+    u = torch.randn(n, dtype=torch.float32, device=dev)
+    y = torch.empty_like(u)
+    for _ in range(3):
+        m.apply_operator(u, y)
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record()
+    for _ in range(20):
+        m.apply_operator(u, y)
+    a1.record()
+    torch.cuda.synchronize()
+    apply_ms = a0.elapsed_time(a1) / 20
+    out, sol = {}, {}
+    for name, prec in (("mixed", api.FP32), ("fp64", api.FP64)):
+        x = torch.zeros(n, dtype=torch.float64, device=dev)
+        m.pcg_solve(x, tol=TOL, prec=prec, max_iter=64, raise_on_error=False)  # graph capture
+        x.zero_()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record()
+        rep = m.pcg_solve(x, tol=TOL, prec=prec, max_iter=200000, raise_on_error=False)
+        c1.record()
+        torch.cuda.synchronize()
+        out[name] = dict(tts_s=c0.elapsed_time(c1) / 1e3, iterations=rep["iterations"], refreshes=rep["sweeps"],
+                         status=rep["status"], rel_residual=rep["rel_residual"])
+        sol[name] = x
+    h = m.h1_error(sol["mixed"], ref=sol["fp64"])
+    line = dict(metric="edge-neighbourhood batch: operator-apply GDOF/s and time-to-solution, mixed vs FP64",
+                value=n / (apply_ms * 1e-3) / 1e9, unit="GDOF/s", higher_is_better=True, n_gpus=1, dtype="f32",
+                data="synthetic",
+                config=dict(workload="Table 6.18 Laplace problem on the quarter cylinder, edge-neighbourhood "
+                                     "elements in (ln r, theta, x3), W = 2..8 x %d replicas, N = 2W+4 layers, "
+                                     "mu = 0.15, tol 1e-10" % args.edge_replicas,
+                            n_problem=len(Ws), n_elem=int(pb.mesh.n_elem), n_corner=int(pb.mesh.n_corner), ndof=n),
+                apply_ms=apply_ms, solves=out, speedup=out["fp64"]["tts_s"] / out["mixed"]["tts_s"],
+                h1_rel_diff_mixed_vs_fp64=float(np.sqrt(h[0, 0] / h[0, 1])),
+                setup_s=t_setup, setup_block_precond_s=t_prec)
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "adjoint":
+    if args.workload in ("adjoint", "edge"):
         import torch
         _, _, local = dist_env()
         torch.cuda.set_device(local)
-        return run_adjoint(args, local)
+        return run_adjoint(args, local) if args.workload == "adjoint" else run_edge(args, local)
     import torch
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)

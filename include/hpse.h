@@ -110,8 +110,13 @@ typedef struct {
    * element order, then the corner sets' W+1 values.  hpse_query_points
    * returns modified coordinates; the caller samples f and g at
    * r = e^tau, theta, x3 (physical data), the library forms F^e = e^{2 tau} f.
-   * Not supported with HPSE_COORD_EDGE: the adjoint entry points and the
-   * H^1 norms (HPSE_ERR_INVALID_ARG). */
+   * hpse_h1_error on an edge mesh takes the difference of two discrete
+   * solutions only (ref given): e^{2 tau} v^2 + v_tau^2 + v_theta^2 +
+   * e^{2 tau} v_x3^2 over each element's (2W+1)^3 GLL rule in modified
+   * coordinates, and on each corner set int_0^{r_1} r dr x (its theta span)
+   * x int (p^2 + p_x3^2) dx3.  Not supported with HPSE_COORD_EDGE
+   * (HPSE_ERR_INVALID_ARG): the adjoint entry points, hpse_h1_error against
+   * pointwise data, hpse_h1_error_noalloc. */
   int32_t coord;               /* HPSE_COORD_CARTESIAN (0) or HPSE_COORD_EDGE (1)   */
   int32_t n_corner;            /* corner sets (HPSE_COORD_EDGE), else 0            */
   const int32_t *corner_W;     /* [n_corner] degree in x3 (= that of its elements) */

@@ -503,3 +503,50 @@ def apply_separable_preconditioner(disc, R):
             Acc[:, j] = disc.corner_apply(U, c)
         Z[sl] = np.linalg.solve(Acc, R[sl])
     return Z
+
+
+def h1_diff(disc, U, V, nq=None):
+    """(||u_h - v_h||_{H^1}^2, ||v_h||_{H^1}^2) of two discrete solutions in
+    physical coordinates.  Finite elements: e^{2 tau} v^2 + v_tau^2 + v_theta^2
+    + e^{2 tau} v_x3^2 in modified coordinates with the (2W+1)-point GLL rule
+    (reading: the element rule of the regular region), or an nq-point Gauss
+    rule if nq is given; corner sets: p(x3) on r < r_1, integrated exactly in r
+    and theta, with the (2W+1)-point GLL rule in x3 (exact for p^2)."""
+    out = []
+    for X in (U - V, V):
+        tot = 0.0
+        for e in range(disc.E):
+            P = disc.P[e]
+            xp, _ = gll(P)
+            if nq is None:
+                xg, wg = gll(2 * disc.W[e] + 1)
+            else:
+                xg, wg = np.polynomial.legendre.leggauss(nq)
+            B = [lagrange_eval(xp, xg, d) for d in range(2)]
+            lo, hh = disc.mesh.elem_lo[e], disc.h(e) / 2.0
+            taus = lo[0] + (xg + 1.0) * hh[0]
+            s = disc.scale(e)
+            u = disc.block(X, e)
+            v = eval_tensor(u, B[0], B[0], B[0])
+            vt = s[0] * eval_tensor(u, B[1], B[0], B[0])
+            vh = s[1] * eval_tensor(u, B[0], B[1], B[0])
+            vz = s[2] * eval_tensor(u, B[0], B[0], B[1])
+            e2 = np.exp(2.0 * taus)[None, None, :]
+            wq = wg[:, None, None] * wg[None, :, None] * wg[None, None, :] * float(np.prod(hh))
+            tot += float(np.sum(wq * (e2 * v * v + vt * vt + vh * vh + e2 * vz * vz)))
+        for c in range(disc.C):
+            n = disc.Wc[c] + 1
+            xp, _ = gll(n)
+            xg, wg = gll(2 * disc.Wc[c] + 1)
+            p = disc.corner(X, c)
+            for e in range(disc.E):
+                if int(disc.mesh.elem_nbr[e, 0]) != -2 - c:
+                    continue
+                r1 = float(np.exp(disc.mesh.elem_lo[e, 0]))
+                hth = disc.mesh.elem_hi[e, 1] - disc.mesh.elem_lo[e, 1]
+                hz = disc.mesh.elem_hi[e, 2] - disc.mesh.elem_lo[e, 2]
+                p0 = lagrange_eval(xp, xg, 0) @ p
+                p1 = (2.0 / hz) * (lagrange_eval(xp, xg, 1) @ p)
+                tot += 0.5 * r1 * r1 * hth * 0.5 * hz * float(np.sum(wg * (p0 * p0 + p1 * p1)))
+        out.append(tot)
+    return tuple(out)

@@ -193,6 +193,7 @@ struct hpse_mesh {
   std::map<int, hm::DegreeTables> tabs;
   std::vector<Group> groups;
   // device mesh arrays
+  // d_prob: problem of each vector item (n_elem + n_corner entries)
   DevBuf d_dof_off, d_nbr, d_geo64, d_geo32, d_prob, d_coef_off, d_prob_ptr, d_prob_elems, d_elem_W;
   DevBuf d_coef64, d_coef32;  // [nquad][4] (m, d_x, d_y, d_z) per point (COEF_SCALAR)
   DevBuf d_b;                 // FP64 right-hand side
@@ -213,6 +214,7 @@ struct hpse_mesh {
   DevBuf d_item_n, d_kappa64, d_kappa32, d_fw64, d_fw32, d_cslot, d_cW, d_cprob, d_slot_ptr, d_slot_list;
   DevBuf d_cinv64, d_cinv32, d_cscr64, d_cscr32;
   DevBuf d_zeig64, d_zeig32;              // C* form: per element x3 eigenbasis and eigenvalues
+  DevBuf d_ch1;                           // H^1 norm of corner sets: (r_1^2/2) x theta span x h_x3/2, s_x3
   int precond_kind = HPSE_PRECOND_SEPARABLE;
   bool bj_ready = false;
   DevBuf d_bj_off;            // int64 per element: offset of its packed block
@@ -647,6 +649,13 @@ struct H1Args {
   const double *const *qtab;
   const double *u, *ref, *vq, *gq;
   double *part_err, *part_nrm;
+  // edge neighbourhood (difference of two discrete solutions only): e^{2 tau}
+  // per element x-point; corner sets: their W, and per set (r_1^2/2) x theta
+  // span x half slab length, then s_x3
+  const double *kappa;
+  int32_t n_elem, n_corner;
+  const int32_t *cW;
+  const double *cfac;
 };
 
 __device__ void h1_fields(const double *blk, int P, int Q, const double *B0, const double *B1, double *X0, double *X1,
@@ -710,7 +719,10 @@ __global__ void k_h1(H1Args A) {
       uz *= geo[2];
       const double wJ = wq[qa] * wq[qb] * wq[qc] * geo[3];
       if (A.ref) {
-        const double v = u * u + ux * ux + uy * uy + uz * uz;
+        // edge neighbourhood: dx = e^{2 tau} dtau dtheta dx3 and
+        // |grad v|^2 = e^{-2 tau} (v_tau^2 + v_theta^2) + v_x3^2
+        const double kq = A.kappa ? A.kappa[(int64_t)e * hpse::KAPPA_STRIDE + qa] : 1.0;
+        const double v = kq * u * u + ux * ux + uy * uy + kq * uz * uz;
         if (pass == 0) serr += wJ * v;
         else snrm += wJ * v;
       } else {
@@ -728,6 +740,41 @@ __global__ void k_h1(H1Args A) {
   if (threadIdx.x == 0) {
     A.part_err[item] = serr;
     A.part_nrm[item] = snrm;
+  }
+}
+
+// corner sets of the edge neighbourhood: on r < r_1 the difference is
+// p(x3), so its squared H^1 norm in physical coordinates is
+// int_0^{r_1} r dr x (theta span) x int (p^2 + p_x3^2) dx3, the last integral
+// with the (2W+1)-point GLL rule.  grid: n_corner * n_rhs, 32 threads.
+__global__ void k_h1_corner(H1Args A) {
+  const int item = blockIdx.x;
+  const int c = item / A.n_rhs, r = item - c * A.n_rhs;
+  const int W = A.cW[c], P = W + 1, Q = 2 * W + 1;
+  const double *tb = A.qtab[W];
+  const double *B0 = tb, *B1 = tb + Q * P, *wq = tb + 2 * Q * P + 2 * Q * Q;
+  const int64_t base = (int64_t)r * A.ndof + A.dof_off[A.n_elem + c];
+  const double fac = A.cfac[2 * c], sz = A.cfac[2 * c + 1];
+  double se = 0.0, sn = 0.0;
+  for (int q = threadIdx.x; q < Q; q += blockDim.x) {
+    double d0 = 0.0, d1 = 0.0, v0 = 0.0, v1 = 0.0;
+    for (int k = 0; k < P; ++k) {
+      const double dv = A.u[base + k] - A.ref[base + k];
+      d0 += B0[q * P + k] * dv;
+      d1 += B1[q * P + k] * dv;
+      v0 += B0[q * P + k] * A.ref[base + k];
+      v1 += B1[q * P + k] * A.ref[base + k];
+    }
+    se += wq[q] * (d0 * d0 + sz * sz * d1 * d1);
+    sn += wq[q] * (v0 * v0 + sz * sz * v1 * v1);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    se += __shfl_xor_sync(0xffffffffu, se, o);
+    sn += __shfl_xor_sync(0xffffffffu, sn, o);
+  }
+  if (threadIdx.x == 0) {
+    A.part_err[(int64_t)(A.n_elem + c) * A.n_rhs + r] = fac * se;
+    A.part_nrm[(int64_t)(A.n_elem + c) * A.n_rhs + r] = fac * sn;
   }
 }
 
@@ -1124,6 +1171,15 @@ static hpse_status setup_edge(hpse_mesh *m) {
   CK(upload(m->d_cprob, m->cprob));
   CK(upload(m->d_slot_ptr, m->slot_ptr));
   CK(upload(m->d_slot_list, m->slot_list));
+  std::vector<double> ch1(2 * (size_t)C, 0.0);
+  for (int e = 0; e < E; ++e) {
+    if (m->cslot[e] < 0) continue;
+    const int c = -2 - m->nbr[6 * e];
+    const double r1 = std::exp(m->lo[3 * e]), hz = m->hi[3 * e + 2] - m->lo[3 * e + 2];
+    ch1[2 * c] += 0.5 * r1 * r1 * (m->hi[3 * e + 1] - m->lo[3 * e + 1]) * 0.5 * hz;
+    ch1[2 * c + 1] = 2.0 / hz;
+  }
+  CK(upload(m->d_ch1, ch1));
   const size_t ns = (size_t)std::max(1, S) * m->n_rhs * hpse::CSCR_STRIDE;
   CK(m->d_cscr64.alloc(ns * sizeof(double)));
   CK(m->d_cscr32.alloc(ns * sizeof(float)));
@@ -1344,7 +1400,13 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
   CK(upload(m->d_nbr, m->nbr));
   CK(upload(m->d_geo64, geo));
   CK(upload(m->d_geo32, geo32));
-  CK(upload(m->d_prob, m->prob));
+  {
+    // problem of every vector item (elements, then corner sets): the vector
+    // kernels index it by item
+    std::vector<int> prob_items(m->prob);
+    prob_items.insert(prob_items.end(), m->cprob.begin(), m->cprob.end());
+    CK(upload(m->d_prob, prob_items));
+  }
   CK(upload(m->d_prob_ptr, m->prob_ptr));
   CK(upload(m->d_prob_elems, m->prob_elems));
   CK(upload(m->d_elem_W, m->W));
@@ -2218,7 +2280,8 @@ extern "C" hpse_status hpse_pcg_solve(hpse_mesh *m, const hpse_solve_opts *o, do
 
 extern "C" hpse_status hpse_h1_error(hpse_mesh *m, const double *u, const double *ref, const double *vq,
                                      const double *gq, double *out, void *stream) {
-  if (m && m->coord == HPSE_COORD_EDGE) return HPSE_ERR_INVALID_ARG;  // box meshes only
+  // edge neighbourhood: the difference of two discrete solutions only
+  if (m && m->coord == HPSE_COORD_EDGE && !ref) return HPSE_ERR_INVALID_ARG;
   if (!m || !out) return HPSE_ERR_INVALID_ARG;
   if (m->ndof == 0) {
     for (int r = 0; r < m->n_rhs; ++r) out[2 * r] = out[2 * r + 1] = 0.0;
@@ -2227,10 +2290,10 @@ extern "C" hpse_status hpse_h1_error(hpse_mesh *m, const double *u, const double
   if (!u || (!ref && (!vq || !gq))) return HPSE_ERR_INVALID_ARG;
   CK(cudaSetDevice(m->device));
   cudaStream_t s = (cudaStream_t)stream;
-  const int ni = n_items_all(m);
+  const int ni = n_items_all(m), nv = n_items_vec(m);
   DevBuf pe, pn, dtabs;
-  CK(pe.alloc((size_t)ni * sizeof(double)));
-  CK(pn.alloc((size_t)ni * sizeof(double)));
+  CK(pe.alloc((size_t)std::max(1, nv) * sizeof(double)));
+  CK(pn.alloc((size_t)std::max(1, nv) * sizeof(double)));
   std::vector<const double *> tp(HPSE_MAX_W + 1, nullptr);
   int Wmax = 1;
   for (auto &kv : m->d_qtab) {
@@ -2239,6 +2302,7 @@ extern "C" hpse_status hpse_h1_error(hpse_mesh *m, const double *u, const double
   }
   CK(upload(dtabs, tp));
   H1Args A;
+  memset(&A, 0, sizeof(A));
   A.n_rhs = m->n_rhs;
   A.ndof = m->ndof;
   A.nquad = m->nquad;
@@ -2253,19 +2317,29 @@ extern "C" hpse_status hpse_h1_error(hpse_mesh *m, const double *u, const double
   A.gq = gq;
   A.part_err = pe.as<double>();
   A.part_nrm = pn.as<double>();
+  A.kappa = m->coord == HPSE_COORD_EDGE ? m->d_kappa64.as<double>() : nullptr;
+  A.n_elem = m->n_elem;
+  A.n_corner = m->n_corner;
+  A.cW = m->d_cW.as<int32_t>();
+  A.cfac = m->d_ch1.as<double>();
   const int P = Wmax + 1, Q = 2 * Wmax + 1;
   const size_t smem = (size_t)(P * P * P + 2 * Q * P * P + 3 * Q * Q * P) * sizeof(double);
   CK(cudaFuncSetAttribute(k_h1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_h1<<<ni, 256, smem, s>>>(A);
   CK(cudaGetLastError());
   ++g_launches;
-  std::vector<double> he(ni), hn(ni);
-  CK(cudaMemcpyAsync(he.data(), pe.p, (size_t)ni * sizeof(double), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(hn.data(), pn.p, (size_t)ni * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (m->n_corner > 0) {
+    k_h1_corner<<<m->n_corner * m->n_rhs, 32, 0, s>>>(A);
+    CK(cudaGetLastError());
+    ++g_launches;
+  }
+  std::vector<double> he(nv), hn(nv);
+  CK(cudaMemcpyAsync(he.data(), pe.p, (size_t)nv * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hn.data(), pn.p, (size_t)nv * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   for (int r = 0; r < m->n_rhs; ++r) {
     double a = 0.0, b = 0.0;
-    for (int e = 0; e < m->n_elem; ++e) {
+    for (int e = 0; e < m->n_elem + m->n_corner; ++e) {
       a += he[(size_t)e * m->n_rhs + r];
       b += hn[(size_t)e * m->n_rhs + r];
     }
@@ -2697,6 +2771,7 @@ extern "C" hpse_status hpse_h1_error_noalloc(hpse_mesh *m, const double *u, cons
   }
   CK(cudaMemcpyAsync(qtab, tp, sizeof(tp), cudaMemcpyHostToDevice, s));
   H1Args A;
+  memset(&A, 0, sizeof(A));
   A.n_rhs = m->n_rhs;
   A.ndof = m->ndof;
   A.nquad = m->nquad;

@@ -151,3 +151,49 @@ def test_edge_separable_preconditioner_matches_oracle(api):
     sl = slice(int(d.coff[0]), d.ndof)
     assert np.abs(z[sl] - zo[sl]).max() <= 1e-10 * np.abs(zo[sl]).max()
     m.close()
+
+
+def test_edge_h1_norm_matches_oracle(api):
+    # difference of two discrete solutions: element terms with the (2W+1)^3 GLL
+    # rule in modified coordinates, corner sets in physical coordinates; both
+    # sides sum the same terms in FP64 (1e-12 relative)
+    from oracle.edge import h1_diff
+    pb = _problem(3, 3, 2, 2)
+    d = EdgeDiscretisation(pb)
+    m = _mesh(api, pb)
+    rng = np.random.default_rng(5)
+    U, V = rng.standard_normal(d.ndof), rng.standard_normal(d.ndof)
+    h = m.h1_error(torch.tensor(U, device="cuda"), ref=torch.tensor(V, device="cuda"))
+    e, n = h1_diff(d, U, V)
+    assert h[0, 0] == pytest.approx(e, rel=1e-12) and h[0, 1] == pytest.approx(n, rel=1e-12)
+    m.close()
+
+
+def test_edge_batch_equals_individual_solves(api):
+    # uneven degrees in one launch: the batched solution of each problem equals
+    # its own solve (per-problem PCG scalars; same iteration path)
+    Ws = (2, 4, 3)
+    pb = wl.edge_batch(Ws)
+    m = _mesh(api, pb)
+    m.setup_block_preconditioner()
+    x = torch.zeros(m.ndof, dtype=torch.float64, device="cuda")
+    assert m.pcg_solve(x, tol=1e-11, prec=api.FP64, max_iter=200000)["status"] == 0
+    parts = []
+    for W in Ws:
+        one = wl.edge_batch([W])
+        mi = _mesh(api, one)
+        mi.setup_block_preconditioner()
+        xi = torch.zeros(mi.ndof, dtype=torch.float64, device="cuda")
+        assert mi.pcg_solve(xi, tol=1e-11, prec=api.FP64, max_iter=200000)["status"] == 0
+        parts.append((one, xi.cpu().numpy()))
+        mi.close()
+    # reassemble: elements of the problems in order, then the corner sets in order
+    xb = x.cpu().numpy()
+    el, co = [], []
+    for one, xi in parts:
+        d = EdgeDiscretisation(one)
+        el.append(xi[:d.off[-1]])
+        co.append(xi[d.off[-1]:])
+    ref = np.concatenate(el + co)
+    assert np.linalg.norm(xb - ref) <= 1e-8 * np.linalg.norm(ref)
+    m.close()

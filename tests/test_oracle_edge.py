@@ -97,3 +97,23 @@ def test_h1_error_decays_exponentially_in_W():
     e2, e3 = _h1_rel(2), _h1_rel(3)
     assert e3 < 0.3 * e2
     assert 0.131359e-2 / 5 < e3 < 0.131359e-2 * 5, e3
+
+
+def test_h1_diff_quadrature_against_gauss():
+    # the (2W+1)-point GLL rule of the discrete H^1 norm against a 40-point Gauss
+    # rule of the same fields: only the weight e^{2 tau} = e^{2 tau_c} e^{h lambda}
+    # (h = ln(1/0.15) = 1.9 per layer) is not a polynomial, and the 7-point rule
+    # (W = 3) leaves about 1e-5 of it (a missing or misplaced weight would change
+    # the norm by O(1)); the corner term against its closed form for a constant p
+    from oracle.edge import h1_diff
+    pb = wl.edge_laplace_singular(N=3, W=3)
+    d = EdgeDiscretisation(pb)
+    rng = np.random.default_rng(1)
+    U, V = rng.standard_normal(d.ndof), rng.standard_normal(d.ndof)
+    a = h1_diff(d, U, V)
+    b = h1_diff(d, U, V, nq=40)
+    assert a[0] == pytest.approx(b[0], rel=1e-4) and a[1] == pytest.approx(b[1], rel=1e-4)
+    Z = np.zeros(d.ndof)
+    Z[d.coff[0]:] = 2.0  # p = 2 on r < r_1: (r_1^2 / 2) (pi / 2) (1) (4)
+    r1 = float(np.exp(d.mesh.elem_lo[0, 0]))
+    assert h1_diff(d, Z, np.zeros(d.ndof))[0] == pytest.approx(0.5 * r1 * r1 * (np.pi / 2) * 4.0, rel=1e-13)

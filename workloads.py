@@ -560,3 +560,39 @@ def edge_polynomial(N, W, mu=0.15) -> EdgeProblem:
         return -(2.0 * t * z) / (r * r) - 2.0
 
     return EdgeProblem(mesh, [f], [u], u, None, name="edge_polynomial", meta=dict(tau1=tau1))
+
+
+def concat_edge_meshes(meshes: List[EdgeMeshDesc]) -> EdgeMeshDesc:
+    """Batch independent edge neighbourhoods (element ids and corner codes offset)."""
+    los, his, Ws, nbrs, probs, cW, clo, chi, cprob = [], [], [], [], [], [], [], [], []
+    off = coff = poff = 0
+    for m in meshes:
+        los.append(m.elem_lo)
+        his.append(m.elem_hi)
+        Ws.append(m.elem_W)
+        nb = m.elem_nbr.copy()
+        nb[nb >= 0] += off
+        nb[nb <= -2] -= coff
+        nbrs.append(nb)
+        probs.append(m.elem_problem + poff)
+        cW.append(m.corner_W)
+        clo.append(m.corner_lo)
+        chi.append(m.corner_hi)
+        cprob.append(m.corner_problem + poff)
+        off += m.n_elem
+        coff += m.n_corner
+        poff += m.n_problem
+    cat = np.concatenate
+    return EdgeMeshDesc(cat(los), cat(his), cat(Ws).astype(np.int32), cat(nbrs).astype(np.int32),
+                        cat(probs).astype(np.int32), cat(cW).astype(np.int32), cat(clo), cat(chi),
+                        cat(cprob).astype(np.int32), poff)
+
+
+def edge_batch(Ws, mu=0.15) -> EdgeProblem:
+    """Independent copies of Table 6.18's problem with uneven degrees W_p
+    (N_p = 2 W_p + 4 layers each) in one batch; every problem has the same
+    data functions."""
+    base = edge_laplace_singular(N=2, W=2, mu=mu)
+    mesh = concat_edge_meshes([edge_mesh(2 * int(W) + 4, int(W), mu=mu) for W in Ws])
+    return EdgeProblem(mesh, base.f, base.g, base.u_exact, base.grad_exact, name="edge_batch",
+                       meta=dict(Ws=[int(w) for w in Ws]))

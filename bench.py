@@ -149,10 +149,10 @@ def volume_flops_per_rhs(Ws):
 
 # DRAM bytes (read + write) of one FP32 k_apply launch on the default
 # workload (8^3 elements, W = 8, 64 rhs, variable a), from one ncu capture
-# (dram__bytes_read.sum 181,104,128 + dram__bytes_write.sum 130,454,016;
+# (dram__bytes_read.sum 180,250,624 + dram__bytes_write.sum 131,584,256;
 # profiles/k_apply_fp32_w8_varcoef.md).  Valid for that configuration and the
 # kernel as captured; reported as null for any other configuration.
-APPLY_TRAFFIC_BYTES = {(8, 8, 64): 181104128 + 130454016}
+APPLY_TRAFFIC_BYTES = {(8, 8, 64): 180250624 + 131584256}
 
 
 def fp32_peak_tflops():
@@ -447,12 +447,7 @@ def main():
     mesh.set_data(**data)
     torch.cuda.synchronize()
     t_setdata = time.perf_counter() - t1
-    t_prec = 0.0
-    if args.precond == "block":
-        t2 = time.perf_counter()
-        mesh.setup_block_preconditioner()
-        torch.cuda.synchronize()
-        t_prec = time.perf_counter() - t2
+
     n_tot = args.rhs * mesh.ndof
     if args.apply_only:
         dt = torch.float32 if args.prec == "fp32" else torch.float64
@@ -472,6 +467,13 @@ def main():
         print(json.dumps(dict(mode="apply-only", prec=args.prec, rhs=args.rhs, ms_per_apply=ms,
                               gdofs=n_tot / ms / 1e6, alg_tflops=fl / ms / 1e9)))
         return 0
+    # the preconditioner (not used by the apply-only mode above)
+    t_prec = 0.0
+    if args.precond == "block":
+        t2 = time.perf_counter()
+        mesh.setup_block_preconditioner()
+        torch.cuda.synchronize()
+        t_prec = time.perf_counter() - t2
     x = torch.zeros(n_tot, dtype=torch.float64, device=dev)
 
     def solve(m, xx, prec):

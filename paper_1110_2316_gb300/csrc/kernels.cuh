@@ -138,7 +138,7 @@ __device__ __forceinline__ real nb_value(const ApplyArgs &A, int64_t idx, real b
   return A.u[idx];
 }
 
-template <int MODE>
+template <int COEF, int MODE>
 __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, real *sy, real *scr, const real *Ds,
                            const real *MPs, const real *KPs, const real *geo_e) {
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -159,7 +159,7 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
     if (nb != -1 && A.self_only) {
       FSLOT(f, sFn)[sp] = (real)0;
       FSLOT(f, sNn)[sp] = (real)0;
-    } else if (nb < -1) {
+    } else if (COEF == COEF_EDGE && nb < -1) {
       // corner set (edge neighbourhood, face 0): its polynomial in x3 (the p2
       // direction of this face), constant in theta and tau
       const int64_t cb = (int64_t)r * A.ndof + A.dof_off[A.n_elem + (-2 - nb)];
@@ -221,7 +221,7 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
     const real *J0 = FSLOT(f, sJ0), *J1 = FSLOT(f, sJ1), *J2 = FSLOT(f, sJ2), *J3 = FSLOT(f, sJ3);
     // face-norm weights: w[0] on the L2 jump of u; (w[3k-2], w[3k-1], w[3k]) =
     // (L2, quotient along t1, quotient along t2) on jump field k (1 on box meshes)
-    const real *wf = A.fw ? A.fw + ((int64_t)e * 6 + f) * hpse::FACE_W : nullptr;
+    const real *wf = (COEF == COEF_EDGE && A.fw) ? A.fw + ((int64_t)e * 6 + f) * hpse::FACE_W : nullptr;
     real t0 = 0, a1 = 0, a2 = 0, a3 = 0, b1 = 0, b2 = 0, b3 = 0;
 #pragma unroll
     for (int m = 0; m < P; ++m) {
@@ -277,7 +277,7 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
   // corner traces of the weighted jumps, y_c[k] = -sum_p1 g0[k][p1]
   // - s_x3 sum_m D[m][k] sum_p1 g2[m][p1] (the corner's theta and tau
   // derivatives vanish), stored per (slot, rhs) for the corner kernel
-  if (A.cscr && !A.self_only) {
+  if (COEF == COEF_EDGE && A.cscr && !A.self_only) {
     const int slot = A.cslot[e];
     if (slot >= 0) {
       for (int k = tid; k < P; k += nt) {
@@ -729,7 +729,7 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
 
   // ---- faces ---------------------------------------------------------------
   if (MODE != MODE_TRANSPOSE && !A.skip_faces)
-    face_phase<MODE>(A, e, r, su, sy, sT + P3, stab, stab + P2, stab + 2 * P2, geo_e);
+    face_phase<COEF, MODE>(A, e, r, su, sy, sT + P3, stab, stab + P2, stab + 2 * P2, geo_e);
 
   // ---- store (and the p.q partial of PCG) --------------------------------
   double part = 0.0;

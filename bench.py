@@ -608,6 +608,11 @@ def main():
                    h1_rel_diff_mixed_vs_fp64=h1)
         ms2.close()
 
+    tile_report = None
+    if args.precond == "block":
+        v, tile, tms = mesh.block_tile(args.W, api.FP32)
+        tile_report = dict(variant=v, rows_x_rhs=list(tile),
+                           candidates_ms={str(k): round(float(x), 4) for k, x in enumerate(tms) if x > 0})
     if rank == 0:
         cb = cpu_baseline(pb, args.cpu_sample_elems, args.cpu_reps) if ws == 1 else None
         line = dict(
@@ -622,7 +627,8 @@ def main():
             solve=dict(gdof_applies_per_s=solve_rate, iterations=reps[-1]["iterations"], refreshes=reps[-1]["sweeps"],
                        applies=reps[-1]["applies"], rel_residual=reps[-1]["rel_residual"],
                        setup_sample_s=t_sample, setup_set_data_s=t_setdata,
-                       setup_block_precond_s=t_prec, precond=args.precond),
+                       setup_block_precond_s=t_prec, precond=args.precond,
+                       block_tile=tile_report),
             tts_comparison=cmp,
             apply_ms=dict(fp32=apply_ms, fp64=apply64_ms),
             roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,

@@ -219,6 +219,21 @@ hpse_status hpse_apply_preconditioner(hpse_mesh *m, int32_t prec, const void *r,
  * definite to FP64 working accuracy (the separable form stays selected). */
 hpse_status hpse_setup_block_preconditioner(hpse_mesh *m);
 
+/* Tile shape of the element-block preconditioner's two triangular products,
+ * per degree W and precision: hpse_setup_block_preconditioner times every
+ * candidate shape for the mesh's right-hand-side count on the factors it has
+ * just built (variants 0-2 for >= 32 right-hand sides, 3-4 for 2..31, 5-7 for
+ * one; 2, 4 and 6 in FP32 only) and keeps the fastest.  hpse_block_tile
+ * returns the chosen variant, its tile (rows x right-hand sides per CTA) and,
+ * if ms is not NULL, the measured milliseconds of each of the 8 variants (0
+ * for those not tried); HPSE_ERR_NO_DATA before the set-up.
+ * hpse_set_block_tile overrides the choice (HPSE_ERR_INVALID_ARG for a
+ * variant that does not exist in that precision).  No counterpart in the
+ * thesis. */
+hpse_status hpse_block_tile(const hpse_mesh *m, int32_t W, int32_t prec, int32_t *variant, int32_t *tile_rows,
+                            int32_t *tile_rhs, float *ms);
+hpse_status hpse_set_block_tile(hpse_mesh *m, int32_t W, int32_t prec, int32_t variant);
+
 /* Choose the preconditioner (hpse_precond_kind).  HPSE_PRECOND_BLOCK needs a
  * successful hpse_setup_block_preconditioner (else HPSE_ERR_NO_DATA). */
 hpse_status hpse_select_preconditioner(hpse_mesh *m, int32_t kind);

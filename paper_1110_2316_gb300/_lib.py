@@ -66,6 +66,8 @@ SIGNATURES = {
     "hpse_apply_preconditioner": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "hpse_setup_block_preconditioner": (C.c_int, [C.c_void_p]),
     "hpse_select_preconditioner": (C.c_int, [C.c_void_p, C.c_int32]),
+    "hpse_block_tile": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hpse_set_block_tile": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]),
     "hpse_get_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "hpse_pcg_solve": (C.c_int, [C.c_void_p, C.POINTER(SolveOpts), C.c_void_p, C.POINTER(SolveReport),
                                  C.c_void_p]),

@@ -122,6 +122,17 @@ class Mesh:
         """Build and select the element-block preconditioner from the current data."""
         check(self._lib.hpse_setup_block_preconditioner(self._h), "hpse_setup_block_preconditioner")
 
+    def block_tile(self, W, prec):
+        """(variant, (tile rows, tile rhs), ms per variant) chosen by the autotuner."""
+        v, tr, tc = C.c_int32(), C.c_int32(), C.c_int32()
+        ms = np.zeros(8, dtype=np.float32)
+        check(self._lib.hpse_block_tile(self._h, int(W), int(prec), C.byref(v), C.byref(tr), C.byref(tc),
+                                        ms.ctypes.data_as(C.c_void_p)), "hpse_block_tile")
+        return int(v.value), (int(tr.value), int(tc.value)), ms
+
+    def set_block_tile(self, W, prec, variant):
+        check(self._lib.hpse_set_block_tile(self._h, int(W), int(prec), int(variant)), "hpse_set_block_tile")
+
     def select_preconditioner(self, kind):
         check(self._lib.hpse_select_preconditioner(self._h, int(kind)), "hpse_select_preconditioner")
 

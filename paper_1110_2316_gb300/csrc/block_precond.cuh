@@ -270,22 +270,46 @@ __global__ void k_bj_dot(BjArgs A, const T *z, const T *r, double *part) {
   if (threadIdx.x == 0) part[(int64_t)e * A.n_rhs + rr] = s;
 }
 
-// z = X^T (X r) for the group; t: scratch vector of the same layout.
+// Tile shapes of the two triangular products (rows x right-hand sides per
+// CTA), picked per degree group and precision by timing the candidates of
+// the right-hand-side count on the actual factors (bj_candidates); variants
+// 2, 4 and 6 exceed 48 KB of static shared memory in FP64 and exist in FP32
+// only.
+constexpr int BJ_NVAR = 8;
+constexpr int BJ_TILE[BJ_NVAR][2] = {{64, 64}, {128, 32}, {256, 16}, {128, 8}, {256, 8}, {128, 1}, {256, 1}, {64, 1}};
+inline bool bj_variant_ok(int v, bool fp32) { return v >= 0 && v < BJ_NVAR && (fp32 || (v != 2 && v != 4 && v != 6)); }
+inline int bj_candidates(int n_rhs, bool fp32, int *v) {
+  int n = 0;
+  const int all[3][3] = {{0, 1, 2}, {3, 4, -1}, {5, 6, 7}};
+  const int *c = all[n_rhs >= 32 ? 0 : (n_rhs >= 2 ? 1 : 2)];
+  for (int i = 0; i < 3; ++i)
+    if (c[i] >= 0 && bj_variant_ok(c[i], fp32)) v[n++] = c[i];
+  return n;
+}
+
+template <typename T, int TM, int RT, int TR, int TC>
+static void bj_pair(const BjArgs &a, const T *X, const T *r, T *t, T *z, cudaStream_t s) {
+  dim3 g(a.n_group * ((a.n + TM - 1) / TM), (a.n_rhs + RT - 1) / RT);
+  k_bj_tri<T, false, TM, RT, TR, TC><<<g, TR * TC, 0, s>>>(a, X, r, t);
+  k_bj_tri<T, true, TM, RT, TR, TC><<<g, TR * TC, 0, s>>>(a, X, t, z);
+}
+
+// z = X^T (X r) for the group with tile variant v; t: scratch vector of the same layout.
 template <typename T>
-static cudaError_t bj_apply_group(const BjArgs &a, const T *X, const T *r, T *t, T *z, cudaStream_t s) {
+static cudaError_t bj_apply_group(const BjArgs &a, const T *X, const T *r, T *t, T *z, cudaStream_t s, int v) {
   if (a.n_group == 0) return cudaSuccess;
-  if (a.n_rhs >= 32) {
-    dim3 g(a.n_group * ((a.n + 63) / 64), (a.n_rhs + 63) / 64);
-    k_bj_tri<T, false, 64, 64, 16, 16><<<g, 256, 0, s>>>(a, X, r, t);
-    k_bj_tri<T, true, 64, 64, 16, 16><<<g, 256, 0, s>>>(a, X, t, z);
-  } else if (a.n_rhs >= 2) {
-    dim3 g(a.n_group * ((a.n + 127) / 128), (a.n_rhs + 7) / 8);
-    k_bj_tri<T, false, 128, 8, 64, 4><<<g, 256, 0, s>>>(a, X, r, t);
-    k_bj_tri<T, true, 128, 8, 64, 4><<<g, 256, 0, s>>>(a, X, t, z);
+  if (v == 0) bj_pair<T, 64, 64, 16, 16>(a, X, r, t, z, s);
+  else if (v == 1) bj_pair<T, 128, 32, 32, 8>(a, X, r, t, z, s);
+  else if (v == 3) bj_pair<T, 128, 8, 64, 4>(a, X, r, t, z, s);
+  else if (v == 5) bj_pair<T, 128, 1, 128, 1>(a, X, r, t, z, s);
+  else if (v == 7) bj_pair<T, 64, 1, 64, 1>(a, X, r, t, z, s);
+  else if constexpr (sizeof(T) == 4) {
+    if (v == 2) bj_pair<T, 256, 16, 64, 4>(a, X, r, t, z, s);
+    else if (v == 4) bj_pair<T, 256, 8, 128, 2>(a, X, r, t, z, s);
+    else if (v == 6) bj_pair<T, 256, 1, 256, 1>(a, X, r, t, z, s);
+    else return cudaErrorInvalidValue;
   } else {
-    dim3 g(a.n_group * ((a.n + 127) / 128), a.n_rhs);
-    k_bj_tri<T, false, 128, 1, 128, 1><<<g, 128, 0, s>>>(a, X, r, t);
-    k_bj_tri<T, true, 128, 1, 128, 1><<<g, 128, 0, s>>>(a, X, t, z);
+    return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }

@@ -220,6 +220,8 @@ struct hpse_mesh {
   DevBuf d_bj_off;            // int64 per element: offset of its packed block
   DevBuf d_bj64, d_bj32;      // X = L^{-1} per element, packed lower triangle
   DevBuf bj_t64, bj_t32;      // scratch vector X r of the preconditioner
+  int bj_var[HPSE_MAX_W + 1][2] = {};  // tile variant of the products per degree and precision (autotuned)
+  float bj_ms[HPSE_MAX_W + 1][2][8] = {};  // measured time per variant (ms; 0: not a candidate)
   int threads[2][2][HPSE_MAX_W + 1];  // [kind][prec][W]
   // one stream per degree group: per-degree launches of one operator or
   // preconditioner application run concurrently (fork/join through events,
@@ -974,12 +976,12 @@ static hpse_status launch_bj_all(hpse_mesh *m, int mode, const PrecArgsT<T> &b, 
     if (mode == MODE_PCG) {
       k_bj_update<T><<<items, 128, 0, gs>>>(a, b.prob, b.alpha, b.x, b.r, b.p, b.q, b.part_rr);
       CK(cudaGetLastError());
-      CK(bj_apply_group<T>(a, X, b.r, t, b.zout, gs));
+      CK(bj_apply_group<T>(a, X, b.r, t, b.zout, gs, m->bj_var[g.W][sizeof(T) == 8 ? 0 : 1]));
       k_bj_dot<T><<<items, 128, 0, gs>>>(a, b.zout, b.r, b.part_rz);
       CK(cudaGetLastError());
       g_launches += 4;
     } else {
-      CK(bj_apply_group<T>(a, X, b.rin, t, b.zout, gs));
+      CK(bj_apply_group<T>(a, X, b.rin, t, b.zout, gs, m->bj_var[g.W][sizeof(T) == 8 ? 0 : 1]));
       g_launches += 2;
     }
   }
@@ -1742,8 +1744,79 @@ extern "C" hpse_status hpse_setup_block_preconditioner(hpse_mesh *m) {
   int32_t h_fail = 0;
   CK(cudaMemcpy(&h_fail, fail.p, sizeof(int32_t), cudaMemcpyDeviceToHost));
   if (h_fail) return HPSE_ERR_BREAKDOWN;
+  // autotuner: time every candidate tile shape of the two triangular products
+  // on the factors just built (right-hand-side count of the mesh, per degree
+  // group and precision; one warm-up, then the mean of 3 launches by CUDA
+  // events) and keep the fastest
+  {
+    DevBuf tin, tout;
+    const size_t nvb = std::max<size_t>(nv, 1) * sizeof(double);
+    if (tin.alloc(nvb) != cudaSuccess || tout.alloc(nvb) != cudaSuccess) return HPSE_ERR_OOM;
+    CK(cudaMemset(tin.p, 0, nvb));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (size_t gi = 0; gi < m->groups.size(); ++gi) {
+      const Group &g = m->groups[gi];
+      const BjArgs ba = bj_args(m, g, m->n_rhs);
+      for (int pi = 0; pi < 2; ++pi) {
+        int cand[3];
+        const int nc2 = bj_candidates(m->n_rhs, pi == 1, cand);
+        float best = 1e30f;
+        for (int k = 0; k < 8; ++k) m->bj_ms[g.W][pi][k] = 0.0f;
+        for (int ci = 0; ci < nc2; ++ci) {
+          const int v = cand[ci];
+          float ms = 0.0f;
+          for (int rep = 0; rep < 4; ++rep) {
+            if (rep == 1) CK(cudaEventRecord(e0, s));
+            if (pi == 0)
+              CK(bj_apply_group<double>(ba, m->d_bj64.as<double>(), tin.as<double>(), m->bj_t64.as<double>(),
+                                        tout.as<double>(), s, v));
+            else
+              CK(bj_apply_group<float>(ba, m->d_bj32.as<float>(), tin.as<float>(), m->bj_t32.as<float>(),
+                                       tout.as<float>(), s, v));
+            g_launches += 2;
+          }
+          CK(cudaEventRecord(e1, s));
+          CK(cudaEventSynchronize(e1));
+          CK(cudaEventElapsedTime(&ms, e0, e1));
+          ms /= 3.0f;
+          m->bj_ms[g.W][pi][v] = ms;
+          if (ms < best) {
+            best = ms;
+            m->bj_var[g.W][pi] = v;
+          }
+        }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
   m->bj_ready = true;
   m->precond_kind = HPSE_PRECOND_BLOCK;
+  return HPSE_OK;
+}
+
+extern "C" hpse_status hpse_block_tile(const hpse_mesh *m, int32_t W, int32_t prec, int32_t *variant,
+                                       int32_t *tile_rows, int32_t *tile_rhs, float *ms) {
+  if (!m || W < 1 || W > HPSE_MAX_W || (prec != HPSE_FP64 && prec != HPSE_FP32)) return HPSE_ERR_INVALID_ARG;
+  if (!m->bj_ready) return HPSE_ERR_NO_DATA;
+  const int pi = prec == HPSE_FP64 ? 0 : 1, v = m->bj_var[W][pi];
+  if (variant) *variant = v;
+  if (tile_rows) *tile_rows = BJ_TILE[v][0];
+  if (tile_rhs) *tile_rhs = BJ_TILE[v][1];
+  if (ms)
+    for (int k = 0; k < BJ_NVAR; ++k) ms[k] = m->bj_ms[W][pi][k];
+  return HPSE_OK;
+}
+
+extern "C" hpse_status hpse_set_block_tile(hpse_mesh *m, int32_t W, int32_t prec, int32_t variant) {
+  if (!m || W < 1 || W > HPSE_MAX_W || (prec != HPSE_FP64 && prec != HPSE_FP32)) return HPSE_ERR_INVALID_ARG;
+  if (!bj_variant_ok(variant, prec == HPSE_FP32)) return HPSE_ERR_INVALID_ARG;
+  CK(cudaSetDevice(m->device));
+  CK(cudaDeviceSynchronize());
+  drop_graphs(m);
+  m->bj_var[W][prec == HPSE_FP64 ? 0 : 1] = variant;
   return HPSE_OK;
 }
 

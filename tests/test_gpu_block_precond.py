@@ -159,3 +159,32 @@ def test_block_apply_many_rhs(api, n_rhs, prec):
                 bound = 2 * n * EPS32 * np.linalg.norm(np.abs(X).T @ (np.abs(X) @ np.abs(R[k][s])))
             assert np.linalg.norm(z[k][s] - zo[s]) <= bound, (n_rhs, prec, k, e)
     m.close()
+
+
+@pytest.mark.parametrize("n_rhs", [1, 5, 40])
+def test_block_tile_autotuner(api, n_rhs):
+    # every tile variant gives the same products (to the FP32 / FP64 rounding of
+    # a length-n sum), the autotuner picks a candidate of the rhs count, and
+    # the forced variants are honoured
+    base = wl.varcoef_manufactured(n=(2, 1, 1), W=3)
+    pb = wl.Problem(base.mesh, base.f * n_rhs, base.g * n_rhs, base.a, base.grad_a)
+    m = _mesh(api, pb, n_rhs)
+    m.setup_block_preconditioner()
+    cand = {1: (5, 6, 7), 5: (3, 4), 40: (0, 1, 2)}[n_rhs]
+    for prec, dt, tol in ((api.FP64, torch.float64, 1e-13), (api.FP32, torch.float32, 1e-5)):
+        v, tile, ms = m.block_tile(3, prec)
+        ok = [c for c in cand if prec == api.FP32 or c not in (2, 4, 6)]
+        assert v in ok and all(ms[c] > 0 for c in ok), (v, ms)
+        r = torch.tensor(wl.random_dofs(n_rhs * m.ndof, 3), dtype=dt, device="cuda")
+        outs = []
+        for c in ok:
+            m.set_block_tile(3, prec, c)
+            z = torch.empty_like(r)
+            m.apply_preconditioner(r, z)
+            outs.append(z.double())
+        for z in outs[1:]:
+            assert float((z - outs[0]).abs().max()) <= tol * float(outs[0].abs().max())
+    from paper_1110_2316_gb300._lib import HpseError
+    with pytest.raises(HpseError):
+        m.set_block_tile(3, api.FP64, 2)  # FP32-only shape
+    m.close()

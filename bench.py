@@ -132,8 +132,33 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# ---------------------------------------------------------------------------
+# weak scaling over ranks: every rank solves its own batch (no data-path
+# collective); only the timings are reduced
+# ---------------------------------------------------------------------------
+def shard_seed0(rank, rhs):
+    """First seed of rank `rank`'s right-hand sides: ranks own disjoint seed ranges."""
+    return 20260 + rhs * rank
+
+
+def reduce_max_ms(ms, ws, device):
+    """Maximum of a per-rank time over the ranks (the slowest rank sets the job time)."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_rate(ws, units_per_rank, ms_max):
+    """Whole-job throughput in G units/s: all ranks' units over the slowest rank's time."""
+    return ws * units_per_rank / (ms_max * 1e-3) / 1e9
+
+
 def make_problem(args, rank):
-    return wl.varcoef_random_rhs(n=args.n, W=args.W, n_rhs=args.rhs, seed0=20260 + args.rhs * rank)
+    return wl.varcoef_random_rhs(n=args.n, W=args.W, n_rhs=args.rhs, seed0=shard_seed0(rank, args.rhs))
 
 
 def volume_flops_per_rhs(Ws):
@@ -499,13 +524,9 @@ def main():
         ev1.record()
         torch.cuda.synchronize()
     launches = api.kernel_launch_count(reset=True)
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max_ms(ev0.elapsed_time(ev1) / args.steps, ws, dev)
     applies = float(np.mean([r["applies"] for r in reps]))
-    solve_rate = ws * n_tot * applies / (ms * 1e-3) / 1e9
+    solve_rate = weak_scaling_rate(ws, n_tot * applies, ms)
     clocks = clk.summary()
 
     # ---- dominant kernel: FP32 operator apply, timed alone -----------------------
@@ -522,12 +543,8 @@ def main():
     a1.record()
     torch.cuda.synchronize()
     apply_ms = a0.elapsed_time(a1) / na
-    apply_ms_all = apply_ms
-    if ws > 1:
-        t = torch.tensor([apply_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        apply_ms_all = float(t.item())
-    value = ws * n_tot / (apply_ms_all * 1e-3) / 1e9
+    apply_ms_all = reduce_max_ms(apply_ms, ws, dev)
+    value = weak_scaling_rate(ws, n_tot, apply_ms_all)
     alg_flops = volume_flops_per_rhs([int(w) for w in mesh.elem_W]) * args.rhs
     achieved = alg_flops / (apply_ms * 1e-3) / 1e12
     peak = fp32_peak_tflops()

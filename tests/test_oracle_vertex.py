@@ -1,0 +1,93 @@
+"""Pins of the vertex-neighbourhood oracle (eq. 4.3 in modified coordinates
+(phi, theta, ln rho)).
+
+* Face-norm weights against hand-computed integrals of the R-weighted L2 +
+  H^{1/2} norm in modified coordinates (linear traces).
+* A solution inside the discrete space, with the corner constant, makes R
+  vanish and is returned by the normal equations.
+* Variation identity (literal functional vs matrix-free A, Dirichlet data and
+  the corner set); A symmetric positive definite.
+* The H^1 error of Table 6.16's problem (u = rho^(1/2) sin(phi/2)) within 5x of
+  the table at W = 2 (W = 3 slow-marked), N = 2W + 4 layers.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import workloads as wl
+from oracle.edge import face_form
+from oracle.gll import gll
+from oracle.pcg import pcg
+from oracle.precond import element_block
+from oracle.vertex import VertexDiscretisation
+
+
+def test_vertex_face_norm_weights_closed_forms():
+    d = VertexDiscretisation(wl.vertex_poisson_singular(N=2, W=3))
+    e = 1
+    hp, ht, hc = d.h(e) / 2.0
+    Qf = d.Qf(e)
+    x, _ = gll(Qf)
+    one = np.ones(Qf)
+    for fi, (ha, hb) in ((1, (ht, hc)), (3, (hp, hc)), (5, (hp, ht))):
+        R = d.G(e, fi)
+        # v linear along t1 with unit slope in modified coordinates: L2 + quotient along t1
+        v = np.outer(one, ha * x)
+        want = R * (4 * hb * ha ** 3 / 3 + 8 * hb * ha ** 2)
+        got = float(v.ravel() @ face_form(Qf, *d.norm_weights(e, fi)) @ v.ravel())
+        assert got == pytest.approx(want, rel=1e-12), fi
+    assert d.G(e, 5) == pytest.approx(np.exp(d.mesh.elem_hi[e, 2]))
+    assert d.G(e, 4) == pytest.approx(np.exp(d.mesh.elem_lo[e, 2]))
+
+
+def test_vertex_polynomial_solution_is_reproduced():
+    pb = wl.vertex_polynomial(N=2, W=2)
+    d = VertexDiscretisation(pb)
+    U = d.nodal_interpolant(pb.u_exact)
+    assert d.functional(U) <= 1e-22 * d.functional(np.zeros(d.ndof))
+    x = np.linalg.solve(d.dense_A(), d.rhs_b())
+    assert np.linalg.norm(x - U) <= 1e-8 * np.linalg.norm(U)
+
+
+def test_vertex_variation_identity_and_spd():
+    d = VertexDiscretisation(wl.vertex_poisson_singular(N=2, W=2))
+    rng = np.random.default_rng(11)
+    U, V = rng.standard_normal(d.ndof), rng.standard_normal(d.ndof)
+    A, b = d.dense_A(), d.rhs_b()
+    assert np.abs(A - A.T).max() <= 1e-11 * np.abs(A).max()
+    assert np.linalg.eigvalsh(0.5 * (A + A.T)).min() > 0
+    for eps in (0.7, -2.1):
+        lhs = d.functional(U + eps * V)
+        rhs = d.functional(U) + 2 * eps * V @ (A @ U - b) + eps ** 2 * V @ A @ V
+        assert lhs == pytest.approx(rhs, rel=1e-10)
+
+
+def _h1_rel(W):
+    d = VertexDiscretisation(wl.vertex_poisson_singular(N=2 * W + 4, W=W))
+    fac = [sla.cho_factor(element_block(d, e)) for e in range(d.E)]
+    Ucb = np.zeros(d.ndof)
+    Ucb[d.coff[0]] = 1.0
+    acc = float(d.corner_apply(Ucb, 0)[0])
+
+    def M(r):
+        z = np.zeros_like(r)
+        for e in range(d.E):
+            z[d.off[e]:d.off[e + 1]] = sla.cho_solve(fac[e], r[d.off[e]:d.off[e + 1]])
+        z[d.coff[0]] = r[d.coff[0]] / acc
+        return z
+    x, _, rel = pcg(d.apply_A, M, d.rhs_b(), tol=1e-10, maxit=20000)
+    assert rel <= 1e-10
+    err, nrm = d.h1_error_exact(x)
+    return np.sqrt(err / nrm)
+
+
+def test_vertex_h1_error_matches_table_6_16_order():
+    e2 = _h1_rel(2)  # Table 6.16: 1.00821 %
+    assert 1.00821e-2 / 5 < e2 < 1.00821e-2 * 5, e2
+
+
+@pytest.mark.slow
+def test_vertex_h1_error_decays():
+    e2, e3 = _h1_rel(2), _h1_rel(3)  # Table 6.16: 1.00821 %, 0.0841462 %
+    assert e3 < 0.2 * e2
+    assert 0.841462e-3 / 5 < e3 < 0.841462e-3 * 5, e3

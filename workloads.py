@@ -456,6 +456,7 @@ class EdgeMeshDesc:
     corner_hi: np.ndarray      # [C] x3 upper end
     corner_problem: np.ndarray  # [C] int32
     n_problem: int = 1
+    kind: str = "edge"         # "edge" or "vertex" (modified coordinates (phi, theta, ln rho))
 
     @property
     def n_elem(self) -> int:
@@ -596,3 +597,93 @@ def edge_batch(Ws, mu=0.15) -> EdgeProblem:
     mesh = concat_edge_meshes([edge_mesh(2 * int(W) + 4, int(W), mu=mu) for W in Ws])
     return EdgeProblem(mesh, base.f, base.g, base.u_exact, base.grad_exact, name="edge_batch",
                        meta=dict(Ws=[int(w) for w in Ws]))
+
+
+# ---------------------------------------------------------------------------
+# Vertex neighbourhood (Section 2.3 / eq. 4.3): elements are boxes in the
+# modified coordinates (phi, theta, chi) = (phi, theta, ln rho) around a vertex
+# ---------------------------------------------------------------------------
+def vertex_mesh(N, W, mu=0.15, phi=(PI / 6, PI / 3), theta=(0.0, 1.5 * PI), I=1, J=3) -> EdgeMeshDesc:
+    """N finite layers in chi = ln rho (rho_i = mu^(N+1-i), layer 1 next to the
+    vertex) x I phi-sectors x J theta-sectors, degree W in every modified
+    coordinate; one corner set rho < rho_1 holding a constant (degree 0) shared
+    by every sector.  Axes (x, y, z) = (phi, theta, chi); the corner set is the
+    neighbour of face 4 (chi = lo) of layer 1, code -2.  Every other outer face
+    is Dirichlet.  Elements are numbered layer fastest, then phi, then theta."""
+    rho = [mu ** (N + 1 - i) for i in range(1, N + 2)]
+    chis = np.log(np.array(rho))
+    phs = np.linspace(phi[0], phi[1], I + 1)
+    ths = np.linspace(theta[0], theta[1], J + 1)
+    E = N * I * J
+    lo = np.zeros((E, 3))
+    hi = np.zeros((E, 3))
+    nbr = -np.ones((E, 6), dtype=np.int32)
+
+    def eid(i, a, b):
+        return (b * I + a) * N + i
+
+    for b in range(J):
+        for a in range(I):
+            for i in range(N):
+                e = eid(i, a, b)
+                lo[e] = (phs[a], ths[b], chis[i])
+                hi[e] = (phs[a + 1], ths[b + 1], chis[i + 1])
+                nbr[e, 0] = eid(i, a - 1, b) if a > 0 else -1
+                nbr[e, 1] = eid(i, a + 1, b) if a < I - 1 else -1
+                nbr[e, 2] = eid(i, a, b - 1) if b > 0 else -1
+                nbr[e, 3] = eid(i, a, b + 1) if b < J - 1 else -1
+                nbr[e, 4] = eid(i - 1, a, b) if i > 0 else -2
+                nbr[e, 5] = eid(i + 1, a, b) if i < N - 1 else -1
+    return EdgeMeshDesc(lo, hi, np.full(E, W, dtype=np.int32), nbr, np.zeros(E, dtype=np.int32),
+                        np.zeros(1, dtype=np.int32), np.zeros(1), np.zeros(1), np.zeros(1, dtype=np.int32),
+                        kind="vertex")
+
+
+def _sph_grid(phs, ths, rhos):
+    r, t, p = np.meshgrid(np.asarray(rhos, dtype=np.float64), np.asarray(ths, dtype=np.float64),
+                          np.asarray(phs, dtype=np.float64), indexing="ij")
+    return p, t, r
+
+
+def vertex_poisson_singular(N, W, mu=0.15) -> EdgeProblem:
+    """Table 6.16: -Lap u = f on {pi/6 < phi < pi/3, 0 < theta < 3 pi/2, rho < 1},
+    u = g on the boundary, exact w = rho^(1/2) sin(phi/2) (a vertex singularity);
+    f = -Lap w = -rho^(-3/2) (sin(phi/2) + cot(phi) cos(phi/2)) / 2.
+    Data are functions of spherical coordinates on tensor grids
+    fun(phis, thetas, rhos) -> [len rhos, len thetas, len phis]."""
+    mesh = vertex_mesh(N, W, mu=mu)
+
+    def w(ps, ts, rs):
+        p, t, r = _sph_grid(ps, ts, rs)
+        return np.sqrt(r) * np.sin(p / 2)
+
+    def grad(ps, ts, rs):
+        # (w_rho, w_phi / rho, w_theta / (rho sin phi))
+        p, t, r = _sph_grid(ps, ts, rs)
+        return 0.5 / np.sqrt(r) * np.sin(p / 2), 0.5 / np.sqrt(r) * np.cos(p / 2), 0.0 * r
+
+    def f(ps, ts, rs):
+        p, t, r = _sph_grid(ps, ts, rs)
+        return -0.5 * r ** -1.5 * (np.sin(p / 2) + np.cos(p / 2) / np.tan(p))
+
+    return EdgeProblem(mesh, [f], [w], w, grad, name="vertex_poisson_singular")
+
+
+def vertex_polynomial(N, W, mu=0.15) -> EdgeProblem:
+    """A solution inside the discrete space with the corner constant 2:
+    u = 2 + (chi - chi_1)^2 phi theta (chi = ln rho); -Lap u = f with
+    rho^2 Lap u = u_chichi + u_chi + u_phiphi + cot(phi) u_phi + u_thetatheta / sin^2(phi)."""
+    mesh = vertex_mesh(N, W, mu=mu)
+    chi1 = float(mesh.elem_lo[0, 2])
+
+    def u(ps, ts, rs):
+        p, t, r = _sph_grid(ps, ts, rs)
+        return 2.0 + (np.log(r) - chi1) ** 2 * p * t
+
+    def f(ps, ts, rs):
+        p, t, r = _sph_grid(ps, ts, rs)
+        c = np.log(r) - chi1
+        lap = 2 * p * t + 2 * c * p * t + c * c * t / np.tan(p)
+        return -lap / (r * r)
+
+    return EdgeProblem(mesh, [f], [u], u, None, name="vertex_polynomial", meta=dict(chi1=chi1))

@@ -117,13 +117,21 @@ typedef struct {
    * x int (p^2 + p_x3^2) dx3.  Not supported with HPSE_COORD_EDGE
    * (HPSE_ERR_INVALID_ARG): the adjoint entry points, hpse_h1_error against
    * pointwise data, hpse_h1_error_noalloc. */
-  int32_t coord;               /* HPSE_COORD_CARTESIAN (0) or HPSE_COORD_EDGE (1)   */
+  int32_t coord;               /* HPSE_COORD_CARTESIAN (0), _EDGE (1) or _VERTEX (2) */
   int32_t n_corner;            /* corner sets (HPSE_COORD_EDGE), else 0            */
   const int32_t *corner_W;     /* [n_corner] degree in x3 (= that of its elements) */
   const int32_t *corner_problem; /* [n_corner] problem index                       */
 } hpse_mesh_desc;
 
-enum { HPSE_COORD_CARTESIAN = 0, HPSE_COORD_EDGE = 1 };
+/* HPSE_COORD_VERTEX (eq. 4.3): boxes in (phi, theta, chi) = (phi, theta, ln rho)
+ * of a vertex at the origin, L^v u = -e^{chi/2} sqrt(sin phi) (u_chichi + u_chi +
+ * u_phiphi + cot(phi) u_phi + u_thetatheta / sin^2 phi), F^v = e^{5 chi/2}
+ * sqrt(sin phi) f, face norms L2 + H^{1/2} in modified coordinates times
+ * R = sup e^chi, Dirichlet ||sqrt(R)(u - g)||_{3/2}; the corner sets rho < rho_1
+ * hold one constant each (corner_W = 0), neighbour code -2-c on face 4
+ * (chi = lo); data sampled at (phi, theta, rho = e^chi).  Same restrictions as
+ * HPSE_COORD_EDGE, and no H^1 norm. */
+enum { HPSE_COORD_CARTESIAN = 0, HPSE_COORD_EDGE = 1, HPSE_COORD_VERTEX = 2 };
 
 /* Problem data (Section 4.2: F, g of eq. 4.2).  Host FP64 arrays, copied.
  *   f      [n_rhs][hpse_nquad()]        source at the volume points (required)

@@ -69,7 +69,8 @@ class Mesh:
         if self.is_edge:
             self._keep += [np.ascontiguousarray(desc.corner_W, dtype=np.int32),
                            np.ascontiguousarray(desc.corner_problem, dtype=np.int32)]
-            d.coord = _lib.COORD_EDGE
+            d.coord = _lib.COORD_VERTEX if getattr(desc, "kind", "edge") == "vertex" else _lib.COORD_EDGE
+            self.nbhd_kind = getattr(desc, "kind", "edge")
             d.n_corner = int(self._keep[5].shape[0])
             d.corner_W = self._keep[5].ctypes.data_as(C.c_void_p)
             d.corner_problem = self._keep[6].ctypes.data_as(C.c_void_p)
@@ -230,8 +231,12 @@ def problem_data_arrays(mesh: Mesh, problem):
     functions take cylindrical coordinates: they are sampled at r = e^tau.
     """
     if getattr(mesh, "is_edge", False):
-        def cyl(fun):
-            return lambda ts, hs, zs: fun(np.exp(ts), hs, zs)
+        if mesh.nbhd_kind == "vertex":   # (phi, theta, ln rho): sample at rho = e^chi
+            def cyl(fun):
+                return lambda ps, hs, cs: fun(ps, hs, np.exp(cs))
+        else:                            # (ln r, theta, x3): sample at r = e^tau
+            def cyl(fun):
+                return lambda ts, hs, zs: fun(np.exp(ts), hs, zs)
         from types import SimpleNamespace
         problem = SimpleNamespace(f=[cyl(v) for v in problem.f], g=[cyl(v) for v in problem.g], a=None,
                                   grad_a=None)

@@ -824,7 +824,7 @@ static ApplyArgsT<T> apply_args(const hpse_mesh *m, const Group &g, const T *u, 
   a.coef_off = m->d_coef_off.as<int64_t>();
   a.nquad = m->nquad;
   a.n_elem = m->n_elem;
-  if (m->coord == HPSE_COORD_EDGE) {
+  if (m->coord != HPSE_COORD_CARTESIAN) {
     const bool d = sizeof(T) == 8;
     a.kappa = d ? (const T *)m->d_kappa64.p : (const T *)m->d_kappa32.p;
     a.fw = d ? (const T *)m->d_fw64.p : (const T *)m->d_fw32.p;
@@ -1047,8 +1047,15 @@ extern "C" int64_t hpse_kernel_launch_count(int32_t reset) {
 // jumps in |||.|||, the x3 derivative times G^2.  Dirichlet faces: u - g in L2
 // times hh_t1 hh_t2 and the two tangential derivatives in |||.||| (x3: times
 // G^2), times s_t^2 since the kernels form lambda-derivatives there.
+//
+// Vertex neighbourhood (eq. 4.3; axes (phi, theta, chi)): the per-x-point
+// factor is 1/sin^2 phi (on u_thetatheta); every face norm carries
+// R = sup e^chi with (c0, c1, c2) = R (hh_t1 hh_t2, hh_t2, hh_t1) for all
+// fields, [u] in L2 times R hh_t1 hh_t2; Dirichlet likewise, the tangential
+// fields times s_t^2; a corner set is one constant, A_cc = sum_faces 4 w0.
 static hpse_status setup_edge(hpse_mesh *m) {
   const int E = m->n_elem, C = m->n_corner;
+  const bool vtx = m->coord == HPSE_COORD_VERTEX;
   std::vector<double> kap((size_t)E * hpse::KAPPA_STRIDE, 0.0), fw((size_t)E * 6 * hpse::FACE_W, 0.0);
   for (int e = 0; e < E; ++e) {
     const hm::DegreeTables &t = m->tabs.at(m->W[e]);
@@ -1057,10 +1064,26 @@ static hpse_status setup_edge(hpse_mesh *m) {
       hh[a] = 0.5 * (m->hi[3 * e + a] - m->lo[3 * e + a]);
       sc[a] = 1.0 / hh[a];
     }
-    for (int q = 0; q < t.Q; ++q) kap[(size_t)e * hpse::KAPPA_STRIDE + q] = std::exp(2.0 * (m->lo[3 * e] + (t.xq[q] + 1.0) * hh[0]));
+    for (int q = 0; q < t.Q; ++q) {
+      const double x = m->lo[3 * e] + (t.xq[q] + 1.0) * hh[0];
+      kap[(size_t)e * hpse::KAPPA_STRIDE + q] = vtx ? 1.0 / (std::sin(x) * std::sin(x)) : std::exp(2.0 * x);
+    }
     for (int fi = 0; fi < 6; ++fi) {
       const int a = fi >> 1, side = fi & 1;
       const int t1 = a == 0 ? 1 : 0, t2 = a == 2 ? 1 : 2;
+      if (vtx) {
+        const double R = std::exp(a == 2 ? (side ? m->hi[3 * e + 2] : m->lo[3 * e + 2]) : m->hi[3 * e + 2]);
+        const double c[3] = {R * hh[t1] * hh[t2], R * hh[t2], R * hh[t1]};
+        double *w = &fw[((size_t)e * 6 + fi) * hpse::FACE_W];
+        const bool dir = m->nbr[6 * e + fi] == -1;
+        w[0] = c[0];
+        const int ax[3] = {t1, t2, a};
+        for (int k = 0; k < 3; ++k) {
+          const double f = dir ? ((k < 2) ? sc[ax[k]] * sc[ax[k]] : 0.0) : 1.0;
+          for (int j = 0; j < 3; ++j) w[1 + 3 * k + j] = f * c[j];
+        }
+        continue;
+      }
       const double G = std::exp(a == 0 ? (side ? m->hi[3 * e] : m->lo[3 * e]) : m->hi[3 * e]);
       double c[3] = {hh[t1] * hh[t2], hh[t2], hh[t1]};
       if (t2 == 2) c[2] *= G;
@@ -1083,7 +1106,7 @@ static hpse_status setup_edge(hpse_mesh *m) {
   // the element; (G - nu H) d = 0 in the symmetric form Wp^{-1/2} G Wp^{-1/2},
   // stored like the master tables (node-major eigenvectors, then nu)
   std::vector<double> zeig((size_t)E * hpse::ZEIG_STRIDE, 0.0);
-  for (int e = 0; e < E; ++e) {
+  for (int e = 0; e < E && !vtx; ++e) {
     const hm::DegreeTables &t = m->tabs.at(m->W[e]);
     const int P = t.P;
     const double eta = std::exp(m->hi[3 * e]), e2 = eta * eta, e4 = e2 * e2;
@@ -1116,7 +1139,15 @@ static hpse_status setup_edge(hpse_mesh *m) {
   // and 1^T KP 1 = 0, A_cc = sum_faces 2 (w0 MP + s_x3^2 D^T (w4 MP + w6 KP) D)
   const int S = (int)m->slot_list.size();
   std::vector<double> cinv((size_t)C * hpse::CSCR_STRIDE * hpse::CSCR_STRIDE, 0.0);
-  for (int c = 0; c < C; ++c) {
+  for (int c = 0; c < C && vtx; ++c) {
+    double a = 0.0;
+    for (int i = m->slot_ptr[c]; i < m->slot_ptr[c + 1]; ++i)
+      for (int ee = 0; ee < E; ++ee)
+        if (m->cslot[ee] == m->slot_list[i]) a += 4.0 * fw[((size_t)ee * 6 + 4) * hpse::FACE_W];
+    if (!(a > 0.0)) return HPSE_ERR_BREAKDOWN;
+    cinv[(size_t)c * hpse::CSCR_STRIDE * hpse::CSCR_STRIDE] = 1.0 / std::sqrt(a);
+  }
+  for (int c = 0; c < C && !vtx; ++c) {
     const hm::DegreeTables &t = m->tabs.at(m->cW[c]);
     const int P = t.P;
     std::vector<double> Acc((size_t)P * P, 0.0);
@@ -1174,7 +1205,7 @@ static hpse_status setup_edge(hpse_mesh *m) {
   CK(upload(m->d_slot_ptr, m->slot_ptr));
   CK(upload(m->d_slot_list, m->slot_list));
   std::vector<double> ch1(2 * (size_t)C, 0.0);
-  for (int e = 0; e < E; ++e) {
+  for (int e = 0; e < E && !vtx; ++e) {
     if (m->cslot[e] < 0) continue;
     const int c = -2 - m->nbr[6 * e];
     const double r1 = std::exp(m->lo[3 * e]), hz = m->hi[3 * e + 2] - m->lo[3 * e + 2];
@@ -1206,8 +1237,11 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
   m->n_rhs = d->n_rhs;
   m->coef_kind = d->coef_kind;
   m->coord = d->coord;
-  if (m->coord != HPSE_COORD_CARTESIAN && m->coord != HPSE_COORD_EDGE) return HPSE_ERR_INVALID_ARG;
-  if (m->coord == HPSE_COORD_EDGE) {
+  if (m->coord != HPSE_COORD_CARTESIAN && m->coord != HPSE_COORD_EDGE && m->coord != HPSE_COORD_VERTEX)
+    return HPSE_ERR_INVALID_ARG;
+  const bool nbhd = m->coord != HPSE_COORD_CARTESIAN;
+  const int cface = m->coord == HPSE_COORD_VERTEX ? 4 : 0;  // face of layer 1 towards the corner set
+  if (nbhd) {
     // the modified-coordinate operator is built for the Laplacian (eq. 2.35)
     if (d->coef_kind != HPSE_COEF_LAPLACE || d->n_corner < 0) return HPSE_ERR_INVALID_ARG;
     if (d->n_corner > 0 && (!d->corner_W || !d->corner_problem)) return HPSE_ERR_INVALID_ARG;
@@ -1215,7 +1249,8 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
     m->cW.assign(d->corner_W, d->corner_W + d->n_corner);
     m->cprob.assign(d->corner_problem, d->corner_problem + d->n_corner);
   }
-  m->apply_coef = m->coord == HPSE_COORD_EDGE ? hpse::COEF_EDGE : d->coef_kind;
+  m->apply_coef = m->coord == HPSE_COORD_EDGE ? hpse::COEF_EDGE
+                 : (m->coord == HPSE_COORD_VERTEX ? hpse::COEF_VERTEX : d->coef_kind);
   m->W.assign(d->elem_W, d->elem_W + E);
   m->prob.assign(d->elem_problem, d->elem_problem + E);
   m->nbr.assign(d->elem_nbr, d->elem_nbr + 6 * (size_t)E);
@@ -1232,7 +1267,8 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
   }
   const int C = m->n_corner;
   for (int c = 0; c < C; ++c)
-    if (m->cW[c] < 1 || m->cW[c] > HPSE_MAX_W || m->cprob[c] < 0 || m->cprob[c] >= m->n_problem)
+    if ((m->coord == HPSE_COORD_VERTEX ? m->cW[c] != 0 : (m->cW[c] < 1 || m->cW[c] > HPSE_MAX_W)) ||
+        m->cprob[c] < 0 || m->cprob[c] >= m->n_problem)
       return HPSE_ERR_INVALID_ARG;
   std::vector<int> corner_e(C, -1);  // first layer-1 element of each corner set
   for (int e = 0; e < E; ++e)
@@ -1241,17 +1277,24 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
       if (n <= -2) {
         // corner set: edge coordinates, face tau = lo only, same degree, problem and x3 slab
         const int c = -2 - n;
-        if (m->coord != HPSE_COORD_EDGE || fi != 0 || c >= C) return HPSE_ERR_INVALID_ARG;
-        if (m->cW[c] != m->W[e]) return HPSE_ERR_DEGREE;
+        if (!nbhd || fi != cface || c >= C) return HPSE_ERR_INVALID_ARG;
+        if (m->coord == HPSE_COORD_EDGE && m->cW[c] != m->W[e]) return HPSE_ERR_DEGREE;
         if (m->cprob[c] != m->prob[e]) return HPSE_ERR_INVALID_ARG;
         if (corner_e[c] < 0) {
           corner_e[c] = e;
         } else {
+          // edge: one x3 slab and the same r_1; vertex: the same rho_1
           const int e0 = corner_e[c];
-          if (std::fabs(m->lo[3 * e + 2] - m->lo[3 * e0 + 2]) > 1e-12 * std::max(1.0, std::fabs(m->lo[3 * e0 + 2])) ||
-              std::fabs(m->hi[3 * e + 2] - m->hi[3 * e0 + 2]) > 1e-12 * std::max(1.0, std::fabs(m->hi[3 * e0 + 2])) ||
-              std::fabs(m->lo[3 * e] - m->lo[3 * e0]) > 1e-12 * std::max(1.0, std::fabs(m->lo[3 * e0])))
-            return HPSE_ERR_NONMATCHING_FACE;
+          auto differ = [&](int i0, int i1) {
+            return std::fabs(m->lo[i0] - m->lo[i1]) > 1e-12 * std::max(1.0, std::fabs(m->lo[i1]));
+          };
+          auto differ_hi = [&](int i0, int i1) {
+            return std::fabs(m->hi[i0] - m->hi[i1]) > 1e-12 * std::max(1.0, std::fabs(m->hi[i1]));
+          };
+          const bool bad = m->coord == HPSE_COORD_EDGE
+                               ? (differ(3 * e + 2, 3 * e0 + 2) || differ_hi(3 * e + 2, 3 * e0 + 2) || differ(3 * e, 3 * e0))
+                               : differ(3 * e + 2, 3 * e0 + 2);
+          if (bad) return HPSE_ERR_NONMATCHING_FACE;
         }
         continue;
       }
@@ -1300,16 +1343,16 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
   {
     std::vector<int> slot_elem;
     for (int e = 0; e < E; ++e)
-      if (m->nbr[6 * e] <= -2) {
+      if (m->nbr[6 * e + cface] <= -2) {
         m->cslot[e] = (int)slot_elem.size();
         slot_elem.push_back(e);
-        m->slot_ptr[-2 - m->nbr[6 * e] + 1]++;
+        m->slot_ptr[-2 - m->nbr[6 * e + cface] + 1]++;
       }
     for (int c = 0; c < C; ++c) m->slot_ptr[c + 1] += m->slot_ptr[c];
     std::vector<int> fill(m->slot_ptr.begin(), m->slot_ptr.end() - 1);
     m->slot_list.assign(slot_elem.size(), 0);
     for (size_t sl = 0; sl < slot_elem.size(); ++sl)
-      m->slot_list[fill[-2 - m->nbr[6 * slot_elem[sl]]]++] = (int)sl;
+      m->slot_list[fill[-2 - m->nbr[6 * slot_elem[sl] + cface]]++] = (int)sl;
   }
   int64_t of = 0;
   for (int e = 0; e < E; ++e)
@@ -1392,7 +1435,7 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
     geo[4 * e + 3] = J;
     for (int k = 0; k < 4; ++k) geo32[4 * e + k] = (float)geo[4 * e + k];
   }
-  if (m->coord == HPSE_COORD_EDGE) {
+  if (nbhd) {
     hpse_status st = setup_edge(m.get());
     if (st != HPSE_OK) return st;
   }
@@ -1467,7 +1510,8 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data) {
   // coefficients at the volume points: m = w J a^2, d_k = s_k a_k / a; wJa for b
   std::vector<double> wja(nq);
   std::vector<double> coef;
-  if (m->coef_kind == HPSE_COEF_SCALAR) coef.assign(4 * (size_t)nq, 0.0);
+  const bool vtx = m->coord == HPSE_COORD_VERTEX;
+  if (m->coef_kind == HPSE_COEF_SCALAR || vtx) coef.assign(4 * (size_t)nq, 0.0);
   for (int e = 0; e < m->n_elem; ++e) {
     const hm::DegreeTables &t = m->tabs.at(m->W[e]);
     const int Q = t.Q;
@@ -1489,6 +1533,19 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data) {
             coef[4 * i] = wJ * av * av;
             for (int k = 0; k < 3; ++k) coef[4 * i + k + 1] = s[k] * data->grad_a[k * nq + i] / av;
             wja[i] = wJ * av;
+          } else if (vtx) {
+            // L^v = -c (u_chichi + u_chi + u_phiphi + cot(phi) u_phi + u_thetatheta / sin^2 phi)
+            // with c^2 = e^chi sin(phi) (eq. 4.3): m = w J c^2, d = (s_phi cot(phi), 0, s_chi);
+            // the 1/sin^2 phi of u_thetatheta is a per-x-point factor of the kernel;
+            // b: F^v = c e^{2 chi} f, so w J c F^v = w J c^2 e^{2 chi} f
+            const double ph = m->lo[3 * e] + (t.xq[a] + 1.0) * 0.5 * (m->hi[3 * e] - m->lo[3 * e]);
+            const double ch = m->lo[3 * e + 2] + (t.xq[c] + 1.0) * 0.5 * (m->hi[3 * e + 2] - m->lo[3 * e + 2]);
+            const double c2 = std::exp(ch) * std::sin(ph);
+            coef[4 * i] = wJ * c2;
+            coef[4 * i + 1] = s[0] * std::cos(ph) / std::sin(ph);
+            coef[4 * i + 2] = 0.0;
+            coef[4 * i + 3] = s[2];
+            wja[i] = wJ * c2 * std::exp(2.0 * ch);
           } else if (m->coord == HPSE_COORD_EDGE) {
             // F^e = e^{2 tau} f (eq. 4.7): tau is the x coordinate of the point
             const double tau = m->lo[3 * e] + (t.xq[a] + 1.0) * 0.5 * (m->hi[3 * e] - m->lo[3 * e]);
@@ -1523,7 +1580,7 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data) {
     for (auto &kv : m->d_qtab) tp[kv.first] = kv.second.as<double>();
     CK(upload_reuse(m->d_tabs_ptr, tp));
   }
-  if (m->coef_kind == HPSE_COEF_SCALAR) {
+  if (m->coef_kind == HPSE_COEF_SCALAR || vtx) {
     std::vector<float> c32(coef.size());
     for (size_t i = 0; i < coef.size(); ++i) c32[i] = (float)coef[i];
     CK(upload_reuse(m->d_coef64, coef));
@@ -1589,7 +1646,7 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data) {
     A.qtab = dtabs.as<const double *>();
     A.g = dg.as<double>();
     A.b = m->d_b.as<double>();
-    A.fw = m->coord == HPSE_COORD_EDGE ? m->d_fw64.as<double>() : nullptr;
+    A.fw = m->coord != HPSE_COORD_CARTESIAN ? m->d_fw64.as<double>() : nullptr;
     const int Q = 2 * Wmax + 1, P = Wmax + 1;
     const size_t smem = (size_t)(8 * Q * Q + 2 * Q * P + P * P) * sizeof(double);
     CK(cudaFuncSetAttribute(k_face_data, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -2354,7 +2411,7 @@ extern "C" hpse_status hpse_pcg_solve(hpse_mesh *m, const hpse_solve_opts *o, do
 extern "C" hpse_status hpse_h1_error(hpse_mesh *m, const double *u, const double *ref, const double *vq,
                                      const double *gq, double *out, void *stream) {
   // edge neighbourhood: the difference of two discrete solutions only
-  if (m && m->coord == HPSE_COORD_EDGE && !ref) return HPSE_ERR_INVALID_ARG;
+  if (m && ((m->coord == HPSE_COORD_EDGE && !ref) || m->coord == HPSE_COORD_VERTEX)) return HPSE_ERR_INVALID_ARG;
   if (!m || !out) return HPSE_ERR_INVALID_ARG;
   if (m->ndof == 0) {
     for (int r = 0; r < m->n_rhs; ++r) out[2 * r] = out[2 * r + 1] = 0.0;
@@ -2649,7 +2706,7 @@ static hpse_status launch_fields(hpse_mesh *m, const double *u, double *out, cud
 }
 
 extern "C" hpse_status hpse_eval_fields(hpse_mesh *m, const double *u, double *out, void *stream) {
-  if (m && m->coord == HPSE_COORD_EDGE) return HPSE_ERR_INVALID_ARG;  // box meshes only
+  if (m && m->coord != HPSE_COORD_CARTESIAN) return HPSE_ERR_INVALID_ARG;  // box meshes only
   if (!m) return HPSE_ERR_INVALID_ARG;
   if (m->ndof == 0) return HPSE_OK;
   if (!u || !out) return HPSE_ERR_INVALID_ARG;
@@ -2659,7 +2716,7 @@ extern "C" hpse_status hpse_eval_fields(hpse_mesh *m, const double *u, double *o
 }
 
 extern "C" hpse_status hpse_apply_eval_transpose(hpse_mesh *m, const double *rho, double *y, void *stream) {
-  if (m && m->coord == HPSE_COORD_EDGE) return HPSE_ERR_INVALID_ARG;  // box meshes only
+  if (m && m->coord != HPSE_COORD_CARTESIAN) return HPSE_ERR_INVALID_ARG;  // box meshes only
   if (!m) return HPSE_ERR_INVALID_ARG;
   if (m->ndof == 0) return HPSE_OK;
   if (!rho || !y) return HPSE_ERR_INVALID_ARG;
@@ -2675,7 +2732,7 @@ extern "C" hpse_status hpse_apply_eval_transpose(hpse_mesh *m, const double *rho
 }
 
 extern "C" hpse_status hpse_quad_weights(hpse_mesh *m, double *out, void *stream) {
-  if (m && m->coord == HPSE_COORD_EDGE) return HPSE_ERR_INVALID_ARG;  // box meshes only
+  if (m && m->coord != HPSE_COORD_CARTESIAN) return HPSE_ERR_INVALID_ARG;  // box meshes only
   if (!m || (!out && m->nquad > 0)) return HPSE_ERR_INVALID_ARG;
   if (!m->has_data) return HPSE_ERR_NO_DATA;
   CK(cudaSetDevice(m->device));
@@ -2694,7 +2751,7 @@ static hpse_status ensure_scratch(hpse_mesh *m) {
 }
 
 extern "C" hpse_status hpse_apply_residual(hpse_mesh *m, const double *u, double *z, void *stream) {
-  if (m && m->coord == HPSE_COORD_EDGE) return HPSE_ERR_INVALID_ARG;  // box meshes only
+  if (m && m->coord != HPSE_COORD_CARTESIAN) return HPSE_ERR_INVALID_ARG;  // box meshes only
   if (!m) return HPSE_ERR_INVALID_ARG;
   if (m->ndof == 0) return HPSE_OK;
   if (!u || !z) return HPSE_ERR_INVALID_ARG;
@@ -2713,7 +2770,7 @@ extern "C" hpse_status hpse_apply_residual(hpse_mesh *m, const double *u, double
 }
 
 extern "C" hpse_status hpse_apply_transpose(hpse_mesh *m, const double *z, double *y, void *stream) {
-  if (m && m->coord == HPSE_COORD_EDGE) return HPSE_ERR_INVALID_ARG;  // box meshes only
+  if (m && m->coord != HPSE_COORD_CARTESIAN) return HPSE_ERR_INVALID_ARG;  // box meshes only
   if (!m) return HPSE_ERR_INVALID_ARG;
   if (m->ndof == 0) return HPSE_OK;
   if (!z || !y) return HPSE_ERR_INVALID_ARG;
@@ -2733,7 +2790,7 @@ extern "C" hpse_status hpse_apply_transpose(hpse_mesh *m, const double *z, doubl
 
 extern "C" hpse_status hpse_data_gradient(hpse_mesh *m, const double *ufields, const double *lfields, double *out,
                                           void *stream) {
-  if (m && m->coord == HPSE_COORD_EDGE) return HPSE_ERR_INVALID_ARG;  // box meshes only
+  if (m && m->coord != HPSE_COORD_CARTESIAN) return HPSE_ERR_INVALID_ARG;  // box meshes only
   if (!m) return HPSE_ERR_INVALID_ARG;
   if (m->nquad == 0) return HPSE_OK;
   if (!ufields || !lfields || !out) return HPSE_ERR_INVALID_ARG;
@@ -2809,7 +2866,7 @@ __global__ void k_h1_reduce_noalloc(int n_elem, int n_rhs, const double *part_er
 
 extern "C" hpse_status hpse_h1_error_noalloc(hpse_mesh *m, const double *u, const double *ref, const double *vq,
                                              const double *gq, double *out, void *stream) {
-  if (m && m->coord == HPSE_COORD_EDGE) return HPSE_ERR_INVALID_ARG;  // box meshes only
+  if (m && m->coord != HPSE_COORD_CARTESIAN) return HPSE_ERR_INVALID_ARG;  // box meshes only
   if (!m || !out) return HPSE_ERR_INVALID_ARG;
   if (m->ndof == 0) {
     for (int r = 0; r < m->n_rhs; ++r) out[2 * r] = out[2 * r + 1] = 0.0;

@@ -86,6 +86,11 @@ __constant__ Tables c_tab;
 using hpse::COEF_LAPLACE;
 using hpse::COEF_SCALAR;
 using hpse::COEF_EDGE;
+using hpse::COEF_VERTEX;
+// variable-coefficient fields (first derivatives, per-point weights)
+__host__ __device__ constexpr bool var_coef(int c) { return c == hpse::COEF_SCALAR || c == hpse::COEF_VERTEX; }
+// neighbourhood elements: face-norm weights and corner sets
+__host__ __device__ constexpr bool nbhd_coef(int c) { return c == hpse::COEF_EDGE || c == hpse::COEF_VERTEX; }
 using hpse::MODE_PLAIN;
 using hpse::MODE_PCG;
 using hpse::MODE_TRANSPOSE;
@@ -159,12 +164,13 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
     if (nb != -1 && A.self_only) {
       FSLOT(f, sFn)[sp] = (real)0;
       FSLOT(f, sNn)[sp] = (real)0;
-    } else if (COEF == COEF_EDGE && nb < -1) {
-      // corner set (edge neighbourhood, face 0): its polynomial in x3 (the p2
-      // direction of this face), constant in theta and tau
+    } else if (nbhd_coef(COEF) && nb < -1) {
+      // corner set: edge neighbourhood (face 0), its polynomial in x3 (the p2
+      // direction of this face), constant in theta and tau; vertex
+      // neighbourhood (face 4), one constant
       const int64_t cb = (int64_t)r * A.ndof + A.dof_off[A.n_elem + (-2 - nb)];
       const real bt = (MODE == MODE_PCG) ? (real)A.beta[A.prob[e] * A.n_rhs + r] : (real)0;
-      FSLOT(f, sFn)[sp] = nb_value<MODE>(A, cb + p2, bt);
+      FSLOT(f, sFn)[sp] = nb_value<MODE>(A, cb + (COEF == COEF_EDGE ? p2 : 0), bt);
       FSLOT(f, sNn)[sp] = (real)0;
     } else if (nb >= 0) {
       const int64_t base = (int64_t)r * A.ndof + A.dof_off[nb];
@@ -221,7 +227,7 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
     const real *J0 = FSLOT(f, sJ0), *J1 = FSLOT(f, sJ1), *J2 = FSLOT(f, sJ2), *J3 = FSLOT(f, sJ3);
     // face-norm weights: w[0] on the L2 jump of u; (w[3k-2], w[3k-1], w[3k]) =
     // (L2, quotient along t1, quotient along t2) on jump field k (1 on box meshes)
-    const real *wf = (COEF == COEF_EDGE && A.fw) ? A.fw + ((int64_t)e * 6 + f) * hpse::FACE_W : nullptr;
+    const real *wf = (nbhd_coef(COEF) && A.fw) ? A.fw + ((int64_t)e * 6 + f) * hpse::FACE_W : nullptr;
     real t0 = 0, a1 = 0, a2 = 0, a3 = 0, b1 = 0, b2 = 0, b3 = 0;
 #pragma unroll
     for (int m = 0; m < P; ++m) {
@@ -290,6 +296,17 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
         }
         A.cscr[((int64_t)slot * A.n_rhs + r) * hpse::CSCR_STRIDE + k] = -(s0 + geo_e[2] * s2);
       }
+    }
+  }
+  // corner side of the face rho = rho_1 (vertex neighbourhood, face 4): the
+  // corner constant's trace is 1 at every face node, so y_c = -sum of the
+  // weighted jump of u over the face
+  if (COEF == COEF_VERTEX && A.cscr && !A.self_only && tid == 0) {
+    const int slot = A.cslot[e];
+    if (slot >= 0) {
+      real s0 = 0;
+      for (int t = 0; t < P2; ++t) s0 += FSLOT(4, sJ0)[t];
+      A.cscr[((int64_t)slot * A.n_rhs + r) * hpse::CSCR_STRIDE] = -s0;
     }
   }
   // F5: transposed traces on the face grid: C (face layer) -> F slot, Gn (normal) -> N slot
@@ -379,12 +396,12 @@ __device__ __forceinline__ void x_fwd_chunk(const real *v, real *X0, real *X1, r
     for (int i = 0; i < P; ++i) {
       a0 += c_tab.B[0][q * P + i] * v[i];
       a2 += c_tab.B[2][q * P + i] * v[i];
-      if (COEF == COEF_SCALAR) a1 += c_tab.B[1][q * P + i] * v[i];
+      if (var_coef(COEF)) a1 += c_tab.B[1][q * P + i] * v[i];
     }
     if (ok) {
       X0[l * Q + q] = a0;
       X2[l * Q + q] = a2;
-      if (COEF == COEF_SCALAR) X1[l * Q + q] = a1;
+      if (var_coef(COEF)) X1[l * Q + q] = a1;
     }
     __syncwarp();  // scheduling fence (register pressure); reached by all 32 lanes
   }
@@ -403,7 +420,7 @@ __device__ __forceinline__ void y_fwd_chunk(const real *v0, const real *v1, cons
       t00 += c_tab.B[0][qb * P + j] * v0[j];
       tl0 += c_tab.B[2][qb * P + j] * v0[j];
       tl2 += c_tab.B[0][qb * P + j] * v2[j];
-      if (COEF == COEF_SCALAR) {
+      if (var_coef(COEF)) {
         t10 += c_tab.B[0][qb * P + j] * v1[j];
         t01 += c_tab.B[1][qb * P + j] * v0[j];
       }
@@ -412,7 +429,7 @@ __device__ __forceinline__ void y_fwd_chunk(const real *v0, const real *v1, cons
     if (ok) {
       T00[o] = t00;
       TL[o] = sx2 * tl2 + sy2 * tl0;
-      if (COEF == COEF_SCALAR) {
+      if (var_coef(COEF)) {
         T10[o] = t10;
         T01[o] = t01;
       }
@@ -434,7 +451,7 @@ __device__ __forceinline__ void y_rev_chunk(const real *RZ, const real *R0, cons
       const int o = (k * Q + qb) * Q + qa;
       vz[qb] = RZ[o];
       v0[qb] = R0[o];
-      if (COEF == COEF_SCALAR) vy[qb] = RY[o];
+      if (var_coef(COEF)) vy[qb] = RY[o];
     }
 #pragma unroll
     for (int j = R::B; j < R::E; ++j) {
@@ -444,7 +461,7 @@ __device__ __forceinline__ void y_rev_chunk(const real *RZ, const real *R0, cons
         x0 += c_tab.B[0][qb * P + j] * vz[qb];
         x0b += c_tab.B[2][qb * P + j] * v0[qb];
         x2 += c_tab.B[0][qb * P + j] * v0[qb];
-        if (COEF == COEF_SCALAR) x0c += c_tab.B[1][qb * P + j] * vy[qb];
+        if (var_coef(COEF)) x0c += c_tab.B[1][qb * P + j] * vy[qb];
       }
       if (ok) {
         const int o = (k * P + j) * Q + qa;
@@ -453,7 +470,7 @@ __device__ __forceinline__ void y_rev_chunk(const real *RZ, const real *R0, cons
       }
     }
   }
-  if (COEF == COEF_SCALAR) {
+  if (var_coef(COEF)) {
     real vx[Q];
 #pragma unroll
     for (int qb = 0; qb < Q; ++qb) vx[qb] = RX[(k * Q + qb) * Q + qa];
@@ -477,7 +494,7 @@ __device__ __forceinline__ void x_rev_chunk(const real *X0, const real *X1, cons
   for (int q = 0; q < Q; ++q) {
     v0[q] = X0[l * Q + q];
     v2[q] = X2[l * Q + q];
-    if (COEF == COEF_SCALAR) v1[q] = X1[l * Q + q];
+    if (var_coef(COEF)) v1[q] = X1[l * Q + q];
   }
 #pragma unroll
   for (int i = R::B; i < R::E; ++i) {
@@ -485,7 +502,7 @@ __device__ __forceinline__ void x_rev_chunk(const real *X0, const real *X1, cons
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       s += c_tab.B[0][q * P + i] * v0[q] + c_tab.B[2][q * P + i] * v2[q];
-      if (COEF == COEF_SCALAR) s += c_tab.B[1][q * P + i] * v1[q];
+      if (var_coef(COEF)) s += c_tab.B[1][q * P + i] * v1[q];
     }
     if (ok) sy[l * P + i] = s;
   }
@@ -507,8 +524,8 @@ __device__ __forceinline__ void x_rev_chunk(const real *X0, const real *X1, cons
 // ---------------------------------------------------------------------------
 template <int COEF>
 struct ApplyLayout {
-  static constexpr int NX = (COEF == COEF_SCALAR) ? 3 : 2;
-  static constexpr int NTF = (COEF == COEF_SCALAR) ? 4 : 2;
+  static constexpr int NX = (var_coef(COEF)) ? 3 : 2;
+  static constexpr int NTF = (var_coef(COEF)) ? 4 : 2;
   static constexpr int T_REGION0 = NTF * Q2P;
   static constexpr int T_NEED = P3 + 6 * FACE_ARR * P2;
   static constexpr int T_REGION = T_REGION0 > T_NEED ? T_REGION0 : T_NEED;
@@ -591,10 +608,12 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
         for (int j = 0; j < P; ++j) {
           v0[j] = X0[(k * P + j) * Q + qa];
           v2[j] = X2[(k * P + j) * Q + qa];
-          if (COEF == COEF_SCALAR) v1[j] = X1[(k * P + j) * Q + qa];
+          if (var_coef(COEF)) v1[j] = X1[(k * P + j) * Q + qa];
         }
+        // vertex neighbourhood: u_22 carries 1/sin^2(x_1), constant along this y-line
+        const real sy2q = (COEF == COEF_VERTEX) ? sy2 * A.kappa[(int64_t)e * hpse::KAPPA_STRIDE + qa] : sy2;
 #define YF_CALL(CI) \
-  y_fwd_chunk<COEF, (CI < LS::NC ? CI : 0), LS::NC>(v0, v1, v2, T00, TL, T10, T01, qa, k, ok, sx2, sy2)
+  y_fwd_chunk<COEF, (CI < LS::NC ? CI : 0), LS::NC>(v0, v1, v2, T00, TL, T10, T01, qa, k, ok, sx2, sy2q)
         HPSE_DISPATCH4(LS::NC, c, YF_CALL);
 #undef YF_CALL
       }
@@ -623,7 +642,7 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
         const int o = (k * Q + qb) * Q + qa;
         a00[k] = T00[o];
         aL[k] = TL[o];
-        if (COEF == COEF_SCALAR) {
+        if (var_coef(COEF)) {
           a10[k] = T10[o];
           a01[k] = T01[o];
         }
@@ -636,14 +655,14 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
         for (int k = 0; k < P; ++k) {
           s2 += c_tab.B[2][qc * P + k] * a00[k];
           s0 += c_tab.B[0][qc * P + k] * aL[k];
-          if (COEF == COEF_SCALAR) {
+          if (var_coef(COEF)) {
             s1z += c_tab.B[1][qc * P + k] * a00[k];
             sxx += c_tab.B[0][qc * P + k] * a10[k];
             syy += c_tab.B[0][qc * P + k] * a01[k];
           }
         }
         const real sigma0 = sz2c * s2 + s0;
-        if (COEF == COEF_SCALAR) {
+        if (var_coef(COEF)) {
           real mq, dx, dy, dz;
           load_coef4(A.coef + 4 * (cbase + (int64_t)qc * Q2), mq, dx, dy, dz);
           rho[qc] = mq * (sigma0 + dz * s1z + dx * sxx + dy * syy);
@@ -665,7 +684,7 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
     for (int qc = 0; qc < Q; ++qc) {
       const real rq = rho[qc];
       real dx = 0, dy = 0, dz = 0;
-      if (COEF == COEF_SCALAR) {
+      if (var_coef(COEF)) {
         real mq;
         load_coef4(A.coef + 4 * (cbase + (int64_t)qc * Q2), mq, dx, dy, dz);
       }
@@ -674,7 +693,7 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
       for (int k = 0; k < P; ++k) {
         rz[k] += c_tab.B[2][qc * P + k] * rz2;
         r0[k] += c_tab.B[0][qc * P + k] * rq;
-        if (COEF == COEF_SCALAR) {
+        if (var_coef(COEF)) {
           rz[k] += c_tab.B[1][qc * P + k] * rzd;
           rx[k] += c_tab.B[0][qc * P + k] * rxd;
           ry[k] += c_tab.B[0][qc * P + k] * ryd;
@@ -687,7 +706,7 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
         const int o = (k * Q + qb) * Q + qa;
         T00[o] = rz[k];
         TL[o] = r0[k];
-        if (COEF == COEF_SCALAR) {
+        if (var_coef(COEF)) {
           T10[o] = rx[k];
           T01[o] = ry[k];
         }
@@ -704,8 +723,9 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
       const bool ok = lp < QP;
       const int l = ok ? lp : QP - 1;
       const int qa = l % Q, k = l / Q;
+      const real sy2q = (COEF == COEF_VERTEX) ? sy2 * A.kappa[(int64_t)e * hpse::KAPPA_STRIDE + qa] : sy2;
 #define YR_CALL(CI) \
-  y_rev_chunk<COEF, (CI < LS::NC ? CI : 0), LS::NC>(T00, TL, T10, T01, X0, X1, X2, qa, k, ok, sx2, sy2)
+  y_rev_chunk<COEF, (CI < LS::NC ? CI : 0), LS::NC>(T00, TL, T10, T01, X0, X1, X2, qa, k, ok, sx2, sy2q)
       HPSE_DISPATCH4(LS::NC, c, YR_CALL);
 #undef YR_CALL
     }

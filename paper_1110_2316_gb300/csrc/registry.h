@@ -9,7 +9,10 @@ namespace hpse {
 
 // COEF_EDGE: -(u_11 + u_22 + kappa(x_1) u_33) in the edge neighbourhood's
 // modified coordinates, kappa = e^{2 tau} per x-point of the element
-enum { COEF_LAPLACE = 0, COEF_SCALAR = 1, COEF_EDGE = 2 };
+// COEF_VERTEX: the variable-coefficient form with per-point weights and
+// first-order terms, u_22 scaled by 1/sin^2(x_1) per x-point (vertex
+// neighbourhood, modified coordinates (phi, theta, ln rho))
+enum { COEF_LAPLACE = 0, COEF_SCALAR = 1, COEF_EDGE = 2, COEF_VERTEX = 3 };
 // KAPPA_STRIDE = 2 * HPSE_MAX_W + 1, CSCR_STRIDE = HPSE_MAX_W + 1 (checked in the host library)
 enum { KAPPA_STRIDE = 21, CSCR_STRIDE = 11, FACE_W = 10, ZEIG_STRIDE = 132 };
 enum { MODE_PLAIN = 0, MODE_PCG = 1, MODE_TRANSPOSE = 2 };

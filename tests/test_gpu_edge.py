@@ -84,7 +84,8 @@ def test_edge_block_preconditioner_matches_oracle(api):
         B = A[sl, sl]
         zo = np.linalg.solve(B, r[sl])
         n = B.shape[0]
-        assert np.linalg.norm(z[sl] - zo) <= n * EPS64 * np.linalg.cond(B) * np.linalg.norm(zo)
+        # n eps kappa for the factorisation, plus the fixed roundings of z = X^T (X r)
+        assert np.linalg.norm(z[sl] - zo) <= (n + 4) * EPS64 * np.linalg.cond(B) * np.linalg.norm(zo)
     m.close()
 
 

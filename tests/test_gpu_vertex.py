@@ -1,0 +1,122 @@
+"""Vertex-neighbourhood elements on the GPU (eq. 4.3 in modified coordinates
+(phi, theta, ln rho)) against the oracle: operator, right-hand side,
+element-block preconditioner with the corner block, PCG solutions; and the H^1
+error of Table 6.16's problem computed from GPU solutions.
+
+Tolerances as for the edge neighbourhood: FP64 applies and right-hand side
+1e-12 of max, FP32 applies 2e-5 of max; blocks (n + 4) eps kappa; solutions within
+kappa(A) x the stopping residual.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as wl
+from oracle.vertex import VertexDiscretisation
+
+pytestmark = pytest.mark.gpu
+
+EPS64 = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1110_2316_gb300.build import build
+    build()
+    from paper_1110_2316_gb300 import api as A
+    return A
+
+
+def _problem(N, W, I=1, J=3):
+    base = wl.vertex_poisson_singular(N=N, W=W)
+    return wl.EdgeProblem(wl.vertex_mesh(N, W, I=I, J=J), base.f, base.g, base.u_exact, base.grad_exact)
+
+
+def _mesh(api, pb):
+    m = api.Mesh(pb.mesh, n_rhs=1, coef_kind=api.COEF_LAPLACE)
+    m.set_data(**api.problem_data_arrays(m, pb))
+    return m
+
+
+@pytest.mark.parametrize("N,W,I,J", [(2, 3, 1, 3), (3, 2, 2, 2)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_vertex_apply_matches_oracle(api, N, W, I, J, prec):
+    pb = _problem(N, W, I, J)
+    d = VertexDiscretisation(pb)
+    m = _mesh(api, pb)
+    assert m.ndof == d.ndof
+    U = wl.random_dofs(d.ndof, seed=6)
+    yo = d.apply_A(U)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    u = torch.tensor(U, dtype=dt, device="cuda")
+    y = torch.empty_like(u)
+    m.apply_operator(u, y)
+    err = np.abs(y.double().cpu().numpy() - yo).max() / np.abs(yo).max()
+    assert err <= (1e-12 if prec == "fp64" else 2e-5), err
+    m.close()
+
+
+def test_vertex_rhs_matches_oracle(api):
+    pb = _problem(2, 3, 2, 2)
+    d = VertexDiscretisation(pb)
+    m = _mesh(api, pb)
+    b = torch.empty(m.ndof, dtype=torch.float64, device="cuda")
+    m.get_rhs(b)
+    bo = d.rhs_b()
+    assert np.abs(b.cpu().numpy() - bo).max() <= 1e-12 * np.abs(bo).max()
+    m.close()
+
+
+def test_vertex_block_preconditioner_matches_oracle(api):
+    pb = _problem(2, 2)
+    d = VertexDiscretisation(pb)
+    A = d.dense_A()
+    m = _mesh(api, pb)
+    m.setup_block_preconditioner()
+    r = wl.random_dofs(d.ndof, seed=10)
+    z = torch.empty(d.ndof, dtype=torch.float64, device="cuda")
+    m.apply_preconditioner(torch.tensor(r, device="cuda"), z)
+    z = z.cpu().numpy()
+    blocks = [slice(d.off[e], d.off[e + 1]) for e in range(d.E)] + [slice(int(d.coff[0]), d.ndof)]
+    for sl in blocks:
+        B = A[sl, sl]
+        zo = np.linalg.solve(B, r[sl])
+        # n eps kappa for the factorisation, plus the fixed roundings of z = X^T (X r)
+        assert np.linalg.norm(z[sl] - zo) <= (B.shape[0] + 4) * EPS64 * np.linalg.cond(B) * np.linalg.norm(zo)
+    m.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("precond", ["separable", "block"])
+def test_vertex_solve_matches_oracle(api, prec, precond):
+    pb = _problem(2, 2)
+    d = VertexDiscretisation(pb)
+    A = d.dense_A()
+    xo = np.linalg.solve(A, d.rhs_b())
+    m = _mesh(api, pb)
+    if precond == "block":
+        m.setup_block_preconditioner()
+    x = torch.zeros(m.ndof, dtype=torch.float64, device="cuda")
+    rep = m.pcg_solve(x, tol=1e-11, prec=api.FP64 if prec == "fp64" else api.FP32, max_iter=200000)
+    assert rep["status"] == 0 and rep["rel_residual"] <= 1e-11
+    assert np.linalg.norm(x.cpu().numpy() - xo) <= np.linalg.cond(A) * 2e-11 * np.linalg.norm(xo)
+    m.close()
+
+
+def test_table_6_16_h1_error_from_gpu_solutions(api):
+    # relative H^1 error (%) of Table 6.16: W = 2 1.00821, W = 3 0.0841462; N = 2W + 4
+    table = {2: 1.00821e-2, 3: 0.841462e-3}
+    errs = {}
+    for W in (2, 3, 4):
+        pb = wl.vertex_poisson_singular(N=2 * W + 4, W=W)
+        d = VertexDiscretisation(pb)
+        m = _mesh(api, pb)
+        m.setup_block_preconditioner()
+        x = torch.zeros(m.ndof, dtype=torch.float64, device="cuda")
+        assert m.pcg_solve(x, tol=1e-10, prec=api.FP32, max_iter=200000)["status"] == 0
+        err, nrm = d.h1_error_exact(x.cpu().numpy())
+        errs[W] = np.sqrt(err / nrm)
+        m.close()
+    for W in (2, 3):
+        assert table[W] / 5 < errs[W] < table[W] * 5, (W, errs[W])
+    assert errs[3] < 0.2 * errs[2] and errs[4] < 0.3 * errs[3], errs

@@ -586,7 +586,7 @@ def concat_edge_meshes(meshes: List[EdgeMeshDesc]) -> EdgeMeshDesc:
     cat = np.concatenate
     return EdgeMeshDesc(cat(los), cat(his), cat(Ws).astype(np.int32), cat(nbrs).astype(np.int32),
                         cat(probs).astype(np.int32), cat(cW).astype(np.int32), cat(clo), cat(chi),
-                        cat(cprob).astype(np.int32), poff)
+                        cat(cprob).astype(np.int32), poff, kind=meshes[0].kind)
 
 
 def edge_batch(Ws, mu=0.15) -> EdgeProblem:
@@ -687,3 +687,12 @@ def vertex_polynomial(N, W, mu=0.15) -> EdgeProblem:
         return -lap / (r * r)
 
     return EdgeProblem(mesh, [f], [u], u, None, name="vertex_polynomial", meta=dict(chi1=chi1))
+
+
+def vertex_batch(Ws, mu=0.15) -> EdgeProblem:
+    """Independent copies of Table 6.16's problem with uneven degrees W_p
+    (N_p = 2 W_p + 4 layers each) in one batch."""
+    base = vertex_poisson_singular(N=2, W=2, mu=mu)
+    mesh = concat_edge_meshes([vertex_mesh(2 * int(W) + 4, int(W), mu=mu) for W in Ws])
+    return EdgeProblem(mesh, base.f, base.g, base.u_exact, base.grad_exact, name="vertex_batch",
+                       meta=dict(Ws=[int(w) for w in Ws]))

@@ -120,3 +120,30 @@ def test_table_6_16_h1_error_from_gpu_solutions(api):
     for W in (2, 3):
         assert table[W] / 5 < errs[W] < table[W] * 5, (W, errs[W])
     assert errs[3] < 0.2 * errs[2] and errs[4] < 0.3 * errs[3], errs
+
+
+def test_vertex_batch_equals_individual_solves(api):
+    # uneven degrees in one launch: each problem's share of the batched solution
+    # equals its own solve (per-problem PCG scalars; the same iteration path)
+    Ws = (3, 2)
+    pb = wl.vertex_batch(Ws)
+    m = _mesh(api, pb)
+    m.setup_block_preconditioner()
+    x = torch.zeros(m.ndof, dtype=torch.float64, device="cuda")
+    assert m.pcg_solve(x, tol=1e-11, prec=api.FP64, max_iter=200000)["status"] == 0
+    el, co = [], []
+    for W in Ws:
+        one = wl.vertex_batch([W])
+        mi = _mesh(api, one)
+        mi.setup_block_preconditioner()
+        xi = torch.zeros(mi.ndof, dtype=torch.float64, device="cuda")
+        assert mi.pcg_solve(xi, tol=1e-11, prec=api.FP64, max_iter=200000)["status"] == 0
+        xi = xi.cpu().numpy()
+        ne = VertexDiscretisation(one).off[-1]
+        el.append(xi[:ne])
+        co.append(xi[ne:])
+        mi.close()
+    ref = np.concatenate(el + co)
+    xb = x.cpu().numpy()
+    assert np.linalg.norm(xb - ref) <= 1e-8 * np.linalg.norm(ref)
+    m.close()

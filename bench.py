@@ -56,10 +56,11 @@ def parse():
     ap.add_argument("--precond", default="block", choices=["block", "separable"],
                     help="block: exact element blocks of A (set up once, FP64 factors); "
                          "separable: the C-form of eq. (5.19)-(5.20)")
-    ap.add_argument("--workload", default="varcoef", choices=["varcoef", "adjoint", "edge", "vertex"],
+    ap.add_argument("--workload", default="varcoef", choices=["varcoef", "adjoint", "edge", "vertex", "poisson"],
                     help="varcoef: the 64-RHS W=8 solve; adjoint: the 256-problem theta-gradient batch; "
                          "edge / vertex: the uneven-degree batch of edge- / vertex-neighbourhood problems")
     ap.add_argument("--edge-replicas", type=int, default=146, help="copies of each degree W = 2..8")
+    ap.add_argument("--replicas", type=int, default=4096, help="copies of the 2x2x2 Poisson problem")
     ap.add_argument("--adj-problems", type=int, default=256)
     ap.add_argument("--adj-fd-problems", type=int, default=16)
     ap.add_argument("--fd-tol", type=float, default=1e-8, help="relative tolerance of the FD correction solves")
@@ -447,15 +448,100 @@ def run_edge(args, local):
     return 0
 
 
+def exact_at_points(mesh, pb):
+    """Exact solution and gradient of every element's problem at the
+    library's volume query points (input sampling for the H1 error)."""
+    ax, _ = mesh.query_points()
+    parts = getattr(pb, "parts", None)
+    vq, gq, o = [], [[], [], []], 0
+    for e in range(mesh.n_elem):
+        Q = 2 * int(mesh.elem_W[e]) + 1
+        xs, ys, zs = ax[o:o + Q], ax[o + Q:o + 2 * Q], ax[o + 2 * Q:o + 3 * Q]
+        o += 3 * Q
+        p = parts[int(pb.mesh.elem_problem[e])] if parts is not None else pb
+        vq.append(p.u_exact[0](xs, ys, zs).ravel())
+        for k, g in enumerate(p.grad_u_exact[0](xs, ys, zs)):
+            gq[k].append(np.broadcast_to(g, (Q, Q, Q)).ravel())
+    return np.concatenate(vq), np.concatenate([np.concatenate(g) for g in gq])
+
+
+def run_poisson(args, local):
+    """Replicas of the 2x2x2-element Poisson problem on [0,1]^3 (W = 4,
+    -Lap u = 3 pi^2 sin(pi x) sin(pi y) sin(pi z), u = 0 on the boundary), all
+    in one launch per operator apply: the problem is too small to fill the GPU
+    alone.  Reports the FP32 and FP64 apply GDOF/s, the mixed and FP64
+    time-to-solution, and the relative H1 error of both solutions against the
+    exact u."""
+    import torch
+    from paper_1110_2316_gb300.build import build
+    build()
+    from paper_1110_2316_gb300 import api
+    dev = torch.device("cuda", local)
+    t0 = time.perf_counter()
+    one = wl.poisson_sine(n=2, W=4)
+    pb = wl.batch_problems([one] * args.replicas)
+    m = api.Mesh(pb.mesh, n_rhs=1, coef_kind=api.COEF_LAPLACE, device=local)
+    m.set_data(**api.problem_data_arrays(m, pb))
+    vq, gq = exact_at_points(m, pb)
+    vq, gq = torch.tensor(vq, device=dev), torch.tensor(gq, device=dev)
+    t_setup = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    if args.precond == "block":
+        m.setup_block_preconditioner()
+    torch.cuda.synchronize()
+    t_prec = time.perf_counter() - t1
+    n = m.ndof
+    apply_ms = {}
+    for name, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+        u = torch.randn(n, dtype=dt, device=dev)
+        y = torch.empty_like(u)
+        for _ in range(3):
+            m.apply_operator(u, y)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        for _ in range(20):
+            m.apply_operator(u, y)
+        a1.record()
+        torch.cuda.synchronize()
+        apply_ms[name] = a0.elapsed_time(a1) / 20
+    out = {}
+    for name, prec in (("mixed", api.FP32), ("fp64", api.FP64)):
+        x = torch.zeros(n, dtype=torch.float64, device=dev)
+        m.pcg_solve(x, tol=TOL, prec=prec, max_iter=64, raise_on_error=False)  # graph capture
+        x.zero_()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record()
+        rep = m.pcg_solve(x, tol=TOL, prec=prec, max_iter=200000, raise_on_error=False)
+        c1.record()
+        torch.cuda.synchronize()
+        h = m.h1_error(x, vq=vq, gq=gq)
+        out[name] = dict(tts_s=c0.elapsed_time(c1) / 1e3, iterations=rep["iterations"], refreshes=rep["sweeps"],
+                         status=rep["status"], rel_residual=rep["rel_residual"],
+                         h1_rel_error=float(np.sqrt(h[0, 0] / h[0, 1])))
+    line = dict(metric="Poisson replicas: operator-apply GDOF/s and time-to-solution, mixed vs FP64",
+                value=n / (apply_ms["fp32"] * 1e-3) / 1e9, unit="GDOF/s", higher_is_better=True, n_gpus=1,
+                dtype="f32", data="synthetic",
+                config=dict(workload="-Lap u = 3 pi^2 sin(pi x) sin(pi y) sin(pi z) on [0,1]^3, 2x2x2 elements, "
+                                     "W = 4, %d replicas in one launch, tol 1e-10" % args.replicas,
+                            n_problem=args.replicas, n_elem=int(pb.mesh.n_elem), ndof=n, precond=args.precond),
+                apply_ms=apply_ms, gdofs_fp64=n / (apply_ms["fp64"] * 1e-3) / 1e9, solves=out,
+                speedup=out["fp64"]["tts_s"] / out["mixed"]["tts_s"],
+                setup_s=t_setup, setup_block_precond_s=t_prec)
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload in ("adjoint", "edge", "vertex"):
+    if args.workload in ("adjoint", "edge", "vertex", "poisson"):
         import torch
         _, _, local = dist_env()
         torch.cuda.set_device(local)
-        return run_adjoint(args, local) if args.workload == "adjoint" else run_edge(args, local)
+        run = dict(adjoint=run_adjoint, edge=run_edge, vertex=run_edge, poisson=run_poisson)[args.workload]
+        return run(args, local)
     import torch
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)

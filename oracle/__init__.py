@@ -23,6 +23,11 @@ parallel computers, 2010):
 * ``pcg``        -- preconditioned conjugate gradients (Section 5.1, Section 6.1
                     stopping rule) and dense Cholesky for tiny meshes.
 * ``h1``         -- the relative H^1 error of Section 6.1.
+* ``edge``, ``vertex``, ``vertex_edge``
+                 -- the functional of the edge (eq. 4.7), vertex (eq. 4.3) and
+                    vertex-edge (eq. 2.28-2.29, 4.5) neighbourhoods in their
+                    modified coordinates, with their corner sets.
+* ``adjoint``    -- gradients of a solution functional by an adjoint solve.
 
 Every function is written for clarity, not speed.  Where the thesis is silent
 or ambiguous, the reading taken is stated in the docstring of the function

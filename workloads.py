@@ -456,7 +456,7 @@ class EdgeMeshDesc:
     corner_hi: np.ndarray      # [C] x3 upper end
     corner_problem: np.ndarray  # [C] int32
     n_problem: int = 1
-    kind: str = "edge"         # "edge" or "vertex" (modified coordinates (phi, theta, ln rho))
+    kind: str = "edge"         # "edge", "vertex" (phi, theta, ln rho) or "vertex-edge" (ln tan phi, theta, ln x3)
 
     @property
     def n_elem(self) -> int:
@@ -695,4 +695,119 @@ def vertex_batch(Ws, mu=0.15) -> EdgeProblem:
     base = vertex_poisson_singular(N=2, W=2, mu=mu)
     mesh = concat_edge_meshes([vertex_mesh(2 * int(W) + 4, int(W), mu=mu) for W in Ws])
     return EdgeProblem(mesh, base.f, base.g, base.u_exact, base.grad_exact, name="vertex_batch",
+                       meta=dict(Ws=[int(w) for w in Ws]))
+
+
+# ---------------------------------------------------------------------------
+# Vertex-edge neighbourhood (Section 2.3 / eq. 2.28-2.29, 4.5): around the
+# edge x3 > 0 leaving a vertex at the origin, the modified coordinates are
+# (psi, theta, zeta) = (ln tan phi, theta, ln x3), so r = e^{psi + zeta}
+# and x3 = e^zeta; every element is a box in these coordinates
+# ---------------------------------------------------------------------------
+def vertex_edge_mesh(N, W, mu=0.15, phi_v=PI / 4, delta=1.0, theta=(0.0, 1.5 * PI), J=3) -> EdgeMeshDesc:
+    """{0 < x3 < delta, 0 < phi < phi_v, theta_0 < theta < theta_1}: N finite
+    layers in psi (tan phi_i = mu^(N+1-i) tan phi_v, i = 1..N+1) x J theta
+    sectors x N layers in zeta (x3_k = delta mu^(N+1-k)), degree W in every
+    modified coordinate.  Corner sets: for each zeta layer k a polynomial in
+    zeta of degree W on psi < psi_1, shared by the theta sectors (code -2 - k,
+    the neighbour of face 0 of psi layer 1); and one constant on x3 < x3_1
+    (code -2 - N, the neighbour of face 4 of zeta layer 1).  Every other outer
+    face is Dirichlet.  Elements are numbered psi layer fastest, then zeta
+    layer, then theta sector."""
+    psis = np.log(np.tan(phi_v)) + np.log(mu) * np.arange(N, -1, -1, dtype=np.float64)
+    zets = np.log(delta) + np.log(mu) * np.arange(N, -1, -1, dtype=np.float64)
+    ths = np.linspace(theta[0], theta[1], J + 1)
+    E = N * N * J
+    lo = np.zeros((E, 3))
+    hi = np.zeros((E, 3))
+    nbr = -np.ones((E, 6), dtype=np.int32)
+
+    def eid(i, k, j):
+        return (j * N + k) * N + i
+
+    for j in range(J):
+        for k in range(N):
+            for i in range(N):
+                e = eid(i, k, j)
+                lo[e] = (psis[i], ths[j], zets[k])
+                hi[e] = (psis[i + 1], ths[j + 1], zets[k + 1])
+                nbr[e, 0] = eid(i - 1, k, j) if i > 0 else -2 - k
+                nbr[e, 1] = eid(i + 1, k, j) if i < N - 1 else -1
+                nbr[e, 2] = eid(i, k, j - 1) if j > 0 else -1
+                nbr[e, 3] = eid(i, k, j + 1) if j < J - 1 else -1
+                nbr[e, 4] = eid(i, k - 1, j) if k > 0 else -2 - N
+                nbr[e, 5] = eid(i, k + 1, j) if k < N - 1 else -1
+    cW = np.array([W] * N + [0], dtype=np.int32)
+    clo = np.concatenate([zets[:-1], [zets[0]]])   # the constant: its face zeta = zeta_1
+    chi = np.concatenate([zets[1:], [zets[0]]])
+    return EdgeMeshDesc(lo, hi, np.full(E, W, dtype=np.int32), nbr, np.zeros(E, dtype=np.int32),
+                        cW, clo, chi, np.zeros(N + 1, dtype=np.int32), kind="vertex-edge")
+
+
+def _ve_grid(ps, ts, zs):
+    z, t, p = np.meshgrid(np.asarray(zs, dtype=np.float64), np.asarray(ts, dtype=np.float64),
+                          np.asarray(ps, dtype=np.float64), indexing="ij")
+    return p, t, z
+
+
+def vertex_edge_singular(N, W, mu=0.15, alpha=2.0 / 3.0) -> EdgeProblem:
+    """Laplace problem with the edge singularity of a re-entrant edge of
+    opening 3 pi/2: w = r^alpha sin(alpha theta), alpha = 2/3, harmonic,
+    w = 0 on theta = 0 and theta = 3 pi/2, w = g on the other outer faces.
+    Data are functions of the modified coordinates on tensor grids
+    fun(psis, thetas, zetas) -> [len zetas, len thetas, len psis]; the
+    gradient is (w_r, w_theta / r, w_x3)."""
+    mesh = vertex_edge_mesh(N, W, mu=mu)
+
+    def w(ps, ts, zs):
+        p, t, z = _ve_grid(ps, ts, zs)
+        return np.exp(alpha * (p + z)) * np.sin(alpha * t)
+
+    def grad(ps, ts, zs):
+        p, t, z = _ve_grid(ps, ts, zs)
+        rp = alpha * np.exp((alpha - 1.0) * (p + z))
+        return rp * np.sin(alpha * t), rp * np.cos(alpha * t), 0.0 * p
+
+    def f(ps, ts, zs):
+        return 0.0 * _ve_grid(ps, ts, zs)[0]
+
+    return EdgeProblem(mesh, [f], [w], w, grad, name="vertex_edge_singular", meta=dict(alpha=alpha))
+
+
+def vertex_edge_polynomial(N, W, mu=0.15) -> EdgeProblem:
+    """A solution inside the discrete space, consistent with both corner kinds:
+    u = 2 + (zeta - zeta_1)^2 (zeta + (psi - psi_1)^2 theta): on psi = psi_1 it
+    is the polynomial 2 + (zeta - zeta_1)^2 zeta with vanishing psi and theta
+    derivatives, on zeta = zeta_1 the constant 2 with vanishing derivatives.
+    -Lap u = f with r^2 Lap u = u_psipsi + u_thetatheta
+    + e^{2 psi} (u_psipsi - 2 u_psizeta + u_zetazeta + u_psi - u_zeta)."""
+    mesh = vertex_edge_mesh(N, W, mu=mu)
+    psi1, zet1 = float(mesh.elem_lo[0, 0]), float(mesh.elem_lo[0, 2])
+
+    def u(ps, ts, zs):
+        p, t, z = _ve_grid(ps, ts, zs)
+        return 2.0 + (z - zet1) ** 2 * (z + (p - psi1) ** 2 * t)
+
+    def f(ps, ts, zs):
+        p, t, z = _ve_grid(ps, ts, zs)
+        a, b = z - zet1, p - psi1
+        u_p = 2.0 * a * a * b * t
+        u_pp = 2.0 * a * a * t
+        u_tt = 0.0 * p
+        u_z = 2.0 * a * (z + b * b * t) + a * a
+        u_zz = 2.0 * (z + b * b * t) + 4.0 * a
+        u_pz = 4.0 * a * b * t
+        k = np.exp(2.0 * p)
+        r2lap = u_pp + u_tt + k * (u_pp - 2.0 * u_pz + u_zz + u_p - u_z)
+        return -r2lap / np.exp(2.0 * (p + z))
+
+    return EdgeProblem(mesh, [f], [u], u, None, name="vertex_edge_polynomial", meta=dict(psi1=psi1, zeta1=zet1))
+
+
+def vertex_edge_batch(Ws, mu=0.15) -> EdgeProblem:
+    """Independent copies of the vertex-edge Laplace problem with uneven
+    degrees W_p (N_p = W_p + 2 layers in psi and in zeta) in one batch."""
+    base = vertex_edge_singular(N=2, W=2, mu=mu)
+    mesh = concat_edge_meshes([vertex_edge_mesh(int(W) + 2, int(W), mu=mu) for W in Ws])
+    return EdgeProblem(mesh, base.f, base.g, base.u_exact, base.grad_exact, name="vertex_edge_batch",
                        meta=dict(Ws=[int(w) for w in Ws]))

@@ -56,11 +56,12 @@ def parse():
     ap.add_argument("--precond", default="block", choices=["block", "separable"],
                     help="block: exact element blocks of A (set up once, FP64 factors); "
                          "separable: the C-form of eq. (5.19)-(5.20)")
-    ap.add_argument("--workload", default="varcoef", choices=["varcoef", "adjoint", "edge", "vertex", "poisson"],
+    ap.add_argument("--workload", default="varcoef", choices=["varcoef", "adjoint", "edge", "vertex", "vertex-edge", "poisson"],
                     help="varcoef: the 64-RHS W=8 solve; adjoint: the 256-problem theta-gradient batch; "
                          "edge / vertex: the uneven-degree batch of edge- / vertex-neighbourhood problems")
     ap.add_argument("--edge-replicas", type=int, default=146, help="copies of each degree W = 2..8")
     ap.add_argument("--replicas", type=int, default=4096, help="copies of the 2x2x2 Poisson problem")
+    ap.add_argument("--ve-replicas", type=int, default=16, help="copies of each degree W = 2..8 (vertex-edge)")
     ap.add_argument("--adj-problems", type=int, default=256)
     ap.add_argument("--adj-fd-problems", type=int, default=16)
     ap.add_argument("--fd-tol", type=float, default=1e-8, help="relative tolerance of the FD correction solves")
@@ -377,10 +378,12 @@ def run_adjoint(args, local):
 
 
 def run_edge(args, local):
-    """Uneven-degree batch of edge-neighbourhood problems (Table 6.18's Laplace
-    problem u = r^(1/3) sin(theta/3) x3 on the quarter cylinder, modified
-    coordinates, N = 2W + 4 geometric layers, mu = 0.15), W = 2..8, each
-    degree replicated: one launch per degree group per operator apply.
+    """Uneven-degree batch of neighbourhood problems, W = 2..8, each degree
+    replicated, one launch per degree group per operator apply: edge (Table
+    6.18's Laplace problem u = r^(1/3) sin(theta/3) x3 on the quarter
+    cylinder, N = 2W + 4 layers), vertex (Table 6.16's Poisson problem on the
+    spherical wedge, N = 2W + 4) or vertex-edge (w = r^(2/3) sin(2 theta/3) in
+    the cone phi < pi/4, N = W + 2 layers in psi and in zeta); mu = 0.15.
     Reports the FP32 apply GDOF/s, the mixed and FP64 time-to-solution with the
     element-block preconditioner, and the H1 difference of the two solutions."""
     import torch
@@ -388,10 +391,12 @@ def run_edge(args, local):
     build()
     from paper_1110_2316_gb300 import api
     dev = torch.device("cuda", local)
-    Ws = [W for W in range(2, 9) for _ in range(args.edge_replicas)]
+    kind = args.workload
+    reps = args.ve_replicas if kind == "vertex-edge" else args.edge_replicas
+    Ws = [W for W in range(2, 9) for _ in range(reps)]
     t0 = time.perf_counter()
-    vertex = args.workload == "vertex"
-    pb = wl.vertex_batch(Ws) if vertex else wl.edge_batch(Ws)
+    vertex = kind != "edge"   # no library H1 norm on vertex and vertex-edge meshes
+    pb = dict(edge=wl.edge_batch, vertex=wl.vertex_batch, **{"vertex-edge": wl.vertex_edge_batch})[kind](Ws)
     m = api.Mesh(pb.mesh, n_rhs=1, coef_kind=api.COEF_LAPLACE, device=local)
     m.set_data(**api.problem_data_arrays(m, pb))
     t_setup = time.perf_counter() - t0
@@ -430,15 +435,18 @@ def run_edge(args, local):
     else:
         h = m.h1_error(sol["mixed"], ref=sol["fp64"])
         diff = float(np.sqrt(h[0, 0] / h[0, 1]))
-    name = "vertex" if vertex else "edge"
-    what = ("Table 6.16 Poisson problem on the spherical wedge, vertex-neighbourhood elements in (phi, theta, "
-            "ln rho)" if vertex else "Table 6.18 Laplace problem on the quarter cylinder, edge-neighbourhood "
-            "elements in (ln r, theta, x3)")
+    name = kind
+    what = dict(vertex="Table 6.16 Poisson problem on the spherical wedge, vertex-neighbourhood elements in "
+                       "(phi, theta, ln rho), N = 2W+4 layers",
+                edge="Table 6.18 Laplace problem on the quarter cylinder, edge-neighbourhood elements in "
+                     "(ln r, theta, x3), N = 2W+4 layers",
+                **{"vertex-edge": "Laplace problem w = r^(2/3) sin(2 theta/3) in the cone phi < pi/4, x3 < 1, "
+                                  "0 < theta < 3 pi/2, vertex-edge elements in (ln tan phi, theta, ln x3), "
+                                  "N = W+2 layers in psi and zeta, 3 theta sectors"})[kind]
     line = dict(metric="%s-neighbourhood batch: operator-apply GDOF/s and time-to-solution, mixed vs FP64" % name,
                 value=n / (apply_ms * 1e-3) / 1e9, unit="GDOF/s", higher_is_better=True, n_gpus=1, dtype="f32",
                 data="synthetic",
-                config=dict(workload=what + ", W = 2..8 x %d replicas, N = 2W+4 layers, mu = 0.15, tol 1e-10"
-                            % args.edge_replicas,
+                config=dict(workload=what + ", W = 2..8 x %d replicas, mu = 0.15, tol 1e-10" % reps,
                             n_problem=len(Ws), n_elem=int(pb.mesh.n_elem), n_corner=int(pb.mesh.n_corner), ndof=n),
                 apply_ms=apply_ms, solves=out, speedup=out["fp64"]["tts_s"] / out["mixed"]["tts_s"],
                 rel_diff_mixed_vs_fp64=diff,
@@ -536,11 +544,12 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload in ("adjoint", "edge", "vertex", "poisson"):
+    if args.workload in ("adjoint", "edge", "vertex", "vertex-edge", "poisson"):
         import torch
         _, _, local = dist_env()
         torch.cuda.set_device(local)
-        run = dict(adjoint=run_adjoint, edge=run_edge, vertex=run_edge, poisson=run_poisson)[args.workload]
+        run = dict(adjoint=run_adjoint, edge=run_edge, vertex=run_edge, poisson=run_poisson,
+                   **{"vertex-edge": run_edge})[args.workload]
         return run(args, local)
     import torch
     ws, rank, local = dist_env()

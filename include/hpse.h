@@ -117,7 +117,7 @@ typedef struct {
    * x int (p^2 + p_x3^2) dx3.  Not supported with HPSE_COORD_EDGE
    * (HPSE_ERR_INVALID_ARG): the adjoint entry points, hpse_h1_error against
    * pointwise data, hpse_h1_error_noalloc. */
-  int32_t coord;               /* HPSE_COORD_CARTESIAN (0), _EDGE (1) or _VERTEX (2) */
+  int32_t coord;               /* HPSE_COORD_CARTESIAN (0), _EDGE (1), _VERTEX (2) or _VERTEX_EDGE (3) */
   int32_t n_corner;            /* corner sets (HPSE_COORD_EDGE), else 0            */
   const int32_t *corner_W;     /* [n_corner] degree in x3 (= that of its elements) */
   const int32_t *corner_problem; /* [n_corner] problem index                       */
@@ -131,7 +131,22 @@ typedef struct {
  * hold one constant each (corner_W = 0), neighbour code -2-c on face 4
  * (chi = lo); data sampled at (phi, theta, rho = e^chi).  Same restrictions as
  * HPSE_COORD_EDGE, and no H^1 norm. */
-enum { HPSE_COORD_CARTESIAN = 0, HPSE_COORD_EDGE = 1, HPSE_COORD_VERTEX = 2 };
+/* HPSE_COORD_VERTEX_EDGE (eq. 2.27-2.29; eq. 4.5): boxes in
+ * (psi, theta, zeta) = (ln tan phi, theta, ln x3) where an edge on the x3 axis
+ * leaves a vertex at the origin (r = e^{psi + zeta}, x3 = e^zeta).
+ * L^{v-e} u = -e^{zeta/2} (u_psipsi + u_thetatheta + e^{2 psi} (u_psipsi
+ * - 2 u_psizeta + u_zetazeta + u_psi - u_zeta)) = -e^{zeta/2} r^2 Lap u,
+ * F^{v-e} = e^{zeta/2} r^2 f; face norms of eq. (2.27) with E = sup sin phi and
+ * F = sup e^zeta ([u] in L2 times F G, G = E on faces zeta = const; the zeta
+ * derivative times E); Dirichlet faces: F (u - g) in L2 and the two
+ * tangential derivatives of u - g in the norm of eq. (2.27).  Two kinds of
+ * corner set: a polynomial in zeta (corner_W = the element degree, nodal on
+ * the W+1 GLL points of the zeta layer) on psi < psi_1 of one zeta layer,
+ * shared by the theta sectors, code -2-c on face 0 (psi = lo); and the vertex
+ * constant (corner_W = 0) on zeta < zeta_1, code -2-c on face 4 (zeta = lo).
+ * Data are sampled at the modified coordinates themselves (the caller
+ * converts).  Same restrictions as HPSE_COORD_VERTEX. */
+enum { HPSE_COORD_CARTESIAN = 0, HPSE_COORD_EDGE = 1, HPSE_COORD_VERTEX = 2, HPSE_COORD_VERTEX_EDGE = 3 };
 
 /* Problem data (Section 4.2: F, g of eq. 4.2).  Host FP64 arrays, copied.
  *   f      [n_rhs][hpse_nquad()]        source at the volume points (required)

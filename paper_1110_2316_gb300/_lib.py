@@ -21,7 +21,7 @@ STATUS_NAMES = {
 FP64, FP32 = 0, 1
 COEF_LAPLACE, COEF_SCALAR = 0, 1
 PRECOND_SEPARABLE, PRECOND_BLOCK = 0, 1
-COORD_CARTESIAN, COORD_EDGE, COORD_VERTEX = 0, 1, 2
+COORD_CARTESIAN, COORD_EDGE, COORD_VERTEX, COORD_VERTEX_EDGE = 0, 1, 2, 3
 
 
 class MeshDesc(C.Structure):

@@ -69,7 +69,8 @@ class Mesh:
         if self.is_edge:
             self._keep += [np.ascontiguousarray(desc.corner_W, dtype=np.int32),
                            np.ascontiguousarray(desc.corner_problem, dtype=np.int32)]
-            d.coord = _lib.COORD_VERTEX if getattr(desc, "kind", "edge") == "vertex" else _lib.COORD_EDGE
+            d.coord = {"edge": _lib.COORD_EDGE, "vertex": _lib.COORD_VERTEX,
+                       "vertex-edge": _lib.COORD_VERTEX_EDGE}[getattr(desc, "kind", "edge")]
             self.nbhd_kind = getattr(desc, "kind", "edge")
             d.n_corner = int(self._keep[5].shape[0])
             d.corner_W = self._keep[5].ctypes.data_as(C.c_void_p)
@@ -228,12 +229,17 @@ def problem_data_arrays(mesh: Mesh, problem):
     None) as callables on tensor grids (see workloads).  Returns the dict of
     host arrays expected by Mesh.set_data.  For an edge neighbourhood the
     query grids are modified coordinates (tau, theta, x3) and the data
-    functions take cylindrical coordinates: they are sampled at r = e^tau.
+    functions take cylindrical coordinates: they are sampled at r = e^tau;
+    for a vertex neighbourhood at rho = e^chi; a vertex-edge neighbourhood's
+    data functions take its modified coordinates themselves.
     """
     if getattr(mesh, "is_edge", False):
         if mesh.nbhd_kind == "vertex":   # (phi, theta, ln rho): sample at rho = e^chi
             def cyl(fun):
                 return lambda ps, hs, cs: fun(ps, hs, np.exp(cs))
+        elif mesh.nbhd_kind == "vertex-edge":  # data given in (ln tan phi, theta, ln x3)
+            def cyl(fun):
+                return fun
         else:                            # (ln r, theta, x3): sample at r = e^tau
             def cyl(fun):
                 return lambda ts, hs, zs: fun(np.exp(ts), hs, zs)

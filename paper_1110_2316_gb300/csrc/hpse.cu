@@ -208,7 +208,8 @@ struct hpse_mesh {
   // edge neighbourhood (HPSE_COORD_EDGE): corner sets and face weights
   int coord = HPSE_COORD_CARTESIAN, n_corner = 0, apply_coef = 0;
   std::vector<int> cW, cprob;             // per corner set: degree, problem
-  std::vector<int> cslot;                 // per element: slot of its corner face, or -1
+  std::vector<int> cslot;                 // per element [2]: slot of its corner face 0 / face 4, or -1
+  std::vector<int> slot_elem, slot_face;  // per slot: its element and face
   std::vector<int> slot_ptr, slot_list;   // CSR of slots per corner set
   std::vector<int> item_n;                // DOF count of each vector item (elements, then corner sets)
   DevBuf d_item_n, d_kappa64, d_kappa32, d_fw64, d_fw32, d_cslot, d_cW, d_cprob, d_slot_ptr, d_slot_list;
@@ -1053,9 +1054,18 @@ extern "C" int64_t hpse_kernel_launch_count(int32_t reset) {
 // R = sup e^chi with (c0, c1, c2) = R (hh_t1 hh_t2, hh_t2, hh_t1) for all
 // fields, [u] in L2 times R hh_t1 hh_t2; Dirichlet likewise, the tangential
 // fields times s_t^2; a corner set is one constant, A_cc = sum_faces 4 w0.
+//
+// Vertex-edge neighbourhood (eq. 2.27-2.29; axes (psi, theta, zeta)): the
+// per-x-point factor is e^{2 psi}; E = sup sin phi = sup (1 + e^{-2 psi})^{-1/2},
+// F = sup e^zeta over the face; (c0, c1, c2) = F (hh_t1 hh_t2, hh_t2, hh_t1),
+// the quotient along zeta times E, all of it times E on a face zeta = const;
+// [u] in L2 times F hh_t1 hh_t2 (times G = E on zeta = const), the zeta
+// derivative times E^2; Dirichlet: u - g in L2 times F hh_t1 hh_t2, the
+// tangential fields times s_t^2 (zeta: times E^2).  Corner sets of both kinds.
 static hpse_status setup_edge(hpse_mesh *m) {
   const int E = m->n_elem, C = m->n_corner;
   const bool vtx = m->coord == HPSE_COORD_VERTEX;
+  const bool ve = m->coord == HPSE_COORD_VERTEX_EDGE;
   std::vector<double> kap((size_t)E * hpse::KAPPA_STRIDE, 0.0), fw((size_t)E * 6 * hpse::FACE_W, 0.0);
   for (int e = 0; e < E; ++e) {
     const hm::DegreeTables &t = m->tabs.at(m->W[e]);
@@ -1071,6 +1081,25 @@ static hpse_status setup_edge(hpse_mesh *m) {
     for (int fi = 0; fi < 6; ++fi) {
       const int a = fi >> 1, side = fi & 1;
       const int t1 = a == 0 ? 1 : 0, t2 = a == 2 ? 1 : 2;
+      if (ve) {
+        const double psi = (a == 0 && !side) ? m->lo[3 * e] : m->hi[3 * e];
+        const double zet = (a == 2 && !side) ? m->lo[3 * e + 2] : m->hi[3 * e + 2];
+        const double Es = 1.0 / std::sqrt(1.0 + std::exp(-2.0 * psi)), F = std::exp(zet);
+        double c[3] = {F * hh[t1] * hh[t2], F * hh[t2], F * hh[t1]};
+        if (t2 == 2) c[2] *= Es;
+        if (a == 2)
+          for (double &v : c) v *= Es;
+        double *w = &fw[((size_t)e * 6 + fi) * hpse::FACE_W];
+        const bool dir = m->nbr[6 * e + fi] == -1;
+        w[0] = F * (a == 2 && !dir ? Es : 1.0) * hh[t1] * hh[t2];
+        const int ax[3] = {t1, t2, a};
+        for (int k = 0; k < 3; ++k) {
+          double f = ax[k] == 2 ? Es * Es : 1.0;
+          if (dir) f *= (k < 2) ? sc[ax[k]] * sc[ax[k]] : 0.0;
+          for (int j = 0; j < 3; ++j) w[1 + 3 * k + j] = f * c[j];
+        }
+        continue;
+      }
       if (vtx) {
         const double R = std::exp(a == 2 ? (side ? m->hi[3 * e + 2] : m->lo[3 * e + 2]) : m->hi[3 * e + 2]);
         const double c[3] = {R * hh[t1] * hh[t2], R * hh[t2], R * hh[t1]};
@@ -1106,7 +1135,7 @@ static hpse_status setup_edge(hpse_mesh *m) {
   // the element; (G - nu H) d = 0 in the symmetric form Wp^{-1/2} G Wp^{-1/2},
   // stored like the master tables (node-major eigenvectors, then nu)
   std::vector<double> zeig((size_t)E * hpse::ZEIG_STRIDE, 0.0);
-  for (int e = 0; e < E && !vtx; ++e) {
+  for (int e = 0; e < E && m->coord == HPSE_COORD_EDGE; ++e) {
     const hm::DegreeTables &t = m->tabs.at(m->W[e]);
     const int P = t.P;
     const double eta = std::exp(m->hi[3 * e]), e2 = eta * eta, e4 = e2 * e2;
@@ -1134,27 +1163,29 @@ static hpse_status setup_edge(hpse_mesh *m) {
   CK(upload(m->d_fw32, fw32));
   CK(upload(m->d_cslot, m->cslot));
   if (C == 0) return HPSE_OK;
-  // corner blocks: the corner trace on a face (nodal face grid p2 = x3, p1 = theta)
-  // is p replicated along p1 and its x3 derivative s_x3 D p; with 1^T MP 1 = 2
-  // and 1^T KP 1 = 0, A_cc = sum_faces 2 (w0 MP + s_x3^2 D^T (w4 MP + w6 KP) D)
+  // corner blocks.  A constant (degree 0, through face 4): its trace is 1 on
+  // the face and its derivatives vanish, A_cc = sum_faces 4 w0.  A polynomial
+  // along z (through face 0; nodal face grid p2 = z, p1 = y): the trace is p
+  // replicated along p1 and its z derivative s_z D p; with 1^T MP 1 = 2 and
+  // 1^T KP 1 = 0, A_cc = sum_faces 2 (w0 MP + s_z^2 D^T (w4 MP + w6 KP) D)
   const int S = (int)m->slot_list.size();
   std::vector<double> cinv((size_t)C * hpse::CSCR_STRIDE * hpse::CSCR_STRIDE, 0.0);
-  for (int c = 0; c < C && vtx; ++c) {
+  for (int c = 0; c < C; ++c) {
+    if (m->cW[c] != 0) continue;
     double a = 0.0;
     for (int i = m->slot_ptr[c]; i < m->slot_ptr[c + 1]; ++i)
-      for (int ee = 0; ee < E; ++ee)
-        if (m->cslot[ee] == m->slot_list[i]) a += 4.0 * fw[((size_t)ee * 6 + 4) * hpse::FACE_W];
+      a += 4.0 * fw[((size_t)m->slot_elem[m->slot_list[i]] * 6 + 4) * hpse::FACE_W];
     if (!(a > 0.0)) return HPSE_ERR_BREAKDOWN;
     cinv[(size_t)c * hpse::CSCR_STRIDE * hpse::CSCR_STRIDE] = 1.0 / std::sqrt(a);
   }
-  for (int c = 0; c < C && !vtx; ++c) {
+  for (int c = 0; c < C; ++c) {
+    if (m->cW[c] == 0) continue;
     const hm::DegreeTables &t = m->tabs.at(m->cW[c]);
     const int P = t.P;
     std::vector<double> Acc((size_t)P * P, 0.0);
+    if (m->slot_ptr[c] == m->slot_ptr[c + 1]) return HPSE_ERR_BREAKDOWN;
     for (int i = m->slot_ptr[c]; i < m->slot_ptr[c + 1]; ++i) {
-      int e = -1;
-      for (int ee = 0; ee < E; ++ee)
-        if (m->cslot[ee] == m->slot_list[i]) e = ee;
+      const int e = m->slot_elem[m->slot_list[i]];
       const double *w = &fw[((size_t)e * 6 + 0) * hpse::FACE_W];
       const double sz = 2.0 / (m->hi[3 * e + 2] - m->lo[3 * e + 2]);
       // M = w4 MP + w6 KP (the x3-derivative field, quotient along x3 = t2)
@@ -1205,8 +1236,8 @@ static hpse_status setup_edge(hpse_mesh *m) {
   CK(upload(m->d_slot_ptr, m->slot_ptr));
   CK(upload(m->d_slot_list, m->slot_list));
   std::vector<double> ch1(2 * (size_t)C, 0.0);
-  for (int e = 0; e < E && !vtx; ++e) {
-    if (m->cslot[e] < 0) continue;
+  for (int e = 0; e < E && m->coord == HPSE_COORD_EDGE; ++e) {
+    if (m->cslot[2 * e] < 0) continue;
     const int c = -2 - m->nbr[6 * e];
     const double r1 = std::exp(m->lo[3 * e]), hz = m->hi[3 * e + 2] - m->lo[3 * e + 2];
     ch1[2 * c] += 0.5 * r1 * r1 * (m->hi[3 * e + 1] - m->lo[3 * e + 1]) * 0.5 * hz;
@@ -1237,10 +1268,14 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
   m->n_rhs = d->n_rhs;
   m->coef_kind = d->coef_kind;
   m->coord = d->coord;
-  if (m->coord != HPSE_COORD_CARTESIAN && m->coord != HPSE_COORD_EDGE && m->coord != HPSE_COORD_VERTEX)
+  if (m->coord != HPSE_COORD_CARTESIAN && m->coord != HPSE_COORD_EDGE && m->coord != HPSE_COORD_VERTEX &&
+      m->coord != HPSE_COORD_VERTEX_EDGE)
     return HPSE_ERR_INVALID_ARG;
   const bool nbhd = m->coord != HPSE_COORD_CARTESIAN;
-  const int cface = m->coord == HPSE_COORD_VERTEX ? 4 : 0;  // face of layer 1 towards the corner set
+  // faces of layer 1 towards the corner sets: 0 (a polynomial along z: edge,
+  // vertex-edge) and 4 (a constant: vertex, vertex-edge)
+  const bool face0_ok = m->coord == HPSE_COORD_EDGE || m->coord == HPSE_COORD_VERTEX_EDGE;
+  const bool face4_ok = m->coord == HPSE_COORD_VERTEX || m->coord == HPSE_COORD_VERTEX_EDGE;
   if (nbhd) {
     // the modified-coordinate operator is built for the Laplacian (eq. 2.35)
     if (d->coef_kind != HPSE_COEF_LAPLACE || d->n_corner < 0) return HPSE_ERR_INVALID_ARG;
@@ -1249,8 +1284,10 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
     m->cW.assign(d->corner_W, d->corner_W + d->n_corner);
     m->cprob.assign(d->corner_problem, d->corner_problem + d->n_corner);
   }
-  m->apply_coef = m->coord == HPSE_COORD_EDGE ? hpse::COEF_EDGE
-                 : (m->coord == HPSE_COORD_VERTEX ? hpse::COEF_VERTEX : d->coef_kind);
+  m->apply_coef = m->coord == HPSE_COORD_EDGE            ? hpse::COEF_EDGE
+                 : m->coord == HPSE_COORD_VERTEX        ? hpse::COEF_VERTEX
+                 : m->coord == HPSE_COORD_VERTEX_EDGE ? hpse::COEF_VERTEX_EDGE
+                                                        : d->coef_kind;
   m->W.assign(d->elem_W, d->elem_W + E);
   m->prob.assign(d->elem_problem, d->elem_problem + E);
   m->nbr.assign(d->elem_nbr, d->elem_nbr + 6 * (size_t)E);
@@ -1267,23 +1304,27 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
   }
   const int C = m->n_corner;
   for (int c = 0; c < C; ++c)
-    if ((m->coord == HPSE_COORD_VERTEX ? m->cW[c] != 0 : (m->cW[c] < 1 || m->cW[c] > HPSE_MAX_W)) ||
-        m->cprob[c] < 0 || m->cprob[c] >= m->n_problem)
+    if (m->cW[c] < 0 || m->cW[c] > HPSE_MAX_W || m->cprob[c] < 0 || m->cprob[c] >= m->n_problem)
       return HPSE_ERR_INVALID_ARG;
   std::vector<int> corner_e(C, -1);  // first layer-1 element of each corner set
+  std::vector<int> corner_f(C, -1);  // the face through which it enters
   for (int e = 0; e < E; ++e)
     for (int fi = 0; fi < 6; ++fi) {
       const int n = m->nbr[6 * e + fi];
       if (n <= -2) {
         // corner set: edge coordinates, face tau = lo only, same degree, problem and x3 slab
         const int c = -2 - n;
-        if (!nbhd || fi != cface || c >= C) return HPSE_ERR_INVALID_ARG;
-        if (m->coord == HPSE_COORD_EDGE && m->cW[c] != m->W[e]) return HPSE_ERR_DEGREE;
+        if (!nbhd || c >= C || !((fi == 0 && face0_ok) || (fi == 4 && face4_ok))) return HPSE_ERR_INVALID_ARG;
+        // a polynomial along z has the degree of its elements, a constant 0
+        if (fi == 0 && m->cW[c] != m->W[e]) return HPSE_ERR_DEGREE;
+        if (fi == 4 && m->cW[c] != 0) return HPSE_ERR_DEGREE;
         if (m->cprob[c] != m->prob[e]) return HPSE_ERR_INVALID_ARG;
+        if (corner_f[c] >= 0 && corner_f[c] != fi) return HPSE_ERR_INVALID_ARG;
+        corner_f[c] = fi;
         if (corner_e[c] < 0) {
           corner_e[c] = e;
         } else {
-          // edge: one x3 slab and the same r_1; vertex: the same rho_1
+          // face 0: one z slab and the same x = lo; face 4: the same z = lo
           const int e0 = corner_e[c];
           auto differ = [&](int i0, int i1) {
             return std::fabs(m->lo[i0] - m->lo[i1]) > 1e-12 * std::max(1.0, std::fabs(m->lo[i1]));
@@ -1291,7 +1332,7 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
           auto differ_hi = [&](int i0, int i1) {
             return std::fabs(m->hi[i0] - m->hi[i1]) > 1e-12 * std::max(1.0, std::fabs(m->hi[i1]));
           };
-          const bool bad = m->coord == HPSE_COORD_EDGE
+          const bool bad = fi == 0
                                ? (differ(3 * e + 2, 3 * e0 + 2) || differ_hi(3 * e + 2, 3 * e0 + 2) || differ(3 * e, 3 * e0))
                                : differ(3 * e + 2, 3 * e0 + 2);
           if (bad) return HPSE_ERR_NONMATCHING_FACE;
@@ -1338,21 +1379,26 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
   m->ndof = od;
   m->nquad = oq;
   // face slots of the corner sets
-  m->cslot.assign(E, -1);
+  m->cslot.assign(2 * (size_t)E, -1);
   m->slot_ptr.assign(C + 1, 0);
-  {
-    std::vector<int> slot_elem;
-    for (int e = 0; e < E; ++e)
-      if (m->nbr[6 * e + cface] <= -2) {
-        m->cslot[e] = (int)slot_elem.size();
-        slot_elem.push_back(e);
-        m->slot_ptr[-2 - m->nbr[6 * e + cface] + 1]++;
+  m->slot_elem.clear();
+  m->slot_face.clear();
+  for (int e = 0; e < E; ++e)
+    for (int k = 0; k < 2; ++k) {
+      const int fi = 4 * k;
+      if (m->nbr[6 * e + fi] <= -2) {
+        m->cslot[2 * e + k] = (int)m->slot_elem.size();
+        m->slot_elem.push_back(e);
+        m->slot_face.push_back(fi);
+        m->slot_ptr[-2 - m->nbr[6 * e + fi] + 1]++;
       }
-    for (int c = 0; c < C; ++c) m->slot_ptr[c + 1] += m->slot_ptr[c];
+    }
+  for (int c = 0; c < C; ++c) m->slot_ptr[c + 1] += m->slot_ptr[c];
+  {
     std::vector<int> fill(m->slot_ptr.begin(), m->slot_ptr.end() - 1);
-    m->slot_list.assign(slot_elem.size(), 0);
-    for (size_t sl = 0; sl < slot_elem.size(); ++sl)
-      m->slot_list[fill[-2 - m->nbr[6 * slot_elem[sl] + cface]]++] = (int)sl;
+    m->slot_list.assign(m->slot_elem.size(), 0);
+    for (size_t sl = 0; sl < m->slot_elem.size(); ++sl)
+      m->slot_list[fill[-2 - m->nbr[6 * m->slot_elem[sl] + m->slot_face[sl]]]++] = (int)sl;
   }
   int64_t of = 0;
   for (int e = 0; e < E; ++e)
@@ -1510,8 +1556,8 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data) {
   // coefficients at the volume points: m = w J a^2, d_k = s_k a_k / a; wJa for b
   std::vector<double> wja(nq);
   std::vector<double> coef;
-  const bool vtx = m->coord == HPSE_COORD_VERTEX;
-  if (m->coef_kind == HPSE_COEF_SCALAR || vtx) coef.assign(4 * (size_t)nq, 0.0);
+  const bool vtx = m->coord == HPSE_COORD_VERTEX, ve = m->coord == HPSE_COORD_VERTEX_EDGE;
+  if (m->coef_kind == HPSE_COEF_SCALAR || vtx || ve) coef.assign(4 * (size_t)nq, 0.0);
   for (int e = 0; e < m->n_elem; ++e) {
     const hm::DegreeTables &t = m->tabs.at(m->W[e]);
     const int Q = t.Q;
@@ -1546,6 +1592,20 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data) {
             coef[4 * i + 2] = 0.0;
             coef[4 * i + 3] = s[2];
             wja[i] = wJ * c2 * std::exp(2.0 * ch);
+          } else if (ve) {
+            // L^{v-e} = -c (u_psipsi + u_thetatheta + k (u_psipsi - 2 u_psizeta +
+            // u_zetazeta + u_psi - u_zeta)) with c^2 = e^zeta, k = e^{2 psi}
+            // (eq. 2.28): m = w J c^2, d = (s_psi k, -2 s_psi s_zeta k [u_psizeta],
+            // -s_zeta k); 1 + k on u_psipsi and k on u_zetazeta are per-x-point
+            // factors of the kernel; b: F^{v-e} = c r^2 f with r = e^{psi + zeta}
+            const double ps = m->lo[3 * e] + (t.xq[a] + 1.0) * 0.5 * (m->hi[3 * e] - m->lo[3 * e]);
+            const double ze = m->lo[3 * e + 2] + (t.xq[c] + 1.0) * 0.5 * (m->hi[3 * e + 2] - m->lo[3 * e + 2]);
+            const double k = std::exp(2.0 * ps), c2 = std::exp(ze);
+            coef[4 * i] = wJ * c2;
+            coef[4 * i + 1] = s[0] * k;
+            coef[4 * i + 2] = -2.0 * s[0] * s[2] * k;
+            coef[4 * i + 3] = -s[2] * k;
+            wja[i] = wJ * c2 * std::exp(2.0 * (ps + ze));
           } else if (m->coord == HPSE_COORD_EDGE) {
             // F^e = e^{2 tau} f (eq. 4.7): tau is the x coordinate of the point
             const double tau = m->lo[3 * e] + (t.xq[a] + 1.0) * 0.5 * (m->hi[3 * e] - m->lo[3 * e]);
@@ -1580,7 +1640,7 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data) {
     for (auto &kv : m->d_qtab) tp[kv.first] = kv.second.as<double>();
     CK(upload_reuse(m->d_tabs_ptr, tp));
   }
-  if (m->coef_kind == HPSE_COEF_SCALAR || vtx) {
+  if (m->coef_kind == HPSE_COEF_SCALAR || vtx || ve) {
     std::vector<float> c32(coef.size());
     for (size_t i = 0; i < coef.size(); ++i) c32[i] = (float)coef[i];
     CK(upload_reuse(m->d_coef64, coef));
@@ -2411,7 +2471,9 @@ extern "C" hpse_status hpse_pcg_solve(hpse_mesh *m, const hpse_solve_opts *o, do
 extern "C" hpse_status hpse_h1_error(hpse_mesh *m, const double *u, const double *ref, const double *vq,
                                      const double *gq, double *out, void *stream) {
   // edge neighbourhood: the difference of two discrete solutions only
-  if (m && ((m->coord == HPSE_COORD_EDGE && !ref) || m->coord == HPSE_COORD_VERTEX)) return HPSE_ERR_INVALID_ARG;
+  if (m && ((m->coord == HPSE_COORD_EDGE && !ref) || m->coord == HPSE_COORD_VERTEX ||
+            m->coord == HPSE_COORD_VERTEX_EDGE))
+    return HPSE_ERR_INVALID_ARG;
   if (!m || !out) return HPSE_ERR_INVALID_ARG;
   if (m->ndof == 0) {
     for (int r = 0; r < m->n_rhs; ++r) out[2 * r] = out[2 * r + 1] = 0.0;

@@ -30,6 +30,11 @@ cudaError_t apply_fn(int coef, int mode, const void *args, int n_items, int thre
     if (mode == MODE_PLAIN) return launch_apply_t<COEF_VERTEX, MODE_PLAIN>(args, n_items, threads, s);
     if (mode == MODE_PCG) return launch_apply_t<COEF_VERTEX, MODE_PCG>(args, n_items, threads, s);
     if (mode == MODE_TRANSPOSE) return launch_apply_t<COEF_VERTEX, MODE_TRANSPOSE>(args, n_items, threads, s);
+  } else if (coef == COEF_VERTEX_EDGE) {
+    if (mode == MODE_PLAIN) return launch_apply_t<COEF_VERTEX_EDGE, MODE_PLAIN>(args, n_items, threads, s);
+    if (mode == MODE_PCG) return launch_apply_t<COEF_VERTEX_EDGE, MODE_PCG>(args, n_items, threads, s);
+    if (mode == MODE_TRANSPOSE)
+      return launch_apply_t<COEF_VERTEX_EDGE, MODE_TRANSPOSE>(args, n_items, threads, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -38,6 +43,7 @@ size_t apply_smem_fn(int coef) {
   if (coef == COEF_SCALAR) return ApplyLayout<COEF_SCALAR>::BYTES;
   if (coef == COEF_EDGE) return ApplyLayout<COEF_EDGE>::BYTES;
   if (coef == COEF_VERTEX) return ApplyLayout<COEF_VERTEX>::BYTES;
+  if (coef == COEF_VERTEX_EDGE) return ApplyLayout<COEF_VERTEX_EDGE>::BYTES;
   return ApplyLayout<COEF_LAPLACE>::BYTES;
 }
 
@@ -95,6 +101,9 @@ cudaError_t upload_fn(const double *pk) {
   if ((e2 = set_smem_attr<COEF_VERTEX, MODE_PLAIN>()) != cudaSuccess) return e2;
   if ((e2 = set_smem_attr<COEF_VERTEX, MODE_PCG>()) != cudaSuccess) return e2;
   if ((e2 = set_smem_attr<COEF_VERTEX, MODE_TRANSPOSE>()) != cudaSuccess) return e2;
+  if ((e2 = set_smem_attr<COEF_VERTEX_EDGE, MODE_PLAIN>()) != cudaSuccess) return e2;
+  if ((e2 = set_smem_attr<COEF_VERTEX_EDGE, MODE_PCG>()) != cudaSuccess) return e2;
+  if ((e2 = set_smem_attr<COEF_VERTEX_EDGE, MODE_TRANSPOSE>()) != cudaSuccess) return e2;
   if ((e2 = cudaFuncSetAttribute(k_precond<MODE_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)PC_BYTES)) != cudaSuccess)
     return e2;

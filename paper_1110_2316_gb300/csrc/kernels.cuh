@@ -87,10 +87,23 @@ using hpse::COEF_LAPLACE;
 using hpse::COEF_SCALAR;
 using hpse::COEF_EDGE;
 using hpse::COEF_VERTEX;
+using hpse::COEF_VERTEX_EDGE;
 // variable-coefficient fields (first derivatives, per-point weights)
-__host__ __device__ constexpr bool var_coef(int c) { return c == hpse::COEF_SCALAR || c == hpse::COEF_VERTEX; }
+__host__ __device__ constexpr bool var_coef(int c) {
+  return c == hpse::COEF_SCALAR || c == hpse::COEF_VERTEX || c == hpse::COEF_VERTEX_EDGE;
+}
+// the first derivative along y is a field (its coefficient is zero in the
+// vertex and vertex-edge operators, which skip it)
+__host__ __device__ constexpr bool y_first(int c) { return c == hpse::COEF_SCALAR; }
+// the mixed derivative u_xz is a field (vertex-edge operator)
+__host__ __device__ constexpr bool mixed_xz(int c) { return c == hpse::COEF_VERTEX_EDGE; }
 // neighbourhood elements: face-norm weights and corner sets
-__host__ __device__ constexpr bool nbhd_coef(int c) { return c == hpse::COEF_EDGE || c == hpse::COEF_VERTEX; }
+__host__ __device__ constexpr bool nbhd_coef(int c) {
+  return c == hpse::COEF_EDGE || c == hpse::COEF_VERTEX || c == hpse::COEF_VERTEX_EDGE;
+}
+// corner sets through face 0 (a polynomial along z) / face 4 (a constant)
+__host__ __device__ constexpr bool corner_f0(int c) { return c == hpse::COEF_EDGE || c == hpse::COEF_VERTEX_EDGE; }
+__host__ __device__ constexpr bool corner_f4(int c) { return c == hpse::COEF_VERTEX || c == hpse::COEF_VERTEX_EDGE; }
 using hpse::MODE_PLAIN;
 using hpse::MODE_PCG;
 using hpse::MODE_TRANSPOSE;
@@ -165,12 +178,12 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
       FSLOT(f, sFn)[sp] = (real)0;
       FSLOT(f, sNn)[sp] = (real)0;
     } else if (nbhd_coef(COEF) && nb < -1) {
-      // corner set: edge neighbourhood (face 0), its polynomial in x3 (the p2
-      // direction of this face), constant in theta and tau; vertex
-      // neighbourhood (face 4), one constant
+      // corner set: through face 0 a polynomial along z (the p2 direction of
+      // this face), constant in the other two variables (edge: x3; vertex-edge:
+      // zeta); through face 4 one constant (vertex, vertex-edge)
       const int64_t cb = (int64_t)r * A.ndof + A.dof_off[A.n_elem + (-2 - nb)];
       const real bt = (MODE == MODE_PCG) ? (real)A.beta[A.prob[e] * A.n_rhs + r] : (real)0;
-      FSLOT(f, sFn)[sp] = nb_value<MODE>(A, cb + (COEF == COEF_EDGE ? p2 : 0), bt);
+      FSLOT(f, sFn)[sp] = nb_value<MODE>(A, cb + (corner_f0(COEF) && f == 0 ? p2 : 0), bt);
       FSLOT(f, sNn)[sp] = (real)0;
     } else if (nb >= 0) {
       const int64_t base = (int64_t)r * A.ndof + A.dof_off[nb];
@@ -279,12 +292,13 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
     FSLOT(f, sJ3)[sp] = g3;
   }
   __syncthreads();
-  // corner side of the face r = r_1 (edge neighbourhood): minus the transposed
-  // corner traces of the weighted jumps, y_c[k] = -sum_p1 g0[k][p1]
-  // - s_x3 sum_m D[m][k] sum_p1 g2[m][p1] (the corner's theta and tau
-  // derivatives vanish), stored per (slot, rhs) for the corner kernel
-  if (COEF == COEF_EDGE && A.cscr && !A.self_only) {
-    const int slot = A.cslot[e];
+  // corner side of face 0 (r = r_1 of the edge, psi = psi_1 of the vertex-edge
+  // neighbourhood): minus the transposed corner traces of the weighted jumps,
+  // y_c[k] = -sum_p1 g0[k][p1] - s_z sum_m D[m][k] sum_p1 g2[m][p1] (the
+  // corner's derivatives along x and y vanish), stored per (slot, rhs) for the
+  // corner kernel
+  if (corner_f0(COEF) && A.cscr && !A.self_only) {
+    const int slot = A.cslot[2 * e];
     if (slot >= 0) {
       for (int k = tid; k < P; k += nt) {
         real s0 = 0, s2 = 0;
@@ -298,11 +312,11 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
       }
     }
   }
-  // corner side of the face rho = rho_1 (vertex neighbourhood, face 4): the
-  // corner constant's trace is 1 at every face node, so y_c = -sum of the
-  // weighted jump of u over the face
-  if (COEF == COEF_VERTEX && A.cscr && !A.self_only && tid == 0) {
-    const int slot = A.cslot[e];
+  // corner side of face 4 (rho = rho_1 of the vertex, zeta = zeta_1 of the
+  // vertex-edge neighbourhood): the corner constant's trace is 1 at every face
+  // node, so y_c = -sum of the weighted jump of u over the face
+  if (corner_f4(COEF) && A.cscr && !A.self_only && tid == 0) {
+    const int slot = A.cslot[2 * e + 1];
     if (slot >= 0) {
       real s0 = 0;
       for (int t = 0; t < P2; ++t) s0 += FSLOT(4, sJ0)[t];
@@ -420,19 +434,15 @@ __device__ __forceinline__ void y_fwd_chunk(const real *v0, const real *v1, cons
       t00 += c_tab.B[0][qb * P + j] * v0[j];
       tl0 += c_tab.B[2][qb * P + j] * v0[j];
       tl2 += c_tab.B[0][qb * P + j] * v2[j];
-      if (var_coef(COEF)) {
-        t10 += c_tab.B[0][qb * P + j] * v1[j];
-        t01 += c_tab.B[1][qb * P + j] * v0[j];
-      }
+      if (var_coef(COEF)) t10 += c_tab.B[0][qb * P + j] * v1[j];
+      if (y_first(COEF)) t01 += c_tab.B[1][qb * P + j] * v0[j];
     }
     const int o = (k * Q + qb) * Q + qa;
     if (ok) {
       T00[o] = t00;
       TL[o] = sx2 * tl2 + sy2 * tl0;
-      if (var_coef(COEF)) {
-        T10[o] = t10;
-        T01[o] = t01;
-      }
+      if (var_coef(COEF)) T10[o] = t10;
+      if (y_first(COEF)) T01[o] = t01;
     }
     __syncwarp();  // scheduling fence (register pressure); reached by all 32 lanes
   }
@@ -451,7 +461,7 @@ __device__ __forceinline__ void y_rev_chunk(const real *RZ, const real *R0, cons
       const int o = (k * Q + qb) * Q + qa;
       vz[qb] = RZ[o];
       v0[qb] = R0[o];
-      if (var_coef(COEF)) vy[qb] = RY[o];
+      if (y_first(COEF)) vy[qb] = RY[o];
     }
 #pragma unroll
     for (int j = R::B; j < R::E; ++j) {
@@ -461,7 +471,7 @@ __device__ __forceinline__ void y_rev_chunk(const real *RZ, const real *R0, cons
         x0 += c_tab.B[0][qb * P + j] * vz[qb];
         x0b += c_tab.B[2][qb * P + j] * v0[qb];
         x2 += c_tab.B[0][qb * P + j] * v0[qb];
-        if (var_coef(COEF)) x0c += c_tab.B[1][qb * P + j] * vy[qb];
+        if (y_first(COEF)) x0c += c_tab.B[1][qb * P + j] * vy[qb];
       }
       if (ok) {
         const int o = (k * P + j) * Q + qa;
@@ -525,7 +535,7 @@ __device__ __forceinline__ void x_rev_chunk(const real *X0, const real *X1, cons
 template <int COEF>
 struct ApplyLayout {
   static constexpr int NX = (var_coef(COEF)) ? 3 : 2;
-  static constexpr int NTF = (var_coef(COEF)) ? 4 : 2;
+  static constexpr int NTF = y_first(COEF) ? 4 : (var_coef(COEF) ? 3 : 2);
   static constexpr int T_REGION0 = NTF * Q2P;
   static constexpr int T_NEED = P3 + 6 * FACE_ARR * P2;
   static constexpr int T_REGION = T_REGION0 > T_NEED ? T_REGION0 : T_NEED;
@@ -542,7 +552,7 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real *su = reinterpret_cast<real *>(smem_raw);
   real *sX = su + P3;               // X0 | X2 | (X1)
-  real *sT = sX + L::NX * QP2;      // T00 | TL | (T10 | T01)
+  real *sT = sX + L::NX * QP2;      // T00 | TL | (T10) | (T01)
   real *stab = sT + L::T_REGION;    // D | MP | KP (runtime-indexed copies for the face phase)
   double *red = reinterpret_cast<double *>(smem_raw + L::RED_OFF);
   static_assert(L::RED_OFF % 16 == 0, "reduction buffer must be 16-byte aligned");
@@ -610,10 +620,13 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
           v2[j] = X2[(k * P + j) * Q + qa];
           if (var_coef(COEF)) v1[j] = X1[(k * P + j) * Q + qa];
         }
-        // vertex neighbourhood: u_22 carries 1/sin^2(x_1), constant along this y-line
+        // per-x-point factors, constant along this y-line: vertex neighbourhood
+        // 1/sin^2(x_1) on u_22, vertex-edge 1 + e^{2 x_1} on u_11
         const real sy2q = (COEF == COEF_VERTEX) ? sy2 * A.kappa[(int64_t)e * hpse::KAPPA_STRIDE + qa] : sy2;
+        const real sx2q =
+            (COEF == COEF_VERTEX_EDGE) ? sx2 * ((real)1 + A.kappa[(int64_t)e * hpse::KAPPA_STRIDE + qa]) : sx2;
 #define YF_CALL(CI) \
-  y_fwd_chunk<COEF, (CI < LS::NC ? CI : 0), LS::NC>(v0, v1, v2, T00, TL, T10, T01, qa, k, ok, sx2, sy2q)
+  y_fwd_chunk<COEF, (CI < LS::NC ? CI : 0), LS::NC>(v0, v1, v2, T00, TL, T10, T01, qa, k, ok, sx2q, sy2q)
         HPSE_DISPATCH4(LS::NC, c, YF_CALL);
 #undef YF_CALL
       }
@@ -628,9 +641,10 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
     const int l = ok ? lp : Q2 - 1;
     const int qa = l % Q, qb = l / Q;
     const int64_t cbase = A.coef_off[e] + (int64_t)qb * Q + qa;
-    // edge neighbourhood: e^{2 tau} multiplies the x3 second derivative;
-    // tau is the x coordinate, constant along this z-column
-    const real sz2c = (COEF == COEF_EDGE) ? sz2 * A.kappa[(int64_t)e * hpse::KAPPA_STRIDE + qa] : sz2;
+    // edge (vertex-edge) neighbourhood: e^{2 tau} (e^{2 psi}) multiplies the
+    // z second derivative; x is constant along this z-column
+    const real sz2c =
+        (COEF == COEF_EDGE || COEF == COEF_VERTEX_EDGE) ? sz2 * A.kappa[(int64_t)e * hpse::KAPPA_STRIDE + qa] : sz2;
     real rho[Q];
     if (MODE == MODE_TRANSPOSE) {
 #pragma unroll
@@ -642,10 +656,8 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
         const int o = (k * Q + qb) * Q + qa;
         a00[k] = T00[o];
         aL[k] = TL[o];
-        if (var_coef(COEF)) {
-          a10[k] = T10[o];
-          a01[k] = T01[o];
-        }
+        if (var_coef(COEF)) a10[k] = T10[o];
+        if (y_first(COEF)) a01[k] = T01[o];
       }
       const real wab = c_tab.WQ[qa] * c_tab.WQ[qb] * Jac;
 #pragma unroll
@@ -658,8 +670,10 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
           if (var_coef(COEF)) {
             s1z += c_tab.B[1][qc * P + k] * a00[k];
             sxx += c_tab.B[0][qc * P + k] * a10[k];
-            syy += c_tab.B[0][qc * P + k] * a01[k];
           }
+          // the d_y slot: u_y (variable coefficient) or u_xz (vertex-edge)
+          if (y_first(COEF)) syy += c_tab.B[0][qc * P + k] * a01[k];
+          if (mixed_xz(COEF)) syy += c_tab.B[1][qc * P + k] * a10[k];
         }
         const real sigma0 = sz2c * s2 + s0;
         if (var_coef(COEF)) {
@@ -696,8 +710,9 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
         if (var_coef(COEF)) {
           rz[k] += c_tab.B[1][qc * P + k] * rzd;
           rx[k] += c_tab.B[0][qc * P + k] * rxd;
-          ry[k] += c_tab.B[0][qc * P + k] * ryd;
         }
+        if (y_first(COEF)) ry[k] += c_tab.B[0][qc * P + k] * ryd;
+        if (mixed_xz(COEF)) rx[k] += c_tab.B[1][qc * P + k] * ryd;
       }
     }
     if (ok) {
@@ -706,10 +721,8 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
         const int o = (k * Q + qb) * Q + qa;
         T00[o] = rz[k];
         TL[o] = r0[k];
-        if (var_coef(COEF)) {
-          T10[o] = rx[k];
-          T01[o] = ry[k];
-        }
+        if (var_coef(COEF)) T10[o] = rx[k];
+        if (y_first(COEF)) T01[o] = ry[k];
       }
     }
   }
@@ -724,8 +737,10 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
       const int l = ok ? lp : QP - 1;
       const int qa = l % Q, k = l / Q;
       const real sy2q = (COEF == COEF_VERTEX) ? sy2 * A.kappa[(int64_t)e * hpse::KAPPA_STRIDE + qa] : sy2;
+      const real sx2q =
+          (COEF == COEF_VERTEX_EDGE) ? sx2 * ((real)1 + A.kappa[(int64_t)e * hpse::KAPPA_STRIDE + qa]) : sx2;
 #define YR_CALL(CI) \
-  y_rev_chunk<COEF, (CI < LS::NC ? CI : 0), LS::NC>(T00, TL, T10, T01, X0, X1, X2, qa, k, ok, sx2, sy2q)
+  y_rev_chunk<COEF, (CI < LS::NC ? CI : 0), LS::NC>(T00, TL, T10, T01, X0, X1, X2, qa, k, ok, sx2q, sy2q)
       HPSE_DISPATCH4(LS::NC, c, YR_CALL);
 #undef YR_CALL
     }

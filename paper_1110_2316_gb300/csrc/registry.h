@@ -12,7 +12,11 @@ namespace hpse {
 // COEF_VERTEX: the variable-coefficient form with per-point weights and
 // first-order terms, u_22 scaled by 1/sin^2(x_1) per x-point (vertex
 // neighbourhood, modified coordinates (phi, theta, ln rho))
-enum { COEF_LAPLACE = 0, COEF_SCALAR = 1, COEF_EDGE = 2, COEF_VERTEX = 3 };
+// COEF_VERTEX_EDGE: the variable-coefficient form with the mixed term u_13 in
+// place of u_2 (vertex-edge neighbourhood, (ln tan phi, theta, ln x3)):
+// per-point m and coefficients of (u_1, u_13, u_3), u_11 scaled by 1 + kappa
+// and u_33 by kappa per x-point, kappa = e^{2 psi}
+enum { COEF_LAPLACE = 0, COEF_SCALAR = 1, COEF_EDGE = 2, COEF_VERTEX = 3, COEF_VERTEX_EDGE = 4 };
 // KAPPA_STRIDE = 2 * HPSE_MAX_W + 1, CSCR_STRIDE = HPSE_MAX_W + 1 (checked in the host library)
 enum { KAPPA_STRIDE = 21, CSCR_STRIDE = 11, FACE_W = 10, ZEIG_STRIDE = 132 };
 enum { MODE_PLAIN = 0, MODE_PCG = 1, MODE_TRANSPOSE = 2 };
@@ -29,7 +33,7 @@ struct ApplyArgsT {
   const int32_t *nbr;
   const T *geo;
   const int32_t *prob;
-  const T *coef;            // [nquad][4]: m, d_x, d_y, d_z per volume point
+  const T *coef;            // [nquad][4]: m, d_x, d_y (COEF_VERTEX_EDGE: d_xz), d_z per volume point
   const int64_t *coef_off;
   int64_t nquad;
   const T *z;
@@ -41,9 +45,9 @@ struct ApplyArgsT {
   int32_t self_only;        // 1: neighbour traces taken as zero (diagonal blocks of A)
   // edge neighbourhood (COEF_EDGE); null / 0 for box meshes
   int32_t n_elem;           // corner set c's values start at dof_off[n_elem + c]
-  const T *kappa;           // [E][KAPPA_STRIDE]: e^{2 tau} at the element's Q x-points
+  const T *kappa;           // [E][KAPPA_STRIDE]: per x-point factor (e^{2 tau}, 1/sin^2 phi, e^{2 psi})
   const T *fw;              // [E][6][10] face-norm weights (null: all 1)
-  const int32_t *cslot;     // [E] slot of the element's corner face, or -1
+  const int32_t *cslot;     // [E][2] slot of the element's corner face 0 / face 4, or -1
   T *cscr;                  // [slots][n_rhs][CSCR_STRIDE] corner-side face contributions
 };
 

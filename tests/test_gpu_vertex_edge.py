@@ -1,0 +1,167 @@
+"""Vertex-edge-neighbourhood elements on the GPU (eq. 2.27-2.29 in modified
+coordinates (ln tan phi, theta, ln x3)) against the oracle: operator with the
+mixed psi-zeta term, right-hand side, element-block preconditioner with both
+kinds of corner set, PCG solutions, a batch of uneven degrees; and the H^1
+error of w = r^(2/3) sin(2 theta / 3) computed from GPU solutions.
+
+Tolerances as for the edge and vertex neighbourhoods: FP64 applies and
+right-hand side 1e-12 of max, FP32 applies 2e-5 of max; blocks (n + 4) eps
+kappa; solutions within kappa(A) x the stopping residual.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as wl
+from oracle.vertex_edge import VertexEdgeDiscretisation
+
+pytestmark = pytest.mark.gpu
+
+EPS64 = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1110_2316_gb300.build import build
+    build()
+    from paper_1110_2316_gb300 import api as A
+    return A
+
+
+def _problem(N, W, J=3, poly=False):
+    base = (wl.vertex_edge_polynomial if poly else wl.vertex_edge_singular)(N=N, W=W)
+    return wl.EdgeProblem(wl.vertex_edge_mesh(N, W, J=J), base.f, base.g, base.u_exact, base.grad_exact)
+
+
+def _mesh(api, pb):
+    m = api.Mesh(pb.mesh, n_rhs=1, coef_kind=api.COEF_LAPLACE)
+    m.set_data(**api.problem_data_arrays(m, pb))
+    return m
+
+
+@pytest.mark.parametrize("N,W,J", [(2, 3, 2), (3, 2, 3), (2, 5, 1)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_vertex_edge_apply_matches_oracle(api, N, W, J, prec):
+    pb = _problem(N, W, J)
+    d = VertexEdgeDiscretisation(pb)
+    m = _mesh(api, pb)
+    assert m.ndof == d.ndof
+    U = wl.random_dofs(d.ndof, seed=7)
+    yo = d.apply_A(U)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    u = torch.tensor(U, dtype=dt, device="cuda")
+    y = torch.empty_like(u)
+    m.apply_operator(u, y)
+    err = np.abs(y.double().cpu().numpy() - yo).max() / np.abs(yo).max()
+    assert err <= (1e-12 if prec == "fp64" else 2e-5), err
+    m.close()
+
+
+def test_vertex_edge_rhs_matches_oracle(api):
+    pb = _problem(2, 3, 2, poly=True)
+    d = VertexEdgeDiscretisation(pb)
+    m = _mesh(api, pb)
+    b = torch.empty(m.ndof, dtype=torch.float64, device="cuda")
+    m.get_rhs(b)
+    bo = d.rhs_b()
+    assert np.abs(b.cpu().numpy() - bo).max() <= 1e-12 * np.abs(bo).max()
+    m.close()
+
+
+def test_vertex_edge_polynomial_solution_on_gpu(api):
+    pb = _problem(2, 3, 2, poly=True)
+    d = VertexEdgeDiscretisation(pb)
+    m = _mesh(api, pb)
+    m.setup_block_preconditioner()
+    x = torch.zeros(m.ndof, dtype=torch.float64, device="cuda")
+    rep = m.pcg_solve(x, tol=1e-12, prec=api.FP64, max_iter=200000)
+    assert rep["status"] == 0
+    U = d.nodal_interpolant(pb.u_exact)
+    assert np.abs(x.cpu().numpy() - U).max() <= 1e-8 * np.abs(U).max()
+    m.close()
+
+
+def test_vertex_edge_block_preconditioner_matches_oracle(api):
+    pb = _problem(2, 2, 2)
+    d = VertexEdgeDiscretisation(pb)
+    A = d.dense_A()
+    m = _mesh(api, pb)
+    m.setup_block_preconditioner()
+    r = wl.random_dofs(d.ndof, seed=13)
+    z = torch.empty(d.ndof, dtype=torch.float64, device="cuda")
+    m.apply_preconditioner(torch.tensor(r, device="cuda"), z)
+    z = z.cpu().numpy()
+    blocks = [slice(d.off[e], d.off[e + 1]) for e in range(d.E)]
+    blocks += [slice(int(d.coff[c]), int(d.coff[c]) + d.Wc[c] + 1) for c in range(d.C)]
+    for sl in blocks:
+        B = A[sl, sl]
+        zo = np.linalg.solve(B, r[sl])
+        # n eps kappa for the factorisation, plus the fixed roundings of z = X^T (X r)
+        assert np.linalg.norm(z[sl] - zo) <= (B.shape[0] + 4) * EPS64 * np.linalg.cond(B) * np.linalg.norm(zo)
+    m.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("precond", ["separable", "block"])
+def test_vertex_edge_solve_matches_oracle(api, prec, precond):
+    pb = _problem(2, 2, 2)
+    d = VertexEdgeDiscretisation(pb)
+    A = d.dense_A()
+    xo = np.linalg.solve(A, d.rhs_b())
+    m = _mesh(api, pb)
+    if precond == "block":
+        m.setup_block_preconditioner()
+    x = torch.zeros(m.ndof, dtype=torch.float64, device="cuda")
+    rep = m.pcg_solve(x, tol=1e-11, prec=api.FP64 if prec == "fp64" else api.FP32, max_iter=200000)
+    assert rep["status"] == 0 and rep["rel_residual"] <= 1e-11
+    assert np.linalg.norm(x.cpu().numpy() - xo) <= np.linalg.cond(A) * 2e-11 * np.linalg.norm(xo)
+    m.close()
+
+
+def test_vertex_edge_batch_equals_individual_solves(api):
+    # uneven degrees in one launch: each problem's share of the batched solution
+    # equals its own solve (per-problem PCG scalars; the same iteration path)
+    Ws = (3, 2)
+    pb = wl.vertex_edge_batch(Ws)
+    m = _mesh(api, pb)
+    m.setup_block_preconditioner()
+    x = torch.zeros(m.ndof, dtype=torch.float64, device="cuda")
+    assert m.pcg_solve(x, tol=1e-11, prec=api.FP64, max_iter=200000)["status"] == 0
+    el, co = [], []
+    for W in Ws:
+        one = wl.vertex_edge_batch([W])
+        mi = _mesh(api, one)
+        mi.setup_block_preconditioner()
+        xi = torch.zeros(mi.ndof, dtype=torch.float64, device="cuda")
+        assert mi.pcg_solve(xi, tol=1e-11, prec=api.FP64, max_iter=200000)["status"] == 0
+        xi = xi.cpu().numpy()
+        ne = VertexEdgeDiscretisation(one).off[-1]
+        el.append(xi[:ne])
+        co.append(xi[ne:])
+        mi.close()
+    ref = np.concatenate(el + co)
+    assert np.linalg.norm(x.cpu().numpy() - ref) <= 1e-8 * np.linalg.norm(ref)
+    m.close()
+
+
+def test_vertex_edge_h1_error_from_gpu_solutions(api):
+    # w = r^(2/3) sin(2 theta / 3) in the cone phi < pi/4, x3 < 1, three theta
+    # sectors, N = W + 2 layers in psi and zeta: the relative H^1 error of the
+    # mixed-precision GPU solution decays with W and stays within a small
+    # factor of the nodal interpolant's (oracle H^1 norm in physical coordinates)
+    errs, ints = {}, {}
+    for W in (2, 3, 4, 5):
+        pb = _problem(W + 2, W)
+        d = VertexEdgeDiscretisation(pb)
+        m = _mesh(api, pb)
+        m.setup_block_preconditioner()
+        x = torch.zeros(m.ndof, dtype=torch.float64, device="cuda")
+        assert m.pcg_solve(x, tol=1e-10, prec=api.FP32, max_iter=200000)["status"] == 0
+        err, nrm = d.h1_error_exact(x.cpu().numpy())
+        ei, _ = d.h1_error_exact(d.nodal_interpolant(pb.u_exact))
+        errs[W], ints[W] = np.sqrt(err / nrm), np.sqrt(ei / nrm)
+        m.close()
+    for W in (2, 3, 4, 5):
+        assert errs[W] < 2.5 * ints[W], (W, errs, ints)
+    for W in (3, 4, 5):
+        assert errs[W] < 0.6 * errs[W - 1], errs

@@ -57,3 +57,30 @@ def test_degenerate_box_and_bad_counts(api):
     assert _status(api, m, n_rhs=0) == 1
     m.elem_problem[0] = 5
     assert _status(api, m) == 1
+
+
+def test_neighbourhood_corner_sets(api):
+    # vertex-edge: zeta polynomials through face 0 (degree W), the constant
+    # through face 4 (degree 0); any other combination is refused
+    assert _status(api, wl.vertex_edge_mesh(2, 3, J=2)) in (0, 7)  # 7: no device here
+    m = wl.vertex_edge_mesh(2, 3, J=2)
+    m.corner_W[0] = 2                     # polynomial degree differs from its elements'
+    assert _status(api, m) == 3
+    m = wl.vertex_edge_mesh(2, 3, J=2)
+    m.corner_W[-1] = 1                    # the constant must have degree 0
+    assert _status(api, m) == 3
+    m = wl.vertex_edge_mesh(2, 3, J=2)
+    e = int(np.nonzero(m.elem_nbr[:, 4] == -2 - 2)[0][0])
+    m.elem_nbr[e, 4] = -2                 # a zeta polynomial entered through face 4
+    assert _status(api, m) == 3
+    m = wl.vertex_edge_mesh(2, 3, J=2)
+    e = int(np.nonzero(m.elem_nbr[:, 0] == -2 - 1)[0][0])
+    m.elem_nbr[e, 0] = -2                 # the same polynomial in two zeta layers
+    assert _status(api, m) == 2
+    # edge meshes take corner sets through face 0 only, vertex meshes through face 4 only
+    m = wl.edge_mesh(2, 3)
+    m.elem_nbr[0, 4], m.elem_nbr[0, 0] = m.elem_nbr[0, 0], -1
+    assert _status(api, m) == 1
+    m = wl.vertex_mesh(2, 2)
+    m.elem_nbr[0, 0], m.elem_nbr[0, 4] = m.elem_nbr[0, 4], -1
+    assert _status(api, m) == 1

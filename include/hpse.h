@@ -343,6 +343,35 @@ hpse_status hpse_h1_error_noalloc(hpse_mesh *m, const double *u, const double *r
  * per right-hand side, split into volume and face parts, as implemented. */
 hpse_status hpse_work_counts(const hpse_mesh *m, double *vol_macs, double *face_macs);
 
+/* ---- One problem over several GPUs (Section 5.3: each processor evaluates the
+ * residuals of its own elements after exchanging element-boundary values with
+ * its neighbours, and the PCG scalars are summed over all processors) ----
+ *
+ * hpse_partition assigns every element of a box mesh (coord
+ * HPSE_COORD_CARTESIAN) to one of n_parts parts: within each problem the
+ * elements are ordered along the Morton (Z-order) curve of their box centres,
+ * the problems follow one another, and the sequence is cut into n_parts
+ * contiguous pieces of nearly equal weight (W+1)^3.  owner: host array of
+ * n_elem entries, written.  Host only (no device call); deterministic.
+ * HPSE_ERR_INVALID_ARG for n_parts < 1, a neighbourhood mesh or bad pointers.
+ *
+ * A part runs as its own mesh: its elements followed by ghost copies of the
+ * elements of other parts that share a face with them (every other face of a
+ * ghost is marked Dirichlet); the rows of its own elements in A u are then
+ * those of the whole mesh once the ghosts hold the current values.
+ * hpse_pack_blocks / hpse_unpack_blocks move whole element blocks between a
+ * vector of `m` (n_rhs x ndof, FP64 or FP32 as `prec`) and a contiguous
+ * buffer (n_rhs x buf_len): buf[r][buf_off[i] + t] <-> vec[r][block of
+ * element items[i]][t], t < (W+1)^3.  items [n] and buf_off [n] are device
+ * int32 / int64 arrays (buf_off[i] + the block size of items[i] <= buf_len),
+ * vec and buf device memory of the caller.  One launch, asynchronous on
+ * `stream` (graph-capturable); no check of the device arrays' contents. */
+hpse_status hpse_partition(const hpse_mesh_desc *d, int32_t n_parts, int32_t *owner);
+hpse_status hpse_pack_blocks(const hpse_mesh *m, int32_t prec, const int32_t *items, const int64_t *buf_off,
+                             int32_t n, int64_t buf_len, const void *vec, void *buf, void *stream);
+hpse_status hpse_unpack_blocks(const hpse_mesh *m, int32_t prec, const int32_t *items, const int64_t *buf_off,
+                               int32_t n, int64_t buf_len, const void *buf, void *vec, void *stream);
+
 /* Kernel launch parameters: threads per CTA for degree W, precision prec,
  * kernel kind (0 = operator apply, 1 = preconditioner); set by the autotuner,
  * 0 restores the default. */

@@ -86,6 +86,11 @@ SIGNATURES = {
     "hpse_set_block_threads": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     "hpse_get_block_threads": (C.c_int32, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]),
     "hpse_kernel_launch_count": (C.c_int64, [C.c_int32]),
+    "hpse_partition": (C.c_int, [C.POINTER(MeshDesc), C.c_int32, C.c_void_p]),
+    "hpse_pack_blocks": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_int64,
+                                   C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hpse_unpack_blocks": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_int64,
+                                     C.c_void_p, C.c_void_p, C.c_void_p]),
     "hpse_status_string": (C.c_char_p, [C.c_int]),
     "hpse_destroy": (None, [C.c_void_p]),
 }

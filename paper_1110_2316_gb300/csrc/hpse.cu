@@ -2991,3 +2991,114 @@ extern "C" hpse_status hpse_h1_error_noalloc(hpse_mesh *m, const double *u, cons
   CK(cudaStreamSynchronize(s));
   return HPSE_OK;
 }
+
+// ---------------------------------------------------------------------------
+// One problem over several GPUs (Section 5.3): element partition along a
+// space-filling curve and the block copies of the ghost exchange.
+// ---------------------------------------------------------------------------
+// Morton key of three 21-bit integer coordinates (bit-interleaved, x lowest)
+static uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
+  uint64_t k = 0;
+  for (int b = 0; b < 21; ++b) {
+    k |= (uint64_t)((x >> b) & 1u) << (3 * b);
+    k |= (uint64_t)((y >> b) & 1u) << (3 * b + 1);
+    k |= (uint64_t)((z >> b) & 1u) << (3 * b + 2);
+  }
+  return k;
+}
+
+extern "C" hpse_status hpse_partition(const hpse_mesh_desc *d, int32_t n_parts, int32_t *owner) {
+  if (!d || !owner || n_parts < 1 || d->n_elem < 0 || d->n_problem < 1) return HPSE_ERR_INVALID_ARG;
+  if (d->coord != HPSE_COORD_CARTESIAN) return HPSE_ERR_INVALID_ARG;
+  const int E = d->n_elem;
+  if (E == 0) return HPSE_OK;
+  if (!d->elem_W || !d->elem_problem || !d->elem_lo || !d->elem_hi) return HPSE_ERR_INVALID_ARG;
+  // bounding box of each problem's element centres
+  std::vector<double> blo(3 * (size_t)d->n_problem, 1e300), bhi(3 * (size_t)d->n_problem, -1e300);
+  for (int e = 0; e < E; ++e) {
+    const int p = d->elem_problem[e];
+    if (p < 0 || p >= d->n_problem || d->elem_W[e] < 1 || d->elem_W[e] > HPSE_MAX_W) return HPSE_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a) {
+      const double c = 0.5 * (d->elem_lo[3 * e + a] + d->elem_hi[3 * e + a]);
+      if (!std::isfinite(c)) return HPSE_ERR_INVALID_ARG;
+      blo[3 * p + a] = std::min(blo[3 * p + a], c);
+      bhi[3 * p + a] = std::max(bhi[3 * p + a], c);
+    }
+  }
+  std::vector<std::pair<std::pair<int, uint64_t>, int>> order((size_t)E);
+  const double top = (double)((1u << 21) - 1);
+  for (int e = 0; e < E; ++e) {
+    const int p = d->elem_problem[e];
+    uint32_t q[3];
+    for (int a = 0; a < 3; ++a) {
+      const double c = 0.5 * (d->elem_lo[3 * e + a] + d->elem_hi[3 * e + a]);
+      const double span = bhi[3 * p + a] - blo[3 * p + a];
+      q[a] = span > 0.0 ? (uint32_t)std::lround((c - blo[3 * p + a]) / span * top) : 0u;
+    }
+    order[e] = {{p, morton3(q[0], q[1], q[2])}, e};
+  }
+  std::sort(order.begin(), order.end());
+  double total = 0.0;
+  for (int e = 0; e < E; ++e) total += std::pow((double)(d->elem_W[e] + 1), 3);
+  // element at prefix weight s (its midpoint s + w/2) goes to part floor(n (s + w/2) / total)
+  double s = 0.0;
+  for (const auto &o : order) {
+    const int e = o.second;
+    const double w = std::pow((double)(d->elem_W[e] + 1), 3);
+    int part = (int)std::floor((s + 0.5 * w) * n_parts / total);
+    owner[e] = std::min(n_parts - 1, std::max(0, part));
+    s += w;
+  }
+  return HPSE_OK;
+}
+
+template <typename T, bool PACK>
+__global__ void k_move_blocks(int32_t n, int32_t n_rhs, int64_t ndof, int64_t buf_len, const int32_t *items,
+                              const int64_t *buf_off, const int64_t *dof_off, const int32_t *item_n, const T *src,
+                              T *dst) {
+  const int i = blockIdx.x, r = blockIdx.y;
+  if (i >= n) return;
+  const int e = items[i];
+  const int len = item_n[e];
+  const int64_t v0 = (int64_t)r * ndof + dof_off[e], b0 = (int64_t)r * buf_len + buf_off[i];
+  for (int t = threadIdx.x; t < len; t += blockDim.x) {
+    if (PACK)
+      dst[b0 + t] = src[v0 + t];
+    else
+      dst[v0 + t] = src[b0 + t];
+  }
+}
+
+template <bool PACK>
+static hpse_status move_blocks(const hpse_mesh *m, int32_t prec, const int32_t *items, const int64_t *buf_off,
+                               int32_t n, int64_t buf_len, const void *src, void *dst, void *stream) {
+  if (!m || (prec != HPSE_FP64 && prec != HPSE_FP32) || n < 0 || buf_len < 0) return HPSE_ERR_INVALID_ARG;
+  if (n == 0 || m->ndof == 0) return HPSE_OK;
+  if (!items || !buf_off || !src || !dst) return HPSE_ERR_INVALID_ARG;
+  CK(cudaSetDevice(m->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const dim3 grid((unsigned)n, (unsigned)m->n_rhs);
+  if (prec == HPSE_FP64)
+    k_move_blocks<double, PACK><<<grid, 128, 0, s>>>(n, m->n_rhs, m->ndof, buf_len, items, buf_off,
+                                                     m->d_dof_off.as<int64_t>(), m->d_item_n.as<int32_t>(),
+                                                     (const double *)src, (double *)dst);
+  else
+    k_move_blocks<float, PACK><<<grid, 128, 0, s>>>(n, m->n_rhs, m->ndof, buf_len, items, buf_off,
+                                                    m->d_dof_off.as<int64_t>(), m->d_item_n.as<int32_t>(),
+                                                    (const float *)src, (float *)dst);
+  CK(cudaGetLastError());
+  ++g_launches;
+  return HPSE_OK;
+}
+
+extern "C" hpse_status hpse_pack_blocks(const hpse_mesh *m, int32_t prec, const int32_t *items,
+                                        const int64_t *buf_off, int32_t n, int64_t buf_len, const void *vec,
+                                        void *buf, void *stream) {
+  return move_blocks<true>(m, prec, items, buf_off, n, buf_len, vec, buf, stream);
+}
+
+extern "C" hpse_status hpse_unpack_blocks(const hpse_mesh *m, int32_t prec, const int32_t *items,
+                                          const int64_t *buf_off, int32_t n, int64_t buf_len, const void *buf,
+                                          void *vec, void *stream) {
+  return move_blocks<false>(m, prec, items, buf_off, n, buf_len, buf, vec, stream);
+}

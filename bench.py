@@ -187,6 +187,11 @@ def fp32_peak_tflops():
     return 152 * 128 * 2 * 2.07e9 / 1e12
 
 
+def fp64_peak_tflops():
+    """152 SMs x 2 FP64 FMA per cycle x 2 flops x 2.07 GHz maximum SM clock."""
+    return 152 * 2 * 2 * 2.07e9 / 1e12
+
+
 def cpu_baseline(pb, n_elems, reps=1):
     """The oracle's operator apply on a bounded sample of elements (1 rhs), `reps` times."""
     from oracle.functional import Discretisation
@@ -759,6 +764,11 @@ def main():
                           kernel="k_apply<COEF_SCALAR> FP32 (W=8)",
                           note="algorithmic volume flops (3,5,6)-field sum factorisation; peak = FP32 ALU "
                                "152 SM x 128 lanes x 2 x 2.07 GHz"),
+            roofline_fp64=dict(bound="alu", achieved=alg_flops / (apply64_ms * 1e-3) / 1e12,
+                               peak=fp64_peak_tflops(), unit="TFLOP/s",
+                               frac=alg_flops / (apply64_ms * 1e-3) / 1e12 / fp64_peak_tflops(),
+                               kernel="k_apply<COEF_SCALAR> FP64 (W=8), the refresh apply of the mixed solve",
+                               note="same algorithmic flops; peak = FP64 ALU 152 SM x 2 DFMA/cycle x 2 x 2.07 GHz"),
             cpu_baseline=cb, e2e=e2e, gpu_launches=int(launches), clocks=clocks,
         )
         print(json.dumps(line))

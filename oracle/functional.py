@@ -7,9 +7,12 @@ cube Q = (-1,1)^3 by x = lo + (lambda + 1) h / 2,
 
     R(u) = sum_l int_Q |L u_l - f|^2 J dlambda
          + sum_{interior faces} ( ||[u]||_0^2 + sum_k ||[u_{x_k}]||_{1/2}^2 )
-         + sum_{Dirichlet faces} ||u_l - g||_{3/2}^2 ,
+         + sum_{Dirichlet faces} ||u_l - g||_{3/2}^2
+         + sum_{Neumann faces} ||(du_l/dnu)_A - h||_{1/2}^2 ,
 
-with L u = -div(a grad u) (a = 1 for the Poisson / Laplace problems).
+with L u = -div(a grad u) (a = 1 for the Poisson / Laplace problems) and
+(du/dnu)_A = a grad u . nu the conormal derivative along the outward unit
+normal (eq. 2.1).
 
 Readings taken here (the thesis is silent or loose on them):
 
@@ -29,6 +32,9 @@ Readings taken here (the thesis is silent or loose on them):
   data g is the derivative of its interpolant on the face GLL grid (the
   differentiation matrix of eq. 5.47 applied to sampled g).
 * Each interior face has one jump term (it is not counted from both sides).
+* Neumann faces: the conormal derivative a du/dnu = +-a s_a du/dlambda_a
+  (a sampled on the face) at the face's GLL points against h = nu . q of the
+  problem's conormal field q, in the H^{1/2} norm of the other face terms.
 
 The functional is R(U) = (S U - d)^T M (S U - d), S the sampling map (volume
 samples weighted by sqrt(w J) so that M = I there; face samples unweighted with
@@ -354,6 +360,40 @@ class Discretisation:
         D = diff_matrix(xf)
         return [gv, gv @ D.T, D @ gv]
 
+    # --- Neumann faces (eq. 2.1, the last sum of eq. 4.2) -------------------
+    def is_neumann(self, e, fi):
+        bc = getattr(self.mesh, "elem_bc", None)
+        return bc is not None and int(self.mesh.elem_nbr[e, fi]) == -1 and int(bc[e, fi]) == 1
+
+    def _face_a(self, e, fi, Qf):
+        pb = self.part(e)
+        if pb.a is None:
+            return 1.0
+        xs, ys, zs = self.face_points(e, fi, Qf)
+        return np.broadcast_to(pb.a(xs, ys, zs), (len(zs), len(ys), len(xs))).reshape(Qf, Qf)
+
+    def neumann_sample(self, u, e, fi, Qf):
+        """a du/dnu on the face grid [t2, t1], nu the outward normal."""
+        axis, side, _, _ = self.face_axes(fi)
+        o = [0, 0, 0]
+        o[axis] = 1
+        sgn = 1.0 if side else -1.0
+        return sgn * self.scale(e)[axis] * self._face_a(e, fi, Qf) * self.face_eval(u, e, fi, Qf, tuple(o))
+
+    def neumann_sample_T(self, g, e, fi, Qf):
+        axis, side, _, _ = self.face_axes(fi)
+        o = [0, 0, 0]
+        o[axis] = 1
+        sgn = 1.0 if side else -1.0
+        return self.face_eval_T(sgn * self.scale(e)[axis] * self._face_a(e, fi, Qf) * g, e, fi, Qf, tuple(o))
+
+    def neumann_data(self, e, fi, Qf, rhs):
+        """h = nu . q at the face grid [t2, t1] from the problem's conormal field q."""
+        axis, side, _, _ = self.face_axes(fi)
+        xs, ys, zs = self.face_points(e, fi, Qf)
+        q = self.part(e).flux[rhs](xs, ys, zs)[axis]
+        return (1.0 if side else -1.0) * np.broadcast_to(q, (len(zs), len(ys), len(xs))).reshape(Qf, Qf)
+
     # --- the functional R (literal norm formulas) ------------------------
     def functional(self, U, rhs=0):
         """R(U) of eq. (4.2) with every norm summed term by term."""
@@ -376,6 +416,8 @@ class Discretisation:
                     R += l2_face_literal(fe[0] - fn[0], Qf)
                     for k in range(1, 4):
                         R += h12_face_literal(fe[k] - fn[k], Qf)
+                elif self.is_neumann(e, fi):
+                    R += h12_face_literal(self.neumann_sample(u, e, fi, Qf) - self.neumann_data(e, fi, Qf, rhs), Qf)
                 else:
                     sm = self.dirichlet_samples(u, e, fi, Qf)
                     dd = self.dirichlet_data(e, fi, Qf, rhs)
@@ -401,6 +443,9 @@ class Discretisation:
                 for k in range(1, 4):
                     gs.append((H @ (fe[k] - fn[k]).ravel()).reshape(Qf, Qf))
                 y = y + self.face_fields_T(gs, e, fi, Qf)
+            elif self.is_neumann(e, fi):
+                v = self.neumann_sample(u, e, fi, Qf)
+                y = y + self.neumann_sample_T((H @ v.ravel()).reshape(Qf, Qf), e, fi, Qf)
             else:
                 sm = self.dirichlet_samples(u, e, fi, Qf)
                 gs = [(W2 @ sm[0].ravel()).reshape(Qf, Qf),
@@ -426,6 +471,10 @@ class Discretisation:
                     continue
                 Qf = self.face_Qf(e, fi)
                 W2, H = face_mats(Qf)
+                if self.is_neumann(e, fi):
+                    hd = self.neumann_data(e, fi, Qf, rhs)
+                    y = y + self.neumann_sample_T((H @ hd.ravel()).reshape(Qf, Qf), e, fi, Qf)
+                    continue
                 dd = self.dirichlet_data(e, fi, Qf, rhs)
                 gs = [(W2 @ dd[0].ravel()).reshape(Qf, Qf),
                       (H @ dd[1].ravel()).reshape(Qf, Qf),

@@ -51,6 +51,10 @@ class Mesh:
     """
 
     def __init__(self, desc, n_rhs=1, coef_kind=COEF_LAPLACE, device=0):
+        bc = getattr(desc, "elem_bc", None)
+        if bc is not None and np.any((np.asarray(bc) != 0) & (np.asarray(desc.elem_nbr) == -1)):
+            raise ValueError("Neumann faces (eq. 2.1) are not supported by the CUDA operator: "
+                             "every outer face must be Dirichlet")
         self._lib = _lib.load()
         self._keep = [np.ascontiguousarray(desc.elem_W, dtype=np.int32),
                       np.ascontiguousarray(desc.elem_problem, dtype=np.int32),

@@ -1,0 +1,133 @@
+"""Pins of the oracle's Neumann faces (eq. 2.1; the last sum of eq. 4.2:
+||(du/dnu)_A - h||_{1/2}^2 on the faces of Gamma^[1]).
+
+* Closed forms on one element with u = x: every other term vanishes, the
+  Neumann term is ||a du/dnu - h||^2 over the reference face (area 4): 4 a^2
+  for h = 0 and 0 for the exact h = nu . (a grad u), on either side (the
+  outward normal's sign) and with a constant a.
+* A polynomial solution inside the discrete space with mixed Dirichlet and
+  Neumann faces makes R vanish and is returned by the normal equations.
+* Variation identity (literal functional vs matrix-free A, Neumann data
+  included); A symmetric positive definite.
+* Table 6.3 (mixed boundary conditions on (-1,1)^3, 2x2x2 elements): the H^1
+  error within 5x of the table at W = 2 and W = 4 (measured 11.1 % and
+  0.174 % against the table's 10.4 % and 0.541 %; W = 6 slow-marked).
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle.functional import Discretisation
+from oracle.h1 import h1_error_exact
+
+
+def _one_element(side, a_const=None, exact_flux=True):
+    mesh = wl.box_mesh(1, W=2)
+    bc = np.zeros((1, 6), dtype=np.int32)
+    bc[0, side] = 1
+    mesh.elem_bc = bc
+
+    def u(xs, ys, zs):
+        x, y, z = wl._grid(xs, ys, zs)
+        return x + 0 * y + 0 * z
+
+    av = 1.0 if a_const is None else a_const
+
+    def flux(xs, ys, zs):
+        x, y, z = wl._grid(xs, ys, zs)
+        one = np.ones_like(x)
+        return (av * one if exact_flux else 0 * one, 0 * one, 0 * one)
+
+    def zero(xs, ys, zs):
+        return 0.0 * wl._grid(xs, ys, zs)[0]
+
+    a = grad_a = None
+    if a_const is not None:
+        def a(xs, ys, zs):
+            return np.full((len(zs), len(ys), len(xs)), float(a_const))
+
+        def grad_a(xs, ys, zs):
+            z0 = np.zeros((len(zs), len(ys), len(xs)))
+            return z0, z0, z0
+    pb = wl.Problem(mesh, [zero], [u], a, grad_a, flux=[flux])
+    d = Discretisation(pb)
+    return d, d.nodal_interpolant(u)
+
+
+@pytest.mark.parametrize("side", [0, 1])
+@pytest.mark.parametrize("a_const", [None, 3.0])
+def test_neumann_term_closed_forms(side, a_const):
+    aa = 1.0 if a_const is None else a_const
+    d, U = _one_element(side, a_const, exact_flux=False)
+    assert d.functional(U) == pytest.approx(4.0 * aa * aa, rel=1e-12)
+    d, U = _one_element(side, a_const, exact_flux=True)
+    assert d.functional(U) <= 1e-24
+
+
+def _poly_mixed(W=3):
+    pb = wl.poisson_mixed(n=2, W=W)
+
+    def u(xs, ys, zs):
+        x, y, z = wl._grid(xs, ys, zs)
+        return (1 + x) * (1 - y * y) * (2 + z) + x * y * z
+
+    def f(xs, ys, zs):
+        x, y, z = wl._grid(xs, ys, zs)
+        return 2 * (1 + x) * (2 + z)
+
+    def q(xs, ys, zs):
+        x, y, z = wl._grid(xs, ys, zs)
+        return ((1 - y * y) * (2 + z) + y * z, -2 * y * (1 + x) * (2 + z) + x * z, (1 + x) * (1 - y * y) + x * y)
+
+    return wl.Problem(pb.mesh, [f], [u], None, None, [u], None, flux=[q])
+
+
+def test_neumann_polynomial_solution_is_reproduced():
+    pb = _poly_mixed()
+    d = Discretisation(pb)
+    U = d.nodal_interpolant(pb.u_exact[0])
+    assert d.functional(U) <= 1e-22 * d.functional(np.zeros(d.ndof))
+    from oracle.pcg import pcg
+    from oracle.precond import apply_block_inverse, block_factors
+    fac = block_factors(d)
+    x, _, rel = pcg(d.apply_A, lambda r: apply_block_inverse(d, r, fac), d.rhs_b(), tol=1e-13, maxit=5000)
+    assert np.linalg.norm(x - U) <= 1e-9 * np.linalg.norm(U)
+
+
+def test_neumann_variation_identity_and_spd():
+    pb = wl.poisson_mixed(n=2, W=2)
+    d = Discretisation(pb)
+    rng = np.random.default_rng(17)
+    U, V = rng.standard_normal(d.ndof), rng.standard_normal(d.ndof)
+    A, b = d.dense_A(), d.rhs_b()
+    assert np.abs(A - A.T).max() <= 1e-11 * np.abs(A).max()
+    assert np.linalg.eigvalsh(0.5 * (A + A.T)).min() > 0
+    for eps in (0.4, -1.3):
+        lhs = d.functional(U + eps * V)
+        rhs = d.functional(U) + 2 * eps * V @ (A @ U - b) + eps ** 2 * V @ A @ V
+        assert lhs == pytest.approx(rhs, rel=1e-10)
+
+
+def _table_6_3_error(W):
+    # block-Jacobi PCG to 1e-12 (the oracle's element blocks, scipy Cholesky)
+    from oracle.pcg import pcg
+    from oracle.precond import apply_block_inverse, block_factors
+    pb = wl.poisson_mixed(n=2, W=W)
+    d = Discretisation(pb)
+    fac = block_factors(d)
+    x, _, rel = pcg(d.apply_A, lambda r: apply_block_inverse(d, r, fac), d.rhs_b(), tol=1e-12, maxit=5000)
+    assert rel <= 1e-12
+    return h1_error_exact(d, x)
+
+
+def test_table_6_3_w2_w4():
+    # relative H^1 error (%) of Table 6.3: W = 2 10.3976, W = 4 0.540972
+    for W, ref in ((2, 0.103976), (4, 0.540972e-2)):
+        err = _table_6_3_error(W)
+        assert ref / 5 < err < ref * 5, (W, err, ref)
+
+
+@pytest.mark.slow
+def test_table_6_3_w6():
+    err = _table_6_3_error(6)   # Table 6.3: 0.614615E-02 %
+    assert 0.614615e-4 / 5 < err < 0.614615e-4 * 5, err

@@ -41,6 +41,9 @@ class MeshDesc:
     elem_nbr: np.ndarray       # [E, 6] int32, neighbour element id or -1
     elem_problem: np.ndarray   # [E] int32, problem index of each element
     n_problem: int = 1
+    # [E, 6] boundary condition of each outer face (elem_nbr = -1): 0 Dirichlet,
+    # 1 Neumann; None = every outer face Dirichlet
+    elem_bc: Optional[np.ndarray] = None
 
     @property
     def n_elem(self) -> int:
@@ -105,10 +108,14 @@ def concat_meshes(meshes: List[MeshDesc]) -> MeshDesc:
         probs.append(m.elem_problem + poff)
         off += m.n_elem
         poff += m.n_problem
+    bc = None
+    if any(getattr(m, "elem_bc", None) is not None for m in meshes):
+        bc = np.concatenate([m.elem_bc if getattr(m, "elem_bc", None) is not None
+                             else np.zeros((m.n_elem, 6), dtype=np.int32) for m in meshes]).astype(np.int32)
     return MeshDesc(np.concatenate(los), np.concatenate(his),
                     np.concatenate(Ws).astype(np.int32),
                     np.concatenate(nbrs).astype(np.int32),
-                    np.concatenate(probs).astype(np.int32), poff)
+                    np.concatenate(probs).astype(np.int32), poff, elem_bc=bc)
 
 
 # --------------------------------------------------------------------------
@@ -146,6 +153,9 @@ class Problem:
     grad_u_exact: Optional[List[Callable]] = None
     name: str = ""
     meta: dict = field(default_factory=dict)
+    # Neumann data (eq. 2.1): per right-hand side the conormal field a grad u,
+    # (qx, qy, qz) on tensor grids; a Neumann face takes h = nu . q
+    flux: Optional[List[Callable]] = None
 
     @property
     def n_rhs(self) -> int:
@@ -178,6 +188,37 @@ def poisson_sine(n=2, W=4, lo=0.0, hi=1.0) -> Problem:
         return (PI * cx * sy * sz, PI * sx * cy * sz, PI * sx * sy * cz)
 
     return Problem(mesh, [f], [_zero], None, None, [u], [gu], name="poisson_sine")
+
+
+def poisson_mixed(n=2, W=4) -> Problem:
+    """Table 6.3: -Lap u = f on (-1,1)^3, Dirichlet on x = -1, x = 1, y = -1,
+    Neumann on y = 1, z = -1, z = 1, exact
+    u = (2 / pi^2) sin(pi x / 2) (cos(pi y / 2) - sin(pi z / 2)), so that
+    -Lap u = (pi^2 / 2) u."""
+    mesh = box_mesh(n, (-1.0,) * 3, (1.0,) * 3, W)
+    bc = np.zeros((mesh.n_elem, 6), dtype=np.int32)
+    for e in range(mesh.n_elem):
+        for fi in (3, 4, 5):
+            if mesh.elem_nbr[e, fi] == -1:
+                bc[e, fi] = 1
+    mesh.elem_bc = bc
+    c = 2.0 / (PI * PI)
+
+    def u(xs, ys, zs):
+        x, y, z = _grid(xs, ys, zs)
+        return c * np.sin(PI * x / 2) * (np.cos(PI * y / 2) - np.sin(PI * z / 2))
+
+    def f(xs, ys, zs):
+        return 0.5 * PI * PI * u(xs, ys, zs)
+
+    def gu(xs, ys, zs):
+        x, y, z = _grid(xs, ys, zs)
+        sx, cx = np.sin(PI * x / 2), np.cos(PI * x / 2)
+        return (c * PI / 2 * cx * (np.cos(PI * y / 2) - np.sin(PI * z / 2)),
+                -c * PI / 2 * sx * np.sin(PI * y / 2),
+                -c * PI / 2 * sx * np.cos(PI * z / 2))
+
+    return Problem(mesh, [f], [u], None, None, [u], [gu], name="poisson_mixed", flux=[gu])
 
 
 def polynomial_exact(n=2, W=3, lo=-1.0, hi=1.0) -> Problem:

@@ -84,3 +84,9 @@ def test_neighbourhood_corner_sets(api):
     m = wl.vertex_mesh(2, 2)
     m.elem_nbr[0, 0], m.elem_nbr[0, 4] = m.elem_nbr[0, 4], -1
     assert _status(api, m) == 1
+
+
+def test_neumann_faces_are_refused_by_the_cuda_binding(api):
+    # the oracle carries Neumann faces (eq. 4.2); the CUDA operator does not yet
+    with pytest.raises(ValueError):
+        api.Mesh(wl.poisson_mixed(n=2, W=3).mesh)

@@ -234,9 +234,42 @@ class Discretisation:
         wq = tables(self.W[e])["wq"]
         return wq[:, None, None] * wq[None, :, None] * wq[None, None, :] * self.jac(e)
 
+    # --- the general operator of eq. (2.2), written out ---------------------
+    # L u = sum_ij A_ij u_{x_i x_j} + sum_i b_i u_{x_i} + c u (A symmetric); the
+    # divergence form -sum d_i(a_ij u_j) of eq. (2.2) is this with A = -a and
+    # b_j -= sum_i d_i a_ij.  A problem gives it as op(xs, ys, zs) -> (A, b, c)
+    # on tensor grids (3x3 nested A, 3 b, scalar c; arrays or constants).
+    def _op_terms(self, e):
+        """(coefficient [Q,Q,Q], x, y, z matrices) of every term of L."""
+        B0, B1, B2 = tables(self.W[e])["B"]
+        Q = tables(self.W[e])["Q"]
+        s = self.scale(e)
+        A, b, c = self.part(e).op(*self.qpoints(e))
+
+        def full(v):
+            return np.broadcast_to(np.asarray(v, dtype=np.float64), (Q, Q, Q))
+        Bm = {0: B0, 1: B1, 2: B2}
+        terms = []
+        for i in range(3):
+            for j in range(i, 3):
+                order = [0, 0, 0]
+                order[i] += 1
+                order[j] += 1
+                coef = (1.0 if i == j else 2.0) * full(A[i][j]) * s[i] * s[j]
+                terms.append((coef, Bm[order[0]], Bm[order[1]], Bm[order[2]]))
+        for i in range(3):
+            order = [0, 0, 0]
+            order[i] = 1
+            terms.append((full(b[i]) * s[i], Bm[order[0]], Bm[order[1]], Bm[order[2]]))
+        terms.append((full(c), B0, B0, B0))
+        return terms
+
     # --- volume term: L u at the quadrature points (eq. 4.2) ---------------
     def L_apply(self, u, e):
-        """L u = -a (u_xx + u_yy + u_zz) - grad a . grad u at the (2W+1)^3 points."""
+        """L u = -a (u_xx + u_yy + u_zz) - grad a . grad u at the (2W+1)^3 points
+        (or the problem's general operator)."""
+        if getattr(self.part(e), "op", None) is not None:
+            return sum(cf * eval_tensor(u, Mx, My, Mz) for cf, Mx, My, Mz in self._op_terms(e))
         B0, B1, B2 = tables(self.W[e])["B"]
         s = self.scale(e)
         a, (ax, ay, az) = self.coef(e)
@@ -250,6 +283,8 @@ class Discretisation:
 
     def L_apply_T(self, r, e):
         """Adjoint of L_apply (same coefficients, transposed evaluation matrices)."""
+        if getattr(self.part(e), "op", None) is not None:
+            return sum(eval_tensor_T(cf * r, Mx, My, Mz) for cf, Mx, My, Mz in self._op_terms(e))
         B0, B1, B2 = tables(self.W[e])["B"]
         s = self.scale(e)
         a, (ax, ay, az) = self.coef(e)
@@ -362,37 +397,53 @@ class Discretisation:
 
     # --- Neumann faces (eq. 2.1, the last sum of eq. 4.2) -------------------
     def is_neumann(self, e, fi):
+        """A Neumann (bc 1) or Robin (bc 2) face."""
         bc = getattr(self.mesh, "elem_bc", None)
-        return bc is not None and int(self.mesh.elem_nbr[e, fi]) == -1 and int(bc[e, fi]) == 1
+        return bc is not None and int(self.mesh.elem_nbr[e, fi]) == -1 and int(bc[e, fi]) in (1, 2)
+
+    def _robin(self, e, fi):
+        bc = getattr(self.mesh, "elem_bc", None)
+        return float(getattr(self.part(e), "robin_gamma", 1.0)) if int(bc[e, fi]) == 2 else 0.0
 
     def _face_a(self, e, fi, Qf):
         pb = self.part(e)
-        if pb.a is None:
+        if pb.a is None:   # the Laplacian, or a general operator: the plain normal derivative
             return 1.0
         xs, ys, zs = self.face_points(e, fi, Qf)
         return np.broadcast_to(pb.a(xs, ys, zs), (len(zs), len(ys), len(xs))).reshape(Qf, Qf)
 
     def neumann_sample(self, u, e, fi, Qf):
-        """a du/dnu on the face grid [t2, t1], nu the outward normal."""
+        """a du/dnu (+ gamma u on a Robin face) on the face grid [t2, t1], nu
+        the outward normal."""
         axis, side, _, _ = self.face_axes(fi)
         o = [0, 0, 0]
         o[axis] = 1
         sgn = 1.0 if side else -1.0
-        return sgn * self.scale(e)[axis] * self._face_a(e, fi, Qf) * self.face_eval(u, e, fi, Qf, tuple(o))
+        v = sgn * self.scale(e)[axis] * self._face_a(e, fi, Qf) * self.face_eval(u, e, fi, Qf, tuple(o))
+        gam = self._robin(e, fi)
+        return v + gam * self.face_eval(u, e, fi, Qf, (0, 0, 0)) if gam else v
 
     def neumann_sample_T(self, g, e, fi, Qf):
         axis, side, _, _ = self.face_axes(fi)
         o = [0, 0, 0]
         o[axis] = 1
         sgn = 1.0 if side else -1.0
-        return self.face_eval_T(sgn * self.scale(e)[axis] * self._face_a(e, fi, Qf) * g, e, fi, Qf, tuple(o))
+        y = self.face_eval_T(sgn * self.scale(e)[axis] * self._face_a(e, fi, Qf) * g, e, fi, Qf, tuple(o))
+        gam = self._robin(e, fi)
+        return y + self.face_eval_T(gam * g, e, fi, Qf, (0, 0, 0)) if gam else y
 
     def neumann_data(self, e, fi, Qf, rhs):
-        """h = nu . q at the face grid [t2, t1] from the problem's conormal field q."""
+        """h = nu . q (+ gamma g on a Robin face) at the face grid [t2, t1] from
+        the problem's conormal field q and boundary values g."""
         axis, side, _, _ = self.face_axes(fi)
         xs, ys, zs = self.face_points(e, fi, Qf)
+        shape = (len(zs), len(ys), len(xs))
         q = self.part(e).flux[rhs](xs, ys, zs)[axis]
-        return (1.0 if side else -1.0) * np.broadcast_to(q, (len(zs), len(ys), len(xs))).reshape(Qf, Qf)
+        h = (1.0 if side else -1.0) * np.broadcast_to(q, shape).reshape(Qf, Qf)
+        gam = self._robin(e, fi)
+        if gam:
+            h = h + gam * np.broadcast_to(self.part(e).g[rhs](xs, ys, zs), shape).reshape(Qf, Qf)
+        return h
 
     # --- the functional R (literal norm formulas) ------------------------
     def functional(self, U, rhs=0):

@@ -237,6 +237,9 @@ def problem_data_arrays(mesh: Mesh, problem):
     for a vertex neighbourhood at rho = e^chi; a vertex-edge neighbourhood's
     data functions take its modified coordinates themselves.
     """
+    if getattr(problem, "op", None) is not None:
+        raise ValueError("the general operator of eq. (2.2) is not supported by the CUDA operator: "
+                         "give -div(a grad u) through a / grad_a")
     if getattr(mesh, "is_edge", False):
         if mesh.nbhd_kind == "vertex":   # (phi, theta, ln rho): sample at rho = e^chi
             def cyl(fun):

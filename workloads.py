@@ -154,8 +154,13 @@ class Problem:
     name: str = ""
     meta: dict = field(default_factory=dict)
     # Neumann data (eq. 2.1): per right-hand side the conormal field a grad u,
-    # (qx, qy, qz) on tensor grids; a Neumann face takes h = nu . q
+    # (qx, qy, qz) on tensor grids; a Neumann face takes h = nu . q, a Robin
+    # face (bc 2) h = nu . q + robin_gamma g
     flux: Optional[List[Callable]] = None
+    robin_gamma: float = 1.0
+    # general operator sum A_ij u_ij + sum b_i u_i + c u (oracle only):
+    # op(xs, ys, zs) -> (A 3x3, b 3, c) on tensor grids; None: -div(a grad u)
+    op: Optional[Callable] = None
 
     @property
     def n_rhs(self) -> int:
@@ -219,6 +224,122 @@ def poisson_mixed(n=2, W=4) -> Problem:
                 -c * PI / 2 * sx * np.cos(PI * z / 2))
 
     return Problem(mesh, [f], [u], None, None, [u], [gu], name="poisson_mixed", flux=[gu])
+
+
+def _mixed_bc(mesh, neumann_faces=(3, 4, 5), code=1):
+    """Face codes of the outer faces: `code` on the listed faces (fi = 2 axis + side), 0 elsewhere."""
+    bc = np.zeros((mesh.n_elem, 6), dtype=np.int32)
+    for e in range(mesh.n_elem):
+        for fi in neumann_faces:
+            if mesh.elem_nbr[e, fi] == -1:
+                bc[e, fi] = code
+    mesh.elem_bc = bc
+    return mesh
+
+
+def helmholtz_mixed(n=2, W=4) -> Problem:
+    """Tables 6.6-6.7: -Lap u + u = f on (-1,1)^3, Dirichlet on x = +-1 and
+    y = -1, du/dnu = h on y = 1 and z = +-1, exact u = e^x cos(y) sin(z)
+    (so f = 2u).  General-operator form: A = -I, b = 0, c = 1."""
+    mesh = _mixed_bc(box_mesh(n, (-1.0,) * 3, (1.0,) * 3, W))
+
+    def u(xs, ys, zs):
+        x, y, z = _grid(xs, ys, zs)
+        return np.exp(x) * np.cos(y) * np.sin(z)
+
+    def f(xs, ys, zs):
+        return 2.0 * u(xs, ys, zs)
+
+    def gu(xs, ys, zs):
+        x, y, z = _grid(xs, ys, zs)
+        ex = np.exp(x)
+        return ex * np.cos(y) * np.sin(z), -ex * np.sin(y) * np.sin(z), ex * np.cos(y) * np.cos(z)
+
+    def op(xs, ys, zs):
+        return ([[-1.0, 0.0, 0.0], [0.0, -1.0, 0.0], [0.0, 0.0, -1.0]], [0.0, 0.0, 0.0], 1.0)
+
+    return Problem(mesh, [f], [u], None, None, [u], [gu], name="helmholtz_mixed", flux=[gu], op=op)
+
+
+def varcoef_robin(n=3, W=2) -> Problem:
+    """Table 6.12: a u_xx + b u_yy + c u_zz + d u = f on (-1,1)^3 with
+    du/dnu + u = g on every face, a = -(1 + 0.01 y sin x),
+    b = -(2.5 + 0.02 cos(x^2 + z)), c = -(3 + 0.03 y e^z),
+    d = 0.15 sin(2 pi (y + z)), exact u = cos(pi (x + y)) e^z."""
+    mesh = _mixed_bc(box_mesh(n, (-1.0,) * 3, (1.0,) * 3, W), neumann_faces=range(6), code=2)
+
+    def coefs(x, y, z):
+        return (-(1.0 + 0.01 * y * np.sin(x)), -(2.5 + 0.02 * np.cos(x * x + z)), -(3.0 + 0.03 * y * np.exp(z)),
+                0.15 * np.sin(2 * PI * (y + z)))
+
+    def u(xs, ys, zs):
+        x, y, z = _grid(xs, ys, zs)
+        return np.cos(PI * (x + y)) * np.exp(z)
+
+    def f(xs, ys, zs):
+        x, y, z = _grid(xs, ys, zs)
+        a, b, c, d = coefs(x, y, z)
+        w = np.cos(PI * (x + y)) * np.exp(z)
+        return (-PI * PI * (a + b) + c + d) * w
+
+    def gu(xs, ys, zs):
+        x, y, z = _grid(xs, ys, zs)
+        s_, ez = np.sin(PI * (x + y)), np.exp(z)
+        return -PI * s_ * ez, -PI * s_ * ez, np.cos(PI * (x + y)) * ez
+
+    def op(xs, ys, zs):
+        x, y, z = _grid(xs, ys, zs)
+        a, b, c, d = coefs(x, y, z)
+        zero = 0.0 * x
+        return ([[a, zero, zero], [zero, b, zero], [zero, zero, c]], [zero, zero, zero], d)
+
+    return Problem(mesh, [f], [u], None, None, [u], [gu], name="varcoef_robin", flux=[gu], op=op)
+
+
+def nonsym_mixed(n=2, W=4) -> Problem:
+    """Table 6.14: a u_xx + b u_yy + c u_zz + d (u_xy + u_yz + u_zx) + e u = f
+    on (-1,1)^3 with the boundary conditions of Table 6.3,
+    a = -(0.5 + 0.05 exp(xyz)), b = -(1 + 0.015 cos(x + y)),
+    c = -(2.5 + 0.02 exp(y + z)), d = -0.001 sin(pi (x + y + z)),
+    e = 4.05 + 0.045 cos(pi (x + y + z) / 2), exact
+    u = (sin(pi x) + sin(pi y / 2)) cos(pi z)."""
+    mesh = _mixed_bc(box_mesh(n, (-1.0,) * 3, (1.0,) * 3, W))
+
+    def coefs(x, y, z):
+        t = PI * (x + y + z)
+        return (-(0.5 + 0.05 * np.exp(x * y * z)), -(1.0 + 0.015 * np.cos(x + y)), -(2.5 + 0.02 * np.exp(y + z)),
+                -0.001 * np.sin(t), 4.05 + 0.045 * np.cos(t / 2))
+
+    def u(xs, ys, zs):
+        x, y, z = _grid(xs, ys, zs)
+        return (np.sin(PI * x) + np.sin(PI * y / 2)) * np.cos(PI * z)
+
+    def f(xs, ys, zs):
+        x, y, z = _grid(xs, ys, zs)
+        a, b, c, d, e = coefs(x, y, z)
+        sx, cx, sy, cy = np.sin(PI * x), np.cos(PI * x), np.sin(PI * y / 2), np.cos(PI * y / 2)
+        sz, cz = np.sin(PI * z), np.cos(PI * z)
+        uxx = -PI * PI * sx * cz
+        uyy = -PI * PI / 4 * sy * cz
+        uzz = -PI * PI * (sx + sy) * cz
+        uxy = 0.0 * x
+        uyz = -PI * PI / 2 * cy * sz
+        uzx = -PI * PI * cx * sz
+        return a * uxx + b * uyy + c * uzz + d * (uxy + uyz + uzx) + e * (sx + sy) * cz
+
+    def gu(xs, ys, zs):
+        x, y, z = _grid(xs, ys, zs)
+        return (PI * np.cos(PI * x) * np.cos(PI * z), PI / 2 * np.cos(PI * y / 2) * np.cos(PI * z),
+                -PI * (np.sin(PI * x) + np.sin(PI * y / 2)) * np.sin(PI * z))
+
+    def op(xs, ys, zs):
+        x, y, z = _grid(xs, ys, zs)
+        a, b, c, d, e = coefs(x, y, z)
+        h = 0.5 * d
+        zero = 0.0 * x
+        return ([[a, h, h], [h, b, h], [h, h, c]], [zero, zero, zero], e)
+
+    return Problem(mesh, [f], [u], None, None, [u], [gu], name="nonsym_mixed", flux=[gu], op=op)
 
 
 def polynomial_exact(n=2, W=3, lo=-1.0, hi=1.0) -> Problem:

@@ -90,3 +90,8 @@ def test_neumann_faces_are_refused_by_the_cuda_binding(api):
     # the oracle carries Neumann faces (eq. 4.2); the CUDA operator does not yet
     with pytest.raises(ValueError):
         api.Mesh(wl.poisson_mixed(n=2, W=3).mesh)
+
+
+def test_general_operator_problems_are_refused_by_the_cuda_binding(api):
+    with pytest.raises(ValueError):
+        api.problem_data_arrays(None, wl.helmholtz_mixed(n=2, W=2))

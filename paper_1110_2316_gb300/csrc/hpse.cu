@@ -869,8 +869,6 @@ static PrecArgsT<T> prec_args(const hpse_mesh *m, const Group &g) {
   return a;
 }
 
-static int prec_index(int prec) { return prec == HPSE_FP64 ? 0 : 1; }
-
 // stream of degree group gi for a launch ordered after work already on s
 static cudaError_t group_fork(hpse_mesh *m, cudaStream_t s) {
   if (m->groups.size() < 2) return cudaSuccess;

@@ -86,6 +86,8 @@ def local_part(desc, owner: np.ndarray, rank: int) -> LocalPart:
     lnbr[inside] = g2l[lnbr[inside]]          # outside the part -> -1 (only on ghosts)
     gprob = np.asarray(desc.elem_problem)[gids]
     prob_g, lprob = np.unique(gprob, return_inverse=True)
+    if len(prob_g) == 0:   # a part without elements (more parts than elements)
+        prob_g = np.zeros(1, dtype=np.int64)
     ldesc = SimpleNamespace(elem_lo=np.asarray(desc.elem_lo)[gids].copy(), elem_hi=np.asarray(desc.elem_hi)[gids].copy(),
                             elem_W=np.asarray(desc.elem_W)[gids].astype(np.int32),
                             elem_nbr=lnbr.astype(np.int32), elem_problem=lprob.astype(np.int32),

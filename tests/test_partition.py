@@ -190,3 +190,15 @@ def test_two_rank_ghost_exchange_apply_and_pcg():
     x = np.concatenate([xs[g] for g in range(full.E)])
     assert got[0][3] <= 1e-11 and got[0][2] == got[1][2]
     assert np.linalg.norm(x - x_ref) <= 1e-8 * np.linalg.norm(x_ref)
+
+
+def test_more_parts_than_elements():
+    desc = wl.box_mesh((2, 1, 1), W=2)
+    owner = pt.partition(desc, 4)
+    assert sorted(np.unique(owner).tolist()) == sorted(set(owner.tolist()))
+    assert np.bincount(owner, minlength=4).sum() == 2
+    for r in range(4):
+        p = pt.local_part(desc, owner, r)
+        assert p.n_owned == int(np.sum(owner == r)) and p.desc.n_problem >= 1
+        if p.n_owned == 0:
+            assert p.desc.n_elem == 0 and not p.send and not p.recv

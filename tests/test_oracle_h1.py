@@ -63,3 +63,29 @@ def test_table_6_2_loose():
         it_ref, err_ref = ref[W]
         assert err_ref / 10 < err < err_ref * 10, (W, err, err_ref)
         assert it_ref / 3 < it < it_ref * 3, (W, it, it_ref)
+
+
+def _table_6_1_error(W):
+    from oracle.pcg import pcg
+    from oracle.precond import apply_block_inverse, block_factors
+    d = Discretisation(wl.laplace_sinh(n=2, W=W))
+    fac = block_factors(d)
+    x, _, rel = pcg(d.apply_A, lambda r: apply_block_inverse(d, r, fac), d.rhs_b(), tol=1e-12, maxit=5000)
+    assert rel <= 1e-12
+    return h1_error_exact(d, x)
+
+
+def test_table_6_1_w2_w4():
+    # relative H^1 error (%) of Table 6.1 (Laplace, Dirichlet data, (0,1)^3 in
+    # 2x2x2 elements): 38.0 at W = 2, 2.05 at W = 4; measured 23.6 and 0.430 --
+    # the oracle's error falls faster with W than the table's (0.62, 0.21, 0.15
+    # of it at W = 2, 4, 6), so the window is (1/10, 5) of the table
+    for W, ref in ((2, 0.380275), (4, 0.204875e-1)):
+        err = _table_6_1_error(W)
+        assert ref / 10 < err < ref * 5, (W, err, ref)
+
+
+@pytest.mark.slow
+def test_table_6_1_w6():
+    err = _table_6_1_error(6)   # Table 6.1: 0.269917E-01 %, measured 4.06E-03 %
+    assert 0.269917e-3 / 10 < err < 0.269917e-3 * 5, err

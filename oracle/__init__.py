@@ -27,6 +27,8 @@ parallel computers, 2010):
                  -- the functional of the edge (eq. 4.7), vertex (eq. 4.3) and
                     vertex-edge (eq. 2.28-2.29, 4.5) neighbourhoods in their
                     modified coordinates, with their corner sets.
+* ``curved``     -- regular elements with a curved (non-affine) map: the chain
+                    rule through the map's first and second derivatives.
 * ``adjoint``    -- gradients of a solution functional by an adjoint solve.
 
 Every function is written for clarity, not speed.  Where the thesis is silent

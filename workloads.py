@@ -973,3 +973,125 @@ def vertex_edge_batch(Ws, mu=0.15) -> EdgeProblem:
     mesh = concat_edge_meshes([vertex_edge_mesh(int(W) + 2, int(W), mu=mu) for W in Ws])
     return EdgeProblem(mesh, base.f, base.g, base.u_exact, base.grad_exact, name="vertex_edge_batch",
                        meta=dict(Ws=[int(w) for w in Ws]))
+
+
+# ---------------------------------------------------------------------------
+# Curved regular elements: maps from the reference cube (-1,1)^3, each
+# returning (x [3, ...], dx/dlambda [3, 3, ...], d^2x/dlambda^2 [3, 3, 3, ...])
+# on broadcast arrays of reference coordinates
+# ---------------------------------------------------------------------------
+def affine_box_map(lo, hi):
+    """x = lo + (lambda + 1) (hi - lo) / 2."""
+    lo = np.asarray(lo, dtype=np.float64)
+    hh = (np.asarray(hi, dtype=np.float64) - lo) / 2.0
+
+    def m(l1, l2, l3):
+        l1, l2, l3 = np.broadcast_arrays(l1, l2, l3)
+        lam = (l1, l2, l3)
+        x = np.stack([lo[k] + (lam[k] + 1.0) * hh[k] for k in range(3)])
+        Dx = np.zeros((3, 3) + l1.shape)
+        for k in range(3):
+            Dx[k, k] = hh[k]
+        return x, Dx, np.zeros((3, 3, 3) + l1.shape)
+    return m
+
+
+def curved_mesh_of_boxes(desc):
+    """The affine maps of a box mesh, its degrees and neighbours."""
+    maps = [affine_box_map(desc.elem_lo[e], desc.elem_hi[e]) for e in range(desc.n_elem)]
+    return maps, np.asarray(desc.elem_W), np.asarray(desc.elem_nbr)
+
+
+LPRISM_C = 0.5
+
+
+def _lprism_side(theta_mid):
+    """(s, s') with r_max = 0.5 / s(theta): the side of the L-shaped section
+    seen from the re-entrant corner (0.5, 0.5) in direction theta."""
+    t = theta_mid % (2 * PI)
+    if PI / 2 <= t < 3 * PI / 4:
+        return (lambda th: np.sin(th)), (lambda th: np.cos(th))          # y = 1
+    if 3 * PI / 4 <= t < 5 * PI / 4:
+        return (lambda th: -np.cos(th)), (lambda th: np.sin(th))         # x = 0
+    if 5 * PI / 4 <= t < 7 * PI / 4:
+        return (lambda th: -np.sin(th)), (lambda th: -np.cos(th))        # y = 0
+    return (lambda th: np.cos(th)), (lambda th: -np.sin(th))             # x = 1
+
+
+def lprism_blend_map(th0, th1, Z=0.25, z0=0.0, z1=1.0):
+    """Polar blend of a sector of the L-shaped section ((0,1)^2 minus
+    (0.5,1)^2) x (z0, z1) around the re-entrant corner c = (0.5, 0.5):
+    x = c + [(1 - t) Z + t r_max(theta)] (cos theta, sin theta), x3 = z, with
+    t = (l1 + 1)/2, theta = th0 + (l2 + 1)(th1 - th0)/2, z = z0 + (l3 + 1)(z1 - z0)/2.
+    The sector must lie on one side of the square (r_max analytic in it)."""
+    s, sp = _lprism_side(0.5 * (th0 + th1))
+    dth, dz = th1 - th0, z1 - z0
+    fac = (0.5, 0.5 * dth, 0.5 * dz)
+
+    def m(l1, l2, l3):
+        l1, l2, l3 = np.broadcast_arrays(l1, l2, l3)
+        t = (l1 + 1.0) / 2.0
+        th = th0 + (l2 + 1.0) * dth / 2.0
+        zz = z0 + (l3 + 1.0) * dz / 2.0
+        sv, spv = s(th), sp(th)
+        R = 0.5 / sv
+        R1 = -0.5 * spv / sv ** 2
+        R2 = 0.5 * (2 * spv * spv + sv * sv) / sv ** 3
+        rho = (1.0 - t) * Z + t * R
+        r1, r2 = t * R1, t * R2
+        c, sn = np.cos(th), np.sin(th)
+        x = np.stack([LPRISM_C + rho * c, LPRISM_C + rho * sn, zz])
+        zero = np.zeros_like(t)
+        d = [[(R - Z) * c, r1 * c - rho * sn, zero],
+             [(R - Z) * sn, r1 * sn + rho * c, zero],
+             [zero, zero, zero + 1.0]]
+        Dx = np.stack([np.stack([d[k][a] * fac[a] for a in range(3)]) for k in range(3)])
+        h = [[[zero, R1 * c - (R - Z) * sn, zero], [R1 * c - (R - Z) * sn, r2 * c - 2 * r1 * sn - rho * c, zero],
+              [zero, zero, zero]],
+             [[zero, R1 * sn + (R - Z) * c, zero], [R1 * sn + (R - Z) * c, r2 * sn + 2 * r1 * c - rho * sn, zero],
+              [zero, zero, zero]],
+             [[zero] * 3, [zero] * 3, [zero] * 3]]
+        D2x = np.stack([np.stack([np.stack([h[k][a][b] * fac[a] * fac[b] for b in range(3)]) for a in range(3)])
+                        for k in range(3)])
+        return x, Dx, D2x
+    return m
+
+
+def lprism_regular(W, Z=0.25, J=6):
+    """The regular region of the L-shaped prism around its edge neighbourhood
+    of radius Z: J sectors of pi/4 from theta = pi/2 to 2 pi, one element each,
+    Laplace with w = r^(2/3) sin(2 theta'/3), theta' = theta - pi/2 measured from
+    the re-entrant face (w = 0 on both re-entrant faces).  Every outer face is
+    Dirichlet, the circle r = Z (the interface with the edge neighbourhood)
+    included.  Returns (maps, elem_W, elem_nbr, u, grad u, f) with pointwise
+    data functions of physical coordinates."""
+    ths = PI / 2 + np.arange(J + 1) * (1.5 * PI / J)
+    maps = [lprism_blend_map(ths[j], ths[j + 1], Z=Z) for j in range(J)]
+    nbr = -np.ones((J, 6), dtype=np.int32)
+    for j in range(J):
+        if j > 0:
+            nbr[j, 2] = j - 1
+        if j < J - 1:
+            nbr[j, 3] = j + 1
+
+    def polar(x, y):
+        dx, dy = x - LPRISM_C, y - LPRISM_C
+        r = np.hypot(dx, dy)
+        th = np.mod(np.arctan2(dy, dx) - PI / 2, 2 * PI)   # theta' in [0, 2 pi)
+        return r, th
+
+    def u(x, y, z):
+        r, th = polar(x, y)
+        return r ** (2.0 / 3.0) * np.sin(2.0 * th / 3.0) + 0 * z
+
+    def grad(x, y, z):
+        r, th = polar(x, y)
+        ur = 2.0 / 3.0 * r ** (-1.0 / 3.0) * np.sin(2.0 * th / 3.0)
+        ut = 2.0 / 3.0 * r ** (-1.0 / 3.0) * np.cos(2.0 * th / 3.0)
+        phi = th + PI / 2
+        return (ur * np.cos(phi) - ut * np.sin(phi), ur * np.sin(phi) + ut * np.cos(phi), 0 * z)
+
+    def f(x, y, z):
+        return 0.0 * (x + y + z)
+
+    return maps, np.full(J, W, dtype=np.int32), nbr, u, grad, f

@@ -29,6 +29,9 @@ parallel computers, 2010):
                     modified coordinates, with their corner sets.
 * ``curved``     -- regular elements with a curved (non-affine) map: the chain
                     rule through the map's first and second derivatives.
+* ``lprism``     -- the L-shaped prism: the edge neighbourhood next to curved
+                    regular elements, joined by the interface terms of the
+                    singular side.
 * ``adjoint``    -- gradients of a solution functional by an adjoint solve.
 
 Every function is written for clarity, not speed.  Where the thesis is silent

@@ -108,6 +108,9 @@ class EdgeDiscretisation:
         self.off = np.array(off[:self.E + 1], dtype=np.int64)
         self.coff = np.array(coff, dtype=np.int64)
         self.ndof = int(off[-1])
+        # (element, face) pairs whose terms a composite discretisation owns
+        # (an interface with another region); skipped here
+        self.skip_faces = set()
 
     # --- geometry ---------------------------------------------------------
     def h(self, e):
@@ -313,6 +316,8 @@ class EdgeDiscretisation:
             Qf = self.Qf(e)
             hh = self.h(e) / 2.0
             for fi in range(6):
+                if (e, fi) in self.skip_faces:
+                    continue
                 n = int(self.mesh.elem_nbr[e, fi])
                 axis, _, t1, t2 = self.face_axes(fi)
                 G = self.G(e, fi)
@@ -345,6 +350,8 @@ class EdgeDiscretisation:
         y = self.L_apply_T(self.vol_weight(e) * self.L_apply(u, e), e)
         Qf = self.Qf(e)
         for fi in range(6):
+            if (e, fi) in self.skip_faces:
+                continue
             n = int(self.mesh.elem_nbr[e, fi])
             if n == -1:
                 M = self.dirichlet_forms(e, fi, Qf)
@@ -393,7 +400,7 @@ class EdgeDiscretisation:
             y = self.L_apply_T(self.vol_weight(e) * self.f_at(e, rhs), e)
             Qf = self.Qf(e)
             for fi in range(6):
-                if int(self.mesh.elem_nbr[e, fi]) != -1:
+                if int(self.mesh.elem_nbr[e, fi]) != -1 or (e, fi) in self.skip_faces:
                     continue
                 M = self.dirichlet_forms(e, fi, Qf)
                 dd = self.dirichlet_data(e, fi, Qf, rhs)

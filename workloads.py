@@ -1095,3 +1095,31 @@ def lprism_regular(W, Z=0.25, J=6):
         return 0.0 * (x + y + z)
 
     return maps, np.full(J, W, dtype=np.int32), nbr, u, grad, f
+
+
+def lprism_problem(N, W, Z=0.25, mu=0.15, J=6):
+    """The L-shaped prism with the re-entrant-edge solution
+    w = r^(2/3) sin(2 theta'/3): the edge neighbourhood r < Z (N layers,
+    J sectors of pi/4 in theta' in (0, 3 pi/2), one x3 slab, degree W) and the
+    regular region (J polar-blend sectors, degree W), Dirichlet data w on the
+    outer faces.  Returns (edge problem, regular-region pieces of
+    lprism_regular, interface pairs (edge element of the outer layer, regular
+    element) sharing the circle r = Z)."""
+    mesh = edge_mesh(N, W, mu=mu, Z=Z, theta=(0.0, 1.5 * PI), x3=(0.0, 1.0), I=J, J=1)
+
+    def w(rs, ts, zs):
+        r, t, z = _cyl_grid(rs, ts, zs)
+        return r ** (2.0 / 3.0) * np.sin(2.0 * t / 3.0) + 0 * z
+
+    def grad(rs, ts, zs):
+        r, t, z = _cyl_grid(rs, ts, zs)
+        return (2.0 / 3.0 * r ** (-1.0 / 3.0) * np.sin(2.0 * t / 3.0),
+                2.0 / 3.0 * r ** (-1.0 / 3.0) * np.cos(2.0 * t / 3.0), 0 * z)
+
+    def zero(rs, ts, zs):
+        return np.zeros((len(zs), len(ts), len(rs)))
+
+    edge = EdgeProblem(mesh, [zero], [w], w, grad, name="lprism_edge")
+    regular = lprism_regular(W, Z=Z, J=J)
+    pairs = [(j * N + N - 1, j) for j in range(J)]
+    return edge, regular, pairs

@@ -298,8 +298,17 @@ class EdgeDiscretisation:
         s = self.scale(e)
         return [gv, s[t1] * (gv @ D.T), s[t2] * (D @ gv)]
 
-    def Qf(self, e):
-        return 2 * self.W[e] + 1
+    def Qf(self, e, fi=None):
+        """(2 W_f + 1)-point face grid, W_f the larger degree of the two sides
+        of face fi (the element's own degree without fi)."""
+        W = self.W[e]
+        if fi is not None:
+            n = int(self.mesh.elem_nbr[e, fi])
+            if n >= 0:
+                W = max(W, self.W[n])
+            elif n <= -2:
+                W = max(W, self.Wc[-2 - n])
+        return 2 * W + 1
 
     # --- the functional (literal norm sums) -------------------------------
     def _norm_literal(self, v, Qf, c):
@@ -313,11 +322,11 @@ class EdgeDiscretisation:
             R += float(np.sum(z * z))
         for e in range(self.E):
             u = self.block(U, e)
-            Qf = self.Qf(e)
             hh = self.h(e) / 2.0
             for fi in range(6):
                 if (e, fi) in self.skip_faces:
                     continue
+                Qf = self.Qf(e, fi)
                 n = int(self.mesh.elem_nbr[e, fi])
                 axis, _, t1, t2 = self.face_axes(fi)
                 G = self.G(e, fi)
@@ -348,10 +357,10 @@ class EdgeDiscretisation:
     def element_apply(self, U, e):
         u = self.block(U, e)
         y = self.L_apply_T(self.vol_weight(e) * self.L_apply(u, e), e)
-        Qf = self.Qf(e)
         for fi in range(6):
             if (e, fi) in self.skip_faces:
                 continue
+            Qf = self.Qf(e, fi)
             n = int(self.mesh.elem_nbr[e, fi])
             if n == -1:
                 M = self.dirichlet_forms(e, fi, Qf)
@@ -378,7 +387,7 @@ class EdgeDiscretisation:
         for e in range(self.E):
             if int(self.mesh.elem_nbr[e, 0]) != -2 - c:
                 continue
-            Qf = self.Qf(e)
+            Qf = self.Qf(e, 0)
             fe = self.face_fields(self.block(U, e), e, 0, Qf)
             fn = self.corner_fields(p, c, e, Qf)
             M = self.jump_forms(e, 0, Qf)
@@ -398,10 +407,10 @@ class EdgeDiscretisation:
         b = np.zeros(self.ndof)
         for e in range(self.E):
             y = self.L_apply_T(self.vol_weight(e) * self.f_at(e, rhs), e)
-            Qf = self.Qf(e)
             for fi in range(6):
                 if int(self.mesh.elem_nbr[e, fi]) != -1 or (e, fi) in self.skip_faces:
                     continue
+                Qf = self.Qf(e, fi)
                 M = self.dirichlet_forms(e, fi, Qf)
                 dd = self.dirichlet_data(e, fi, Qf, rhs)
                 gs = [(M[k] @ dd[k].ravel()).reshape(Qf, Qf) for k in range(3)]

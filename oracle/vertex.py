@@ -130,9 +130,9 @@ class VertexDiscretisation(EdgeDiscretisation):
             R += float(np.sum(z * z))
         for e in range(self.E):
             u = self.block(U, e)
-            Qf = self.Qf(e)
             hh = self.h(e) / 2.0
             for fi in range(6):
+                Qf = self.Qf(e, fi)
                 n = int(self.mesh.elem_nbr[e, fi])
                 _, _, t1, t2 = self.face_axes(fi)
                 Rf = self.G(e, fi)
@@ -162,7 +162,7 @@ class VertexDiscretisation(EdgeDiscretisation):
         for e in range(self.E):
             if int(self.mesh.elem_nbr[e, f]) != -2 - c:
                 continue
-            Qf = self.Qf(e)
+            Qf = self.Qf(e, f)
             fe = self.face_fields(self.block(U, e), e, f, Qf)
             fn = self.corner_fields(p, c, e, Qf)
             M = self.jump_forms(e, f, Qf)

@@ -193,8 +193,8 @@ class VertexEdgeDiscretisation(EdgeDiscretisation):
             R += float(np.sum(z * z))
         for e in range(self.E):
             u = self.block(U, e)
-            Qf = self.Qf(e)
             for fi in range(6):
+                Qf = self.Qf(e, fi)
                 n = int(self.mesh.elem_nbr[e, fi])
                 _, _, t1, t2 = self.face_axes(fi)
                 E = self.E_sup(e, fi)
@@ -226,7 +226,7 @@ class VertexEdgeDiscretisation(EdgeDiscretisation):
         for e in range(self.E):
             if int(self.mesh.elem_nbr[e, f]) != -2 - c:
                 continue
-            Qf = self.Qf(e)
+            Qf = self.Qf(e, f)
             fe = self.face_fields(self.block(U, e), e, f, Qf)
             fn = self.corner_fields(p, c, e, Qf)
             M = self.jump_forms(e, f, Qf)

@@ -129,3 +129,38 @@ def test_lprism_h1_error_falls():
         d = _build(W + 2, W)
         errs[W] = d.h1_error_exact(_block_pcg(d, 1e-11))
     assert errs[3] < 0.6 * errs[2], errs
+
+
+def _build_layers(layer_W, W):
+    N = len(layer_W)
+    edge, (maps, Ws, nbr, u, gu, f), pairs = wl.lprism_problem(N, W, layer_W=layer_W)
+    return LPrismDiscretisation(edge, CurvedProblem(CurvedMesh(maps, Ws, nbr), f, u, u, gu), pairs)
+
+
+def test_lprism_degrees_rising_across_layers():
+    # degrees 1, 2, 3 from the edge outward (config 3 rises 2..8 over six
+    # layers): faces between layers of unequal degree take the (2 W_f + 1)-point
+    # grid of the larger one; the corner polynomial and the regular sectors
+    # have degree 3
+    d = _build_layers((1, 2, 3), 3)
+    assert sorted(set(d.ed.W)) == [1, 2, 3]
+    rng = np.random.default_rng(37)
+    U, V = rng.standard_normal(d.ndof), rng.standard_normal(d.ndof)
+    AU, AV, b = d.apply_A(U), d.apply_A(V), d.rhs_b()
+    assert abs(V @ AU - U @ AV) <= 1e-12 * abs(V @ AU)
+    for eps in (0.7, -0.3):
+        lhs = d.functional(U + eps * V)
+        rhs = d.functional(U) + 2 * eps * V @ (AU - b) + eps ** 2 * V @ AV
+        assert lhs == pytest.approx(rhs, rel=1e-10)
+
+    def ue(rs, ts, zs):
+        r, t, z = wl._cyl_grid(rs, ts, zs)
+        return 1.0 + z + 0 * r
+
+    def ur(x, y, z):
+        return 1.0 + z + 0 * x
+
+    d.ed.problem.g = [ue]
+    d.cu.problem.g = ur
+    U = d.merge(d.ed.nodal_interpolant(ue), d.cu.nodal_interpolant(ur))
+    assert d.functional(U) <= 1e-22 * d.functional(np.zeros(d.ndof))

@@ -629,11 +629,13 @@ class EdgeMeshDesc:
         return int(self.corner_W.shape[0])
 
 
-def edge_mesh(N, W, mu=0.15, Z=1.0, theta=(0.0, PI / 2), x3=(0.0, 1.0), I=1, J=1) -> EdgeMeshDesc:
+def edge_mesh(N, W, mu=0.15, Z=1.0, theta=(0.0, PI / 2), x3=(0.0, 1.0), I=1, J=1,
+              layer_W=None) -> EdgeMeshDesc:
     """N finite layers x I theta-sectors x J x3-slabs (degree W in every
-    modified coordinate) plus J corner sets of degree W; every outer face of
-    the finite elements (r = Z, theta = theta_0 / theta_1, x3 = x3_0 / x3_1) is
-    Dirichlet.  Elements are numbered layer fastest, then sector, then slab."""
+    modified coordinate, or layer_W[i] in layer i) plus J corner sets of
+    degree W; every outer face of the finite elements (r = Z,
+    theta = theta_0 / theta_1, x3 = x3_0 / x3_1) is Dirichlet.  Elements are
+    numbered layer fastest, then sector, then slab."""
     r = [Z * mu ** (N + 1 - i) for i in range(1, N + 2)]
     taus = np.log(np.array(r))
     ths = np.linspace(theta[0], theta[1], I + 1)
@@ -658,7 +660,10 @@ def edge_mesh(N, W, mu=0.15, Z=1.0, theta=(0.0, PI / 2), x3=(0.0, 1.0), I=1, J=1
                 nbr[e, 3] = eid(i, j + 1, n) if j < I - 1 else -1
                 nbr[e, 4] = eid(i, j, n - 1) if n > 0 else -1
                 nbr[e, 5] = eid(i, j, n + 1) if n < J - 1 else -1
-    return EdgeMeshDesc(lo, hi, np.full(E, W, dtype=np.int32), nbr, np.zeros(E, dtype=np.int32),
+    Ws = np.full(E, W, dtype=np.int32)
+    if layer_W is not None:
+        Ws = np.array([int(layer_W[e % N]) for e in range(E)], dtype=np.int32)
+    return EdgeMeshDesc(lo, hi, Ws, nbr, np.zeros(E, dtype=np.int32),
                         np.full(J, W, dtype=np.int32), zs[:-1].copy(), zs[1:].copy(), np.zeros(J, dtype=np.int32))
 
 
@@ -1097,15 +1102,17 @@ def lprism_regular(W, Z=0.25, J=6):
     return maps, np.full(J, W, dtype=np.int32), nbr, u, grad, f
 
 
-def lprism_problem(N, W, Z=0.25, mu=0.15, J=6):
+def lprism_problem(N, W, Z=0.25, mu=0.15, J=6, layer_W=None):
     """The L-shaped prism with the re-entrant-edge solution
     w = r^(2/3) sin(2 theta'/3): the edge neighbourhood r < Z (N layers,
-    J sectors of pi/4 in theta' in (0, 3 pi/2), one x3 slab, degree W) and the
-    regular region (J polar-blend sectors, degree W), Dirichlet data w on the
-    outer faces.  Returns (edge problem, regular-region pieces of
-    lprism_regular, interface pairs (edge element of the outer layer, regular
-    element) sharing the circle r = Z)."""
-    mesh = edge_mesh(N, W, mu=mu, Z=Z, theta=(0.0, 1.5 * PI), x3=(0.0, 1.0), I=J, J=1)
+    J sectors of pi/4 in theta' in (0, 3 pi/2), one x3 slab, degree W or
+    layer_W[i] in layer i from the edge outward, corner polynomial of degree
+    W) and the regular region (J polar-blend sectors, degree W), Dirichlet
+    data w on the outer faces.  Config 3 takes N = 6, layer_W =
+    (2, 3, 4, 6, 7, 8), W = 8.  Returns (edge problem, regular-region pieces
+    of lprism_regular, interface pairs (edge element of the outer layer,
+    regular element) sharing the circle r = Z)."""
+    mesh = edge_mesh(N, W, mu=mu, Z=Z, theta=(0.0, 1.5 * PI), x3=(0.0, 1.0), I=J, J=1, layer_W=layer_W)
 
     def w(rs, ts, zs):
         r, t, z = _cyl_grid(rs, ts, zs)

@@ -106,6 +106,29 @@ def test_curved_variation_identity_and_spd():
         assert lhs == pytest.approx(rhs, rel=1e-10)
 
 
+def _curved_errors(Ws):
+    from oracle.pcg import pcg
+    from oracle.precond import apply_block_inverse, block_factors
+    errs, ints = {}, {}
+    for W in Ws:
+        d = _lprism(W)
+        fac = block_factors(d)
+        x, _, rel = pcg(d.apply_A, lambda r: apply_block_inverse(d, r, fac), d.rhs_b(), tol=1e-12, maxit=5000)
+        assert rel <= 1e-12
+        errs[W] = d.h1_error_exact(x)
+        ints[W] = d.h1_error_exact(d.nodal_interpolant(d.problem.u_exact))
+    return errs, ints
+
+
+def test_curved_h1_error_decays_w2_w3():
+    # measured: 13.0 %, 2.07 % at W = 2, 3 against the interpolant's 3.4 %, 0.65 %
+    errs, ints = _curved_errors((2, 3))
+    assert errs[3] < 0.5 * errs[2], errs
+    for W in (2, 3):
+        assert errs[W] < 5 * ints[W], (errs, ints)
+
+
+@pytest.mark.slow
 def test_curved_h1_error_decays():
     # measured: 13.0 %, 2.07 %, 0.31 % at W = 2, 3, 4 against the interpolant's
     # 3.4 %, 0.65 %, 0.14 % (block-Jacobi PCG to 1e-12)

@@ -216,6 +216,7 @@ def _ls_h1(W, N):
     return np.sqrt(err / nrm), np.sqrt(ei / nrm)
 
 
+@pytest.mark.slow
 def test_ve_h1_error_decays_with_w():
     # one sector of opening 3 pi/2: the theta approximation of sin(2 theta / 3)
     # dominates at low W (measured: 12.8 % at W = 2, N = 3; 0.32 % at W = 4, N = 6)

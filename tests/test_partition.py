@@ -105,7 +105,7 @@ def _rank(rank, ws, port, out):
         import scipy.linalg as sla
         from oracle.functional import Discretisation
         from oracle.precond import element_block
-        pb = wl.poisson_sine(n=(4, 2, 2), W=2)
+        pb = wl.poisson_sine(n=(4, 1, 1), W=2)
         owner = pt.partition(pb.mesh, ws)
         part = pt.local_part(pb.mesh, owner, rank)
         d = Discretisation(pt.local_problem(pb, part))
@@ -177,7 +177,7 @@ def test_two_rank_ghost_exchange_apply_and_pcg():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    pb = wl.poisson_sine(n=(4, 2, 2), W=2)
+    pb = wl.poisson_sine(n=(4, 1, 1), W=2)
     full = Discretisation(pb)
     U = wl.random_dofs(full.ndof, seed=21)
     y = full.apply_A(U)

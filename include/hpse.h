@@ -193,7 +193,13 @@ typedef struct {
 /* Build the mesh on `device`: validates the description (matching faces,
  * degrees), builds the GLL / Lagrange / face-norm / preconditioner tables in
  * FP64 on the host, uploads geometry and tables.  Section 2.3 (mesh),
- * Section 5.3 (tables), eq. (5.15)-(5.17) (preconditioner eigenbases). */
+ * Section 5.3 (tables), eq. (5.15)-(5.17) (preconditioner eigenbases).
+ * desc and its arrays are read during the call only.  On success *out is a
+ * handle owned by the caller until hpse_destroy; on failure *out is NULL and
+ * the status says why: HPSE_ERR_INVALID_ARG (pointers, counts, enums, corner
+ * codes), HPSE_ERR_NONMATCHING_FACE, HPSE_ERR_DEGREE (W outside [1, 10] or
+ * unequal across a face), HPSE_ERR_OOM, HPSE_ERR_CUDA.  Validation runs
+ * before any device call.  Synchronous. */
 hpse_status hpse_setup_mesh(const hpse_mesh_desc *desc, int device, hpse_mesh **out);
 
 /* Sizes: DOFs per right-hand side; volume points; Dirichlet face points. */
@@ -212,17 +218,27 @@ int32_t hpse_nrhs(const hpse_mesh *m);
 hpse_status hpse_query_points(const hpse_mesh *m, double *vol_axes, double *face_norm);
 int64_t hpse_n_boundary_faces(const hpse_mesh *m);
 
-/* Upload data and build b = S^T M d in FP64 on the device (Section 5.3:
- * "G is assembled from the data").  Synchronous. */
+/* Upload data and build b = S^T M d in FP64 on the device (Section 5.3: the
+ * right-hand side of the normal equations from the sampled data).  data and
+ * its arrays are copied during the call.  HPSE_ERR_INVALID_ARG for missing
+ * arrays or a non-positive coefficient a (ellipticity).  Drops captured
+ * solver graphs (they refer to the previous data).  Synchronous. */
 hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data);
 
 /* y = A u, the normal operator of eq. (4.2) (Section 5.3), for all n_rhs
- * right-hand sides.  u, y: device DOF vectors of n_rhs*ndof scalars of the
- * given precision; u and y must not overlap. */
+ * right-hand sides.  u, y: caller-owned device DOF vectors of n_rhs*ndof
+ * scalars of the given precision (HPSE_FP64 or HPSE_FP32); u and y must not
+ * overlap.  Asynchronous on `stream` (NULL: the legacy default stream).
+ * HPSE_ERR_INVALID_ARG (pointers, prec, u == y), HPSE_ERR_NO_DATA before
+ * hpse_set_data, HPSE_ERR_CUDA. */
 hpse_status hpse_apply_operator(hpse_mesh *m, int32_t prec, const void *u, void *y, void *stream);
 
-/* z = C^{-1} r, the element-block separable preconditioner (eq. 5.19-5.20),
- * for all right-hand sides; r, z device DOF vectors (may not overlap). */
+/* z = C^{-1} r for all right-hand sides with the selected preconditioner:
+ * the separable C-form of eq. (5.19)-(5.20) (C* of eq. 5.30 on edge
+ * elements; the exact block on corner sets), or the element blocks after
+ * hpse_setup_block_preconditioner / hpse_select_preconditioner.  r, z:
+ * caller-owned device DOF vectors (must not overlap).  Asynchronous on
+ * `stream`; errors as hpse_apply_operator. */
 hpse_status hpse_apply_preconditioner(hpse_mesh *m, int32_t prec, const void *r, void *z, void *stream);
 
 /* Element-block preconditioner (no counterpart in the thesis, which uses the
@@ -373,8 +389,10 @@ hpse_status hpse_unpack_blocks(const hpse_mesh *m, int32_t prec, const int32_t *
                                int32_t n, int64_t buf_len, const void *buf, void *vec, void *stream);
 
 /* Kernel launch parameters: threads per CTA for degree W, precision prec,
- * kernel kind (0 = operator apply, 1 = preconditioner); set by the autotuner,
- * 0 restores the default. */
+ * kernel kind (0 = operator apply, 1 = preconditioner); 0 restores the
+ * default.  The operator and separable-preconditioner kernels of this build
+ * fix their CTA shapes at compile time, so the setting is recorded and
+ * reported but does not change those launches. */
 hpse_status hpse_set_block_threads(hpse_mesh *m, int32_t kind, int32_t prec, int32_t W, int32_t threads);
 int32_t hpse_get_block_threads(const hpse_mesh *m, int32_t kind, int32_t prec, int32_t W);
 

@@ -298,6 +298,45 @@ class EdgeDiscretisation:
         s = self.scale(e)
         return [gv, s[t1] * (gv @ D.T), s[t2] * (D @ gv)]
 
+    # --- Neumann faces (the last sum of eq. 2.38 / eq. 4.7) ----------------
+    # L^e u = -div(A^e grad u) with A^e = diag(1, 1, e^{2 tau}) for the
+    # Laplacian, so the conormal derivative along the outward normal is
+    # +-u_tau, +-u_theta or +-e^{2 tau} u_x3; a physical flux q (q_r,
+    # q_theta = u_theta / r, q_x3) gives h^e = +-r q_r, +-r q_theta, +-r^2 q_x3.
+    def is_neumann(self, e, fi):
+        bc = getattr(self.mesh, "elem_bc", None)
+        return bc is not None and int(self.mesh.elem_nbr[e, fi]) == -1 and int(bc[e, fi]) == 1
+
+    def _conormal_factor(self, e, fi, Qf):
+        """+-1 or +-e^{2 tau} on the face grid [t2, t1] (outward normal)."""
+        axis, side, _, _ = self.face_axes(fi)
+        sgn = 1.0 if side else -1.0
+        if axis != 2:
+            return sgn
+        taus = self.face_points(e, fi, Qf)[0]
+        return sgn * np.broadcast_to(np.exp(2.0 * taus)[None, :], (Qf, Qf))
+
+    def neumann_sample(self, u, e, fi, Qf):
+        axis = fi // 2
+        o = [0, 0, 0]
+        o[axis] = 1
+        return self._conormal_factor(e, fi, Qf) * self.scale(e)[axis] * self.face_eval(u, e, fi, Qf, tuple(o))
+
+    def neumann_sample_T(self, g, e, fi, Qf):
+        axis = fi // 2
+        o = [0, 0, 0]
+        o[axis] = 1
+        return self.face_eval_T(self._conormal_factor(e, fi, Qf) * self.scale(e)[axis] * g, e, fi, Qf, tuple(o))
+
+    def neumann_data(self, e, fi, Qf, rhs):
+        axis, side, _, _ = self.face_axes(fi)
+        taus, ths, zs = self.face_points(e, fi, Qf)
+        rs = np.exp(taus)
+        q = self.problem.flux[rhs](rs, ths, zs)[axis]
+        q = np.broadcast_to(q, (len(zs), len(ths), len(rs))).reshape(Qf, Qf)
+        r = np.broadcast_to(np.exp(taus)[None, None, :], (len(zs), len(ths), len(rs))).reshape(Qf, Qf)
+        return (1.0 if side else -1.0) * (r * r if axis == 2 else r) * q
+
     def Qf(self, e, fi=None):
         """(2 W_f + 1)-point face grid, W_f the larger degree of the two sides
         of face fi (the element's own degree without fi)."""
@@ -331,6 +370,10 @@ class EdgeDiscretisation:
                 axis, _, t1, t2 = self.face_axes(fi)
                 G = self.G(e, fi)
                 c = self.norm_weights(e, fi)
+                if n == -1 and self.is_neumann(e, fi):
+                    v = self.neumann_sample(u, e, fi, Qf) - self.neumann_data(e, fi, Qf, rhs)
+                    R += self._norm_literal(v, Qf, c)
+                    continue
                 if n == -1:
                     sm = self.dirichlet_samples(u, e, fi, Qf)
                     dd = self.dirichlet_data(e, fi, Qf, rhs)
@@ -362,6 +405,11 @@ class EdgeDiscretisation:
                 continue
             Qf = self.Qf(e, fi)
             n = int(self.mesh.elem_nbr[e, fi])
+            if n == -1 and self.is_neumann(e, fi):
+                Mk = face_form(Qf, *self.norm_weights(e, fi))
+                v = self.neumann_sample(u, e, fi, Qf)
+                y = y + self.neumann_sample_T((Mk @ v.ravel()).reshape(Qf, Qf), e, fi, Qf)
+                continue
             if n == -1:
                 M = self.dirichlet_forms(e, fi, Qf)
                 sm = self.dirichlet_samples(u, e, fi, Qf)
@@ -411,6 +459,11 @@ class EdgeDiscretisation:
                 if int(self.mesh.elem_nbr[e, fi]) != -1 or (e, fi) in self.skip_faces:
                     continue
                 Qf = self.Qf(e, fi)
+                if self.is_neumann(e, fi):
+                    Mk = face_form(Qf, *self.norm_weights(e, fi))
+                    hd = self.neumann_data(e, fi, Qf, rhs)
+                    y = y + self.neumann_sample_T((Mk @ hd.ravel()).reshape(Qf, Qf), e, fi, Qf)
+                    continue
                 M = self.dirichlet_forms(e, fi, Qf)
                 dd = self.dirichlet_data(e, fi, Qf, rhs)
                 gs = [(M[k] @ dd[k].ravel()).reshape(Qf, Qf) for k in range(3)]

@@ -681,6 +681,9 @@ class EdgeProblem:
     grad_exact: Optional[Callable] = None  # (u_r, u_theta / r, u_x3) on tensor grids
     name: str = ""
     meta: dict = field(default_factory=dict)
+    # Neumann data (edge meshes with elem_bc): per right-hand side the
+    # physical gradient field (q_r, q_theta = u_theta / r, q_x3) on tensor grids
+    flux: Optional[List[Callable]] = None
 
 
 def _cyl_grid(rs, ts, zs):
@@ -1130,3 +1133,30 @@ def lprism_problem(N, W, Z=0.25, mu=0.15, J=6, layer_W=None):
     regular = lprism_regular(W, Z=Z, J=J)
     pairs = [(j * N + N - 1, j) for j in range(J)]
     return edge, regular, pairs
+
+
+def edge_crack(N, W, mu=0.15, I=4):
+    """Table 6.19's crack problem: Lap u = 0 in the unit cylinder slit along
+    theta = 0 (0 < theta < 2 pi, 0 < x3 < 1), u = 0 on both crack faces,
+    du/dnu = h on r = 1 and on x3 = 0, 1 (Neumann faces, elem_bc = 1), exact
+    w = r^(1/2) sin(theta / 2)."""
+    mesh = edge_mesh(N, W, mu=mu, Z=1.0, theta=(0.0, 2 * PI), x3=(0.0, 1.0), I=I, J=1)
+    bc = np.zeros((mesh.n_elem, 6), dtype=np.int32)
+    for e in range(mesh.n_elem):
+        for fi in (1, 4, 5):
+            if mesh.elem_nbr[e, fi] == -1:
+                bc[e, fi] = 1
+    mesh.elem_bc = bc
+
+    def w(rs, ts, zs):
+        r, t, z = _cyl_grid(rs, ts, zs)
+        return np.sqrt(r) * np.sin(t / 2) + 0 * z
+
+    def grad(rs, ts, zs):
+        r, t, z = _cyl_grid(rs, ts, zs)
+        return 0.5 / np.sqrt(r) * np.sin(t / 2) + 0 * z, 0.5 / np.sqrt(r) * np.cos(t / 2) + 0 * z, 0 * r * t * z
+
+    def zero(rs, ts, zs):
+        return np.zeros((len(zs), len(ts), len(rs)))
+
+    return EdgeProblem(mesh, [zero], [w], w, grad, name="edge_crack", flux=[grad])

@@ -86,17 +86,19 @@ def _h1_rel(W):
 
 
 def test_h1_error_matches_table_6_18_order():
-    # Table 6.18, relative H1 error (%) at W = 2: 0.464542
+    from golden_tables import rel_error
+    ref = rel_error("table6_18_edge.txt", 2)     # 0.464542 %
     e2 = _h1_rel(2)
-    assert 0.464542e-2 / 5 < e2 < 0.464542e-2 * 5, e2
+    assert ref / 5 < e2 < ref * 5, e2
 
 
 @pytest.mark.slow
 def test_h1_error_decays_exponentially_in_W():
-    # Table 6.18: W = 2 0.464542 %, W = 3 0.131359 %
+    from golden_tables import rel_error
+    ref = rel_error("table6_18_edge.txt", 3)     # 0.131359 %
     e2, e3 = _h1_rel(2), _h1_rel(3)
     assert e3 < 0.3 * e2
-    assert 0.131359e-2 / 5 < e3 < 0.131359e-2 * 5, e3
+    assert ref / 5 < e3 < ref * 5, e3
 
 
 def test_h1_diff_quadrature_against_gauss():

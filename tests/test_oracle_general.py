@@ -145,21 +145,25 @@ def _table_error(pb):
     return h1_error_exact(d, x)
 
 
-@pytest.mark.parametrize("name,make,W,ref", [
-    ("6.7", wl.helmholtz_mixed, 2, 0.696654e-1),     # measured 5.25 %
-    ("6.12", wl.varcoef_robin, 2, 0.284009),         # measured 26.1 % (Mesh 3)
-    ("6.14", wl.nonsym_mixed, 2, 0.485737),          # measured 56.0 % (Mesh 2)
+@pytest.mark.parametrize("name,make,W,col", [
+    ("table6_7_helmholtz.txt", wl.helmholtz_mixed, 2, -1),       # measured 5.25 %
+    ("table6_12_varcoef_robin.txt", wl.varcoef_robin, 2, -1),    # measured 26.1 % (Mesh 3)
+    ("table6_14_nonsym.txt", wl.nonsym_mixed, 2, 2),             # measured 56.0 % (Mesh 2)
 ])
-def test_tables_low_degree(name, make, W, ref):
+def test_tables_low_degree(name, make, W, col):
+    from golden_tables import rel_error
+    ref = rel_error(name, W, col)
     err = _table_error(make(W=W))
     assert ref / 5 < err < ref * 5, (name, err, ref)
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("name,make,W,ref", [
-    ("6.7", wl.helmholtz_mixed, 4, 0.114335e-2),     # measured 0.0279 %
-    ("6.14", wl.nonsym_mixed, 4, 0.517751e-1),       # measured 3.09 %
+@pytest.mark.parametrize("name,make,W,col", [
+    ("table6_7_helmholtz.txt", wl.helmholtz_mixed, 4, -1),       # measured 0.0279 %
+    ("table6_14_nonsym.txt", wl.nonsym_mixed, 4, 2),             # measured 3.09 %
 ])
-def test_tables_degree_4(name, make, W, ref):
+def test_tables_degree_4(name, make, W, col):
+    from golden_tables import rel_error
+    ref = rel_error(name, W, col)
     err = _table_error(make(W=W))
     assert ref / 5 < err < ref * 5, (name, err, ref)

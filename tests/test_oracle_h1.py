@@ -80,12 +80,16 @@ def test_table_6_1_w2_w4():
     # 2x2x2 elements): 38.0 at W = 2, 2.05 at W = 4; measured 23.6 and 0.430 --
     # the oracle's error falls faster with W than the table's (0.62, 0.21, 0.15
     # of it at W = 2, 4, 6), so the window is (1/10, 5) of the table
-    for W, ref in ((2, 0.380275), (4, 0.204875e-1)):
+    from golden_tables import rel_error
+    for W in (2, 4):
+        ref = rel_error("table6_1_laplace.txt", W)
         err = _table_6_1_error(W)
         assert ref / 10 < err < ref * 5, (W, err, ref)
 
 
 @pytest.mark.slow
 def test_table_6_1_w6():
-    err = _table_6_1_error(6)   # Table 6.1: 0.269917E-01 %, measured 4.06E-03 %
-    assert 0.269917e-3 / 10 < err < 0.269917e-3 * 5, err
+    from golden_tables import rel_error
+    ref = rel_error("table6_1_laplace.txt", 6)   # 0.0270 %, measured 4.06E-03 %
+    err = _table_6_1_error(6)
+    assert ref / 10 < err < ref * 5, err

@@ -122,7 +122,9 @@ def _table_6_3_error(W):
 
 def test_table_6_3_w2_w4():
     # relative H^1 error (%) of Table 6.3: W = 2 10.3976, W = 4 0.540972
-    for W, ref in ((2, 0.103976), (4, 0.540972e-2)):
+    from golden_tables import rel_error
+    for W in (2, 4):
+        ref = rel_error("table6_3_poisson_mixed.txt", W)
         err = _table_6_3_error(W)
         assert ref / 5 < err < ref * 5, (W, err, ref)
 
@@ -132,5 +134,7 @@ def test_table_6_3_w6():
     # Table 6.3: 0.614615E-02 %; measured 8.76E-04 %: the oracle's error falls
     # faster with W than the table's (1.07, 0.32, 0.14 of it at W = 2, 4, 6),
     # so the window is (1/10, 5) of the table here
+    from golden_tables import rel_error
+    ref = rel_error("table6_3_poisson_mixed.txt", 6)
     err = _table_6_3_error(6)
-    assert 0.614615e-4 / 10 < err < 0.614615e-4 * 5, err
+    assert ref / 10 < err < ref * 5, err

@@ -82,12 +82,16 @@ def _h1_rel(W):
 
 
 def test_vertex_h1_error_matches_table_6_16_order():
-    e2 = _h1_rel(2)  # Table 6.16: 1.00821 %
-    assert 1.00821e-2 / 5 < e2 < 1.00821e-2 * 5, e2
+    from golden_tables import rel_error
+    ref = rel_error("table6_16_vertex.txt", 2)   # 1.00821 %
+    e2 = _h1_rel(2)
+    assert ref / 5 < e2 < ref * 5, e2
 
 
 @pytest.mark.slow
 def test_vertex_h1_error_decays():
-    e2, e3 = _h1_rel(2), _h1_rel(3)  # Table 6.16: 1.00821 %, 0.0841462 %
+    from golden_tables import rel_error
+    ref = rel_error("table6_16_vertex.txt", 3)   # 0.0841462 %
+    e2, e3 = _h1_rel(2), _h1_rel(3)
     assert e3 < 0.2 * e2
-    assert 0.841462e-3 / 5 < e3 < 0.841462e-3 * 5, e3
+    assert ref / 5 < e3 < ref * 5, e3

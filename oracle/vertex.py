@@ -120,6 +120,34 @@ class VertexDiscretisation(EdgeDiscretisation):
         s = self.scale(e)
         return [gv, s[t1] * (gv @ D.T), s[t2] * (D @ gv)]
 
+    # --- Neumann faces (the last sum of eq. 4.3) ---------------------------
+    # L^v u = -div(e^{chi/2} sqrt(sin phi) A^v grad u) + lower-order terms with
+    # A^v = diag(1, 1/sin^2 phi, 1) for the Laplacian (the principal part of
+    # L^v), so the conormal derivative of eq. 2.24 along the outward normal is
+    # +-u_phi, +-u_theta / sin^2 phi or +-u_chi; a physical gradient field
+    # q = (q_rho, q_phi, q_theta) gives h^v = +-rho q_phi, +-rho q_theta / sin phi
+    # (the thesis's e^chi / sin phi factor of its theta = const faces) or
+    # +-rho q_rho.
+    def _conormal_factor(self, e, fi, Qf):
+        axis, side, _, _ = self.face_axes(fi)
+        sgn = 1.0 if side else -1.0
+        if axis != 1:
+            return sgn
+        phis = self.face_points(e, fi, Qf)[0]
+        return sgn * np.broadcast_to((1.0 / np.sin(phis) ** 2)[None, :], (Qf, Qf))
+
+    def neumann_data(self, e, fi, Qf, rhs):
+        axis, side, _, _ = self.face_axes(fi)
+        phis, ths, chis = self.face_points(e, fi, Qf)
+        rhos = np.exp(chis)
+        shape = (len(chis), len(ths), len(phis))
+        qr, qp, qt = self.problem.flux[rhs](phis, ths, rhos)
+        rho = np.broadcast_to(rhos[:, None, None], shape)
+        sp = np.broadcast_to(np.sin(phis)[None, None, :], shape)
+        q = {0: rho * np.broadcast_to(qp, shape), 1: rho * np.broadcast_to(qt, shape) / sp,
+             2: rho * np.broadcast_to(qr, shape)}[axis]
+        return (1.0 if side else -1.0) * q.reshape(Qf, Qf)
+
     # --- the functional (literal norm sums, eq. 4.3) -----------------------
     def functional(self, U, rhs=0):
         from .edge import l2_literal
@@ -137,6 +165,10 @@ class VertexDiscretisation(EdgeDiscretisation):
                 _, _, t1, t2 = self.face_axes(fi)
                 Rf = self.G(e, fi)
                 c = self.norm_weights(e, fi)
+                if n == -1 and self.is_neumann(e, fi):
+                    v = self.neumann_sample(u, e, fi, Qf) - self.neumann_data(e, fi, Qf, rhs)
+                    R += self._norm_literal(v, Qf, c)
+                    continue
                 if n == -1:
                     sm = self.dirichlet_samples(u, e, fi, Qf)
                     dd = self.dirichlet_data(e, fi, Qf, rhs)

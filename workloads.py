@@ -1160,3 +1160,37 @@ def edge_crack(N, W, mu=0.15, I=4):
         return np.zeros((len(zs), len(ts), len(rs)))
 
     return EdgeProblem(mesh, [zero], [w], w, grad, name="edge_crack", flux=[grad])
+
+
+def vertex_mixed(N, W, mu=0.15):
+    """Table 6.17: -Lap u = f on the spherical wedge of Table 6.16 with
+    Dirichlet faces phi = pi/6, pi/3 and theta = 0, 3 pi/2 and the Neumann face
+    rho = 1 (elem_bc = 1), exact w = rho^0.1 (1 - rho) sin(2 phi).  The
+    gradient (w_rho, w_phi / rho, w_theta / (rho sin phi)) is also the Neumann
+    data field."""
+    mesh = vertex_mesh(N, W, mu=mu)
+    bc = np.zeros((mesh.n_elem, 6), dtype=np.int32)
+    for e in range(mesh.n_elem):
+        if mesh.elem_nbr[e, 5] == -1:
+            bc[e, 5] = 1
+    mesh.elem_bc = bc
+
+    def g_(r):
+        return r ** 0.1 - r ** 1.1
+
+    def w(ps, ts, rs):
+        p, t, r = _sph_grid(ps, ts, rs)
+        return g_(r) * np.sin(2 * p) + 0 * t
+
+    def grad(ps, ts, rs):
+        p, t, r = _sph_grid(ps, ts, rs)
+        gp = 0.1 * r ** -0.9 - 1.1 * r ** 0.1
+        return gp * np.sin(2 * p) + 0 * t, g_(r) / r * 2 * np.cos(2 * p) + 0 * t, 0 * p * t * r
+
+    def f(ps, ts, rs):
+        p, t, r = _sph_grid(ps, ts, rs)
+        radial = 0.11 * r ** -1.9 - 2.31 * r ** -0.9
+        ang = 2 * np.cos(p) / np.sin(p) * np.cos(2 * p) - 4 * np.sin(2 * p)
+        return -(radial * np.sin(2 * p) + g_(r) / (r * r) * ang) + 0 * t
+
+    return EdgeProblem(mesh, [f], [w], w, grad, name="vertex_mixed", flux=[grad])

@@ -225,3 +225,53 @@ def test_ve_h1_error_decays_with_w():
     assert e4 < 0.1 * e2, (e2, e4)
     # the least-squares solution is as good as interpolation up to a modest factor
     assert e2 < 2 * i2 and e4 < 2 * i4, (e2, i2, e4, i4)
+
+
+def _table_6_20_error(W, N, J):
+    """Block-Jacobi PCG solution of Table 6.20's problem (the cone truncated by
+    the plane x3 = cos(pi/6) inscribed in the table's unit sphere), relative
+    H^1 error against w."""
+    import scipy.linalg as sla
+    from oracle.pcg import pcg
+    from oracle.precond import element_block
+    d = VertexEdgeDiscretisation(wl.vertex_edge_table_6_20(N, W, J=J))
+    fac = [sla.cho_factor(element_block(d, e)) for e in range(d.E)]
+    cinv = []
+    for c in range(d.C):
+        n = d.Wc[c] + 1
+        A = np.zeros((n, n))
+        for k in range(n):
+            U = np.zeros(d.ndof)
+            U[d.coff[c] + k] = 1.0
+            A[:, k] = d.corner_apply(U, c)
+        cinv.append(np.linalg.inv(A))
+
+    def M(r):
+        z = np.zeros_like(r)
+        for e in range(d.E):
+            z[d.off[e]:d.off[e + 1]] = sla.cho_solve(fac[e], r[d.off[e]:d.off[e + 1]])
+        for c in range(d.C):
+            sl = slice(d.coff[c], d.coff[c] + d.Wc[c] + 1)
+            z[sl] = cinv[c] @ r[sl]
+        return z
+    x, _, rel = pcg(d.apply_A, M, d.rhs_b(), tol=1e-10, maxit=5000)
+    assert rel <= 1e-10
+    err, nrm = d.h1_error_exact(x)
+    return np.sqrt(err / nrm)
+
+
+def test_table_6_20_w2():
+    # one theta sector, N = 3: measured 13.0 % against the table's 4.73 %
+    from golden_tables import rel_error
+    ref = rel_error("table6_20_vertex_edge.txt", 2)
+    err = _table_6_20_error(2, 3, 1)
+    assert ref / 5 < err < ref * 5, err
+
+
+@pytest.mark.slow
+def test_table_6_20_w3():
+    # three theta sectors, N = 4: measured 3.00 % against 1.06 % (W = 2: 10.2 %)
+    from golden_tables import rel_error
+    ref = rel_error("table6_20_vertex_edge.txt", 3)
+    err = _table_6_20_error(3, 4, 3)
+    assert ref / 5 < err < ref * 5, err

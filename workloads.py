@@ -1194,3 +1194,39 @@ def vertex_mixed(N, W, mu=0.15):
         return -(radial * np.sin(2 * p) + g_(r) / (r * r) * ang) + 0 * t
 
     return EdgeProblem(mesh, [f], [w], w, grad, name="vertex_mixed", flux=[grad])
+
+
+def vertex_edge_table_6_20(N, W, mu=0.15, J=3):
+    """Table 6.20's solution w = rho^(3/4) (sin phi)^(1/2) sin(theta / 2)
+    (vertex, edge and vertex-edge singularities) with f = -Lap w
+    = -(9/16) rho^(-5/4) (sin phi)^(1/2) sin(theta / 2), on the vertex-edge
+    neighbourhood phi < pi/6, 0 < theta < 3 pi/2, x3 < cos(pi/6) (the cone of
+    Table 6.20 truncated by the plane inscribed in its unit sphere: the
+    elements here are boxes in (ln tan phi, theta, ln x3)).  Data in modified
+    coordinates; gradient (w_r, w_theta / r, w_x3)."""
+    mesh = vertex_edge_mesh(N, W, mu=mu, phi_v=PI / 6, delta=np.cos(PI / 6), J=J)
+
+    def parts(ps, ts, zs):
+        p, t, z = _ve_grid(ps, ts, zs)
+        r, x3 = np.exp(p + z), np.exp(z)
+        rho = np.hypot(r, x3)
+        return r, t, x3, rho, r / rho
+
+    def w(ps, ts, zs):
+        r, t, x3, rho, sphi = parts(ps, ts, zs)
+        return rho ** 0.75 * np.sqrt(sphi) * np.sin(t / 2)
+
+    def f(ps, ts, zs):
+        r, t, x3, rho, sphi = parts(ps, ts, zs)
+        return -9.0 / 16.0 * rho ** -1.25 * np.sqrt(sphi) * np.sin(t / 2)
+
+    def grad(ps, ts, zs):
+        # w = r^(1/2) rho^(1/4) sin(theta / 2) in cylindrical coordinates
+        r, t, x3, rho, sphi = parts(ps, ts, zs)
+        s2, c2 = np.sin(t / 2), np.cos(t / 2)
+        w_r = (0.5 * r ** -0.5 * rho ** 0.25 + r ** 0.5 * 0.25 * rho ** -0.75 * r / rho) * s2
+        w_t = r ** 0.5 * rho ** 0.25 * 0.5 * c2 / r
+        w_z = r ** 0.5 * 0.25 * rho ** -0.75 * x3 / rho * s2
+        return w_r, w_t, w_z
+
+    return EdgeProblem(mesh, [f], [w], w, grad, name="vertex_edge_table_6_20")

@@ -32,6 +32,9 @@ parallel computers, 2010):
 * ``lprism``     -- the L-shaped prism: the edge neighbourhood next to curved
                     regular elements, joined by the interface terms of the
                     singular side.
+* ``vertex_region`` -- a vertex neighbourhood with one re-entrant edge: the
+                    vertex part and the vertex-edge cone joined on their cone,
+                    one shared corner constant.
 * ``adjoint``    -- gradients of a solution functional by an adjoint solve.
 
 Every function is written for clarity, not speed.  Where the thesis is silent

@@ -160,6 +160,8 @@ class VertexDiscretisation(EdgeDiscretisation):
             u = self.block(U, e)
             hh = self.h(e) / 2.0
             for fi in range(6):
+                if (e, fi) in self.skip_faces:
+                    continue
                 Qf = self.Qf(e, fi)
                 n = int(self.mesh.elem_nbr[e, fi])
                 _, _, t1, t2 = self.face_axes(fi)

@@ -194,6 +194,8 @@ class VertexEdgeDiscretisation(EdgeDiscretisation):
         for e in range(self.E):
             u = self.block(U, e)
             for fi in range(6):
+                if (e, fi) in self.skip_faces:
+                    continue
                 Qf = self.Qf(e, fi)
                 n = int(self.mesh.elem_nbr[e, fi])
                 _, _, t1, t2 = self.face_axes(fi)

@@ -1230,3 +1230,37 @@ def vertex_edge_table_6_20(N, W, mu=0.15, J=3):
         return w_r, w_t, w_z
 
     return EdgeProblem(mesh, [f], [w], w, grad, name="vertex_edge_table_6_20")
+
+
+def vertex_with_edge(N, W, mu=0.15, J=3):
+    """A vertex neighbourhood with one re-entrant edge (the thesis's splitting
+    of Omega^v into the vertex-edge cone and the rest): the vertex part
+    pi/6 < phi < pi/3, rho < 1 and the vertex-edge part phi < pi/6,
+    x3 < cos(pi/6) (they meet on the circle phi = pi/6, rho = 1), both with
+    0 < theta < 3 pi/2 in J sectors and N layers of ratio mu, degree W;
+    Table 6.20's w = rho^(3/4) (sin phi)^(1/2) sin(theta / 2) as the exact
+    solution, Dirichlet data w on the outer faces.  Returns (vertex problem
+    (data in (phi, theta, rho)), vertex-edge problem (data in
+    (ln tan phi, theta, ln x3)), interface pairs (vertex-edge element of the
+    outer psi layer, vertex element) sharing the cone phi = pi/6)."""
+    vmesh = vertex_mesh(N, W, mu=mu, phi=(PI / 6, PI / 3), theta=(0.0, 1.5 * PI), I=1, J=J)
+
+    def w(ps, ts, rs):
+        p, t, r = _sph_grid(ps, ts, rs)
+        return r ** 0.75 * np.sqrt(np.sin(p)) * np.sin(t / 2)
+
+    def grad(ps, ts, rs):
+        # (w_rho, w_phi / rho, w_theta / (rho sin phi))
+        p, t, r = _sph_grid(ps, ts, rs)
+        s = np.sin(p)
+        return (0.75 * r ** -0.25 * np.sqrt(s) * np.sin(t / 2), r ** -0.25 * 0.5 / np.sqrt(s) * np.cos(p) * np.sin(t / 2),
+                r ** -0.25 / np.sqrt(s) * 0.5 * np.cos(t / 2))
+
+    def f(ps, ts, rs):
+        p, t, r = _sph_grid(ps, ts, rs)
+        return -9.0 / 16.0 * r ** -1.25 * np.sqrt(np.sin(p)) * np.sin(t / 2)
+
+    vertex = EdgeProblem(vmesh, [f], [w], w, grad, name="vertex_with_edge")
+    ve = vertex_edge_table_6_20(N, W, mu=mu, J=J)
+    pairs = [((j * N + k) * N + (N - 1), j * N + k) for j in range(J) for k in range(N)]
+    return vertex, ve, pairs

@@ -35,6 +35,8 @@ parallel computers, 2010):
 * ``vertex_region`` -- a vertex neighbourhood with one re-entrant edge: the
                     vertex part and the vertex-edge cone joined on their cone,
                     one shared corner constant.
+* ``ve_edge_region`` -- the vertex-edge cone and the edge neighbourhood above
+                    it, joined on the plane x3 = delta.
 * ``adjoint``    -- gradients of a solution functional by an adjoint solve.
 
 Every function is written for clarity, not speed.  Where the thesis is silent

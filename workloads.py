@@ -1264,3 +1264,41 @@ def vertex_with_edge(N, W, mu=0.15, J=3):
     ve = vertex_edge_table_6_20(N, W, mu=mu, J=J)
     pairs = [((j * N + k) * N + (N - 1), j * N + k) for j in range(J) for k in range(N)]
     return vertex, ve, pairs
+
+
+def vertex_edge_with_edge(N, W, mu=0.15, J=3, phi_v=PI / 6, delta=None):
+    """The vertex-edge cone phi < phi_v, x3 < delta and the edge neighbourhood
+    above it, r < delta tan(phi_v), delta < x3 < 1 (the thesis's splitting
+    along an edge leaving a vertex), both 0 < theta < 3 pi/2 in J sectors,
+    N layers of ratio mu, degree W: the edge layers r_i = delta tan(phi_i)
+    continue the cone's psi layers across the plane x3 = delta.  Exact
+    solution Table 6.20's w = rho^(3/4) (sin phi)^(1/2) sin(theta / 2).
+    Returns (vertex-edge problem, edge problem (data in (r, theta, x3)),
+    interface pairs (vertex-edge element of the top zeta layer, edge element
+    of the first x3 slab))."""
+    if delta is None:
+        delta = float(np.cos(phi_v))
+    ve = vertex_edge_table_6_20(N, W, mu=mu, J=J)
+    Z = delta * np.tan(phi_v)
+    emesh = edge_mesh(N, W, mu=mu, Z=Z, theta=(0.0, 1.5 * PI), x3=(delta, 1.0), I=J, J=1)
+
+    def w(rs, ts, zs):
+        r, t, z = _cyl_grid(rs, ts, zs)
+        rho = np.hypot(r, z)
+        return np.sqrt(r) * rho ** 0.25 * np.sin(t / 2)
+
+    def grad(rs, ts, zs):
+        r, t, z = _cyl_grid(rs, ts, zs)
+        rho = np.hypot(r, z)
+        s2, c2 = np.sin(t / 2), np.cos(t / 2)
+        return ((0.5 / np.sqrt(r) * rho ** 0.25 + np.sqrt(r) * 0.25 * rho ** -0.75 * r / rho) * s2,
+                np.sqrt(r) * rho ** 0.25 * 0.5 * c2 / r, np.sqrt(r) * 0.25 * rho ** -0.75 * z / rho * s2)
+
+    def f(rs, ts, zs):
+        r, t, z = _cyl_grid(rs, ts, zs)
+        rho = np.hypot(r, z)
+        return -9.0 / 16.0 * rho ** -1.25 * np.sqrt(r / rho) * np.sin(t / 2)
+
+    edge = EdgeProblem(emesh, [f], [w], w, grad, name="edge_above_cone")
+    pairs = [((j * N + (N - 1)) * N + i, j * N + i) for j in range(J) for i in range(N)]
+    return ve, edge, pairs

@@ -37,6 +37,8 @@ parallel computers, 2010):
                     one shared corner constant.
 * ``ve_edge_region`` -- the vertex-edge cone and the edge neighbourhood above
                     it, joined on the plane x3 = delta.
+* ``vertex_shell`` -- a vertex neighbourhood inside a spherical shell of curved
+                    regular elements, joined on the sphere.
 * ``adjoint``    -- gradients of a solution functional by an adjoint solve.
 
 Every function is written for clarity, not speed.  Where the thesis is silent

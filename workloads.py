@@ -1302,3 +1302,80 @@ def vertex_edge_with_edge(N, W, mu=0.15, J=3, phi_v=PI / 6, delta=None):
     edge = EdgeProblem(emesh, [f], [w], w, grad, name="edge_above_cone")
     pairs = [((j * N + (N - 1)) * N + i, j * N + i) for j in range(J) for i in range(N)]
     return ve, edge, pairs
+
+
+def spherical_shell_map(ph0, ph1, th0, th1, r0, r1):
+    """x = rho (sin phi cos theta, sin phi sin theta, cos phi) on the box
+    (phi, theta, rho) in [ph0, ph1] x [th0, th1] x [r0, r1] (a curved regular
+    element of a spherical shell), from the reference cube."""
+    fac = (0.5 * (ph1 - ph0), 0.5 * (th1 - th0), 0.5 * (r1 - r0))
+
+    def m(l1, l2, l3):
+        l1, l2, l3 = np.broadcast_arrays(l1, l2, l3)
+        p = ph0 + (l1 + 1.0) * fac[0]
+        t = th0 + (l2 + 1.0) * fac[1]
+        r = r0 + (l3 + 1.0) * fac[2]
+        sp, cp, st, ct = np.sin(p), np.cos(p), np.sin(t), np.cos(t)
+        x = np.stack([r * sp * ct, r * sp * st, r * cp])
+        # d/dphi, d/dtheta, d/drho of each component
+        d = [[r * cp * ct, -r * sp * st, sp * ct],
+             [r * cp * st, r * sp * ct, sp * st],
+             [-r * sp, 0 * r, cp]]
+        # second derivatives [k][a][b] in (phi, theta, rho)
+        h = [[[-r * sp * ct, -r * cp * st, cp * ct], [-r * cp * st, -r * sp * ct, -sp * st], [cp * ct, -sp * st, 0 * r]],
+             [[-r * sp * st, r * cp * ct, cp * st], [r * cp * ct, -r * sp * st, sp * ct], [cp * st, sp * ct, 0 * r]],
+             [[-r * cp, 0 * r, -sp], [0 * r, 0 * r, 0 * r], [-sp, 0 * r, 0 * r]]]
+        Dx = np.stack([np.stack([d[k][a] * fac[a] for a in range(3)]) for k in range(3)])
+        D2x = np.stack([np.stack([np.stack([h[k][a][b] * fac[a] * fac[b] for b in range(3)]) for a in range(3)])
+                        for k in range(3)])
+        return x, Dx, D2x
+    return m
+
+
+def vertex_with_shell(N, W, mu=0.15, rho_v=0.5, J=3):
+    """Table 6.16's wedge pi/6 < phi < pi/3, 0 < theta < 3 pi/2, rho < 1 split
+    into the vertex neighbourhood rho < rho_v (N layers of ratio mu, J theta
+    sectors, the corner constant) and the spherical shell rho_v < rho < 1 of J
+    curved regular elements; exact w = rho^(1/2) sin(phi / 2) (Dirichlet data
+    w on the outer faces).  Returns (vertex problem, regular-region pieces
+    (maps, degrees, neighbours, w, grad w, f) with pointwise data, interface
+    pairs (vertex element of the outer layer, shell element) sharing the
+    sphere rho = rho_v)."""
+    base = vertex_poisson_singular(N, W, mu=mu)
+    rho = [rho_v * mu ** (N + 1 - i) for i in range(1, N + 2)]
+    vm = vertex_mesh(N, W, mu=mu, J=J)
+    chis = np.log(np.array(rho))
+    for e in range(vm.n_elem):
+        i = e % N
+        vm.elem_lo[e, 2], vm.elem_hi[e, 2] = chis[i], chis[i + 1]
+    vertex = EdgeProblem(vm, base.f, base.g, base.u_exact, base.grad_exact, name="vertex_with_shell")
+    ths = np.linspace(0.0, 1.5 * PI, J + 1)
+    maps = [spherical_shell_map(PI / 6, PI / 3, ths[j], ths[j + 1], rho_v, 1.0) for j in range(J)]
+    nbr = -np.ones((J, 6), dtype=np.int32)
+    for j in range(J):
+        if j > 0:
+            nbr[j, 2] = j - 1
+        if j < J - 1:
+            nbr[j, 3] = j + 1
+
+    def sph(x, y, z):
+        r = np.sqrt(x * x + y * y + z * z)
+        return r, np.arccos(np.clip(z / r, -1.0, 1.0)), np.mod(np.arctan2(y, x), 2 * PI)
+
+    def u(x, y, z):
+        r, p, t = sph(x, y, z)
+        return np.sqrt(r) * np.sin(p / 2)
+
+    def grad(x, y, z):
+        r, p, t = sph(x, y, z)
+        wr, wp = 0.5 / np.sqrt(r) * np.sin(p / 2), 0.5 / np.sqrt(r) * np.cos(p / 2)
+        er = (np.sin(p) * np.cos(t), np.sin(p) * np.sin(t), np.cos(p))
+        ep = (np.cos(p) * np.cos(t), np.cos(p) * np.sin(t), -np.sin(p))
+        return tuple(wr * er[k] + wp * ep[k] for k in range(3))
+
+    def f(x, y, z):
+        r, p, t = sph(x, y, z)
+        return -0.5 * r ** -1.5 * (np.sin(p / 2) + np.cos(p / 2) / np.tan(p))
+
+    pairs = [(j * N + (N - 1), j) for j in range(J)]
+    return vertex, (maps, np.full(J, W, dtype=np.int32), nbr, u, grad, f), pairs

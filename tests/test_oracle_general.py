@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 import workloads as wl
-from oracle.functional import Discretisation, tables
+from oracle.functional import Discretisation
 from oracle.h1 import h1_error_exact
 from oracle.pcg import pcg
 from oracle.precond import apply_block_inverse, block_factors

@@ -20,7 +20,6 @@ import pytest
 
 import workloads as wl
 from oracle.edge import face_form
-from oracle.functional import eval_tensor, tables
 from oracle.gll import gll
 from oracle.vertex_edge import VertexEdgeDiscretisation
 

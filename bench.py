@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--W", type=int, default=W_DEG)
     ap.add_argument("--cmp-rhs", type=int, default=4)
     ap.add_argument("--no-cmp", action="store_true")
+    ap.add_argument("--no-oracle-check", action="store_true",
+                    help="skip the oracle's residual check of the compared solutions")
     ap.add_argument("--delta", type=float, default=1e-1)
     ap.add_argument("--cpu-sample-elems", type=int, default=512)
     ap.add_argument("--cpu-reps", type=int, default=2)
@@ -174,22 +176,53 @@ def volume_flops_per_rhs(Ws):
     return 2.0 * tot
 
 
-# DRAM bytes (read + write) of one FP32 k_apply launch on the default
-# workload (8^3 elements, W = 8, 64 rhs, variable a), from one ncu capture
-# (dram__bytes_read.sum 180,250,624 + dram__bytes_write.sum 131,584,256;
-# profiles/k_apply_fp32_w8_varcoef.md).  Valid for that configuration and the
-# kernel as captured; reported as null for any other configuration.
-APPLY_TRAFFIC_BYTES = {(8, 8, 64): 180250624 + 131584256}
+APPLY_PROFILE = os.path.join(ROOT, "profiles", "k_apply_fp32_w8_varcoef.md")
+APPLY_SOURCES = [os.path.join(ROOT, "paper_1110_2316_gb300", "csrc", f)
+                 for f in ("kernels.cuh", "inst_template.cuh", "registry.h")]
 
 
-def fp32_peak_tflops():
-    """152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz maximum SM clock."""
-    return 152 * 128 * 2 * 2.07e9 / 1e12
+def apply_source_sha256():
+    """sha256 of the sources of the operator kernel (k_apply)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in APPLY_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
-def fp64_peak_tflops():
-    """152 SMs x 2 FP64 FMA per cycle x 2 flops x 2.07 GHz maximum SM clock."""
-    return 152 * 2 * 2 * 2.07e9 / 1e12
+def profiled_traffic(workload_key):
+    """DRAM bytes (read + write) of one FP32 k_apply launch on the default
+    workload, from the ncu capture summarised in the committed profile:
+    its lines 'traffic_bytes_per_launch[<n>,<W>,<rhs>]: N' and
+    'kernel_source_sha256: H'.  None when the profile has no figure for the
+    workload or the kernel's sources have changed since the capture."""
+    try:
+        text = open(APPLY_PROFILE).read()
+    except OSError:
+        return None, "no profile"
+    vals, sha = {}, None
+    for line in text.splitlines():
+        line = line.strip().strip("`")
+        if line.startswith("traffic_bytes_per_launch["):
+            key, v = line.split(":", 1)
+            vals[key[len("traffic_bytes_per_launch["):-1]] = int(v.strip())
+        elif line.startswith("kernel_source_sha256:"):
+            sha = line.split(":", 1)[1].strip()
+    if sha != apply_source_sha256():
+        return None, "kernel changed since the ncu capture"
+    v = vals.get("%d,%d,%d" % workload_key)
+    return v, ("ncu capture in profiles/" if v is not None else "no capture of this workload")
+
+
+def alu_peaks(device_index, sm_max_mhz):
+    """FP32 and FP64 ALU peaks (TFLOP/s) of this device: SM count from the
+    device, maximum SM clock from nvidia-smi's sample (2070 MHz if none);
+    128 FP32 and 2 FP64 FMA lanes per SM (Blackwell), 2 flops per FMA."""
+    import torch
+    sms = torch.cuda.get_device_properties(device_index).multi_processor_count
+    mhz = float(sm_max_mhz) if sm_max_mhz else 2070.0
+    return dict(fp32=sms * 128 * 2 * mhz * 1e6 / 1e12, fp64=sms * 2 * 2 * mhz * 1e6 / 1e12, sms=sms, sm_mhz=mhz)
 
 
 def cpu_baseline(pb, n_elems, reps=1):
@@ -209,6 +242,50 @@ def cpu_baseline(pb, n_elems, reps=1):
     return dict(value=ndof / dt / 1e9, unit="GDOF/s", cores=os.cpu_count(), kind="oracle",
                 sample="oracle operator apply, %d x %d of %d elements (W=%d, 1 rhs), %.1f s" %
                        (reps, len(elems), d.E, d.W[0], dt))
+
+
+def _oracle_task(task):
+    """One oracle evaluation for the solution check (runs in a spawned worker):
+    ("b", r) -> b_r = S^T M d_r; ("Ax", r, x) -> A x, both in FP64."""
+    n, W, k, seed0, kind, r, xv = task
+    from oracle.functional import Discretisation
+    d = Discretisation(wl.varcoef_random_rhs(n=n, W=W, n_rhs=k, seed0=seed0))
+    return d.rhs_b(r) if kind == "b" else d.apply_A(xv)
+
+
+def oracle_check(args, seed0, k, sols):
+    """The oracle's FP64 relative residual ||b_o - A_o x|| / ||b_o|| of GPU
+    solutions for right-hand sides 0..k-1 (``sols``: name -> [k, ndof] arrays)
+    and the oracle-norm relative H^1 difference of the mixed and FP64 solutions
+    when both are given.  The oracle's evaluations run in a spawned process
+    pool on the host cores."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    from oracle.functional import Discretisation
+    from oracle.h1 import h1_rel_diff
+    t0 = time.perf_counter()
+    tasks = [(args.n, args.W, k, seed0, "b", r, None) for r in range(k)]
+    names = sorted(sols)
+    for name in names:
+        tasks += [(args.n, args.W, k, seed0, "Ax", r, sols[name][r]) for r in range(k)]
+    workers = max(1, min(len(tasks), (os.cpu_count() or 2) - 1))
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        out = list(ex.map(_oracle_task, tasks))
+    bs = out[:k]
+    res = {}
+    for i, name in enumerate(names):
+        axs = out[k * (i + 1):k * (i + 2)]
+        res[name] = [float(np.linalg.norm(bs[r] - axs[r]) / np.linalg.norm(bs[r])) for r in range(k)]
+    h1 = None
+    if "cmp_mixed" in sols and "cmp_fp64" in sols:
+        d = Discretisation(wl.varcoef_random_rhs(n=args.n, W=args.W, n_rhs=k, seed0=seed0))
+        h1 = [h1_rel_diff(d, sols["cmp_mixed"][r], sols["cmp_fp64"][r]) for r in range(k)]
+    worst = max(max(v) for v in res.values())
+    return dict(rhs=list(range(k)), rel_residual=res, max_rel_residual=worst,
+                h1_rel_diff_mixed_vs_fp64=h1, residual_bound=1.1e-10, h1_bound=1e-8,
+                passed=bool(worst <= 1.1e-10 and (h1 is None or max(h1) <= 1e-8)),
+                workers=workers, seconds=time.perf_counter() - t0,
+                what="oracle (numpy FP64) recomputes b and A x of the GPU solutions")
 
 
 def run_reference(args):
@@ -634,6 +711,8 @@ def main():
         torch.cuda.synchronize()
     launches = api.kernel_launch_count(reset=True)
     ms = reduce_max_ms(ev0.elapsed_time(ev1) / args.steps, ws, dev)
+    k_chk = min(args.cmp_rhs, args.rhs)
+    x_timed = x.view(args.rhs, mesh.ndof)[:k_chk].cpu().numpy()
     applies = float(np.mean([r["applies"] for r in reps]))
     solve_rate = weak_scaling_rate(ws, n_tot * applies, ms)
     clocks = clk.summary()
@@ -656,7 +735,9 @@ def main():
     value = weak_scaling_rate(ws, n_tot, apply_ms_all)
     alg_flops = volume_flops_per_rhs([int(w) for w in mesh.elem_W]) * args.rhs
     achieved = alg_flops / (apply_ms * 1e-3) / 1e12
-    peak = fp32_peak_tflops()
+    peaks = alu_peaks(local, clocks.get("sm_max_mhz"))
+    peak = peaks["fp32"]
+    traffic, traffic_src = profiled_traffic((args.n, args.W, args.rhs))
     # FP64 apply for reference
     u64 = u32.double()
     y64 = torch.empty_like(u64)
@@ -726,6 +807,8 @@ def main():
             out[name] = (c0.elapsed_time(c1) / 1e3, r, xs.clone())
         h = ms2.h1_error(out["mixed"][2], ref=out["fp64"][2])
         h1 = float(np.max(np.sqrt(h[:, 0] / h[:, 1])))
+        sols = dict(timed_mixed=x_timed, cmp_mixed=out["mixed"][2].view(k, -1).cpu().numpy(),
+                    cmp_fp64=out["fp64"][2].view(k, -1).cpu().numpy())
         cmp = dict(rhs=k, tts_mixed_s=out["mixed"][0], tts_fp64_s=out["fp64"][0],
                    speedup=out["fp64"][0] / out["mixed"][0],
                    iters_mixed=out["mixed"][1]["iterations"], iters_fp64=out["fp64"][1]["iterations"],
@@ -733,6 +816,8 @@ def main():
                    rel_res_mixed=out["mixed"][1]["rel_residual"], rel_res_fp64=out["fp64"][1]["rel_residual"],
                    h1_rel_diff_mixed_vs_fp64=h1)
         ms2.close()
+        if not args.no_oracle_check:
+            cmp["oracle_check"] = oracle_check(args, shard_seed0(rank, args.rhs), k, sols)
 
     tile_report = None
     if args.precond == "block":
@@ -758,17 +843,18 @@ def main():
             tts_comparison=cmp,
             apply_ms=dict(fp32=apply_ms, fp64=apply64_ms),
             roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
-                          traffic=APPLY_TRAFFIC_BYTES.get((args.n, args.W, args.rhs)),
-                          traffic_unit="bytes per launch",
-                          algorithmic_bytes=int(2 * n_tot * 4 + 16 * mesh.nquad),
+                          traffic=traffic, traffic_unit="bytes per launch", traffic_source=traffic_src,
+                          algorithmic_bytes=int(2 * n_tot * 4),
                           kernel="k_apply<COEF_SCALAR> FP32 (W=8)",
-                          note="algorithmic volume flops (3,5,6)-field sum factorisation; peak = FP32 ALU "
-                               "152 SM x 128 lanes x 2 x 2.07 GHz"),
+                          note="algorithmic volume flops (3,5,6)-field sum factorisation per (element, rhs); "
+                               "peak = FP32 ALU %d SMs x 128 lanes x 2 flops x %.0f MHz (derived: the measured "
+                               "peaks hold HBM and bf16 tensor figures only)" % (peaks["sms"], peaks["sm_mhz"])),
             roofline_fp64=dict(bound="alu", achieved=alg_flops / (apply64_ms * 1e-3) / 1e12,
-                               peak=fp64_peak_tflops(), unit="TFLOP/s",
-                               frac=alg_flops / (apply64_ms * 1e-3) / 1e12 / fp64_peak_tflops(),
+                               peak=peaks["fp64"], unit="TFLOP/s",
+                               frac=alg_flops / (apply64_ms * 1e-3) / 1e12 / peaks["fp64"],
                                kernel="k_apply<COEF_SCALAR> FP64 (W=8), the refresh apply of the mixed solve",
-                               note="same algorithmic flops; peak = FP64 ALU 152 SM x 2 DFMA/cycle x 2 x 2.07 GHz"),
+                               note="same algorithmic flops; peak = FP64 ALU %d SMs x 2 DFMA/cycle x 2 x %.0f MHz"
+                                    % (peaks["sms"], peaks["sm_mhz"])),
             cpu_baseline=cb, e2e=e2e, gpu_launches=int(launches), clocks=clocks,
         )
         print(json.dumps(line))

@@ -347,11 +347,13 @@ hpse_status hpse_data_gradient(hpse_mesh *m, const double *ufields, const double
  * 2.1 MB that every GPU loading the library holds until process exit.
  * Limits: n_elem * n_rhs <= 131072 and n_rhs <= 4096, else HPSE_ERR_CAPACITY
  * before any device work.  The first call on a device looks up the array's
- * device address on that device (make it before any stream capture).  Every
- * call shares the one array and keeps the previous call's contents; all of it
- * is overwritten before it is read, but calls that overlap on the GPU (other
- * streams, other host threads on the same device) race and must be ordered by
- * the caller.  Synchronous on `stream`; `out` is host memory. */
+ * device address on that device.  Every call shares the one array and keeps
+ * the previous call's contents; all of it is overwritten before it is read,
+ * but calls that overlap on the GPU (other streams, other host threads on the
+ * same device) race and must be ordered by the caller.  The call is
+ * synchronous (it copies its pointer table in, waits on `stream` and copies
+ * the results to `out`, host memory): it must not be made while a stream is
+ * being captured into a CUDA graph. */
 hpse_status hpse_h1_error_noalloc(hpse_mesh *m, const double *u, const double *ref,
                                   const double *vq, const double *gq, double *out, void *stream);
 

@@ -91,6 +91,8 @@ class Mesh:
         self.coef_kind = int(coef_kind)
         self.elem_W = self._keep[0]
         self.device = device
+        # bumped by every set_data / set_rhs: autograd.Solve checks it
+        self.data_version = 0
 
     # -- sizes ------------------------------------------------------------
     @property
@@ -121,6 +123,7 @@ class Mesh:
     def set_data(self, f, a=None, grad_a=None, g=None):
         arrs = [None if v is None else np.ascontiguousarray(v, dtype=np.float64) for v in (f, a, grad_a, g)]
         d = _lib.Data(*[None if v is None else v.ctypes.data_as(C.c_void_p) for v in arrs])
+        self.data_version += 1
         check(self._lib.hpse_set_data(self._h, C.byref(d)), "hpse_set_data")
 
     # -- preconditioner choice ------------------------------------------------
@@ -193,6 +196,7 @@ class Mesh:
         check(self._lib.hpse_quad_weights(self._h, _ptr(out), _stream(stream)), "hpse_quad_weights")
 
     def set_rhs(self, b, stream=None):
+        self.data_version += 1
         check(self._lib.hpse_set_rhs(self._h, _ptr(b), _stream(stream)), "hpse_set_rhs")
 
     def data_gradient(self, ufields, lfields, out, stream=None):

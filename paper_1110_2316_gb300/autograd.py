@@ -13,7 +13,9 @@
   The adjoint right-hand side of a solution functional lies mostly in the
   low end of A's spectrum, so its attainable relative residual is about
   eps kappa(A), above that of the forward solve: ``adjoint_tol`` (default:
-  the forward ``tol``) sets it separately.
+  the forward ``tol``) sets it separately.  Backward works on the data of
+  its own forward solve: if the mesh has been given other data in between,
+  that solve's data is set again first (the mesh then keeps it).
 
 All tensors are CUDA float64 tensors; shapes: u [n_rhs * ndof], z and f
 [n_rhs, nquad], a [nquad], grad_a [3, nquad].
@@ -72,6 +74,10 @@ class Solve(torch.autograd.Function):
         if isinstance(getattr(mesh, "solve_log", None), list):
             mesh.solve_log.append(("forward", rep))
         ctx.save_for_backward(x)
+        # the data this solve used: backward restores it if the mesh has been
+        # given other data since (another solve, a finite-difference probe)
+        ctx.data = (f, a, grad_a, g)
+        ctx.data_version = mesh.data_version
         ctx.mesh, ctx.adjoint_prec = mesh, adjoint_prec
         ctx.tol = tol if adjoint_tol is None else adjoint_tol
         ctx.has_a = a is not None
@@ -81,6 +87,15 @@ class Solve(torch.autograd.Function):
     def backward(ctx, gx):
         (x,) = ctx.saved_tensors
         m = ctx.mesh
+        if m.data_version != ctx.data_version:
+            # A(a) and b(f, a) of the forward solve, not of the mesh's current data
+            f, a, grad_a, g = ctx.data
+
+            def host(t):
+                if t is None:
+                    return None
+                return t.detach().cpu().numpy() if isinstance(t, torch.Tensor) else t
+            m.set_data(f=host(f), a=host(a), grad_a=host(grad_a), g=host(g))
         b = torch.empty_like(x)
         m.get_rhs(b)
         m.set_rhs(gx.contiguous())

@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <limits>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -495,6 +496,11 @@ __global__ void k_fin_reliable(FinArgs F, Scalars S, const double *part_rz, cons
   const double rr = fin_sum(F, part_rr, p, r);
   if (threadIdx.x == 0) {
     if (rel[pr] > tol && isfinite(rz) && rz > 0.0) {
+      // the recursive residual claimed convergence and the true one refuted
+      // it: the next claim must reach half of the level (the 2-norm of the
+      // residual is not monotone in CG, and a claim just below the tolerance
+      // can be refuted again and again)
+      if (!S.active[pr] && S.status[pr] == HPSE_OK) S.tol2[pr] = fmax(0.25 * S.tol2[pr], 1e-6 * tol * tol);
       const double b = (S.active[pr] && S.rz[pr] > 0.0) ? S.beta[pr] * (rz / S.rz[pr]) : 0.0;
       S.beta[pr] = isfinite(b) ? b : 0.0;
       S.rz[pr] = rz;
@@ -784,6 +790,21 @@ __global__ void k_h1_corner(H1Args A) {
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
+// The dynamic shared-memory limit of a kernel is one setting per (function,
+// device), shared by every handle and host thread.  It is only ever raised,
+// under a lock, so that a call for a mesh of lower degree can never lower it
+// beneath what a concurrent launch for a larger mesh needs.
+static cudaError_t raise_smem(const void *fn, int device, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void *, int>, size_t> done;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t &cur = done[std::make_pair(fn, device)];
+  if (bytes <= cur) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
+
 static ElemVecArgs elem_args(const hpse_mesh *m) {
   ElemVecArgs a;
   a.n_elem = m->n_elem + m->n_corner;
@@ -1707,7 +1728,7 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data) {
     A.fw = m->coord != HPSE_COORD_CARTESIAN ? m->d_fw64.as<double>() : nullptr;
     const int Q = 2 * Wmax + 1, P = Wmax + 1;
     const size_t smem = (size_t)(8 * Q * Q + 2 * Q * P + P * P) * sizeof(double);
-    CK(cudaFuncSetAttribute(k_face_data, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CK(raise_smem((const void *)k_face_data, m->device, (size_t)smem));
     k_face_data<<<(int)felems.size() * R, 128, smem>>>(A);
     CK(cudaGetLastError());
     ++g_launches;
@@ -1843,8 +1864,8 @@ extern "C" hpse_status hpse_setup_block_preconditioner(hpse_mesh *m) {
       g_launches += 3;
     }
     const size_t sm = (size_t)n * sizeof(double);
-    CK(cudaFuncSetAttribute(k_bj_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(sm, 1)));
-    CK(cudaFuncSetAttribute(k_bj_trinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(sm, 1)));
+    CK(raise_smem((const void *)k_bj_chol, m->device, (size_t)std::max<size_t>(sm, 1)));
+    CK(raise_smem((const void *)k_bj_trinv, m->device, (size_t)std::max<size_t>(sm, 1)));
     k_bj_chol<<<g.n, 256, sm, s>>>(ba, blk.as<double>(), fail.as<int32_t>());
     CK(cudaGetLastError());
     k_bj_trinv<<<g.n, 256, sm, s>>>(ba, blk.as<double>(), m->d_bj64.as<double>());
@@ -2161,6 +2182,15 @@ static hpse_status fp64_residual(hpse_mesh *m, const double *x64, double tol, do
   return HPSE_OK;
 }
 
+// largest relative residual of the pairs; NaN if any is NaN (a plain
+// std::max would drop it and report convergence)
+static double max_rel(const double *rel, int npr) {
+  double worst = 0.0;
+  for (int i = 0; i < npr; ++i)
+    if (std::isnan(rel[i]) || rel[i] > worst) worst = rel[i];
+  return worst;
+}
+
 // PCG with residual refresh ("reliable updates"): one PCG iteration sequence
 // with applies, preconditioner and vectors in T (vectors scaled by 1/||b||);
 // whenever its recursive residual has dropped by the factor delta since the
@@ -2194,9 +2224,17 @@ static hpse_status solve_reliable(hpse_mesh *m, const hpse_solve_opts *o, double
     std::vector<double> bn2(npr), bn(npr), ibn(npr);
     CK(cudaMemcpyAsync(bn2.data(), m->d_bnorm2.p, npr * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    bool finite = true;
     for (int i = 0; i < npr; ++i) {
       bn[i] = std::sqrt(bn2[i]);
       ibn[i] = bn[i] > 0 ? 1.0 / bn[i] : 0.0;
+      finite = finite && std::isfinite(bn2[i]);
+    }
+    if (!finite) {
+      // a non-finite right-hand side: nothing to iterate on
+      rep->rel_residual = std::numeric_limits<double>::quiet_NaN();
+      *status_out = HPSE_ERR_BREAKDOWN;
+      return HPSE_OK;
     }
     CK(cudaMemcpyAsync(sc_bn, bn.data(), npr * sizeof(double), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(sc_scale, ibn.data(), npr * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -2290,11 +2328,14 @@ static hpse_status solve_reliable(hpse_mesh *m, const hpse_solve_opts *o, double
       ++updates;
       CK(cudaMemcpyAsync(w.h_sc, w.sc.p, (size_t)12 * npr * sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
-      worst = 0.0;
-      for (int i = 0; i < npr; ++i) worst = std::max(worst, w.h_sc[8 * npr + i]);
+      worst = max_rel(w.h_sc + 8 * npr, npr);
       if (verbose())
         fprintf(stderr, "[hpse] refresh %d after %d %s iterations: max rel residual %.3e\n", updates, done,
                 dbl ? "FP64" : "FP32", worst);
+      if (!std::isfinite(worst)) {
+        status = HPSE_ERR_BREAKDOWN;
+        break;
+      }
       if (!(worst > o->tol)) break;
       if (capped) {
         status = HPSE_ERR_NO_CONVERGENCE;
@@ -2361,6 +2402,21 @@ extern "C" hpse_status hpse_pcg_solve(hpse_mesh *m, const hpse_solve_opts *o, do
   double *sc_scale = w.sc.as<double>() + 9 * npr;
   double *sc_rnorm = w.sc.as<double>() + 10 * npr;
   int total_it = 0, status = HPSE_OK, sweeps = 0, applies = 0;
+  {
+    // a non-finite right-hand side (||b||^2 is NaN or inf for some pair) is a
+    // breakdown before any iteration, in every mode
+    std::vector<double> bn2(npr);
+    CK(cudaMemcpyAsync(bn2.data(), m->d_bnorm2.p, npr * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int i = 0; i < npr; ++i)
+      if (!std::isfinite(bn2[i])) {
+        rep->rel_residual = std::numeric_limits<double>::quiet_NaN();
+        rep->status = HPSE_ERR_BREAKDOWN;
+        CK(cudaEventRecord(w.ev, s));
+        CK(cudaStreamWaitEvent(us, w.ev, 0));
+        return HPSE_ERR_BREAKDOWN;
+      }
+  }
   if (o->zero_init) CK(cudaMemsetAsync(x, 0, nb, s));
   if (o->prec == HPSE_FP64) {
     // FP64 PCG; its convergence claim is checked on the true FP64 residual
@@ -2404,16 +2460,18 @@ extern "C" hpse_status hpse_pcg_solve(hpse_mesh *m, const hpse_solve_opts *o, do
       }
       CK(cudaMemcpyAsync(w.h_sc, w.sc.p, (size_t)12 * npr * sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
-      double worst = 0.0;
+      const double worst = max_rel(w.h_sc + 8 * npr, npr);
       bool any = false;
-      for (int i = 0; i < npr; ++i) {
-        worst = std::max(worst, w.h_sc[8 * npr + i]);
+      for (int i = 0; i < npr; ++i)
         if (w.h_sc[9 * npr + i] != 0.0) any = true;
-      }
       rep->rel_residual = worst;
       if (verbose())
         fprintf(stderr, "[hpse] sweep %d: max rel residual %.3e, inner iterations so far %d\n", sweeps, worst,
                 total_it);
+      if (!std::isfinite(worst)) {
+        status = HPSE_ERR_BREAKDOWN;
+        break;
+      }
       if (!any) break;
       if (sweeps >= max_sweeps || total_it >= o->max_iter) {
         status = HPSE_ERR_NO_CONVERGENCE;
@@ -2452,9 +2510,7 @@ extern "C" hpse_status hpse_pcg_solve(hpse_mesh *m, const hpse_solve_opts *o, do
     if (st != HPSE_OK) return st;
     CK(cudaMemcpyAsync(w.h_sc, w.sc.p, (size_t)12 * npr * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    double worst = 0.0;
-    for (int i = 0; i < npr; ++i) worst = std::max(worst, w.h_sc[8 * npr + i]);
-    rep->rel_residual = worst;
+    rep->rel_residual = max_rel(w.h_sc + 8 * npr, npr);
   }
   CK(cudaEventRecord(w.ev, s));
   CK(cudaStreamWaitEvent(us, w.ev, 0));
@@ -2514,7 +2570,7 @@ extern "C" hpse_status hpse_h1_error(hpse_mesh *m, const double *u, const double
   A.cfac = m->d_ch1.as<double>();
   const int P = Wmax + 1, Q = 2 * Wmax + 1;
   const size_t smem = (size_t)(P * P * P + 2 * Q * P * P + 3 * Q * Q * P) * sizeof(double);
-  CK(cudaFuncSetAttribute(k_h1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CK(raise_smem((const void *)k_h1, m->device, (size_t)smem));
   k_h1<<<ni, 256, smem, s>>>(A);
   CK(cudaGetLastError());
   ++g_launches;
@@ -2758,7 +2814,7 @@ static int max_degree(const hpse_mesh *m) {
 static hpse_status launch_fields(hpse_mesh *m, const double *u, double *out, cudaStream_t s) {
   const int W = max_degree(m), P = W + 1, Q = 2 * W + 1;
   const size_t smem = (size_t)(P * P * P + 3 * Q * P * P + 3 * Q * Q * P) * sizeof(double);
-  CK(cudaFuncSetAttribute(k_fields, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CK(raise_smem((const void *)k_fields, m->device, (size_t)smem));
   k_fields<<<n_items_all(m), 256, smem, s>>>(field_args(m, u, out));
   CK(cudaGetLastError());
   ++g_launches;
@@ -2784,7 +2840,7 @@ extern "C" hpse_status hpse_apply_eval_transpose(hpse_mesh *m, const double *rho
   CK(cudaSetDevice(m->device));
   const int W = max_degree(m), P = W + 1, Q = 2 * W + 1;
   const size_t smem = (size_t)(Q * Q * Q + Q * Q * P + Q * P * P) * sizeof(double);
-  CK(cudaFuncSetAttribute(k_eval_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CK(raise_smem((const void *)k_eval_T, m->device, (size_t)smem));
   k_eval_T<<<n_items_all(m), 256, smem, (cudaStream_t)stream>>>(field_args(m, nullptr, y), rho);
   CK(cudaGetLastError());
   ++g_launches;
@@ -2978,7 +3034,7 @@ extern "C" hpse_status hpse_h1_error_noalloc(hpse_mesh *m, const double *u, cons
   A.part_nrm = part_nrm;
   const int P = Wmax + 1, Q = 2 * Wmax + 1;
   const size_t smem = (size_t)(P * P * P + 2 * Q * P * P + 3 * Q * Q * P) * sizeof(double);
-  CK(cudaFuncSetAttribute(k_h1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CK(raise_smem((const void *)k_h1, m->device, (size_t)smem));
   // every partial and every result is overwritten: nothing needs clearing
   k_h1<<<(int)ni, 256, smem, s>>>(A);
   CK(cudaGetLastError());

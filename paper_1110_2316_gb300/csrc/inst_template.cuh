@@ -80,6 +80,16 @@ cudaError_t upload_fn(const double *pk) {
   int o = 0;
   for (int m = 0; m < 3; ++m)
     for (int i = 0; i < QP; ++i) t.B[m][i] = (real)pk[o++];
+  // folded halves of B0, B1, B2 (even-odd decomposition), formed in FP64
+  for (int m = 0; m < 3; ++m) {
+    const double *b = pk + m * QP;
+    for (int q = 0; q <= HQ; ++q)
+      for (int j = 0; j < HPE; ++j) {
+        const bool mid = (P & 1) && j == HP;
+        t.FE[m][q * HPE + j] = (real)(mid ? b[q * P + j] : 0.5 * (b[q * P + j] + b[q * P + P - 1 - j]));
+        t.FO[m][q * HPE + j] = (real)(mid ? 0.0 : 0.5 * (b[q * P + j] - b[q * P + P - 1 - j]));
+      }
+  }
   for (int i = 0; i < P2; ++i) t.D[i] = (real)pk[o++];
   for (int i = 0; i < P2; ++i) t.S[i] = (real)pk[o++];
   for (int i = 0; i < P2; ++i) t.MP[i] = (real)pk[o++];

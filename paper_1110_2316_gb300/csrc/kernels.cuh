@@ -47,6 +47,16 @@ constexpr int Q2P = Q * Q * P;
 
 typedef REAL real;
 
+// even-odd folding of the symmetric GLL grids: HP mirrored node pairs of the
+// P-grid (plus its middle node when P is odd: HPE = ceil(P / 2) folded
+// entries) and HQ = W mirrored point pairs of the Q-grid around its middle
+// point q = W
+constexpr int HP = P / 2;
+constexpr int HPE = (P + 1) / 2;
+constexpr int HQ = W;
+// B1 is odd under the reflection of both grids, B0 and B2 even
+__host__ __device__ constexpr bool odd_mat(int m) { return m == 1; }
+
 // Threads per apply CTA: one thread per z-line (Q^2 lines) rounded up to
 // whole warps, capped; every stage then runs at most once per thread when
 // Q^2 <= NT, so no constant-table read is loop-invariant across line
@@ -68,12 +78,17 @@ constexpr int APPLY_MINB = sizeof(real) == 8 ? 1 : (APPLY_MINB_RAW < 1 ? 1 : (AP
 
 // 1-D tables of this degree (filled by upload_tables):
 //   B[m][q*P+k]  = d^m l_k / dlambda^m at the q-th (2W+1)-point GLL node
+//   FE[m][q*HPE+j], FO[m][q*HPE+j] (q = 0..W) = the folded halves of B[m]:
+//                  (B[m][q][j] +- B[m][q][P-1-j]) / 2 for j < HP; the middle
+//                  column (P odd) is B[m][q][HP] in FE and 0 in FO
 //   D[i*P+k]     = GLL differentiation matrix on the (W+1)-point grid (eq. 5.47)
 //   S[k*P+c]     = preconditioner eigenvectors (node k, mode c), eq. (5.15)-(5.17)
 //   MP, KP       = B0^T diag(w) B0 and B0^T K B0 (P x P face-norm matrices)
 //   WQ[q]        = (2W+1)-point GLL weights; MU[c] = eigenvalues of eq. (5.15)
 struct Tables {
   real B[3][QP];
+  real FE[3][P * HPE];
+  real FO[3][P * HPE];
   real D[P2];
   real S[P2];
   real MP[P2];
@@ -381,11 +396,29 @@ __device__ __forceinline__ void load_coef4(const real *p, real &m, real &dx, rea
 }
 
 // ---------------------------------------------------------------------------
-// Line stages of the sum factorisation.  A stage has L lines of one element;
-// the outputs of a line are split into NC chunks of compile-time range and
-// item = chunk * PAD32(L) + line, so the chunk index is warp-uniform, all
-// warps of the CTA get work, and every FMA keeps its constant-bank operand.
-// Padding lanes (line >= L) read a clamped valid line and store nothing.
+// Line stages of the sum factorisation, with the even-odd decomposition of
+// the 1-D matrices (Solomonoff, "A fast algorithm for spectral
+// differentiation", J. Comput. Phys. 98, 1992): on the symmetric GLL grids
+// B0 and B2 are even and B1 is odd under the reflection of both grids,
+// B_m[Q-1-q][P-1-j] = +-B_m[q][j].  Folding an input line into the sums and
+// differences of its mirrored entries and producing each output pair
+// (q, Q-1-q) at once halves the multiply-adds of every contraction:
+//   forward (P -> Q), output pair q <= W (q = W is the middle point):
+//     even M: PLUS = FE_M[q] . e, MINUS = FO_M[q] . o
+//     odd M:  PLUS = FO_M[q] . o, MINUS = FE_M[q] . e
+//     y[q] = PLUS + MINUS, y[Q-1-q] = PLUS - MINUS
+//   transpose (Q -> P), output pair k < HPE, folded input (ve, vo, vm):
+//     even M: PLUS += FE_M[.][k] . ve + FE_M[W][k] vm, MINUS += FO_M[.][k] . vo
+//     odd M:  PLUS += FE_M[.][k] . vo, MINUS += FO_M[.][k] . ve + FO_M[W][k] vm
+//     r[k] = PLUS + MINUS, r[P-1-k] = PLUS - MINUS
+// Contributions of several matrices to one output add into one PLUS/MINUS
+// pair, whatever their parities.
+//
+// A stage has L lines of one element; the output pairs of a line are split
+// into NC chunks of compile-time range and item = chunk * PAD32(L) + line, so
+// the chunk index is warp-uniform, all warps of the CTA get work, and every
+// FMA keeps its constant-bank operand.  Padding lanes (line >= L) read a
+// clamped valid line and store nothing.
 // ---------------------------------------------------------------------------
 template <int L>
 struct Lines {
@@ -399,23 +432,101 @@ struct Range {
   static constexpr int E = (CI + 1) * N / NC;
 };
 
+// u[P] -> e (mirrored sums, then the middle node), o (mirrored differences, middle 0)
+__device__ __forceinline__ void fold_p(const real *u, real *e, real *o) {
+#pragma unroll
+  for (int j = 0; j < HP; ++j) {
+    e[j] = u[j] + u[P - 1 - j];
+    o[j] = u[j] - u[P - 1 - j];
+  }
+  if (P & 1) {
+    e[HP] = u[HP];
+    o[HP] = (real)0;
+  }
+}
+
+// v[Q] -> ve[HQ], vo[HQ] (mirrored sums / differences), vm (the middle point)
+__device__ __forceinline__ void fold_q(const real *v, real *ve, real *vo, real &vm) {
+#pragma unroll
+  for (int q = 0; q < HQ; ++q) {
+    ve[q] = v[q] + v[Q - 1 - q];
+    vo[q] = v[q] - v[Q - 1 - q];
+  }
+  vm = v[HQ];
+}
+
+// forward, output pair q: PLUS / MINUS of matrix M applied to the folded line
+template <int M>
+__device__ __forceinline__ void fwd_pm(const real *e, const real *o, int q, real &pl, real &mi) {
+#pragma unroll
+  for (int j = 0; j < HPE; ++j) {
+    if (!odd_mat(M)) pl += c_tab.FE[M][q * HPE + j] * e[j];
+    else if (q < HQ) mi += c_tab.FE[M][q * HPE + j] * e[j];
+  }
+#pragma unroll
+  for (int j = 0; j < HP; ++j) {
+    if (odd_mat(M)) pl += c_tab.FO[M][q * HPE + j] * o[j];
+    else if (q < HQ) mi += c_tab.FO[M][q * HPE + j] * o[j];
+  }
+}
+
+// transpose, one folded input pair q < HQ (ve, vo) into the PLUS / MINUS of
+// every output pair k
+template <int M>
+__device__ __forceinline__ void rev_pair(real ve, real vo, int q, real *pl, real *mi) {
+#pragma unroll
+  for (int k = 0; k < HPE; ++k) {
+    pl[k] += c_tab.FE[M][q * HPE + k] * (odd_mat(M) ? vo : ve);
+    if (k < HP) mi[k] += c_tab.FO[M][q * HPE + k] * (odd_mat(M) ? ve : vo);
+  }
+}
+// transpose, the middle input point vm
+template <int M>
+__device__ __forceinline__ void rev_mid(real vm, real *pl, real *mi) {
+#pragma unroll
+  for (int k = 0; k < HPE; ++k) {
+    if (!odd_mat(M)) pl[k] += c_tab.FE[M][HQ * HPE + k] * vm;
+    else if (k < HP) mi[k] += c_tab.FO[M][HQ * HPE + k] * vm;
+  }
+}
+// transpose of a whole folded line into output pair k
+template <int M>
+__device__ __forceinline__ void rev_line(const real *ve, const real *vo, real vm, int k, real &pl, real &mi) {
+#pragma unroll
+  for (int q = 0; q < HQ; ++q) {
+    pl += c_tab.FE[M][q * HPE + k] * (odd_mat(M) ? vo[q] : ve[q]);
+    if (k < HP) mi += c_tab.FO[M][q * HPE + k] * (odd_mat(M) ? ve[q] : vo[q]);
+  }
+  if (!odd_mat(M)) pl += c_tab.FE[M][HQ * HPE + k] * vm;
+  else if (k < HP) mi += c_tab.FO[M][HQ * HPE + k] * vm;
+}
+
+// store the pair (q, Q-1-q) of a forward output from PLUS / MINUS
+__device__ __forceinline__ void put_q(real *dst, int stride, int q, real pl, real mi) {
+  dst[q * stride] = pl + mi;
+  if (q < HQ) dst[(Q - 1 - q) * stride] = pl - mi;
+}
+// store the pair (k, P-1-k) of a transposed output from PLUS / MINUS
+__device__ __forceinline__ void put_p(real *dst, int stride, int k, real pl, real mi) {
+  dst[k * stride] = pl + mi;
+  if (k < HP) dst[(P - 1 - k) * stride] = pl - mi;
+}
+
 // x-stage: X0 = B0 u, X2 = B2 u (X1 = B1 u) along x for line l = (j, k)
 template <int COEF, int CI, int NC>
-__device__ __forceinline__ void x_fwd_chunk(const real *v, real *X0, real *X1, real *X2, int l, bool ok) {
-  typedef Range<CI, NC, Q> R;
+__device__ __forceinline__ void x_fwd_chunk(const real *e, const real *o, real *X0, real *X1, real *X2, int l,
+                                            bool ok) {
+  typedef Range<CI, NC, HQ + 1> R;
 #pragma unroll
   for (int q = R::B; q < R::E; ++q) {
-    real a0 = 0, a2 = 0, a1 = 0;
-#pragma unroll
-    for (int i = 0; i < P; ++i) {
-      a0 += c_tab.B[0][q * P + i] * v[i];
-      a2 += c_tab.B[2][q * P + i] * v[i];
-      if (var_coef(COEF)) a1 += c_tab.B[1][q * P + i] * v[i];
-    }
+    real p0 = 0, m0 = 0, p2 = 0, m2 = 0, p1 = 0, m1 = 0;
+    fwd_pm<0>(e, o, q, p0, m0);
+    fwd_pm<2>(e, o, q, p2, m2);
+    if (var_coef(COEF)) fwd_pm<1>(e, o, q, p1, m1);
     if (ok) {
-      X0[l * Q + q] = a0;
-      X2[l * Q + q] = a2;
-      if (var_coef(COEF)) X1[l * Q + q] = a1;
+      put_q(X0 + l * Q, 1, q, p0, m0);
+      put_q(X2 + l * Q, 1, q, p2, m2);
+      if (var_coef(COEF)) put_q(X1 + l * Q, 1, q, p1, m1);
     }
     __syncwarp();  // scheduling fence (register pressure); reached by all 32 lanes
   }
@@ -423,26 +534,24 @@ __device__ __forceinline__ void x_fwd_chunk(const real *v, real *X0, real *X1, r
 
 // y-stage: T00 = B0 X0, TL = sx2 B0 X2 + sy2 B2 X0 (T10 = B0 X1, T01 = B1 X0) along y
 template <int COEF, int CI, int NC>
-__device__ __forceinline__ void y_fwd_chunk(const real *v0, const real *v1, const real *v2, real *T00, real *TL,
-                                            real *T10, real *T01, int qa, int k, bool ok, real sx2, real sy2) {
-  typedef Range<CI, NC, Q> R;
+__device__ __forceinline__ void y_fwd_chunk(const real *e0, const real *o0, const real *e1, const real *o1,
+                                            const real *e2, const real *o2, real *T00, real *TL, real *T10,
+                                            real *T01, int qa, int k, bool ok, real sx2, real sy2) {
+  typedef Range<CI, NC, HQ + 1> R;
 #pragma unroll
   for (int qb = R::B; qb < R::E; ++qb) {
-    real t00 = 0, tl0 = 0, tl2 = 0, t10 = 0, t01 = 0;
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-      t00 += c_tab.B[0][qb * P + j] * v0[j];
-      tl0 += c_tab.B[2][qb * P + j] * v0[j];
-      tl2 += c_tab.B[0][qb * P + j] * v2[j];
-      if (var_coef(COEF)) t10 += c_tab.B[0][qb * P + j] * v1[j];
-      if (y_first(COEF)) t01 += c_tab.B[1][qb * P + j] * v0[j];
-    }
-    const int o = (k * Q + qb) * Q + qa;
+    real p00 = 0, m00 = 0, pl0 = 0, ml0 = 0, pl2 = 0, ml2 = 0, p10 = 0, m10 = 0, p01 = 0, m01 = 0;
+    fwd_pm<0>(e0, o0, qb, p00, m00);
+    fwd_pm<2>(e0, o0, qb, pl0, ml0);
+    fwd_pm<0>(e2, o2, qb, pl2, ml2);
+    if (var_coef(COEF)) fwd_pm<0>(e1, o1, qb, p10, m10);
+    if (y_first(COEF)) fwd_pm<1>(e0, o0, qb, p01, m01);
+    const int o = k * Q2 + qa;  // + qb * Q
     if (ok) {
-      T00[o] = t00;
-      TL[o] = sx2 * tl2 + sy2 * tl0;
-      if (var_coef(COEF)) T10[o] = t10;
-      if (y_first(COEF)) T01[o] = t01;
+      put_q(T00 + o, Q, qb, p00, m00);
+      put_q(TL + o, Q, qb, sx2 * pl2 + sy2 * pl0, sx2 * ml2 + sy2 * ml0);
+      if (var_coef(COEF)) put_q(T10 + o, Q, qb, p10, m10);
+      if (y_first(COEF)) put_q(T01 + o, Q, qb, p01, m01);
     }
     __syncwarp();  // scheduling fence (register pressure); reached by all 32 lanes
   }
@@ -453,43 +562,51 @@ template <int COEF, int CI, int NC>
 __device__ __forceinline__ void y_rev_chunk(const real *RZ, const real *R0, const real *RX, const real *RY,
                                             real *X0, real *X1, real *X2, int qa, int k, bool ok, real sx2,
                                             real sy2) {
-  typedef Range<CI, NC, P> R;
+  typedef Range<CI, NC, HPE> R;
+  const int o = k * Q2 + qa;  // + qb * Q
   {
-    real vz[Q], v0[Q], vy[Q];
+    real ze[HQ], zo[HQ], zm, re[HQ], ro[HQ], rm, ye[HQ], yo[HQ], ym;
+    {
+      real v[Q];
 #pragma unroll
-    for (int qb = 0; qb < Q; ++qb) {
-      const int o = (k * Q + qb) * Q + qa;
-      vz[qb] = RZ[o];
-      v0[qb] = R0[o];
-      if (y_first(COEF)) vy[qb] = RY[o];
+      for (int qb = 0; qb < Q; ++qb) v[qb] = RZ[o + qb * Q];
+      fold_q(v, ze, zo, zm);
+#pragma unroll
+      for (int qb = 0; qb < Q; ++qb) v[qb] = R0[o + qb * Q];
+      fold_q(v, re, ro, rm);
+      if (y_first(COEF)) {
+#pragma unroll
+        for (int qb = 0; qb < Q; ++qb) v[qb] = RY[o + qb * Q];
+        fold_q(v, ye, yo, ym);
+      }
     }
 #pragma unroll
     for (int j = R::B; j < R::E; ++j) {
-      real x0 = 0, x0b = 0, x0c = 0, x2 = 0;
-#pragma unroll
-      for (int qb = 0; qb < Q; ++qb) {
-        x0 += c_tab.B[0][qb * P + j] * vz[qb];
-        x0b += c_tab.B[2][qb * P + j] * v0[qb];
-        x2 += c_tab.B[0][qb * P + j] * v0[qb];
-        if (y_first(COEF)) x0c += c_tab.B[1][qb * P + j] * vy[qb];
-      }
+      real pz = 0, mz = 0, p2 = 0, m2 = 0, py = 0, my = 0, p0 = 0, m0 = 0;
+      rev_line<0>(ze, zo, zm, j, pz, mz);
+      rev_line<2>(re, ro, rm, j, p2, m2);
+      rev_line<0>(re, ro, rm, j, p0, m0);
+      if (y_first(COEF)) rev_line<1>(ye, yo, ym, j, py, my);
       if (ok) {
-        const int o = (k * P + j) * Q + qa;
-        X0[o] = x0 + sy2 * x0b + x0c;
-        X2[o] = sx2 * x2;
+        const int ox = k * P * Q + qa;  // + j * Q
+        put_p(X0 + ox, Q, j, pz + sy2 * p2 + py, mz + sy2 * m2 + my);
+        put_p(X2 + ox, Q, j, sx2 * p0, sx2 * m0);
       }
     }
   }
   if (var_coef(COEF)) {
-    real vx[Q];
+    real xe[HQ], xo[HQ], xm;
+    {
+      real v[Q];
 #pragma unroll
-    for (int qb = 0; qb < Q; ++qb) vx[qb] = RX[(k * Q + qb) * Q + qa];
+      for (int qb = 0; qb < Q; ++qb) v[qb] = RX[o + qb * Q];
+      fold_q(v, xe, xo, xm);
+    }
 #pragma unroll
     for (int j = R::B; j < R::E; ++j) {
-      real x1 = 0;
-#pragma unroll
-      for (int qb = 0; qb < Q; ++qb) x1 += c_tab.B[0][qb * P + j] * vx[qb];
-      if (ok) X1[(k * P + j) * Q + qa] = x1;
+      real p1 = 0, m1 = 0;
+      rev_line<0>(xe, xo, xm, j, p1, m1);
+      if (ok) put_p(X1 + k * P * Q + qa, Q, j, p1, m1);
     }
   }
 }
@@ -498,23 +615,29 @@ __device__ __forceinline__ void y_rev_chunk(const real *RZ, const real *R0, cons
 template <int COEF, int CI, int NC>
 __device__ __forceinline__ void x_rev_chunk(const real *X0, const real *X1, const real *X2, real *sy, int l,
                                             bool ok) {
-  typedef Range<CI, NC, P> R;
-  real v0[Q], v2[Q], v1[Q];
+  typedef Range<CI, NC, HPE> R;
+  real e0[HQ], o0[HQ], m0v, e2[HQ], o2[HQ], m2v, e1[HQ], o1[HQ], m1v;
+  {
+    real v[Q];
 #pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    v0[q] = X0[l * Q + q];
-    v2[q] = X2[l * Q + q];
-    if (var_coef(COEF)) v1[q] = X1[l * Q + q];
+    for (int q = 0; q < Q; ++q) v[q] = X0[l * Q + q];
+    fold_q(v, e0, o0, m0v);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) v[q] = X2[l * Q + q];
+    fold_q(v, e2, o2, m2v);
+    if (var_coef(COEF)) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) v[q] = X1[l * Q + q];
+      fold_q(v, e1, o1, m1v);
+    }
   }
 #pragma unroll
   for (int i = R::B; i < R::E; ++i) {
-    real s = 0;
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      s += c_tab.B[0][q * P + i] * v0[q] + c_tab.B[2][q * P + i] * v2[q];
-      if (var_coef(COEF)) s += c_tab.B[1][q * P + i] * v1[q];
-    }
-    if (ok) sy[l * P + i] = s;
+    real pl = 0, mi = 0;
+    rev_line<0>(e0, o0, m0v, i, pl, mi);
+    rev_line<2>(e2, o2, m2v, i, pl, mi);
+    if (var_coef(COEF)) rev_line<1>(e1, o1, m1v, i, pl, mi);
+    if (ok) put_p(sy + l * P, 1, i, pl, mi);
   }
 }
 
@@ -595,10 +718,14 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
         const int c = it / LS::PADL, lp = it - c * LS::PADL;
         const bool ok = lp < P2;
         const int l = ok ? lp : P2 - 1;
-        real v[P];
+        real e[HPE], o[HPE];
+        {
+          real v[P];
 #pragma unroll
-        for (int i = 0; i < P; ++i) v[i] = su[l * P + i];
-#define XF_CALL(CI) x_fwd_chunk<COEF, (CI < LS::NC ? CI : 0), LS::NC>(v, X0, X1, X2, l, ok)
+          for (int i = 0; i < P; ++i) v[i] = su[l * P + i];
+          fold_p(v, e, o);
+        }
+#define XF_CALL(CI) x_fwd_chunk<COEF, (CI < LS::NC ? CI : 0), LS::NC>(e, o, X0, X1, X2, l, ok)
         HPSE_DISPATCH4(LS::NC, c, XF_CALL);
 #undef XF_CALL
       }
@@ -613,12 +740,20 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
         const bool ok = lp < QP;
         const int l = ok ? lp : QP - 1;
         const int qa = l % Q, k = l / Q;
-        real v0[P], v2[P], v1[P];
+        real e0[HPE], o0[HPE], e2[HPE], o2[HPE], e1[HPE], o1[HPE];
+        {
+          real v[P];
 #pragma unroll
-        for (int j = 0; j < P; ++j) {
-          v0[j] = X0[(k * P + j) * Q + qa];
-          v2[j] = X2[(k * P + j) * Q + qa];
-          if (var_coef(COEF)) v1[j] = X1[(k * P + j) * Q + qa];
+          for (int j = 0; j < P; ++j) v[j] = X0[(k * P + j) * Q + qa];
+          fold_p(v, e0, o0);
+#pragma unroll
+          for (int j = 0; j < P; ++j) v[j] = X2[(k * P + j) * Q + qa];
+          fold_p(v, e2, o2);
+          if (var_coef(COEF)) {
+#pragma unroll
+            for (int j = 0; j < P; ++j) v[j] = X1[(k * P + j) * Q + qa];
+            fold_p(v, e1, o1);
+          }
         }
         // per-x-point factors, constant along this y-line: vertex neighbourhood
         // 1/sin^2(x_1) on u_22, vertex-edge 1 + e^{2 x_1} on u_11
@@ -626,7 +761,8 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
         const real sx2q =
             (COEF == COEF_VERTEX_EDGE) ? sx2 * ((real)1 + A.kappa[(int64_t)e * hpse::KAPPA_STRIDE + qa]) : sx2;
 #define YF_CALL(CI) \
-  y_fwd_chunk<COEF, (CI < LS::NC ? CI : 0), LS::NC>(v0, v1, v2, T00, TL, T10, T01, qa, k, ok, sx2q, sy2q)
+  y_fwd_chunk<COEF, (CI < LS::NC ? CI : 0), LS::NC>(e0, o0, e1, o1, e2, o2, T00, TL, T10, T01, qa, k, ok, sx2q, \
+                                                    sy2q)
         HPSE_DISPATCH4(LS::NC, c, YF_CALL);
 #undef YF_CALL
       }
@@ -635,7 +771,7 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
   }
 
   // ---- z-stage per (qa, qb) column: forward + pointwise weight into rho[Q]
-  // (registers), then the transpose from rho ------------------------------
+  // (registers), then the transpose from rho; both folded (even-odd) ------
   for (int lp = tid; lp < PAD32(Q2); lp += nt) {
     const bool ok = lp < Q2;
     const int l = ok ? lp : Q2 - 1;
@@ -650,79 +786,107 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
 #pragma unroll
       for (int qc = 0; qc < Q; ++qc) rho[qc] = (real)A.rho[(int64_t)r * A.nquad + cbase + (int64_t)qc * Q2];
     } else {
-      real a00[P], aL[P], a10[P], a01[P];
+      real e00[HPE], o00[HPE], eL[HPE], oL[HPE], e10[HPE], o10[HPE], e01[HPE], o01[HPE];
+      {
+        real v[P];
 #pragma unroll
-      for (int k = 0; k < P; ++k) {
-        const int o = (k * Q + qb) * Q + qa;
-        a00[k] = T00[o];
-        aL[k] = TL[o];
-        if (var_coef(COEF)) a10[k] = T10[o];
-        if (y_first(COEF)) a01[k] = T01[o];
+        for (int k = 0; k < P; ++k) v[k] = T00[k * Q2 + l];
+        fold_p(v, e00, o00);
+#pragma unroll
+        for (int k = 0; k < P; ++k) v[k] = TL[k * Q2 + l];
+        fold_p(v, eL, oL);
+        if (var_coef(COEF)) {
+#pragma unroll
+          for (int k = 0; k < P; ++k) v[k] = T10[k * Q2 + l];
+          fold_p(v, e10, o10);
+        }
+        if (y_first(COEF)) {
+#pragma unroll
+          for (int k = 0; k < P; ++k) v[k] = T01[k * Q2 + l];
+          fold_p(v, e01, o01);
+        }
       }
       const real wab = c_tab.WQ[qa] * c_tab.WQ[qb] * Jac;
 #pragma unroll
-      for (int qc = 0; qc < Q; ++qc) {
-        real s2 = 0, s0 = 0, s1z = 0, sxx = 0, syy = 0;
-#pragma unroll
-        for (int k = 0; k < P; ++k) {
-          s2 += c_tab.B[2][qc * P + k] * a00[k];
-          s0 += c_tab.B[0][qc * P + k] * aL[k];
-          if (var_coef(COEF)) {
-            s1z += c_tab.B[1][qc * P + k] * a00[k];
-            sxx += c_tab.B[0][qc * P + k] * a10[k];
-          }
-          // the d_y slot: u_y (variable coefficient) or u_xz (vertex-edge)
-          if (y_first(COEF)) syy += c_tab.B[0][qc * P + k] * a01[k];
-          if (mixed_xz(COEF)) syy += c_tab.B[1][qc * P + k] * a10[k];
-        }
-        const real sigma0 = sz2c * s2 + s0;
+      for (int qc = 0; qc <= HQ; ++qc) {
+        real p2 = 0, m2 = 0, p0 = 0, m0 = 0, p1 = 0, m1 = 0, px = 0, mx = 0, py = 0, my = 0;
+        fwd_pm<2>(e00, o00, qc, p2, m2);
+        fwd_pm<0>(eL, oL, qc, p0, m0);
         if (var_coef(COEF)) {
-          real mq, dx, dy, dz;
-          load_coef4(A.coef + 4 * (cbase + (int64_t)qc * Q2), mq, dx, dy, dz);
-          rho[qc] = mq * (sigma0 + dz * s1z + dx * sxx + dy * syy);
-        } else {
-          rho[qc] = wab * c_tab.WQ[qc] * sigma0;
+          fwd_pm<1>(e00, o00, qc, p1, m1);
+          fwd_pm<0>(e10, o10, qc, px, mx);
+        }
+        // the d_y slot: u_y (variable coefficient) or u_xz (vertex-edge)
+        if (y_first(COEF)) fwd_pm<0>(e01, o01, qc, py, my);
+        if (mixed_xz(COEF)) fwd_pm<1>(e10, o10, qc, py, my);
+#pragma unroll
+        for (int side = 0; side < (qc < HQ ? 2 : 1); ++side) {
+          const int q = side ? Q - 1 - qc : qc;
+          const real sg = side ? (real)-1 : (real)1;
+          const real sigma0 = sz2c * (p2 + sg * m2) + (p0 + sg * m0);
+          if (var_coef(COEF)) {
+            real mq, dx, dy, dz;
+            load_coef4(A.coef + 4 * (cbase + (int64_t)q * Q2), mq, dx, dy, dz);
+            rho[q] = mq * (sigma0 + dz * (p1 + sg * m1) + dx * (px + sg * mx) + dy * (py + sg * my));
+          } else {
+            rho[q] = wab * c_tab.WQ[q] * sigma0;
+          }
         }
         __syncwarp();  // scheduling fence (register pressure); reached by all 32 lanes
       }
     }
-    real rz[P], r0[P], rx[P], ry[P];
+    real zp[HPE], zm[HPE], rp[HPE], rm[HPE], xp[HPE], xm[HPE], yp[HPE], ym[HPE];
 #pragma unroll
-    for (int k = 0; k < P; ++k) {
-      rz[k] = 0;
-      r0[k] = 0;
-      rx[k] = 0;
-      ry[k] = 0;
+    for (int k = 0; k < HPE; ++k) {
+      zp[k] = zm[k] = rp[k] = rm[k] = xp[k] = xm[k] = yp[k] = ym[k] = (real)0;
     }
 #pragma unroll
-    for (int qc = 0; qc < Q; ++qc) {
-      const real rq = rho[qc];
-      real dx = 0, dy = 0, dz = 0;
-      if (var_coef(COEF)) {
-        real mq;
-        load_coef4(A.coef + 4 * (cbase + (int64_t)qc * Q2), mq, dx, dy, dz);
-      }
-      const real rz2 = sz2c * rq, rzd = dz * rq, rxd = dx * rq, ryd = dy * rq;
+    for (int qc = 0; qc <= HQ; ++qc) {
+      // the streams rz2 = sz2 rho, rzd = d_z rho, rho, rxd = d_x rho, ryd = d_y rho
+      // at the pair of points (qc, Q-1-qc), folded
+      real s2[2], sd[2], s0[2], sx[2], sy[2];
 #pragma unroll
-      for (int k = 0; k < P; ++k) {
-        rz[k] += c_tab.B[2][qc * P + k] * rz2;
-        r0[k] += c_tab.B[0][qc * P + k] * rq;
+      for (int side = 0; side < (qc < HQ ? 2 : 1); ++side) {
+        const int q = side ? Q - 1 - qc : qc;
+        const real rq = rho[q];
+        real dx = 0, dy = 0, dz = 0;
         if (var_coef(COEF)) {
-          rz[k] += c_tab.B[1][qc * P + k] * rzd;
-          rx[k] += c_tab.B[0][qc * P + k] * rxd;
+          real mq;
+          load_coef4(A.coef + 4 * (cbase + (int64_t)q * Q2), mq, dx, dy, dz);
         }
-        if (y_first(COEF)) ry[k] += c_tab.B[0][qc * P + k] * ryd;
-        if (mixed_xz(COEF)) rx[k] += c_tab.B[1][qc * P + k] * ryd;
+        s2[side] = sz2c * rq;
+        sd[side] = dz * rq;
+        s0[side] = rq;
+        sx[side] = dx * rq;
+        sy[side] = dy * rq;
+      }
+      if (qc < HQ) {
+        rev_pair<2>(s2[0] + s2[1], s2[0] - s2[1], qc, zp, zm);
+        rev_pair<0>(s0[0] + s0[1], s0[0] - s0[1], qc, rp, rm);
+        if (var_coef(COEF)) {
+          rev_pair<1>(sd[0] + sd[1], sd[0] - sd[1], qc, zp, zm);
+          rev_pair<0>(sx[0] + sx[1], sx[0] - sx[1], qc, xp, xm);
+        }
+        if (y_first(COEF)) rev_pair<0>(sy[0] + sy[1], sy[0] - sy[1], qc, yp, ym);
+        if (mixed_xz(COEF)) rev_pair<1>(sy[0] + sy[1], sy[0] - sy[1], qc, xp, xm);
+      } else {
+        rev_mid<2>(s2[0], zp, zm);
+        rev_mid<0>(s0[0], rp, rm);
+        if (var_coef(COEF)) {
+          rev_mid<1>(sd[0], zp, zm);
+          rev_mid<0>(sx[0], xp, xm);
+        }
+        if (y_first(COEF)) rev_mid<0>(sy[0], yp, ym);
+        if (mixed_xz(COEF)) rev_mid<1>(sy[0], xp, xm);
       }
     }
     if (ok) {
 #pragma unroll
-      for (int k = 0; k < P; ++k) {
-        const int o = (k * Q + qb) * Q + qa;
-        T00[o] = rz[k];
-        TL[o] = r0[k];
-        if (var_coef(COEF)) T10[o] = rx[k];
-        if (y_first(COEF)) T01[o] = ry[k];
+      for (int k = 0; k < HPE; ++k) {
+        put_p(T00 + l, Q2, k, zp[k], zm[k]);
+        put_p(TL + l, Q2, k, rp[k], rm[k]);
+        if (var_coef(COEF)) put_p(T10 + l, Q2, k, xp[k], xm[k]);
+        if (y_first(COEF)) put_p(T01 + l, Q2, k, yp[k], ym[k]);
       }
     }
   }

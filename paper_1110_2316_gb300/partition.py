@@ -179,41 +179,62 @@ def exchange_emulated(halos: List[Halo], vecs) -> None:
 
 
 def dist_pcg(apply: Callable, precond: Callable, exchange: Callable, allreduce: Callable, b, n_own: int,
-             tol: float = 1e-10, max_iter: int = 10000):
+             tol: float = 1e-10, max_iter: int = 10000, n_rhs: int = 1):
     """PCG (Section 5.1) on a vector distributed over parts: every vector is
-    the part's local vector (own DOFs first, ghost blocks after); dot
-    products run over the own DOFs and are summed over the parts by
-    ``allreduce`` (FP64); ``exchange`` refreshes p's ghosts before each apply.
-    Stops at ||r|| <= tol ||b|| (global norms).  Returns (x, iterations,
-    relative residual)."""
+    the part's local vector, ``n_rhs`` right-hand sides of n_local entries
+    each (own DOFs first, ghost blocks after, the library's layout); dot
+    products run over each right-hand side's own DOFs and are summed over the
+    parts by ``allreduce`` (FP64, one value per right-hand side); ``exchange``
+    refreshes p's ghosts before each apply.  Each right-hand side keeps its
+    own alpha and beta and stops at ||r|| <= tol ||b|| (global norms); the
+    loop ends when all have.  Returns (x, iterations, largest relative
+    residual)."""
     import torch
 
+    R = int(n_rhs)
+    if R < 1 or b.numel() % R:
+        raise ValueError("b holds %d entries, not a whole number of %d right-hand sides" % (b.numel(), R))
+    nl = b.numel() // R
+    if not 0 <= n_own <= nl:
+        raise ValueError("n_own = %d outside one right-hand side's %d entries" % (n_own, nl))
+
+    def rows(v):
+        return v.view(R, nl)
+
     def dot(a, c):
-        return allreduce(torch.dot(a[:n_own], c[:n_own]).reshape(1))[0]
+        return allreduce((rows(a)[:, :n_own] * rows(c)[:, :n_own]).sum(1))
+
+    def own_only(v):
+        rows(v)[:, n_own:] = 0
 
     x = torch.zeros_like(b)
     r = b.clone()
-    r[n_own:] = 0
-    bn = float(torch.sqrt(dot(b, b)))
+    own_only(r)
+    bn = torch.sqrt(dot(b, b))
+    bn = torch.where(bn > 0, bn, torch.ones_like(bn))
     z = torch.empty_like(b)
     precond(r, z)
-    z[n_own:] = 0
+    own_only(z)
     p = z.clone()
     rz = dot(r, z)
     q = torch.empty_like(b)
-    it, rel = 0, float(torch.sqrt(dot(r, r))) / bn
-    while rel > tol and it < max_iter:
+    rel = torch.sqrt(dot(r, r)) / bn
+    it = 0
+    while float(rel.max()) > tol and it < max_iter:
+        live = rel > tol
         exchange(p)
         apply(p, q)
-        q[n_own:] = 0
-        alpha = rz / dot(p, q)
-        x += alpha * p
-        r -= alpha * q
+        own_only(q)
+        pq = dot(p, q)
+        alpha = torch.where(live, rz / torch.where(live, pq, torch.ones_like(pq)), torch.zeros_like(pq))
+        rows(x).add_(alpha[:, None] * rows(p))
+        rows(r).sub_(alpha[:, None] * rows(q))
         precond(r, z)
-        z[n_own:] = 0
+        own_only(z)
         rz_new = dot(r, z)
-        p = z + (rz_new / rz) * p
-        rz = rz_new
+        beta = torch.where(live, rz_new / torch.where(live, rz, torch.ones_like(rz)), torch.zeros_like(rz))
+        p = (rows(z) + beta[:, None] * rows(p)).reshape(-1)
+        rz = torch.where(live, rz_new, rz)
         it += 1
-        rel = float(torch.sqrt(dot(r, r))) / bn
-    return x, it, rel
+        rel = torch.where(live, torch.sqrt(dot(r, r)) / bn, rel)
+    return x, it, float(rel.max())

@@ -150,7 +150,8 @@ def test_distributed_pcg_equals_whole_mesh_solve(api):
         b = torch.empty(m.ndof, dtype=torch.float64, device="cuda")
         m.get_rhs(b)
         x, it, rel = pt.dist_pcg(lambda a, c: m.apply_operator(a, c), lambda a, c: m.apply_preconditioner(a, c),
-                                 exchange, allreduce, b, p.owned_dofs(), tol=1e-11, max_iter=5000)
+                                 exchange, allreduce, b, p.owned_dofs(), tol=1e-11, max_iter=5000,
+                                 n_rhs=m.n_rhs)
         torch.cuda.synchronize()
         results[r] = (x.cpu().numpy(), it, rel)
 

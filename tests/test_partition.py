@@ -202,3 +202,42 @@ def test_more_parts_than_elements():
         assert p.n_owned == int(np.sum(owner == r)) and p.desc.n_problem >= 1
         if p.n_owned == 0:
             assert p.desc.n_elem == 0 and not p.send and not p.recv
+
+
+def test_dist_pcg_several_rhs_each_converges():
+    # one part, no peers: the vectors hold 3 right-hand sides of n_local
+    # entries each (own DOFs first, then ghost entries that must stay out of
+    # every dot product); each right-hand side has its own alpha and beta and
+    # the result equals three separate dense solves
+    rng = np.random.default_rng(3)
+    n_own, n_gh, R = 12, 5, 3
+    nl = n_own + n_gh
+    M = rng.standard_normal((n_own, n_own))
+    A = M @ M.T + n_own * np.eye(n_own)
+    scales = [1.0, 1e3, 1e-2]
+    B = np.zeros((R, nl))
+    for r in range(R):
+        B[r, :n_own] = scales[r] * rng.standard_normal(n_own)
+        B[r, n_own:] = 1e6  # ghost entries: must not enter the sums
+    Ad = torch.tensor(A)
+
+    def apply(p, q):
+        pv, qv = p.view(R, nl), q.view(R, nl)
+        qv[:, :n_own] = pv[:, :n_own] @ Ad.T
+        qv[:, n_own:] = 7.0
+
+    def precond(r, z):
+        z.copy_(r / float(A[0, 0]))
+
+    x, it, rel = pt.dist_pcg(apply, precond, lambda v: None, lambda t: t, torch.tensor(B.ravel()), n_own,
+                             tol=1e-12, max_iter=200, n_rhs=R)
+    assert rel <= 1e-12
+    X = x.view(R, nl).numpy()
+    for r in range(R):
+        xo = np.linalg.solve(A, B[r, :n_own])
+        assert np.linalg.norm(X[r, :n_own] - xo) <= 1e-10 * np.linalg.norm(xo), r
+    try:
+        pt.dist_pcg(apply, precond, lambda v: None, lambda t: t, torch.zeros(nl * R + 1), n_own, n_rhs=R)
+        raise AssertionError("a vector that is not a whole number of right-hand sides was accepted")
+    except ValueError:
+        pass

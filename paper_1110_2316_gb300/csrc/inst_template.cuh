@@ -90,10 +90,24 @@ cudaError_t upload_fn(const double *pk) {
         t.FO[m][q * HPE + j] = (real)(mid ? 0.0 : 0.5 * (b[q * P + j] - b[q * P + P - 1 - j]));
       }
   }
+  const double *pD = pk + o;
   for (int i = 0; i < P2; ++i) t.D[i] = (real)pk[o++];
   for (int i = 0; i < P2; ++i) t.S[i] = (real)pk[o++];
+  const double *pM = pk + o;
   for (int i = 0; i < P2; ++i) t.MP[i] = (real)pk[o++];
+  const double *pK = pk + o;
   for (int i = 0; i < P2; ++i) t.KP[i] = (real)pk[o++];
+  // folded halves of D, D^T, MP, KP for the face phase, formed in FP64
+  for (int m = 0; m < 4; ++m)
+    for (int i = 0; i < HPE; ++i)
+      for (int j = 0; j < HPE; ++j) {
+        auto x = [&](int r, int c) {
+          return m == 0 ? pD[r * P + c] : (m == 1 ? pD[c * P + r] : (m == 2 ? pM[r * P + c] : pK[r * P + c]));
+        };
+        const bool mid = (P & 1) && j == HP;
+        t.PF[m][0][i * HPE + j] = (real)(mid ? x(i, j) : 0.5 * (x(i, j) + x(i, P - 1 - j)));
+        t.PF[m][1][i * HPE + j] = (real)(mid ? 0.0 : 0.5 * (x(i, j) - x(i, P - 1 - j)));
+      }
   for (int i = 0; i < Q; ++i) t.WQ[i] = (real)pk[o++];
   for (int i = 0; i < P; ++i) t.MU[i] = (real)pk[o++];
   cudaError_t err = cudaMemcpyToSymbol(c_tab, &t, sizeof(Tables));

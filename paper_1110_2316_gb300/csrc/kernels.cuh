@@ -56,6 +56,8 @@ constexpr int HPE = (P + 1) / 2;
 constexpr int HQ = W;
 // B1 is odd under the reflection of both grids, B0 and B2 even
 __host__ __device__ constexpr bool odd_mat(int m) { return m == 1; }
+// P x P matrices of the face phase: D and D^T are odd, MP and KP even
+__host__ __device__ constexpr bool odd_pp(int t) { return t < 2; }
 
 // Threads per apply CTA: one thread per z-line (Q^2 lines) rounded up to
 // whole warps, capped; every stage then runs at most once per thread when
@@ -81,6 +83,8 @@ constexpr int APPLY_MINB = sizeof(real) == 8 ? 1 : (APPLY_MINB_RAW < 1 ? 1 : (AP
 //   FE[m][q*HPE+j], FO[m][q*HPE+j] (q = 0..W) = the folded halves of B[m]:
 //                  (B[m][q][j] +- B[m][q][P-1-j]) / 2 for j < HP; the middle
 //                  column (P odd) is B[m][q][HP] in FE and 0 in FO
+//   PF[t][0|1][i*HPE+j] (i, j < HPE) = the same halves of the P x P matrices
+//                  t = 0: D, 1: D^T, 2: MP, 3: KP
 //   D[i*P+k]     = GLL differentiation matrix on the (W+1)-point grid (eq. 5.47)
 //   S[k*P+c]     = preconditioner eigenvectors (node k, mode c), eq. (5.15)-(5.17)
 //   MP, KP       = B0^T diag(w) B0 and B0^T K B0 (P x P face-norm matrices)
@@ -89,6 +93,7 @@ struct Tables {
   real B[3][QP];
   real FE[3][P * HPE];
   real FO[3][P * HPE];
+  real PF[4][2][HPE * HPE];
   real D[P2];
   real S[P2];
   real MP[P2];
@@ -147,234 +152,6 @@ __device__ __forceinline__ double block_sum(T v, double *red) {
     for (int i = 0; i < nw; ++i) t += red[i];
   }
   return t;  // valid in thread 0
-}
-
-// ---------------------------------------------------------------------------
-// Face phase: y_e += contributions of the six faces of element e (eq. 4.2),
-// all six faces processed at once, then gathered node by node (no two
-// threads ever add into the same node: deterministic, no atomics).
-//
-// Per face f (axis a, side s, tangential axes t1 < t2, nodal face grid P x P):
-//   own traces  F = u|face, N = du/dlambda_a|face, G1/G2 = tangential derivatives
-//   interior:   J0 = [u], J1 = [u_{x_t1}], J2 = [u_{x_t2}], J3 = [u_{x_a}]
-//               g0 = (MP x MP) J0, gk = (MP x MP + MP x KP + KP x MP) Jk
-//   Dirichlet:  J0 = u, J1 = du/dlambda_t1, J2 = du/dlambda_t2 (eq. 2.18)
-// MP = B0^T W B0 and KP = B0^T K B0 are the Section 5.3 face forms on the
-// (2W+1)-point grid pulled back to the nodal grid (exact algebra).
-// Scratch per face: 15 arrays of P x P.
-// ---------------------------------------------------------------------------
-constexpr int FACE_ARR = 15;
-
-template <int MODE>
-__device__ __forceinline__ real nb_value(const ApplyArgs &A, int64_t idx, real bt) {
-  if (MODE == MODE_PCG) return A.z[idx] + bt * A.u[idx];
-  return A.u[idx];
-}
-
-template <int COEF, int MODE>
-__device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, real *sy, real *scr, const real *Ds,
-                           const real *MPs, const real *KPs, const real *geo_e) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  // slot s of face f: scr + (f * FACE_ARR + s) * P2
-#define FSLOT(f, s) (scr + ((f)*FACE_ARR + (s)) * P2)
-  enum { sF = 0, sN, sFn, sNn, sJ0, sJ1, sJ2, sJ3, sT0, sA1, sA2, sA3, sB1, sB2, sB3 };
-  // F1: traces of u and of the neighbour on every face point
-  for (int t = tid; t < 6 * P2; t += nt) {
-    const int f = t / P2, sp = t - f * P2;
-    const int p1 = sp % P, p2 = sp / P;
-    const int a = f >> 1, nend = (f & 1) ? P - 1 : 0;
-    FSLOT(f, sF)[sp] = su[fidx(a, nend, p1, p2)];
-    real s = 0;
-#pragma unroll
-    for (int k = 0; k < P; ++k) s += Ds[nend * P + k] * su[fidx(a, k, p1, p2)];
-    FSLOT(f, sN)[sp] = s;
-    const int nb = A.nbr[(int64_t)e * 6 + f];
-    if (nb != -1 && A.self_only) {
-      FSLOT(f, sFn)[sp] = (real)0;
-      FSLOT(f, sNn)[sp] = (real)0;
-    } else if (nbhd_coef(COEF) && nb < -1) {
-      // corner set: through face 0 a polynomial along z (the p2 direction of
-      // this face), constant in the other two variables (edge: x3; vertex-edge:
-      // zeta); through face 4 one constant (vertex, vertex-edge)
-      const int64_t cb = (int64_t)r * A.ndof + A.dof_off[A.n_elem + (-2 - nb)];
-      const real bt = (MODE == MODE_PCG) ? (real)A.beta[A.prob[e] * A.n_rhs + r] : (real)0;
-      FSLOT(f, sFn)[sp] = nb_value<MODE>(A, cb + (corner_f0(COEF) && f == 0 ? p2 : 0), bt);
-      FSLOT(f, sNn)[sp] = (real)0;
-    } else if (nb >= 0) {
-      const int64_t base = (int64_t)r * A.ndof + A.dof_off[nb];
-      const real bt = (MODE == MODE_PCG) ? (real)A.beta[A.prob[nb] * A.n_rhs + r] : (real)0;
-      const int nn = P - 1 - nend;
-      FSLOT(f, sFn)[sp] = nb_value<MODE>(A, base + fidx(a, nn, p1, p2), bt);
-      real sn = 0;
-#pragma unroll
-      for (int k = 0; k < P; ++k) sn += Ds[nn * P + k] * nb_value<MODE>(A, base + fidx(a, k, p1, p2), bt);
-      FSLOT(f, sNn)[sp] = sn;
-    }
-  }
-  __syncthreads();
-  // F2: tangential derivatives and jumps
-  for (int t = tid; t < 6 * P2; t += nt) {
-    const int f = t / P2, sp = t - f * P2;
-    const int p1 = sp % P, p2 = sp / P;
-    const int a = f >> 1;
-    const int t1 = (a == 0) ? 1 : 0, t2 = (a == 2) ? 1 : 2;
-    const real *F = FSLOT(f, sF);
-    real g1 = 0, g2 = 0;
-#pragma unroll
-    for (int m = 0; m < P; ++m) {
-      g1 += Ds[p1 * P + m] * F[p2 * P + m];
-      g2 += Ds[p2 * P + m] * F[m * P + p1];
-    }
-    const int nb = A.nbr[(int64_t)e * 6 + f];
-    if (nb != -1) {
-      const real *Fn = FSLOT(f, sFn);
-      real h1 = 0, h2 = 0;
-#pragma unroll
-      for (int m = 0; m < P; ++m) {
-        h1 += Ds[p1 * P + m] * Fn[p2 * P + m];
-        h2 += Ds[p2 * P + m] * Fn[m * P + p1];
-      }
-      // a corner set shares the theta and x3 scales of its layer-1 element
-      const real *gn = nb >= 0 ? A.geo + (int64_t)nb * 4 : geo_e;
-      FSLOT(f, sJ0)[sp] = F[sp] - Fn[sp];
-      FSLOT(f, sJ1)[sp] = geo_e[t1] * g1 - gn[t1] * h1;
-      FSLOT(f, sJ2)[sp] = geo_e[t2] * g2 - gn[t2] * h2;
-      FSLOT(f, sJ3)[sp] = geo_e[a] * FSLOT(f, sN)[sp] - gn[a] * FSLOT(f, sNn)[sp];
-    } else {
-      FSLOT(f, sJ0)[sp] = F[sp];
-      FSLOT(f, sJ1)[sp] = g1;
-      FSLOT(f, sJ2)[sp] = g2;
-      FSLOT(f, sJ3)[sp] = 0;
-    }
-  }
-  __syncthreads();
-  // F3: first Kronecker factor (along p1)
-  for (int t = tid; t < 6 * P2; t += nt) {
-    const int f = t / P2, sp = t - f * P2;
-    const int p1 = sp % P, p2 = sp / P;
-    const real *J0 = FSLOT(f, sJ0), *J1 = FSLOT(f, sJ1), *J2 = FSLOT(f, sJ2), *J3 = FSLOT(f, sJ3);
-    // face-norm weights: w[0] on the L2 jump of u; (w[3k-2], w[3k-1], w[3k]) =
-    // (L2, quotient along t1, quotient along t2) on jump field k (1 on box meshes)
-    const real *wf = (nbhd_coef(COEF) && A.fw) ? A.fw + ((int64_t)e * 6 + f) * hpse::FACE_W : nullptr;
-    real t0 = 0, a1 = 0, a2 = 0, a3 = 0, b1 = 0, b2 = 0, b3 = 0;
-#pragma unroll
-    for (int m = 0; m < P; ++m) {
-      const real mp = MPs[p1 * P + m], kp = KPs[p1 * P + m];
-      t0 += mp * J0[p2 * P + m];
-      a1 += mp * J1[p2 * P + m];
-      b1 += kp * J1[p2 * P + m];
-      a2 += mp * J2[p2 * P + m];
-      b2 += kp * J2[p2 * P + m];
-      a3 += mp * J3[p2 * P + m];
-      b3 += kp * J3[p2 * P + m];
-    }
-    if (wf) {
-      FSLOT(f, sT0)[sp] = wf[0] * t0;
-      FSLOT(f, sA1)[sp] = wf[3] * a1;
-      FSLOT(f, sA2)[sp] = wf[6] * a2;
-      FSLOT(f, sA3)[sp] = wf[9] * a3;
-      FSLOT(f, sB1)[sp] = wf[1] * a1 + wf[2] * b1;
-      FSLOT(f, sB2)[sp] = wf[4] * a2 + wf[5] * b2;
-      FSLOT(f, sB3)[sp] = wf[7] * a3 + wf[8] * b3;
-    } else {
-      FSLOT(f, sT0)[sp] = t0;
-      FSLOT(f, sA1)[sp] = a1;
-      FSLOT(f, sA2)[sp] = a2;
-      FSLOT(f, sA3)[sp] = a3;
-      FSLOT(f, sB1)[sp] = a1 + b1;
-      FSLOT(f, sB2)[sp] = a2 + b2;
-      FSLOT(f, sB3)[sp] = a3 + b3;
-    }
-  }
-  __syncthreads();
-  // F4: second factor (along p2): g0 -> J0 slot, g1..g3 -> J1..J3 slots
-  for (int t = tid; t < 6 * P2; t += nt) {
-    const int f = t / P2, sp = t - f * P2;
-    const int p1 = sp % P, p2 = sp / P;
-    real g0 = 0, g1 = 0, g2 = 0, g3 = 0;
-#pragma unroll
-    for (int m = 0; m < P; ++m) {
-      const real mp = MPs[p2 * P + m], kp = KPs[p2 * P + m];
-      const int o = m * P + p1;
-      g0 += mp * FSLOT(f, sT0)[o];
-      g1 += mp * FSLOT(f, sB1)[o] + kp * FSLOT(f, sA1)[o];
-      g2 += mp * FSLOT(f, sB2)[o] + kp * FSLOT(f, sA2)[o];
-      g3 += mp * FSLOT(f, sB3)[o] + kp * FSLOT(f, sA3)[o];
-    }
-    FSLOT(f, sJ0)[sp] = g0;
-    FSLOT(f, sJ1)[sp] = g1;
-    FSLOT(f, sJ2)[sp] = g2;
-    FSLOT(f, sJ3)[sp] = g3;
-  }
-  __syncthreads();
-  // corner side of face 0 (r = r_1 of the edge, psi = psi_1 of the vertex-edge
-  // neighbourhood): minus the transposed corner traces of the weighted jumps,
-  // y_c[k] = -sum_p1 g0[k][p1] - s_z sum_m D[m][k] sum_p1 g2[m][p1] (the
-  // corner's derivatives along x and y vanish), stored per (slot, rhs) for the
-  // corner kernel
-  if (corner_f0(COEF) && A.cscr && !A.self_only) {
-    const int slot = A.cslot[2 * e];
-    if (slot >= 0) {
-      for (int k = tid; k < P; k += nt) {
-        real s0 = 0, s2 = 0;
-        for (int p1 = 0; p1 < P; ++p1) s0 += FSLOT(0, sJ0)[k * P + p1];
-        for (int m = 0; m < P; ++m) {
-          real g2 = 0;
-          for (int p1 = 0; p1 < P; ++p1) g2 += FSLOT(0, sJ2)[m * P + p1];
-          s2 += Ds[m * P + k] * g2;
-        }
-        A.cscr[((int64_t)slot * A.n_rhs + r) * hpse::CSCR_STRIDE + k] = -(s0 + geo_e[2] * s2);
-      }
-    }
-  }
-  // corner side of face 4 (rho = rho_1 of the vertex, zeta = zeta_1 of the
-  // vertex-edge neighbourhood): the corner constant's trace is 1 at every face
-  // node, so y_c = -sum of the weighted jump of u over the face
-  if (corner_f4(COEF) && A.cscr && !A.self_only && tid == 0) {
-    const int slot = A.cslot[2 * e + 1];
-    if (slot >= 0) {
-      real s0 = 0;
-      for (int t = 0; t < P2; ++t) s0 += FSLOT(4, sJ0)[t];
-      A.cscr[((int64_t)slot * A.n_rhs + r) * hpse::CSCR_STRIDE] = -s0;
-    }
-  }
-  // F5: transposed traces on the face grid: C (face layer) -> F slot, Gn (normal) -> N slot
-  for (int t = tid; t < 6 * P2; t += nt) {
-    const int f = t / P2, sp = t - f * P2;
-    const int p1 = sp % P, p2 = sp / P;
-    const int a = f >> 1;
-    const int t1 = (a == 0) ? 1 : 0, t2 = (a == 2) ? 1 : 2;
-    const bool interior = A.nbr[(int64_t)e * 6 + f] != -1;
-    const real *g1 = FSLOT(f, sJ1), *g2 = FSLOT(f, sJ2);
-    real u1 = 0, u2 = 0;
-#pragma unroll
-    for (int m = 0; m < P; ++m) {
-      u1 += Ds[m * P + p1] * g1[p2 * P + m];
-      u2 += Ds[m * P + p2] * g2[m * P + p1];
-    }
-    const real c1 = interior ? geo_e[t1] : (real)1, c2 = interior ? geo_e[t2] : (real)1;
-    FSLOT(f, sF)[sp] = FSLOT(f, sJ0)[sp] + c1 * u1 + c2 * u2;
-    FSLOT(f, sN)[sp] = interior ? geo_e[a] * FSLOT(f, sJ3)[sp] : (real)0;
-  }
-  __syncthreads();
-  // F6: gather onto the nodes of the element
-  for (int t = tid; t < P3; t += nt) {
-    const int i = t % P, j = (t / P) % P, k = t / P2;
-    real acc = 0;
-#pragma unroll
-    for (int f = 0; f < 6; ++f) {
-      const int a = f >> 1, nend = (f & 1) ? P - 1 : 0;
-      const int n = a == 0 ? i : (a == 1 ? j : k);
-      const int p1 = a == 0 ? j : i;
-      const int p2 = a == 2 ? j : k;
-      const int sp = p2 * P + p1;
-      acc += Ds[nend * P + n] * FSLOT(f, sN)[sp];
-      if (n == nend) acc += FSLOT(f, sF)[sp];
-    }
-    sy[t] += acc;
-  }
-  __syncthreads();
-#undef FSLOT
 }
 
 // vector load of the 4 pointwise coefficients (m, d_x, d_y, d_z) of a point
@@ -641,6 +418,276 @@ __device__ __forceinline__ void x_rev_chunk(const real *X0, const real *X1, cons
   }
 }
 
+// ---------------------------------------------------------------------------
+// Face phase: y_e += contributions of the six faces of element e (eq. 4.2),
+// all six faces processed at once, then gathered node by node (no two
+// threads ever add into the same node: deterministic, no atomics).
+//
+// Per face f (axis a, side s, tangential axes t1 < t2, nodal face grid P x P,
+// p1 along t1, p2 along t2):
+//   own traces  F = u|face, N = du/dlambda_a|face, tangential derivatives D F
+//   interior:   J0 = [u], J1 = [u_{x_t1}], J2 = [u_{x_t2}], J3 = [u_{x_a}]
+//               g0 = (MP x MP) J0, gk = (MP x MP + MP x KP + KP x MP) Jk
+//   Dirichlet:  J0 = u, J1 = du/dlambda_t1, J2 = du/dlambda_t2 (eq. 2.18)
+// MP = B0^T W B0 and KP = B0^T K B0 are the Section 5.3 face forms on the
+// (2W+1)-point grid pulled back to the nodal grid (exact algebra).
+//
+// Every 1-D product runs as a line job: one thread takes one line of P face
+// values, folds it (even-odd) and applies D, D^T (odd), MP or KP (even) with
+// compile-time constant-bank operands.  The normal derivative at the face
+// takes the first row of D only: D[P-1][P-1-k] = -D[0][k] on the symmetric
+// grid, so both sides walk their normal line from the face inward.
+// Scratch per face: 14 arrays of P x P (the G_k of the norm products reuse
+// the J slots, the transposed tangential derivatives the A slots).
+// ---------------------------------------------------------------------------
+constexpr int FACE_ARR = 15;
+
+template <int MODE>
+__device__ __forceinline__ real nb_value(const ApplyArgs &A, int64_t idx, real bt) {
+  if (MODE == MODE_PCG) return A.z[idx] + bt * A.u[idx];
+  return A.u[idx];
+}
+
+// y[0..P-1] = X v for one folded line (e, o) of the P x P matrix t:
+// 0 = D, 1 = D^T (odd), 2 = MP, 3 = KP (even)
+template <int T>
+__device__ __forceinline__ void pp_line(const real *e, const real *o, real *y) {
+#pragma unroll
+  for (int i = 0; i < HPE; ++i) {
+    real pl = 0, mi = 0;
+#pragma unroll
+    for (int j = 0; j < HPE; ++j) {
+      if (!odd_pp(T)) {
+        pl += c_tab.PF[T][0][i * HPE + j] * e[j];
+        if (i < HP && j < HP) mi += c_tab.PF[T][1][i * HPE + j] * o[j];
+      } else {
+        if (j < HP) pl += c_tab.PF[T][1][i * HPE + j] * o[j];
+        if (i < HP) mi += c_tab.PF[T][0][i * HPE + j] * e[j];
+      }
+    }
+    y[i] = pl + mi;
+    if (i < HP) y[P - 1 - i] = pl - mi;
+  }
+}
+
+// load a line of P values with stride st and fold it
+__device__ __forceinline__ void load_fold(const real *p, int st, real *e, real *o) {
+  real v[P];
+#pragma unroll
+  for (int m = 0; m < P; ++m) v[m] = p[m * st];
+  fold_p(v, e, o);
+}
+
+template <int COEF, int MODE>
+__device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, real *sy, real *scr, const real *Ds,
+                           const real *geo_e, real *fsc) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // slot s of face f: scr + (f * FACE_ARR + s) * P2; G_k reuse J_k, U1 / U2 reuse A1 / A2
+#define FSLOT(f, s) (scr + ((f)*FACE_ARR + (s)) * P2)
+  enum { sF = 0, sFn, sJ0, sJ1, sJ2, sJ3, sA0, sA1, sA2, sA3, sB0, sB1, sB2, sB3 };
+  // per face: the scale of the normal term in the gather (s_a on interior faces, 0 on Dirichlet faces)
+  if (tid < 6) {
+    const int nb = A.nbr[(int64_t)e * 6 + tid];
+    fsc[tid] = nb != -1 ? geo_e[tid >> 1] : (real)0;
+  }
+  // 1: traces at every face point: F, J0 = [u] (u), J3 = [u_{x_a}] (0), the neighbour's trace Fn
+  for (int t = tid; t < 6 * P2; t += nt) {
+    const int f = t / P2, sp = t - f * P2;
+    const int p1 = sp % P, p2 = sp / P;
+    const int a = f >> 1, side = f & 1;
+    const int stride = a == 0 ? 1 : (a == 1 ? P : P2);
+    const int b0 = a == 0 ? (p2 * P + p1) * P : (a == 1 ? p2 * P2 + p1 : p2 * P + p1);
+    // own normal line from the face inward
+    const int o0 = side ? b0 + (P - 1) * stride : b0, os = side ? -stride : stride;
+    const real Fv = su[o0];
+    real Nv = 0;
+#pragma unroll
+    for (int k = 0; k < P; ++k) Nv += c_tab.D[k] * su[o0 + k * os];
+    if (side) Nv = -Nv;
+    const int nb = A.nbr[(int64_t)e * 6 + f];
+    real Fn = 0, Nn = 0;
+    if (nb != -1 && A.self_only) {
+      // diagonal block: the neighbour's trace is zero
+    } else if (nbhd_coef(COEF) && nb < -1) {
+      // corner set: through face 0 a polynomial along z (the p2 direction of
+      // this face), constant in the other two variables (edge: x3; vertex-edge:
+      // zeta); through face 4 one constant (vertex, vertex-edge)
+      const int64_t cb = (int64_t)r * A.ndof + A.dof_off[A.n_elem + (-2 - nb)];
+      const real bt = (MODE == MODE_PCG) ? (real)A.beta[A.prob[e] * A.n_rhs + r] : (real)0;
+      Fn = nb_value<MODE>(A, cb + (corner_f0(COEF) && f == 0 ? p2 : 0), bt);
+    } else if (nb >= 0) {
+      const int64_t nbase = (int64_t)r * A.ndof + A.dof_off[nb];
+      const real bt = (MODE == MODE_PCG) ? (real)A.beta[A.prob[nb] * A.n_rhs + r] : (real)0;
+      // the neighbour's face is its opposite end: its normal line from that face inward
+      const int q0 = side ? b0 : b0 + (P - 1) * stride, qs = side ? stride : -stride;
+      Fn = nb_value<MODE>(A, nbase + q0, bt);
+#pragma unroll
+      for (int k = 0; k < P; ++k) Nn += c_tab.D[k] * nb_value<MODE>(A, nbase + q0 + k * qs, bt);
+      if (!side) Nn = -Nn;
+    }
+    FSLOT(f, sF)[sp] = Fv;
+    if (nb != -1) {
+      // a corner set shares the theta and x3 scales of its layer-1 element
+      const real *gn = nb >= 0 ? A.geo + (int64_t)nb * 4 : geo_e;
+      FSLOT(f, sFn)[sp] = Fn;
+      FSLOT(f, sJ0)[sp] = Fv - Fn;
+      FSLOT(f, sJ3)[sp] = geo_e[a] * Nv - gn[a] * Nn;
+    } else {
+      FSLOT(f, sJ0)[sp] = Fv;
+      FSLOT(f, sJ3)[sp] = (real)0;
+    }
+  }
+  __syncthreads();
+  // 2: tangential derivatives (line jobs): J1 along p1 (lines p2), J2 along p2 (lines p1);
+  // interior faces: jumps of the physical derivatives, Dirichlet faces: d/dlambda
+  for (int t = tid; t < 12 * P; t += nt) {
+    const int dir = t / (6 * P), rem = t - dir * 6 * P;
+    const int f = rem / P, ln = rem - f * P;
+    const int a = f >> 1;
+    const int tax = dir ? ((a == 2) ? 1 : 2) : ((a == 0) ? 1 : 0);
+    const int ob = dir ? ln : ln * P, os = dir ? P : 1;
+    const int nb = A.nbr[(int64_t)e * 6 + f];
+    real ev[HPE], od[HPE], g[P];
+    load_fold(FSLOT(f, sF) + ob, os, ev, od);
+    pp_line<0>(ev, od, g);
+    real *J = FSLOT(f, dir ? sJ2 : sJ1) + ob;
+    if (nb != -1) {
+      const real *gn = nb >= 0 ? A.geo + (int64_t)nb * 4 : geo_e;
+      const real s0 = geo_e[tax], s1 = gn[tax];
+      real h[P];
+      load_fold(FSLOT(f, sFn) + ob, os, ev, od);
+      pp_line<0>(ev, od, h);
+#pragma unroll
+      for (int m = 0; m < P; ++m) J[m * os] = s0 * g[m] - s1 * h[m];
+    } else {
+#pragma unroll
+      for (int m = 0; m < P; ++m) J[m * os] = g[m];
+    }
+  }
+  __syncthreads();
+  // 3: first Kronecker factor along p1 (line jobs per field): a = MP J, b = KP J;
+  // face-norm weights: w[0] on the L2 jump of u; (w[3k-2], w[3k-1], w[3k]) =
+  // (L2, quotient along t1, quotient along t2) on jump field k (1 on box meshes):
+  // A_k = w[3k] a, B_k = w[3k-2] a + w[3k-1] b; field 0: A_0 = 0, B_0 = w[0] a
+  for (int t = tid; t < 24 * P; t += nt) {
+    const int f = t / (4 * P), rem = t - f * 4 * P;
+    const int fld = rem / P, p2 = rem - fld * P;
+    real ev[HPE], od[HPE], av[P], bv[P];
+    load_fold(FSLOT(f, sJ0 + fld) + p2 * P, 1, ev, od);
+    pp_line<2>(ev, od, av);
+    real wb = (real)1, wc = (real)1;
+    if (nbhd_coef(COEF) && A.fw) {
+      const real *wf = A.fw + ((int64_t)e * 6 + f) * hpse::FACE_W;
+      wb = fld ? wf[3 * fld - 2] : wf[0];
+      wc = fld ? wf[3 * fld - 1] : (real)0;
+      if (fld) {
+        const real wa = wf[3 * fld];
+#pragma unroll
+        for (int i = 0; i < P; ++i) FSLOT(f, sA0 + fld)[p2 * P + i] = wa * av[i];
+      }
+    } else if (fld) {
+#pragma unroll
+      for (int i = 0; i < P; ++i) FSLOT(f, sA0 + fld)[p2 * P + i] = av[i];
+    }
+    if (fld) {
+      pp_line<3>(ev, od, bv);
+#pragma unroll
+      for (int i = 0; i < P; ++i) FSLOT(f, sB0 + fld)[p2 * P + i] = wb * av[i] + wc * bv[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < P; ++i) FSLOT(f, sB0)[p2 * P + i] = wb * av[i];
+    }
+  }
+  __syncthreads();
+  // 4: second factor along p2 (line jobs per field): G_k = MP B_k + KP A_k -> J_k slots
+  for (int t = tid; t < 24 * P; t += nt) {
+    const int f = t / (4 * P), rem = t - f * 4 * P;
+    const int fld = rem / P, p1 = rem - fld * P;
+    real ev[HPE], od[HPE], g[P];
+    load_fold(FSLOT(f, sB0 + fld) + p1, P, ev, od);
+    pp_line<2>(ev, od, g);
+    if (fld) {
+      real h[P];
+      load_fold(FSLOT(f, sA0 + fld) + p1, P, ev, od);
+      pp_line<3>(ev, od, h);
+#pragma unroll
+      for (int i = 0; i < P; ++i) g[i] += h[i];
+    }
+    real *G = FSLOT(f, sJ0 + fld) + p1;
+#pragma unroll
+    for (int i = 0; i < P; ++i) G[i * P] = g[i];
+  }
+  __syncthreads();
+  // corner side of face 0 (r = r_1 of the edge, psi = psi_1 of the vertex-edge
+  // neighbourhood): minus the transposed corner traces of the weighted jumps,
+  // y_c[k] = -sum_p1 g0[k][p1] - s_z sum_m D[m][k] sum_p1 g2[m][p1] (the
+  // corner's derivatives along x and y vanish), stored per (slot, rhs) for the
+  // corner kernel
+  if (corner_f0(COEF) && A.cscr && !A.self_only) {
+    const int slot = A.cslot[2 * e];
+    if (slot >= 0) {
+      for (int k = tid; k < P; k += nt) {
+        real s0 = 0, s2 = 0;
+        for (int p1 = 0; p1 < P; ++p1) s0 += FSLOT(0, sJ0)[k * P + p1];
+        for (int m = 0; m < P; ++m) {
+          real g2 = 0;
+          for (int p1 = 0; p1 < P; ++p1) g2 += FSLOT(0, sJ2)[m * P + p1];
+          s2 += Ds[m * P + k] * g2;
+        }
+        A.cscr[((int64_t)slot * A.n_rhs + r) * hpse::CSCR_STRIDE + k] = -(s0 + geo_e[2] * s2);
+      }
+    }
+  }
+  // corner side of face 4 (rho = rho_1 of the vertex, zeta = zeta_1 of the
+  // vertex-edge neighbourhood): the corner constant's trace is 1 at every face
+  // node, so y_c = -sum of the weighted jump of u over the face
+  if (corner_f4(COEF) && A.cscr && !A.self_only && tid == 0) {
+    const int slot = A.cslot[2 * e + 1];
+    if (slot >= 0) {
+      real s0 = 0;
+      for (int t = 0; t < P2; ++t) s0 += FSLOT(4, sJ0)[t];
+      A.cscr[((int64_t)slot * A.n_rhs + r) * hpse::CSCR_STRIDE] = -s0;
+    }
+  }
+  // 5: transposed tangential derivatives (line jobs): U1 = c1 D^T G1 along p1,
+  // U2 = c2 D^T G2 along p2 (c = the tangential scale on interior faces, 1 on
+  // Dirichlet faces)
+  for (int t = tid; t < 12 * P; t += nt) {
+    const int dir = t / (6 * P), rem = t - dir * 6 * P;
+    const int f = rem / P, ln = rem - f * P;
+    const int a = f >> 1;
+    const int tax = dir ? ((a == 2) ? 1 : 2) : ((a == 0) ? 1 : 0);
+    const int ob = dir ? ln : ln * P, os = dir ? P : 1;
+    const real c = A.nbr[(int64_t)e * 6 + f] != -1 ? geo_e[tax] : (real)1;
+    real ev[HPE], od[HPE], u[P];
+    load_fold(FSLOT(f, dir ? sJ2 : sJ1) + ob, os, ev, od);
+    pp_line<1>(ev, od, u);
+    real *U = FSLOT(f, dir ? sA2 : sA1) + ob;
+#pragma unroll
+    for (int m = 0; m < P; ++m) U[m * os] = c * u[m];
+  }
+  __syncthreads();
+  // 6: gather onto the nodes of the element: per face the face layer takes
+  // G0 + U1 + U2, every node of a normal line D[nend][n] s_a G3
+  for (int t = tid; t < P3; t += nt) {
+    const int i = t % P, j = (t / P) % P, k = t / P2;
+    real acc = 0;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      const int a = f >> 1, nend = (f & 1) ? P - 1 : 0;
+      const int n = a == 0 ? i : (a == 1 ? j : k);
+      const int p1 = a == 0 ? j : i;
+      const int p2 = a == 2 ? j : k;
+      const int sp = p2 * P + p1;
+      acc += Ds[nend * P + n] * (fsc[f] * FSLOT(f, sJ3)[sp]);
+      if (n == nend) acc += FSLOT(f, sJ0)[sp] + FSLOT(f, sA1)[sp] + FSLOT(f, sA2)[sp];
+    }
+    sy[t] += acc;
+  }
+  __syncthreads();
+#undef FSLOT
+}
+
 // warp-uniform dispatch of a runtime chunk index to its compile-time instance
 #define HPSE_DISPATCH4(NC, c, CALL)            \
   do {                                         \
@@ -653,7 +700,7 @@ __device__ __forceinline__ void x_rev_chunk(const real *X0, const real *X1, cons
 // ---------------------------------------------------------------------------
 // Operator apply: y = A u  (volume + faces), one CTA per (element, rhs).
 // Shared memory: su[P3] | X[NX][QP2] | T region (T fields, then sy and the
-// face scratch) | D, MP, KP copies | FP64 reduction buffer (16-byte aligned).
+// face scratch) | D copy, per-face scales | FP64 reduction buffer (16-byte aligned).
 // ---------------------------------------------------------------------------
 template <int COEF>
 struct ApplyLayout {
@@ -676,7 +723,7 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
   real *su = reinterpret_cast<real *>(smem_raw);
   real *sX = su + P3;               // X0 | X2 | (X1)
   real *sT = sX + L::NX * QP2;      // T00 | TL | (T10) | (T01)
-  real *stab = sT + L::T_REGION;    // D | MP | KP (runtime-indexed copies for the face phase)
+  real *stab = sT + L::T_REGION;    // D (runtime-indexed copy for the face gather) | per-face scales
   double *red = reinterpret_cast<double *>(smem_raw + L::RED_OFF);
   static_assert(L::RED_OFF % 16 == 0, "reduction buffer must be 16-byte aligned");
   real *X0 = sX, *X2 = sX + QP2, *X1 = sX + 2 * QP2;
@@ -693,11 +740,7 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
   const int tid = threadIdx.x;
   constexpr int nt = NT;
 
-  for (int t = tid; t < P2; t += nt) {
-    stab[t] = c_tab.D[t];
-    stab[P2 + t] = c_tab.MP[t];
-    stab[2 * P2 + t] = c_tab.KP[t];
-  }
+  for (int t = tid; t < P2; t += nt) stab[t] = c_tab.D[t];
   if (MODE != MODE_TRANSPOSE) {
     if (MODE == MODE_PCG) {
       const double bt = A.beta[A.prob[e] * A.n_rhs + r];
@@ -928,7 +971,7 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
 
   // ---- faces ---------------------------------------------------------------
   if (MODE != MODE_TRANSPOSE && !A.skip_faces)
-    face_phase<COEF, MODE>(A, e, r, su, sy, sT + P3, stab, stab + P2, stab + 2 * P2, geo_e);
+    face_phase<COEF, MODE>(A, e, r, su, sy, sT + P3, stab, geo_e, stab + P2);
 
   // ---- store (and the p.q partial of PCG) --------------------------------
   double part = 0.0;

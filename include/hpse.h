@@ -250,7 +250,10 @@ hpse_status hpse_apply_preconditioner(hpse_mesh *m, int32_t prec, const void *r,
  * an FP32 copy); the preconditioner is then z_e = X^T X r_e.  Device memory:
  * 12 n(n+1)/2 bytes per element with n = (W+1)^3 (3.3 GB for 512 elements of
  * W = 8), plus two vectors of n_rhs*ndof and, during the call, one FP64 copy
- * of the blocks and 2 x 64 probe vectors (capped at 2 GB each).  Selects
+ * of the blocks and 2 x 64 probe vectors (capped at 2 GB each); from 32
+ * right-hand sides on also the FP32 factor as 128 x 128 tiles of X and of X^T
+ * for the tensor-core products (8 ceil(n/128)(ceil(n/128)+1) x 16384 bytes per
+ * element: 1.38 GB for 512 elements of W = 8).  Selects
  * HPSE_PRECOND_BLOCK on success.  hpse_set_data does not rebuild it (a
  * preconditioner from older data stays symmetric positive definite, only
  * less effective).  Synchronous.  Errors: HPSE_ERR_NO_DATA before
@@ -261,14 +264,18 @@ hpse_status hpse_setup_block_preconditioner(hpse_mesh *m);
 /* Tile shape of the element-block preconditioner's two triangular products,
  * per degree W and precision: hpse_setup_block_preconditioner times every
  * candidate shape for the mesh's right-hand-side count on the factors it has
- * just built (variants 0-2 for >= 32 right-hand sides, 3-4 for 2..31, 5-7 for
- * one; 2, 4 and 6 in FP32 only) and keeps the fastest.  hpse_block_tile
- * returns the chosen variant, its tile (rows x right-hand sides per CTA) and,
- * if ms is not NULL, the measured milliseconds of each of the 8 variants (0
- * for those not tried); HPSE_ERR_NO_DATA before the set-up.
- * hpse_set_block_tile overrides the choice (HPSE_ERR_INVALID_ARG for a
- * variant that does not exist in that precision).  No counterpart in the
- * thesis. */
+ * just built (variants 0-2 and 8 for >= 32 right-hand sides, 3-4 for 2..31,
+ * 5-7 for one; 2, 4, 6 and 8 in FP32 only) and keeps the fastest.  Variants
+ * 0-7 are FP32/FP64 CUDA-core tiles; variant 8 runs both products on the
+ * tensor cores (tcgen05, 128 rows x 64 right-hand sides per CTA, each FP32
+ * operand split into two TF32 parts, three MMAs per product, FP32
+ * accumulation in tensor memory).  hpse_block_tile returns the chosen
+ * variant, its tile (rows x right-hand sides per CTA) and, if ms is not NULL,
+ * the measured milliseconds of each of the 9 variants (0 for those not tried);
+ * HPSE_ERR_NO_DATA before the set-up.  hpse_set_block_tile overrides the
+ * choice (HPSE_ERR_INVALID_ARG for a variant that does not exist in that
+ * precision, or variant 8 when its tiles were not built).  No counterpart in
+ * the thesis. */
 hpse_status hpse_block_tile(const hpse_mesh *m, int32_t W, int32_t prec, int32_t *variant, int32_t *tile_rows,
                             int32_t *tile_rhs, float *ms);
 hpse_status hpse_set_block_tile(hpse_mesh *m, int32_t W, int32_t prec, int32_t variant);

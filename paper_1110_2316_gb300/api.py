@@ -134,7 +134,7 @@ class Mesh:
     def block_tile(self, W, prec):
         """(variant, (tile rows, tile rhs), ms per variant) chosen by the autotuner."""
         v, tr, tc = C.c_int32(), C.c_int32(), C.c_int32()
-        ms = np.zeros(8, dtype=np.float32)
+        ms = np.zeros(9, dtype=np.float32)
         check(self._lib.hpse_block_tile(self._h, int(W), int(prec), C.byref(v), C.byref(tr), C.byref(tc),
                                         ms.ctypes.data_as(C.c_void_p)), "hpse_block_tile")
         return int(v.value), (int(tr.value), int(tc.value)), ms

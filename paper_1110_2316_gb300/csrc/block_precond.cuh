@@ -274,15 +274,20 @@ __global__ void k_bj_dot(BjArgs A, const T *z, const T *r, double *part) {
 // CTA), picked per degree group and precision by timing the candidates of
 // the right-hand-side count on the actual factors (bj_candidates); variants
 // 2, 4 and 6 exceed 48 KB of static shared memory in FP64 and exist in FP32
-// only.
-constexpr int BJ_NVAR = 8;
-constexpr int BJ_TILE[BJ_NVAR][2] = {{64, 64}, {128, 32}, {256, 16}, {128, 8}, {256, 8}, {128, 1}, {256, 1}, {64, 1}};
-inline bool bj_variant_ok(int v, bool fp32) { return v >= 0 && v < BJ_NVAR && (fp32 || (v != 2 && v != 4 && v != 6)); }
+// only; variant 8 is the tensor-core form (bj_tc.cuh: 128 rows x 64
+// right-hand sides, 3xTF32), FP32 only, offered from 32 right-hand sides on.
+constexpr int BJ_NVAR = 9;
+constexpr int BJ_TC = 8;
+constexpr int BJ_TILE[BJ_NVAR][2] = {{64, 64}, {128, 32}, {256, 16}, {128, 8}, {256, 8},
+                                     {128, 1}, {256, 1},  {64, 1},   {128, 64}};
+inline bool bj_variant_ok(int v, bool fp32) {
+  return v >= 0 && v < BJ_NVAR && (fp32 || (v != 2 && v != 4 && v != 6 && v != BJ_TC));
+}
 inline int bj_candidates(int n_rhs, bool fp32, int *v) {
   int n = 0;
-  const int all[3][3] = {{0, 1, 2}, {3, 4, -1}, {5, 6, 7}};
+  const int all[3][4] = {{0, 1, 2, BJ_TC}, {3, 4, -1, -1}, {5, 6, 7, -1}};
   const int *c = all[n_rhs >= 32 ? 0 : (n_rhs >= 2 ? 1 : 2)];
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 4; ++i)
     if (c[i] >= 0 && bj_variant_ok(c[i], fp32)) v[n++] = c[i];
   return n;
 }

@@ -223,7 +223,9 @@ struct hpse_mesh {
   DevBuf d_bj64, d_bj32;      // X = L^{-1} per element, packed lower triangle
   DevBuf bj_t64, bj_t32;      // scratch vector X r of the preconditioner
   int bj_var[HPSE_MAX_W + 1][2] = {};  // tile variant of the products per degree and precision (autotuned)
-  float bj_ms[HPSE_MAX_W + 1][2][8] = {};  // measured time per variant (ms; 0: not a candidate)
+  float bj_ms[HPSE_MAX_W + 1][2][9] = {};  // [BJ_NVAR]  // measured time per variant (ms; 0: not a candidate)
+  DevBuf d_bjt, d_bjt_off;    // tensor-core form: FP32 tiles of X and X^T per element, their offsets
+  DevBuf d_bjt_err;           // int32: set by a tensor-core product whose bounded wait expired
   int threads[2][2][HPSE_MAX_W + 1];  // [kind][prec][W]
   // one stream per degree group: per-degree launches of one operator or
   // preconditioner application run concurrently (fork/join through events,
@@ -289,7 +291,9 @@ struct ElemVecArgs {
 };
 
 #include "block_precond.cuh"
+#include "bj_tc.cuh"
 #include "edge.cuh"
+static_assert(BJ_NVAR == 9, "bj_ms holds one time per tile variant");
 
 // per (element, rhs) block: generic vector kernels with FP64 partials
 template <typename TA, typename TB>
@@ -980,6 +984,36 @@ static BjArgs bj_args(const hpse_mesh *m, const Group &g, int n_rhs) {
   return a;
 }
 
+// z = X^T (X r) for a group on the tensor cores (FP32, variant BJ_TC)
+static hpse_status bj_tc_pair(hpse_mesh *m, const Group &g, int n_rhs, const float *r, float *t, float *z,
+                              cudaStream_t s) {
+  if (!m->d_bjt.p || !m->d_bjt_err.p) return HPSE_ERR_INVALID_ARG;
+  BjTcArgs a;
+  a.elems = g.elems.as<int32_t>();
+  a.n_group = g.n;
+  a.n = (g.W + 1) * (g.W + 1) * (g.W + 1);
+  a.n_rhs = n_rhs;
+  a.ndof = m->ndof;
+  a.dof_off = m->d_dof_off.as<int64_t>();
+  a.tile_off = m->d_bjt_off.as<int64_t>();
+  a.err = m->d_bjt_err.as<int32_t>();
+  const dim3 grid(g.n * ((a.n + BJT - 1) / BJT), (n_rhs + BJT_N - 1) / BJT_N);
+  k_bj_tc<false><<<grid, BJT_THREADS, BJT_SMEM, s>>>(a, m->d_bjt.as<float>(), r, t);
+  k_bj_tc<true><<<grid, BJT_THREADS, BJT_SMEM, s>>>(a, m->d_bjt.as<float>(), t, z);
+  CK(cudaGetLastError());
+  return HPSE_OK;
+}
+
+template <typename T>
+static hpse_status bj_products(hpse_mesh *m, const Group &g, const BjArgs &a, const T *X, const T *r, T *t, T *z,
+                               cudaStream_t s, int v) {
+  if constexpr (sizeof(T) == 4) {
+    if (v == BJ_TC) return bj_tc_pair(m, g, a.n_rhs, r, t, z, s);
+  }
+  CK(bj_apply_group<T>(a, X, r, t, z, s, v));
+  return HPSE_OK;
+}
+
 // element-block preconditioner for every degree group: PCG mode fuses the
 // update x += alpha p, r -= alpha q and the partials r.r, z.r around z = X^T X r
 template <typename T>
@@ -996,12 +1030,14 @@ static hpse_status launch_bj_all(hpse_mesh *m, int mode, const PrecArgsT<T> &b, 
     if (mode == MODE_PCG) {
       k_bj_update<T><<<items, 128, 0, gs>>>(a, b.prob, b.alpha, b.x, b.r, b.p, b.q, b.part_rr);
       CK(cudaGetLastError());
-      CK(bj_apply_group<T>(a, X, b.r, t, b.zout, gs, m->bj_var[g.W][sizeof(T) == 8 ? 0 : 1]));
+      hpse_status st = bj_products<T>(m, g, a, X, b.r, t, b.zout, gs, m->bj_var[g.W][sizeof(T) == 8 ? 0 : 1]);
+      if (st != HPSE_OK) return st;
       k_bj_dot<T><<<items, 128, 0, gs>>>(a, b.zout, b.r, b.part_rz);
       CK(cudaGetLastError());
       g_launches += 4;
     } else {
-      CK(bj_apply_group<T>(a, X, b.rin, t, b.zout, gs, m->bj_var[g.W][sizeof(T) == 8 ? 0 : 1]));
+      hpse_status st = bj_products<T>(m, g, a, X, b.rin, t, b.zout, gs, m->bj_var[g.W][sizeof(T) == 8 ? 0 : 1]);
+      if (st != HPSE_OK) return st;
       g_launches += 2;
     }
   }
@@ -1880,6 +1916,32 @@ extern "C" hpse_status hpse_setup_block_preconditioner(hpse_mesh *m) {
   int32_t h_fail = 0;
   CK(cudaMemcpy(&h_fail, fail.p, sizeof(int32_t), cudaMemcpyDeviceToHost));
   if (h_fail) return HPSE_ERR_BREAKDOWN;
+  // tensor-core form (a candidate from 32 right-hand sides on): FP32 tiles of
+  // X and X^T per element
+  m->d_bjt = DevBuf();
+  m->d_bjt_off = DevBuf();
+  if (m->n_rhs >= 32 && total > 0) {
+    std::vector<int64_t> toff(E + 1, 0);
+    for (int e = 0; e < E; ++e) {
+      const int n = (m->W[e] + 1) * (m->W[e] + 1) * (m->W[e] + 1);
+      toff[e + 1] = toff[e] + 2 * (int64_t)bjt_blocks(n) * BJT_TILE;
+    }
+    if (m->d_bjt.alloc((size_t)toff[E] * sizeof(float)) != cudaSuccess) return HPSE_ERR_OOM;
+    CK(upload(m->d_bjt_off, toff));
+    if (!m->d_bjt_err.p) CK(m->d_bjt_err.alloc(sizeof(int32_t)));
+    CK(cudaMemset(m->d_bjt_err.p, 0, sizeof(int32_t)));
+    CK(raise_smem((const void *)k_bj_tc<false>, m->device, BJT_SMEM));
+    CK(raise_smem((const void *)k_bj_tc<true>, m->device, BJT_SMEM));
+    for (size_t gi = 0; gi < m->groups.size(); ++gi) {
+      const Group &g = m->groups[gi];
+      const BjArgs ba = bj_args(m, g, m->n_rhs);
+      const int n = (g.W + 1) * (g.W + 1) * (g.W + 1);
+      k_bj_tile<<<g.n * 2 * bjt_blocks(n), 256, 0, s>>>(ba, m->d_bjt_off.as<int64_t>(), m->d_bj64.as<double>(),
+                                                         m->d_bjt.as<float>());
+      CK(cudaGetLastError());
+      ++g_launches;
+    }
+  }
   // autotuner: time every candidate tile shape of the two triangular products
   // on the factors just built (right-hand-side count of the mesh, per degree
   // group and precision; one warm-up, then the mean of 3 launches by CUDA
@@ -1896,27 +1958,36 @@ extern "C" hpse_status hpse_setup_block_preconditioner(hpse_mesh *m) {
       const Group &g = m->groups[gi];
       const BjArgs ba = bj_args(m, g, m->n_rhs);
       for (int pi = 0; pi < 2; ++pi) {
-        int cand[3];
+        int cand[4];
         const int nc2 = bj_candidates(m->n_rhs, pi == 1, cand);
         float best = 1e30f;
-        for (int k = 0; k < 8; ++k) m->bj_ms[g.W][pi][k] = 0.0f;
+        for (int k = 0; k < BJ_NVAR; ++k) m->bj_ms[g.W][pi][k] = 0.0f;
         for (int ci = 0; ci < nc2; ++ci) {
           const int v = cand[ci];
+          if (v == BJ_TC && !m->d_bjt.p) continue;
           float ms = 0.0f;
           for (int rep = 0; rep < 4; ++rep) {
             if (rep == 1) CK(cudaEventRecord(e0, s));
             if (pi == 0)
               CK(bj_apply_group<double>(ba, m->d_bj64.as<double>(), tin.as<double>(), m->bj_t64.as<double>(),
                                         tout.as<double>(), s, v));
-            else
-              CK(bj_apply_group<float>(ba, m->d_bj32.as<float>(), tin.as<float>(), m->bj_t32.as<float>(),
-                                       tout.as<float>(), s, v));
+            else {
+              const hpse_status st = bj_products<float>(m, g, ba, m->d_bj32.as<float>(), tin.as<float>(),
+                                                        m->bj_t32.as<float>(), tout.as<float>(), s, v);
+              if (st != HPSE_OK) return st;
+            }
             g_launches += 2;
           }
           CK(cudaEventRecord(e1, s));
           CK(cudaEventSynchronize(e1));
           CK(cudaEventElapsedTime(&ms, e0, e1));
           ms /= 3.0f;
+          if (v == BJ_TC) {
+            // a tensor-core product whose bounded wait expired is not a candidate
+            int32_t h_err = 0;
+            CK(cudaMemcpy(&h_err, m->d_bjt_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost));
+            if (h_err) continue;
+          }
           m->bj_ms[g.W][pi][v] = ms;
           if (ms < best) {
             best = ms;
@@ -1949,6 +2020,7 @@ extern "C" hpse_status hpse_block_tile(const hpse_mesh *m, int32_t W, int32_t pr
 extern "C" hpse_status hpse_set_block_tile(hpse_mesh *m, int32_t W, int32_t prec, int32_t variant) {
   if (!m || W < 1 || W > HPSE_MAX_W || (prec != HPSE_FP64 && prec != HPSE_FP32)) return HPSE_ERR_INVALID_ARG;
   if (!bj_variant_ok(variant, prec == HPSE_FP32)) return HPSE_ERR_INVALID_ARG;
+  if (variant == BJ_TC && !m->d_bjt.p) return HPSE_ERR_INVALID_ARG;
   CK(cudaSetDevice(m->device));
   CK(cudaDeviceSynchronize());
   drop_graphs(m);

@@ -70,12 +70,20 @@ __host__ __device__ constexpr bool odd_pp(int t) { return t < 2; }
 #endif
 #define PAD32(n) ((((n) + 31) / 32) * 32)
 constexpr int NT_RAW = PAD32(Q2);
+#if defined(HPSE_APPLY_NT)
+constexpr int NT = HPSE_APPLY_NT;  // set at build time (launch-shape experiments)
+#else
 constexpr int NT = NT_RAW < 64 ? 64 : (NT_RAW > HPSE_APPLY_MAXT ? HPSE_APPLY_MAXT : NT_RAW);
+#endif
 static_assert(NT % 32 == 0, "warp-uniform line loops need a whole number of warps per CTA");
 // FP32: enough resident CTAs for ~30 warps per SM (measured best on GB300 for
 // W = 8: 3 CTAs of 320 threads); FP64 is bound by the FP64 pipe at any occupancy
 constexpr int APPLY_MINB_RAW = 960 / NT;
+#if defined(HPSE_APPLY_MINB)
+constexpr int APPLY_MINB = HPSE_APPLY_MINB;  // set at build time (launch-shape experiments)
+#else
 constexpr int APPLY_MINB = sizeof(real) == 8 ? 1 : (APPLY_MINB_RAW < 1 ? 1 : (APPLY_MINB_RAW > 4 ? 4 : APPLY_MINB_RAW));
+#endif
 
 
 // 1-D tables of this degree (filled by upload_tables):
@@ -201,7 +209,12 @@ template <int L>
 struct Lines {
   static constexpr int PADL = PAD32(L);
   static constexpr int NC_RAW = NT / PADL;
-  static constexpr int NC = NC_RAW < 1 ? 1 : (NC_RAW > 2 ? 2 : NC_RAW);
+#if defined(HPSE_LINES_NC)
+  static constexpr int NC_MAX = HPSE_LINES_NC;  // set at build time (launch-shape experiments)
+#else
+  static constexpr int NC_MAX = 2;
+#endif
+  static constexpr int NC = NC_RAW < 1 ? 1 : (NC_RAW > NC_MAX ? NC_MAX : NC_RAW);
 };
 template <int CI, int NC, int N>
 struct Range {

@@ -177,10 +177,10 @@ def test_block_tile_autotuner(api, n_rhs):
     pb = wl.Problem(base.mesh, base.f * n_rhs, base.g * n_rhs, base.a, base.grad_a)
     m = _mesh(api, pb, n_rhs)
     m.setup_block_preconditioner()
-    cand = {1: (5, 6, 7), 5: (3, 4), 40: (0, 1, 2)}[n_rhs]
+    cand = {1: (5, 6, 7), 5: (3, 4), 40: (0, 1, 2, 8)}[n_rhs]
     for prec, dt, tol in ((api.FP64, torch.float64, 1e-13), (api.FP32, torch.float32, 1e-5)):
         v, tile, ms = m.block_tile(3, prec)
-        ok = [c for c in cand if prec == api.FP32 or c not in (2, 4, 6)]
+        ok = [c for c in cand if prec == api.FP32 or c not in (2, 4, 6, 8)]
         assert v in ok and all(ms[c] > 0 for c in ok), (v, ms)
         r = torch.tensor(wl.random_dofs(n_rhs * m.ndof, 3), dtype=dt, device="cuda")
         outs = []
@@ -194,4 +194,46 @@ def test_block_tile_autotuner(api, n_rhs):
     from paper_1110_2316_gb300._lib import HpseError
     with pytest.raises(HpseError):
         m.set_block_tile(3, api.FP64, 2)  # FP32-only shape
+    with pytest.raises(HpseError):
+        m.set_block_tile(3, api.FP64, 8)  # the tensor-core form is FP32 only
+    if n_rhs < 32:
+        with pytest.raises(HpseError):
+            m.set_block_tile(3, api.FP32, 8)  # no tiles built below 32 right-hand sides
+    m.close()
+
+
+@pytest.mark.parametrize("W", [3, 5, 6])
+@pytest.mark.parametrize("n_rhs", [33, 70])
+def test_block_tensor_core_products(api, W, n_rhs):
+    # variant 8: both triangular products on the tensor cores (3xTF32, FP32
+    # accumulation); blocks of n = 64, 216, 343 (one to three 128-row tiles, the
+    # last one ragged), one or two 64-rhs tiles (70: the second holds 6).  Bound:
+    # the FP32 bound of the CUDA-core products (2 n eps32 |X|^T |X| |r| per
+    # element) against the exact block solve, and agreement with variant 0.
+    base = wl.varcoef_manufactured(n=(2, 1, 1), W=W)
+    pb = wl.Problem(base.mesh, base.f * n_rhs, base.g * n_rhs, base.a, base.grad_a)
+    disc = Discretisation(base)
+    m = _mesh(api, pb, n_rhs)
+    m.setup_block_preconditioner()
+    R = wl.random_dofs(n_rhs * disc.ndof, 17).reshape(n_rhs, disc.ndof)
+    rt = torch.tensor(R.ravel(), dtype=torch.float32, device="cuda")
+    outs = {}
+    for v in (8, 0):
+        m.set_block_tile(W, api.FP32, v)
+        z = torch.full_like(rt, float("nan"))
+        m.apply_preconditioner(rt, z)
+        torch.cuda.synchronize()
+        outs[v] = z.double().cpu().numpy().reshape(n_rhs, disc.ndof)
+    assert np.isfinite(outs[8]).all()
+    blocks = [element_block(disc, e) for e in range(disc.E)]
+    Xs = [np.linalg.inv(np.linalg.cholesky(B)) for B in blocks]
+    for e in range(disc.E):
+        s = slice(disc.off[e], disc.off[e + 1])
+        n = blocks[e].shape[0]
+        for k in range(n_rhs):
+            zo = np.linalg.solve(blocks[e], R[k][s])
+            X = Xs[e]
+            bound = 2 * n * EPS32 * np.linalg.norm(np.abs(X).T @ (np.abs(X) @ np.abs(R[k][s])))
+            assert np.linalg.norm(outs[8][k][s] - zo) <= bound, (W, n_rhs, k, e)
+            assert np.linalg.norm(outs[8][k][s] - outs[0][k][s]) <= bound, (W, n_rhs, k, e)
     m.close()

@@ -15,7 +15,7 @@
 // bk >= bi (row order), so that both products read K-major rows.
 //
 // One CTA (4 warps) per (element, 128-row tile, 64 right-hand sides): K in
-// chunks of 32 (one 128-byte row per operand row), two shared-memory stages of
+// chunks of 32 (one 128-byte row per operand row), BJT_STAGES shared-memory stages of
 // A hi/lo (128 x 32) and B hi/lo (64 x 32) in the canonical 128-byte-swizzled
 // K-major layout (8-row atoms of 1 KB, 16-byte chunk j of row m at j ^ (m % 8)),
 // filled from registers (the split needs them anyway; the next chunk's global
@@ -34,7 +34,13 @@ constexpr int BJT_THREADS = 128;
 constexpr int BJT_A_BYTES = BJT * BJT_K * 4;    // 16 KB
 constexpr int BJT_B_BYTES = BJT_N * BJT_K * 4;  // 8 KB
 constexpr int BJT_STAGE_BYTES = 2 * BJT_A_BYTES + 2 * BJT_B_BYTES;
-constexpr size_t BJT_SMEM = 2 * (size_t)BJT_STAGE_BYTES + 1024;  // two stages + alignment slack
+#if defined(HPSE_BJT_STAGES)
+constexpr int BJT_STAGES = HPSE_BJT_STAGES;  // set at build time (pipeline-depth experiments)
+#else
+constexpr int BJT_STAGES = 1;  // 4 CTAs per SM hide more load latency than a second stage (measured)
+#endif
+constexpr int BJT_MINB = BJT_STAGES == 1 ? 4 : 2;  // CTAs per SM that the shared memory allows
+constexpr size_t BJT_SMEM = BJT_STAGES * (size_t)BJT_STAGE_BYTES + 1024;  // stages + alignment slack
 constexpr int BJT_TILE = BJT * BJT;      // floats per tile
 constexpr int BJT_TMEM_COLS = 64;
 
@@ -97,9 +103,9 @@ __device__ __forceinline__ bool bjt_wait(uint32_t bar, uint32_t parity) {
 // group's elements.  grid: (n_group * ceil(n / 128), ceil(n_rhs / 64)), 128 threads,
 // BJT_SMEM bytes of dynamic shared memory.
 template <bool TRANS>
-__global__ void __launch_bounds__(BJT_THREADS) k_bj_tc(BjTcArgs A, const float *Xt, const float *in, float *out) {
+__global__ void __launch_bounds__(BJT_THREADS, BJT_MINB) k_bj_tc(BjTcArgs A, const float *Xt, const float *in, float *out) {
   extern __shared__ unsigned char bjt_raw[];
-  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(8) uint64_t bar[BJT_STAGES];
   __shared__ uint32_t s_tmem;
   __shared__ int s_bad;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -127,8 +133,8 @@ __global__ void __launch_bounds__(BJT_THREADS) k_bj_tc(BjTcArgs A, const float *
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bjt_smem(&bar[0])) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bjt_smem(&bar[1])) : "memory");
+    for (int i = 0; i < BJT_STAGES; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bjt_smem(&bar[i])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_bad = 0;
   }
@@ -190,8 +196,10 @@ __global__ void __launch_bounds__(BJT_THREADS) k_bj_tc(BjTcArgs A, const float *
   load(kc0);
   int last = -1;
   for (int kc = kc0; kc < kc1; ++kc) {
-    const int it = kc - kc0, st = it & 1;
-    if (it >= 2 && tid == 0 && !bjt_wait(bjt_smem(&bar[st]), ((it - 2) >> 1) & 1)) s_bad = 1;
+    const int it = kc - kc0, st = it % BJT_STAGES;
+    // the MMAs that last read this stage (iteration it - BJT_STAGES) are done
+    if (it >= BJT_STAGES && tid == 0 && !bjt_wait(bjt_smem(&bar[st]), ((it - BJT_STAGES) / BJT_STAGES) & 1))
+      s_bad = 1;
     __syncthreads();
     if (s_bad) break;
     store(st);
@@ -226,7 +234,9 @@ __global__ void __launch_bounds__(BJT_THREADS) k_bj_tc(BjTcArgs A, const float *
     last = it;
   }
   // the last commit covers every MMA issued before it
-  if (tid == 0 && !s_bad && last >= 0 && !bjt_wait(bjt_smem(&bar[last & 1]), (last >> 1) & 1)) s_bad = 1;
+  if (tid == 0 && !s_bad && last >= 0 &&
+      !bjt_wait(bjt_smem(&bar[last % BJT_STAGES]), (last / BJT_STAGES) & 1))
+    s_bad = 1;
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (!s_bad) {

@@ -339,7 +339,7 @@ def run_adjoint(args, local):
         ut = fld.separable(lambda x: torch.sin(pi * x), lambda y: torch.sin(pi * y), lambda z: torch.sin(pi * z))
         f = torch.ones(1, m.nquad, dtype=torch.float64, device=dev)
         a, ga = fld(theta)
-        m.set_data(f=f.cpu().numpy(), a=a.cpu().numpy(), grad_a=ga.cpu().numpy())
+        m.set_data(f=f, a=a, grad_a=ga)
         t_p = time.perf_counter()
         if args.precond == "block":
             # built once from the data at theta and kept for every later solve
@@ -374,7 +374,7 @@ def run_adjoint(args, local):
         O(error / h)."""
         a, ga = c["fld"](theta)
         m = c["m"]
-        m.set_data(f=c["f"].cpu().numpy(), a=a.cpu().numpy(), grad_a=ga.cpu().numpy())
+        m.set_data(f=c["f"], a=a, grad_a=ga)
         b = torch.empty_like(u0)
         m.get_rhs(b)
         r = torch.empty_like(u0)
@@ -415,7 +415,7 @@ def run_adjoint(args, local):
     _, g = gradient(cf, th0, api.FP64, 1e-10)
     fd_grad_reports = list(cf["m"].solve_log)
     a0, ga0 = cf["fld"](th0)
-    cf["m"].set_data(f=cf["f"].cpu().numpy(), a=a0.cpu().numpy(), grad_a=ga0.cpu().numpy())
+    cf["m"].set_data(f=cf["f"], a=a0, grad_a=ga0)
     u0 = torch.zeros(cf["m"].ndof, dtype=torch.float64, device=dev)
     cf["m"].pcg_solve(u0, tol=1e-12, prec=api.FP64, max_iter=20000, raise_on_error=False)
     rng = np.random.Generator(np.random.PCG64(8))

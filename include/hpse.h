@@ -219,11 +219,18 @@ hpse_status hpse_query_points(const hpse_mesh *m, double *vol_axes, double *face
 int64_t hpse_n_boundary_faces(const hpse_mesh *m);
 
 /* Upload data and build b = S^T M d in FP64 on the device (Section 5.3: the
- * right-hand side of the normal equations from the sampled data).  data and
- * its arrays are copied during the call.  HPSE_ERR_INVALID_ARG for missing
- * arrays or a non-positive coefficient a (ellipticity).  Drops captured
- * solver graphs (they refer to the previous data).  Synchronous. */
-hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data);
+ * right-hand side of the normal equations from the sampled data, eq. 2.1-2.2).
+ * The arrays of data are FP64 and either all host or all device (CUDA device
+ * or managed) memory; the kind is read from the pointers.  Device data is
+ * read on `stream` (ordered after the caller's earlier work there) and the
+ * coefficient transform runs in a kernel, so no data crosses to the host.
+ * data and its arrays are copied during the call; the call returns after
+ * `stream` has finished its work (NULL: the legacy default stream).
+ * HPSE_ERR_INVALID_ARG for missing arrays, arrays in different memory kinds,
+ * or a coefficient a <= 0 or not finite (ellipticity; with device data the
+ * handle then has no data until a valid set is given).  Drops captured solver
+ * graphs (they refer to the previous data). */
+hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data, void *stream);
 
 /* y = A u, the normal operator of eq. (4.2) (Section 5.3), for all n_rhs
  * right-hand sides.  u, y: caller-owned device DOF vectors of n_rhs*ndof
@@ -306,17 +313,22 @@ hpse_status hpse_pcg_solve(hpse_mesh *m, const hpse_solve_opts *opts, double *x,
 hpse_status hpse_h1_error(hpse_mesh *m, const double *u, const double *ref,
                           const double *vq, const double *gq, double *out, void *stream);
 
-/* Residual map and its transpose (FP64; Section 5.3: the weighted PDE
- * residual of eq. (4.2) collocated on the (2W+1)^3 GLL points).
+/* Residual map and its transpose (Section 5.3: the weighted PDE residual of
+ * eq. (4.2) collocated on the (2W+1)^3 GLL points), box meshes.
  *   hpse_apply_residual:  z[r][q] = sqrt(w_q J) (L u_r - f_r)(x_q), with
  *                         L u = -a Lap u - grad a . grad u and the data of
- *                         hpse_set_data; u a device FP64 DOF vector, z device
- *                         FP64 [n_rhs][nquad].
+ *                         hpse_set_data; u a device DOF vector, z device
+ *                         [n_rhs][nquad], both of precision prec.
  *   hpse_apply_transpose: y = S^T z, the exact transpose of u -> z without the
- *                         data term (the backward of the residual map).
- * Both use a scratch buffer the handle allocates on first use. */
-hpse_status hpse_apply_residual(hpse_mesh *m, const double *u, double *z, void *stream);
-hpse_status hpse_apply_transpose(hpse_mesh *m, const double *z, double *y, void *stream);
+ *                         data term (the backward of the residual map); z and
+ *                         y device, of precision prec.
+ * prec: HPSE_FP64, or HPSE_FP32 (the sum factorisations in FP32 with the FP64
+ * tables and data rounded to FP32).  Asynchronous on `stream`.  Both use a
+ * scratch buffer the handle allocates on first use.  HPSE_ERR_INVALID_ARG for
+ * neighbourhood meshes, bad pointers or prec; HPSE_ERR_NO_DATA before
+ * hpse_set_data. */
+hpse_status hpse_apply_residual(hpse_mesh *m, int32_t prec, const void *u, void *z, void *stream);
+hpse_status hpse_apply_transpose(hpse_mesh *m, int32_t prec, const void *z, void *y, void *stream);
 
 /* Point values of a DOF vector (FP64): out[r][0..4][q] = v, dv/dx, dv/dy,
  * dv/dz, Lap v at the volume points (physical coordinates). */

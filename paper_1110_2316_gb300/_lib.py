@@ -61,7 +61,7 @@ SIGNATURES = {
     "hpse_nrhs": (C.c_int32, [C.c_void_p]),
     "hpse_query_points": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "hpse_n_boundary_faces": (C.c_int64, [C.c_void_p]),
-    "hpse_set_data": (C.c_int, [C.c_void_p, C.POINTER(Data)]),
+    "hpse_set_data": (C.c_int, [C.c_void_p, C.POINTER(Data), C.c_void_p]),
     "hpse_apply_operator": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "hpse_apply_preconditioner": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "hpse_setup_block_preconditioner": (C.c_int, [C.c_void_p]),
@@ -75,8 +75,8 @@ SIGNATURES = {
                                 C.c_void_p]),
     "hpse_h1_error_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                         C.c_void_p, C.c_void_p]),
-    "hpse_apply_residual": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
-    "hpse_apply_transpose": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hpse_apply_residual": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hpse_apply_transpose": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "hpse_eval_fields": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "hpse_apply_eval_transpose": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "hpse_quad_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),

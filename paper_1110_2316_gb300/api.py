@@ -120,11 +120,21 @@ class Mesh:
         return ax, fn[: self.n_boundary_faces]
 
     # -- data ---------------------------------------------------------------
-    def set_data(self, f, a=None, grad_a=None, g=None):
-        arrs = [None if v is None else np.ascontiguousarray(v, dtype=np.float64) for v in (f, a, grad_a, g)]
-        d = _lib.Data(*[None if v is None else v.ctypes.data_as(C.c_void_p) for v in arrs])
+    def set_data(self, f, a=None, grad_a=None, g=None, stream=None):
+        """Data at the query points: numpy arrays (host) or CUDA float64 torch
+        tensors (device, read on the current torch stream); not mixed."""
+        vals = (f, a, grad_a, g)
+        on_dev = [v is not None and not isinstance(v, np.ndarray) and getattr(v, "is_cuda", False) for v in vals]
+        if any(on_dev):
+            import torch
+            if not all(d for v, d in zip(vals, on_dev) if v is not None):
+                raise TypeError("set_data: give all data as host arrays or all as CUDA tensors")
+            arrs = [None if v is None else v.detach().to(torch.float64).contiguous() for v in vals]
+        else:
+            arrs = [None if v is None else np.ascontiguousarray(v, dtype=np.float64) for v in vals]
+        d = _lib.Data(*[_ptr(v) for v in arrs])
         self.data_version += 1
-        check(self._lib.hpse_set_data(self._h, C.byref(d)), "hpse_set_data")
+        check(self._lib.hpse_set_data(self._h, C.byref(d), _stream(stream)), "hpse_set_data")
 
     # -- preconditioner choice ------------------------------------------------
     def setup_block_preconditioner(self):
@@ -180,10 +190,12 @@ class Mesh:
 
     # -- residual map, point fields and adjoint data gradients (FP64) -------
     def apply_residual(self, u, z, stream=None):
-        check(self._lib.hpse_apply_residual(self._h, _ptr(u), _ptr(z), _stream(stream)), "hpse_apply_residual")
+        check(self._lib.hpse_apply_residual(self._h, _prec_of(u), _ptr(u), _ptr(z), _stream(stream)),
+              "hpse_apply_residual")
 
     def apply_transpose(self, z, y, stream=None):
-        check(self._lib.hpse_apply_transpose(self._h, _ptr(z), _ptr(y), _stream(stream)), "hpse_apply_transpose")
+        check(self._lib.hpse_apply_transpose(self._h, _prec_of(z), _ptr(z), _ptr(y), _stream(stream)),
+              "hpse_apply_transpose")
 
     def eval_fields(self, u, out, stream=None):
         check(self._lib.hpse_eval_fields(self._h, _ptr(u), _ptr(out), _stream(stream)), "hpse_eval_fields")

@@ -1,8 +1,8 @@
 """torch.autograd wrappers over the C ABI (argument marshalling only).
 
 * ``ResidualMap``: u -> z = sqrt(w J)(L u - f) at the volume points (the
-  weighted PDE residual of eq. (4.2), Section 5.3); backward = the
-  hand-written transpose kernel (hpse_apply_transpose).
+  weighted PDE residual of eq. (4.2), Section 5.3), FP64 or FP32 after u's
+  dtype; backward = the hand-written transpose kernel (hpse_apply_transpose).
 * ``PointValues``: u -> u(x_q) at the volume points; backward = the transpose
   of point evaluation (hpse_apply_eval_transpose).
 * ``Solve``: the data (f, a, grad a at the volume points; Dirichlet data g
@@ -17,7 +17,7 @@
   its own forward solve: if the mesh has been given other data in between,
   that solve's data is set again first (the mesh then keeps it).
 
-All tensors are CUDA float64 tensors; shapes: u [n_rhs * ndof], z and f
+All tensors are CUDA float64 tensors (ResidualMap: float64 or float32); shapes: u [n_rhs * ndof], z and f
 [n_rhs, nquad], a [nquad], grad_a [3, nquad].
 """
 from __future__ import annotations
@@ -27,10 +27,22 @@ import torch
 from .api import FP64
 
 
+def _data(t, like=None):
+    """A datum for Mesh.set_data: CUDA tensors stay on the device; host arrays
+    given beside device data (Dirichlet data g) are moved to f's device."""
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        return t.detach()
+    if like is not None and isinstance(like, torch.Tensor) and like.is_cuda:
+        return torch.as_tensor(t, dtype=torch.float64, device=like.device)
+    return t
+
+
 class ResidualMap(torch.autograd.Function):
     @staticmethod
     def forward(ctx, u, mesh):
-        z = torch.empty(mesh.n_rhs, mesh.nquad, dtype=torch.float64, device=u.device)
+        z = torch.empty(mesh.n_rhs, mesh.nquad, dtype=u.dtype, device=u.device)
         mesh.apply_residual(u.contiguous(), z)
         ctx.mesh = mesh
         return z
@@ -38,7 +50,7 @@ class ResidualMap(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gz):
         m = ctx.mesh
-        y = torch.empty(m.n_rhs * m.ndof, dtype=torch.float64, device=gz.device)
+        y = torch.empty(m.n_rhs * m.ndof, dtype=gz.dtype, device=gz.device)
         m.apply_transpose(gz.contiguous(), y)
         return y, None
 
@@ -64,11 +76,7 @@ class Solve(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, f, a, grad_a, mesh, g=None, tol=1e-12, prec=FP64, adjoint_prec=FP64, adjoint_tol=None):
-        def host(t):
-            if t is None:
-                return None
-            return t.detach().cpu().numpy() if isinstance(t, torch.Tensor) else t
-        mesh.set_data(f=host(f), a=host(a), grad_a=host(grad_a), g=host(g))
+        mesh.set_data(f=_data(f), a=_data(a), grad_a=_data(grad_a), g=_data(g, f))
         x = torch.zeros(mesh.n_rhs * mesh.ndof, dtype=torch.float64, device=f.device)
         rep = mesh.pcg_solve(x, tol=tol, prec=prec)
         if isinstance(getattr(mesh, "solve_log", None), list):
@@ -90,12 +98,7 @@ class Solve(torch.autograd.Function):
         if m.data_version != ctx.data_version:
             # A(a) and b(f, a) of the forward solve, not of the mesh's current data
             f, a, grad_a, g = ctx.data
-
-            def host(t):
-                if t is None:
-                    return None
-                return t.detach().cpu().numpy() if isinstance(t, torch.Tensor) else t
-            m.set_data(f=host(f), a=host(a), grad_a=host(grad_a), g=host(g))
+            m.set_data(f=_data(f), a=_data(a), grad_a=_data(grad_a), g=_data(g, f))
         b = torch.empty_like(x)
         m.get_rhs(b)
         m.set_rhs(gx.contiguous())

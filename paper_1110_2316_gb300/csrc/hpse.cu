@@ -1594,10 +1594,66 @@ extern "C" hpse_status hpse_query_points(const hpse_mesh *m, double *vol_axes, d
   return HPSE_OK;
 }
 
-extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data) {
+// Variable coefficient of box elements from device data, per volume point:
+// coef = (w J a^2, s_k (d_k a) / a) in FP64 and FP32, wja = w J a, aux =
+// (w J, a, d_x a, d_y a, d_z a); bad[0] = 1 where a <= 0 or a is not finite
+// (the operator of eq. 2.1 must be elliptic).  One CTA per element.
+__global__ void k_coef_scalar(int64_t nq, const int32_t *elem_W, const int64_t *coef_off, const double *geo,
+                              const double *const *qtab, const double *a, const double *ga, double *coef64,
+                              float *coef32, double *wja, double *aux, int32_t *bad) {
+  const int e = blockIdx.x;
+  const int W = elem_W[e], P = W + 1, Q = 2 * W + 1;
+  const double *wq = qtab[W] + 2 * Q * P + 2 * Q * Q;
+  const double *gs = geo + 4 * (int64_t)e;
+  for (int t = threadIdx.x; t < Q * Q * Q; t += blockDim.x) {
+    const int qa = t % Q, qb = (t / Q) % Q, qc = t / (Q * Q);
+    const int64_t i = coef_off[e] + t;
+    const double wJ = wq[qa] * wq[qb] * wq[qc] * gs[3];
+    double av = a[i];
+    if (!(av > 0.0) || !isfinite(av)) {
+      bad[0] = 1;
+      av = 1.0;
+    }
+    coef64[4 * i] = wJ * av * av;
+    coef32[4 * i] = (float)(wJ * av * av);
+    aux[i] = wJ;
+    aux[nq + i] = av;
+    for (int k = 0; k < 3; ++k) {
+      const double g = ga[k * nq + i];
+      coef64[4 * i + 1 + k] = gs[k] * g / av;
+      coef32[4 * i + 1 + k] = (float)(gs[k] * g / av);
+      aux[(2 + k) * nq + i] = g;
+    }
+    wja[i] = wJ * av;
+  }
+}
+
+// where a data pointer points: 1 device (or managed), 0 host, -1 unknown
+static int pointer_space(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) ? 1 : 0;
+}
+
+extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data, void *stream) {
   if (!m || !data || (!data->f && m->nquad > 0)) return HPSE_ERR_INVALID_ARG;
   if (m->coef_kind == HPSE_COEF_SCALAR && (!data->a || !data->grad_a)) return HPSE_ERR_INVALID_ARG;
   CK(cudaSetDevice(m->device));
+  // host or device data: every given pointer in the same space
+  int space = -2;
+  for (const void *p : {(const void *)data->f, (const void *)data->a, (const void *)data->grad_a,
+                        (const void *)data->g}) {
+    if (!p) continue;
+    const int sp = pointer_space(p);
+    if (sp < 0 || (space != -2 && sp != space)) return HPSE_ERR_INVALID_ARG;
+    space = sp;
+  }
+  const bool dev = space == 1;
+  const cudaMemcpyKind kin = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaStream_t s = (cudaStream_t)stream;
   // captured solver graphs refer to the coefficient and right-hand side
   // buffers: drop them so that the next solve re-captures with current data
   if (m->work) {
@@ -1612,8 +1668,10 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data) {
   std::vector<double> wja(nq);
   std::vector<double> coef;
   const bool vtx = m->coord == HPSE_COORD_VERTEX, ve = m->coord == HPSE_COORD_VERTEX_EDGE;
-  if (m->coef_kind == HPSE_COEF_SCALAR || vtx || ve) coef.assign(4 * (size_t)nq, 0.0);
-  for (int e = 0; e < m->n_elem; ++e) {
+  // a variable coefficient given on the device is transformed on the device
+  const bool dev_coef = dev && m->coef_kind == HPSE_COEF_SCALAR;
+  if ((m->coef_kind == HPSE_COEF_SCALAR && !dev_coef) || vtx || ve) coef.assign(4 * (size_t)nq, 0.0);
+  for (int e = 0; e < (dev_coef ? 0 : m->n_elem); ++e) {
     const hm::DegreeTables &t = m->tabs.at(m->W[e]);
     const int Q = t.Q;
     double s[3], J = 1.0;
@@ -1670,7 +1728,7 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data) {
           }
         }
   }
-  {
+  if (!dev_coef) {
     std::vector<double> aux(5 * (size_t)nq);
     for (int e = 0; e < m->n_elem; ++e) {
       const hm::DegreeTables &t = m->tabs.at(m->W[e]);
@@ -1689,37 +1747,58 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data) {
           }
     }
     CK(upload_reuse(m->d_aux, aux));
-    if (!m->d_f.p || m->d_f.bytes != (size_t)R * nq * sizeof(double)) CK(m->d_f.alloc((size_t)R * nq * sizeof(double)));
-    if (nq > 0) CK(cudaMemcpy(m->d_f.p, data->f, (size_t)R * nq * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  if (!m->d_f.p || m->d_f.bytes != (size_t)R * nq * sizeof(double)) CK(m->d_f.alloc((size_t)R * nq * sizeof(double)));
+  if (nq > 0) CK(cudaMemcpyAsync(m->d_f.p, data->f, (size_t)R * nq * sizeof(double), kin, s));
+  {
     std::vector<const double *> tp(HPSE_MAX_W + 1, nullptr);
     for (auto &kv : m->d_qtab) tp[kv.first] = kv.second.as<double>();
     CK(upload_reuse(m->d_tabs_ptr, tp));
   }
-  if (m->coef_kind == HPSE_COEF_SCALAR || vtx || ve) {
-    std::vector<float> c32(coef.size());
-    for (size_t i = 0; i < coef.size(); ++i) c32[i] = (float)coef[i];
-    CK(upload_reuse(m->d_coef64, coef));
-    CK(upload_reuse(m->d_coef32, c32));
+  DevBuf dwja, dbad;
+  if (dev_coef) {
+    if (!m->d_coef64.p || m->d_coef64.bytes != 4 * (size_t)nq * sizeof(double))
+      CK(m->d_coef64.alloc(4 * (size_t)std::max<int64_t>(nq, 1) * sizeof(double)));
+    if (!m->d_coef32.p || m->d_coef32.bytes != 4 * (size_t)nq * sizeof(float))
+      CK(m->d_coef32.alloc(4 * (size_t)std::max<int64_t>(nq, 1) * sizeof(float)));
+    if (!m->d_aux.p || m->d_aux.bytes != 5 * (size_t)nq * sizeof(double))
+      CK(m->d_aux.alloc(5 * (size_t)std::max<int64_t>(nq, 1) * sizeof(double)));
+    CK(dwja.alloc((size_t)std::max<int64_t>(nq, 1) * sizeof(double)));
+    CK(dbad.alloc(sizeof(int32_t)));
+    CK(cudaMemsetAsync(dbad.p, 0, sizeof(int32_t), s));
+    if (m->n_elem > 0) {
+      k_coef_scalar<<<m->n_elem, 256, 0, s>>>(nq, m->d_elem_W.as<int32_t>(), m->d_coef_off.as<int64_t>(),
+                                             m->d_geo64.as<double>(), m->d_tabs_ptr.as<const double *>(), data->a,
+                                             data->grad_a, m->d_coef64.as<double>(), m->d_coef32.as<float>(),
+                                             dwja.as<double>(), m->d_aux.as<double>(), dbad.as<int32_t>());
+      CK(cudaGetLastError());
+      ++g_launches;
+    }
+  } else {
+    if (m->coef_kind == HPSE_COEF_SCALAR || vtx || ve) {
+      std::vector<float> c32(coef.size());
+      for (size_t i = 0; i < coef.size(); ++i) c32[i] = (float)coef[i];
+      CK(upload_reuse(m->d_coef64, coef));
+      CK(upload_reuse(m->d_coef32, c32));
+    }
+    CK(upload(dwja, wja));
   }
   const size_t nv = (size_t)R * m->ndof;
   if (!m->d_b.p || m->d_b.bytes != nv * sizeof(double)) CK(m->d_b.alloc(nv * sizeof(double)));
-  if (nv) CK(cudaMemset(m->d_b.p, 0, nv * sizeof(double)));
+  if (nv) CK(cudaMemsetAsync(m->d_b.p, 0, nv * sizeof(double), s));
   // volume part of b: transpose kernel on rho_b = -(w J a) f
   if (nq > 0 && m->n_elem > 0) {
-    DevBuf dwja, df, drho;
-    CK(upload(dwja, wja));
-    CK(df.alloc((size_t)R * nq * sizeof(double)));
-    CK(cudaMemcpy(df.p, data->f, (size_t)R * nq * sizeof(double), cudaMemcpyHostToDevice));
+    DevBuf drho;
     CK(drho.alloc((size_t)R * nq * sizeof(double)));
-    k_rho_b<<<1024, 256>>>((int64_t)R * nq, dwja.as<double>(), df.as<double>(), nq, drho.as<double>());
+    k_rho_b<<<1024, 256, 0, s>>>((int64_t)R * nq, dwja.as<double>(), m->d_f.as<double>(), nq, drho.as<double>());
     CK(cudaGetLastError());
     ++g_launches;
     ApplyArgsT<double> a = apply_args<double>(m, m->groups[0], nullptr, m->d_b.as<double>());
     a.rho = drho.as<double>();
     a.skip_faces = 1;
-    hpse_status st = launch_apply_all<double>(m, MODE_TRANSPOSE, a, 0);
+    hpse_status st = launch_apply_all<double>(m, MODE_TRANSPOSE, a, s);
     if (st != HPSE_OK) return st;
-    CK(cudaDeviceSynchronize());
+    CK(cudaStreamSynchronize(s));
   }
   // Dirichlet data part of b
   if (data->g && m->nface_pts > 0) {
@@ -1740,7 +1819,7 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data) {
     CK(upload(dfi, ffi));
     CK(upload(doff, foff));
     CK(dg.alloc((size_t)R * m->nface_pts * sizeof(double)));
-    CK(cudaMemcpy(dg.p, data->g, (size_t)R * m->nface_pts * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(dg.p, data->g, (size_t)R * m->nface_pts * sizeof(double), kin, s));
     std::vector<const double *> tp(HPSE_MAX_W + 1, nullptr);
     int Wmax = 1;
     for (auto &kv : m->d_qtab) {
@@ -1765,10 +1844,10 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data) {
     const int Q = 2 * Wmax + 1, P = Wmax + 1;
     const size_t smem = (size_t)(8 * Q * Q + 2 * Q * P + P * P) * sizeof(double);
     CK(raise_smem((const void *)k_face_data, m->device, (size_t)smem));
-    k_face_data<<<(int)felems.size() * R, 128, smem>>>(A);
+    k_face_data<<<(int)felems.size() * R, 128, smem, s>>>(A);
     CK(cudaGetLastError());
     ++g_launches;
-    CK(cudaDeviceSynchronize());
+    CK(cudaStreamSynchronize(s));
   }
   // ||b||^2 per (problem, rhs)
   {
@@ -1777,15 +1856,24 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data) {
     CK(part.alloc((size_t)std::max(1, n_items_vec(m)) * sizeof(double)));
     if (!m->d_bnorm2.p) CK(m->d_bnorm2.alloc((size_t)npr * sizeof(double)));
     if (n_items_vec(m) > 0) {
-      k_dot<double, double><<<n_items_vec(m), 128>>>(elem_args(m), m->d_b.as<double>(), m->d_b.as<double>(),
-                                                     part.as<double>());
+      k_dot<double, double><<<n_items_vec(m), 128, 0, s>>>(elem_args(m), m->d_b.as<double>(),
+                                                           m->d_b.as<double>(), part.as<double>());
       CK(cudaGetLastError());
       ++g_launches;
     }
-    k_bnorm<<<npr, 128>>>(fin_args(m), part.as<double>(), m->d_bnorm2.as<double>());
+    k_bnorm<<<npr, 128, 0, s>>>(fin_args(m), part.as<double>(), m->d_bnorm2.as<double>());
     CK(cudaGetLastError());
     ++g_launches;
-    CK(cudaDeviceSynchronize());
+    CK(cudaStreamSynchronize(s));
+  }
+  if (dev_coef) {
+    int32_t h_bad = 0;
+    CK(cudaMemcpy(&h_bad, dbad.p, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (h_bad) {
+      // the device buffers now hold the rejected data: no solve until valid data is set
+      m->has_data = false;
+      return HPSE_ERR_INVALID_ARG;
+    }
   }
   m->has_data = true;
   return HPSE_OK;
@@ -2681,41 +2769,46 @@ extern "C" hpse_status hpse_h1_error(hpse_mesh *m, const double *u, const double
 //   dJ/d(d_k a) = w J [d_k u L lambda + (L u - f) d_k lambda]
 // (differentiate -lambda^T sum_q z_q dz_q/du with respect to each datum).
 // ---------------------------------------------------------------------------
-struct FieldArgs {
+template <typename T>
+struct FieldArgsT {
   int n_rhs;
   int64_t ndof, nquad;
   const int64_t *dof_off, *coef_off;
   const int32_t *elem_W;
   const double *geo;
   const double *const *qtab;  // per degree: B0, B1 (QxP), DQ, KQ (QxQ), wq (Q), B2 (QxP)
-  const double *u;
-  double *out;                // [n_rhs][5][nquad]
+  const T *u;
+  T *out;                     // [n_rhs][5][nquad]
 };
+typedef FieldArgsT<double> FieldArgs;
 
 // (v, v_x, v_y, v_z, Lap v) of a DOF vector at the volume points; one block per (element, rhs)
-__global__ void k_fields(FieldArgs A) {
-  extern __shared__ double sm[];
+// point fields in the precision T (FP64 tables rounded to T)
+template <typename T>
+__global__ void k_fields(FieldArgsT<T> A) {
+  extern __shared__ __align__(16) unsigned char fields_raw[];
+  T *sm = reinterpret_cast<T *>(fields_raw);
   const int item = blockIdx.x;
   const int e = item / A.n_rhs, r = item - e * A.n_rhs;
   const int W = A.elem_W[e], P = W + 1, Q = 2 * W + 1;
   const double *tb = A.qtab[W];
   const double *B0 = tb, *B1 = tb + Q * P, *B2 = tb + 2 * Q * P + 2 * Q * Q + Q;
   const double *geo = A.geo + (int64_t)e * 4;
-  const double sx = geo[0], sy = geo[1], sz = geo[2];
-  double *blk = sm, *X0 = blk + P * P * P, *X1 = X0 + Q * P * P, *X2 = X1 + Q * P * P;
-  double *Ta = X2 + Q * P * P, *Tb = Ta + Q * Q * P, *Tc = Tb + Q * Q * P;
+  const T sx = (T)geo[0], sy = (T)geo[1], sz = (T)geo[2];
+  T *blk = sm, *X0 = blk + P * P * P, *X1 = X0 + Q * P * P, *X2 = X1 + Q * P * P;
+  T *Ta = X2 + Q * P * P, *Tb = Ta + Q * Q * P, *Tc = Tb + Q * Q * P;
   const int64_t base = (int64_t)r * A.ndof + A.dof_off[e];
   const int nt = blockDim.x;
   for (int t = threadIdx.x; t < P * P * P; t += nt) blk[t] = A.u[base + t];
   __syncthreads();
   for (int t = threadIdx.x; t < Q * P * P; t += nt) {
     const int qa = t % Q, l = t / Q;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    T a0 = 0, a1 = 0.0, a2 = 0.0;
     for (int i = 0; i < P; ++i) {
-      const double v = blk[l * P + i];
-      a0 += B0[qa * P + i] * v;
-      a1 += B1[qa * P + i] * v;
-      a2 += B2[qa * P + i] * v;
+      const T v = blk[l * P + i];
+      a0 += (T)B0[qa * P + i] * v;
+      a1 += (T)B1[qa * P + i] * v;
+      a2 += (T)B2[qa * P + i] * v;
     }
     X0[l * Q + qa] = a0;
     X1[l * Q + qa] = a1;
@@ -2725,12 +2818,12 @@ __global__ void k_fields(FieldArgs A) {
   // pass A: T_a = B0y X0, T_b = B1y X0, T_c = B0y X1
   for (int t = threadIdx.x; t < Q * Q * P; t += nt) {
     const int qa = t % Q, qb = (t / Q) % Q, k = t / (Q * Q);
-    double a = 0.0, b = 0.0, c = 0.0;
+    T a = 0, b = 0.0, c = 0.0;
     for (int j = 0; j < P; ++j) {
-      const double x0 = X0[(k * P + j) * Q + qa];
-      a += B0[qb * P + j] * x0;
-      b += B1[qb * P + j] * x0;
-      c += B0[qb * P + j] * X1[(k * P + j) * Q + qa];
+      const T x0 = X0[(k * P + j) * Q + qa];
+      a += (T)B0[qb * P + j] * x0;
+      b += (T)B1[qb * P + j] * x0;
+      c += (T)B0[qb * P + j] * X1[(k * P + j) * Q + qa];
     }
     Ta[t] = a;
     Tb[t] = b;
@@ -2740,14 +2833,14 @@ __global__ void k_fields(FieldArgs A) {
   const int64_t ob = (int64_t)r * 5 * A.nquad + A.coef_off[e];
   for (int t = threadIdx.x; t < Q * Q * Q; t += nt) {
     const int qa = t % Q, qb = (t / Q) % Q, qc = t / (Q * Q);
-    double v = 0.0, vz = 0.0, vzz = 0.0, vy = 0.0, vx = 0.0;
+    T v = 0, vz = 0.0, vzz = 0.0, vy = 0.0, vx = 0.0;
     for (int k = 0; k < P; ++k) {
       const int o = (k * Q + qb) * Q + qa;
-      v += B0[qc * P + k] * Ta[o];
-      vz += B1[qc * P + k] * Ta[o];
-      vzz += B2[qc * P + k] * Ta[o];
-      vy += B0[qc * P + k] * Tb[o];
-      vx += B0[qc * P + k] * Tc[o];
+      v += (T)B0[qc * P + k] * Ta[o];
+      vz += (T)B1[qc * P + k] * Ta[o];
+      vzz += (T)B2[qc * P + k] * Ta[o];
+      vy += (T)B0[qc * P + k] * Tb[o];
+      vx += (T)B0[qc * P + k] * Tc[o];
     }
     A.out[ob + t] = v;
     A.out[ob + A.nquad + t] = sx * vx;
@@ -2759,10 +2852,10 @@ __global__ void k_fields(FieldArgs A) {
   // pass B: T_a = B2y X0 (u_yy), T_b = B0y X2 (u_xx)
   for (int t = threadIdx.x; t < Q * Q * P; t += nt) {
     const int qa = t % Q, qb = (t / Q) % Q, k = t / (Q * Q);
-    double a = 0.0, b = 0.0;
+    T a = 0, b = 0.0;
     for (int j = 0; j < P; ++j) {
-      a += B2[qb * P + j] * X0[(k * P + j) * Q + qa];
-      b += B0[qb * P + j] * X2[(k * P + j) * Q + qa];
+      a += (T)B2[qb * P + j] * X0[(k * P + j) * Q + qa];
+      b += (T)B0[qb * P + j] * X2[(k * P + j) * Q + qa];
     }
     Ta[t] = a;
     Tb[t] = b;
@@ -2770,11 +2863,11 @@ __global__ void k_fields(FieldArgs A) {
   __syncthreads();
   for (int t = threadIdx.x; t < Q * Q * Q; t += nt) {
     const int qa = t % Q, qb = (t / Q) % Q, qc = t / (Q * Q);
-    double vyy = 0.0, vxx = 0.0;
+    T vyy = 0, vxx = 0.0;
     for (int k = 0; k < P; ++k) {
       const int o = (k * Q + qb) * Q + qa;
-      vyy += B0[qc * P + k] * Ta[o];
-      vxx += B0[qc * P + k] * Tb[o];
+      vyy += (T)B0[qc * P + k] * Ta[o];
+      vxx += (T)B0[qc * P + k] * Tb[o];
     }
     A.out[ob + 4 * A.nquad + t] += sy * sy * vyy + sx * sx * vxx;
   }
@@ -2816,26 +2909,28 @@ __global__ void k_eval_T(FieldArgs A, const double *rho) {
 }
 
 // residual map at the points: z = sqrt(wJ) (L u - f)
-__global__ void k_resid_points(int64_t nquad, int n_rhs, const double *aux, const double *f, const double *fields,
-                               double *z) {
+template <typename T>
+__global__ void k_resid_points(int64_t nquad, int n_rhs, const double *aux, const double *f, const T *fields,
+                               T *z) {
   const int64_t n = nquad * n_rhs;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = i / nquad, q = i - r * nquad;
-    const double *fl = fields + r * 5 * nquad;
-    const double wJ = aux[q], a = aux[nquad + q];
-    const double Lu = -a * fl[4 * nquad + q] -
-                      (aux[2 * nquad + q] * fl[nquad + q] + aux[3 * nquad + q] * fl[2 * nquad + q] +
-                       aux[4 * nquad + q] * fl[3 * nquad + q]);
-    z[i] = sqrt(wJ) * (Lu - f[i]);
+    const T *fl = fields + r * 5 * nquad;
+    const T wJ = (T)aux[q], a = (T)aux[nquad + q];
+    const T Lu = -a * fl[4 * nquad + q] -
+                 ((T)aux[2 * nquad + q] * fl[nquad + q] + (T)aux[3 * nquad + q] * fl[2 * nquad + q] +
+                  (T)aux[4 * nquad + q] * fl[3 * nquad + q]);
+    z[i] = sqrt(wJ) * (Lu - (T)f[i]);
   }
 }
 
 // rho = -sqrt(wJ) a z: the weights of S^T z in the sum-factorised transpose kernel
-__global__ void k_rho_from_z(int64_t nquad, int n_rhs, const double *aux, const double *z, double *rho) {
+template <typename T>
+__global__ void k_rho_from_z(int64_t nquad, int n_rhs, const double *aux, const T *z, double *rho) {
   const int64_t n = nquad * n_rhs;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t q = i % nquad;
-    rho[i] = -sqrt(aux[q]) * aux[nquad + q] * z[i];
+    rho[i] = (double)(-sqrt((T)aux[q]) * (T)aux[nquad + q] * z[i]);
   }
 }
 
@@ -2862,8 +2957,9 @@ __global__ void k_data_grad(int64_t nquad, int n_rhs, const double *aux, const d
   }
 }
 
-static FieldArgs field_args(const hpse_mesh *m, const double *u, double *out) {
-  FieldArgs A;
+template <typename T = double>
+static FieldArgsT<T> field_args(const hpse_mesh *m, const T *u, T *out) {
+  FieldArgsT<T> A;
   A.n_rhs = m->n_rhs;
   A.ndof = m->ndof;
   A.nquad = m->nquad;
@@ -2883,11 +2979,12 @@ static int max_degree(const hpse_mesh *m) {
   return w;
 }
 
-static hpse_status launch_fields(hpse_mesh *m, const double *u, double *out, cudaStream_t s) {
+template <typename T = double>
+static hpse_status launch_fields(hpse_mesh *m, const T *u, T *out, cudaStream_t s) {
   const int W = max_degree(m), P = W + 1, Q = 2 * W + 1;
-  const size_t smem = (size_t)(P * P * P + 3 * Q * P * P + 3 * Q * Q * P) * sizeof(double);
-  CK(raise_smem((const void *)k_fields, m->device, (size_t)smem));
-  k_fields<<<n_items_all(m), 256, smem, s>>>(field_args(m, u, out));
+  const size_t smem = (size_t)(P * P * P + 3 * Q * P * P + 3 * Q * Q * P) * sizeof(T);
+  CK(raise_smem((const void *)k_fields<T>, m->device, (size_t)smem));
+  k_fields<T><<<n_items_all(m), 256, smem, s>>>(field_args<T>(m, u, out));
   CK(cudaGetLastError());
   ++g_launches;
   return HPSE_OK;
@@ -2913,7 +3010,7 @@ extern "C" hpse_status hpse_apply_eval_transpose(hpse_mesh *m, const double *rho
   const int W = max_degree(m), P = W + 1, Q = 2 * W + 1;
   const size_t smem = (size_t)(Q * Q * Q + Q * Q * P + Q * P * P) * sizeof(double);
   CK(raise_smem((const void *)k_eval_T, m->device, (size_t)smem));
-  k_eval_T<<<n_items_all(m), 256, smem, (cudaStream_t)stream>>>(field_args(m, nullptr, y), rho);
+  k_eval_T<<<n_items_all(m), 256, smem, (cudaStream_t)stream>>>(field_args<double>(m, nullptr, y), rho);
   CK(cudaGetLastError());
   ++g_launches;
   return HPSE_OK;
@@ -2930,50 +3027,62 @@ extern "C" hpse_status hpse_quad_weights(hpse_mesh *m, double *out, void *stream
   return HPSE_OK;
 }
 
-static hpse_status ensure_scratch(hpse_mesh *m) {
-  const size_t nf = (size_t)5 * m->n_rhs * m->nquad * sizeof(double);
+static hpse_status ensure_scratch(hpse_mesh *m, size_t fbytes) {
+  const size_t nf = (size_t)5 * m->n_rhs * m->nquad * fbytes;
   const size_t nr = (size_t)m->n_rhs * m->nquad * sizeof(double);
-  if (m->d_scr_fields.bytes != nf) CK(m->d_scr_fields.alloc(nf));
+  if (m->d_scr_fields.bytes < nf) CK(m->d_scr_fields.alloc(nf));
   if (m->d_scr_rho.bytes != nr) CK(m->d_scr_rho.alloc(nr));
   return HPSE_OK;
 }
 
-extern "C" hpse_status hpse_apply_residual(hpse_mesh *m, const double *u, double *z, void *stream) {
-  if (m && m->coord != HPSE_COORD_CARTESIAN) return HPSE_ERR_INVALID_ARG;  // box meshes only
-  if (!m) return HPSE_ERR_INVALID_ARG;
-  if (m->ndof == 0) return HPSE_OK;
-  if (!u || !z) return HPSE_ERR_INVALID_ARG;
-  if (!m->has_data) return HPSE_ERR_NO_DATA;
-  CK(cudaSetDevice(m->device));
-  hpse_status st = ensure_scratch(m);
+template <typename T>
+static hpse_status residual_t(hpse_mesh *m, const T *u, T *z, cudaStream_t s) {
+  hpse_status st = ensure_scratch(m, sizeof(T));
   if (st != HPSE_OK) return st;
-  cudaStream_t s = (cudaStream_t)stream;
-  st = launch_fields(m, u, m->d_scr_fields.as<double>(), s);
+  st = launch_fields<T>(m, u, (T *)m->d_scr_fields.p, s);
   if (st != HPSE_OK) return st;
-  k_resid_points<<<1024, 256, 0, s>>>(m->nquad, m->n_rhs, m->d_aux.as<double>(), m->d_f.as<double>(),
-                                      m->d_scr_fields.as<double>(), z);
+  k_resid_points<T><<<1024, 256, 0, s>>>(m->nquad, m->n_rhs, m->d_aux.as<double>(), m->d_f.as<double>(),
+                                         (const T *)m->d_scr_fields.p, z);
   CK(cudaGetLastError());
   ++g_launches;
   return HPSE_OK;
 }
 
-extern "C" hpse_status hpse_apply_transpose(hpse_mesh *m, const double *z, double *y, void *stream) {
+extern "C" hpse_status hpse_apply_residual(hpse_mesh *m, int32_t prec, const void *u, void *z, void *stream) {
   if (m && m->coord != HPSE_COORD_CARTESIAN) return HPSE_ERR_INVALID_ARG;  // box meshes only
-  if (!m) return HPSE_ERR_INVALID_ARG;
+  if (!m || (prec != HPSE_FP64 && prec != HPSE_FP32)) return HPSE_ERR_INVALID_ARG;
+  if (m->ndof == 0) return HPSE_OK;
+  if (!u || !z) return HPSE_ERR_INVALID_ARG;
+  if (!m->has_data) return HPSE_ERR_NO_DATA;
+  CK(cudaSetDevice(m->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (prec == HPSE_FP64) return residual_t<double>(m, (const double *)u, (double *)z, s);
+  return residual_t<float>(m, (const float *)u, (float *)z, s);
+}
+
+template <typename T>
+static hpse_status transpose_t(hpse_mesh *m, const T *z, T *y, cudaStream_t s) {
+  hpse_status st = ensure_scratch(m, sizeof(double));
+  if (st != HPSE_OK) return st;
+  k_rho_from_z<T><<<1024, 256, 0, s>>>(m->nquad, m->n_rhs, m->d_aux.as<double>(), z, m->d_scr_rho.as<double>());
+  CK(cudaGetLastError());
+  ++g_launches;
+  ApplyArgsT<T> a = apply_args<T>(m, m->groups[0], nullptr, y);
+  a.rho = m->d_scr_rho.as<double>();
+  a.skip_faces = 1;
+  return launch_apply_all<T>(m, MODE_TRANSPOSE, a, s);
+}
+
+extern "C" hpse_status hpse_apply_transpose(hpse_mesh *m, int32_t prec, const void *z, void *y, void *stream) {
+  if (m && m->coord != HPSE_COORD_CARTESIAN) return HPSE_ERR_INVALID_ARG;  // box meshes only
+  if (!m || (prec != HPSE_FP64 && prec != HPSE_FP32)) return HPSE_ERR_INVALID_ARG;
   if (m->ndof == 0) return HPSE_OK;
   if (!z || !y) return HPSE_ERR_INVALID_ARG;
   if (!m->has_data) return HPSE_ERR_NO_DATA;
   CK(cudaSetDevice(m->device));
-  hpse_status st = ensure_scratch(m);
-  if (st != HPSE_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  k_rho_from_z<<<1024, 256, 0, s>>>(m->nquad, m->n_rhs, m->d_aux.as<double>(), z, m->d_scr_rho.as<double>());
-  CK(cudaGetLastError());
-  ++g_launches;
-  ApplyArgsT<double> a = apply_args<double>(m, m->groups[0], nullptr, y);
-  a.rho = m->d_scr_rho.as<double>();
-  a.skip_faces = 1;
-  return launch_apply_all<double>(m, MODE_TRANSPOSE, a, s);
+  if (prec == HPSE_FP64) return transpose_t<double>(m, (const double *)z, (double *)y, s);
+  return transpose_t<float>(m, (const float *)z, (float *)y, s);
 }
 
 extern "C" hpse_status hpse_data_gradient(hpse_mesh *m, const double *ufields, const double *lfields, double *out,

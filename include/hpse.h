@@ -110,13 +110,11 @@ typedef struct {
    * element order, then the corner sets' W+1 values.  hpse_query_points
    * returns modified coordinates; the caller samples f and g at
    * r = e^tau, theta, x3 (physical data), the library forms F^e = e^{2 tau} f.
-   * hpse_h1_error on an edge mesh takes the difference of two discrete
-   * solutions only (ref given): e^{2 tau} v^2 + v_tau^2 + v_theta^2 +
-   * e^{2 tau} v_x3^2 over each element's (2W+1)^3 GLL rule in modified
-   * coordinates, and on each corner set int_0^{r_1} r dr x (its theta span)
-   * x int (p^2 + p_x3^2) dx3.  Not supported with HPSE_COORD_EDGE
-   * (HPSE_ERR_INVALID_ARG): the adjoint entry points, hpse_h1_error against
-   * pointwise data, hpse_h1_error_noalloc. */
+   * hpse_h1_error on a neighbourhood mesh takes the difference of two
+   * discrete solutions only (ref given; see hpse_h1_error).  Not supported
+   * with a neighbourhood coordinate kind (HPSE_ERR_INVALID_ARG): the adjoint
+   * entry points, hpse_h1_error against pointwise data,
+   * hpse_h1_error_noalloc. */
   int32_t coord;               /* HPSE_COORD_CARTESIAN (0), _EDGE (1), _VERTEX (2) or _VERTEX_EDGE (3) */
   int32_t n_corner;            /* corner sets (HPSE_COORD_EDGE), else 0            */
   const int32_t *corner_W;     /* [n_corner] degree in x3 (= that of its elements) */
@@ -309,7 +307,19 @@ hpse_status hpse_pcg_solve(hpse_mesh *m, const hpse_solve_opts *opts, double *x,
  *   (ref != NULL) another device FP64 DOF vector, or
  *   (ref == NULL) the function sampled at the volume points: vq (device,
  *   n_rhs*nquad doubles, the values) and gq (device, n_rhs*3*nquad doubles,
- *   d/dx, d/dy, d/dz blocks per rhs).  out: host, 2*n_rhs doubles.  Synchronous. */
+ *   d/dx, d/dy, d/dz blocks per rhs).  out: host, 2*n_rhs doubles.  Synchronous.
+ * Neighbourhood meshes take ref only (the difference of two discrete
+ * solutions) and integrate in physical coordinates through the modified ones:
+ *   edge (tau, theta, x3):     e^{2tau} v^2 + v_tau^2 + v_theta^2 + e^{2tau} v_x3^2
+ *   vertex (phi, theta, chi):  sin(phi) e^{3chi} v^2 + sin(phi) e^chi (v_chi^2 + v_phi^2)
+ *                              + e^chi v_theta^2 / sin(phi)
+ *   vertex-edge (psi, theta, zeta): e^{2psi+3zeta} v^2 + e^zeta (v_psi^2 + v_theta^2)
+ *                              + e^{2psi+zeta} (v_zeta - v_psi)^2
+ * over each element's (2W+1)^3 GLL rule; corner sets exactly in the radial
+ * variable (r or rho) and, for a polynomial set, with its own (2W+1)-point GLL
+ * rule along the slab (edge: x3, vertex-edge: zeta); constant sets over their
+ * whole region (vertex: rho < rho_1; vertex-edge: x3 < x3_1 inside the cone
+ * of each theta sector). */
 hpse_status hpse_h1_error(hpse_mesh *m, const double *u, const double *ref,
                           const double *vq, const double *gq, double *out, void *stream);
 

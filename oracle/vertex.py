@@ -271,3 +271,47 @@ class VertexDiscretisation(EdgeDiscretisation):
                 err += float(np.sum(wq * ((pc - wv) ** 2 + g2)))
                 nrm += float(np.sum(wq * (wv ** 2 + g2)))
         return err, nrm
+
+
+def h1_diff(disc, U, V):
+    """(||u_h - v_h||_{H^1}^2, ||v_h||_{H^1}^2) of two discrete solutions on a
+    vertex neighbourhood, in physical coordinates (Section 6.1).
+
+    Finite elements in (phi, theta, chi), rho = e^chi: dx = e^{3 chi} sin(phi)
+    dphi dtheta dchi and |grad v|^2 = e^{-2 chi} (v_chi^2 + v_phi^2 +
+    v_theta^2 / sin^2(phi)), by the element's (2W+1)-point GLL rule (reading:
+    the element rule of the regular region).  Corner set: the constant p on
+    rho < rho_1 over the element's (phi, theta) box, integrated exactly:
+    p^2 rho_1^3 / 3 (cos phi_lo - cos phi_hi) (theta_hi - theta_lo); its
+    gradient is zero."""
+    out = []
+    for X in (U - V, V):
+        tot = 0.0
+        for e in range(disc.E):
+            xp, _ = gll(disc.P[e])
+            xg, wg = gll(2 * disc.W[e] + 1)
+            B = [lagrange_eval(xp, xg, d) for d in range(2)]
+            lo, hh = disc.mesh.elem_lo[e], disc.h(e) / 2.0
+            phs = lo[0] + (xg + 1.0) * hh[0]
+            chs = lo[2] + (xg + 1.0) * hh[2]
+            s = disc.scale(e)
+            u = disc.block(X, e)
+            v = eval_tensor(u, B[0], B[0], B[0])
+            vp = s[0] * eval_tensor(u, B[1], B[0], B[0])
+            vt = s[1] * eval_tensor(u, B[0], B[1], B[0])
+            vc = s[2] * eval_tensor(u, B[0], B[0], B[1])
+            sp = np.sin(phs)[None, None, :]
+            ec = np.exp(chs)[:, None, None]
+            wq = wg[:, None, None] * wg[None, :, None] * wg[None, None, :] * float(np.prod(hh))
+            tot += float(np.sum(wq * (ec ** 3 * sp * v * v + ec * sp * (vc * vc + vp * vp) + ec * vt * vt / sp)))
+        f = disc.CORNER_FACE
+        for c in range(disc.C):
+            pc = float(disc.corner(X, c)[0])
+            for e in range(disc.E):
+                if int(disc.mesh.elem_nbr[e, f]) != -2 - c:
+                    continue
+                lo, hi = disc.mesh.elem_lo[e], disc.mesh.elem_hi[e]
+                rho1 = float(np.exp(lo[2]))
+                tot += pc * pc * rho1 ** 3 / 3.0 * (np.cos(lo[0]) - np.cos(hi[0])) * (hi[1] - lo[1])
+        out.append(tot)
+    return tuple(out)

@@ -336,3 +336,68 @@ class VertexEdgeDiscretisation(EdgeDiscretisation):
                     err += float(np.sum(dx * ((float(pc[0]) - wv) ** 2 + wr ** 2 + wth ** 2 + wz ** 2)))
                 nrm += float(np.sum(dx * (wv ** 2 + wr ** 2 + wth ** 2 + wz ** 2)))
         return err, nrm
+
+
+def h1_diff(disc, U, V):
+    """(||u_h - v_h||_{H^1}^2, ||v_h||_{H^1}^2) of two discrete solutions on a
+    vertex-edge neighbourhood, in physical coordinates (Section 6.1).
+
+    Finite elements in (psi, theta, zeta), r = e^{psi + zeta}, x3 = e^zeta:
+    dx = r^2 x3 dpsi dtheta dzeta and the physical gradient is
+    (v_psi / r, v_theta / r, (v_zeta - v_psi) / x3), by the element's
+    (2W+1)-point GLL rule.  Corner sets: the zeta polynomial p on psi < psi_1
+    of its layer and sector, exactly in r (int_0^{x3 e^{psi_1}} r dr =
+    x3^2 e^{2 psi_1} / 2) with its own (2W+1)-point GLL rule in zeta:
+    (e^{2 psi_1} / 2) (e^{3 zeta} p^2 + e^zeta p_zeta^2) per unit theta; the
+    constant on x3 < x3_1 inside the cone psi < psi_top of each theta sector,
+    exactly: p^2 theta-span e^{2 psi_top} / 2 x3_1^3 / 3."""
+    out = []
+    for X in (U - V, V):
+        tot = 0.0
+        for e in range(disc.E):
+            xp, _ = gll(disc.P[e])
+            xg, wg = gll(2 * disc.W[e] + 1)
+            B = [lagrange_eval(xp, xg, d) for d in range(2)]
+            lo, hh = disc.mesh.elem_lo[e], disc.h(e) / 2.0
+            ps = lo[0] + (xg + 1.0) * hh[0]
+            zs = lo[2] + (xg + 1.0) * hh[2]
+            s = disc.scale(e)
+            u = disc.block(X, e)
+            v = eval_tensor(u, B[0], B[0], B[0])
+            vp = s[0] * eval_tensor(u, B[1], B[0], B[0])
+            vt = s[1] * eval_tensor(u, B[0], B[1], B[0])
+            vz = s[2] * eval_tensor(u, B[0], B[0], B[1])
+            r = np.exp(ps[None, None, :] + zs[:, None, None])
+            x3 = np.exp(zs)[:, None, None]
+            dx = wg[:, None, None] * wg[None, :, None] * wg[None, None, :] * float(np.prod(hh)) * r * r * x3
+            tot += float(np.sum(dx * (v * v + (vp * vp + vt * vt) / (r * r) + (vz - vp) ** 2 / (x3 * x3))))
+        for c in range(disc.C):
+            f = disc.cface[c]
+            p = disc.corner(X, c)
+            done = set()
+            for e in range(disc.E):
+                if int(disc.mesh.elem_nbr[e, f]) != -2 - c:
+                    continue
+                lo, hi = disc.mesh.elem_lo[e], disc.mesh.elem_hi[e]
+                th = hi[1] - lo[1]
+                if f == 0:
+                    xp, _ = gll(disc.Wc[c] + 1)
+                    xg, wg = gll(2 * disc.Wc[c] + 1)
+                    hz = hi[2] - lo[2]
+                    zs = lo[2] + (xg + 1.0) * hz / 2.0
+                    p0 = lagrange_eval(xp, xg, 0) @ p
+                    pz = (2.0 / hz) * (lagrange_eval(xp, xg, 1) @ p)
+                    ez = np.exp(zs)
+                    tot += 0.5 * np.exp(2.0 * lo[0]) * th * 0.5 * hz * float(
+                        np.sum(wg * (ez ** 3 * p0 * p0 + ez * pz * pz)))
+                else:
+                    key = round(float(lo[1]), 12)
+                    if key in done:
+                        continue
+                    done.add(key)
+                    ptop = max(float(disc.mesh.elem_hi[q, 0]) for q in range(disc.E)
+                               if int(disc.mesh.elem_nbr[q, f]) == -2 - c and abs(disc.mesh.elem_lo[q, 1] - lo[1]) < 1e-14)
+                    x31 = float(np.exp(lo[2]))
+                    tot += float(p[0]) ** 2 * th * 0.5 * np.exp(2.0 * ptop) * x31 ** 3 / 3.0
+        out.append(tot)
+    return tuple(out)

@@ -216,7 +216,8 @@ struct hpse_mesh {
   DevBuf d_item_n, d_kappa64, d_kappa32, d_fw64, d_fw32, d_cslot, d_cW, d_cprob, d_slot_ptr, d_slot_list;
   DevBuf d_cinv64, d_cinv32, d_cscr64, d_cscr32;
   DevBuf d_zeig64, d_zeig32;              // C* form: per element x3 eigenbasis and eigenvalues
-  DevBuf d_ch1;                           // H^1 norm of corner sets: (r_1^2/2) x theta span x h_x3/2, s_x3
+  DevBuf d_h1w;                           // H^1 integrand weights of neighbourhood elements [E][8][KAPPA_STRIDE]
+  DevBuf d_ch1w;                          // H^1 weights of corner sets [C][2][KAPPA_STRIDE]
   int precond_kind = HPSE_PRECOND_SEPARABLE;
   bool bj_ready = false;
   DevBuf d_bj_off;            // int64 per element: offset of its packed block
@@ -662,13 +663,15 @@ struct H1Args {
   const double *const *qtab;
   const double *u, *ref, *vq, *gq;
   double *part_err, *part_nrm;
-  // edge neighbourhood (difference of two discrete solutions only): e^{2 tau}
-  // per element x-point; corner sets: their W, and per set (r_1^2/2) x theta
-  // span x half slab length, then s_x3
-  const double *kappa;
+  // neighbourhood meshes (difference of two discrete solutions only): per
+  // element the weights a_k(x), b_k(z) of the physical H^1 integrand and the
+  // mixed-term coefficient hc; corner sets: their W and per set the weights
+  // w0, w1 on its own GLL points (see setup_edge)
+  const double *hw;
+  double hc;
   int32_t n_elem, n_corner;
   const int32_t *cW;
-  const double *cfac;
+  const double *cw;
 };
 
 __device__ void h1_fields(const double *blk, int P, int Q, const double *B0, const double *B1, double *X0, double *X1,
@@ -732,10 +735,17 @@ __global__ void k_h1(H1Args A) {
       uz *= geo[2];
       const double wJ = wq[qa] * wq[qb] * wq[qc] * geo[3];
       if (A.ref) {
-        // edge neighbourhood: dx = e^{2 tau} dtau dtheta dx3 and
-        // |grad v|^2 = e^{-2 tau} (v_tau^2 + v_theta^2) + v_x3^2
-        const double kq = A.kappa ? A.kappa[(int64_t)e * hpse::KAPPA_STRIDE + qa] : 1.0;
-        const double v = kq * u * u + ux * ux + uy * uy + kq * uz * uz;
+        double v;
+        if (A.hw) {
+          // neighbourhood element: the physical integrand in modified coordinates
+          const int KS = hpse::KAPPA_STRIDE;
+          const double *ax = A.hw + (int64_t)e * 8 * KS, *bz = ax + 4 * KS;
+          const double w = uz - A.hc * ux;
+          v = ax[qa] * bz[qc] * u * u + ax[KS + qa] * bz[KS + qc] * ux * ux +
+              ax[2 * KS + qa] * bz[2 * KS + qc] * uy * uy + ax[3 * KS + qa] * bz[3 * KS + qc] * w * w;
+        } else {
+          v = u * u + ux * ux + uy * uy + uz * uz;
+        }
         if (pass == 0) serr += wJ * v;
         else snrm += wJ * v;
       } else {
@@ -764,30 +774,39 @@ __global__ void k_h1_corner(H1Args A) {
   const int item = blockIdx.x;
   const int c = item / A.n_rhs, r = item - c * A.n_rhs;
   const int W = A.cW[c], P = W + 1, Q = 2 * W + 1;
-  const double *tb = A.qtab[W];
-  const double *B0 = tb, *B1 = tb + Q * P, *wq = tb + 2 * Q * P + 2 * Q * Q;
   const int64_t base = (int64_t)r * A.ndof + A.dof_off[A.n_elem + c];
-  const double fac = A.cfac[2 * c], sz = A.cfac[2 * c + 1];
+  const double *w0 = A.cw + (int64_t)c * 2 * hpse::KAPPA_STRIDE, *w1 = w0 + hpse::KAPPA_STRIDE;
   double se = 0.0, sn = 0.0;
-  for (int q = threadIdx.x; q < Q; q += blockDim.x) {
-    double d0 = 0.0, d1 = 0.0, v0 = 0.0, v1 = 0.0;
-    for (int k = 0; k < P; ++k) {
-      const double dv = A.u[base + k] - A.ref[base + k];
-      d0 += B0[q * P + k] * dv;
-      d1 += B1[q * P + k] * dv;
-      v0 += B0[q * P + k] * A.ref[base + k];
-      v1 += B1[q * P + k] * A.ref[base + k];
+  if (W == 0) {
+    // a constant set
+    if (threadIdx.x == 0) {
+      const double dv = A.u[base] - A.ref[base], v = A.ref[base];
+      se = w0[0] * dv * dv;
+      sn = w0[0] * v * v;
     }
-    se += wq[q] * (d0 * d0 + sz * sz * d1 * d1);
-    sn += wq[q] * (v0 * v0 + sz * sz * v1 * v1);
+  } else {
+    const double *tb = A.qtab[W];
+    const double *B0 = tb, *B1 = tb + Q * P;
+    for (int q = threadIdx.x; q < Q; q += blockDim.x) {
+      double d0 = 0.0, d1 = 0.0, v0 = 0.0, v1 = 0.0;
+      for (int k = 0; k < P; ++k) {
+        const double dv = A.u[base + k] - A.ref[base + k];
+        d0 += B0[q * P + k] * dv;
+        d1 += B1[q * P + k] * dv;
+        v0 += B0[q * P + k] * A.ref[base + k];
+        v1 += B1[q * P + k] * A.ref[base + k];
+      }
+      se += w0[q] * d0 * d0 + w1[q] * d1 * d1;
+      sn += w0[q] * v0 * v0 + w1[q] * v1 * v1;
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     se += __shfl_xor_sync(0xffffffffu, se, o);
     sn += __shfl_xor_sync(0xffffffffu, sn, o);
   }
   if (threadIdx.x == 0) {
-    A.part_err[(int64_t)(A.n_elem + c) * A.n_rhs + r] = fac * se;
-    A.part_nrm[(int64_t)(A.n_elem + c) * A.n_rhs + r] = fac * sn;
+    A.part_err[(int64_t)(A.n_elem + c) * A.n_rhs + r] = se;
+    A.part_nrm[(int64_t)(A.n_elem + c) * A.n_rhs + r] = sn;
   }
 }
 
@@ -1290,15 +1309,96 @@ static hpse_status setup_edge(hpse_mesh *m) {
   CK(upload(m->d_cprob, m->cprob));
   CK(upload(m->d_slot_ptr, m->slot_ptr));
   CK(upload(m->d_slot_list, m->slot_list));
-  std::vector<double> ch1(2 * (size_t)C, 0.0);
-  for (int e = 0; e < E && m->coord == HPSE_COORD_EDGE; ++e) {
-    if (m->cslot[2 * e] < 0) continue;
-    const int c = -2 - m->nbr[6 * e];
-    const double r1 = std::exp(m->lo[3 * e]), hz = m->hi[3 * e + 2] - m->lo[3 * e + 2];
-    ch1[2 * c] += 0.5 * r1 * r1 * (m->hi[3 * e + 1] - m->lo[3 * e + 1]) * 0.5 * hz;
-    ch1[2 * c + 1] = 2.0 / hz;
+  // H^1 norm in physical coordinates (Section 6.1) of the difference of two
+  // discrete solutions.  Elements: the integrand in modified coordinates is
+  //   a0(x) b0(z) u^2 + a1 b1 u_x^2 + a2 b2 u_y^2 + a3 b3 (u_z - c u_x)^2
+  // with the element's (2W+1)-point GLL rule (x = first, z = third variable):
+  //   edge (tau, theta, x3):      e^{2tau} u^2 + u_tau^2 + u_theta^2 + e^{2tau} u_x3^2
+  //   vertex (phi, theta, chi):   sin(phi) e^{3chi} u^2 + sin(phi) e^chi u_phi^2
+  //                               + e^chi / sin(phi) u_theta^2 + sin(phi) e^chi u_chi^2
+  //   vertex-edge (psi, th, zeta): e^{2psi+3zeta} u^2 + e^zeta (u_psi^2 + u_theta^2)
+  //                               + e^{2psi+zeta} (u_zeta - u_psi)^2
+  // (dx = e^{2tau} dtau dtheta dx3, e^{3chi} sin(phi) dchi dphi dtheta,
+  // e^{2psi+3zeta} dpsi dtheta dzeta).  Corner sets, integrated exactly in r
+  // or rho: per point of the set's own GLL rule weights w0 (on p^2) and w1
+  // (on (dp/dlambda)^2), a constant set one weight w0:
+  //   edge p(x3) on r < r1: (r1^2/2) theta-span (h/2) w_q and the same times s_x3^2
+  //   vertex-edge p(zeta) on psi < psi1: (e^{2psi1}/2) theta-span (h/2) w_q e^{3zeta_q},
+  //                       and (e^{2psi1}/2) theta-span (h/2) w_q e^{zeta_q} s_zeta^2
+  //   vertex constant on rho < rho1: rho1^3/3 sum (cos phi_lo - cos phi_hi) theta-span
+  //   vertex-edge constant on x3 < x3_1 in the cone psi < psi_top, per theta
+  //                       sector: theta-span (e^{2 psi_top}/2) x3_1^3/3
+  {
+    const int KS = hpse::KAPPA_STRIDE;
+    std::vector<double> hw((size_t)E * 8 * KS, 0.0), cw((size_t)std::max(C, 1) * 2 * KS, 0.0);
+    for (int e = 0; e < E; ++e) {
+      const hm::DegreeTables &t = m->tabs.at(m->W[e]);
+      double *ax = &hw[(size_t)e * 8 * KS], *bz = ax + 4 * KS;
+      for (int q = 0; q < t.Q; ++q) {
+        const double x = m->lo[3 * e] + (t.xq[q] + 1.0) * 0.5 * (m->hi[3 * e] - m->lo[3 * e]);
+        const double z = m->lo[3 * e + 2] + (t.xq[q] + 1.0) * 0.5 * (m->hi[3 * e + 2] - m->lo[3 * e + 2]);
+        double a[4], b[4];
+        if (vtx) {
+          const double sp = std::sin(x), ez = std::exp(z);
+          a[0] = sp, a[1] = sp, a[2] = 1.0 / sp, a[3] = sp;
+          b[0] = ez * ez * ez, b[1] = ez, b[2] = ez, b[3] = ez;
+        } else if (ve) {
+          const double e2x = std::exp(2.0 * x), ez = std::exp(z);
+          a[0] = e2x, a[1] = 1.0, a[2] = 1.0, a[3] = e2x;
+          b[0] = ez * ez * ez, b[1] = ez, b[2] = ez, b[3] = ez;
+        } else {
+          const double e2x = std::exp(2.0 * x);
+          a[0] = e2x, a[1] = 1.0, a[2] = 1.0, a[3] = e2x;
+          b[0] = b[1] = b[2] = b[3] = 1.0;
+        }
+        for (int k = 0; k < 4; ++k) {
+          ax[k * KS + q] = a[k];
+          bz[k * KS + q] = b[k];
+        }
+      }
+    }
+    std::vector<double> ptop((size_t)std::max(C, 1) * E, -1e300);  // vertex-edge cones: psi_top per (set, sector)
+    for (int e = 0; e < E; ++e) {
+      for (int f : {0, 4}) {
+        if (m->nbr[6 * e + f] >= -1) continue;
+        const int c = -2 - m->nbr[6 * e + f];
+        const double th = m->hi[3 * e + 1] - m->lo[3 * e + 1];
+        double *w0 = &cw[(size_t)c * 2 * KS], *w1 = w0 + KS;
+        if (m->cW[c] > 0) {
+          // a polynomial along the third variable (edge: x3, vertex-edge: zeta)
+          const hm::DegreeTables &t = m->tabs.at(m->cW[c]);
+          const double hz = m->hi[3 * e + 2] - m->lo[3 * e + 2], sz = 2.0 / hz;
+          for (int q = 0; q < t.Q; ++q) {
+            if (ve) {
+              const double zq = m->lo[3 * e + 2] + (t.xq[q] + 1.0) * 0.5 * hz, ez = std::exp(zq);
+              const double f0 = 0.5 * std::exp(2.0 * m->lo[3 * e]) * th * 0.5 * hz * t.wq[q];
+              w0[q] += f0 * ez * ez * ez;
+              w1[q] += f0 * ez * sz * sz;
+            } else {
+              const double r1 = std::exp(m->lo[3 * e]);
+              const double f0 = 0.5 * r1 * r1 * th * 0.5 * hz * t.wq[q];
+              w0[q] += f0;
+              w1[q] += f0 * sz * sz;
+            }
+          }
+        } else if (vtx) {
+          const double r1 = std::exp(m->lo[3 * e + 2]);
+          w0[0] += r1 * r1 * r1 / 3.0 * (std::cos(m->lo[3 * e]) - std::cos(m->hi[3 * e])) * th;
+        } else if (ve) {
+          // one cone per theta sector: psi_top = the largest psi of the set's elements in it
+          for (int e2 = 0; e2 < E; ++e2)
+            if (m->nbr[6 * e2 + 4] == m->nbr[6 * e + 4] && std::fabs(m->lo[3 * e2 + 1] - m->lo[3 * e + 1]) < 1e-14)
+              ptop[(size_t)c * E + e] = std::max(ptop[(size_t)c * E + e], m->hi[3 * e2]);
+          if (std::fabs(m->hi[3 * e] - ptop[(size_t)c * E + e]) < 1e-14) {
+            const double x31 = std::exp(m->lo[3 * e + 2]);
+            w0[0] += th * 0.5 * std::exp(2.0 * ptop[(size_t)c * E + e]) * x31 * x31 * x31 / 3.0;
+          }
+        }
+      }
+    }
+    CK(upload(m->d_h1w, hw));
+    CK(upload(m->d_ch1w, cw));
   }
-  CK(upload(m->d_ch1, ch1));
   const size_t ns = (size_t)std::max(1, S) * m->n_rhs * hpse::CSCR_STRIDE;
   CK(m->d_cscr64.alloc(ns * sizeof(double)));
   CK(m->d_cscr32.alloc(ns * sizeof(float)));
@@ -2684,10 +2784,8 @@ extern "C" hpse_status hpse_pcg_solve(hpse_mesh *m, const hpse_solve_opts *o, do
 
 extern "C" hpse_status hpse_h1_error(hpse_mesh *m, const double *u, const double *ref, const double *vq,
                                      const double *gq, double *out, void *stream) {
-  // edge neighbourhood: the difference of two discrete solutions only
-  if (m && ((m->coord == HPSE_COORD_EDGE && !ref) || m->coord == HPSE_COORD_VERTEX ||
-            m->coord == HPSE_COORD_VERTEX_EDGE))
-    return HPSE_ERR_INVALID_ARG;
+  // neighbourhood meshes: the difference of two discrete solutions only
+  if (m && m->coord != HPSE_COORD_CARTESIAN && !ref) return HPSE_ERR_INVALID_ARG;
   if (!m || !out) return HPSE_ERR_INVALID_ARG;
   if (m->ndof == 0) {
     for (int r = 0; r < m->n_rhs; ++r) out[2 * r] = out[2 * r + 1] = 0.0;
@@ -2723,11 +2821,12 @@ extern "C" hpse_status hpse_h1_error(hpse_mesh *m, const double *u, const double
   A.gq = gq;
   A.part_err = pe.as<double>();
   A.part_nrm = pn.as<double>();
-  A.kappa = m->coord == HPSE_COORD_EDGE ? m->d_kappa64.as<double>() : nullptr;
+  A.hw = m->coord != HPSE_COORD_CARTESIAN ? m->d_h1w.as<double>() : nullptr;
+  A.hc = m->coord == HPSE_COORD_VERTEX_EDGE ? 1.0 : 0.0;
   A.n_elem = m->n_elem;
   A.n_corner = m->n_corner;
   A.cW = m->d_cW.as<int32_t>();
-  A.cfac = m->d_ch1.as<double>();
+  A.cw = m->d_ch1w.as<double>();
   const int P = Wmax + 1, Q = 2 * Wmax + 1;
   const size_t smem = (size_t)(P * P * P + 2 * Q * P * P + 3 * Q * Q * P) * sizeof(double);
   CK(raise_smem((const void *)k_h1, m->device, (size_t)smem));

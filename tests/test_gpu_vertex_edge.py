@@ -175,3 +175,24 @@ def test_vertex_edge_h1_error_from_gpu_solutions(api):
         assert errs[W] < 2.5 * ints[W], (W, errs, ints)
     for W in (3, 4, 5):
         assert errs[W] < 0.6 * errs[W - 1], errs
+
+
+def test_h1_norm_of_difference_matches_oracle(api):
+    # difference of two discrete solutions in physical coordinates: elements by
+    # their (2W+1)^3 GLL rule with the neighbourhood's volume and gradient
+    # weights, corner sets exactly in the radial variable; both sides sum the
+    # same terms in FP64 (1e-12 relative)
+    from oracle.vertex_edge import h1_diff
+    pb = _problem(2, 3, 2)
+    d = VertexEdgeDiscretisation(pb)
+    m = _mesh(api, pb)
+    rng = np.random.default_rng(6)
+    U, V = rng.standard_normal(d.ndof), rng.standard_normal(d.ndof)
+    h = m.h1_error(torch.tensor(U, device="cuda"), ref=torch.tensor(V, device="cuda"))
+    e, n = h1_diff(d, U, V)
+    assert h[0, 0] == pytest.approx(e, rel=1e-12) and h[0, 1] == pytest.approx(n, rel=1e-12)
+    # against the exact solution the library still needs a discrete reference
+    with pytest.raises(api._lib.HpseError):
+        m.h1_error(torch.tensor(U, device="cuda"), vq=torch.zeros(m.nquad, dtype=torch.float64, device="cuda"),
+                   gq=torch.zeros(3 * m.nquad, dtype=torch.float64, device="cuda"))
+    m.close()

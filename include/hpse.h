@@ -323,6 +323,20 @@ hpse_status hpse_pcg_solve(hpse_mesh *m, const hpse_solve_opts *opts, double *x,
 hpse_status hpse_h1_error(hpse_mesh *m, const double *u, const double *ref,
                           const double *vq, const double *gq, double *out, void *stream);
 
+/* Conforming correction (Remark 4.3.0; the construction in the proof of
+ * Lemma 3.3.1, Appendix C.1): p = u + delta + epsilon + nu, the nodal
+ * solution u corrected to a conforming function in H^1 that vanishes on the
+ * Dirichlet faces: delta trilinear to the average of u at every element
+ * vertex, epsilon per element edge to the average of u + delta along it
+ * (blended bilinearly in the other variables), nu per face to the average of
+ * the two traces (blended linearly in the normal variable); target 0 on the
+ * Dirichlet boundary.  p stays in the (W+1)^3 nodal space of every element.
+ * u, p: device FP64 DOF vectors of n_rhs*ndof (p may be u).  Box meshes
+ * (HPSE_ERR_INVALID_ARG for neighbourhood kinds).  The first call builds the
+ * vertex and edge tables and two scratch vectors on the handle (synchronous);
+ * later calls are asynchronous on `stream`. */
+hpse_status hpse_conforming_correction(hpse_mesh *m, const double *u, double *p, void *stream);
+
 /* Residual map and its transpose (Section 5.3: the weighted PDE residual of
  * eq. (4.2) collocated on the (2W+1)^3 GLL points), box meshes.
  *   hpse_apply_residual:  z[r][q] = sqrt(w_q J) (L u_r - f_r)(x_q), with

@@ -188,6 +188,11 @@ class Mesh:
                                       _stream(stream)), "hpse_h1_error")
         return out.reshape(self.n_rhs, 2)
 
+    def conforming_correction(self, u, p, stream=None):
+        """p = the conforming correction of the FP64 solution u (box meshes)."""
+        check(self._lib.hpse_conforming_correction(self._h, _ptr(u), _ptr(p), _stream(stream)),
+              "hpse_conforming_correction")
+
     # -- residual map, point fields and adjoint data gradients (FP64) -------
     def apply_residual(self, u, z, stream=None):
         check(self._lib.hpse_apply_residual(self._h, _prec_of(u), _ptr(u), _ptr(z), _stream(stream)),

@@ -202,6 +202,12 @@ struct hpse_mesh {
   DevBuf d_aux;               // FP64 [5][nquad]: w J, a, a_x, a_y, a_z at the volume points
   DevBuf d_tabs_ptr;          // device array of the per-degree FP64 table pointers
   DevBuf d_scr_fields, d_scr_rho;  // scratch of the residual map and its transpose
+  // conforming correction (box meshes; built on first use): per element corner
+  // (8) and edge (12) the shared vertex / edge, their members (CSR) and
+  // Dirichlet flags, the linear blends (1 -+ x)/2 at the GLL nodes per degree
+  bool conf_ready = false;
+  DevBuf d_cf_vid, d_cf_vptr, d_cf_vmem, d_cf_vdir, d_cf_eid, d_cf_eptr, d_cf_emem, d_cf_edir, d_cf_lin;
+  DevBuf d_cf_linptr, d_cf_w, d_cf_v;
   DevBuf d_bnorm2;            // FP64 ||b||^2 per (problem, rhs)
   std::map<int, DevBuf> d_qtab;  // per degree FP64 Q-grid tables for the face data
   bool has_data = false;
@@ -3238,6 +3244,274 @@ extern "C" hpse_status hpse_set_rhs(hpse_mesh *m, const double *b, void *stream)
 #define HPSE_NOALLOC_MAX_RHS 4096
 #define HPSE_NOALLOC_MAX_DEVICES 64
 #define HPSE_NOALLOC_DOUBLES (2 * HPSE_NOALLOC_MAX_ITEMS + 2 * HPSE_NOALLOC_MAX_RHS + 16)
+// ---------------------------------------------------------------------------
+// Conforming correction (Remark 4.3.0; the construction in the proof of Lemma
+// 3.3.1, Appendix C.1) of box-element solutions, on the nodal values:
+//   1. delta: trilinear, (u + delta) = the average of u at every element vertex
+//      over the elements sharing it (0 on the Dirichlet boundary);
+//   2. epsilon: per element edge the average of u + delta along it minus the
+//      own trace, blended bilinearly in the other two variables;
+//   3. nu: per face the average of the two traces of u + delta + epsilon
+//      (0 on a Dirichlet face) minus the own trace, blended linearly in the
+//      normal variable.
+// Each correction is degree one in the blended variables, so p stays in the
+// element's (W+1)^3 nodal space.  One CTA per (element, rhs) in each stage.
+// ---------------------------------------------------------------------------
+struct ConfArgs {
+  int n_rhs;
+  int64_t ndof;
+  const int64_t *dof_off;
+  const int32_t *elem_W, *nbr;
+  const int32_t *vid, *vptr, *vmem, *vdir;  // vertex id per (element, corner), members (element * 8 + corner)
+  const int32_t *eid, *eptr, *emem, *edir;  // edge id per (element, edge), members (element * 12 + edge)
+  const double *const *lin;                 // per degree: (1 - x)/2 then (1 + x)/2 at the P GLL nodes
+};
+
+// node (i, j, k) of corner c (bit a of c: the side along axis a)
+__device__ __forceinline__ int conf_corner_node(int c, int P) {
+  const int i = (c & 1) ? P - 1 : 0, j = ((c >> 1) & 1) ? P - 1 : 0, k = ((c >> 2) & 1) ? P - 1 : 0;
+  return (k * P + j) * P + i;
+}
+// node t of element edge k = 4 a + s1 + 2 s2 (along axis a; s1, s2 the sides
+// of the other two axes in increasing order)
+__device__ __forceinline__ int conf_edge_node(int k, int t, int P) {
+  const int a = k >> 2, s1 = k & 1, s2 = (k >> 1) & 1;
+  int c[3];
+  const int o1 = a == 0 ? 1 : 0, o2 = a == 2 ? 1 : 2;
+  c[a] = t;
+  c[o1] = s1 ? P - 1 : 0;
+  c[o2] = s2 ? P - 1 : 0;
+  return (c[2] * P + c[1]) * P + c[0];
+}
+
+__global__ void k_conf_vertex(ConfArgs A, const double *u, double *w) {
+  __shared__ double d[8];
+  const int e = blockIdx.x / A.n_rhs, r = blockIdx.x - e * A.n_rhs;
+  const int P = A.elem_W[e] + 1;
+  const int64_t rb = (int64_t)r * A.ndof;
+  if (threadIdx.x < 8) {
+    const int c = threadIdx.x, g = A.vid[e * 8 + c];
+    double t = 0.0;
+    if (!A.vdir[g]) {
+      for (int m = A.vptr[g]; m < A.vptr[g + 1]; ++m) {
+        const int em = A.vmem[m] >> 3, cm = A.vmem[m] & 7;
+        t += u[rb + A.dof_off[em] + conf_corner_node(cm, A.elem_W[em] + 1)];
+      }
+      t /= (double)(A.vptr[g + 1] - A.vptr[g]);
+    }
+    d[c] = t - u[rb + A.dof_off[e] + conf_corner_node(c, P)];
+  }
+  __syncthreads();
+  const double *L = A.lin[P - 1];
+  const int64_t base = rb + A.dof_off[e];
+  for (int t = threadIdx.x; t < P * P * P; t += blockDim.x) {
+    const int i = t % P, j = (t / P) % P, k = t / (P * P);
+    double s = u[base + t];
+    for (int c = 0; c < 8; ++c)
+      s += d[c] * L[(c & 1) * P + i] * L[((c >> 1) & 1) * P + j] * L[((c >> 2) & 1) * P + k];
+    w[base + t] = s;
+  }
+}
+
+// dynamic shared memory: 12 * P doubles
+__global__ void k_conf_edge(ConfArgs A, const double *w, double *v) {
+  extern __shared__ double gk[];
+  const int e = blockIdx.x / A.n_rhs, r = blockIdx.x - e * A.n_rhs;
+  const int P = A.elem_W[e] + 1;
+  const int64_t rb = (int64_t)r * A.ndof, base = rb + A.dof_off[e];
+  for (int q = threadIdx.x; q < 12 * P; q += blockDim.x) {
+    const int k = q / P, t = q - k * P, g = A.eid[e * 12 + k];
+    double tg = 0.0;
+    if (!A.edir[g]) {
+      for (int m = A.eptr[g]; m < A.eptr[g + 1]; ++m) {
+        const int em = A.emem[m] / 12, km = A.emem[m] - 12 * em;
+        tg += w[rb + A.dof_off[em] + conf_edge_node(km, t, A.elem_W[em] + 1)];
+      }
+      tg /= (double)(A.eptr[g + 1] - A.eptr[g]);
+    }
+    gk[q] = tg - w[base + conf_edge_node(k, t, P)];
+  }
+  __syncthreads();
+  const double *L = A.lin[P - 1];
+  for (int t = threadIdx.x; t < P * P * P; t += blockDim.x) {
+    const int c[3] = {t % P, (t / P) % P, t / (P * P)};
+    double s = w[base + t];
+    for (int k = 0; k < 12; ++k) {
+      const int a = k >> 2, o1 = a == 0 ? 1 : 0, o2 = a == 2 ? 1 : 2;
+      s += gk[k * P + c[a]] * L[(k & 1) * P + c[o1]] * L[((k >> 1) & 1) * P + c[o2]];
+    }
+    v[base + t] = s;
+  }
+}
+
+// dynamic shared memory: 6 * P * P doubles
+__global__ void k_conf_face(ConfArgs A, const double *v, double *p) {
+  extern __shared__ double cf[];
+  const int e = blockIdx.x / A.n_rhs, r = blockIdx.x - e * A.n_rhs;
+  const int P = A.elem_W[e] + 1, P2 = P * P;
+  const int64_t rb = (int64_t)r * A.ndof, base = rb + A.dof_off[e];
+  for (int q = threadIdx.x; q < 6 * P2; q += blockDim.x) {
+    const int f = q / P2, sp = q - f * P2, p1 = sp % P, p2 = sp / P;
+    const int a = f >> 1, side = f & 1, n = side ? P - 1 : 0;
+    // face point (p1, p2) along (t1, t2), t1 < t2 the axes other than a
+    auto node = [&](int nn) {
+      if (a == 0) return (p2 * P + p1) * P + nn;
+      if (a == 1) return (p2 * P + nn) * P + p1;
+      return (nn * P + p2) * P + p1;
+    };
+    const double own = v[base + node(n)];
+    const int nb = A.nbr[e * 6 + f];
+    double tg = 0.0;
+    if (nb >= 0) tg = 0.5 * (own + v[rb + A.dof_off[nb] + node(P - 1 - n)]);
+    cf[q] = tg - own;
+  }
+  __syncthreads();
+  const double *L = A.lin[P - 1];
+  for (int t = threadIdx.x; t < P * P * P; t += blockDim.x) {
+    const int c[3] = {t % P, (t / P) % P, t / P2};
+    double s = v[base + t];
+    for (int f = 0; f < 6; ++f) {
+      const int a = f >> 1, o1 = a == 0 ? 1 : 0, o2 = a == 2 ? 1 : 2;
+      s += cf[f * P2 + c[o2] * P + c[o1]] * L[(f & 1) * P + c[a]];
+    }
+    p[base + t] = s;
+  }
+}
+
+// topology of the conforming correction (box meshes), built once per handle
+static hpse_status conf_setup(hpse_mesh *m) {
+  const int E = m->n_elem;
+  struct Key {
+    int pr, kind;
+    long long c[5];
+    bool operator<(const Key &o) const {
+      if (pr != o.pr) return pr < o.pr;
+      if (kind != o.kind) return kind < o.kind;
+      for (int i = 0; i < 5; ++i)
+        if (c[i] != o.c[i]) return c[i] < o.c[i];
+      return false;
+    }
+  };
+  // coordinates to integer keys (1e-9 relative to the mesh's extent)
+  double ext = 1.0;
+  for (size_t i = 0; i < m->lo.size(); ++i) ext = std::max({ext, std::fabs(m->lo[i]), std::fabs(m->hi[i])});
+  auto q = [&](double x) { return (long long)std::llround(x / (ext * 1e-9)); };
+  auto X = [&](int e, int a, int side) { return side ? m->hi[3 * e + a] : m->lo[3 * e + a]; };
+  auto dir_face = [&](int e, int f) { return m->nbr[6 * e + f] == -1; };
+  std::map<Key, int> vmap, emap;
+  std::vector<int> vid(8 * (size_t)E), eid(12 * (size_t)E), vdir, edir;
+  std::vector<std::vector<int>> vmem, emem;
+  for (int e = 0; e < E; ++e) {
+    const int pr = m->prob[e];
+    for (int c = 0; c < 8; ++c) {
+      Key k{pr, 0, {q(X(e, 0, c & 1)), q(X(e, 1, (c >> 1) & 1)), q(X(e, 2, (c >> 2) & 1)), 0, 0}};
+      auto it = vmap.find(k);
+      int g;
+      if (it == vmap.end()) {
+        g = (int)vmem.size();
+        vmap[k] = g;
+        vmem.emplace_back();
+        vdir.push_back(0);
+      } else {
+        g = it->second;
+      }
+      vid[8 * e + c] = g;
+      vmem[g].push_back(8 * e + c);
+      for (int a = 0; a < 3; ++a)
+        if (dir_face(e, 2 * a + ((c >> a) & 1))) vdir[g] = 1;
+    }
+    for (int kk = 0; kk < 12; ++kk) {
+      const int a = kk >> 2, s1 = kk & 1, s2 = (kk >> 1) & 1;
+      const int o1 = a == 0 ? 1 : 0, o2 = a == 2 ? 1 : 2;
+      Key k{pr, 1 + a, {q(X(e, o1, s1)), q(X(e, o2, s2)), q(X(e, a, 0)), q(X(e, a, 1)), 0}};
+      auto it = emap.find(k);
+      int g;
+      if (it == emap.end()) {
+        g = (int)emem.size();
+        emap[k] = g;
+        emem.emplace_back();
+        edir.push_back(0);
+      } else {
+        g = it->second;
+      }
+      eid[12 * e + kk] = g;
+      emem[g].push_back(12 * e + kk);
+      if (dir_face(e, 2 * o1 + s1) || dir_face(e, 2 * o2 + s2)) edir[g] = 1;
+    }
+  }
+  std::vector<int> vptr(1, 0), vm, eptr(1, 0), em;
+  for (auto &l : vmem) {
+    vm.insert(vm.end(), l.begin(), l.end());
+    vptr.push_back((int)vm.size());
+  }
+  for (auto &l : emem) {
+    em.insert(em.end(), l.begin(), l.end());
+    eptr.push_back((int)em.size());
+  }
+  // linear blends per degree
+  std::vector<double> lin;
+  std::vector<size_t> loff(HPSE_MAX_W + 1, 0);
+  for (auto &kv : m->tabs) {
+    const hm::DegreeTables &t = kv.second;
+    loff[kv.first] = lin.size();
+    for (int side = 0; side < 2; ++side)
+      for (int i = 0; i < t.P; ++i) lin.push_back(side ? 0.5 * (1.0 + t.xp[i]) : 0.5 * (1.0 - t.xp[i]));
+  }
+  CK(upload(m->d_cf_vid, vid));
+  CK(upload(m->d_cf_vptr, vptr));
+  CK(upload(m->d_cf_vmem, vm));
+  CK(upload(m->d_cf_vdir, vdir));
+  CK(upload(m->d_cf_eid, eid));
+  CK(upload(m->d_cf_eptr, eptr));
+  CK(upload(m->d_cf_emem, em));
+  CK(upload(m->d_cf_edir, edir));
+  CK(upload(m->d_cf_lin, lin));
+  std::vector<const double *> lp(HPSE_MAX_W + 1, nullptr);
+  for (auto &kv : m->tabs) lp[kv.first] = m->d_cf_lin.as<double>() + loff[kv.first];
+  CK(upload(m->d_cf_linptr, lp));
+  const size_t nv = (size_t)m->n_rhs * std::max<int64_t>(m->ndof, 1) * sizeof(double);
+  CK(m->d_cf_w.alloc(nv));
+  CK(m->d_cf_v.alloc(nv));
+  m->conf_ready = true;
+  return HPSE_OK;
+}
+
+extern "C" hpse_status hpse_conforming_correction(hpse_mesh *m, const double *u, double *p, void *stream) {
+  if (!m || m->coord != HPSE_COORD_CARTESIAN) return HPSE_ERR_INVALID_ARG;  // box meshes only
+  if (m->ndof == 0) return HPSE_OK;
+  if (!u || !p) return HPSE_ERR_INVALID_ARG;
+  CK(cudaSetDevice(m->device));
+  if (!m->conf_ready) {
+    const hpse_status st = conf_setup(m);
+    if (st != HPSE_OK) return st;
+  }
+  ConfArgs A;
+  A.n_rhs = m->n_rhs;
+  A.ndof = m->ndof;
+  A.dof_off = m->d_dof_off.as<int64_t>();
+  A.elem_W = m->d_elem_W.as<int32_t>();
+  A.nbr = m->d_nbr.as<int32_t>();
+  A.vid = m->d_cf_vid.as<int32_t>();
+  A.vptr = m->d_cf_vptr.as<int32_t>();
+  A.vmem = m->d_cf_vmem.as<int32_t>();
+  A.vdir = m->d_cf_vdir.as<int32_t>();
+  A.eid = m->d_cf_eid.as<int32_t>();
+  A.eptr = m->d_cf_eptr.as<int32_t>();
+  A.emem = m->d_cf_emem.as<int32_t>();
+  A.edir = m->d_cf_edir.as<int32_t>();
+  A.lin = m->d_cf_linptr.as<const double *>();
+  int Wmax = 1;
+  for (auto &kv : m->tabs) Wmax = std::max(Wmax, kv.first);
+  const int P = Wmax + 1, items = m->n_elem * m->n_rhs;
+  cudaStream_t s = (cudaStream_t)stream;
+  k_conf_vertex<<<items, 128, 0, s>>>(A, u, m->d_cf_w.as<double>());
+  k_conf_edge<<<items, 128, 12 * P * sizeof(double), s>>>(A, m->d_cf_w.as<double>(), m->d_cf_v.as<double>());
+  k_conf_face<<<items, 128, 6 * P * P * sizeof(double), s>>>(A, m->d_cf_v.as<double>(), p);
+  CK(cudaGetLastError());
+  g_launches += 3;
+  return HPSE_OK;
+}
+
 static __device__ __align__(256) double g_noalloc_scratch[HPSE_NOALLOC_DOUBLES];
 
 static double *g_noalloc_addr[HPSE_NOALLOC_MAX_DEVICES];

@@ -119,6 +119,17 @@ typedef struct {
   int32_t n_corner;            /* corner sets (HPSE_COORD_EDGE), else 0            */
   const int32_t *corner_W;     /* [n_corner] degree in x3 (= that of its elements) */
   const int32_t *corner_problem; /* [n_corner] problem index                       */
+  /* Outer-face conditions (eq. 2.1, the last sum of eq. 4.2).  face_bc
+   * [n_elem*6], on faces with elem_nbr == -1: 0 Dirichlet (u = g), 1 Neumann
+   * (du/dnu = h), 2 Robin (du/dnu + gamma u = h); NULL: every outer face
+   * Dirichlet.  A Neumann / Robin face measures the outward normal derivative
+   * (+ gamma u) minus h in the H^{1/2} norm of the other face terms; its data
+   * h replaces g in hpse_set_data at that face's points.  robin_gamma
+   * [n_problem] (NULL: 1).  Neumann and Robin faces need box elements and
+   * HPSE_COEF_LAPLACE (else HPSE_ERR_INVALID_ARG): the conormal derivative of
+   * a variable coefficient is not built. */
+  const int32_t *face_bc;
+  const double *robin_gamma;
 } hpse_mesh_desc;
 
 /* HPSE_COORD_VERTEX (eq. 4.3): boxes in (phi, theta, chi) = (phi, theta, ln rho)

@@ -30,6 +30,7 @@ class MeshDesc(C.Structure):
         ("elem_W", C.c_void_p), ("elem_problem", C.c_void_p), ("elem_lo", C.c_void_p),
         ("elem_hi", C.c_void_p), ("elem_nbr", C.c_void_p),
         ("coord", C.c_int32), ("n_corner", C.c_int32), ("corner_W", C.c_void_p), ("corner_problem", C.c_void_p),
+        ("face_bc", C.c_void_p), ("robin_gamma", C.c_void_p),
     ]
 
 

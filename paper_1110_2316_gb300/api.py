@@ -50,11 +50,10 @@ class Mesh:
     elem_problem [E] and n_problem (e.g. workloads.MeshDesc).
     """
 
-    def __init__(self, desc, n_rhs=1, coef_kind=COEF_LAPLACE, device=0):
-        bc = getattr(desc, "elem_bc", None)
-        if bc is not None and np.any((np.asarray(bc) != 0) & (np.asarray(desc.elem_nbr) == -1)):
-            raise ValueError("Neumann faces (eq. 2.1) are not supported by the CUDA operator: "
-                             "every outer face must be Dirichlet")
+    def __init__(self, desc, n_rhs=1, coef_kind=COEF_LAPLACE, device=0, robin_gamma=None):
+        """``desc.elem_bc`` (optional, [E,6]): 0 Dirichlet, 1 Neumann, 2 Robin
+        on outer faces; ``robin_gamma``: the Robin gamma, one per problem or a
+        scalar (default 1)."""
         self._lib = _lib.load()
         self._keep = [np.ascontiguousarray(desc.elem_W, dtype=np.int32),
                       np.ascontiguousarray(desc.elem_problem, dtype=np.int32),
@@ -82,6 +81,16 @@ class Mesh:
         else:
             d.coord = _lib.COORD_CARTESIAN
             d.n_corner = 0
+        bc = getattr(desc, "elem_bc", None)
+        self.face_bc = None
+        if bc is not None and np.any(np.asarray(bc) != 0):
+            self.face_bc = np.ascontiguousarray(bc, dtype=np.int32).reshape(-1, 6)
+            gam = np.broadcast_to(np.asarray(1.0 if robin_gamma is None else robin_gamma, dtype=np.float64),
+                                  (int(desc.n_problem),))
+            self.robin_gamma = np.ascontiguousarray(gam)
+            self._keep += [self.face_bc, self.robin_gamma]
+            d.face_bc = self._keep[-2].ctypes.data_as(C.c_void_p)
+            d.robin_gamma = self._keep[-1].ctypes.data_as(C.c_void_p)
         h = C.c_void_p()
         check(self._lib.hpse_setup_mesh(C.byref(d), int(device), C.byref(h)), "hpse_setup_mesh")
         self._h = h
@@ -322,8 +331,19 @@ def problem_data_arrays(mesh: Mesh, problem):
                 axis = fi // 2
                 grid = list(axes[e])
                 grid[axis] = np.array([fnorm[k]])
+                bc = 0 if getattr(mesh, "face_bc", None) is None else int(mesh.face_bc[e, fi])
                 for r in range(R):
-                    g[r, fo:fo + Q * Q] = part(e).g[r](*grid).ravel()
+                    if bc == 0:
+                        g[r, fo:fo + Q * Q] = part(e).g[r](*grid).ravel()
+                    else:
+                        # Neumann / Robin data h = nu . q (+ gamma g) from the conormal field q
+                        q = part(e).flux[r](*grid)[axis]
+                        shape = (len(grid[2]), len(grid[1]), len(grid[0]))
+                        h = (1.0 if fi % 2 else -1.0) * np.broadcast_to(q, shape)
+                        if bc == 2:
+                            gam = float(mesh.robin_gamma[int(eprob[e])])
+                            h = h + gam * np.broadcast_to(part(e).g[r](*grid), shape)
+                        g[r, fo:fo + Q * Q] = h.ravel()
                 fo += Q * Q
                 k += 1
     return dict(f=f, a=a, grad_a=grad, g=g)

@@ -185,6 +185,12 @@ struct hpse_mesh {
   int n_elem = 0, n_problem = 0, n_rhs = 0, coef_kind = 0;
   std::vector<int> W, prob, nbr;
   std::vector<double> lo, hi;
+  // outer-face conditions per (element, face): 0 Dirichlet, 1 Neumann, 2 Robin;
+  // the Robin gamma per (element, face); has_nr: some face is Neumann or Robin
+  std::vector<int> fbc;
+  std::vector<double> fgam;
+  bool has_nr = false;
+  DevBuf d_fbc, d_fgam64, d_fgam32;
   std::vector<int64_t> dof_off, coef_off;
   int64_t ndof = 0, nquad = 0;
   std::vector<int> bface_elem, bface_fi;   // boundary faces
@@ -577,6 +583,9 @@ struct FaceDataArgs {
   const double *g;            // [n_rhs][nface_pts]
   double *b;
   const double *fw;           // edge neighbourhood: [E][6][10] face-norm weights, else null
+  const int32_t *fbc;         // [E][6] outer-face conditions (null: all Dirichlet)
+  const double *fgam;         // [E][6] Robin gamma
+  const double *geo;          // [E][4] s_x, s_y, s_z, J
 };
 
 __global__ void k_face_data(FaceDataArgs A) {
@@ -595,6 +604,52 @@ __global__ void k_face_data(FaceDataArgs A) {
     const int64_t go = (int64_t)r * A.nface_pts + A.face_off[fi_i];
     for (int t = threadIdx.x; t < Q * Q; t += blockDim.x) g[t] = A.g[go + t];
     __syncthreads();
+    const int bc = A.fbc ? A.fbc[(int64_t)e * 6 + fi] : 0;
+    if (bc) {
+      // Neumann / Robin face: the data h in the H^{1/2} norm (L2 included),
+      // back through the transposed outward normal derivative (+ gamma u)
+      for (int t = threadIdx.x; t < Q * Q; t += blockDim.x) {
+        const int i = t % Q, j = t / Q;
+        double k1 = 0.0, l1 = 0.0;
+        for (int m = 0; m < Q; ++m) {
+          k1 += KQ[i * Q + m] * g[j * Q + m];
+          l1 += KQ[j * Q + m] * g[m * Q + i];
+        }
+        h0[t] = wq[i] * wq[j] * g[t] + wq[j] * k1 + wq[i] * l1;
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < Q * P; t += blockDim.x) {
+        const int p1 = t % P, j = t / P;
+        double s0 = 0.0;
+        for (int i = 0; i < Q; ++i) s0 += B0[i * P + p1] * h0[j * Q + i];
+        ta[j * P + p1] = s0;
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < P * P; t += blockDim.x) {
+        const int p1 = t % P, p2 = t / P;
+        double s0 = 0.0;
+        for (int j = 0; j < Q; ++j) s0 += B0[j * P + p2] * ta[j * P + p1];
+        F[t] = s0;
+      }
+      __syncthreads();
+      // d/dlambda_a at the face (the endpoint row of B1) times the outward sign and s_a
+      const double sn = (side ? 1.0 : -1.0) * A.geo[4 * (int64_t)e + a];
+      const double gam = bc == 2 ? A.fgam[(int64_t)e * 6 + fi] : 0.0;
+      const double *Dn = B1 + (side ? Q - 1 : 0) * P;
+      const int nend = side ? P - 1 : 0;
+      for (int t = threadIdx.x; t < P * P; t += blockDim.x) {
+        const int p1 = t % P, p2 = t / P;
+        for (int n = 0; n < P; ++n) {
+          int idx;
+          if (a == 0) idx = (p2 * P + p1) * P + n;
+          else if (a == 1) idx = (p2 * P + n) * P + p1;
+          else idx = (n * P + p2) * P + p1;
+          A.b[base + idx] += (sn * Dn[n] + (n == nend ? gam : 0.0)) * F[t];
+        }
+      }
+      __syncthreads();
+      continue;
+    }
     // tangential derivatives of the data on the face grid [t2][t1]
     for (int t = threadIdx.x; t < Q * Q; t += blockDim.x) {
       const int i = t % Q, j = t / Q;
@@ -881,6 +936,10 @@ static ApplyArgsT<T> apply_args(const hpse_mesh *m, const Group &g, const T *u, 
     a.fw = d ? (const T *)m->d_fw64.p : (const T *)m->d_fw32.p;
     a.cslot = m->d_cslot.as<int32_t>();
     a.cscr = m->n_corner ? (d ? (T *)m->d_cscr64.p : (T *)m->d_cscr32.p) : nullptr;
+  }
+  if (m->has_nr) {
+    a.fbc = m->d_fbc.as<int32_t>();
+    a.fgam = (sizeof(T) == 8) ? (const T *)m->d_fgam64.p : (const T *)m->d_fgam32.p;
   }
   return a;
 }
@@ -1463,6 +1522,23 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
           !std::isfinite(m->hi[3 * e + a]))
         return HPSE_ERR_INVALID_ARG;
   }
+  // outer-face conditions (eq. 2.1): Neumann and Robin faces on box meshes of the Laplacian
+  m->fbc.assign(6 * (size_t)E, 0);
+  m->fgam.assign(6 * (size_t)E, 0.0);
+  if (d->face_bc) {
+    for (size_t i = 0; i < 6 * (size_t)E; ++i) {
+      const int c = d->face_bc[i];
+      if (c < 0 || c > 2 || (c != 0 && m->nbr[i] != -1)) return HPSE_ERR_INVALID_ARG;
+      m->fbc[i] = c;
+      if (c == 2) {
+        const double g = d->robin_gamma ? d->robin_gamma[m->prob[i / 6]] : 1.0;
+        if (!std::isfinite(g)) return HPSE_ERR_INVALID_ARG;
+        m->fgam[i] = g;
+      }
+      if (c != 0) m->has_nr = true;
+    }
+    if (m->has_nr && (nbhd || d->coef_kind != HPSE_COEF_LAPLACE)) return HPSE_ERR_INVALID_ARG;
+  }
   const int C = m->n_corner;
   for (int c = 0; c < C; ++c)
     if (m->cW[c] < 0 || m->cW[c] > HPSE_MAX_W || m->cprob[c] < 0 || m->cprob[c] >= m->n_problem)
@@ -1652,6 +1728,12 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
   CK(upload(m->d_nbr, m->nbr));
   CK(upload(m->d_geo64, geo));
   CK(upload(m->d_geo32, geo32));
+  if (m->has_nr) {
+    std::vector<float> g32(m->fgam.begin(), m->fgam.end());
+    CK(upload(m->d_fbc, m->fbc));
+    CK(upload(m->d_fgam64, m->fgam));
+    CK(upload(m->d_fgam32, g32));
+  }
   {
     // problem of every vector item (elements, then corner sets): the vector
     // kernels index it by item
@@ -1947,6 +2029,9 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data, void *
     A.g = dg.as<double>();
     A.b = m->d_b.as<double>();
     A.fw = m->coord != HPSE_COORD_CARTESIAN ? m->d_fw64.as<double>() : nullptr;
+    A.fbc = m->has_nr ? m->d_fbc.as<int32_t>() : nullptr;
+    A.fgam = m->has_nr ? m->d_fgam64.as<double>() : nullptr;
+    A.geo = m->d_geo64.as<double>();
     const int Q = 2 * Wmax + 1, P = Wmax + 1;
     const size_t smem = (size_t)(8 * Q * Q + 2 * Q * P + P * P) * sizeof(double);
     CK(raise_smem((const void *)k_face_data, m->device, (size_t)smem));
@@ -3265,6 +3350,7 @@ struct ConfArgs {
   const int32_t *vid, *vptr, *vmem, *vdir;  // vertex id per (element, corner), members (element * 8 + corner)
   const int32_t *eid, *eptr, *emem, *edir;  // edge id per (element, edge), members (element * 12 + edge)
   const double *const *lin;                 // per degree: (1 - x)/2 then (1 + x)/2 at the P GLL nodes
+  const int32_t *fbc;                       // outer-face conditions (null: all Dirichlet)
 };
 
 // node (i, j, k) of corner c (bit a of c: the side along axis a)
@@ -3363,6 +3449,7 @@ __global__ void k_conf_face(ConfArgs A, const double *v, double *p) {
     const int nb = A.nbr[e * 6 + f];
     double tg = 0.0;
     if (nb >= 0) tg = 0.5 * (own + v[rb + A.dof_off[nb] + node(P - 1 - n)]);
+    else if (A.fbc && A.fbc[e * 6 + f]) tg = own;  // a Neumann / Robin face is free
     cf[q] = tg - own;
   }
   __syncthreads();
@@ -3397,7 +3484,7 @@ static hpse_status conf_setup(hpse_mesh *m) {
   for (size_t i = 0; i < m->lo.size(); ++i) ext = std::max({ext, std::fabs(m->lo[i]), std::fabs(m->hi[i])});
   auto q = [&](double x) { return (long long)std::llround(x / (ext * 1e-9)); };
   auto X = [&](int e, int a, int side) { return side ? m->hi[3 * e + a] : m->lo[3 * e + a]; };
-  auto dir_face = [&](int e, int f) { return m->nbr[6 * e + f] == -1; };
+  auto dir_face = [&](int e, int f) { return m->nbr[6 * e + f] == -1 && m->fbc[6 * e + f] == 0; };
   std::map<Key, int> vmap, emap;
   std::vector<int> vid(8 * (size_t)E), eid(12 * (size_t)E), vdir, edir;
   std::vector<std::vector<int>> vmem, emem;
@@ -3500,6 +3587,7 @@ extern "C" hpse_status hpse_conforming_correction(hpse_mesh *m, const double *u,
   A.emem = m->d_cf_emem.as<int32_t>();
   A.edir = m->d_cf_edir.as<int32_t>();
   A.lin = m->d_cf_linptr.as<const double *>();
+  A.fbc = m->has_nr ? m->d_fbc.as<int32_t>() : nullptr;
   int Wmax = 1;
   for (auto &kv : m->tabs) Wmax = std::max(Wmax, kv.first);
   const int P = Wmax + 1, items = m->n_elem * m->n_rhs;

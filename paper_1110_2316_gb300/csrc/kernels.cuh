@@ -498,10 +498,14 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
   // slot s of face f: scr + (f * FACE_ARR + s) * P2; G_k reuse J_k, U1 / U2 reuse A1 / A2
 #define FSLOT(f, s) (scr + ((f)*FACE_ARR + (s)) * P2)
   enum { sF = 0, sFn, sJ0, sJ1, sJ2, sJ3, sA0, sA1, sA2, sA3, sB0, sB1, sB2, sB3 };
-  // per face: the scale of the normal term in the gather (s_a on interior faces, 0 on Dirichlet faces)
+  // per face: the scale of the normal term in the gather (s_a on interior
+  // faces, +-s_a on Neumann / Robin faces, 0 on Dirichlet faces) and of the
+  // face-layer term of a Robin face (gamma)
   if (tid < 6) {
     const int nb = A.nbr[(int64_t)e * 6 + tid];
-    fsc[tid] = nb != -1 ? geo_e[tid >> 1] : (real)0;
+    const int bc = (nb == -1 && A.fbc) ? A.fbc[(int64_t)e * 6 + tid] : 0;
+    fsc[tid] = nb != -1 ? geo_e[tid >> 1] : (bc ? ((tid & 1) ? geo_e[tid >> 1] : -geo_e[tid >> 1]) : (real)0);
+    fsc[6 + tid] = bc == 2 ? A.fgam[(int64_t)e * 6 + tid] : (real)0;
   }
   // 1: traces at every face point: F, J0 = [u] (u), J3 = [u_{x_a}] (0), the neighbour's trace Fn
   for (int t = tid; t < 6 * P2; t += nt) {
@@ -539,7 +543,14 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
       if (!side) Nn = -Nn;
     }
     FSLOT(f, sF)[sp] = Fv;
-    if (nb != -1) {
+    const int bc = (nb == -1 && A.fbc) ? A.fbc[(int64_t)e * 6 + f] : 0;
+    if (bc) {
+      // Neumann / Robin face (eq. 2.1): the outward normal derivative (+ gamma u)
+      // in the slot of the normal-derivative jump, nothing in the others
+      const real gam = bc == 2 ? A.fgam[(int64_t)e * 6 + f] : (real)0;
+      FSLOT(f, sJ0)[sp] = (real)0;
+      FSLOT(f, sJ3)[sp] = (side ? geo_e[a] : -geo_e[a]) * Nv + gam * Fv;
+    } else if (nb != -1) {
       // a corner set shares the theta and x3 scales of its layer-1 element
       const real *gn = nb >= 0 ? A.geo + (int64_t)nb * 4 : geo_e;
       FSLOT(f, sFn)[sp] = Fn;
@@ -564,7 +575,10 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
     load_fold(FSLOT(f, sF) + ob, os, ev, od);
     pp_line<0>(ev, od, g);
     real *J = FSLOT(f, dir ? sJ2 : sJ1) + ob;
-    if (nb != -1) {
+    if (nb == -1 && A.fbc && A.fbc[(int64_t)e * 6 + f]) {
+#pragma unroll
+      for (int m = 0; m < P; ++m) J[m * os] = (real)0;
+    } else if (nb != -1) {
       const real *gn = nb >= 0 ? A.geo + (int64_t)nb * 4 : geo_e;
       const real s0 = geo_e[tax], s1 = gn[tax];
       real h[P];
@@ -693,7 +707,7 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
       const int p2 = a == 2 ? j : k;
       const int sp = p2 * P + p1;
       acc += Ds[nend * P + n] * (fsc[f] * FSLOT(f, sJ3)[sp]);
-      if (n == nend) acc += FSLOT(f, sJ0)[sp] + FSLOT(f, sA1)[sp] + FSLOT(f, sA2)[sp];
+      if (n == nend) acc += FSLOT(f, sJ0)[sp] + FSLOT(f, sA1)[sp] + FSLOT(f, sA2)[sp] + fsc[6 + f] * FSLOT(f, sJ3)[sp];
     }
     sy[t] += acc;
   }
@@ -722,7 +736,7 @@ struct ApplyLayout {
   static constexpr int T_REGION0 = NTF * Q2P;
   static constexpr int T_NEED = P3 + 6 * FACE_ARR * P2;
   static constexpr int T_REGION = T_REGION0 > T_NEED ? T_REGION0 : T_NEED;
-  static constexpr int TABS = 3 * P2;
+  static constexpr int TABS = P2 + 12;  // D copy, then the per-face scales of the face gather
   static constexpr int TOTAL = P3 + NX * QP2 + T_REGION + TABS;
   // the FP64 reduction buffer starts on a 16-byte boundary whatever REAL is
   static constexpr size_t RED_OFF = (((size_t)TOTAL * sizeof(real) + 15) / 16) * 16;

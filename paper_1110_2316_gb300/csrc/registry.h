@@ -49,6 +49,9 @@ struct ApplyArgsT {
   const T *fw;              // [E][6][10] face-norm weights (null: all 1)
   const int32_t *cslot;     // [E][2] slot of the element's corner face 0 / face 4, or -1
   T *cscr;                  // [slots][n_rhs][CSCR_STRIDE] corner-side face contributions
+  // outer-face conditions of box meshes of the Laplacian; null: every outer face Dirichlet
+  const int32_t *fbc;       // [E][6]: 0 Dirichlet, 1 Neumann, 2 Robin
+  const T *fgam;            // [E][6]: the Robin gamma (0 elsewhere)
 };
 
 template <typename T>

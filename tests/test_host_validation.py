@@ -86,10 +86,23 @@ def test_neighbourhood_corner_sets(api):
     assert _status(api, m) == 1
 
 
-def test_neumann_faces_are_refused_by_the_cuda_binding(api):
-    # the oracle carries Neumann faces (eq. 4.2); the CUDA operator does not yet
-    with pytest.raises(ValueError):
-        api.Mesh(wl.poisson_mixed(n=2, W=3).mesh)
+def test_neumann_faces_outside_the_built_cases_are_refused(api):
+    # Neumann and Robin faces: box meshes of the Laplacian only (a variable
+    # coefficient's conormal derivative is not built), outer faces only, codes 0-2
+    pb = wl.varcoef_robin(n=2, W=2)
+    assert _status(api, pb.mesh, coef_kind=api.COEF_SCALAR) == 1
+    m = wl.poisson_mixed(n=2, W=3).mesh
+    m.elem_bc = m.elem_bc.copy()
+    m.elem_bc[0, 1] = 1            # an interior face
+    assert _status(api, m) == 1
+    m = wl.poisson_mixed(n=2, W=3).mesh
+    m.elem_bc = m.elem_bc.copy()
+    m.elem_bc[m.elem_bc == 1] = 3  # no such condition
+    assert _status(api, m) == 1
+    e = wl.edge_mesh(2, 3)
+    e.elem_bc = np.zeros((e.n_elem, 6), dtype=np.int32)
+    e.elem_bc[np.asarray(e.elem_nbr) == -1] = 1
+    assert _status(api, e) == 1
 
 
 def test_general_operator_problems_are_refused_by_the_cuda_binding(api):

@@ -13,7 +13,8 @@
   The adjoint right-hand side of a solution functional lies mostly in the
   low end of A's spectrum, so its attainable relative residual is about
   eps kappa(A), above that of the forward solve: ``adjoint_tol`` (default:
-  the forward ``tol``) sets it separately.  Backward works on the data of
+  the forward ``tol``) sets it separately, and an adjoint solve that stops at
+  its attainable level within 10x of it is accepted (and logged).  Backward works on the data of
   its own forward solve: if the mesh has been given other data in between,
   that solve's data is set again first (the mesh then keeps it).
 
@@ -103,9 +104,16 @@ class Solve(torch.autograd.Function):
         m.get_rhs(b)
         m.set_rhs(gx.contiguous())
         lam = torch.zeros_like(x)
-        rep = m.pcg_solve(lam, tol=ctx.tol, prec=ctx.adjoint_prec)
+        rep = m.pcg_solve(lam, tol=ctx.tol, prec=ctx.adjoint_prec, raise_on_error=False)
         if isinstance(getattr(m, "solve_log", None), list):
             m.solve_log.append(("adjoint", rep))
+        # the adjoint right-hand side sits in the low end of A's spectrum: its
+        # FP64-attainable residual (about eps kappa(A)) can lie just above the
+        # requested tolerance; a solve that stopped there (within 10x) is kept
+        if rep["status"] != 0 and not (rep["status"] == 5 and rep["rel_residual"] <= 10 * ctx.tol):
+            from ._lib import HpseError
+            m.set_rhs(b)
+            raise HpseError(rep["status"], "adjoint hpse_pcg_solve")
         m.set_rhs(b)
         uf = torch.empty(m.n_rhs, 5, m.nquad, dtype=torch.float64, device=x.device)
         lf = torch.empty_like(uf)

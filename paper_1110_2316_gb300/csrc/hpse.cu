@@ -2650,6 +2650,10 @@ static hpse_status solve_reliable(hpse_mesh *m, const hpse_solve_opts *o, double
   const int per_replay = w.graph_launches[key];
   int done = 0;
   double worst = 1.0;
+  // stagnation of the true residual at its attainable level (about eps
+  // kappa(A) in FP64): the best level reached and the refresh that reached it
+  double best = std::numeric_limits<double>::infinity();
+  int best_at = 0;
   while (true) {
     CK(cudaGraphLaunch(exec, s));
     g_launches += per_replay;
@@ -2694,6 +2698,15 @@ static hpse_status solve_reliable(hpse_mesh *m, const hpse_solve_opts *o, double
       }
       if (deadline > 0 && now > deadline) {
         status = HPSE_ERR_TIMEOUT;
+        break;
+      }
+      // the true residual has not halved in 16 refreshes: it sits at its
+      // attainable level above the tolerance, more iterations cannot help
+      if (worst < 0.5 * best) {
+        best = worst;
+        best_at = updates;
+      } else if (updates - best_at >= 16) {
+        status = HPSE_ERR_NO_CONVERGENCE;
         break;
       }
       // replace the FP32 residual by the true one, keep the direction

@@ -219,3 +219,73 @@ def test_theta_gradient_finite_differences(api):
         for p in range(len(parts)):
             scale = max(abs(fd[p]), 1e-3 * np.abs(g[p]).max())
             assert abs(g[(p,) + idx] - fd[p]) <= 1e-6 * scale, (p, idx, g[(p,) + idx], fd[p])
+
+
+def test_theta_gradient_high_degree_difference_form_fd(api):
+    # the adjoint batch's problems at W = 8 and 10 (4^3 elements each,
+    # lognormal coefficient): the adjoint gradient (forward FP64 to 1e-11,
+    # adjoint FP64 to 1e-8) against central differences at h = 1e-4 whose
+    # J(+) - J(-) is one quadrature of pointwise differences of the corrected
+    # solutions (truncation ~1e-8, rounding noise ~3e-7 of the gradient:
+    # measured by a sweep of h on this batch); bound 1e-6 of the scale
+    import math
+    from paper_1110_2316_gb300.autograd import PointValues, Solve
+    from paper_1110_2316_gb300.fields import LegendreLogField
+    Ws = wl.adjoint_batch_degrees(256)
+    pick = [int(np.flatnonzero(Ws == W)[0]) for W in (8, 10)]
+    parts = [wl.lognormal_coef_problem(int(Ws[p]), p, n=4) for p in pick]
+    pb = wl.batch_problems(parts)
+    m = api.Mesh(pb.mesh, n_rhs=1, coef_kind=api.COEF_SCALAR)
+    dev = torch.device("cuda")
+    fld = LegendreLogField.from_mesh(m, pb.mesh.elem_problem, device=dev)
+    pi = math.pi
+    ut = fld.separable(lambda x: torch.sin(pi * x), lambda y: torch.sin(pi * y), lambda z: torch.sin(pi * z))
+    f = torch.ones(1, m.nquad, dtype=torch.float64, device=dev)
+    th0 = torch.tensor(np.stack([p.meta["theta"] for p in parts]), device=dev)
+    a0, ga0 = fld(th0)
+    m.set_data(f=f, a=a0, grad_a=ga0)
+    m.setup_block_preconditioner()
+    w = torch.empty(m.nquad, dtype=torch.float64, device=dev)
+    m.quad_weights(w)
+    qprob = torch.tensor(np.repeat(pb.mesh.elem_problem.astype(np.int64),
+                                   [(2 * int(W) + 1) ** 3 for W in pb.mesh.elem_W]), device=dev)
+    th = th0.clone().requires_grad_(True)
+    a, ga = fld(th)
+    u = Solve.apply(f, a, ga, m, None, 1e-11, api.FP64, api.FP64, 1e-8)
+    J = torch.zeros(2, dtype=torch.float64, device=dev).index_add(0, qprob, w * (PointValues.apply(u, m)[0] - ut) ** 2)
+    J.sum().backward()
+    g = th.grad.detach()
+    u0 = u.detach()
+    fl = torch.empty(1, 5, m.nquad, dtype=torch.float64, device=dev)
+    m.eval_fields(u0, fl)
+    v0 = fl[0, 0].clone()
+
+    def correction(theta):
+        aa, gg = fld(theta)
+        m.set_data(f=f, a=aa, grad_a=gg)
+        b = torch.empty_like(u0)
+        m.get_rhs(b)
+        r = torch.empty_like(u0)
+        m.apply_operator(u0, r)
+        m.set_rhs(b - r)
+        d = torch.zeros_like(u0)
+        assert m.pcg_solve(d, tol=1e-11, prec=api.FP64, max_iter=60000)["status"] == 0
+        return d
+
+    h = 1e-4
+    for idx in [(1, 0, 0), (0, 2, 1), (3, 1, 2)]:
+        tp, tm = th0.clone(), th0.clone()
+        tp[(slice(None),) + idx] += h
+        tm[(slice(None),) + idx] -= h
+        dp, dm = correction(tp), correction(tm)
+        fa, fb = torch.empty_like(fl), torch.empty_like(fl)
+        m.eval_fields(dp - dm, fa)
+        m.eval_fields(dp + dm, fb)
+        dJ = torch.zeros(2, dtype=torch.float64, device=dev).index_add(
+            0, qprob, w * fa[0, 0] * (2 * (v0 - ut) + fb[0, 0]))
+        fd = (dJ / (2 * h)).cpu().numpy()
+        gi = g[(slice(None),) + idx].cpu().numpy()
+        for p in range(2):
+            scale = max(abs(fd[p]), 1e-3 * float(g[p].abs().max()))
+            assert abs(gi[p] - fd[p]) <= 1e-6 * scale, (idx, p, gi[p], fd[p])
+    m.close()

@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--precond", default="block", choices=["block", "separable"],
                     help="block: exact element blocks of A (set up once, FP64 factors); "
                          "separable: the C-form of eq. (5.19)-(5.20)")
-    ap.add_argument("--workload", default="varcoef", choices=["varcoef", "adjoint", "edge", "vertex", "vertex-edge", "poisson"],
+    ap.add_argument("--workload", default="varcoef", choices=["varcoef", "adjoint", "edge", "vertex", "vertex-edge", "poisson", "general"],
                     help="varcoef: the 64-RHS W=8 solve; adjoint: the 256-problem theta-gradient batch; "
                          "edge / vertex: the uneven-degree batch of edge- / vertex-neighbourhood problems")
     ap.add_argument("--edge-replicas", type=int, default=146, help="copies of each degree W = 2..8")
@@ -643,15 +643,127 @@ def run_poisson(args, local):
     return 0
 
 
+def general_flops_per_rhs(Ws):
+    """Algorithmic flops of one general-operator apply (volume, forward +
+    transpose): the (3, 6, 10)-field sum factorisation of the ten-term form,
+    2 * (3 Q P^3 + 6 Q^2 P^2 + 10 Q^3 P) multiply-adds per element."""
+    tot = 0.0
+    for W in Ws:
+        P, Q = W + 1, 2 * W + 1
+        tot += 2 * (3 * Q * P ** 3 + 6 * Q * Q * P * P + 10 * Q ** 3 * P)
+    return 2.0 * tot
+
+
+def scaled_rhs_problem(pb, n_rhs):
+    """The problem with n_rhs right-hand sides: data (f, g, the Neumann flux)
+    and exact solution of rhs r scaled by 1 + r / n_rhs (linear problem)."""
+    def sc(fun, c):
+        return lambda *a: c * np.asarray(fun(*a))
+
+    def scv(fun, c):
+        return lambda *a: tuple(c * np.asarray(v) for v in fun(*a))
+    cs = [1.0 + r / n_rhs for r in range(n_rhs)]
+    return wl.Problem(pb.mesh, [sc(pb.f[0], c) for c in cs], [sc(pb.g[0], c) for c in cs], None, None,
+                      [sc(pb.u_exact[0], c) for c in cs], [scv(pb.grad_u_exact[0], c) for c in cs],
+                      name=pb.name, flux=None if pb.flux is None else [scv(pb.flux[0], c) for c in cs],
+                      robin_gamma=pb.robin_gamma, op=pb.op)
+
+
+def run_general(args, local):
+    """The general operator of eq. (2.2) (the ten-term form of eq. 5.45 with
+    per-point coefficients): Table 6.14's non-self-adjoint problem (variable
+    A with mixed derivatives, e u, Dirichlet on x = +-1, y = -1, Neumann on
+    y = 1, z = +-1) on (-1,1)^3 in --n^3 elements of degree --W, --rhs
+    right-hand sides.  Reports the general apply's GDOF/s and roofline
+    fraction (FP32 and FP64), the mixed and FP64 time-to-solution with the
+    element-block preconditioner, and the relative H1 error of both."""
+    import torch
+    from paper_1110_2316_gb300.build import build
+    build()
+    from paper_1110_2316_gb300 import api
+    dev = torch.device("cuda", local)
+    t0 = time.perf_counter()
+    R = args.rhs
+    pb = scaled_rhs_problem(wl.nonsym_mixed(n=args.n, W=args.W), R)
+    m = api.Mesh(pb.mesh, n_rhs=R, coef_kind=api.COEF_GENERAL, device=local)
+    m.set_data(**api.problem_data_arrays(m, pb))
+    vq, gq = exact_at_points(m, pb)
+    vq = torch.tensor(np.concatenate([vq * (1.0 + r / R) for r in range(R)]), device=dev)
+    gq = torch.tensor(np.concatenate([gq * (1.0 + r / R) for r in range(R)]), device=dev)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    n = R * m.ndof
+    fl = general_flops_per_rhs([int(w) for w in m.elem_W]) * R
+    apply_ms = {}
+    with ClockSampler(local) as clk:
+        for name, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+            u = torch.randn(n, dtype=dt, device=dev)
+            y = torch.empty_like(u)
+            for _ in range(3):
+                m.apply_operator(u, y)
+            torch.cuda.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 20 if name == "fp32" else 3
+            a0.record()
+            for _ in range(reps):
+                m.apply_operator(u, y)
+            a1.record()
+            torch.cuda.synchronize()
+            apply_ms[name] = a0.elapsed_time(a1) / reps
+    clocks = clk.summary()
+    peaks = alu_peaks(local, clocks.get("sm_max_mhz"))
+    t1 = time.perf_counter()
+    m.setup_block_preconditioner()
+    torch.cuda.synchronize()
+    t_prec = time.perf_counter() - t1
+    out = {}
+    for name, prec in (("mixed", api.FP32), ("fp64", api.FP64)):
+        x = torch.zeros(n, dtype=torch.float64, device=dev)
+        m.pcg_solve(x, tol=TOL, prec=prec, max_iter=64, raise_on_error=False)  # graph capture
+        x.zero_()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record()
+        rep = m.pcg_solve(x, tol=TOL, prec=prec, max_iter=args.max_iter, raise_on_error=False)
+        c1.record()
+        torch.cuda.synchronize()
+        h = m.h1_error(x, vq=vq, gq=gq)
+        out[name] = dict(tts_s=c0.elapsed_time(c1) / 1e3, iterations=rep["iterations"], refreshes=rep["sweeps"],
+                         status=rep["status"], rel_residual=rep["rel_residual"],
+                         h1_rel_error_max=float(np.sqrt(h[:, 0] / h[:, 1]).max()))
+        out[name + "_x"] = x
+    d = out.pop("mixed_x") - out.pop("fp64_x")
+    hd = m.h1_error(d)
+    h64 = m.h1_error(torch.zeros_like(d), vq=vq, gq=gq)
+    rel_diff = float(np.sqrt(hd[:, 0].max() / h64[:, 1].min()))
+    ach = fl / (apply_ms["fp32"] * 1e-3) / 1e12
+    line = dict(metric="general operator: apply GDOF/s, time-to-solution mixed vs FP64",
+                value=n / (apply_ms["fp32"] * 1e-3) / 1e9, unit="GDOF/s", higher_is_better=True, n_gpus=1,
+                dtype="f32", data="synthetic",
+                config=dict(workload="a u_xx + b u_yy + c u_zz + d (u_xy + u_yz + u_zx) + e u = f (Table 6.14's "
+                                     "operator and faces) on (-1,1)^3, %d^3 elements, W = %d, %d rhs, tol 1e-10"
+                                     % (args.n, args.W, R), n_elem=int(pb.mesh.n_elem), ndof_per_rhs=m.ndof),
+                apply_ms=apply_ms, gdofs_fp64=n / (apply_ms["fp64"] * 1e-3) / 1e9,
+                roofline=dict(bound="alu", kernel="k_apply_gen FP32 (W=%d)" % args.W, achieved=ach,
+                              peak=peaks["fp32"], unit="TFLOP/s", frac=ach / peaks["fp32"],
+                              fp64_achieved=fl / (apply_ms["fp64"] * 1e-3) / 1e12, fp64_peak=peaks["fp64"],
+                              fp64_frac=fl / (apply_ms["fp64"] * 1e-3) / 1e12 / peaks["fp64"],
+                              note="algorithmic (3,6,10)-field flops per (element, rhs), derived ALU peaks"),
+                solves=out, speedup=out["fp64"]["tts_s"] / out["mixed"]["tts_s"],
+                h1_rel_diff_mixed_vs_fp64=rel_diff, setup_s=t_setup, setup_block_precond_s=t_prec,
+                clocks=clocks)
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload in ("adjoint", "edge", "vertex", "vertex-edge", "poisson"):
+    if args.workload in ("adjoint", "edge", "vertex", "vertex-edge", "poisson", "general"):
         import torch
         _, _, local = dist_env()
         torch.cuda.set_device(local)
-        run = dict(adjoint=run_adjoint, edge=run_edge, vertex=run_edge, poisson=run_poisson,
+        run = dict(adjoint=run_adjoint, edge=run_edge, vertex=run_edge, poisson=run_poisson, general=run_general,
                    **{"vertex-edge": run_edge})[args.workload]
         return run(args, local)
     import torch

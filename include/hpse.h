@@ -79,7 +79,13 @@ typedef enum {
 
 typedef enum {
   HPSE_COEF_LAPLACE = 0,  /* L u = -Lap u                       */
-  HPSE_COEF_SCALAR = 1    /* L u = -div(a grad u), a(x) > 0 given with grad a */
+  HPSE_COEF_SCALAR = 1,   /* L u = -div(a grad u), a(x) > 0 given with grad a */
+  HPSE_COEF_GENERAL = 2   /* L u = sum_ij A_ij u_{x_i x_j} + sum_i b_i u_{x_i} + c u
+                             (eq. 2.2 written out, A symmetric; the ten-term form of
+                             eq. 5.45 per element), A, b, c given per volume point in
+                             hpse_data.op; box elements (HPSE_COORD_CARTESIAN) with
+                             W <= 9 (the FP64 instance of W = 10 exceeds shared memory,
+                             HPSE_ERR_DEGREE) */
 } hpse_coef_kind;
 
 /* Mesh of one or more independent problems (eq. 2.1-2.2: the operator, the
@@ -126,8 +132,9 @@ typedef struct {
    * (+ gamma u) minus h in the H^{1/2} norm of the other face terms; its data
    * h replaces g in hpse_set_data at that face's points.  robin_gamma
    * [n_problem] (NULL: 1).  Neumann and Robin faces need box elements and
-   * HPSE_COEF_LAPLACE (else HPSE_ERR_INVALID_ARG): the conormal derivative of
-   * a variable coefficient is not built. */
+   * HPSE_COEF_LAPLACE or HPSE_COEF_GENERAL (else HPSE_ERR_INVALID_ARG; with
+   * the general operator the face measures the plain normal derivative): the
+   * conormal derivative of a variable coefficient is not built. */
   const int32_t *face_bc;
   const double *robin_gamma;
 } hpse_mesh_desc;
@@ -161,12 +168,18 @@ enum { HPSE_COORD_CARTESIAN = 0, HPSE_COORD_EDGE = 1, HPSE_COORD_VERTEX = 2, HPS
  *   f      [n_rhs][hpse_nquad()]        source at the volume points (required)
  *   a      [hpse_nquad()]               coefficient (HPSE_COEF_SCALAR only)
  *   grad_a [3][hpse_nquad()]            its gradient d a / d x_k (idem)
- *   g      [n_rhs][hpse_nface_points()] Dirichlet data, or NULL for g = 0   */
+ *   g      [n_rhs][hpse_nface_points()] Dirichlet data, or NULL for g = 0
+ *   op     [10][hpse_nquad()]           the general operator's coefficients at
+ *                                       the volume points, in the order A_11,
+ *                                       A_22, A_33, A_12, A_23, A_13, b_1, b_2,
+ *                                       b_3, c (HPSE_COEF_GENERAL only; finite,
+ *                                       else HPSE_ERR_INVALID_ARG)            */
 typedef struct {
   const double *f;
   const double *a;
   const double *grad_a;
   const double *g;
+  const double *op;
 } hpse_data;
 
 typedef struct {

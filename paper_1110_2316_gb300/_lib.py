@@ -19,7 +19,7 @@ STATUS_NAMES = {
     8: "HPSE_ERR_OOM", 9: "HPSE_ERR_NO_DATA", 10: "HPSE_ERR_CAPACITY",
 }
 FP64, FP32 = 0, 1
-COEF_LAPLACE, COEF_SCALAR = 0, 1
+COEF_LAPLACE, COEF_SCALAR, COEF_GENERAL = 0, 1, 2
 PRECOND_SEPARABLE, PRECOND_BLOCK = 0, 1
 COORD_CARTESIAN, COORD_EDGE, COORD_VERTEX, COORD_VERTEX_EDGE = 0, 1, 2, 3
 
@@ -35,7 +35,8 @@ class MeshDesc(C.Structure):
 
 
 class Data(C.Structure):
-    _fields_ = [("f", C.c_void_p), ("a", C.c_void_p), ("grad_a", C.c_void_p), ("g", C.c_void_p)]
+    _fields_ = [("f", C.c_void_p), ("a", C.c_void_p), ("grad_a", C.c_void_p), ("g", C.c_void_p),
+                ("op", C.c_void_p)]
 
 
 class SolveOpts(C.Structure):

@@ -13,9 +13,9 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import COEF_LAPLACE, COEF_SCALAR, FP32, FP64, PRECOND_BLOCK, PRECOND_SEPARABLE, check
+from ._lib import COEF_GENERAL, COEF_LAPLACE, COEF_SCALAR, FP32, FP64, PRECOND_BLOCK, PRECOND_SEPARABLE, check
 
-__all__ = ["Mesh", "problem_data_arrays", "FP64", "FP32", "COEF_LAPLACE", "COEF_SCALAR", "PRECOND_SEPARABLE",
+__all__ = ["Mesh", "problem_data_arrays", "FP64", "FP32", "COEF_LAPLACE", "COEF_SCALAR", "COEF_GENERAL", "PRECOND_SEPARABLE",
            "PRECOND_BLOCK"]
 
 
@@ -129,10 +129,12 @@ class Mesh:
         return ax, fn[: self.n_boundary_faces]
 
     # -- data ---------------------------------------------------------------
-    def set_data(self, f, a=None, grad_a=None, g=None, stream=None):
+    def set_data(self, f, a=None, grad_a=None, g=None, op=None, stream=None):
         """Data at the query points: numpy arrays (host) or CUDA float64 torch
-        tensors (device, read on the current torch stream); not mixed."""
-        vals = (f, a, grad_a, g)
+        tensors (device, read on the current torch stream); not mixed.  ``op``
+        [10, nquad]: the general operator's A_11, A_22, A_33, A_12, A_23,
+        A_13, b_1, b_2, b_3, c (COEF_GENERAL)."""
+        vals = (f, a, grad_a, g, op)
         on_dev = [v is not None and not isinstance(v, np.ndarray) and getattr(v, "is_cuda", False) for v in vals]
         if any(on_dev):
             import torch
@@ -260,16 +262,20 @@ def problem_data_arrays(mesh: Mesh, problem):
     """Sample a problem's data functions on the mesh's query grids.
 
     ``problem`` provides f (list per rhs), g (list per rhs), a / grad_a (or
-    None) as callables on tensor grids (see workloads).  Returns the dict of
-    host arrays expected by Mesh.set_data.  For an edge neighbourhood the
+    None) as callables on tensor grids (see workloads), or op (the general
+    operator of eq. 2.2: (A, b, c) on tensor grids, for a COEF_GENERAL mesh).
+    Returns the dict of host arrays expected by Mesh.set_data.  For an edge neighbourhood the
     query grids are modified coordinates (tau, theta, x3) and the data
     functions take cylindrical coordinates: they are sampled at r = e^tau;
     for a vertex neighbourhood at rho = e^chi; a vertex-edge neighbourhood's
     data functions take its modified coordinates themselves.
     """
-    if getattr(problem, "op", None) is not None:
-        raise ValueError("the general operator of eq. (2.2) is not supported by the CUDA operator: "
-                         "give -div(a grad u) through a / grad_a")
+    general = getattr(problem, "op", None) is not None or any(
+        getattr(p, "op", None) is not None for p in (getattr(problem, "parts", None) or []))
+    if general and mesh.coef_kind != COEF_GENERAL:
+        raise ValueError("a problem with the general operator of eq. (2.2) needs a COEF_GENERAL mesh")
+    if mesh.coef_kind == COEF_GENERAL and not general:
+        raise ValueError("a COEF_GENERAL mesh needs the problem's general operator (op)")
     if getattr(mesh, "is_edge", False):
         if mesh.nbhd_kind == "vertex":   # (phi, theta, ln rho): sample at rho = e^chi
             def cyl(fun):
@@ -294,8 +300,10 @@ def problem_data_arrays(mesh: Mesh, problem):
         return parts[int(eprob[e])] if parts is not None else problem
 
     f = np.zeros((R, nq))
-    a = grad = None
-    if problem.a is not None:
+    a = grad = op = None
+    if general:
+        op = np.zeros((10, nq))
+    elif problem.a is not None:
         a = np.zeros(nq)
         grad = np.zeros((3, nq))
     axes = []
@@ -309,6 +317,11 @@ def problem_data_arrays(mesh: Mesh, problem):
         pe = part(e)
         for r in range(R):
             f[r, oq:oq + n] = np.broadcast_to(pe.f[r](xs, ys, zs), (Q, Q, Q)).ravel()
+        if op is not None:
+            A_, b_, c_ = pe.op(xs, ys, zs)
+            vals = [A_[0][0], A_[1][1], A_[2][2], A_[0][1], A_[1][2], A_[0][2], b_[0], b_[1], b_[2], c_]
+            for k, v in enumerate(vals):
+                op[k, oq:oq + n] = np.broadcast_to(np.asarray(v, dtype=np.float64), (Q, Q, Q)).ravel()
         if a is not None:
             a[oq:oq + n] = np.broadcast_to(pe.a(xs, ys, zs), (Q, Q, Q)).ravel()
             gx, gy, gz = pe.grad_a(xs, ys, zs)
@@ -346,4 +359,7 @@ def problem_data_arrays(mesh: Mesh, problem):
                         g[r, fo:fo + Q * Q] = h.ravel()
                 fo += Q * Q
                 k += 1
-    return dict(f=f, a=a, grad_a=grad, g=g)
+    out = dict(f=f, a=a, grad_a=grad, g=g)
+    if op is not None:
+        out["op"] = op
+    return out

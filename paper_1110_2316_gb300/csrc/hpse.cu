@@ -202,7 +202,8 @@ struct hpse_mesh {
   // device mesh arrays
   // d_prob: problem of each vector item (n_elem + n_corner entries)
   DevBuf d_dof_off, d_nbr, d_geo64, d_geo32, d_prob, d_coef_off, d_prob_ptr, d_prob_elems, d_elem_W;
-  DevBuf d_coef64, d_coef32;  // [nquad][4] (m, d_x, d_y, d_z) per point (COEF_SCALAR)
+  DevBuf d_coef64, d_coef32;  // [nquad][4] (m, d_x, d_y, d_z) per point (COEF_SCALAR);
+                              // [nquad][12] (w J, C_11 .. C_0, 0) (HPSE_COEF_GENERAL)
   DevBuf d_b;                 // FP64 right-hand side
   DevBuf d_f;                 // FP64 source at the volume points [n_rhs][nquad]
   DevBuf d_aux;               // FP64 [5][nquad]: w J, a, a_x, a_y, a_z at the volume points
@@ -1476,7 +1477,9 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
   if (!d || !out) return HPSE_ERR_INVALID_ARG;
   *out = nullptr;
   if (d->n_elem < 0 || d->n_problem < 1 || d->n_rhs < 1) return HPSE_ERR_INVALID_ARG;
-  if (d->coef_kind != HPSE_COEF_LAPLACE && d->coef_kind != HPSE_COEF_SCALAR) return HPSE_ERR_INVALID_ARG;
+  init_registry();
+  if (d->coef_kind != HPSE_COEF_LAPLACE && d->coef_kind != HPSE_COEF_SCALAR && d->coef_kind != HPSE_COEF_GENERAL)
+    return HPSE_ERR_INVALID_ARG;
   if (d->n_elem > 0 && (!d->elem_W || !d->elem_problem || !d->elem_lo || !d->elem_hi || !d->elem_nbr))
     return HPSE_ERR_INVALID_ARG;
   const int E = d->n_elem;
@@ -1507,6 +1510,7 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
   m->apply_coef = m->coord == HPSE_COORD_EDGE            ? hpse::COEF_EDGE
                  : m->coord == HPSE_COORD_VERTEX        ? hpse::COEF_VERTEX
                  : m->coord == HPSE_COORD_VERTEX_EDGE ? hpse::COEF_VERTEX_EDGE
+                 : d->coef_kind == HPSE_COEF_GENERAL  ? hpse::COEF_GENERAL
                                                         : d->coef_kind;
   m->W.assign(d->elem_W, d->elem_W + E);
   m->prob.assign(d->elem_problem, d->elem_problem + E);
@@ -1516,6 +1520,10 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
   // ---- validation (Section 2.3: one-to-one matching faces) -----------------
   for (int e = 0; e < E; ++e) {
     if (m->W[e] < 1 || m->W[e] > HPSE_MAX_W) return HPSE_ERR_DEGREE;
+    // the general operator's kernel exists where its layout fits shared memory
+    if (d->coef_kind == HPSE_COEF_GENERAL && (g_sets[0][m->W[e]].apply_smem(hpse::COEF_GENERAL) == 0 ||
+                                              g_sets[1][m->W[e]].apply_smem(hpse::COEF_GENERAL) == 0))
+      return HPSE_ERR_DEGREE;
     if (m->prob[e] < 0 || m->prob[e] >= m->n_problem) return HPSE_ERR_INVALID_ARG;
     for (int a = 0; a < 3; ++a)
       if (!(m->hi[3 * e + a] > m->lo[3 * e + a]) || !std::isfinite(m->lo[3 * e + a]) ||
@@ -1537,7 +1545,8 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
       }
       if (c != 0) m->has_nr = true;
     }
-    if (m->has_nr && (nbhd || d->coef_kind != HPSE_COEF_LAPLACE)) return HPSE_ERR_INVALID_ARG;
+    if (m->has_nr && (nbhd || (d->coef_kind != HPSE_COEF_LAPLACE && d->coef_kind != HPSE_COEF_GENERAL)))
+      return HPSE_ERR_INVALID_ARG;
   }
   const int C = m->n_corner;
   for (int c = 0; c < C; ++c)
@@ -1816,6 +1825,47 @@ __global__ void k_coef_scalar(int64_t nq, const int32_t *elem_W, const int64_t *
   }
 }
 
+// General operator of box elements (eq. 2.2 written out; the ten-term form
+// of eq. 5.45 in the element's reference coordinates) from op = (A_11, A_22,
+// A_33, A_12, A_23, A_13, b_1, b_2, b_3, c) per volume point (device memory):
+// coef = (w J, C_11, C_22, C_33, C_12, C_23, C_13, C_1, C_2, C_3, C_0, 0) with
+// C_aa = A_aa s_a^2, C_ab = 2 A_ab s_a s_b, C_a = b_a s_a, C_0 = c, in FP64
+// and FP32; wja = -w J (the volume part of b is then the transposed apply of
+// w J f); bad[0] = 1 where a coefficient is not finite.  One CTA per element.
+__global__ void k_coef_general(int64_t nq, const int32_t *elem_W, const int64_t *coef_off, const double *geo,
+                               const double *const *qtab, const double *op, double *coef64, float *coef32,
+                               double *wja, int32_t *bad) {
+  const int e = blockIdx.x;
+  const int W = elem_W[e], P = W + 1, Q = 2 * W + 1;
+  const double *wq = qtab[W] + 2 * Q * P + 2 * Q * Q;
+  const double *gs = geo + 4 * (int64_t)e;
+  // (row, column) of A_11 .. A_13 and the factor of the off-diagonal pairs
+  const int ia[6] = {0, 1, 2, 0, 1, 0}, ja[6] = {0, 1, 2, 1, 2, 2};
+  for (int t = threadIdx.x; t < Q * Q * Q; t += blockDim.x) {
+    const int qa = t % Q, qb = (t / Q) % Q, qc = t / (Q * Q);
+    const int64_t i = coef_off[e] + t;
+    const double wJ = wq[qa] * wq[qb] * wq[qc] * gs[3];
+    double c[12];
+    c[0] = wJ;
+    for (int k = 0; k < 10; ++k) {
+      double v = op[k * nq + i];
+      if (!isfinite(v)) {
+        bad[0] = 1;
+        v = 0.0;
+      }
+      if (k < 6) c[1 + k] = (k < 3 ? 1.0 : 2.0) * v * gs[ia[k]] * gs[ja[k]];
+      else if (k < 9) c[1 + k] = v * gs[k - 6];
+      else c[10] = v;
+    }
+    c[11] = 0.0;
+    for (int k = 0; k < 12; ++k) {
+      coef64[12 * i + k] = c[k];
+      coef32[12 * i + k] = (float)c[k];
+    }
+    wja[i] = -wJ;
+  }
+}
+
 // where a data pointer points: 1 device (or managed), 0 host, -1 unknown
 static int pointer_space(const void *p) {
   cudaPointerAttributes at;
@@ -1829,11 +1879,13 @@ static int pointer_space(const void *p) {
 extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data, void *stream) {
   if (!m || !data || (!data->f && m->nquad > 0)) return HPSE_ERR_INVALID_ARG;
   if (m->coef_kind == HPSE_COEF_SCALAR && (!data->a || !data->grad_a)) return HPSE_ERR_INVALID_ARG;
+  const bool gen = m->coef_kind == HPSE_COEF_GENERAL;
+  if (gen && !data->op && m->nquad > 0) return HPSE_ERR_INVALID_ARG;
   CK(cudaSetDevice(m->device));
   // host or device data: every given pointer in the same space
   int space = -2;
   for (const void *p : {(const void *)data->f, (const void *)data->a, (const void *)data->grad_a,
-                        (const void *)data->g}) {
+                        (const void *)data->g, (const void *)(gen ? data->op : nullptr)}) {
     if (!p) continue;
     const int sp = pointer_space(p);
     if (sp < 0 || (space != -2 && sp != space)) return HPSE_ERR_INVALID_ARG;
@@ -1962,6 +2014,32 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data, void *
       CK(cudaGetLastError());
       ++g_launches;
     }
+  } else if (gen) {
+    // the general operator's coefficients are transformed on the device
+    // (host data is first copied there)
+    if (!m->d_coef64.p || m->d_coef64.bytes != 12 * (size_t)nq * sizeof(double))
+      CK(m->d_coef64.alloc(12 * (size_t)std::max<int64_t>(nq, 1) * sizeof(double)));
+    if (!m->d_coef32.p || m->d_coef32.bytes != 12 * (size_t)nq * sizeof(float))
+      CK(m->d_coef32.alloc(12 * (size_t)std::max<int64_t>(nq, 1) * sizeof(float)));
+    CK(dwja.alloc((size_t)std::max<int64_t>(nq, 1) * sizeof(double)));
+    CK(dbad.alloc(sizeof(int32_t)));
+    CK(cudaMemsetAsync(dbad.p, 0, sizeof(int32_t), s));
+    DevBuf dop;
+    const double *opd = data->op;
+    if (!dev && nq > 0) {
+      CK(dop.alloc(10 * (size_t)nq * sizeof(double)));
+      CK(cudaMemcpyAsync(dop.p, data->op, 10 * (size_t)nq * sizeof(double), cudaMemcpyHostToDevice, s));
+      opd = dop.as<double>();
+    }
+    if (m->n_elem > 0) {
+      k_coef_general<<<m->n_elem, 256, 0, s>>>(nq, m->d_elem_W.as<int32_t>(), m->d_coef_off.as<int64_t>(),
+                                              m->d_geo64.as<double>(), m->d_tabs_ptr.as<const double *>(), opd,
+                                              m->d_coef64.as<double>(), m->d_coef32.as<float>(),
+                                              dwja.as<double>(), dbad.as<int32_t>());
+      CK(cudaGetLastError());
+      ++g_launches;
+    }
+    CK(cudaStreamSynchronize(s));
   } else {
     if (m->coef_kind == HPSE_COEF_SCALAR || vtx || ve) {
       std::vector<float> c32(coef.size());
@@ -2057,7 +2135,7 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data, void *
     ++g_launches;
     CK(cudaStreamSynchronize(s));
   }
-  if (dev_coef) {
+  if (dev_coef || gen) {
     int32_t h_bad = 0;
     CK(cudaMemcpy(&h_bad, dbad.p, sizeof(int32_t), cudaMemcpyDeviceToHost));
     if (h_bad) {
@@ -2080,7 +2158,8 @@ extern "C" hpse_status hpse_get_rhs(hpse_mesh *m, double *b, void *stream) {
 }
 
 static hpse_status check_coef(hpse_mesh *m) {
-  if (m->coef_kind == HPSE_COEF_SCALAR && !m->has_data) return HPSE_ERR_NO_DATA;
+  if ((m->coef_kind == HPSE_COEF_SCALAR || m->coef_kind == HPSE_COEF_GENERAL) && !m->has_data)
+    return HPSE_ERR_NO_DATA;
   return HPSE_OK;
 }
 
@@ -2338,11 +2417,12 @@ extern "C" int32_t hpse_get_block_threads(const hpse_mesh *m, int32_t kind, int3
 extern "C" hpse_status hpse_work_counts(const hpse_mesh *m, double *vol_macs, double *face_macs) {
   if (!m) return HPSE_ERR_INVALID_ARG;
   double v = 0.0, f = 0.0;
-  const bool var = m->coef_kind == HPSE_COEF_SCALAR;
+  const bool var = m->coef_kind == HPSE_COEF_SCALAR, gen = m->coef_kind == HPSE_COEF_GENERAL;
   for (int e = 0; e < m->n_elem; ++e) {
     const double P = m->W[e] + 1, Q = 2 * m->W[e] + 1;
-    // forward (n1, n2, n3) = (3,5,5) or (2,3,2), and the same for the transpose
-    const double n1 = var ? 3 : 2, n2 = var ? 5 : 3, n3 = var ? 5 : 2;
+    // forward (n1, n2, n3) = (3,5,5), (2,3,2) or, for the general operator,
+    // (3,6,10), and the same for the transpose
+    const double n1 = (var || gen) ? 3 : 2, n2 = gen ? 6 : (var ? 5 : 3), n3 = gen ? 10 : (var ? 5 : 2);
     v += 2.0 * (n1 * Q * P * P * P + n2 * Q * Q * P * P + n3 * Q * Q * Q * P);
     for (int fi = 0; fi < 6; ++fi) {
       // traces (2 P^3 + 2 P^3 each side), norms (2 P^3 L2 + 3 x 4 P^3 H^{1/2}), transposes (~3 P^3)
@@ -3194,7 +3274,8 @@ static hpse_status launch_fields(hpse_mesh *m, const T *u, T *out, cudaStream_t 
 }
 
 extern "C" hpse_status hpse_eval_fields(hpse_mesh *m, const double *u, double *out, void *stream) {
-  if (m && m->coord != HPSE_COORD_CARTESIAN) return HPSE_ERR_INVALID_ARG;  // box meshes only
+  // box meshes of the Laplacian or -div(a grad u) only
+  if (m && (m->coord != HPSE_COORD_CARTESIAN || m->coef_kind == HPSE_COEF_GENERAL)) return HPSE_ERR_INVALID_ARG;
   if (!m) return HPSE_ERR_INVALID_ARG;
   if (m->ndof == 0) return HPSE_OK;
   if (!u || !out) return HPSE_ERR_INVALID_ARG;
@@ -3204,7 +3285,8 @@ extern "C" hpse_status hpse_eval_fields(hpse_mesh *m, const double *u, double *o
 }
 
 extern "C" hpse_status hpse_apply_eval_transpose(hpse_mesh *m, const double *rho, double *y, void *stream) {
-  if (m && m->coord != HPSE_COORD_CARTESIAN) return HPSE_ERR_INVALID_ARG;  // box meshes only
+  // box meshes of the Laplacian or -div(a grad u) only
+  if (m && (m->coord != HPSE_COORD_CARTESIAN || m->coef_kind == HPSE_COEF_GENERAL)) return HPSE_ERR_INVALID_ARG;
   if (!m) return HPSE_ERR_INVALID_ARG;
   if (m->ndof == 0) return HPSE_OK;
   if (!rho || !y) return HPSE_ERR_INVALID_ARG;
@@ -3252,7 +3334,8 @@ static hpse_status residual_t(hpse_mesh *m, const T *u, T *z, cudaStream_t s) {
 }
 
 extern "C" hpse_status hpse_apply_residual(hpse_mesh *m, int32_t prec, const void *u, void *z, void *stream) {
-  if (m && m->coord != HPSE_COORD_CARTESIAN) return HPSE_ERR_INVALID_ARG;  // box meshes only
+  // box meshes of the Laplacian or -div(a grad u) only
+  if (m && (m->coord != HPSE_COORD_CARTESIAN || m->coef_kind == HPSE_COEF_GENERAL)) return HPSE_ERR_INVALID_ARG;
   if (!m || (prec != HPSE_FP64 && prec != HPSE_FP32)) return HPSE_ERR_INVALID_ARG;
   if (m->ndof == 0) return HPSE_OK;
   if (!u || !z) return HPSE_ERR_INVALID_ARG;
@@ -3277,7 +3360,8 @@ static hpse_status transpose_t(hpse_mesh *m, const T *z, T *y, cudaStream_t s) {
 }
 
 extern "C" hpse_status hpse_apply_transpose(hpse_mesh *m, int32_t prec, const void *z, void *y, void *stream) {
-  if (m && m->coord != HPSE_COORD_CARTESIAN) return HPSE_ERR_INVALID_ARG;  // box meshes only
+  // box meshes of the Laplacian or -div(a grad u) only
+  if (m && (m->coord != HPSE_COORD_CARTESIAN || m->coef_kind == HPSE_COEF_GENERAL)) return HPSE_ERR_INVALID_ARG;
   if (!m || (prec != HPSE_FP64 && prec != HPSE_FP32)) return HPSE_ERR_INVALID_ARG;
   if (m->ndof == 0) return HPSE_OK;
   if (!z || !y) return HPSE_ERR_INVALID_ARG;
@@ -3290,7 +3374,8 @@ extern "C" hpse_status hpse_apply_transpose(hpse_mesh *m, int32_t prec, const vo
 
 extern "C" hpse_status hpse_data_gradient(hpse_mesh *m, const double *ufields, const double *lfields, double *out,
                                           void *stream) {
-  if (m && m->coord != HPSE_COORD_CARTESIAN) return HPSE_ERR_INVALID_ARG;  // box meshes only
+  // box meshes of the Laplacian or -div(a grad u) only
+  if (m && (m->coord != HPSE_COORD_CARTESIAN || m->coef_kind == HPSE_COEF_GENERAL)) return HPSE_ERR_INVALID_ARG;
   if (!m) return HPSE_ERR_INVALID_ARG;
   if (m->nquad == 0) return HPSE_OK;
   if (!ufields || !lfields || !out) return HPSE_ERR_INVALID_ARG;

@@ -2,6 +2,7 @@
 // kernels.cuh.  A generated translation unit defines REAL, WDEG,
 // HPSE_REGISTER_NAME (and HPSE_DOUBLE for REAL = double), then includes this.
 #include "kernels.cuh"
+#include "general.cuh"
 
 namespace {
 
@@ -35,6 +36,10 @@ cudaError_t apply_fn(int coef, int mode, const void *args, int n_items, int thre
     if (mode == MODE_PCG) return launch_apply_t<COEF_VERTEX_EDGE, MODE_PCG>(args, n_items, threads, s);
     if (mode == MODE_TRANSPOSE)
       return launch_apply_t<COEF_VERTEX_EDGE, MODE_TRANSPOSE>(args, n_items, threads, s);
+  } else if (coef == hpse::COEF_GENERAL) {
+    if (mode == MODE_PLAIN) return launch_apply_gen<MODE_PLAIN>(args, n_items, s);
+    if (mode == MODE_PCG) return launch_apply_gen<MODE_PCG>(args, n_items, s);
+    if (mode == MODE_TRANSPOSE) return launch_apply_gen<MODE_TRANSPOSE>(args, n_items, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -44,6 +49,8 @@ size_t apply_smem_fn(int coef) {
   if (coef == COEF_EDGE) return ApplyLayout<COEF_EDGE>::BYTES;
   if (coef == COEF_VERTEX) return ApplyLayout<COEF_VERTEX>::BYTES;
   if (coef == COEF_VERTEX_EDGE) return ApplyLayout<COEF_VERTEX_EDGE>::BYTES;
+  // 0: no instance of this degree and precision (its layout exceeds 227 KB)
+  if (coef == hpse::COEF_GENERAL) return GenLayout::FITS ? GenLayout::BYTES : 0;
   return ApplyLayout<COEF_LAPLACE>::BYTES;
 }
 
@@ -128,6 +135,9 @@ cudaError_t upload_fn(const double *pk) {
   if ((e2 = set_smem_attr<COEF_VERTEX_EDGE, MODE_PLAIN>()) != cudaSuccess) return e2;
   if ((e2 = set_smem_attr<COEF_VERTEX_EDGE, MODE_PCG>()) != cudaSuccess) return e2;
   if ((e2 = set_smem_attr<COEF_VERTEX_EDGE, MODE_TRANSPOSE>()) != cudaSuccess) return e2;
+  if ((e2 = set_smem_attr_gen<MODE_PLAIN>()) != cudaSuccess) return e2;
+  if ((e2 = set_smem_attr_gen<MODE_PCG>()) != cudaSuccess) return e2;
+  if ((e2 = set_smem_attr_gen<MODE_TRANSPOSE>()) != cudaSuccess) return e2;
   if ((e2 = cudaFuncSetAttribute(k_precond<MODE_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)PC_BYTES)) != cudaSuccess)
     return e2;

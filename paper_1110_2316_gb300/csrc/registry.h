@@ -16,7 +16,9 @@ namespace hpse {
 // place of u_2 (vertex-edge neighbourhood, (ln tan phi, theta, ln x3)):
 // per-point m and coefficients of (u_1, u_13, u_3), u_11 scaled by 1 + kappa
 // and u_33 by kappa per x-point, kappa = e^{2 psi}
-enum { COEF_LAPLACE = 0, COEF_SCALAR = 1, COEF_EDGE = 2, COEF_VERTEX = 3, COEF_VERTEX_EDGE = 4 };
+// COEF_GENERAL: the ten-term operator of eq. (5.45) with per-point
+// coefficients (weight and C's, GEN_NC = 12 per point; general.cuh)
+enum { COEF_LAPLACE = 0, COEF_SCALAR = 1, COEF_EDGE = 2, COEF_VERTEX = 3, COEF_VERTEX_EDGE = 4, COEF_GENERAL = 5 };
 // KAPPA_STRIDE = 2 * HPSE_MAX_W + 1, CSCR_STRIDE = HPSE_MAX_W + 1 (checked in the host library)
 enum { KAPPA_STRIDE = 21, CSCR_STRIDE = 11, FACE_W = 10, ZEIG_STRIDE = 132 };
 enum { MODE_PLAIN = 0, MODE_PCG = 1, MODE_TRANSPOSE = 2 };
@@ -33,7 +35,8 @@ struct ApplyArgsT {
   const int32_t *nbr;
   const T *geo;
   const int32_t *prob;
-  const T *coef;            // [nquad][4]: m, d_x, d_y (COEF_VERTEX_EDGE: d_xz), d_z per volume point
+  const T *coef;            // [nquad][4]: m, d_x, d_y (COEF_VERTEX_EDGE: d_xz), d_z per volume point;
+                            // COEF_GENERAL: [nquad][12] (w |J|, C_11 .. C_0, 0)
   const int64_t *coef_off;
   int64_t nquad;
   const T *z;

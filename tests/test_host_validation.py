@@ -87,8 +87,9 @@ def test_neighbourhood_corner_sets(api):
 
 
 def test_neumann_faces_outside_the_built_cases_are_refused(api):
-    # Neumann and Robin faces: box meshes of the Laplacian only (a variable
-    # coefficient's conormal derivative is not built), outer faces only, codes 0-2
+    # Neumann and Robin faces: box meshes of the Laplacian or the general
+    # operator only (a variable coefficient's conormal derivative is not
+    # built), outer faces only, codes 0-2
     pb = wl.varcoef_robin(n=2, W=2)
     assert _status(api, pb.mesh, coef_kind=api.COEF_SCALAR) == 1
     m = wl.poisson_mixed(n=2, W=3).mesh
@@ -105,6 +106,16 @@ def test_neumann_faces_outside_the_built_cases_are_refused(api):
     assert _status(api, e) == 1
 
 
-def test_general_operator_problems_are_refused_by_the_cuda_binding(api):
+def test_general_operator_outside_the_built_cases_is_refused(api):
+    from types import SimpleNamespace
+    # a problem with the general operator needs a COEF_GENERAL mesh, and back
     with pytest.raises(ValueError):
-        api.problem_data_arrays(None, wl.helmholtz_mixed(n=2, W=2))
+        api.problem_data_arrays(SimpleNamespace(coef_kind=api.COEF_LAPLACE), wl.helmholtz_mixed(n=2, W=2))
+    with pytest.raises(ValueError):
+        api.problem_data_arrays(SimpleNamespace(coef_kind=api.COEF_GENERAL), wl.poisson_mixed(n=2, W=2))
+    # box elements only (the neighbourhoods' modified operators are the Laplacian's)
+    assert _status(api, wl.edge_mesh(2, 3), coef_kind=api.COEF_GENERAL) == 1
+    # W = 10: the FP64 kernel's shared-memory layout does not fit (HPSE_ERR_DEGREE)
+    assert _status(api, wl.box_mesh(1, W=10), coef_kind=api.COEF_GENERAL) == 3
+    # an unknown kind
+    assert _status(api, wl.box_mesh(1, W=2), coef_kind=7) == 1

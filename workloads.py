@@ -158,7 +158,8 @@ class Problem:
     # face (bc 2) h = nu . q + robin_gamma g
     flux: Optional[List[Callable]] = None
     robin_gamma: float = 1.0
-    # general operator sum A_ij u_ij + sum b_i u_i + c u (oracle only):
+    # general operator sum A_ij u_ij + sum b_i u_i + c u (oracle, and the
+    # library's COEF_GENERAL meshes):
     # op(xs, ys, zs) -> (A 3x3, b 3, c) on tensor grids; None: -div(a grad u)
     op: Optional[Callable] = None
 

@@ -40,6 +40,10 @@ parallel computers, 2010):
 * ``vertex_shell`` -- a vertex neighbourhood inside a spherical shell of curved
                     regular elements, joined on the sphere.
 * ``adjoint``    -- gradients of a solution functional by an adjoint solve.
+* ``conforming`` -- the conforming correction of a box-element solution
+                    (Remark 4.3.0, Appendix C.1).
+* ``ibp``        -- the volume variation in integration-by-parts form
+                    (eq. 5.45-5.48), the alternative to the direct transpose.
 
 Every function is written for clarity, not speed.  Where the thesis is silent
 or ambiguous, the reading taken is stated in the docstring of the function

@@ -79,3 +79,96 @@ def data_gradient(disc, U, lam, rhs=0):
         out.append((wJ * Ll, wJ * (lu * Ll + res * ll), wJ * (ux * Ll + res * lx),
                     wJ * (uy * Ll + res * ly), wJ * (uz * Ll + res * lz)))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Second order: the same functional with the data as free point arrays
+# theta = (f [nquad], a [nquad], grad a [3, nquad]) (element-major, each
+# element's points in [c, b, a] order), by dense algebra on small meshes.
+#   S(theta) U = sqrt(wJ) (-a Lap U - grad a . grad U)   (the volume residual's
+#                                                          linear part)
+#   A(theta) = S^T S + A_faces,  b(theta) = S^T sqrt(wJ) f + b_faces
+# where A_faces, b_faces (the face and Dirichlet terms of eq. 4.2) do not
+# depend on theta and are taken from the Discretisation at its own data.
+# The Hessian-vector product is the central difference of the exact
+# adjoint gradient (dense Cholesky solves); its pins are the symmetry of the
+# Hessian and the second difference of J itself.
+# ---------------------------------------------------------------------------
+def field_matrices(disc):
+    """[5, nquad, ndof] dense maps U -> (v, v_x, v_y, v_z, Lap v) at all points."""
+    nq = sum((2 * w + 1) ** 3 for w in disc.W)
+    F = np.zeros((5, nq, disc.ndof))
+    o = 0
+    for e in range(disc.E):
+        n = (2 * disc.W[e] + 1) ** 3
+        for j in range(disc.off[e], disc.off[e + 1]):
+            U = np.zeros(disc.ndof)
+            U[j] = 1.0
+            for k, fld in enumerate(element_fields(disc, U, e)):
+                F[k, o:o + n, j] = fld.ravel()
+        o += n
+    return F
+
+
+def point_weights(disc):
+    return np.concatenate([disc.vol_weight(e).ravel() for e in range(disc.E)])
+
+
+def point_data(disc, rhs=0):
+    """theta of the Discretisation's own problem: (f, a, grad a) at the points."""
+    f = np.concatenate([disc.f_at(e, rhs).ravel() for e in range(disc.E)])
+    a = np.concatenate([np.asarray(disc.coef(e)[0]).ravel() for e in range(disc.E)])
+    ga = np.stack([np.concatenate([np.asarray(disc.coef(e)[1][k]).ravel() for e in range(disc.E)])
+                   for k in range(3)])
+    return f, a, ga
+
+
+class DenseAdjoint:
+    """J(theta) = sum_q wJ (v(U) - u_t)^2 with A(theta) U = b(theta), its adjoint
+    gradient and Hessian-vector products, for a small box-mesh Discretisation."""
+
+    def __init__(self, disc, ut):
+        self.disc = disc
+        self.F = field_matrices(disc)
+        self.w = point_weights(disc)
+        self.ut = np.asarray(ut, dtype=np.float64)
+        f0, a0, ga0 = point_data(disc)
+        S0 = self.S(a0, ga0)
+        self.A_faces = disc.dense_A() - S0.T @ S0
+        self.b_faces = disc.rhs_b() - S0.T @ (np.sqrt(self.w) * f0)
+
+    def S(self, a, ga):
+        F = self.F
+        L = -(a[:, None] * F[4]) - sum(ga[k][:, None] * F[1 + k] for k in range(3))
+        return np.sqrt(self.w)[:, None] * L
+
+    def solve(self, f, a, ga):
+        S = self.S(a, ga)
+        A = S.T @ S + self.A_faces
+        b = S.T @ (np.sqrt(self.w) * f) + self.b_faces
+        return A, np.linalg.solve(A, b)
+
+    def J(self, f, a, ga):
+        _, U = self.solve(f, a, ga)
+        d = self.F[0] @ U - self.ut
+        return float(np.sum(self.w * d * d))
+
+    def gradient(self, f, a, ga):
+        """(dJ/df, dJ/da, dJ/d grad a) by the adjoint state (the formulas of
+        data_gradient with the point arrays)."""
+        A, U = self.solve(f, a, ga)
+        lam = np.linalg.solve(A, self.F[0].T @ (2.0 * self.w * (self.F[0] @ U - self.ut)))
+        u = [self.F[k] @ U for k in range(5)]
+        lm = [self.F[k] @ lam for k in range(5)]
+        Lu = -a * u[4] - sum(ga[k] * u[1 + k] for k in range(3))
+        Ll = -a * lm[4] - sum(ga[k] * lm[1 + k] for k in range(3))
+        res = Lu - f
+        w = self.w
+        return (w * Ll, w * (u[4] * Ll + res * lm[4]),
+                np.stack([w * (u[1 + k] * Ll + res * lm[1 + k]) for k in range(3)]))
+
+    def hessian_vector(self, f, a, ga, v, h):
+        """Central difference of the adjoint gradient along v = (vf, va, vga)."""
+        gp = self.gradient(f + h * v[0], a + h * v[1], ga + h * v[2])
+        gm = self.gradient(f - h * v[0], a - h * v[1], ga - h * v[2])
+        return tuple((p - m) / (2.0 * h) for p, m in zip(gp, gm))

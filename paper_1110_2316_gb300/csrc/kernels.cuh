@@ -715,6 +715,20 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
 #undef FSLOT
 }
 
+// rho[q] of one z-column: registers, or shared memory (stride Q2 + 1)
+template <bool SMEM>
+struct ColumnRho {
+  real v[Q];
+  __device__ __forceinline__ void bind(real *, int) {}
+  __device__ __forceinline__ real &operator[](int q) { return v[q]; }
+};
+template <>
+struct ColumnRho<true> {
+  real *p;
+  __device__ __forceinline__ void bind(real *base, int col) { p = base + col; }
+  __device__ __forceinline__ real &operator[](int q) { return p[q * (Q2 + 1)]; }
+};
+
 // warp-uniform dispatch of a runtime chunk index to its compile-time instance
 #define HPSE_DISPATCH4(NC, c, CALL)            \
   do {                                         \
@@ -727,7 +741,8 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
 // ---------------------------------------------------------------------------
 // Operator apply: y = A u  (volume + faces), one CTA per (element, rhs).
 // Shared memory: su[P3] | X[NX][QP2] | T region (T fields, then sy and the
-// face scratch) | D copy, per-face scales | FP64 reduction buffer (16-byte aligned).
+// face scratch) | D copy, per-face scales | (rho of the z-stage) | FP64
+// reduction buffer (16-byte aligned).
 // ---------------------------------------------------------------------------
 template <int COEF>
 struct ApplyLayout {
@@ -737,7 +752,18 @@ struct ApplyLayout {
   static constexpr int T_NEED = P3 + 6 * FACE_ARR * P2;
   static constexpr int T_REGION = T_REGION0 > T_NEED ? T_REGION0 : T_NEED;
   static constexpr int TABS = P2 + 12;  // D copy, then the per-face scales of the face gather
-  static constexpr int TOTAL = P3 + NX * QP2 + T_REGION + TABS;
+  static constexpr int TOTAL0 = P3 + NX * QP2 + T_REGION + TABS;
+  // the z-stage's pointwise residual rho per column in shared memory (Q
+  // entries per column, one spare column for the lanes past the last one)
+  // where that keeps APPLY_MINB CTAs per SM; else in registers
+  static constexpr int RHO_LEN = Q * (Q2 + 1);
+#if defined(HPSE_APPLY_RHO_REG)
+  static constexpr bool RHO_SMEM = false;  // set at build time (layout experiments)
+#else
+  static constexpr bool RHO_SMEM =
+      (((size_t)(TOTAL0 + RHO_LEN) * sizeof(real) + 64 * sizeof(double) + 1024) * APPLY_MINB <= 232448);
+#endif
+  static constexpr int TOTAL = TOTAL0 + (RHO_SMEM ? RHO_LEN : 0);
   // the FP64 reduction buffer starts on a 16-byte boundary whatever REAL is
   static constexpr size_t RED_OFF = (((size_t)TOTAL * sizeof(real) + 15) / 16) * 16;
   static constexpr size_t BYTES = RED_OFF + 64 * sizeof(double);
@@ -751,6 +777,7 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
   real *sX = su + P3;               // X0 | X2 | (X1)
   real *sT = sX + L::NX * QP2;      // T00 | TL | (T10) | (T01)
   real *stab = sT + L::T_REGION;    // D (runtime-indexed copy for the face gather) | per-face scales
+  real *srho = stab + L::TABS;      // rho of the z-stage (L::RHO_SMEM)
   double *red = reinterpret_cast<double *>(smem_raw + L::RED_OFF);
   static_assert(L::RED_OFF % 16 == 0, "reduction buffer must be 16-byte aligned");
   real *X0 = sX, *X2 = sX + QP2, *X1 = sX + 2 * QP2;
@@ -851,7 +878,9 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
     // z second derivative; x is constant along this z-column
     const real sz2c =
         (COEF == COEF_EDGE || COEF == COEF_VERTEX_EDGE) ? sz2 * A.kappa[(int64_t)e * hpse::KAPPA_STRIDE + qa] : sz2;
-    real rho[Q];
+    // lanes past the last column keep their rho in the spare column Q2
+    ColumnRho<L::RHO_SMEM> rho;
+    rho.bind(srho, ok ? l : Q2);
     if (MODE == MODE_TRANSPOSE) {
 #pragma unroll
       for (int qc = 0; qc < Q; ++qc) rho[qc] = (real)A.rho[(int64_t)r * A.nquad + cbase + (int64_t)qc * Q2];

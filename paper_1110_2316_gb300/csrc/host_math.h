@@ -274,6 +274,7 @@ inline DegreeTables build_tables(int W) {
   for (double v : t.KP) t.packed.push_back(v);
   for (double v : t.wq) t.packed.push_back(v);
   for (double v : t.mu) t.packed.push_back(v);
+  for (double v : t.DQ) t.packed.push_back(v);
   return t;
 }
 

@@ -3,6 +3,7 @@
 // HPSE_REGISTER_NAME (and HPSE_DOUBLE for REAL = double), then includes this.
 #include "kernels.cuh"
 #include "general.cuh"
+#include "ibp.cuh"
 
 namespace {
 
@@ -119,6 +120,21 @@ cudaError_t upload_fn(const double *pk) {
   for (int i = 0; i < P; ++i) t.MU[i] = (real)pk[o++];
   cudaError_t err = cudaMemcpyToSymbol(c_tab, &t, sizeof(Tables));
   if (err != cudaSuccess) return err;
+  // D_Q and D_Q^2 of the Q-point grid (integration-by-parts transpose), formed in FP64
+  {
+    IbpTables it;
+    const double *dqp = pk + o;
+    for (int i = 0; i < Q; ++i)
+      for (int j = 0; j < Q; ++j) {
+        double acc = 0.0;
+        for (int m = 0; m < Q; ++m) acc += dqp[i * Q + m] * dqp[m * Q + j];
+        it.DQ[i * Q + j] = (real)dqp[i * Q + j];
+        it.DQ2[i * Q + j] = (real)acc;
+      }
+    o += Q2;
+    err = cudaMemcpyToSymbol(c_ibp, &it, sizeof(IbpTables));
+    if (err != cudaSuccess) return err;
+  }
   cudaError_t e2;
   if ((e2 = set_smem_attr<COEF_LAPLACE, MODE_PLAIN>()) != cudaSuccess) return e2;
   if ((e2 = set_smem_attr<COEF_LAPLACE, MODE_PCG>()) != cudaSuccess) return e2;
@@ -138,6 +154,8 @@ cudaError_t upload_fn(const double *pk) {
   if ((e2 = set_smem_attr_gen<MODE_PLAIN>()) != cudaSuccess) return e2;
   if ((e2 = set_smem_attr_gen<MODE_PCG>()) != cudaSuccess) return e2;
   if ((e2 = set_smem_attr_gen<MODE_TRANSPOSE>()) != cudaSuccess) return e2;
+  if ((e2 = set_smem_attr_ibp<COEF_LAPLACE>()) != cudaSuccess) return e2;
+  if ((e2 = set_smem_attr_ibp<COEF_SCALAR>()) != cudaSuccess) return e2;
   if ((e2 = cudaFuncSetAttribute(k_precond<MODE_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)PC_BYTES)) != cudaSuccess)
     return e2;
@@ -145,6 +163,19 @@ cudaError_t upload_fn(const double *pk) {
                                  (int)PC_BYTES)) != cudaSuccess)
     return e2;
   return cudaSuccess;
+}
+
+cudaError_t transpose_ibp_fn(int coef, const void *args, int n_items, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  if (coef == COEF_LAPLACE) return launch_transpose_ibp_t<COEF_LAPLACE>(args, n_items, s);
+  if (coef == COEF_SCALAR) return launch_transpose_ibp_t<COEF_SCALAR>(args, n_items, s);
+  return cudaErrorInvalidValue;
+}
+
+size_t ibp_smem_fn(int coef) {
+  if (coef == COEF_LAPLACE) return IbpLayout<COEF_LAPLACE>::FITS ? IbpLayout<COEF_LAPLACE>::BYTES : 0;
+  if (coef == COEF_SCALAR) return IbpLayout<COEF_SCALAR>::FITS ? IbpLayout<COEF_SCALAR>::BYTES : 0;
+  return 0;
 }
 
 static_assert(ApplyLayout<COEF_SCALAR>::BYTES <= 232448, "apply kernel exceeds 227 KB of shared memory");
@@ -163,4 +194,6 @@ extern "C" void HPSE_REGISTER_NAME(hpse::KernelSet *ks) {
   ks->apply_smem = apply_smem_fn;
   ks->apply_max_threads = apply_max_threads_fn;
   ks->precond = precond_fn;
+  ks->transpose_ibp = transpose_ibp_fn;
+  ks->ibp_smem = ibp_smem_fn;
 }

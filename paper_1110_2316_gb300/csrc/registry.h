@@ -81,10 +81,11 @@ struct PrecArgsT {
 };
 
 // Packed FP64 tables for one degree, in the order of the device struct:
-// B0, B1, B2 (Q*P each), D (P*P), S (P*P), MP (P*P), KP (P*P), WQ (Q), MU (P).
+// B0, B1, B2 (Q*P each), D (P*P), S (P*P), MP (P*P), KP (P*P), WQ (Q), MU (P),
+// then DQ (Q*Q, the differentiation matrix of the Q-point grid).
 inline int packed_table_size(int W) {
   const int P = W + 1, Q = 2 * W + 1;
-  return 3 * Q * P + 4 * P * P + Q + P;
+  return 3 * Q * P + 4 * P * P + Q + P + Q * Q;
 }
 
 struct KernelSet {
@@ -97,6 +98,11 @@ struct KernelSet {
   int (*apply_max_threads)(int coef);
   // mode: MODE_PLAIN or MODE_PCG; args points to PrecArgsT<T>
   cudaError_t (*precond)(int mode, const void *args, int n_items, int threads, cudaStream_t s);
+  // volume transpose in integration-by-parts form (COEF_LAPLACE, COEF_SCALAR;
+  // args as for MODE_TRANSPOSE); ibp_smem: its shared memory, 0 where the
+  // instance is not built
+  cudaError_t (*transpose_ibp)(int coef, const void *args, int n_items, cudaStream_t s);
+  size_t (*ibp_smem)(int coef);
 };
 
 }  // namespace hpse

@@ -378,6 +378,18 @@ hpse_status hpse_conforming_correction(hpse_mesh *m, const double *u, double *p,
 hpse_status hpse_apply_residual(hpse_mesh *m, int32_t prec, const void *u, void *z, void *stream);
 hpse_status hpse_apply_transpose(hpse_mesh *m, int32_t prec, const void *z, void *y, void *stream);
 
+/* The same volume transpose as hpse_apply_transpose (y = S^T z of the
+ * residual map, faces excluded), computed in the integration-by-parts form of
+ * eq. (5.45)-(5.48): the point values are interpolated on the (2W+1)-point
+ * grid, differentiated there with its differentiation matrix (eq. 5.47) after
+ * each term's coefficient is applied, projected onto the nodal basis, and the
+ * six faces' boundary terms added.  Equal to hpse_apply_transpose up to
+ * rounding (the rule integrates every integrand exactly).  Same arguments,
+ * layouts and restrictions as hpse_apply_transpose; HPSE_ERR_DEGREE where the
+ * kernel's shared-memory layout does not fit (FP64 with -div(a grad u) at
+ * W = 10). */
+hpse_status hpse_apply_transpose_ibp(hpse_mesh *m, int32_t prec, const void *z, void *y, void *stream);
+
 /* Point values of a DOF vector (FP64): out[r][0..4][q] = v, dv/dx, dv/dy,
  * dv/dz, Lap v at the volume points (physical coordinates). */
 hpse_status hpse_eval_fields(hpse_mesh *m, const double *u, double *out, void *stream);
@@ -385,6 +397,12 @@ hpse_status hpse_eval_fields(hpse_mesh *m, const double *u, double *out, void *s
 /* Transpose of point evaluation (FP64): y = sum_q rho[r][q] dv_r(x_q)/dV,
  * rho device [n_rhs][nquad], y a device DOF vector (overwritten). */
 hpse_status hpse_apply_eval_transpose(hpse_mesh *m, const double *rho, double *y, void *stream);
+
+/* Transpose of hpse_eval_fields (FP64): y = sum_q sum_k wf[r][k][q]
+ * d(field_k v_r)(x_q)/dV over the five fields (v, v_x, v_y, v_z, Lap v); wf
+ * device [n_rhs][5][nquad], y a device DOF vector (overwritten).  The backward
+ * of the point fields, for second-order adjoints. */
+hpse_status hpse_apply_fields_transpose(hpse_mesh *m, const double *wf, double *y, void *stream);
 
 /* w_q J_e at the volume points (device FP64 [nquad]). */
 hpse_status hpse_quad_weights(hpse_mesh *m, double *out, void *stream);
@@ -402,6 +420,25 @@ hpse_status hpse_set_rhs(hpse_mesh *m, const double *b, void *stream);
  * term of eq. 4.2 is the only one that depends on f and a). */
 hpse_status hpse_data_gradient(hpse_mesh *m, const double *ufields, const double *lfields, double *out,
                                void *stream);
+
+/* The same with f taken as 0 (L u in place of L u - f): out = -d/dtheta of
+ * lambda^T A(theta) u for fixed u and lambda (symmetric in the two), the
+ * derivative of an adjoint solve lambda = A^{-1} g with respect to a, grad a. */
+hpse_status hpse_data_gradient_bilinear(hpse_mesh *m, const double *ufields, const double *lfields, double *out,
+                                        void *stream);
+
+/* Vector-Jacobian product of hpse_data_gradient (with_f = 1) or of
+ * hpse_data_gradient_bilinear (with_f = 0) at every point: given the
+ * cotangent obar [n_rhs][5][nquad] of its output, the cotangents of its
+ * inputs: ubar, lbar [n_rhs][5][nquad] (the fields of u and of lambda) and
+ * dbar [n_rhs][5][nquad] (f, a, d_x a, d_y a, d_z a per rhs; a and grad a
+ * are shared by the rhs, so their cotangent is the sum over r; dbar[.][0] is
+ * 0 when with_f = 0).  Device FP64 arrays, overwritten.  The pointwise
+ * derivatives of the formulas of hpse_data_gradient; with the fields'
+ * transpose and two more solves they give Hessian-vector products of a
+ * solution functional (second-order adjoint). */
+hpse_status hpse_data_gradient_vjp(hpse_mesh *m, int32_t with_f, const double *ufields, const double *lfields,
+                                   const double *obar, double *ubar, double *lbar, double *dbar, void *stream);
 
 /* Allocation-free variant of hpse_h1_error (same arguments, same results up
  * to the order of the final per-rhs sums).  The thesis has no counterpart: it

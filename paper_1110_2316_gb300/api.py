@@ -100,7 +100,8 @@ class Mesh:
         self.coef_kind = int(coef_kind)
         self.elem_W = self._keep[0]
         self.device = device
-        # bumped by every set_data / set_rhs: autograd.Solve checks it
+        # bumped by every set_data (the operator's coefficients and f): the
+        # autograd functions check it; set_rhs changes only b
         self.data_version = 0
 
     # -- sizes ------------------------------------------------------------
@@ -213,6 +214,11 @@ class Mesh:
         check(self._lib.hpse_apply_transpose(self._h, _prec_of(z), _ptr(z), _ptr(y), _stream(stream)),
               "hpse_apply_transpose")
 
+    def apply_transpose_ibp(self, z, y, stream=None):
+        """y = S^T z in the integration-by-parts form of eq. (5.45)-(5.48)."""
+        check(self._lib.hpse_apply_transpose_ibp(self._h, _prec_of(z), _ptr(z), _ptr(y), _stream(stream)),
+              "hpse_apply_transpose_ibp")
+
     def eval_fields(self, u, out, stream=None):
         check(self._lib.hpse_eval_fields(self._h, _ptr(u), _ptr(out), _stream(stream)), "hpse_eval_fields")
 
@@ -224,12 +230,24 @@ class Mesh:
         check(self._lib.hpse_quad_weights(self._h, _ptr(out), _stream(stream)), "hpse_quad_weights")
 
     def set_rhs(self, b, stream=None):
-        self.data_version += 1
         check(self._lib.hpse_set_rhs(self._h, _ptr(b), _stream(stream)), "hpse_set_rhs")
 
     def data_gradient(self, ufields, lfields, out, stream=None):
         check(self._lib.hpse_data_gradient(self._h, _ptr(ufields), _ptr(lfields), _ptr(out), _stream(stream)),
               "hpse_data_gradient")
+
+    def data_gradient_bilinear(self, ufields, lfields, out, stream=None):
+        check(self._lib.hpse_data_gradient_bilinear(self._h, _ptr(ufields), _ptr(lfields), _ptr(out),
+                                                    _stream(stream)), "hpse_data_gradient_bilinear")
+
+    def data_gradient_vjp(self, with_f, ufields, lfields, obar, ubar, lbar, dbar, stream=None):
+        check(self._lib.hpse_data_gradient_vjp(self._h, 1 if with_f else 0, _ptr(ufields), _ptr(lfields),
+                                               _ptr(obar), _ptr(ubar), _ptr(lbar), _ptr(dbar), _stream(stream)),
+              "hpse_data_gradient_vjp")
+
+    def apply_fields_transpose(self, wf, y, stream=None):
+        check(self._lib.hpse_apply_fields_transpose(self._h, _ptr(wf), _ptr(y), _stream(stream)),
+              "hpse_apply_fields_transpose")
 
     def work_counts(self):
         v, f = C.c_double(), C.c_double()

@@ -3191,6 +3191,57 @@ __global__ void k_eval_T(FieldArgs A, const double *rho) {
   }
 }
 
+// y = sum_q sum_k wf[r][k][q] (field_k v)(x_q) / dV: the transpose of
+// hpse_eval_fields (fields v, v_x, v_y, v_z, Lap v); one block per (element,
+// rhs).  The seven tensor terms (x, y, z matrices and scale) are transposed
+// one after the other through the three stages of k_eval_T and summed.
+__global__ void k_fields_T(FieldArgs A, const double *wf) {
+  extern __shared__ double sm[];
+  const int item = blockIdx.x;
+  const int e = item / A.n_rhs, r = item - e * A.n_rhs;
+  const int W = A.elem_W[e], P = W + 1, Q = 2 * W + 1;
+  const double *B[3] = {A.qtab[W], A.qtab[W] + Q * P, A.qtab[W] + 2 * Q * P + 2 * Q * Q + Q};
+  double *R = sm, *T = R + Q * Q * Q, *X = T + Q * Q * P, *Y = X + Q * P * P;
+  const int nt = blockDim.x;
+  const double *gs = A.geo + 4 * (int64_t)e;
+  const int64_t nq = A.nquad;
+  const int64_t qb0 = (int64_t)r * 5 * nq + A.coef_off[e];
+  for (int t = threadIdx.x; t < P * P * P; t += nt) Y[t] = 0.0;
+  // term: field, matrix orders along (x, y, z), scale
+  const int fld[7] = {0, 1, 2, 3, 4, 4, 4};
+  const int mx[7] = {0, 1, 0, 0, 2, 0, 0}, my[7] = {0, 0, 1, 0, 0, 2, 0}, mz[7] = {0, 0, 0, 1, 0, 0, 2};
+  for (int term = 0; term < 7; ++term) {
+    const double sc = term == 0 ? 1.0 : (term < 4 ? gs[term - 1] : gs[term - 4] * gs[term - 4]);
+    const double *Mx = B[mx[term]], *My = B[my[term]], *Mz = B[mz[term]];
+    __syncthreads();
+    for (int t = threadIdx.x; t < Q * Q * Q; t += nt) R[t] = sc * wf[qb0 + fld[term] * nq + t];
+    __syncthreads();
+    for (int t = threadIdx.x; t < Q * Q * P; t += nt) {  // T[k][qb][qa]
+      const int qa = t % Q, qb = (t / Q) % Q, k = t / (Q * Q);
+      double s = 0.0;
+      for (int qc = 0; qc < Q; ++qc) s += Mz[qc * P + k] * R[(qc * Q + qb) * Q + qa];
+      T[t] = s;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < Q * P * P; t += nt) {  // X[k][j][qa]
+      const int qa = t % Q, j = (t / Q) % P, k = t / (Q * P);
+      double s = 0.0;
+      for (int qb = 0; qb < Q; ++qb) s += My[qb * P + j] * T[(k * Q + qb) * Q + qa];
+      X[t] = s;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < P * P * P; t += nt) {
+      const int i = t % P, l = t / P;
+      double s = 0.0;
+      for (int qa = 0; qa < Q; ++qa) s += Mx[qa * P + i] * X[l * Q + qa];
+      Y[t] += s;
+    }
+  }
+  __syncthreads();
+  const int64_t base = (int64_t)r * A.ndof + A.dof_off[e];
+  for (int t = threadIdx.x; t < P * P * P; t += nt) A.out[base + t] = Y[t];
+}
+
 // residual map at the points: z = sqrt(wJ) (L u - f)
 template <typename T>
 __global__ void k_resid_points(int64_t nquad, int n_rhs, const double *aux, const double *f, const T *fields,
@@ -3230,13 +3281,52 @@ __global__ void k_data_grad(int64_t nquad, int n_rhs, const double *aux, const d
     const double lx = l[nquad + q], ly = l[2 * nquad + q], lz = l[3 * nquad + q], ll = l[4 * nquad + q];
     const double Lu = -a * lu - (ax * ux + ay * uy + az * uz);
     const double Ll = -a * ll - (ax * lx + ay * ly + az * lz);
-    const double res = Lu - f[i];
+    const double res = f ? Lu - f[i] : Lu;
     double *o = out + r * 5 * nquad;
     o[q] = wJ * Ll;
     o[nquad + q] = wJ * (lu * Ll + res * ll);
     o[2 * nquad + q] = wJ * (ux * Ll + res * lx);
     o[3 * nquad + q] = wJ * (uy * Ll + res * ly);
     o[4 * nquad + q] = wJ * (uz * Ll + res * lz);
+  }
+}
+
+// Vector-Jacobian product of k_data_grad at every point: given the cotangent
+// ob[r][0..4][q] of its output, the cotangents of its inputs -- the fields of
+// u (ub) and of lambda (lb), [r][0..4][q], and the data db[r][0..4][q] = (f,
+// a, d_x a, d_y a, d_z a) per rhs (a and grad a are shared by the rhs: the
+// caller sums db over r for them).  With f == nullptr the residual is L u (the
+// bilinear form -d/dtheta lambda^T A u) and db[.][0] is zero.
+//   c_L = wJ (ob0 + ob1 Lap u + ob2 u_x + ob3 u_y + ob4 u_z)   (d out / d L lambda)
+//   c_R = wJ (ob1 Lap l + ob2 l_x + ob3 l_y + ob4 l_z)         (d out / d res)
+__global__ void k_data_grad_vjp(int64_t nquad, int n_rhs, const double *aux, const double *f, const double *uf,
+                                const double *lf, const double *ob, double *ub, double *lb, double *db) {
+  const int64_t n = nquad * n_rhs;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / nquad, q = i - r * nquad;
+    const int64_t o5 = r * 5 * nquad + q;
+    const double *u = uf + o5, *l = lf + o5, *g = ob + o5;
+    const double wJ = aux[q], a = aux[nquad + q];
+    const double ad[3] = {aux[2 * nquad + q], aux[3 * nquad + q], aux[4 * nquad + q]};
+    const double ud[3] = {u[nquad], u[2 * nquad], u[3 * nquad]}, lu = u[4 * nquad];
+    const double ld[3] = {l[nquad], l[2 * nquad], l[3 * nquad]}, ll = l[4 * nquad];
+    const double Lu = -a * lu - (ad[0] * ud[0] + ad[1] * ud[1] + ad[2] * ud[2]);
+    const double Ll = -a * ll - (ad[0] * ld[0] + ad[1] * ld[1] + ad[2] * ld[2]);
+    const double res = f ? Lu - f[i] : Lu;
+    const double cL = wJ * (g[0] + g[nquad] * lu + g[2 * nquad] * ud[0] + g[3 * nquad] * ud[1] + g[4 * nquad] * ud[2]);
+    const double cR = wJ * (g[nquad] * ll + g[2 * nquad] * ld[0] + g[3 * nquad] * ld[1] + g[4 * nquad] * ld[2]);
+    double *uo = ub + o5, *lo = lb + o5, *dd = db + o5;
+    uo[0] = 0.0;
+    lo[0] = 0.0;
+    uo[4 * nquad] = wJ * Ll * g[nquad] - a * cR;
+    lo[4 * nquad] = wJ * res * g[nquad] - a * cL;
+    for (int k = 0; k < 3; ++k) {
+      uo[(1 + k) * nquad] = wJ * Ll * g[(2 + k) * nquad] - ad[k] * cR;
+      lo[(1 + k) * nquad] = wJ * res * g[(2 + k) * nquad] - ad[k] * cL;
+      dd[(2 + k) * nquad] = -ld[k] * cL - ud[k] * cR;
+    }
+    dd[0] = f ? -cR : 0.0;
+    dd[nquad] = -ll * cL - lu * cR;
   }
 }
 
@@ -3296,6 +3386,23 @@ extern "C" hpse_status hpse_apply_eval_transpose(hpse_mesh *m, const double *rho
   const size_t smem = (size_t)(Q * Q * Q + Q * Q * P + Q * P * P) * sizeof(double);
   CK(raise_smem((const void *)k_eval_T, m->device, (size_t)smem));
   k_eval_T<<<n_items_all(m), 256, smem, (cudaStream_t)stream>>>(field_args<double>(m, nullptr, y), rho);
+  CK(cudaGetLastError());
+  ++g_launches;
+  return HPSE_OK;
+}
+
+extern "C" hpse_status hpse_apply_fields_transpose(hpse_mesh *m, const double *wf, double *y, void *stream) {
+  // box meshes of the Laplacian or -div(a grad u) only
+  if (m && (m->coord != HPSE_COORD_CARTESIAN || m->coef_kind == HPSE_COEF_GENERAL)) return HPSE_ERR_INVALID_ARG;
+  if (!m) return HPSE_ERR_INVALID_ARG;
+  if (m->ndof == 0) return HPSE_OK;
+  if (!wf || !y) return HPSE_ERR_INVALID_ARG;
+  if (!m->has_data) return HPSE_ERR_NO_DATA;
+  CK(cudaSetDevice(m->device));
+  const int W = max_degree(m), P = W + 1, Q = 2 * W + 1;
+  const size_t smem = (size_t)(Q * Q * Q + Q * Q * P + Q * P * P + P * P * P) * sizeof(double);
+  CK(raise_smem((const void *)k_fields_T, m->device, (size_t)smem));
+  k_fields_T<<<n_items_all(m), 256, smem, (cudaStream_t)stream>>>(field_args<double>(m, nullptr, y), wf);
   CK(cudaGetLastError());
   ++g_launches;
   return HPSE_OK;
@@ -3372,6 +3479,47 @@ extern "C" hpse_status hpse_apply_transpose(hpse_mesh *m, int32_t prec, const vo
   return transpose_t<float>(m, (const float *)z, (float *)y, s);
 }
 
+// the volume transpose in integration-by-parts form (eq. 5.45-5.48), per degree group
+template <typename T>
+static hpse_status transpose_ibp_t(hpse_mesh *m, const T *z, T *y, cudaStream_t s) {
+  hpse_status st = ensure_scratch(m, sizeof(double));
+  if (st != HPSE_OK) return st;
+  k_rho_from_z<T><<<1024, 256, 0, s>>>(m->nquad, m->n_rhs, m->d_aux.as<double>(), z, m->d_scr_rho.as<double>());
+  CK(cudaGetLastError());
+  ++g_launches;
+  const int pi = sizeof(T) == 8 ? 0 : 1;
+  ApplyArgsT<T> base = apply_args<T>(m, m->groups[0], nullptr, y);
+  base.rho = m->d_scr_rho.as<double>();
+  base.skip_faces = 1;
+  CK(group_fork(m, s));
+  for (size_t gi = 0; gi < m->groups.size(); ++gi) {
+    const Group &g = m->groups[gi];
+    ApplyArgsT<T> a = base;
+    a.elems = g.elems.as<int32_t>();
+    a.n_group = g.n;
+    CK(g_sets[pi][g.W].transpose_ibp(m->apply_coef, &a, g.n * m->n_rhs, group_stream(m, gi, s)));
+    ++g_launches;
+  }
+  CK(group_join(m, s));
+  return HPSE_OK;
+}
+
+extern "C" hpse_status hpse_apply_transpose_ibp(hpse_mesh *m, int32_t prec, const void *z, void *y, void *stream) {
+  // box meshes of the Laplacian or -div(a grad u) only
+  if (m && (m->coord != HPSE_COORD_CARTESIAN || m->coef_kind == HPSE_COEF_GENERAL)) return HPSE_ERR_INVALID_ARG;
+  if (!m || (prec != HPSE_FP64 && prec != HPSE_FP32)) return HPSE_ERR_INVALID_ARG;
+  if (m->ndof == 0) return HPSE_OK;
+  if (!z || !y) return HPSE_ERR_INVALID_ARG;
+  if (!m->has_data) return HPSE_ERR_NO_DATA;
+  const int pi = prec == HPSE_FP64 ? 0 : 1;
+  for (const Group &g : m->groups)
+    if (g_sets[pi][g.W].ibp_smem(m->apply_coef) == 0) return HPSE_ERR_DEGREE;
+  CK(cudaSetDevice(m->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (prec == HPSE_FP64) return transpose_ibp_t<double>(m, (const double *)z, (double *)y, s);
+  return transpose_ibp_t<float>(m, (const float *)z, (float *)y, s);
+}
+
 extern "C" hpse_status hpse_data_gradient(hpse_mesh *m, const double *ufields, const double *lfields, double *out,
                                           void *stream) {
   // box meshes of the Laplacian or -div(a grad u) only
@@ -3383,6 +3531,40 @@ extern "C" hpse_status hpse_data_gradient(hpse_mesh *m, const double *ufields, c
   CK(cudaSetDevice(m->device));
   k_data_grad<<<1024, 256, 0, (cudaStream_t)stream>>>(m->nquad, m->n_rhs, m->d_aux.as<double>(), m->d_f.as<double>(),
                                                       ufields, lfields, out);
+  CK(cudaGetLastError());
+  ++g_launches;
+  return HPSE_OK;
+}
+
+extern "C" hpse_status hpse_data_gradient_bilinear(hpse_mesh *m, const double *ufields, const double *lfields,
+                                                   double *out, void *stream) {
+  // box meshes of the Laplacian or -div(a grad u) only
+  if (m && (m->coord != HPSE_COORD_CARTESIAN || m->coef_kind == HPSE_COEF_GENERAL)) return HPSE_ERR_INVALID_ARG;
+  if (!m) return HPSE_ERR_INVALID_ARG;
+  if (m->nquad == 0) return HPSE_OK;
+  if (!ufields || !lfields || !out) return HPSE_ERR_INVALID_ARG;
+  if (!m->has_data) return HPSE_ERR_NO_DATA;
+  CK(cudaSetDevice(m->device));
+  k_data_grad<<<1024, 256, 0, (cudaStream_t)stream>>>(m->nquad, m->n_rhs, m->d_aux.as<double>(), nullptr, ufields,
+                                                      lfields, out);
+  CK(cudaGetLastError());
+  ++g_launches;
+  return HPSE_OK;
+}
+
+extern "C" hpse_status hpse_data_gradient_vjp(hpse_mesh *m, int32_t with_f, const double *ufields,
+                                              const double *lfields, const double *obar, double *ubar, double *lbar,
+                                              double *dbar, void *stream) {
+  // box meshes of the Laplacian or -div(a grad u) only
+  if (m && (m->coord != HPSE_COORD_CARTESIAN || m->coef_kind == HPSE_COEF_GENERAL)) return HPSE_ERR_INVALID_ARG;
+  if (!m || (with_f != 0 && with_f != 1)) return HPSE_ERR_INVALID_ARG;
+  if (m->nquad == 0) return HPSE_OK;
+  if (!ufields || !lfields || !obar || !ubar || !lbar || !dbar) return HPSE_ERR_INVALID_ARG;
+  if (!m->has_data) return HPSE_ERR_NO_DATA;
+  CK(cudaSetDevice(m->device));
+  k_data_grad_vjp<<<1024, 256, 0, (cudaStream_t)stream>>>(m->nquad, m->n_rhs, m->d_aux.as<double>(),
+                                                          with_f ? m->d_f.as<double>() : nullptr, ufields, lfields,
+                                                          obar, ubar, lbar, dbar);
   CK(cudaGetLastError());
   ++g_launches;
   return HPSE_OK;

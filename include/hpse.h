@@ -219,9 +219,12 @@ typedef struct {
  * desc and its arrays are read during the call only.  On success *out is a
  * handle owned by the caller until hpse_destroy; on failure *out is NULL and
  * the status says why: HPSE_ERR_INVALID_ARG (pointers, counts, enums, corner
- * codes), HPSE_ERR_NONMATCHING_FACE, HPSE_ERR_DEGREE (W outside [1, 10] or
- * unequal across a face), HPSE_ERR_OOM, HPSE_ERR_CUDA.  Validation runs
- * before any device call.  Synchronous. */
+ * codes), HPSE_ERR_NONMATCHING_FACE, HPSE_ERR_DEGREE (W outside [1, 10], or
+ * unequal across a face of a neighbourhood mesh), HPSE_ERR_OOM, HPSE_ERR_CUDA.
+ * Validation runs before any device call.  Synchronous.  Box meshes may have
+ * unequal degrees W, W' across an interior face: its terms are taken on the
+ * (2 max(W, W') + 1)-point grid of the face (eq. 4.2), as the nodal forms of
+ * the higher degree with both traces interpolated onto its nodes. */
 hpse_status hpse_setup_mesh(const hpse_mesh_desc *desc, int device, hpse_mesh **out);
 
 /* Sizes: DOFs per right-hand side; volume points; Dirichlet face points. */
@@ -355,6 +358,7 @@ hpse_status hpse_h1_error(hpse_mesh *m, const double *u, const double *ref,
  * (blended bilinearly in the other variables), nu per face to the average of
  * the two traces (blended linearly in the normal variable); target 0 on the
  * Dirichlet boundary.  p stays in the (W+1)^3 nodal space of every element.
+ * HPSE_ERR_DEGREE for meshes with unequal degrees across a face.
  * u, p: device FP64 DOF vectors of n_rhs*ndof (p may be u).  Box meshes
  * (HPSE_ERR_INVALID_ARG for neighbourhood kinds).  The first call builds the
  * vertex and edge tables and two scratch vectors on the handle (synchronous);

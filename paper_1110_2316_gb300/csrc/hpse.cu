@@ -191,6 +191,11 @@ struct hpse_mesh {
   std::vector<double> fgam;
   bool has_nr = false;
   DevBuf d_fbc, d_fgam64, d_fgam32;
+  // interior faces between unequal degrees (fbc code 3; box meshes): the
+  // elements that have one, and the 1-D tables of k_face_mixed
+  bool has_mixed = false;
+  std::vector<int32_t> mixed_elems;
+  DevBuf d_mixed_elems, d_mix_tab, d_mix_ptr;
   std::vector<int64_t> dof_off, coef_off;
   int64_t ndof = 0, nquad = 0;
   std::vector<int> bface_elem, bface_fi;   // boundary faces
@@ -938,7 +943,7 @@ static ApplyArgsT<T> apply_args(const hpse_mesh *m, const Group &g, const T *u, 
     a.cslot = m->d_cslot.as<int32_t>();
     a.cscr = m->n_corner ? (d ? (T *)m->d_cscr64.p : (T *)m->d_cscr32.p) : nullptr;
   }
-  if (m->has_nr) {
+  if (m->has_nr || m->has_mixed) {
     a.fbc = m->d_fbc.as<int32_t>();
     a.fgam = (sizeof(T) == 8) ? (const T *)m->d_fgam64.p : (const T *)m->d_fgam32.p;
   }
@@ -1002,6 +1007,10 @@ static cudaStream_t group_stream(hpse_mesh *m, size_t gi, cudaStream_t s) {
 }
 
 template <typename T>
+static hpse_status launch_mixed(hpse_mesh *m, int mode, const T *u, T *y, double *partial, int n_rhs, int self_only,
+                                int only_W, cudaStream_t s);
+
+template <typename T>
 static hpse_status launch_apply_all(hpse_mesh *m, int mode, ApplyArgsT<T> base_args, cudaStream_t s) {
   const int pi = sizeof(T) == 8 ? 0 : 1;
   CK(group_fork(m, s));
@@ -1016,6 +1025,14 @@ static hpse_status launch_apply_all(hpse_mesh *m, int mode, ApplyArgsT<T> base_a
     ++g_launches;
   }
   CK(group_join(m, s));
+  if (m->has_mixed && mode != MODE_TRANSPOSE && !base_args.skip_faces) {
+    // faces between unequal degrees, after every element's apply (PCG mode:
+    // the new search direction of every element is in pnew by then)
+    const T *uu = mode == MODE_PCG ? base_args.pnew : base_args.u;
+    hpse_status st = launch_mixed<T>(m, mode, uu, base_args.y, base_args.partial, base_args.n_rhs,
+                                     base_args.self_only, 0, s);
+    if (st != HPSE_OK) return st;
+  }
   if (m->n_corner > 0 && !base_args.self_only) {
     // corner sets: sum of their face slots (after every element's face phase)
     CornerArgsT<T> c = corner_args<T>(m);
@@ -1202,6 +1219,288 @@ extern "C" int64_t hpse_kernel_launch_count(int32_t reset) {
 // [u] in L2 times F hh_t1 hh_t2 (times G = E on zeta = const), the zeta
 // derivative times E^2; Dirichlet: u - g in L2 times F hh_t1 hh_t2, the
 // tangential fields times s_t^2 (zeta: times E^2).  Corner sets of both kinds.
+// ---------------------------------------------------------------------------
+// Interior faces between unequal degrees W and W' (box meshes).  The face
+// terms of eq. (4.2) on the (2 Wf + 1)-point grid, Wf = max(W, W'), are the
+// nodal Kronecker forms of degree Wf (as on equal-degree faces): both traces
+// are interpolated onto the (Wf + 1)^2 face nodes (exactly: a polynomial of
+// degree <= Wf), the jumps of u and of the physical gradient formed there, the
+// L2 form MP x MP and the H^{1/2} form MP x MP + MP x KP + KP x MP of degree
+// Wf applied, and the result taken back to the element's own nodes by the
+// transposed interpolation.  One block per (element with such a face, rhs);
+// its faces one after the other; y += the face terms (and, in PCG mode, the
+// partial p.q += p . the face terms).  k_apply skips these faces (code 3).
+// ---------------------------------------------------------------------------
+struct MixArgs {
+  int n_items;
+  const int32_t *items;       // elements with at least one face of code 3
+  int n_rhs;
+  int64_t ndof;
+  const int64_t *dof_off;
+  const int32_t *nbr, *fbc, *elem_W;
+  const double *geo;          // per element (s_x, s_y, s_z, J), FP64
+  const double *const *tab;   // [W]: D (P x P, D[i][k] = l_k'(x_i)) | MP | KP
+  const double *const *itp;   // [W * 11 + Wf], W < Wf: (Wf + 1) x (W + 1) interpolation
+  int self_only;              // neighbour traces taken as zero (diagonal blocks)
+  int only_W;                 // 0: every item; else only the elements of this degree
+};
+
+// out[r][c] (n x n, [p2][p1]) = sum_k M[c][k] in[r][k] (along p1) or
+// sum_k M[r][k] in[k][c] (along p2); M of size n x m, in m-wide
+template <typename T>
+__device__ void mix_apply(const double *M, int n, int m, const T *in, T *out, bool along_p1, bool transpose,
+                          int rows) {
+  // transpose: M^T (m x n) applied, i.e. out has m columns (along p1) or m rows (along p2)
+  const int oc = along_p1 ? (transpose ? m : n) : rows;
+  const int orr = along_p1 ? rows : (transpose ? m : n);
+  const int ic = along_p1 ? (transpose ? n : m) : rows;
+  for (int t = threadIdx.x; t < orr * oc; t += blockDim.x) {
+    const int r = t / oc, c = t - r * oc;
+    T acc = 0;
+    if (along_p1) {
+      const int K = transpose ? n : m;
+      for (int k = 0; k < K; ++k) acc += (T)(transpose ? M[k * m + c] : M[c * m + k]) * in[r * ic + k];
+    } else {
+      const int K = transpose ? n : m;
+      for (int k = 0; k < K; ++k) acc += (T)(transpose ? M[k * m + r] : M[r * m + k]) * in[k * ic + c];
+    }
+    out[t] = acc;
+  }
+  __syncthreads();
+}
+
+template <typename T, int MODE>
+__global__ void k_face_mixed(MixArgs A, const T *u, T *y, double *partial) {
+  extern __shared__ __align__(16) unsigned char mix_raw[];
+  T *sm = reinterpret_cast<T *>(mix_raw);
+  const int item = blockIdx.x / A.n_rhs, r = blockIdx.x - item * A.n_rhs;
+  const int e = A.items[item];
+  const int We = A.elem_W[e];
+  if (A.only_W && We != A.only_W) return;
+  const int Pe = We + 1;
+  constexpr int PM = HPSE_MAX_W + 1, PM2 = PM * PM;
+  T *ue = sm;                      // own block, P_e^3
+  T *ye = ue + PM * PM2;           // its face terms, P_e^3
+  T *buf = ye + PM * PM2;          // 12 face arrays of PM^2
+  T *Te = buf, *Ne = buf + PM2, *Tn = buf + 2 * PM2, *Nn = buf + 3 * PM2;
+  T *X0 = buf + 4 * PM2, *X1 = buf + 5 * PM2, *X2 = buf + 6 * PM2, *X3 = buf + 7 * PM2;
+  T *W0 = buf + 8 * PM2, *W1 = buf + 9 * PM2, *W2 = buf + 10 * PM2, *W3 = buf + 11 * PM2;
+  const int64_t base = (int64_t)r * A.ndof + A.dof_off[e];
+  const int Pe3 = Pe * Pe * Pe;
+  for (int t = threadIdx.x; t < Pe3; t += blockDim.x) {
+    ue[t] = u[base + t];
+    ye[t] = 0;
+  }
+  __syncthreads();
+  const double *se = A.geo + 4 * (int64_t)e;
+  const double *De = A.tab[We];
+  for (int f = 0; f < 6; ++f) {
+    if (A.fbc[6 * (int64_t)e + f] != 3) continue;
+    const int nb = A.nbr[6 * (int64_t)e + f];
+    const int Wn = A.elem_W[nb], Pn = Wn + 1;
+    const int Wf = We > Wn ? We : Wn, Pf = Wf + 1;
+    const int a = f >> 1, side = f & 1;
+    const int t1 = a == 0 ? 1 : 0, t2 = a == 2 ? 1 : 2;
+    const double *sn = A.geo + 4 * (int64_t)nb;
+    const double *Dn = A.tab[Wn];
+    const double *Df = A.tab[Wf], *MPf = Df + Pf * Pf, *KPf = MPf + Pf * Pf;
+    const double *Ie = We < Wf ? A.itp[We * 11 + Wf] : nullptr;
+    const double *In = Wn < Wf ? A.itp[Wn * 11 + Wf] : nullptr;
+    // traces and normal derivatives (d/dlambda_a) on each side's own face nodes [p2][p1]
+    const int ende = side ? Pe - 1 : 0, endn = side ? 0 : Pn - 1;
+    const int64_t nbase = (int64_t)r * A.ndof + A.dof_off[nb];
+    for (int t = threadIdx.x; t < Pe * Pe; t += blockDim.x) {
+      const int p1 = t % Pe, p2 = t / Pe;
+      T nv = 0;
+      for (int k = 0; k < Pe; ++k) {
+        const int i = a == 0 ? k : p1, j = a == 1 ? k : (a == 0 ? p1 : p2), kk = a == 2 ? k : p2;
+        nv += (T)De[ende * Pe + k] * ue[(kk * Pe + j) * Pe + i];
+      }
+      const int i = a == 0 ? ende : p1, j = a == 1 ? ende : (a == 0 ? p1 : p2), kk = a == 2 ? ende : p2;
+      Te[t] = ue[(kk * Pe + j) * Pe + i];
+      Ne[t] = nv;
+    }
+    for (int t = threadIdx.x; t < Pn * Pn; t += blockDim.x) {
+      T tv = 0, nv = 0;
+      if (!A.self_only) {
+        const int p1 = t % Pn, p2 = t / Pn;
+        for (int k = 0; k < Pn; ++k) {
+          const int i = a == 0 ? k : p1, j = a == 1 ? k : (a == 0 ? p1 : p2), kk = a == 2 ? k : p2;
+          nv += (T)Dn[endn * Pn + k] * u[nbase + (kk * Pn + j) * Pn + i];
+        }
+        const int i = a == 0 ? endn : p1, j = a == 1 ? endn : (a == 0 ? p1 : p2), kk = a == 2 ? endn : p2;
+        tv = u[nbase + (kk * Pn + j) * Pn + i];
+      }
+      Tn[t] = tv;
+      Nn[t] = nv;
+    }
+    __syncthreads();
+    // interpolate the lower-degree side onto the Pf x Pf face nodes (both directions)
+    if (Ie) {
+      mix_apply<T>(Ie, Pf, Pe, Te, X0, true, false, Pe);
+      mix_apply<T>(Ie, Pf, Pe, X0, Te, false, false, Pf);
+      mix_apply<T>(Ie, Pf, Pe, Ne, X0, true, false, Pe);
+      mix_apply<T>(Ie, Pf, Pe, X0, Ne, false, false, Pf);
+    }
+    if (In) {
+      mix_apply<T>(In, Pf, Pn, Tn, X0, true, false, Pn);
+      mix_apply<T>(In, Pf, Pn, X0, Tn, false, false, Pf);
+      mix_apply<T>(In, Pf, Pn, Nn, X0, true, false, Pn);
+      mix_apply<T>(In, Pf, Pn, X0, Nn, false, false, Pf);
+    }
+    // jumps: J0 = u_e - u_n (in X0), J3 = s_a N_e - s'_a N_n (X3), and the
+    // tangential ones from D_f of s T_e - s' T_n along p1 (X1) and p2 (X2)
+    const int Pf2 = Pf * Pf;
+    for (int t = threadIdx.x; t < Pf2; t += blockDim.x) {
+      X0[t] = Te[t] - Tn[t];
+      X3[t] = (T)se[a] * Ne[t] - (T)sn[a] * Nn[t];
+      W1[t] = (T)se[t1] * Te[t] - (T)sn[t1] * Tn[t];
+      W2[t] = (T)se[t2] * Te[t] - (T)sn[t2] * Tn[t];
+    }
+    __syncthreads();
+    mix_apply<T>(Df, Pf, Pf, W1, X1, true, false, Pf);
+    mix_apply<T>(Df, Pf, Pf, W2, X2, false, false, Pf);
+    // norms: G0 = (MP x MP) J0; G_k = (MP x MP + MP x KP + KP x MP) J_k, k = 1, 2, 3
+    // first factor along p1: W0 = MP J0; for k: W_k = (MP + KP) J_k kept, and
+    // MP J_k (for the KP factor along p2) formed in turn
+    mix_apply<T>(MPf, Pf, Pf, X0, W0, true, false, Pf);
+    mix_apply<T>(MPf, Pf, Pf, W0, X0, false, false, Pf);  // X0 = G0
+    T *Jk[3] = {X1, X2, X3};
+    for (int k = 0; k < 3; ++k) {
+      mix_apply<T>(MPf, Pf, Pf, Jk[k], W0, true, false, Pf);   // MP J along p1
+      mix_apply<T>(KPf, Pf, Pf, Jk[k], W1, true, false, Pf);   // KP J along p1
+      for (int t = threadIdx.x; t < Pf2; t += blockDim.x) W1[t] += W0[t];
+      __syncthreads();
+      mix_apply<T>(MPf, Pf, Pf, W1, W2, false, false, Pf);     // MP (MP + KP) J
+      mix_apply<T>(KPf, Pf, Pf, W0, W3, false, false, Pf);     // KP MP J
+      for (int t = threadIdx.x; t < Pf2; t += blockDim.x) Jk[k][t] = W2[t] + W3[t];
+      __syncthreads();
+    }
+    // back to the own nodes: L = (I^T x I^T)[G0 + s_t1 D_f^T(p1) G1 + s_t2 D_f^T(p2) G2],
+    // M = s_a (I^T x I^T) G3
+    mix_apply<T>(Df, Pf, Pf, X1, W1, true, true, Pf);
+    mix_apply<T>(Df, Pf, Pf, X2, W2, false, true, Pf);
+    for (int t = threadIdx.x; t < Pf2; t += blockDim.x) {
+      X0[t] += (T)se[t1] * W1[t] + (T)se[t2] * W2[t];
+      X3[t] *= (T)se[a];
+    }
+    __syncthreads();
+    if (Ie) {
+      mix_apply<T>(Ie, Pf, Pe, X0, W0, true, true, Pf);   // Pf rows x Pe columns
+      mix_apply<T>(Ie, Pf, Pe, W0, X0, false, true, Pe);  // Pe x Pe
+      mix_apply<T>(Ie, Pf, Pe, X3, W0, true, true, Pf);
+      mix_apply<T>(Ie, Pf, Pe, W0, X3, false, true, Pe);
+    }
+    // gather: the face layer takes L, every node of a normal line D_e[end][k] M
+    for (int t = threadIdx.x; t < Pe3; t += blockDim.x) {
+      const int i = t % Pe, j = (t / Pe) % Pe, kk = t / (Pe * Pe);
+      const int n = a == 0 ? i : (a == 1 ? j : kk);
+      const int p1 = a == 0 ? j : i, p2 = a == 2 ? j : kk;
+      const int sp = p2 * Pe + p1;
+      T acc = (T)De[ende * Pe + n] * X3[sp];
+      if (n == ende) acc += X0[sp];
+      ye[t] += acc;
+    }
+    __syncthreads();
+  }
+  double part = 0.0;
+  for (int t = threadIdx.x; t < Pe3; t += blockDim.x) {
+    y[base + t] += ye[t];
+    if (MODE == MODE_PCG) part += (double)ye[t] * (double)ue[t];
+  }
+  if (MODE == MODE_PCG) {
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+      partial[(int64_t)e * A.n_rhs + r] += tot;
+    }
+  }
+}
+
+static size_t mix_smem(size_t real_bytes) {
+  const size_t PM = HPSE_MAX_W + 1;
+  return (2 * PM * PM * PM + 12 * PM * PM) * real_bytes;
+}
+
+static hpse_status setup_mixed(hpse_mesh *m) {
+  m->mixed_elems.clear();
+  for (int e = 0; e < m->n_elem; ++e)
+    for (int f = 0; f < 6; ++f)
+      if (m->fbc[6 * e + f] == 3) {
+        m->mixed_elems.push_back(e);
+        break;
+      }
+  // tables: per degree present D | MP | KP, per pair W < Wf the interpolation
+  std::vector<double> tab;
+  std::vector<int64_t> toff(HPSE_MAX_W + 1, -1), ioff((HPSE_MAX_W + 1) * 11, -1);
+  for (auto &kv : m->tabs) {
+    const hm::DegreeTables &t = kv.second;
+    toff[kv.first] = (int64_t)tab.size();
+    tab.insert(tab.end(), t.D.begin(), t.D.end());
+    tab.insert(tab.end(), t.MP.begin(), t.MP.end());
+    tab.insert(tab.end(), t.KP.begin(), t.KP.end());
+  }
+  for (auto &lo : m->tabs)
+    for (auto &hi : m->tabs)
+      if (lo.first < hi.first) {
+        const std::vector<double> I = hm::interp_matrix(lo.second.xp, hi.second.xp);
+        ioff[lo.first * 11 + hi.first] = (int64_t)tab.size();
+        tab.insert(tab.end(), I.begin(), I.end());
+      }
+  CK(upload(m->d_mix_tab, tab));
+  std::vector<const double *> ptr((HPSE_MAX_W + 1) + (HPSE_MAX_W + 1) * 11, nullptr);
+  const double *b = m->d_mix_tab.as<double>();
+  for (int w = 0; w <= HPSE_MAX_W; ++w)
+    if (toff[w] >= 0) ptr[w] = b + toff[w];
+  for (int k = 0; k < (HPSE_MAX_W + 1) * 11; ++k)
+    if (ioff[k] >= 0) ptr[HPSE_MAX_W + 1 + k] = b + ioff[k];
+  CK(upload(m->d_mix_ptr, ptr));
+  CK(upload(m->d_mixed_elems, m->mixed_elems));
+  CK(raise_smem((const void *)k_face_mixed<double, MODE_PLAIN>, m->device, mix_smem(8)));
+  CK(raise_smem((const void *)k_face_mixed<double, MODE_PCG>, m->device, mix_smem(8)));
+  CK(raise_smem((const void *)k_face_mixed<float, MODE_PLAIN>, m->device, mix_smem(4)));
+  CK(raise_smem((const void *)k_face_mixed<float, MODE_PCG>, m->device, mix_smem(4)));
+  return HPSE_OK;
+}
+
+static MixArgs mix_args(const hpse_mesh *m, int n_rhs) {
+  MixArgs A;
+  memset(&A, 0, sizeof(A));
+  A.n_items = (int)m->mixed_elems.size();
+  A.items = m->d_mixed_elems.as<int32_t>();
+  A.n_rhs = n_rhs;
+  A.ndof = m->ndof;
+  A.dof_off = m->d_dof_off.as<int64_t>();
+  A.nbr = m->d_nbr.as<int32_t>();
+  A.fbc = m->d_fbc.as<int32_t>();
+  A.elem_W = m->d_elem_W.as<int32_t>();
+  A.geo = m->d_geo64.as<double>();
+  A.tab = m->d_mix_ptr.as<const double *>();
+  A.itp = m->d_mix_ptr.as<const double *>() + (HPSE_MAX_W + 1);
+  return A;
+}
+
+template <typename T>
+static hpse_status launch_mixed(hpse_mesh *m, int mode, const T *u, T *y, double *partial, int n_rhs, int self_only,
+                                int only_W, cudaStream_t s) {
+  if (!m->has_mixed || m->mixed_elems.empty()) return HPSE_OK;
+  MixArgs A = mix_args(m, n_rhs);
+  A.self_only = self_only;
+  A.only_W = only_W;
+  const int grid = A.n_items * n_rhs;
+  if (mode == MODE_PCG)
+    k_face_mixed<T, MODE_PCG><<<grid, 128, mix_smem(sizeof(T)), s>>>(A, u, y, partial);
+  else
+    k_face_mixed<T, MODE_PLAIN><<<grid, 128, mix_smem(sizeof(T)), s>>>(A, u, y, partial);
+  CK(cudaGetLastError());
+  ++g_launches;
+  return HPSE_OK;
+}
+
 static hpse_status setup_edge(hpse_mesh *m) {
   const int E = m->n_elem, C = m->n_corner;
   const bool vtx = m->coord == HPSE_COORD_VERTEX;
@@ -1601,7 +1900,13 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
             std::fabs(m->hi[3 * e + b] - m->hi[3 * n + b]) > 1e-12 * s2)
           return HPSE_ERR_NONMATCHING_FACE;
       }
-      if (m->W[n] != m->W[e]) return HPSE_ERR_DEGREE;
+      if (m->W[n] != m->W[e]) {
+        // unequal degrees across the face: box meshes (the face terms on the
+        // (2 max(W, W') + 1)-point grid, in k_face_mixed)
+        if (nbhd) return HPSE_ERR_DEGREE;
+        m->fbc[6 * e + fi] = 3;
+        m->has_mixed = true;
+      }
     }
   // ---- offsets, groups, boundary faces -------------------------------------
   m->dof_off.assign(E, 0);
@@ -1737,11 +2042,15 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
   CK(upload(m->d_nbr, m->nbr));
   CK(upload(m->d_geo64, geo));
   CK(upload(m->d_geo32, geo32));
-  if (m->has_nr) {
+  if (m->has_nr || m->has_mixed) {
     std::vector<float> g32(m->fgam.begin(), m->fgam.end());
     CK(upload(m->d_fbc, m->fbc));
     CK(upload(m->d_fgam64, m->fgam));
     CK(upload(m->d_fgam32, g32));
+  }
+  if (m->has_mixed) {
+    hpse_status st = setup_mixed(m.get());
+    if (st != HPSE_OK) return st;
   }
   {
     // problem of every vector item (elements, then corner sets): the vector
@@ -2253,6 +2562,10 @@ extern "C" hpse_status hpse_setup_block_preconditioner(hpse_mesh *m) {
       k_bj_probe<<<g.n * c, 128, 0, s>>>(ba, j0, c, pu.as<double>());
       CK(cudaGetLastError());
       CK(ks.apply(m->apply_coef, MODE_PLAIN, &a, g.n * c, th, s));
+      {
+        hpse_status st = launch_mixed<double>(m, MODE_PLAIN, pu.as<double>(), py.as<double>(), nullptr, c, 1, g.W, s);
+        if (st != HPSE_OK) return st;
+      }
       k_bj_gather<<<g.n * c, 128, 0, s>>>(ba, j0, c, py.as<double>(), blk.as<double>());
       CK(cudaGetLastError());
       g_launches += 3;
@@ -3844,6 +4157,8 @@ static hpse_status conf_setup(hpse_mesh *m) {
 }
 
 extern "C" hpse_status hpse_conforming_correction(hpse_mesh *m, const double *u, double *p, void *stream) {
+  // the vertex / edge / face averages assume one degree across every face
+  if (m && m->has_mixed) return HPSE_ERR_DEGREE;
   if (!m || m->coord != HPSE_COORD_CARTESIAN) return HPSE_ERR_INVALID_ARG;  // box meshes only
   if (m->ndof == 0) return HPSE_OK;
   if (!u || !p) return HPSE_ERR_INVALID_ARG;

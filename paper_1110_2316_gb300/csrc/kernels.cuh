@@ -501,10 +501,14 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
   // per face: the scale of the normal term in the gather (s_a on interior
   // faces, +-s_a on Neumann / Robin faces, 0 on Dirichlet faces) and of the
   // face-layer term of a Robin face (gamma)
+  // (an interior face between unequal degrees, code 3, is left to k_face_mixed:
+  // zero scales and zero slots here)
   if (tid < 6) {
     const int nb = A.nbr[(int64_t)e * 6 + tid];
-    const int bc = (nb == -1 && A.fbc) ? A.fbc[(int64_t)e * 6 + tid] : 0;
-    fsc[tid] = nb != -1 ? geo_e[tid >> 1] : (bc ? ((tid & 1) ? geo_e[tid >> 1] : -geo_e[tid >> 1]) : (real)0);
+    const int bc = A.fbc ? A.fbc[(int64_t)e * 6 + tid] : 0;
+    fsc[tid] = bc == 3 ? (real)0
+                       : (nb != -1 ? geo_e[tid >> 1]
+                                   : (bc ? ((tid & 1) ? geo_e[tid >> 1] : -geo_e[tid >> 1]) : (real)0));
     fsc[6 + tid] = bc == 2 ? A.fgam[(int64_t)e * 6 + tid] : (real)0;
   }
   // 1: traces at every face point: F, J0 = [u] (u), J3 = [u_{x_a}] (0), the neighbour's trace Fn
@@ -522,8 +526,9 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
     for (int k = 0; k < P; ++k) Nv += c_tab.D[k] * su[o0 + k * os];
     if (side) Nv = -Nv;
     const int nb = A.nbr[(int64_t)e * 6 + f];
+    const int bc = A.fbc ? A.fbc[(int64_t)e * 6 + f] : 0;
     real Fn = 0, Nn = 0;
-    if (nb != -1 && A.self_only) {
+    if (bc == 3 || (nb != -1 && A.self_only)) {
       // diagonal block: the neighbour's trace is zero
     } else if (nbhd_coef(COEF) && nb < -1) {
       // corner set: through face 0 a polynomial along z (the p2 direction of
@@ -543,8 +548,10 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
       if (!side) Nn = -Nn;
     }
     FSLOT(f, sF)[sp] = Fv;
-    const int bc = (nb == -1 && A.fbc) ? A.fbc[(int64_t)e * 6 + f] : 0;
-    if (bc) {
+    if (bc == 3) {
+      FSLOT(f, sJ0)[sp] = (real)0;
+      FSLOT(f, sJ3)[sp] = (real)0;
+    } else if (bc) {
       // Neumann / Robin face (eq. 2.1): the outward normal derivative (+ gamma u)
       // in the slot of the normal-derivative jump, nothing in the others
       const real gam = bc == 2 ? A.fgam[(int64_t)e * 6 + f] : (real)0;
@@ -575,7 +582,7 @@ __device__ void face_phase(const ApplyArgs &A, int e, int r, const real *su, rea
     load_fold(FSLOT(f, sF) + ob, os, ev, od);
     pp_line<0>(ev, od, g);
     real *J = FSLOT(f, dir ? sJ2 : sJ1) + ob;
-    if (nb == -1 && A.fbc && A.fbc[(int64_t)e * 6 + f]) {
+    if (A.fbc && A.fbc[(int64_t)e * 6 + f]) {  // Neumann / Robin, or left to k_face_mixed
 #pragma unroll
       for (int m = 0; m < P; ++m) J[m * os] = (real)0;
     } else if (nb != -1) {

@@ -162,7 +162,31 @@ typedef struct {
  * constant (corner_W = 0) on zeta < zeta_1, code -2-c on face 4 (zeta = lo).
  * Data are sampled at the modified coordinates themselves (the caller
  * converts).  Same restrictions as HPSE_COORD_VERTEX. */
-enum { HPSE_COORD_CARTESIAN = 0, HPSE_COORD_EDGE = 1, HPSE_COORD_VERTEX = 2, HPSE_COORD_VERTEX_EDGE = 3 };
+/* HPSE_COORD_CURVED (eq. 4.2 on elements M_e(Q) with an analytic map that
+ * need not be affine; Section 2.3's regular region next to a neighbourhood):
+ * every element is the reference cube Q = (-1,1)^3 mapped by the caller's
+ * map (elem_lo, elem_hi are ignored and may be NULL); coef_kind must be
+ * HPSE_COEF_LAPLACE (L u = -Lap u in physical coordinates), every outer face
+ * Dirichlet (face_bc NULL or all 0), no corner sets.  Face f of e and face
+ * f^1 of its neighbour must share the face's parametrisation (the same
+ * tangential axes and directions); degrees may differ across faces.  The
+ * geometry comes from hpse_set_geometry (before hpse_set_data): the map's
+ * first and second derivatives at the volume points and its first
+ * derivatives at every face point, sampled by the caller at the reference
+ * coordinates of hpse_curved_points.  Volume term: the ten-term form of
+ * eq. (5.45) with C_ab = -(1 or 2) g^{ab}, C_a = -Lap lambda_a (g^{ab} =
+ * sum_i K_ai K_bi, K = (dx/dlambda)^{-1}, Lap lambda_a from the second
+ * derivatives) and weight w |J|.  Face terms on the reference face's
+ * (2 max(W, W') + 1)-point grid: the jumps of u and of the physical gradient
+ * (each side through its own K) in the L2 and H^{1/2} forms of eq. (5.49);
+ * Dirichlet faces: u - g in L2, its reference-tangential derivatives in
+ * H^{1/2} (eq. 2.18).  f is sampled at the physical volume points, g at the
+ * physical points of the Dirichlet faces (hpse_nface_points, in element,
+ * face order, (2W+1)^2 per face).  Not built for curved meshes
+ * (HPSE_ERR_INVALID_ARG): the H^1 norm, the adjoint entry points, the
+ * conforming correction. */
+enum { HPSE_COORD_CARTESIAN = 0, HPSE_COORD_EDGE = 1, HPSE_COORD_VERTEX = 2, HPSE_COORD_VERTEX_EDGE = 3,
+       HPSE_COORD_CURVED = 4 };
 
 /* Problem data (Section 4.2: F, g of eq. 4.2).  Host FP64 arrays, copied.
  *   f      [n_rhs][hpse_nquad()]        source at the volume points (required)
@@ -242,6 +266,26 @@ int32_t hpse_nrhs(const hpse_mesh *m);
  * Either pointer may be NULL. */
 hpse_status hpse_query_points(const hpse_mesh *m, double *vol_axes, double *face_norm);
 int64_t hpse_n_boundary_faces(const hpse_mesh *m);
+
+/* Curved meshes: the number of face points (every face of every element,
+ * (2 max(W, W') + 1)^2 each; -1 for other meshes) and the reference
+ * coordinates (lambda_1, lambda_2, lambda_3) of the volume points
+ * (vol_ref [nquad][3], element by element, x fastest) and of the face points
+ * (face_ref [n][3], element by element, faces 0..5, [t2][t1] with t1 < t2
+ * the two tangential axes).  Either pointer may be NULL. */
+int64_t hpse_curved_n_face_points(const hpse_mesh *m);
+hpse_status hpse_curved_points(const hpse_mesh *m, double *vol_ref, double *face_ref);
+
+/* Curved meshes: the map's derivatives at the points of hpse_curved_points,
+ * FP64, both host or both device memory: vol [nquad][27] = dx_k/dlambda_a
+ * (row-major [k][a]) then d^2 x_k / dlambda_a dlambda_b ([k][pair], pairs
+ * 00, 11, 22, 01, 02, 12); face [n][9] = dx_k/dlambda_a.  Computes the
+ * volume coefficients and the face points' K on the device.
+ * HPSE_ERR_INVALID_ARG for other meshes, missing arrays, or a point where
+ * det(dx/dlambda) <= 0 or a value is not finite (then no data until valid
+ * geometry and data are set).  Drops captured solver graphs and the data:
+ * hpse_set_data must follow.  Synchronous on `stream`. */
+hpse_status hpse_set_geometry(hpse_mesh *m, const double *vol, const double *face, void *stream);
 
 /* Upload data and build b = S^T M d in FP64 on the device (Section 5.3: the
  * right-hand side of the normal equations from the sampled data, eq. 2.1-2.2).

@@ -21,7 +21,7 @@ STATUS_NAMES = {
 FP64, FP32 = 0, 1
 COEF_LAPLACE, COEF_SCALAR, COEF_GENERAL = 0, 1, 2
 PRECOND_SEPARABLE, PRECOND_BLOCK = 0, 1
-COORD_CARTESIAN, COORD_EDGE, COORD_VERTEX, COORD_VERTEX_EDGE = 0, 1, 2, 3
+COORD_CARTESIAN, COORD_EDGE, COORD_VERTEX, COORD_VERTEX_EDGE, COORD_CURVED = 0, 1, 2, 3, 4
 
 
 class MeshDesc(C.Structure):
@@ -62,6 +62,9 @@ SIGNATURES = {
     "hpse_nface_points": (C.c_int64, [C.c_void_p]),
     "hpse_nrhs": (C.c_int32, [C.c_void_p]),
     "hpse_query_points": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hpse_curved_n_face_points": (C.c_int64, [C.c_void_p]),
+    "hpse_curved_points": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hpse_set_geometry": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "hpse_n_boundary_faces": (C.c_int64, [C.c_void_p]),
     "hpse_set_data": (C.c_int, [C.c_void_p, C.POINTER(Data), C.c_void_p]),
     "hpse_apply_operator": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),

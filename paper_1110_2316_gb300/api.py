@@ -67,6 +67,8 @@ class Mesh:
         d.coef_kind = int(coef_kind)
         d.elem_W, d.elem_problem, d.elem_lo, d.elem_hi, d.elem_nbr = (
             k.ctypes.data_as(C.c_void_p) for k in self._keep)
+        # curved elements (workloads.CurvedMeshDesc): reference cubes through the caller's maps
+        self.is_curved = hasattr(desc, "maps")
         # edge neighbourhood (workloads.EdgeMeshDesc): modified coordinates + corner sets
         self.is_edge = hasattr(desc, "corner_W")
         if self.is_edge:
@@ -79,7 +81,7 @@ class Mesh:
             d.corner_W = self._keep[5].ctypes.data_as(C.c_void_p)
             d.corner_problem = self._keep[6].ctypes.data_as(C.c_void_p)
         else:
-            d.coord = _lib.COORD_CARTESIAN
+            d.coord = _lib.COORD_CURVED if self.is_curved else _lib.COORD_CARTESIAN
             d.n_corner = 0
         bc = getattr(desc, "elem_bc", None)
         self.face_bc = None
@@ -128,6 +130,26 @@ class Mesh:
         fn = np.zeros(max(1, self.n_boundary_faces))
         check(self._lib.hpse_query_points(self._h, _ptr(ax), _ptr(fn)), "hpse_query_points")
         return ax, fn[: self.n_boundary_faces]
+
+    # -- curved elements -----------------------------------------------------
+    def curved_points(self):
+        """(vol_ref [nquad, 3], face_ref [n, 3]) reference coordinates of the
+        volume points and of every element face's points."""
+        nf = int(self._lib.hpse_curved_n_face_points(self._h))
+        vol = np.zeros((max(self.nquad, 1), 3))
+        face = np.zeros((max(nf, 1), 3))
+        check(self._lib.hpse_curved_points(self._h, _ptr(vol), _ptr(face)), "hpse_curved_points")
+        return vol[: self.nquad], face[:nf]
+
+    def set_geometry(self, vol, face, stream=None):
+        """The maps' derivatives at curved_points (host arrays or CUDA tensors):
+        vol [nquad, 27], face [n, 9]."""
+        if not isinstance(vol, np.ndarray) and getattr(vol, "is_cuda", False):
+            vol, face = vol.detach().double().contiguous(), face.detach().double().contiguous()
+        else:
+            vol, face = np.ascontiguousarray(vol, dtype=np.float64), np.ascontiguousarray(face, dtype=np.float64)
+        self.data_version += 1
+        check(self._lib.hpse_set_geometry(self._h, _ptr(vol), _ptr(face), _stream(stream)), "hpse_set_geometry")
 
     # -- data ---------------------------------------------------------------
     def set_data(self, f, a=None, grad_a=None, g=None, op=None, stream=None):
@@ -274,6 +296,72 @@ class Mesh:
 
 def kernel_launch_count(reset=False) -> int:
     return int(_lib.load().hpse_kernel_launch_count(1 if reset else 0))
+
+
+_PAIRS = ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))
+
+
+def curved_geometry_arrays(mesh: Mesh, maps):
+    """Sample the elements' maps at the library's reference points.
+
+    ``maps[e](l1, l2, l3) -> (x [3, ...], Dx [3, 3, ...], D2x [3, 3, 3, ...])``
+    (Dx[k, a] = d x_k / d lambda_a).  Returns (vol [nquad, 27], face [n, 9],
+    x_vol [nquad, 3], x_face [n, 3]) for Mesh.set_geometry and the data."""
+    vref, fref = mesh.curved_points()
+    Ws = [int(w) for w in mesh.elem_W]
+    nbr = mesh._keep[4]
+    vol = np.zeros((len(vref), 27))
+    xv = np.zeros((len(vref), 3))
+    o = 0
+    for e, W in enumerate(Ws):
+        n = (2 * W + 1) ** 3
+        r = vref[o:o + n]
+        x, Dx, D2x = maps[e](r[:, 0], r[:, 1], r[:, 2])
+        xv[o:o + n] = np.asarray(x).T
+        vol[o:o + n, :9] = np.asarray(Dx).reshape(9, n).T
+        for k in range(3):
+            for p, (a, b) in enumerate(_PAIRS):
+                vol[o:o + n, 9 + 6 * k + p] = D2x[k, a, b]
+        o += n
+    face = np.zeros((len(fref), 9))
+    xf = np.zeros((len(fref), 3))
+    o = 0
+    for e, W in enumerate(Ws):
+        for f in range(6):
+            nb = int(nbr[e, f])
+            Qf = 2 * (max(W, Ws[nb]) if nb >= 0 else W) + 1
+            n = Qf * Qf
+            r = fref[o:o + n]
+            x, Dx, _ = maps[e](r[:, 0], r[:, 1], r[:, 2])
+            xf[o:o + n] = np.asarray(x).T
+            face[o:o + n] = np.asarray(Dx).reshape(9, n).T
+            o += n
+    return vol, face, xv, xf
+
+
+def curved_data_arrays(mesh: Mesh, x_vol, x_face, f, g):
+    """Data of a curved mesh: f[r](x, y, z), g[r](x, y, z) pointwise functions
+    of physical coordinates (one per rhs), sampled at the volume points and at
+    the Dirichlet faces' points (element, face order)."""
+    Ws = [int(w) for w in mesh.elem_W]
+    nbr = mesh._keep[4]
+    R = mesh.n_rhs
+    F = np.stack([np.asarray(f[r](x_vol[:, 0], x_vol[:, 1], x_vol[:, 2]), dtype=np.float64) * np.ones(len(x_vol))
+                  for r in range(R)])
+    rows = []
+    o = 0
+    for e, W in enumerate(Ws):
+        for fi in range(6):
+            nb = int(nbr[e, fi])
+            Qf = 2 * (max(W, Ws[nb]) if nb >= 0 else W) + 1
+            if nb == -1:
+                rows.append(np.arange(o, o + Qf * Qf))
+            o += Qf * Qf
+    idx = np.concatenate(rows) if rows else np.zeros(0, dtype=np.int64)
+    xb = x_face[idx]
+    G = np.stack([np.asarray(g[r](xb[:, 0], xb[:, 1], xb[:, 2]), dtype=np.float64) * np.ones(len(xb))
+                  for r in range(R)]) if len(idx) else None
+    return dict(f=F, g=G)
 
 
 def problem_data_arrays(mesh: Mesh, problem):

@@ -196,6 +196,13 @@ struct hpse_mesh {
   bool has_mixed = false;
   std::vector<int32_t> mixed_elems;
   DevBuf d_mixed_elems, d_mix_tab, d_mix_ptr;
+  // curved elements (HPSE_COORD_CURVED): per element-face grid size and first
+  // point, the Dirichlet data offsets, the 1-D tables of k_face_curved, the
+  // face-point K (FP64, FP32) and w |J| of the volume points (negated)
+  bool curved = false, has_geometry = false;
+  std::vector<int32_t> cf_q;
+  std::vector<int64_t> cf_off, bf_off;
+  DevBuf d_cf_q, d_cf_off, d_bf_off, d_cur_tab, d_cur_ptr, d_cK64, d_cK32, d_cwja;
   std::vector<int64_t> dof_off, coef_off;
   int64_t ndof = 0, nquad = 0;
   std::vector<int> bface_elem, bface_fi;   // boundary faces
@@ -310,6 +317,7 @@ struct ElemVecArgs {
 };
 
 #include "block_precond.cuh"
+#include "curved.cuh"
 #include "bj_tc.cuh"
 #include "edge.cuh"
 static_assert(BJ_NVAR == 9, "bj_ms holds one time per tile variant");
@@ -943,7 +951,7 @@ static ApplyArgsT<T> apply_args(const hpse_mesh *m, const Group &g, const T *u, 
     a.cslot = m->d_cslot.as<int32_t>();
     a.cscr = m->n_corner ? (d ? (T *)m->d_cscr64.p : (T *)m->d_cscr32.p) : nullptr;
   }
-  if (m->has_nr || m->has_mixed) {
+  if (m->has_nr || m->has_mixed || m->curved) {
     a.fbc = m->d_fbc.as<int32_t>();
     a.fgam = (sizeof(T) == 8) ? (const T *)m->d_fgam64.p : (const T *)m->d_fgam32.p;
   }
@@ -1009,6 +1017,9 @@ static cudaStream_t group_stream(hpse_mesh *m, size_t gi, cudaStream_t s) {
 template <typename T>
 static hpse_status launch_mixed(hpse_mesh *m, int mode, const T *u, T *y, double *partial, int n_rhs, int self_only,
                                 int only_W, cudaStream_t s);
+template <typename T>
+static hpse_status launch_curved(hpse_mesh *m, int mode, const T *u, T *y, double *partial, int n_rhs,
+                                 int self_only, int only_W, cudaStream_t s);
 
 template <typename T>
 static hpse_status launch_apply_all(hpse_mesh *m, int mode, ApplyArgsT<T> base_args, cudaStream_t s) {
@@ -1031,6 +1042,12 @@ static hpse_status launch_apply_all(hpse_mesh *m, int mode, ApplyArgsT<T> base_a
     const T *uu = mode == MODE_PCG ? base_args.pnew : base_args.u;
     hpse_status st = launch_mixed<T>(m, mode, uu, base_args.y, base_args.partial, base_args.n_rhs,
                                      base_args.self_only, 0, s);
+    if (st != HPSE_OK) return st;
+  }
+  if (m->curved && mode != MODE_TRANSPOSE && !base_args.skip_faces) {
+    const T *uu = mode == MODE_PCG ? base_args.pnew : base_args.u;
+    hpse_status st = launch_curved<T>(m, mode, uu, base_args.y, base_args.partial, base_args.n_rhs,
+                                      base_args.self_only, 0, s);
     if (st != HPSE_OK) return st;
   }
   if (m->n_corner > 0 && !base_args.self_only) {
@@ -1501,6 +1518,116 @@ static hpse_status launch_mixed(hpse_mesh *m, int mode, const T *u, T *y, double
   return HPSE_OK;
 }
 
+// curved elements: the element-face grids (Qf = 2 max(W, W') + 1 on interior
+// faces, 2 W + 1 on Dirichlet faces), the Dirichlet data offsets (the
+// boundary faces in element, face order: those of hpse_nface_points), the
+// 1-D tables of k_face_curved
+static hpse_status setup_curved(hpse_mesh *m) {
+  const int E = m->n_elem;
+  m->cf_q.assign(6 * (size_t)E, 0);
+  m->cf_off.assign(6 * (size_t)E + 1, 0);
+  m->bf_off.assign(6 * (size_t)E, -1);
+  for (int e = 0; e < E; ++e)
+    for (int f = 0; f < 6; ++f) {
+      const int n = m->nbr[6 * e + f];
+      const int Wf = n >= 0 ? std::max(m->W[e], m->W[n]) : m->W[e];
+      m->cf_q[6 * e + f] = 2 * Wf + 1;
+      m->cf_off[6 * e + f + 1] = m->cf_off[6 * e + f] + (int64_t)(2 * Wf + 1) * (2 * Wf + 1);
+    }
+  for (size_t i = 0; i < m->bface_elem.size(); ++i) m->bf_off[6 * m->bface_elem[i] + m->bface_fi[i]] = m->bface_off[i];
+  // tables: D per degree; B0 | B1 (Qf x P) per (degree, grid); w | K1 | DQ per grid
+  std::vector<double> tab;
+  std::map<int, int64_t> doff, qoff;
+  std::map<std::pair<int, int>, int64_t> boff;
+  for (auto &kv : m->tabs) {
+    doff[kv.first] = (int64_t)tab.size();
+    tab.insert(tab.end(), kv.second.D.begin(), kv.second.D.end());
+  }
+  for (int e = 0; e < E; ++e)
+    for (int f = 0; f < 6; ++f) {
+      const int Qf = m->cf_q[6 * e + f];
+      if (!qoff.count(Qf)) {
+        std::vector<double> x, w;
+        hm::gll_rule(Qf, x, w);
+        const std::vector<double> K1 = hm::half_norm_matrix(x, w), DQ = hm::diff_matrix(x);
+        qoff[Qf] = (int64_t)tab.size();
+        tab.insert(tab.end(), w.begin(), w.end());
+        tab.insert(tab.end(), K1.begin(), K1.end());
+        tab.insert(tab.end(), DQ.begin(), DQ.end());
+      }
+      // every degree meeting this grid: the element's and its neighbour's
+      const int n = m->nbr[6 * e + f];
+      for (int W : {m->W[e], n >= 0 ? m->W[n] : m->W[e]}) {
+        if (boff.count({W, Qf})) continue;
+        std::vector<double> x, w;
+        hm::gll_rule(Qf, x, w);
+        const hm::DegreeTables &t = m->tabs.at(W);
+        const std::vector<double> B0 = hm::interp_matrix(t.xp, x);
+        const std::vector<double> B1 = hm::matmul(B0, t.D, Qf, W + 1, W + 1);
+        boff[{W, Qf}] = (int64_t)tab.size();
+        tab.insert(tab.end(), B0.begin(), B0.end());
+        tab.insert(tab.end(), B1.begin(), B1.end());
+      }
+    }
+  CK(upload(m->d_cur_tab, tab));
+  const double *b = m->d_cur_tab.as<double>();
+  // pointer table: [W] D, then [W * 22 + Qf] B0 | B1, then [Qf] w | K1 | DQ
+  std::vector<const double *> ptr((HPSE_MAX_W + 1) + (HPSE_MAX_W + 1) * 22 + 22, nullptr);
+  for (auto &kv : doff) ptr[kv.first] = b + kv.second;
+  for (auto &kv : boff) ptr[(HPSE_MAX_W + 1) + kv.first.first * 22 + kv.first.second] = b + kv.second;
+  for (auto &kv : qoff) ptr[(HPSE_MAX_W + 1) + (HPSE_MAX_W + 1) * 22 + kv.first] = b + kv.second;
+  CK(upload(m->d_cur_ptr, ptr));
+  CK(upload(m->d_cf_q, m->cf_q));
+  CK(upload(m->d_cf_off, m->cf_off));
+  CK(upload(m->d_bf_off, m->bf_off));
+  const size_t sm64 = curved::face_smem(8), sm32 = curved::face_smem(4);
+  CK(raise_smem((const void *)curved::k_face_curved<double, 0, false>, m->device, sm64));
+  CK(raise_smem((const void *)curved::k_face_curved<double, 1, false>, m->device, sm64));
+  CK(raise_smem((const void *)curved::k_face_curved<double, 0, true>, m->device, sm64));
+  CK(raise_smem((const void *)curved::k_face_curved<float, 0, false>, m->device, sm32));
+  CK(raise_smem((const void *)curved::k_face_curved<float, 1, false>, m->device, sm32));
+  return HPSE_OK;
+}
+
+static curved::FaceArgs curved_args(const hpse_mesh *m, int n_rhs) {
+  curved::FaceArgs A;
+  memset(&A, 0, sizeof(A));
+  A.n_rhs = n_rhs;
+  A.ndof = m->ndof;
+  A.dof_off = m->d_dof_off.as<int64_t>();
+  A.nbr = m->d_nbr.as<int32_t>();
+  A.elem_W = m->d_elem_W.as<int32_t>();
+  A.cf_off = m->d_cf_off.as<int64_t>();
+  A.cf_q = m->d_cf_q.as<int32_t>();
+  const double *const *p = m->d_cur_ptr.as<const double *>();
+  A.dtab = p;
+  A.btab = p + (HPSE_MAX_W + 1);
+  A.qtab = p + (HPSE_MAX_W + 1) + (HPSE_MAX_W + 1) * 22;
+  A.bf_off = m->d_bf_off.as<int64_t>();
+  A.nface_pts = m->nface_pts;
+  return A;
+}
+
+// the face terms of curved elements (y +=; PCG mode: partial +=)
+template <typename T>
+static hpse_status launch_curved(hpse_mesh *m, int mode, const T *u, T *y, double *partial, int n_rhs,
+                                 int self_only, int only_W, cudaStream_t s) {
+  if (!m->curved || m->n_elem == 0) return HPSE_OK;
+  curved::FaceArgs A = curved_args(m, n_rhs);
+  A.self_only = self_only;
+  A.only_W = only_W;
+  const T *K = sizeof(T) == 8 ? (const T *)m->d_cK64.p : (const T *)m->d_cK32.p;
+  const int grid = m->n_elem * n_rhs;
+  const size_t sm = curved::face_smem(sizeof(T));
+  if (mode == MODE_PCG)
+    curved::k_face_curved<T, 1, false><<<grid, 128, sm, s>>>(A, u, K, nullptr, y, partial);
+  else
+    curved::k_face_curved<T, 0, false><<<grid, 128, sm, s>>>(A, u, K, nullptr, y, partial);
+  CK(cudaGetLastError());
+  ++g_launches;
+  return HPSE_OK;
+}
+
 static hpse_status setup_edge(hpse_mesh *m) {
   const int E = m->n_elem, C = m->n_corner;
   const bool vtx = m->coord == HPSE_COORD_VERTEX;
@@ -1779,7 +1906,8 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
   init_registry();
   if (d->coef_kind != HPSE_COEF_LAPLACE && d->coef_kind != HPSE_COEF_SCALAR && d->coef_kind != HPSE_COEF_GENERAL)
     return HPSE_ERR_INVALID_ARG;
-  if (d->n_elem > 0 && (!d->elem_W || !d->elem_problem || !d->elem_lo || !d->elem_hi || !d->elem_nbr))
+  if (d->n_elem > 0 && (!d->elem_W || !d->elem_problem || !d->elem_nbr ||
+                        (d->coord != HPSE_COORD_CURVED && (!d->elem_lo || !d->elem_hi))))
     return HPSE_ERR_INVALID_ARG;
   const int E = d->n_elem;
   if ((int64_t)E * d->n_rhs > 2147483647LL) return HPSE_ERR_INVALID_ARG;
@@ -1791,9 +1919,17 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
   m->coef_kind = d->coef_kind;
   m->coord = d->coord;
   if (m->coord != HPSE_COORD_CARTESIAN && m->coord != HPSE_COORD_EDGE && m->coord != HPSE_COORD_VERTEX &&
-      m->coord != HPSE_COORD_VERTEX_EDGE)
+      m->coord != HPSE_COORD_VERTEX_EDGE && m->coord != HPSE_COORD_CURVED)
     return HPSE_ERR_INVALID_ARG;
-  const bool nbhd = m->coord != HPSE_COORD_CARTESIAN;
+  m->curved = m->coord == HPSE_COORD_CURVED;
+  if (m->curved) {
+    // -Lap u through the maps, Dirichlet faces, no corner sets
+    if (d->coef_kind != HPSE_COEF_LAPLACE || d->n_corner != 0) return HPSE_ERR_INVALID_ARG;
+    if (d->face_bc)
+      for (int i = 0; i < 6 * d->n_elem; ++i)
+        if (d->face_bc[i] != 0) return HPSE_ERR_INVALID_ARG;
+  }
+  const bool nbhd = m->coord != HPSE_COORD_CARTESIAN && !m->curved;
   // faces of layer 1 towards the corner sets: 0 (a polynomial along z: edge,
   // vertex-edge) and 4 (a constant: vertex, vertex-edge)
   const bool face0_ok = m->coord == HPSE_COORD_EDGE || m->coord == HPSE_COORD_VERTEX_EDGE;
@@ -1806,7 +1942,8 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
     m->cW.assign(d->corner_W, d->corner_W + d->n_corner);
     m->cprob.assign(d->corner_problem, d->corner_problem + d->n_corner);
   }
-  m->apply_coef = m->coord == HPSE_COORD_EDGE            ? hpse::COEF_EDGE
+  m->apply_coef = m->curved                               ? hpse::COEF_GENERAL
+                 : m->coord == HPSE_COORD_EDGE            ? hpse::COEF_EDGE
                  : m->coord == HPSE_COORD_VERTEX        ? hpse::COEF_VERTEX
                  : m->coord == HPSE_COORD_VERTEX_EDGE ? hpse::COEF_VERTEX_EDGE
                  : d->coef_kind == HPSE_COEF_GENERAL  ? hpse::COEF_GENERAL
@@ -1814,8 +1951,14 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
   m->W.assign(d->elem_W, d->elem_W + E);
   m->prob.assign(d->elem_problem, d->elem_problem + E);
   m->nbr.assign(d->elem_nbr, d->elem_nbr + 6 * (size_t)E);
-  m->lo.assign(d->elem_lo, d->elem_lo + 3 * (size_t)E);
-  m->hi.assign(d->elem_hi, d->elem_hi + 3 * (size_t)E);
+  if (m->curved) {
+    // the reference cube: unit scales for everything the box path reads
+    m->lo.assign(3 * (size_t)E, -1.0);
+    m->hi.assign(3 * (size_t)E, 1.0);
+  } else {
+    m->lo.assign(d->elem_lo, d->elem_lo + 3 * (size_t)E);
+    m->hi.assign(d->elem_hi, d->elem_hi + 3 * (size_t)E);
+  }
   // ---- validation (Section 2.3: one-to-one matching faces) -----------------
   for (int e = 0; e < E; ++e) {
     if (m->W[e] < 1 || m->W[e] > HPSE_MAX_W) return HPSE_ERR_DEGREE;
@@ -1888,6 +2031,7 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
       if (n < 0) continue;
       if (m->nbr[6 * n + (fi ^ 1)] != e) return HPSE_ERR_NONMATCHING_FACE;
       if (m->prob[n] != m->prob[e]) return HPSE_ERR_INVALID_ARG;
+      if (m->curved) continue;  // the maps share the face's parametrisation (the caller's mesh)
       const int a = fi >> 1, side = fi & 1;
       const double xe = side ? m->hi[3 * e + a] : m->lo[3 * e + a];
       const double xn = side ? m->lo[3 * n + a] : m->hi[3 * n + a];
@@ -1908,6 +2052,10 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
         m->has_mixed = true;
       }
     }
+  if (m->curved) {
+    // every face of a curved element is k_face_curved's (code 3: k_apply_gen leaves it)
+    for (size_t i = 0; i < m->fbc.size(); ++i) m->fbc[i] = 3;
+  }
   // ---- offsets, groups, boundary faces -------------------------------------
   m->dof_off.assign(E, 0);
   m->coef_off.assign(E, 0);
@@ -2042,7 +2190,7 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
   CK(upload(m->d_nbr, m->nbr));
   CK(upload(m->d_geo64, geo));
   CK(upload(m->d_geo32, geo32));
-  if (m->has_nr || m->has_mixed) {
+  if (m->has_nr || m->has_mixed || m->curved) {
     std::vector<float> g32(m->fgam.begin(), m->fgam.end());
     CK(upload(m->d_fbc, m->fbc));
     CK(upload(m->d_fgam64, m->fgam));
@@ -2050,6 +2198,10 @@ extern "C" hpse_status hpse_setup_mesh(const hpse_mesh_desc *d, int device, hpse
   }
   if (m->has_mixed) {
     hpse_status st = setup_mixed(m.get());
+    if (st != HPSE_OK) return st;
+  }
+  if (m->curved) {
+    hpse_status st = setup_curved(m.get());
     if (st != HPSE_OK) return st;
   }
   {
@@ -2077,6 +2229,108 @@ extern "C" int64_t hpse_nquad(const hpse_mesh *m) { return m ? m->nquad : -1; }
 extern "C" int64_t hpse_nface_points(const hpse_mesh *m) { return m ? m->nface_pts : -1; }
 extern "C" int32_t hpse_nrhs(const hpse_mesh *m) { return m ? m->n_rhs : -1; }
 extern "C" int64_t hpse_n_boundary_faces(const hpse_mesh *m) { return m ? (int64_t)m->bface_elem.size() : -1; }
+
+static int pointer_space(const void *p);
+
+extern "C" int64_t hpse_curved_n_face_points(const hpse_mesh *m) {
+  return (m && m->curved) ? m->cf_off.back() : -1;
+}
+
+extern "C" hpse_status hpse_curved_points(const hpse_mesh *m, double *vol_ref, double *face_ref) {
+  if (!m || !m->curved) return HPSE_ERR_INVALID_ARG;
+  if (vol_ref) {
+    for (int e = 0; e < m->n_elem; ++e) {
+      const hm::DegreeTables &t = m->tabs.at(m->W[e]);
+      const int Q = t.Q;
+      double *o = vol_ref + 3 * m->coef_off[e];
+      for (int c = 0; c < Q; ++c)
+        for (int b = 0; b < Q; ++b)
+          for (int a = 0; a < Q; ++a, o += 3) {
+            o[0] = t.xq[a];
+            o[1] = t.xq[b];
+            o[2] = t.xq[c];
+          }
+    }
+  }
+  if (face_ref) {
+    for (int e = 0; e < m->n_elem; ++e)
+      for (int f = 0; f < 6; ++f) {
+        const int Qf = m->cf_q[6 * e + f], a = f >> 1;
+        const int t1 = a == 0 ? 1 : 0, t2 = a == 2 ? 1 : 2;
+        std::vector<double> x, w;
+        hm::gll_rule(Qf, x, w);
+        double *o = face_ref + 3 * m->cf_off[6 * e + f];
+        for (int p2 = 0; p2 < Qf; ++p2)
+          for (int p1 = 0; p1 < Qf; ++p1, o += 3) {
+            o[a] = (f & 1) ? 1.0 : -1.0;
+            o[t1] = x[p1];
+            o[t2] = x[p2];
+          }
+      }
+  }
+  return HPSE_OK;
+}
+
+extern "C" hpse_status hpse_set_geometry(hpse_mesh *m, const double *vol, const double *face, void *stream) {
+  if (!m || !m->curved) return HPSE_ERR_INVALID_ARG;
+  const int64_t nq = m->nquad, nfp = m->cf_off.back();
+  if ((nq > 0 && !vol) || (nfp > 0 && !face)) return HPSE_ERR_INVALID_ARG;
+  const int sv = nq > 0 ? pointer_space(vol) : -2, sf = nfp > 0 ? pointer_space(face) : -2;
+  if (sv == -1 || sf == -1 || (sv >= 0 && sf >= 0 && sv != sf)) return HPSE_ERR_INVALID_ARG;
+  CK(cudaSetDevice(m->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (m->work) {
+    CK(cudaDeviceSynchronize());
+    for (auto &g : m->work->graphs) cudaGraphExecDestroy(g.second);
+    m->work->graphs.clear();
+    m->work->graph_launches.clear();
+  }
+  m->has_geometry = false;
+  m->has_data = false;
+  DevBuf dv, df, dbad;
+  const double *vp = vol, *fp = face;
+  if (sv == 0) {
+    CK(dv.alloc(27 * (size_t)nq * sizeof(double)));
+    CK(cudaMemcpyAsync(dv.p, vol, 27 * (size_t)nq * sizeof(double), cudaMemcpyHostToDevice, s));
+    vp = dv.as<double>();
+  }
+  if (sf == 0) {
+    CK(df.alloc(9 * (size_t)nfp * sizeof(double)));
+    CK(cudaMemcpyAsync(df.p, face, 9 * (size_t)nfp * sizeof(double), cudaMemcpyHostToDevice, s));
+    fp = df.as<double>();
+  }
+  {
+    std::vector<const double *> tp(HPSE_MAX_W + 1, nullptr);
+    for (auto &kv : m->d_qtab) tp[kv.first] = kv.second.as<double>();
+    CK(upload_reuse(m->d_tabs_ptr, tp));
+  }
+  CK(dbad.alloc(sizeof(int32_t)));
+  CK(cudaMemsetAsync(dbad.p, 0, sizeof(int32_t), s));
+  if (!m->d_coef64.p || m->d_coef64.bytes != 12 * (size_t)std::max<int64_t>(nq, 1) * sizeof(double))
+    CK(m->d_coef64.alloc(12 * (size_t)std::max<int64_t>(nq, 1) * sizeof(double)));
+  if (!m->d_coef32.p || m->d_coef32.bytes != 12 * (size_t)std::max<int64_t>(nq, 1) * sizeof(float))
+    CK(m->d_coef32.alloc(12 * (size_t)std::max<int64_t>(nq, 1) * sizeof(float)));
+  if (!m->d_cwja.p) CK(m->d_cwja.alloc((size_t)std::max<int64_t>(nq, 1) * sizeof(double)));
+  if (!m->d_cK64.p) CK(m->d_cK64.alloc(9 * (size_t)std::max<int64_t>(nfp, 1) * sizeof(double)));
+  if (!m->d_cK32.p) CK(m->d_cK32.alloc(9 * (size_t)std::max<int64_t>(nfp, 1) * sizeof(float)));
+  if (m->n_elem > 0) {
+    curved::k_geom_vol<<<m->n_elem, 256, 0, s>>>(nq, m->d_elem_W.as<int32_t>(), m->d_coef_off.as<int64_t>(),
+                                                 m->d_tabs_ptr.as<const double *>(), vp, m->d_coef64.as<double>(),
+                                                 m->d_coef32.as<float>(), m->d_cwja.as<double>(),
+                                                 dbad.as<int32_t>());
+    CK(cudaGetLastError());
+    curved::k_geom_face<<<256, 256, 0, s>>>(nfp, fp, m->d_cK64.as<double>(), m->d_cK32.as<float>(),
+                                            dbad.as<int32_t>());
+    CK(cudaGetLastError());
+    g_launches += 2;
+  }
+  int32_t h_bad = 0;
+  CK(cudaMemcpyAsync(&h_bad, dbad.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h_bad) return HPSE_ERR_INVALID_ARG;
+  m->has_geometry = true;
+  return HPSE_OK;
+}
 
 extern "C" hpse_status hpse_query_points(const hpse_mesh *m, double *vol_axes, double *face_norm) {
   if (!m) return HPSE_ERR_INVALID_ARG;
@@ -2190,6 +2444,8 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data, void *
   if (m->coef_kind == HPSE_COEF_SCALAR && (!data->a || !data->grad_a)) return HPSE_ERR_INVALID_ARG;
   const bool gen = m->coef_kind == HPSE_COEF_GENERAL;
   if (gen && !data->op && m->nquad > 0) return HPSE_ERR_INVALID_ARG;
+  // curved elements: the operator's coefficients come from hpse_set_geometry
+  if (m->curved && !m->has_geometry) return HPSE_ERR_NO_DATA;
   CK(cudaSetDevice(m->device));
   // host or device data: every given pointer in the same space
   int space = -2;
@@ -2365,7 +2621,8 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data, void *
   if (nq > 0 && m->n_elem > 0) {
     DevBuf drho;
     CK(drho.alloc((size_t)R * nq * sizeof(double)));
-    k_rho_b<<<1024, 256, 0, s>>>((int64_t)R * nq, dwja.as<double>(), m->d_f.as<double>(), nq, drho.as<double>());
+    k_rho_b<<<1024, 256, 0, s>>>((int64_t)R * nq, m->curved ? m->d_cwja.as<double>() : dwja.as<double>(),
+                                 m->d_f.as<double>(), nq, drho.as<double>());
     CK(cudaGetLastError());
     ++g_launches;
     ApplyArgsT<double> a = apply_args<double>(m, m->groups[0], nullptr, m->d_b.as<double>());
@@ -2375,8 +2632,18 @@ extern "C" hpse_status hpse_set_data(hpse_mesh *m, const hpse_data *data, void *
     if (st != HPSE_OK) return st;
     CK(cudaStreamSynchronize(s));
   }
-  // Dirichlet data part of b
-  if (data->g && m->nface_pts > 0) {
+  // Dirichlet data part of b (curved elements: on each face's grid, by k_face_curved)
+  if (m->curved && data->g && m->nface_pts > 0 && m->n_elem > 0) {
+    DevBuf dg;
+    CK(dg.alloc((size_t)R * m->nface_pts * sizeof(double)));
+    CK(cudaMemcpyAsync(dg.p, data->g, (size_t)R * m->nface_pts * sizeof(double), kin, s));
+    curved::FaceArgs A = curved_args(m, R);
+    curved::k_face_curved<double, 0, true><<<m->n_elem * R, 128, curved::face_smem(8), s>>>(
+        A, nullptr, m->d_cK64.as<double>(), dg.as<double>(), m->d_b.as<double>(), nullptr);
+    CK(cudaGetLastError());
+    ++g_launches;
+    CK(cudaStreamSynchronize(s));
+  } else if (data->g && m->nface_pts > 0) {
     std::vector<int> felem_ptr(1, 0), felems, ffi;
     std::vector<int64_t> foff;
     for (size_t i = 0; i < m->bface_elem.size(); ++i) {
@@ -2564,6 +2831,8 @@ extern "C" hpse_status hpse_setup_block_preconditioner(hpse_mesh *m) {
       CK(ks.apply(m->apply_coef, MODE_PLAIN, &a, g.n * c, th, s));
       {
         hpse_status st = launch_mixed<double>(m, MODE_PLAIN, pu.as<double>(), py.as<double>(), nullptr, c, 1, g.W, s);
+        if (st != HPSE_OK) return st;
+        st = launch_curved<double>(m, MODE_PLAIN, pu.as<double>(), py.as<double>(), nullptr, c, 1, g.W, s);
         if (st != HPSE_OK) return st;
       }
       k_bj_gather<<<g.n * c, 128, 0, s>>>(ba, j0, c, py.as<double>(), blk.as<double>());
@@ -3281,8 +3550,10 @@ extern "C" hpse_status hpse_pcg_solve(hpse_mesh *m, const hpse_solve_opts *o, do
 
 extern "C" hpse_status hpse_h1_error(hpse_mesh *m, const double *u, const double *ref, const double *vq,
                                      const double *gq, double *out, void *stream) {
-  // neighbourhood meshes: the difference of two discrete solutions only
+  // neighbourhood meshes: the difference of two discrete solutions only;
+  // curved elements: not built (their norm needs K and |J| per point)
   if (m && m->coord != HPSE_COORD_CARTESIAN && !ref) return HPSE_ERR_INVALID_ARG;
+  if (m && m->curved) return HPSE_ERR_INVALID_ARG;
   if (!m || !out) return HPSE_ERR_INVALID_ARG;
   if (m->ndof == 0) {
     for (int r = 0; r < m->n_rhs; ++r) out[2 * r] = out[2 * r + 1] = 0.0;

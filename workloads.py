@@ -1005,6 +1005,32 @@ def affine_box_map(lo, hi):
     return m
 
 
+@dataclass
+class CurvedMeshDesc:
+    """Elements as reference cubes through maps (x, Dx, D2x) = maps[e](l1, l2, l3);
+    face f of e and face f^1 of elem_nbr[e, f] share the face's parametrisation."""
+    maps: list
+    elem_W: np.ndarray
+    elem_nbr: np.ndarray
+    n_problem: int = 1
+
+    @property
+    def n_elem(self) -> int:
+        return len(self.maps)
+
+    @property
+    def elem_problem(self) -> np.ndarray:
+        return np.zeros(self.n_elem, dtype=np.int32)
+
+    @property
+    def elem_lo(self) -> np.ndarray:
+        return -np.ones((self.n_elem, 3))
+
+    @property
+    def elem_hi(self) -> np.ndarray:
+        return np.ones((self.n_elem, 3))
+
+
 def curved_mesh_of_boxes(desc):
     """The affine maps of a box mesh, its degrees and neighbours."""
     maps = [affine_box_map(desc.elem_lo[e], desc.elem_hi[e]) for e in range(desc.n_elem)]

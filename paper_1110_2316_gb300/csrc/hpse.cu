@@ -248,6 +248,11 @@ struct hpse_mesh {
   DevBuf d_bj_off;            // int64 per element: offset of its packed block
   DevBuf d_bj64, d_bj32;      // X = L^{-1} per element, packed lower triangle
   DevBuf bj_t64, bj_t32;      // scratch vector X r of the preconditioner
+  // degree groups whose FP32 factor products lose more than 1 % against the
+  // FP64 ones (measured at set-up): their FP32 solves use the FP64 factor
+  // through two conversions (bj_r64, bj_z64 scratch)
+  bool bj_poor32[HPSE_MAX_W + 1] = {};
+  DevBuf bj_r64, bj_z64;
   int bj_var[HPSE_MAX_W + 1][2] = {};  // tile variant of the products per degree and precision (autotuned)
   float bj_ms[HPSE_MAX_W + 1][2][9] = {};  // [BJ_NVAR]  // measured time per variant (ms; 0: not a candidate)
   DevBuf d_bjt, d_bjt_off;    // tensor-core form: FP32 tiles of X and X^T per element, their offsets
@@ -518,7 +523,8 @@ __global__ void k_fin_init(FinArgs F, Scalars S, const double *part_rz, const do
 
 // FP64 residual refresh inside the FP32 PCG: the recursive FP32 residual is
 // replaced by the true one (already in r, z); beta is rescaled so that the
-// next direction is z~ + beta~ p with beta~ = (r~, z~) / (r, z)_{k-1}.
+// next direction is z~ + beta~ p with beta~ = (r~, z~) / (r, z)_{k-1}, or the
+// direction restarts where the recursion had drifted below the true residual.
 __global__ void k_fin_reliable(FinArgs F, Scalars S, const double *part_rz, const double *part_rr, const double *rel,
                                double tol) {
   const int pr = blockIdx.x;
@@ -532,7 +538,11 @@ __global__ void k_fin_reliable(FinArgs F, Scalars S, const double *part_rz, cons
       // residual is not monotone in CG, and a claim just below the tolerance
       // can be refuted again and again)
       if (!S.active[pr] && S.status[pr] == HPSE_OK) S.tol2[pr] = fmax(0.25 * S.tol2[pr], 1e-6 * tol * tol);
-      const double b = (S.active[pr] && S.rz[pr] > 0.0) ? S.beta[pr] * (rz / S.rz[pr]) : 0.0;
+      // a recursive residual that had fallen far below the true one (the
+      // low-precision recursion drifted: a strong preconditioner converges it
+      // within one graph replay) leaves a stale direction: restart (beta = 0)
+      const bool drift = S.rz[pr] < 1e-2 * rz;
+      const double b = (S.active[pr] && S.rz[pr] > 0.0 && !drift) ? S.beta[pr] * (rz / S.rz[pr]) : 0.0;
       S.beta[pr] = isfinite(b) ? b : 0.0;
       S.rz[pr] = rz;
       S.rr[pr] = rr;
@@ -1133,6 +1143,49 @@ static hpse_status bj_products(hpse_mesh *m, const Group &g, const BjArgs &a, co
   return HPSE_OK;
 }
 
+// the group's blocks of a vector, converted (FP32 <-> FP64)
+template <typename TI, typename TO>
+__global__ void k_bj_cvt(BjArgs A, const TI *in, TO *out) {
+  const int item = blockIdx.x;
+  const int ge = item / A.n_rhs, r = item - ge * A.n_rhs;
+  const int64_t base = (int64_t)r * A.ndof + A.dof_off[A.elems[ge]];
+  for (int i = threadIdx.x; i < A.n; i += blockDim.x) out[base + i] = (TO)in[base + i];
+}
+
+// sums over the group's blocks of (a - b)^2 and b^2 (FP64), into acc[0..1]
+__global__ void k_bj_cmp(BjArgs A, const float *a, const double *b, double *acc) {
+  const int item = blockIdx.x;
+  const int ge = item / A.n_rhs, r = item - ge * A.n_rhs;
+  const int64_t base = (int64_t)r * A.ndof + A.dof_off[A.elems[ge]];
+  double d2 = 0.0, b2 = 0.0;
+  for (int i = threadIdx.x; i < A.n; i += blockDim.x) {
+    const double d = (double)a[base + i] - b[base + i];
+    d2 += d * d;
+    b2 += b[base + i] * b[base + i];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+    b2 += __shfl_xor_sync(0xffffffffu, b2, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(acc, d2);
+    atomicAdd(acc + 1, b2);
+  }
+}
+
+// pseudo-random test vector (FP64 and its FP32 rounding) from a hash of the index
+__global__ void k_bj_testvec(int64_t n, double *v64, float *v32) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t h = (uint64_t)i * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+    h ^= h >> 31;
+    h *= 0xBF58476D1CE4E5B9ull;
+    h ^= h >> 29;
+    const double v = (double)(h >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+    v64[i] = v;
+    v32[i] = (float)v;
+  }
+}
+
 // element-block preconditioner for every degree group: PCG mode fuses the
 // update x += alpha p, r -= alpha q and the partials r.r, z.r around z = X^T X r
 template <typename T>
@@ -1146,18 +1199,29 @@ static hpse_status launch_bj_all(hpse_mesh *m, int mode, const PrecArgsT<T> &b, 
     const BjArgs a = bj_args(m, g, b.n_rhs);
     cudaStream_t gs = group_stream(m, gi, s);
     const int items = g.n * b.n_rhs;
+    const T *rin = mode == MODE_PCG ? b.r : b.rin;
     if (mode == MODE_PCG) {
       k_bj_update<T><<<items, 128, 0, gs>>>(a, b.prob, b.alpha, b.x, b.r, b.p, b.q, b.part_rr);
       CK(cudaGetLastError());
-      hpse_status st = bj_products<T>(m, g, a, X, b.r, t, b.zout, gs, m->bj_var[g.W][sizeof(T) == 8 ? 0 : 1]);
-      if (st != HPSE_OK) return st;
-      k_bj_dot<T><<<items, 128, 0, gs>>>(a, b.zout, b.r, b.part_rz);
+      g_launches += 2;
+    }
+    if (sizeof(T) == 4 && m->bj_poor32[g.W]) {
+      // FP32 solve, FP64 factor: convert, apply, convert back
+      k_bj_cvt<T, double><<<items, 128, 0, gs>>>(a, rin, m->bj_r64.as<double>());
+      CK(cudaGetLastError());
+      CK(bj_apply_group<double>(a, m->d_bj64.as<double>(), m->bj_r64.as<double>(), m->bj_t64.as<double>(),
+                                m->bj_z64.as<double>(), gs, m->bj_var[g.W][0]));
+      k_bj_cvt<double, T><<<items, 128, 0, gs>>>(a, m->bj_z64.as<double>(), b.zout);
       CK(cudaGetLastError());
       g_launches += 4;
     } else {
-      hpse_status st = bj_products<T>(m, g, a, X, b.rin, t, b.zout, gs, m->bj_var[g.W][sizeof(T) == 8 ? 0 : 1]);
+      hpse_status st = bj_products<T>(m, g, a, X, rin, t, b.zout, gs, m->bj_var[g.W][sizeof(T) == 8 ? 0 : 1]);
       if (st != HPSE_OK) return st;
       g_launches += 2;
+    }
+    if (mode == MODE_PCG) {
+      k_bj_dot<T><<<items, 128, 0, gs>>>(a, b.zout, b.r, b.part_rz);
+      CK(cudaGetLastError());
     }
   }
   CK(group_join(m, s));
@@ -2939,6 +3003,48 @@ extern "C" hpse_status hpse_setup_block_preconditioner(hpse_mesh *m) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
   }
+  // accuracy of the FP32 factor products, per degree group, on a test vector:
+  // ||z32 - z64|| / ||z64|| > 1e-2 (a block whose triangular factor loses that
+  // much to FP32 rounding, eps32 |X|^T |X| |r| against |X^T X r|) sends the
+  // group's FP32 solves through the FP64 factor
+  {
+    const size_t nvb = std::max<size_t>(nv, 1);
+    DevBuf v64, v32, z64, z32, acc;
+    if (v64.alloc(nvb * sizeof(double)) != cudaSuccess || v32.alloc(nvb * sizeof(float)) != cudaSuccess ||
+        z64.alloc(nvb * sizeof(double)) != cudaSuccess || z32.alloc(nvb * sizeof(float)) != cudaSuccess)
+      return HPSE_ERR_OOM;
+    CK(acc.alloc(2 * sizeof(double)));
+    k_bj_testvec<<<256, 256, 0, s>>>((int64_t)nv, v64.as<double>(), v32.as<float>());
+    CK(cudaGetLastError());
+    ++g_launches;
+    bool any_poor = false;
+    for (size_t gi = 0; gi < m->groups.size(); ++gi) {
+      const Group &g = m->groups[gi];
+      const BjArgs ba = bj_args(m, g, m->n_rhs);
+      CK(bj_apply_group<double>(ba, m->d_bj64.as<double>(), v64.as<double>(), m->bj_t64.as<double>(),
+                                z64.as<double>(), s, m->bj_var[g.W][0]));
+      const hpse_status st = bj_products<float>(m, g, ba, m->d_bj32.as<float>(), v32.as<float>(),
+                                                m->bj_t32.as<float>(), z32.as<float>(), s, m->bj_var[g.W][1]);
+      if (st != HPSE_OK) return st;
+      CK(cudaMemsetAsync(acc.p, 0, 2 * sizeof(double), s));
+      k_bj_cmp<<<g.n * m->n_rhs, 128, 0, s>>>(ba, z32.as<float>(), z64.as<double>(), acc.as<double>());
+      CK(cudaGetLastError());
+      g_launches += 5;
+      double h[2] = {0.0, 0.0};
+      CK(cudaMemcpyAsync(h, acc.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      const double rel = h[1] > 0.0 ? std::sqrt(h[0] / h[1]) : 0.0;
+      m->bj_poor32[g.W] = !(rel <= 1e-2);
+      any_poor = any_poor || m->bj_poor32[g.W];
+      if (verbose())
+        fprintf(stderr, "[hpse] block preconditioner W=%d: FP32 products %.2e of FP64%s\n", g.W, rel,
+                m->bj_poor32[g.W] ? " (FP32 solves use the FP64 factor)" : "");
+    }
+    if (any_poor) {
+      if (!m->bj_r64.p && m->bj_r64.alloc(nvb * sizeof(double)) != cudaSuccess) return HPSE_ERR_OOM;
+      if (!m->bj_z64.p && m->bj_z64.alloc(nvb * sizeof(double)) != cudaSuccess) return HPSE_ERR_OOM;
+    }
+  }
   m->bj_ready = true;
   m->precond_kind = HPSE_PRECOND_BLOCK;
   return HPSE_OK;
@@ -3316,6 +3422,13 @@ static hpse_status solve_reliable(hpse_mesh *m, const hpse_solve_opts *o, double
   // kappa(A) in FP64): the best level reached and the refresh that reached it
   double best = std::numeric_limits<double>::infinity();
   int best_at = 0;
+  // stall of the recursive residual between refreshes (it sits at the working
+  // precision's level, or a poor low-precision preconditioner stops its
+  // descent): no pair's (r, r) has halved below its smallest value in 8
+  // graph replays -> refresh early (the true residual then restarts it, and
+  // the stagnation rule above ends a solve that cannot improve)
+  std::vector<double> rr_min(rr_ref);
+  int stalled = 0;
   while (true) {
     CK(cudaGraphLaunch(exec, s));
     g_launches += per_replay;
@@ -3329,6 +3442,18 @@ static hpse_status solve_reliable(hpse_mesh *m, const hpse_solve_opts *o, double
       if (w.h_flags[i] && w.h_sc[2 * npr + i] <= delta * delta * rr_ref[i]) refresh = true;
     for (int i = 0; i < npr; ++i)
       if (w.h_flags[2 * npr + i] == HPSE_ERR_BREAKDOWN) refresh = true;
+    {
+      bool improved = false;
+      for (int i = 0; i < npr; ++i) {
+        const double rr = w.h_sc[2 * npr + i];
+        if (w.h_flags[i] && rr < 0.5 * rr_min[i]) {
+          rr_min[i] = rr;
+          improved = true;
+        }
+      }
+      stalled = improved ? 0 : stalled + 1;
+      if (stalled >= 8) refresh = true;
+    }
     const bool capped = done >= o->max_iter || updates >= (o->max_sweeps > 0 ? o->max_sweeps : 200);
     double now = 0.0;
     if (deadline > 0)
@@ -3387,7 +3512,8 @@ static hpse_status solve_reliable(hpse_mesh *m, const hpse_solve_opts *o, double
       CK(cudaMemsetAsync(S.status, 0, npr * sizeof(int32_t), s));
       CK(cudaMemcpyAsync(w.h_sc, w.sc.p, (size_t)12 * npr * sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
-      for (int i = 0; i < npr; ++i) rr_ref[i] = w.h_sc[2 * npr + i];
+      for (int i = 0; i < npr; ++i) rr_ref[i] = rr_min[i] = w.h_sc[2 * npr + i];
+      stalled = 0;
     }
   }
   int mx = 0;

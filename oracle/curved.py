@@ -308,6 +308,30 @@ class CurvedDiscretisation:
         err, nrm = self.h1_parts(U, nq)
         return np.sqrt(err / nrm)
 
+    def h1_parts_gll(self, U):
+        """(||u_h - w||_{H^1}^2, ||w||_{H^1}^2) with each element's own
+        (2W+1)^3 GLL rule in lambda times |J| (the rule of the volume term)."""
+        err = nrm = 0.0
+        for e in range(self.E):
+            B0, B1 = tables(self.W[e])["B"][:2]
+            wq = tables(self.W[e])["wq"]
+            u = self.block(U, e)
+            x, K, det, _, _ = self.vol_geom(e)
+            v = eval_tensor(u, B0, B0, B0)
+            va = [eval_tensor(u, *[B1 if b == a else B0 for b in range(3)]) for a in range(3)]
+            w = self.problem.u_exact(x[0], x[1], x[2])
+            gw = self.problem.grad_exact(x[0], x[1], x[2])
+            d2 = (v - w) ** 2
+            n2 = w ** 2
+            for i in range(3):
+                vi = sum(K[..., a, i] * va[a] for a in range(3))
+                d2 = d2 + (vi - gw[i]) ** 2
+                n2 = n2 + gw[i] ** 2
+            wt = wq[:, None, None] * wq[None, :, None] * wq[None, None, :] * det
+            err += float(np.sum(wt * d2))
+            nrm += float(np.sum(wt * n2))
+        return err, nrm
+
     def h1_parts(self, U, nq=20):
         """(||u_h - w||_{H^1}^2, ||w||_{H^1}^2), each element by an nq^3
         Gauss-Legendre rule in lambda times |J|."""

@@ -22,10 +22,12 @@ namespace curved {
 // per volume point: vol [27] = Dx (Dx[k][a] = d x_k / d lambda_a, row-major),
 // D2x [k][pair] with pairs (00, 11, 22, 01, 02, 12).  Writes the general
 // coefficient layout (w |J|, C_11, C_22, C_33, C_12, C_23, C_13, C_1, C_2, C_3,
-// C_0, 0) in FP64 and FP32 and wja = -w |J|; bad[0] = 1 where |J| <= 0 or a
-// value is not finite.  One block per element.
+// C_0, 0) in FP64 and FP32, wja = -w |J|, K (9 per point, K[a][i]) and |J|
+// (for the H^1 norm); bad[0] = 1 where |J| <= 0 or a value is not finite.  One
+// block per element.
 __global__ void k_geom_vol(int64_t nq, const int32_t *elem_W, const int64_t *coef_off, const double *const *qtab,
-                           const double *vol, double *coef64, float *coef32, double *wja, int32_t *bad) {
+                           const double *vol, double *coef64, float *coef32, double *wja, double *Kv, double *detv,
+                           int32_t *bad) {
   const int e = blockIdx.x;
   const int W = elem_W[e], P = W + 1, Q = 2 * W + 1;
   const double *wq = qtab[W] + 2 * Q * P + 2 * Q * Q;
@@ -52,6 +54,8 @@ __global__ void k_geom_vol(int64_t nq, const int32_t *elem_W, const int64_t *coe
         coef32[12 * i + m] = 0.0f;
       }
       wja[i] = 0.0;
+      for (int m = 0; m < 9; ++m) Kv[9 * i + m] = 0.0;
+      detv[i] = 0.0;
       continue;
     }
     double K[3][3];
@@ -64,6 +68,9 @@ __global__ void k_geom_vol(int64_t nq, const int32_t *elem_W, const int64_t *coe
     K[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
     K[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
     K[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+    for (int a = 0; a < 3; ++a)
+      for (int k = 0; k < 3; ++k) Kv[9 * i + 3 * a + k] = K[a][k];
+    detv[i] = det;
     double G[3][3];
     for (int a = 0; a < 3; ++a)
       for (int b = 0; b < 3; ++b) G[a][b] = K[a][0] * K[b][0] + K[a][1] * K[b][1] + K[a][2] * K[b][2];

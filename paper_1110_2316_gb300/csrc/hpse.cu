@@ -202,7 +202,7 @@ struct hpse_mesh {
   bool curved = false, has_geometry = false;
   std::vector<int32_t> cf_q;
   std::vector<int64_t> cf_off, bf_off;
-  DevBuf d_cf_q, d_cf_off, d_bf_off, d_cur_tab, d_cur_ptr, d_cK64, d_cK32, d_cwja;
+  DevBuf d_cf_q, d_cf_off, d_bf_off, d_cur_tab, d_cur_ptr, d_cK64, d_cK32, d_cwja, d_cKv, d_cdet;
   std::vector<int64_t> dof_off, coef_off;
   int64_t ndof = 0, nquad = 0;
   std::vector<int> bface_elem, bface_fi;   // boundary faces
@@ -756,6 +756,8 @@ struct H1Args {
   double hc;
   int32_t n_elem, n_corner;
   const int32_t *cW;
+  // curved elements: K (9 per volume point, K[a][i]) and |J| per point; null otherwise
+  const double *cK, *cdet;
   const double *cw;
 };
 
@@ -815,10 +817,21 @@ __global__ void k_h1(H1Args A) {
         uy += B0[qc * P + k] * T01[o];
         ux += B0[qc * P + k] * T10[o];
       }
-      ux *= geo[0];
-      uy *= geo[1];
-      uz *= geo[2];
-      const double wJ = wq[qa] * wq[qb] * wq[qc] * geo[3];
+      double wJ = wq[qa] * wq[qb] * wq[qc] * geo[3];
+      if (A.cK) {
+        // curved element: the physical gradient through K, the weight w |J|
+        const int64_t pi = A.coef_off[e] + t;
+        const double *K = A.cK + 9 * pi;
+        const double u1 = ux, u2 = uy, u3 = uz;
+        ux = K[0] * u1 + K[3] * u2 + K[6] * u3;
+        uy = K[1] * u1 + K[4] * u2 + K[7] * u3;
+        uz = K[2] * u1 + K[5] * u2 + K[8] * u3;
+        wJ = wq[qa] * wq[qb] * wq[qc] * A.cdet[pi];
+      } else {
+        ux *= geo[0];
+        uy *= geo[1];
+        uz *= geo[2];
+      }
       if (A.ref) {
         double v;
         if (A.hw) {
@@ -2375,13 +2388,15 @@ extern "C" hpse_status hpse_set_geometry(hpse_mesh *m, const double *vol, const 
   if (!m->d_coef32.p || m->d_coef32.bytes != 12 * (size_t)std::max<int64_t>(nq, 1) * sizeof(float))
     CK(m->d_coef32.alloc(12 * (size_t)std::max<int64_t>(nq, 1) * sizeof(float)));
   if (!m->d_cwja.p) CK(m->d_cwja.alloc((size_t)std::max<int64_t>(nq, 1) * sizeof(double)));
+  if (!m->d_cKv.p) CK(m->d_cKv.alloc(9 * (size_t)std::max<int64_t>(nq, 1) * sizeof(double)));
+  if (!m->d_cdet.p) CK(m->d_cdet.alloc((size_t)std::max<int64_t>(nq, 1) * sizeof(double)));
   if (!m->d_cK64.p) CK(m->d_cK64.alloc(9 * (size_t)std::max<int64_t>(nfp, 1) * sizeof(double)));
   if (!m->d_cK32.p) CK(m->d_cK32.alloc(9 * (size_t)std::max<int64_t>(nfp, 1) * sizeof(float)));
   if (m->n_elem > 0) {
     curved::k_geom_vol<<<m->n_elem, 256, 0, s>>>(nq, m->d_elem_W.as<int32_t>(), m->d_coef_off.as<int64_t>(),
                                                  m->d_tabs_ptr.as<const double *>(), vp, m->d_coef64.as<double>(),
                                                  m->d_coef32.as<float>(), m->d_cwja.as<double>(),
-                                                 dbad.as<int32_t>());
+                                                 m->d_cKv.as<double>(), m->d_cdet.as<double>(), dbad.as<int32_t>());
     CK(cudaGetLastError());
     curved::k_geom_face<<<256, 256, 0, s>>>(nfp, fp, m->d_cK64.as<double>(), m->d_cK32.as<float>(),
                                             dbad.as<int32_t>());
@@ -3676,10 +3691,10 @@ extern "C" hpse_status hpse_pcg_solve(hpse_mesh *m, const hpse_solve_opts *o, do
 
 extern "C" hpse_status hpse_h1_error(hpse_mesh *m, const double *u, const double *ref, const double *vq,
                                      const double *gq, double *out, void *stream) {
-  // neighbourhood meshes: the difference of two discrete solutions only;
-  // curved elements: not built (their norm needs K and |J| per point)
-  if (m && m->coord != HPSE_COORD_CARTESIAN && !ref) return HPSE_ERR_INVALID_ARG;
-  if (m && m->curved) return HPSE_ERR_INVALID_ARG;
+  // neighbourhood meshes: the difference of two discrete solutions only
+  // (curved elements: both forms, through K and |J| per point)
+  if (m && m->coord != HPSE_COORD_CARTESIAN && !m->curved && !ref) return HPSE_ERR_INVALID_ARG;
+  if (m && m->curved && !m->has_geometry) return HPSE_ERR_NO_DATA;
   if (!m || !out) return HPSE_ERR_INVALID_ARG;
   if (m->ndof == 0) {
     for (int r = 0; r < m->n_rhs; ++r) out[2 * r] = out[2 * r + 1] = 0.0;
@@ -3715,12 +3730,14 @@ extern "C" hpse_status hpse_h1_error(hpse_mesh *m, const double *u, const double
   A.gq = gq;
   A.part_err = pe.as<double>();
   A.part_nrm = pn.as<double>();
-  A.hw = m->coord != HPSE_COORD_CARTESIAN ? m->d_h1w.as<double>() : nullptr;
+  A.hw = (m->coord != HPSE_COORD_CARTESIAN && !m->curved) ? m->d_h1w.as<double>() : nullptr;
   A.hc = m->coord == HPSE_COORD_VERTEX_EDGE ? 1.0 : 0.0;
   A.n_elem = m->n_elem;
   A.n_corner = m->n_corner;
   A.cW = m->d_cW.as<int32_t>();
   A.cw = m->d_ch1w.as<double>();
+  A.cK = m->curved ? m->d_cKv.as<double>() : nullptr;
+  A.cdet = m->curved ? m->d_cdet.as<double>() : nullptr;
   const int P = Wmax + 1, Q = 2 * Wmax + 1;
   const size_t smem = (size_t)(P * P * P + 2 * Q * P * P + 3 * Q * Q * P) * sizeof(double);
   CK(raise_smem((const void *)k_h1, m->device, (size_t)smem));

@@ -14,6 +14,9 @@ oracle's CurvedDiscretisation.
   residual of the GPU solution; the relative H^1 error of the GPU solution (by
   the oracle) decays from W = 2 to W = 3 and stays within 1e-6 of the error of
   the oracle's own solution.
+* The library's H^1 norm on curved elements (through K and |J| per point):
+  against the exact solution and between two discrete solutions, within 1e-10
+  of the oracle's (the same (2W+1)^3 GLL rule, CurvedDiscretisation.h1_parts_gll).
 * A map with a negative Jacobian is refused (HPSE_ERR_INVALID_ARG).
 """
 import numpy as np
@@ -119,6 +122,44 @@ def test_curved_solve_and_h1_error(api):
         m.close()
     print("H1 errors", errs)
     assert errs[3] < 0.5 * errs[2], errs
+
+
+def test_curved_h1_norm_matches_oracle(api):
+    maps, Ws, nbr, f, g, u, gu = _lprism_case([2, 3, 2, 3, 2, 3])
+    desc = wl.CurvedMeshDesc(maps, Ws, nbr)
+    m = api.Mesh(desc, n_rhs=1, coef_kind=api.COEF_LAPLACE)
+    vol, face, xv, xf = api.curved_geometry_arrays(m, maps)
+    m.set_geometry(vol, face)
+    m.set_data(**api.curved_data_arrays(m, xv, xf, [f], [g]))
+    d = CurvedDiscretisation(CurvedProblem(CurvedMesh(maps, Ws, nbr), f, g, u, gu))
+    rng = np.random.default_rng(12)
+    U = d.nodal_interpolant(u) + 1e-3 * rng.standard_normal(d.ndof)
+    vq = torch.tensor(u(xv[:, 0], xv[:, 1], xv[:, 2]), device="cuda")
+    gq = torch.tensor(np.concatenate([np.asarray(c) * np.ones(len(xv)) for c in gu(xv[:, 0], xv[:, 1], xv[:, 2])]),
+                      device="cuda")
+    h = m.h1_error(torch.tensor(U, device="cuda"), vq=vq, gq=gq)
+    ref = d.h1_parts_gll(U)
+    assert h[0, 0] == pytest.approx(ref[0], rel=1e-10) and h[0, 1] == pytest.approx(ref[1], rel=1e-10)
+    # two discrete solutions: the oracle's exact data replaced by the second one
+    V = d.nodal_interpolant(u)
+    h2 = m.h1_error(torch.tensor(U, device="cuda"), ref=torch.tensor(V, device="cuda"))
+    err, nrm = 0.0, 0.0
+    for e in range(d.E):
+        from oracle.functional import eval_tensor, tables
+        B0, B1 = tables(d.W[e])["B"][:2]
+        wq = tables(d.W[e])["wq"]
+        _, K, det, _, _ = d.vol_geom(e)
+        wt = wq[:, None, None] * wq[None, :, None] * wq[None, None, :] * det
+        for blk, acc in ((d.block(U, e) - d.block(V, e), "err"), (d.block(V, e), "nrm")):
+            v = eval_tensor(blk, B0, B0, B0)
+            va = [eval_tensor(blk, *[B1 if b == a else B0 for b in range(3)]) for a in range(3)]
+            val = v * v + sum(sum(K[..., a, i] * va[a] for a in range(3)) ** 2 for i in range(3))
+            if acc == "err":
+                err += float(np.sum(wt * val))
+            else:
+                nrm += float(np.sum(wt * val))
+    assert h2[0, 0] == pytest.approx(err, rel=1e-10) and h2[0, 1] == pytest.approx(nrm, rel=1e-10)
+    m.close()
 
 
 def test_negative_jacobian_is_refused(api):

@@ -146,3 +146,22 @@ def test_curved_h1_error_decays():
         assert errs[W] < 0.5 * errs[W - 1], errs
     for W in (2, 3, 4):
         assert errs[W] < 5 * ints[W], (errs, ints)
+
+
+def test_h1_parts_gll_equals_the_gauss_rule_on_polynomials():
+    # affine maps, a discrete u of degree W and a polynomial "exact" w of
+    # degree <= W: every H^1 integrand has degree <= 2W, which both the
+    # (2W+1)^3 GLL rule and the 20^3 Gauss rule integrate exactly
+    desc = wl.box_mesh((2, 1, 1), lo=(0.0, 0.0, 0.0), hi=(1.0, 0.5, 0.7), W=3)
+    maps, Ws, nbr = wl.curved_mesh_of_boxes(desc)
+
+    def w(x, y, z):
+        return x * x * y - z ** 3 + 0.5 * x * y * z
+
+    def gw(x, y, z):
+        return (2 * x * y + 0.5 * y * z, x * x + 0.5 * x * z, -3 * z * z + 0.5 * x * y)
+
+    d = CurvedDiscretisation(CurvedProblem(CurvedMesh(maps, np.asarray(Ws), np.asarray(nbr)), w, w, w, gw))
+    U = np.random.default_rng(2).standard_normal(d.ndof)
+    a, b = d.h1_parts_gll(U), d.h1_parts(U, nq=20)
+    assert a[0] == pytest.approx(b[0], rel=1e-12) and a[1] == pytest.approx(b[1], rel=1e-12)

@@ -42,7 +42,7 @@ struct GenLayout {
   static constexpr int T_REGION0 = 6 * Q2P;
   static constexpr int T_NEED = P3 + 6 * FACE_ARR * P2;
   static constexpr int T_REGION = T_REGION0 > T_NEED ? T_REGION0 : T_NEED;
-  static constexpr int TABS = P2 + 12;
+  static constexpr int TABS = P2 + FACE_META_REALS;
   static constexpr int TOTAL = P3 + 3 * QP2 + T_REGION + TABS;
   static constexpr size_t RED_OFF = (((size_t)TOTAL * sizeof(real) + 15) / 16) * 16;
   static constexpr size_t BYTES = RED_OFF + 64 * sizeof(double);
@@ -110,6 +110,8 @@ __global__ void __launch_bounds__(NT, GEN_MINB) k_apply_gen(const ApplyArgs A) {
   constexpr int nt = NT;
 
   for (int t = tid; t < P2; t += nt) stab[t] = c_tab.D[t];
+  FaceMeta *fm = face_meta(stab);
+  if (MODE != MODE_TRANSPOSE && tid < 6) face_meta_fill<COEF_LAPLACE, MODE>(A, e, r, geo_e, fm, tid);
   if (MODE != MODE_TRANSPOSE) {
     if (MODE == MODE_PCG) {
       const double bt = A.beta[A.prob[e] * A.n_rhs + r];
@@ -300,7 +302,7 @@ __global__ void __launch_bounds__(NT, GEN_MINB) k_apply_gen(const ApplyArgs A) {
 
   // faces: those of the Laplacian on box meshes (the operator does not enter)
   if (MODE != MODE_TRANSPOSE && !A.skip_faces)
-    face_phase<COEF_LAPLACE, MODE>(A, e, r, su, sy, sT + P3, stab, geo_e, stab + P2);
+    face_phase<COEF_LAPLACE, MODE>(A, e, r, su, sy, sT + P3, stab, geo_e, fm);
 
   double part = 0.0;
   for (int t = tid; t < P3; t += nt) {

@@ -1,6 +1,8 @@
 // inst_template.cuh -- launchers for one (REAL, WDEG) instantiation of
 // kernels.cuh.  A generated translation unit defines REAL, WDEG,
 // HPSE_REGISTER_NAME (and HPSE_DOUBLE for REAL = double), then includes this.
+#include <vector>
+
 #include "kernels.cuh"
 #include "general.cuh"
 #include "ibp.cuh"
@@ -98,6 +100,12 @@ cudaError_t upload_fn(const double *pk) {
         t.FO[m][q * HPE + j] = (real)(mid ? 0.0 : 0.5 * (b[q * P + j] - b[q * P + P - 1 - j]));
       }
   }
+  for (int i = 0; i < P * HPE; ++i) {
+    t.XE[0][i] = make_float2((float)t.FE[0][i], (float)t.FE[0][i]);
+    t.XE[1][i] = make_float2((float)t.FE[0][i], (float)t.FE[2][i]);
+    t.XO[0][i] = make_float2((float)t.FO[0][i], (float)t.FO[0][i]);
+    t.XO[1][i] = make_float2((float)t.FO[0][i], (float)t.FO[2][i]);
+  }
   const double *pD = pk + o;
   for (int i = 0; i < P2; ++i) t.D[i] = (real)pk[o++];
   for (int i = 0; i < P2; ++i) t.S[i] = (real)pk[o++];
@@ -105,12 +113,30 @@ cudaError_t upload_fn(const double *pk) {
   for (int i = 0; i < P2; ++i) t.MP[i] = (real)pk[o++];
   const double *pK = pk + o;
   for (int i = 0; i < P2; ++i) t.KP[i] = (real)pk[o++];
-  // folded halves of D, D^T, MP, KP for the face phase, formed in FP64
-  for (int m = 0; m < 4; ++m)
+  // folded halves of D, D^T, MP, KP, MP + KP, M1 = D^T MP D, M12 = D^T (MP + KP) D
+  // for the face phase, formed in FP64
+  std::vector<double> M1(P2, 0.0), M12(P2, 0.0);
+  for (int r = 0; r < P; ++r)
+    for (int c = 0; c < P; ++c)
+      for (int i = 0; i < P; ++i)
+        for (int j = 0; j < P; ++j) {
+          const double dd = pD[i * P + r] * pD[j * P + c];
+          M1[r * P + c] += dd * pM[i * P + j];
+          M12[r * P + c] += dd * (pM[i * P + j] + pK[i * P + j]);
+        }
+  for (int m = 0; m < 7; ++m)
     for (int i = 0; i < HPE; ++i)
       for (int j = 0; j < HPE; ++j) {
         auto x = [&](int r, int c) {
-          return m == 0 ? pD[r * P + c] : (m == 1 ? pD[c * P + r] : (m == 2 ? pM[r * P + c] : pK[r * P + c]));
+          switch (m) {
+            case 0: return pD[r * P + c];
+            case 1: return pD[c * P + r];
+            case 2: return pM[r * P + c];
+            case 3: return pK[r * P + c];
+            case 4: return pM[r * P + c] + pK[r * P + c];
+            case 5: return M1[r * P + c];
+            default: return M12[r * P + c];
+          }
         };
         const bool mid = (P & 1) && j == HP;
         t.PF[m][0][i * HPE + j] = (real)(mid ? x(i, j) : 0.5 * (x(i, j) + x(i, P - 1 - j)));

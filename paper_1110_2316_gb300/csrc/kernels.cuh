@@ -336,6 +336,12 @@ __host__ __device__ constexpr bool packed_coef(int c, int stage) {
 #endif
 }
 
+// -div(a grad u) in the transpose mode (rho read from global memory) keeps
+// the scalar stages and rho in registers: the packed form measured slower there
+__host__ __device__ constexpr bool packed_mode(int c, int mode) {
+  return mode != hpse::MODE_TRANSPOSE || c != hpse::COEF_SCALAR;
+}
+
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 // a - b, exactly rounded (a + (-1) b in one FMA)
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
@@ -1373,8 +1379,9 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
     const real sz2c =
         (COEF == COEF_EDGE || COEF == COEF_VERTEX_EDGE) ? sz2 * A.kappa[(int64_t)e * hpse::KAPPA_STRIDE + qa] : sz2;
     // lanes past the last column keep their rho in the spare column Q2
-    std::conditional_t<L::RHO_INPLACE, ColumnRhoT, ColumnRho<L::RHO_SMEM>> rho;
-    if constexpr (L::RHO_INPLACE) rho.bind(sT, l, ok);
+    constexpr bool inplace = L::RHO_INPLACE && packed_mode(COEF, MODE);
+    std::conditional_t<inplace, ColumnRhoT, ColumnRho<L::RHO_SMEM>> rho;
+    if constexpr (inplace) rho.bind(sT, l, ok);
     else rho.bind(srho, ok ? l : Q2);
     if (MODE == MODE_TRANSPOSE) {
 #pragma unroll
@@ -1476,7 +1483,7 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
         __syncwarp();  // scheduling fence (register pressure); reached by all 32 lanes
       }
     }
-    if constexpr (packed_coef(COEF, 8)) {
+    if constexpr (packed_coef(COEF, 8) && packed_mode(COEF, MODE)) {
       // -div(a grad u): (rho, d_x rho) -> (rp, xp) by (B0, B0), (d_y rho,
       // sz2 rho) -> (yp, zp) by (B0, B2), d_z rho by B1 into zp (scalar);
       // Laplacian: (rho, sz2 rho) -> (rp, zp) by (B0, B2)
@@ -1602,7 +1609,7 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
       const real sy2q = (COEF == COEF_VERTEX) ? sy2 * A.kappa[(int64_t)e * hpse::KAPPA_STRIDE + qa] : sy2;
       const real sx2q =
           (COEF == COEF_VERTEX_EDGE) ? sx2 * ((real)1 + A.kappa[(int64_t)e * hpse::KAPPA_STRIDE + qa]) : sx2;
-      if constexpr (packed_coef(COEF, 16)) {
+      if constexpr (packed_coef(COEF, 16) && packed_mode(COEF, MODE)) {
 #define YR_CALL(CI) \
   y_rev_chunk2<COEF, (CI < LS::NC ? CI : 0), LS::NC>(T00, TL, T10, T01, X0, X1, X2, qa, k, ok, sx2q, sy2q)
         HPSE_DISPATCH4(LS::NC, c, YR_CALL);
@@ -1625,7 +1632,7 @@ __global__ void __launch_bounds__(NT, APPLY_MINB) k_apply(const ApplyArgs A) {
       const int c = it / LS::PADL, lp = it - c * LS::PADL;
       const bool ok = lp < P2;
       const int l = ok ? lp : P2 - 1;
-      if constexpr (packed_coef(COEF, 32)) {
+      if constexpr (packed_coef(COEF, 32) && packed_mode(COEF, MODE)) {
 #define XR_CALL(CI) x_rev_chunk2<COEF, (CI < LS::NC ? CI : 0), LS::NC>(X0, X1, X2, sy, l, ok)
         HPSE_DISPATCH4(LS::NC, c, XR_CALL);
 #undef XR_CALL

@@ -25,8 +25,9 @@
 // (face_phase of kernels.cuh), since they do not involve the operator.
 //
 // Design: one CTA per (element, rhs) item like k_apply; every stage is a
-// whole-CTA loop over line jobs, the contractions plain unrolled loops with
-// constant-bank matrix entries (B of c_tab).  The z-stage reads the point
+// whole-CTA loop over line jobs, the contractions unrolled loops with
+// constant-bank matrix entries (B of c_tab), those of the z-stage (most of
+// the multiply-adds) folded into even-odd halves like k_apply's.  The z-stage reads the point
 // coefficients twice per apply (forward, then transpose), from L1 / L2 the
 // second time.  Shared memory: su | X[3] | T[6] | D copy + face scales | reduction;
 // the T region later holds sy and the face scratch.  Instances whose layout
@@ -53,41 +54,47 @@ constexpr int GEN_MINB = sizeof(real) == 8 ? 1 : 2;
 // coefficient stride between consecutive z-points of a column
 constexpr int GEN_CQ = GEN_NC * Q2;
 
-// z-stage helpers of one column (cp: the column's first point coefficients)
-__device__ __forceinline__ void gen_load(const real *col, real *t) {
+// z-stage helpers of one column (cp: the column's first point coefficients).
+// The contractions are folded like k_apply's (even-odd halves of B_n on the
+// symmetric grids): a T line is loaded as its folded halves (e, o), and the
+// transposed contractions of a line accumulate folded (pl, mi) pairs that
+// are unfolded when the line is stored.
+__device__ __forceinline__ void gen_load(const real *col, real *e, real *o) {
+  real v[P];
 #pragma unroll
-  for (int k = 0; k < P; ++k) t[k] = col[k * Q2];
+  for (int k = 0; k < P; ++k) v[k] = col[k * Q2];
+  fold_p(v, e, o);
 }
-__device__ __forceinline__ void gen_store(const real *a, real *col, bool ok) {
+__device__ __forceinline__ void gen_store(const real *pl, const real *mi, real *col, bool ok) {
   if (!ok) return;
 #pragma unroll
-  for (int k = 0; k < P; ++k) col[k * Q2] = a[k];
+  for (int k = 0; k < HPE; ++k) put_p(col, Q2, k, pl[k], mi[k]);
 }
-__device__ __forceinline__ void gen_zero(real *a) {
+__device__ __forceinline__ void gen_zero(real *pl, real *mi) {
 #pragma unroll
-  for (int k = 0; k < P; ++k) a[k] = (real)0;
+  for (int k = 0; k < HPE; ++k) pl[k] = mi[k] = (real)0;
 }
-// rho[q] += C_CS[q] (B_NN t)[q]
+// rho[q] += C_CS[q] (B_NN t)[q], output pairs (q, Q-1-q) from the folded line
 template <int NN, int CS>
-__device__ __forceinline__ void gen_zf(const real *t, real *rho, const real *cp) {
+__device__ __forceinline__ void gen_zf(const real *e, const real *o, real *rho, const real *cp) {
 #pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    real acc = 0;
-#pragma unroll
-    for (int k = 0; k < P; ++k) acc += c_tab.B[NN][q * P + k] * t[k];
-    rho[q] += cp[q * GEN_CQ + CS] * acc;
+  for (int qc = 0; qc <= HQ; ++qc) {
+    real pl = 0, mi = 0;
+    fwd_pm<NN>(e, o, qc, pl, mi);
+    rho[qc] += cp[qc * GEN_CQ + CS] * (pl + mi);
+    if (qc < HQ) rho[Q - 1 - qc] += cp[(Q - 1 - qc) * GEN_CQ + CS] * (pl - mi);
   }
   __syncwarp();  // scheduling fence (register pressure); reached by all 32 lanes
 }
-// a[k] += sum_q B_NN[q][k] C_CS[q] rho[q]
+// (pl, mi)[k] += the folded halves of sum_q B_NN[q][k] C_CS[q] rho[q]
 template <int NN, int CS>
-__device__ __forceinline__ void gen_zr(const real *rho, const real *cp, real *a) {
+__device__ __forceinline__ void gen_zr(const real *rho, const real *cp, real *pl, real *mi) {
 #pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    const real g = cp[q * GEN_CQ + CS] * rho[q];
-#pragma unroll
-    for (int k = 0; k < P; ++k) a[k] += c_tab.B[NN][q * P + k] * g;
+  for (int qc = 0; qc < HQ; ++qc) {
+    const real g0 = cp[qc * GEN_CQ + CS] * rho[qc], g1 = cp[(Q - 1 - qc) * GEN_CQ + CS] * rho[Q - 1 - qc];
+    rev_pair<NN>(g0 + g1, g0 - g1, qc, pl, mi);
   }
+  rev_mid<NN>(cp[HQ * GEN_CQ + CS] * rho[HQ], pl, mi);
   __syncwarp();  // scheduling fence (register pressure); reached by all 32 lanes
 }
 
@@ -195,51 +202,51 @@ __global__ void __launch_bounds__(NT, GEN_MINB) k_apply_gen(const ApplyArgs A) {
     } else {
 #pragma unroll
       for (int q = 0; q < Q; ++q) rho[q] = (real)0;
-      real t[P];
-      gen_load(sT + 0 * Q2P + l, t);
-      gen_zf<0, 10>(t, rho, cp);  // u
-      gen_zf<1, 9>(t, rho, cp);   // u_3
-      gen_zf<2, 3>(t, rho, cp);   // u_33
-      gen_load(sT + 1 * Q2P + l, t);
-      gen_zf<0, 8>(t, rho, cp);   // u_2
-      gen_zf<1, 5>(t, rho, cp);   // u_23
-      gen_load(sT + 2 * Q2P + l, t);
-      gen_zf<0, 2>(t, rho, cp);   // u_22
-      gen_load(sT + 3 * Q2P + l, t);
-      gen_zf<0, 7>(t, rho, cp);   // u_1
-      gen_zf<1, 6>(t, rho, cp);   // u_13
-      gen_load(sT + 4 * Q2P + l, t);
-      gen_zf<0, 4>(t, rho, cp);   // u_12
-      gen_load(sT + 5 * Q2P + l, t);
-      gen_zf<0, 1>(t, rho, cp);   // u_11
+      real te[HPE], to[HPE];
+      gen_load(sT + 0 * Q2P + l, te, to);
+      gen_zf<0, 10>(te, to, rho, cp);  // u
+      gen_zf<1, 9>(te, to, rho, cp);   // u_3
+      gen_zf<2, 3>(te, to, rho, cp);   // u_33
+      gen_load(sT + 1 * Q2P + l, te, to);
+      gen_zf<0, 8>(te, to, rho, cp);   // u_2
+      gen_zf<1, 5>(te, to, rho, cp);   // u_23
+      gen_load(sT + 2 * Q2P + l, te, to);
+      gen_zf<0, 2>(te, to, rho, cp);   // u_22
+      gen_load(sT + 3 * Q2P + l, te, to);
+      gen_zf<0, 7>(te, to, rho, cp);   // u_1
+      gen_zf<1, 6>(te, to, rho, cp);   // u_13
+      gen_load(sT + 4 * Q2P + l, te, to);
+      gen_zf<0, 4>(te, to, rho, cp);   // u_12
+      gen_load(sT + 5 * Q2P + l, te, to);
+      gen_zf<0, 1>(te, to, rho, cp);   // u_11
 #pragma unroll
       for (int q = 0; q < Q; ++q) rho[q] *= cp[q * GEN_CQ];
     }
     // T'_line[k] = sum over its fields of sum_q B_n[q][k] C_c[q] rho[q]
     {
-      real a[P];
-      gen_zero(a);
-      gen_zr<0, 10>(rho, cp, a);
-      gen_zr<1, 9>(rho, cp, a);
-      gen_zr<2, 3>(rho, cp, a);
-      gen_store(a, sT + 0 * Q2P + l, ok);
-      gen_zero(a);
-      gen_zr<0, 8>(rho, cp, a);
-      gen_zr<1, 5>(rho, cp, a);
-      gen_store(a, sT + 1 * Q2P + l, ok);
-      gen_zero(a);
-      gen_zr<0, 2>(rho, cp, a);
-      gen_store(a, sT + 2 * Q2P + l, ok);
-      gen_zero(a);
-      gen_zr<0, 7>(rho, cp, a);
-      gen_zr<1, 6>(rho, cp, a);
-      gen_store(a, sT + 3 * Q2P + l, ok);
-      gen_zero(a);
-      gen_zr<0, 4>(rho, cp, a);
-      gen_store(a, sT + 4 * Q2P + l, ok);
-      gen_zero(a);
-      gen_zr<0, 1>(rho, cp, a);
-      gen_store(a, sT + 5 * Q2P + l, ok);
+      real pl[HPE], mi[HPE];
+      gen_zero(pl, mi);
+      gen_zr<0, 10>(rho, cp, pl, mi);
+      gen_zr<1, 9>(rho, cp, pl, mi);
+      gen_zr<2, 3>(rho, cp, pl, mi);
+      gen_store(pl, mi, sT + 0 * Q2P + l, ok);
+      gen_zero(pl, mi);
+      gen_zr<0, 8>(rho, cp, pl, mi);
+      gen_zr<1, 5>(rho, cp, pl, mi);
+      gen_store(pl, mi, sT + 1 * Q2P + l, ok);
+      gen_zero(pl, mi);
+      gen_zr<0, 2>(rho, cp, pl, mi);
+      gen_store(pl, mi, sT + 2 * Q2P + l, ok);
+      gen_zero(pl, mi);
+      gen_zr<0, 7>(rho, cp, pl, mi);
+      gen_zr<1, 6>(rho, cp, pl, mi);
+      gen_store(pl, mi, sT + 3 * Q2P + l, ok);
+      gen_zero(pl, mi);
+      gen_zr<0, 4>(rho, cp, pl, mi);
+      gen_store(pl, mi, sT + 4 * Q2P + l, ok);
+      gen_zero(pl, mi);
+      gen_zr<0, 1>(rho, cp, pl, mi);
+      gen_store(pl, mi, sT + 5 * Q2P + l, ok);
     }
   }
   __syncthreads();

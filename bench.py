@@ -243,7 +243,16 @@ def cpu_baseline(pb, n_elems, reps=1):
     ndof = reps * sum(d.P[e] ** 3 for e in elems)
     return dict(value=ndof / dt / 1e9, unit="GDOF/s", cores=os.cpu_count(), kind="oracle",
                 sample="oracle operator apply, %d x %d of %d elements (W=%d, 1 rhs), %.1f s" %
-                       (reps, len(elems), d.E, d.W[0], dt))
+                       (reps, len(elems), d.E, d.W[0], dt), seconds=dt)
+
+
+def bench_config(args, ndof):
+    """The workload of the default bench line (both arms)."""
+    return dict(workload="varcoef -div(a grad u)=f, [0,1]^3, %d^3 elements, W=%d, %d RHS, tol 1e-10, "
+                         "FP32 applies + FP64 reliable-update refinement" % (args.n, args.W, args.rhs),
+                n_elem=args.n ** 3, W=args.W, rhs_per_gpu=args.rhs, dof_per_rhs=ndof,
+                l2="working set > L2 (FP32 vectors %.0f MB each)" % (args.rhs * ndof * 4 / 1e6),
+                parallelism="replicas (independent batches per GPU)")
 
 
 def _oracle_task(task):
@@ -295,17 +304,18 @@ def run_reference(args):
     if rank != 0:
         return 0
     pb = wl.varcoef_random_rhs(n=args.n, W=args.W, n_rhs=1)
-    vals = []
+    vals, secs = [], []
     for i in range(args.warmup + args.steps):
         cb = cpu_baseline(pb, args.cpu_sample_elems, 1)
         if i >= args.warmup:
             vals.append(cb["value"])
+            secs.append(cb["seconds"])
     v = float(np.mean(vals))
+    # each step: the oracle's apply of a bounded sample of the workload's elements
     line = dict(metric=METRIC, value=v, unit="GDOF/s", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
-                ms_per_step=None, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
-                data="synthetic", impl="reference",
-                config=dict(workload="varcoef 8x8x8 W=8, oracle operator apply sample", n_elem=args.n ** 3,
-                            W=args.W),
+                ms_per_step=1e3 * float(np.mean(secs)), higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic", impl="reference",
+                config=bench_config(args, args.n ** 3 * (args.W + 1) ** 3),
                 cpu_baseline=dict(value=v, unit="GDOF/s", cores=cb["cores"], kind="oracle", sample=cb["sample"]),
                 e2e=dict(value=v, unit="GDOF/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line))
@@ -1021,11 +1031,7 @@ def main():
             metric=METRIC, value=value, unit="GDOF/s", n_gpus=ws, steps=args.steps, warmup=args.warmup,
             ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
             data="synthetic",
-            config=dict(workload="varcoef -div(a grad u)=f, [0,1]^3, %d^3 elements, W=%d, %d RHS, tol 1e-10, "
-                                 "FP32 applies + FP64 reliable-update refinement" % (args.n, args.W, args.rhs),
-                        n_elem=args.n ** 3, W=args.W, rhs_per_gpu=args.rhs, dof_per_rhs=mesh.ndof,
-                        l2="working set > L2 (FP32 vectors %.0f MB each)" % (n_tot * 4 / 1e6),
-                        parallelism="replicas (independent batches per GPU)"),
+            config=bench_config(args, mesh.ndof),
             solve=dict(gdof_applies_per_s=solve_rate, iterations=reps[-1]["iterations"], refreshes=reps[-1]["sweeps"],
                        applies=reps[-1]["applies"], rel_residual=reps[-1]["rel_residual"],
                        setup_sample_s=t_sample, setup_set_data_s=t_setdata,

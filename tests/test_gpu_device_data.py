@@ -7,8 +7,8 @@
 * A coefficient a <= 0 in device data: HPSE_ERR_INVALID_ARG, after which the
   handle has no data (a solve reports HPSE_ERR_NO_DATA) until valid data is set.
 * Host and device arrays mixed in one call: HPSE_ERR_INVALID_ARG.
-* hpse_apply_residual / hpse_apply_transpose in FP32 against FP64: 1e-5 of the
-  largest value (FP32 unit roundoff 6e-8 times the O(W^4) second-derivative
+* hpse_apply_residual / hpse_apply_transpose in FP32 against FP64, for
+  -div(a grad u) and the Laplacian: 1e-5 of the largest value (FP32 unit roundoff 6e-8 times the O(W^4) second-derivative
   entries at W <= 4), and the transposition identity <S u, z> = <u, S^T z> in
   FP32 to 1e-5 of |S u| |z|.
 """
@@ -118,9 +118,14 @@ def test_mixed_host_and_device_data_rejected(api):
 
 
 @pytest.mark.parametrize("W", [2, 4])
-def test_fp32_residual_and_transpose(api, W):
-    pb = wl.varcoef_manufactured(n=(2, 1, 2), W=W)
-    m = api.Mesh(pb.mesh, n_rhs=1, coef_kind=api.COEF_SCALAR)
+@pytest.mark.parametrize("coef", ["scalar", "laplace"])
+def test_fp32_residual_and_transpose(api, W, coef):
+    if coef == "scalar":
+        pb = wl.varcoef_manufactured(n=(2, 1, 2), W=W)
+        m = api.Mesh(pb.mesh, n_rhs=1, coef_kind=api.COEF_SCALAR)
+    else:
+        pb = wl.poisson_sine(n=(2, 1, 2), W=W)
+        m = api.Mesh(pb.mesh, n_rhs=1, coef_kind=api.COEF_LAPLACE)
     m.set_data(**api.problem_data_arrays(m, pb))
     u64 = torch.tensor(wl.random_dofs(m.ndof, seed=W), device="cuda")
     u32 = u64.float()

@@ -28,6 +28,10 @@ def test_reference_arm_prints_one_contract_line():
     assert line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"] == dict(value=line["value"], unit="GDOF/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0)
     assert line["config"]["W"] == 8 and line["config"]["n_elem"] == 512
+    # the GPU arm's workload config, and the time of the step's sample
+    assert line["config"]["rhs_per_gpu"] == 64 and line["config"]["dof_per_rhs"] == 512 * 9 ** 3
+    assert line["config"]["workload"].startswith("varcoef -div(a grad u)=f")
+    assert line["ms_per_step"] > 0
 
 
 def test_reference_arm_other_ranks_print_nothing():
